@@ -1,0 +1,214 @@
+/*
+ * bem.h -- C ABI of the GB300 FMM-accelerated collocation boundary element
+ * library (Carley, "BEM3D: a free adaptive fast multipole boundary element
+ * library").
+ *
+ * The library computes, on one CUDA device, the two matrix-vector products of
+ * the discrete exterior boundary integral equation (Section 2.1, Eq. 1-3)
+ *
+ *      A phi = B chi,   A = diag(C) - D,   B = -S,   C_i = 1 + sum_j D0_ij,
+ *
+ *      D_ij = sum_m int L_j dG/dn1 dS_m,   S_ij = sum_m int L_j G dS_m,
+ *
+ * with G = 1/(4 pi R) (Laplace, Eq. 1a) or exp(jkR)/(4 pi R) (Helmholtz, Eq.
+ * 1b) and D0 the Laplace double layer, by the adaptive fast multipole method
+ * of Section 3 (octree over vertices, Taylor expansions, convergence-radius
+ * separation), and solves the system by restarted GMRES.  The sign of Eq. 1 is
+ * read as the exterior problem, C phi = int (phi dG/dn1 - G dphi/dn1) dS.
+ *
+ * Conventions for every call:
+ *   - Return value: BEM_OK (0) or a negative BEM_E* code; bem_last_error()
+ *     then returns a message for the calling thread.
+ *   - Host arrays passed in are copied; the caller keeps ownership.
+ *   - Device arrays (x_dev, y_dev, chi_dev, phi_dev) are owned by the caller,
+ *     must be allocated on the plan's device and stay alive until the given
+ *     stream has passed the call.  Work is ordered on that stream
+ *     (cudaStream_t passed as void*; NULL = the legacy default stream).
+ *   - Handles belong to the library until the matching *_destroy call.
+ *   - Real vectors are float64; Helmholtz vectors are complex float64 stored
+ *     as interleaved (re, im) pairs.
+ *   - Elements are counter-clockwise seen from outside (outward normal).
+ *     6-node triangles list corners 0, 1, 2, then the mid-side nodes of
+ *     edges 0-1, 1-2, 2-0.
+ */
+#ifndef BEM_H
+#define BEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BEM_OK 0
+#define BEM_EINVAL (-1)   /* bad argument (message says which) */
+#define BEM_ENOMEM (-2)   /* device or host allocation failed */
+#define BEM_ECUDA (-3)    /* a CUDA call failed (message has the CUDA error) */
+#define BEM_ENOCONV (-4)  /* solver stopped before the tolerance; solution written */
+#define BEM_ETIMEOUT (-5) /* a bounded device wait gave up */
+#define BEM_EBUSY (-6)    /* resource in use */
+
+#define BEM_TRI3 1        /* flat 3-node triangle (first order, Section 2.2) */
+#define BEM_TRI6 2        /* curved 6-node triangle (second order, Section 2.2) */
+
+#define BEM_LAPLACE 0     /* G = 1/(4 pi R), Eq. 1a */
+#define BEM_HELMHOLTZ 1   /* G = exp(jkR)/(4 pi R), Eq. 1b, time factor exp(-j omega t) */
+
+#define BEM_F64 0         /* every stage in float64 */
+#define BEM_MIXED 1       /* near field and expansions in float32, Krylov in float64 */
+
+#define BEM_OP_A 0        /* y = C x - D x  (x indexed by node) */
+#define BEM_OP_B 1        /* y = -S x       (x indexed by chi index) */
+
+typedef struct bem_ctx bem_ctx;
+typedef struct bem_mesh bem_mesh;
+typedef struct bem_plan bem_plan;
+
+/* Fast multipole and quadrature parameters.
+ *   p            expansion order: terms with total degree |alpha|+|beta| <= p
+ *                are kept in the local expansion (Eq. 7); moments to degree p.
+ *   leaf_size    B of Section 3.1: a box holding B or more vertices is split.
+ *   eta          separation factor: two boxes interact through expansions iff
+ *                |x_c1 - x_c2| > eta (r_C1 + r_C2); eta = 1 is Eq. 13.
+ *   max_level    deepest tree level (<= 20).
+ *   leaf_descend 1: a leaf keeps opening non-leaf near-list boxes until each
+ *                entry is separated or a leaf; 0: the whole subtree is near.
+ *   precision    BEM_F64 or BEM_MIXED.
+ *   n_duffy      Gauss-Legendre order of the Duffy self-element rule.
+ *   tau_near     near-singular threshold: |x_i - X_e(1/3,1/3)| < tau h_e.
+ *   max_subdiv   depth limit of the near-singular 4-way subdivision. */
+typedef struct {
+    int p;
+    int leaf_size;
+    double eta;
+    int max_level;
+    int leaf_descend;
+    int precision;
+    int n_duffy;
+    double tau_near;
+    int max_subdiv;
+} bem_fmm_params;
+
+typedef struct {
+    int restart;      /* GMRES restart length (30) */
+    double tol;       /* stop when ||b - A x|| / ||b|| <= tol */
+    int max_iter;     /* total Arnoldi steps allowed */
+} bem_solve_params;
+
+typedef struct {
+    int iters;            /* Arnoldi steps taken */
+    int restarts;         /* true-residual evaluations */
+    double rel_residual;  /* last true relative residual */
+    int status;           /* BEM_OK or BEM_ENOCONV */
+} bem_solve_info;
+
+/* Octree export for parity checks (Sections 3.1, 3.4, 3.6).  Call
+ * bem_plan_tree_sizes() to fill the counts, allocate the arrays on the host,
+ * then bem_plan_export_tree().  Boxes are numbered level by level. */
+typedef struct {
+    int64_t n_boxes, n_near, n_inter, n_nodes, n_elems;
+    double lo[3], side;            /* root cube: lower corner and edge */
+    int32_t *level;                /* [n_boxes] */
+    int64_t *ijk;                  /* [n_boxes][3] integer box coordinates at its level */
+    int32_t *parent;               /* [n_boxes], -1 for the root */
+    int32_t *leaf;                 /* [n_boxes] 1 if leaf */
+    double *centre;                /* [n_boxes][3] */
+    double *radius;                /* [n_boxes] convergence radius r_C (Eq. 12 for parents) */
+    int64_t *near_ptr, *near_idx;  /* CSR near-field lists */
+    int64_t *inter_ptr, *inter_idx;/* CSR interaction lists */
+    int64_t *leaf_of_node;         /* [n_nodes] leaf box of every vertex */
+    int64_t *owner;                /* [n_elems] leaf owning each element (leaf of its node 0) */
+} bem_tree_view;
+
+/* Defaults: p 8, leaf_size 64, eta 2, max_level 20, leaf_descend 1, F64,
+ * n_duffy 12, tau_near 2, max_subdiv 6. */
+void bem_fmm_params_default(bem_fmm_params *params);
+void bem_solve_params_default(bem_solve_params *params);
+
+/* Context on one CUDA device.  Fails with BEM_ECUDA if the device is absent. */
+int bem_ctx_create(int device, bem_ctx **out);
+void bem_ctx_destroy(bem_ctx *ctx);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *bem_last_error(void);
+
+/* Mesh of the surface S (Section 2.2), host side only (ctx may be NULL for a
+ * mesh that is only inspected; bem_plan_create needs a context).
+ * nodes: host float64 [n_nodes][3];
+ * elems: host int32 [n_elems][3 or 6] node indices.  The Neumann data index
+ * space is built here by the sharp-edge rule of Section 2.3: at every node,
+ * element normals within edge_angle_deg of a cluster's first normal share one
+ * chi index.  The potential phi keeps one index per node.
+ * BEM_EINVAL on a bad element type, an out-of-range node index or a
+ * degenerate element. */
+int bem_mesh_create(bem_ctx *ctx, const double *nodes, int64_t n_nodes, const int32_t *elems,
+                    int64_t n_elems, int elem_type, double edge_angle_deg, bem_mesh **out);
+void bem_mesh_destroy(bem_mesh *mesh);
+
+/* n_phi = number of nodes, n_chi = number of Neumann-data indices. */
+int bem_mesh_sizes(const bem_mesh *mesh, int64_t *n_phi, int64_t *n_chi);
+
+/* chi index of every (element, local node): host int32 [n_elems][npe]. */
+int bem_mesh_chi_index(const bem_mesh *mesh, int32_t *elem_local_to_chi);
+
+/* Builds on the device everything the matrix multiplication needs
+ * (Section 3.6, set-up): quadrature geometry, the octree over vertices
+ * (Morton codes, Section 3.1), element ownership, convergence radii
+ * (Section 3.4, Eq. 12), near-field and interaction lists (Section 3.6),
+ * the stored near-field correction for singular and near-singular pairs and
+ * the diagonal C_i.  Blocks until done.  green: BEM_LAPLACE or
+ * BEM_HELMHOLTZ with wavenumber k.  params NULL = defaults. */
+int bem_plan_create(bem_mesh *mesh, int green, double k, const bem_fmm_params *params,
+                    void *cuda_stream, bem_plan **out);
+void bem_plan_destroy(bem_plan *plan);
+
+/* One fast matrix multiplication (Section 3.6, steps 1-4) plus the stored
+ * correction and the diagonal: op BEM_OP_A: y = C x - D x; BEM_OP_B: y = -S x.
+ * x_dev: device [n_phi] (op A) or [n_chi] (op B); y_dev: device [n_phi].
+ * Stream ordered; no host synchronisation. */
+int bem_matvec(bem_plan *plan, int op, const void *x_dev, void *y_dev, void *cuda_stream);
+
+/* Solves A phi = B chi for nrhs right-hand sides: b = B chi by one
+ * matrix multiplication, then restarted GMRES with float64 Arnoldi (CGS2),
+ * Givens rotations and a true residual at every restart.  chi_dev: device
+ * [nrhs][n_chi]; phi_dev: device [nrhs][n_phi] (written).  info: host array
+ * of nrhs entries (may be NULL).  Returns BEM_ENOCONV if any right-hand side
+ * stopped at max_iter; its best iterate is written.  Synchronises the stream
+ * once per restart cycle. */
+int bem_solve(bem_plan *plan, const void *chi_dev, void *phi_dev, int nrhs,
+              const bem_solve_params *params, bem_solve_info *info, void *cuda_stream);
+
+/* Tree export (see bem_tree_view).  Blocks. */
+int bem_plan_tree_sizes(const bem_plan *plan, bem_tree_view *view);
+int bem_plan_export_tree(const bem_plan *plan, bem_tree_view *view);
+
+/* Stored near-field correction (special-rule minus regular-rule integrals of
+ * singular and near-singular pairs) as host COO triplets.  counts[0] = nnz of
+ * the double-layer part (columns: node index), counts[1] = nnz of the
+ * single-layer part (columns: chi index).  Call with NULL arrays to get the
+ * counts.  Values are float64 (complex pairs for Helmholtz). */
+int bem_plan_export_correction(const bem_plan *plan, int64_t *counts, int64_t *rowD, int64_t *colD,
+                               double *valD, int64_t *rowS, int64_t *colS, double *valS);
+
+/* Multipole moments and local expansions left by the last bem_matvec, per
+ * box (level-by-level numbering) and multi-index, unscaled, float64 (complex
+ * pairs for Helmholtz); mnk: host int32 [n_p][3] multi-indices.  Blocks. */
+int bem_plan_export_expansions(const bem_plan *plan, int32_t *mnk, double *moments, double *locals);
+
+/* Diagonal C_i = 1 + sum_j D0_ij (Eq. 2-3) as computed at set-up: host [n_phi]. */
+int bem_plan_diagonal(const bem_plan *plan, double *c);
+
+/* Device memory held by the plan, in bytes. */
+int bem_plan_footprint(const bem_plan *plan, size_t *hbm_bytes);
+
+/* Integer counters of the plan: [0] n_boxes, [1] n_leaves, [2] n_levels,
+ * [3] near-list entries, [4] interaction-list entries, [5] near-field
+ * source-target pairs per matrix multiplication, [6] correction nnz (D),
+ * [7] correction nnz (S), [8] quadrature points, [9] n_p. */
+int bem_plan_stats(const bem_plan *plan, int64_t *stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BEM_H */

@@ -1,0 +1,213 @@
+// Internal declarations of the GB300 BEM/FMM library: plan layout in HBM,
+// error plumbing and small device helpers shared by the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/bem.h"
+
+namespace bem {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+void set_error(const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+
+#define BEM_CUDA(call)                                                      \
+    do {                                                                    \
+        cudaError_t e_ = (call);                                            \
+        if (e_ != cudaSuccess) return ::bem::cuda_fail(e_, #call, __FILE__, __LINE__); \
+    } while (0)
+#define BEM_TRY(call)                                                       \
+    do {                                                                    \
+        int r_ = (call);                                                    \
+        if (r_ != BEM_OK) return r_;                                        \
+    } while (0)
+#define BEM_LAUNCH_CHECK() BEM_CUDA(cudaGetLastError())
+
+constexpr int QBITS = 21;   // Morton bits per axis
+constexpr int PMAX = 16;    // largest supported expansion order
+constexpr int NQ = 7;       // regular quadrature points per element
+
+// ---------------------------------------------------------------------------
+// device buffers owned by a plan
+// ---------------------------------------------------------------------------
+struct Arena {
+    std::vector<void *> ptrs;
+    std::vector<size_t> sizes;
+    size_t bytes = 0;                   // bytes currently held
+    template <class T>
+    int alloc(T **p, size_t n) {
+        *p = nullptr;
+        if (n == 0) n = 1;
+        cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc", __FILE__, __LINE__);
+        ptrs.push_back(*p);
+        sizes.push_back(n * sizeof(T));
+        bytes += n * sizeof(T);
+        return BEM_OK;
+    }
+    void release(void *p) {
+        for (size_t i = 0; i < ptrs.size(); i++)
+            if (ptrs[i] == p && p) {
+                cudaFree(p);
+                ptrs[i] = nullptr;
+                bytes -= sizes[i];
+            }
+    }
+    ~Arena() {
+        for (void *p : ptrs)
+            if (p) cudaFree(p);
+    }
+};
+
+// Multi-index tables for |alpha| <= p, ordered by degree, then m, n descending.
+struct MIndex {
+    int p = 0, np = 0;
+    std::vector<int> m, n, k;
+    std::vector<int> deg_off;          // first index of each degree, size p+2
+    std::vector<int> idx3;             // [(m*(p+1)+n)*(p+1)+k] -> index or -1
+    void init(int p_);
+};
+
+// Tree and plan state (everything device-resident unless named h_*).
+struct Tree {
+    int nlev = 0;                       // number of levels (root = level 0)
+    std::vector<int> lev_off;           // box range of each level, size nlev+1
+    int nbox = 0, nleaf = 0;
+    double lo[3] = {0, 0, 0}, side = 0;
+    // boxes (level-by-level numbering)
+    int *level = nullptr, *ix = nullptr, *iy = nullptr, *iz = nullptr;
+    int *parent = nullptr, *child0 = nullptr, *nchild = nullptr;
+    int *nb = nullptr, *ne = nullptr;   // node range in Morton order
+    int *eb = nullptr, *ee = nullptr;   // element range in owner order
+    double *cx = nullptr, *cy = nullptr, *cz = nullptr, *r = nullptr;
+    int *leaves = nullptr;              // box ids of the leaves
+    int *near_ptr = nullptr, *near_idx = nullptr;
+    int *inter_ptr = nullptr, *inter_idx = nullptr;
+    int64_t n_near = 0, n_inter = 0;
+    // vertices
+    unsigned long long *codes = nullptr; // sorted Morton codes
+    int *node_perm = nullptr;           // Morton position -> node
+    int *node_rank = nullptr;           // node -> Morton position
+    int *leaf_of_node = nullptr;        // node -> leaf box
+    double *tx = nullptr, *ty = nullptr, *tz = nullptr;  // vertices in Morton order
+    // elements, in owner order (sorted by Morton rank of their node 0)
+    int *elem_perm = nullptr;           // sorted position -> element
+    int *el_phi = nullptr, *el_chi = nullptr;  // [E][npe] indices, sorted order
+};
+
+struct Quad {                           // regular 7-point sources, owner order
+    double *x = nullptr, *y = nullptr, *z = nullptr;
+    double *nx = nullptr, *ny = nullptr, *nz = nullptr, *w = nullptr;
+    float *fx = nullptr, *fy = nullptr, *fz = nullptr;   // offsets from the owning leaf centre
+    float *fnx = nullptr, *fny = nullptr, *fnz = nullptr, *fw = nullptr;
+};
+
+struct Correction {                     // CSR by node (row), special - regular
+    int *ptrD = nullptr, *colD = nullptr;
+    int *ptrS = nullptr, *colS = nullptr;
+    double *valD = nullptr, *valS = nullptr;       // complex pairs for Helmholtz
+    float *fvalD = nullptr, *fvalS = nullptr;
+    int64_t nnzD = 0, nnzS = 0;
+};
+
+}  // namespace bem
+
+struct bem_ctx {
+    int device = 0;
+    int sm_count = 0;
+};
+
+struct bem_mesh {
+    bem_ctx *ctx = nullptr;
+    int64_t n_nodes = 0, n_elems = 0, n_chi = 0;
+    int npe = 0, elem_type = 0;
+    double edge_angle = 30.0;
+    std::vector<double> nodes;          // [n][3]
+    std::vector<int32_t> elems;         // [E][npe]
+    std::vector<int32_t> chi;           // [E][npe]
+};
+
+struct bem_plan {
+    bem_mesh *mesh = nullptr;
+    int device = 0, sm_count = 0;
+    int green = BEM_LAPLACE;
+    double k = 0.0;
+    bem_fmm_params prm{};
+    int64_t N = 0, E = 0, Q = 0, nchi = 0;
+    int npe = 0;
+    bem::Arena arena;
+    bem::MIndex mi;
+    bem::Tree t;
+    bem::Quad q;
+    bem::Correction corr;
+    // device copies of mesh data (original order)
+    double *nodes = nullptr;            // [N][3]
+    int *elems = nullptr, *chi = nullptr;
+    // multi-index tables on the device
+    int *d_m = nullptr, *d_n = nullptr, *d_k = nullptr, *d_idx3 = nullptr;
+    double *d_binom = nullptr;          // [(PMAX+1)^2]
+    double *d_fact = nullptr;           // [2*PMAX+2]
+    // work buffers of one matrix multiplication
+    double *f = nullptr;                // quadrature strengths [Q] (x2 for complex)
+    double *M = nullptr, *L = nullptr;  // [nbox][np] scaled moments / locals (x2 complex)
+    double *ytmp = nullptr;             // [N] far + near regular sums (x2 complex)
+    double *C = nullptr;                // diagonal [N]
+    float *fM = nullptr, *fL = nullptr, *ff = nullptr;   // mixed-precision copies
+    const void **xptr = nullptr;        // device slot: input vector of the next matvec
+    void **yptr = nullptr;              // device slot: output vector
+    int *skip = nullptr;                // device flag: kernels return at once when set
+    // graphs
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    cudaStream_t capture_stream = nullptr;
+    // counters
+    int64_t near_pairs = 0;
+    int last_op = -1;
+    // GMRES workspace
+    double *V = nullptr, *H = nullptr, *gs = nullptr, *w = nullptr, *xk = nullptr, *bvec = nullptr;
+    double *scal = nullptr;             // device scalars
+    int *istate = nullptr;              // device ints: [0] converged flag, [1] steps in cycle
+    int gm_restart = 0;
+    cudaGraphExec_t cycle_graph = nullptr;
+    ~bem_plan();
+};
+
+namespace bem {
+// stages (each returns BEM_OK or an error code)
+int build_tree(bem_plan *P, cudaStream_t s);
+int build_geometry(bem_plan *P, cudaStream_t s);
+int build_radii_lists(bem_plan *P, cudaStream_t s);
+int build_correction(bem_plan *P, cudaStream_t s);
+int alloc_fmm(bem_plan *P);
+int enqueue_matvec(bem_plan *P, int op, int green, double k, cudaStream_t s);
+int set_slots(bem_plan *P, const void *x, void *y, cudaStream_t s);
+int enqueue_matvec_raw(bem_plan *P, int op, int green, double k, int with_diag, cudaStream_t s);
+int compute_diagonal(bem_plan *P, cudaStream_t s);
+int solve(bem_plan *P, const void *chi, void *phi, int nrhs, const bem_solve_params *sp,
+          bem_solve_info *info, cudaStream_t s);
+int64_t mesh_chi_index(const double *nodes, int64_t nn, const int32_t *elems, int64_t ne, int npe,
+                       double angle_deg, int32_t *chi);
+// radix sort of (key, value) pairs, stable, ascending in the low `bits` bits of key
+int radix_sort_pairs(unsigned long long *keys, int *vals, unsigned long long *tmpk, int *tmpv,
+                     int n, int bits, unsigned int *hist, int nblk_cap, cudaStream_t s);
+int scan_exclusive(const int *in, int *out, int n, int *total_dev, cudaStream_t s);
+}  // namespace bem
+
+#ifdef __CUDACC__
+// ---------------------------------------------------------------------------
+// device helpers: FP64 with explicit rounding (no FMA contraction) where the
+// tree, radii and pair classification must follow a fixed operation order
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double dist3_rn(double ax, double ay, double az, double bx, double by,
+                                           double bz) {
+    double dx = __dsub_rn(ax, bx), dy = __dsub_rn(ay, by), dz = __dsub_rn(az, bz);
+    return __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+}
+#endif

@@ -1,0 +1,820 @@
+// One fast matrix multiplication (Section 3.6, steps 1-4) on the device:
+//
+//   P2Q  quadrature-point strengths f_q = w_q J_q sum_a L_a(xi_q) x_idx(e,a)
+//   P2M  leaf moments I_alpha = sum_q f_q (x_q - c)^alpha            (Eq. 6, monopoles)
+//        or sum_q f_q n_q . grad (x_q - c)^alpha                       (dipoles)
+//   M2M  coefficient shift child -> parent                            (Eq. 8)
+//   M2L  local expansion from the interaction list                     (Eq. 7)
+//   L2L  expansion shift parent -> child, with binomials               (Eq. 9)
+//   L2P  local expansion at every vertex of a leaf, fused with
+//   P2P  the regular-rule sum over the elements of the near-field boxes
+//   then the stored special-pair correction and the diagonal C.
+//
+// Moments and locals are stored scaled by powers of the box edge h:
+// Ms_alpha = I_alpha / h^|alpha|, Ls_beta = F_beta h^|beta|, so that every
+// shift factor is an exact power of two and float32 storage stays in range.
+// Green's-function derivatives come from Tausch's recursions (Section 3.3)
+// evaluated per interaction pair at r / h_t.
+//
+// Templates: R = double (BEM_F64) or float (BEM_MIXED); C = 1 (real, Laplace)
+// or 2 (complex, Helmholtz); DL selects dipole (op A) or monopole (op B)
+// sources.
+#include <cmath>
+
+#include "bem_internal.cuh"
+
+namespace bem {
+
+__constant__ double c_Lq[2][NQ][6];   // shape values at the 7 rule points (tri3, tri6)
+
+struct Tabs {
+    const int *m, *n, *k, *idx3;
+    const double *binom, *fact;
+    int p, np;
+};
+
+struct TreeView {
+    const int *level, *ix, *iy, *iz, *parent, *child0, *nchild, *nb, *ne, *eb, *ee, *leaves;
+    const int *near_ptr, *near_idx, *inter_ptr, *inter_idx, *node_perm;
+    const double *cx, *cy, *cz, *tx, *ty, *tz;
+    double side;
+};
+
+struct QuadView {
+    const double *x, *y, *z, *nx, *ny, *nz, *w;
+    const float *fx, *fy, *fz, *fnx, *fny, *fnz, *fw;
+};
+
+template <class R> struct Vec { R v[2]; };
+
+__device__ __forceinline__ int deg_of(int m, int n, int k) { return m + n + k; }
+
+// ---------------------------------------------------------------------------
+// P2Q
+// ---------------------------------------------------------------------------
+template <class R, int C>
+__global__ void k_p2q(int Q, int npe, const int *__restrict__ el_idx, const double *__restrict__ w,
+                      const void *const *__restrict__ xslot, R *__restrict__ f, const int *__restrict__ skip) {
+    if (skip && *skip) return;
+    int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= Q) return;
+    const double *x = (const double *)*xslot;
+    int i = o / NQ, q = o - i * NQ, t6 = npe == 6;
+    double acc[C];
+#pragma unroll
+    for (int c = 0; c < C; c++) acc[c] = 0.0;
+    for (int a = 0; a < npe; a++) {
+        double L = c_Lq[t6][q][a];
+        int j = el_idx[(size_t)i * npe + a];
+#pragma unroll
+        for (int c = 0; c < C; c++) acc[c] += L * x[(size_t)j * C + c];
+    }
+    double ww = w[o];
+#pragma unroll
+    for (int c = 0; c < C; c++) f[(size_t)o * C + c] = (R)(ww * acc[c]);
+}
+
+// ---------------------------------------------------------------------------
+// P2M: one block per leaf, threads over multi-indices, sources in batches of 32
+// ---------------------------------------------------------------------------
+constexpr int P2M_T = 128, P2M_B = 32, P2M_SLOTS = (969 + P2M_T - 1) / P2M_T;
+
+template <class R, int C, bool DL>
+__global__ void __launch_bounds__(P2M_T) k_p2m(int nleaf, Tabs tb, TreeView tv, QuadView qv, const R *__restrict__ f,
+                                               R *__restrict__ M, const int *__restrict__ skip) {
+    if (skip && *skip) return;
+    const int li = blockIdx.x;
+    if (li >= nleaf) return;
+    const int b = tv.leaves[li];
+    const int p = tb.p, np = tb.np, tid = threadIdx.x;
+    __shared__ R pw[3][PMAX + 1][P2M_B];
+    __shared__ R sf[P2M_B][C];
+    __shared__ R sn[3][P2M_B];
+    const double h = scalbn(tv.side, -tv.level[b]);
+    const R hinv = (R)(1.0 / h);
+    const double c0 = tv.cx[b], c1 = tv.cy[b], c2 = tv.cz[b];
+    int am[P2M_SLOTS], an[P2M_SLOTS], ak[P2M_SLOTS];
+    R acc[P2M_SLOTS][C];
+#pragma unroll
+    for (int s = 0; s < P2M_SLOTS; s++) {
+        int a = tid + s * P2M_T;
+        am[s] = a < np ? tb.m[a] : 0;
+        an[s] = a < np ? tb.n[a] : 0;
+        ak[s] = a < np ? tb.k[a] : 0;
+#pragma unroll
+        for (int c = 0; c < C; c++) acc[s][c] = (R)0;
+    }
+    const int q0 = tv.eb[b] * NQ, q1 = tv.ee[b] * NQ;
+    for (int base = q0; base < q1; base += P2M_B) {
+        const int nb = min(P2M_B, q1 - base);
+        __syncthreads();
+        if (tid < 3 * P2M_B) {
+            int pt = tid % P2M_B, ax = tid / P2M_B;
+            R d = (R)0;
+            if (pt < nb) {
+                int o = base + pt;
+                if constexpr (sizeof(R) == sizeof(double)) {
+                    double xx = ax == 0 ? qv.x[o] - c0 : (ax == 1 ? qv.y[o] - c1 : qv.z[o] - c2);
+                    d = (R)(xx / h);
+                } else {
+                    // float path: offsets from the owning leaf (this box) centre
+                    R xx = ax == 0 ? (R)qv.fx[o] : (ax == 1 ? (R)qv.fy[o] : (R)qv.fz[o]);
+                    d = xx * hinv;
+                }
+            }
+            R v = (R)1;
+            for (int e = 0; e <= p; e++) {
+                pw[ax][e][pt] = v;
+                v *= d;
+            }
+        } else if (tid < 3 * P2M_B + P2M_B) {
+            int pt = tid - 3 * P2M_B;
+            int o = base + pt;
+#pragma unroll
+            for (int c = 0; c < C; c++) sf[pt][c] = pt < nb ? f[(size_t)o * C + c] : (R)0;
+            if (DL) {
+                if constexpr (sizeof(R) == sizeof(double)) {
+                    sn[0][pt] = pt < nb ? (R)qv.nx[o] : (R)0;
+                    sn[1][pt] = pt < nb ? (R)qv.ny[o] : (R)0;
+                    sn[2][pt] = pt < nb ? (R)qv.nz[o] : (R)0;
+                } else {
+                    sn[0][pt] = pt < nb ? (R)qv.fnx[o] : (R)0;
+                    sn[1][pt] = pt < nb ? (R)qv.fny[o] : (R)0;
+                    sn[2][pt] = pt < nb ? (R)qv.fnz[o] : (R)0;
+                }
+            }
+        }
+        __syncthreads();
+        for (int pt = 0; pt < nb; pt++) {
+#pragma unroll
+            for (int s = 0; s < P2M_SLOTS; s++) {
+                if (tid + s * P2M_T >= np) break;
+                const int m = am[s], n = an[s], k = ak[s];
+                R val;
+                if (!DL) {
+                    val = pw[0][m][pt] * pw[1][n][pt] * pw[2][k][pt];
+                } else {
+                    val = (R)0;
+                    if (m) val += (R)m * sn[0][pt] * pw[0][m - 1][pt] * pw[1][n][pt] * pw[2][k][pt];
+                    if (n) val += (R)n * sn[1][pt] * pw[0][m][pt] * pw[1][n - 1][pt] * pw[2][k][pt];
+                    if (k) val += (R)k * sn[2][pt] * pw[0][m][pt] * pw[1][n][pt] * pw[2][k - 1][pt];
+                    val *= hinv;
+                }
+#pragma unroll
+                for (int c = 0; c < C; c++) acc[s][c] += val * sf[pt][c];
+            }
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < P2M_SLOTS; s++) {
+        int a = tid + s * P2M_T;
+        if (a < np)
+#pragma unroll
+            for (int c = 0; c < C; c++) M[((size_t)b * np + a) * C + c] = acc[s][c];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// M2M (Eq. 8) for the parents of one level; child offset is +-h_child/2 per
+// axis, i.e. +-1/4 of the parent edge:
+//   Ms'_a = sum_{b<=a} C(a,b) s^b 2^-(|a|+|b|) Ms_{a-b}
+// ---------------------------------------------------------------------------
+constexpr int TR_T = 128, TR_SLOTS = (969 + TR_T - 1) / TR_T;
+
+template <class R, int C>
+__global__ void __launch_bounds__(TR_T) k_m2m(int off, int cnt, Tabs tb, TreeView tv, R *__restrict__ M,
+                                              const int *__restrict__ skip) {
+    if (skip && *skip) return;
+    extern __shared__ unsigned char smem_raw[];
+    const int b = off + blockIdx.x;
+    if (blockIdx.x >= cnt || tv.nchild[b] == 0) return;
+    const int p = tb.p, np = tb.np, tid = threadIdx.x, P1 = p + 1;
+    R *sM = (R *)smem_raw;                                   // [np][C]
+    int *sidx = (int *)(sM + np * C);                        // [(p+1)^3]
+    double *sbin = (double *)(((uintptr_t)(sidx + P1 * P1 * P1) + 15) & ~(uintptr_t)15);   // [(p+1)^2]
+    for (int t = tid; t < P1 * P1 * P1; t += TR_T) sidx[t] = tb.idx3[t];
+    for (int t = tid; t < P1 * P1; t += TR_T) sbin[t] = tb.binom[(t / P1) * (PMAX + 1) + t % P1];
+    R acc[TR_SLOTS][C];
+#pragma unroll
+    for (int s = 0; s < TR_SLOTS; s++)
+#pragma unroll
+        for (int c = 0; c < C; c++) acc[s][c] = (R)0;
+    for (int ch = tv.child0[b]; ch < tv.child0[b] + tv.nchild[b]; ch++) {
+        __syncthreads();
+        for (int t = tid; t < np * C; t += TR_T) sM[t] = M[(size_t)ch * np * C + t];
+        __syncthreads();
+        const int sx = (tv.ix[ch] & 1) ? 1 : -1, sy = (tv.iy[ch] & 1) ? 1 : -1, sz = (tv.iz[ch] & 1) ? 1 : -1;
+#pragma unroll
+        for (int s = 0; s < TR_SLOTS; s++) {
+            int a = tid + s * TR_T;
+            if (a >= np) break;
+            const int m = tb.m[a], n = tb.n[a], k = tb.k[a], da = m + n + k;
+            for (int q = 0; q <= m; q++) {
+                const double cq = sbin[m * P1 + q] * ((sx < 0 && (q & 1)) ? -1.0 : 1.0);
+                for (int r = 0; r <= n; r++) {
+                    const double cr = cq * sbin[n * P1 + r] * ((sy < 0 && (r & 1)) ? -1.0 : 1.0);
+                    for (int t = 0; t <= k; t++) {
+                        const double ct = cr * sbin[k * P1 + t] * ((sz < 0 && (t & 1)) ? -1.0 : 1.0);
+                        const R coef = (R)scalbn(ct, -(da + q + r + t));
+                        const int src = sidx[((m - q) * P1 + (n - r)) * P1 + (k - t)];
+#pragma unroll
+                        for (int c = 0; c < C; c++) acc[s][c] += coef * sM[src * C + c];
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < TR_SLOTS; s++) {
+        int a = tid + s * TR_T;
+        if (a < np)
+#pragma unroll
+            for (int c = 0; c < C; c++) M[((size_t)b * np + a) * C + c] = acc[s][c];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// L2L (Eq. 9 with binomials) for the boxes of one level:
+//   Ls'_b += sum_{g: |b|+|g|<=p} C(b+g, b) s^g 2^-(2|g|+|b|) Ls_{b+g}
+// ---------------------------------------------------------------------------
+template <class R, int C>
+__global__ void __launch_bounds__(TR_T) k_l2l(int off, int cnt, Tabs tb, TreeView tv, R *__restrict__ L,
+                                              const int *__restrict__ skip) {
+    if (skip && *skip) return;
+    extern __shared__ unsigned char smem_raw[];
+    const int b = off + blockIdx.x;
+    if (blockIdx.x >= cnt) return;
+    const int par = tv.parent[b];
+    const int p = tb.p, np = tb.np, tid = threadIdx.x, P1 = p + 1;
+    R *sL = (R *)smem_raw;
+    int *sidx = (int *)(sL + np * C);
+    double *sbin = (double *)(((uintptr_t)(sidx + P1 * P1 * P1) + 15) & ~(uintptr_t)15);
+    for (int t = tid; t < P1 * P1 * P1; t += TR_T) sidx[t] = tb.idx3[t];
+    for (int t = tid; t < P1 * P1; t += TR_T) sbin[t] = tb.binom[(t / P1) * (PMAX + 1) + t % P1];
+    for (int t = tid; t < np * C; t += TR_T) sL[t] = L[(size_t)par * np * C + t];
+    __syncthreads();
+    const int sx = (tv.ix[b] & 1) ? 1 : -1, sy = (tv.iy[b] & 1) ? 1 : -1, sz = (tv.iz[b] & 1) ? 1 : -1;
+#pragma unroll
+    for (int s = 0; s < TR_SLOTS; s++) {
+        int a = tid + s * TR_T;
+        if (a >= np) break;
+        const int m = tb.m[a], n = tb.n[a], k = tb.k[a], db = m + n + k;
+        R acc[C];
+#pragma unroll
+        for (int c = 0; c < C; c++) acc[c] = (R)0;
+        for (int q = 0; q + m <= p; q++) {
+            const double cq = sbin[(m + q) * P1 + m] * ((sx < 0 && (q & 1)) ? -1.0 : 1.0);
+            for (int r = 0; q + r + m + n <= p; r++) {
+                const double cr = cq * sbin[(n + r) * P1 + n] * ((sy < 0 && (r & 1)) ? -1.0 : 1.0);
+                for (int t = 0; q + r + t + db <= p; t++) {
+                    const double ct = cr * sbin[(k + t) * P1 + k] * ((sz < 0 && (t & 1)) ? -1.0 : 1.0);
+                    const R coef = (R)scalbn(ct, -(2 * (q + r + t) + db));
+                    const int src = sidx[((m + q) * P1 + (n + r)) * P1 + (k + t)];
+#pragma unroll
+                    for (int c = 0; c < C; c++) acc[c] += coef * sL[src * C + c];
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < C; c++) L[((size_t)b * np + a) * C + c] += acc[c];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// M2L (Eq. 7), SIMT: one block per target box, every interaction-list source
+// in turn.  For a pair with r = c_t - c_s, rho = r / h_t and khat = k h_t:
+//   D[g]   = d^g Ghat(rho) by Tausch's recursions (Section 3.3),
+//   mh[a]  = (-1)^|a| (h_s/h_t)^|a| Ms_s[a] / a!,
+//   acc[b] += sum_a D[a+b] mh[a];  finally Ls_t[b] = acc[b] / (h_t b!).
+// ---------------------------------------------------------------------------
+template <class R, int C>
+struct M2LShared {
+    // layout offsets inside dynamic shared memory
+    static size_t bytes(int p, int np) {
+        int P1 = p + 1;
+        size_t s = 0;
+        s += sizeof(int) * P1 * P1 * P1;           // idx3
+        s += sizeof(int) * 3 * np;                 // m n k
+        s = (s + 15) & ~(size_t)15;
+        s += sizeof(R) * (size_t)(p + 2) * 2;      // G^(h), complex pairs
+        s += sizeof(R) * (size_t)np * C * 3;       // two Tausch buffers + mh
+        return s + 64;
+    }
+};
+
+template <class R, int C>
+__device__ __forceinline__ void cmul_acc(R *acc, const R *d, const R *m) {
+    if (C == 1) {
+        acc[0] += d[0] * m[0];
+    } else {
+        acc[0] += d[0] * m[0] - d[1] * m[1];
+        acc[1] += d[0] * m[1] + d[1] * m[0];
+    }
+}
+
+template <class R, int C>
+__global__ void __launch_bounds__(TR_T) k_m2l(int nbox, Tabs tb, TreeView tv, double kwave, const R *__restrict__ M,
+                                              R *__restrict__ L, const int *__restrict__ skip) {
+    if (skip && *skip) return;
+    extern __shared__ unsigned char smem_raw[];
+    const int t = blockIdx.x;
+    if (t >= nbox) return;
+    const int p = tb.p, np = tb.np, tid = threadIdx.x, P1 = p + 1;
+    int *sidx = (int *)smem_raw;
+    int *sm = sidx + P1 * P1 * P1, *sn = sm + np, *sk = sn + np;
+    R *Gh = (R *)(((uintptr_t)(sk + np) + 15) & ~(uintptr_t)15);  // [(p+2)][2]
+    R *bufA = Gh + (p + 2) * 2, *bufB = bufA + np * C, *mh = bufB + np * C;
+    for (int u = tid; u < P1 * P1 * P1; u += TR_T) sidx[u] = tb.idx3[u];
+    for (int u = tid; u < np; u += TR_T) { sm[u] = tb.m[u]; sn[u] = tb.n[u]; sk[u] = tb.k[u]; }
+    const double ht = scalbn(tv.side, -tv.level[t]);
+    R acc[TR_SLOTS][C];
+#pragma unroll
+    for (int s = 0; s < TR_SLOTS; s++)
+#pragma unroll
+        for (int c = 0; c < C; c++) acc[s][c] = (R)0;
+    const int i0 = tv.inter_ptr[t], i1 = tv.inter_ptr[t + 1];
+    for (int it = i0; it < i1; it++) {
+        const int src = tv.inter_idx[it];
+        const double rx = (tv.cx[t] - tv.cx[src]) / ht, ry = (tv.cy[t] - tv.cy[src]) / ht,
+                     rz = (tv.cz[t] - tv.cz[src]) / ht;
+        const R rho[3] = {(R)rx, (R)ry, (R)rz};
+        const int dlev = tv.level[t] - tv.level[src];                    // h_s / h_t = 2^dlev
+        __syncthreads();
+        if (tid == 0) {
+            // G^(h), h = 0..p (Tausch): Laplace G^(h+1) = -(2h+1) G^(h) / rho^2;
+            // Helmholtz adds -khat^2 G^(h-1) / rho^2 with G^(-1) = -j e^{j khat rho} / (4 pi khat).
+            double r2 = rx * rx + ry * ry + rz * rz, r1 = sqrt(r2);
+            const double inv4pi = 0.25 / M_PI;
+            if (C == 1) {
+                double g = inv4pi / r1;
+                for (int h = 0; h <= p; h++) {
+                    Gh[2 * h] = (R)g;
+                    Gh[2 * h + 1] = (R)0;
+                    g = -(2.0 * h + 1.0) * g / r2;
+                }
+            } else {
+                double kh = kwave * ht, sn_, cs_;
+                sincos(kh * r1, &sn_, &cs_);
+                double g0r = cs_ * inv4pi / r1, g0i = sn_ * inv4pi / r1;
+                double gmr = sn_ * inv4pi / kh, gmi = -cs_ * inv4pi / kh;   // -j e / (4 pi kh)
+                double pr = gmr, pi = gmi, cr = g0r, ci = g0i;
+                for (int h = 0; h <= p; h++) {
+                    Gh[2 * h] = (R)cr;
+                    Gh[2 * h + 1] = (R)ci;
+                    double nr = -((2.0 * h + 1.0) * cr + kh * kh * pr) / r2;
+                    double ni = -((2.0 * h + 1.0) * ci + kh * kh * pi) / r2;
+                    pr = cr; pi = ci; cr = nr; ci = ni;
+                }
+            }
+        }
+        // scaled, signed, factorial-divided source moments
+        for (int u = tid; u < np; u += TR_T) {
+            const int d = sm[u] + sn[u] + sk[u];
+            const double fa = tb.fact[sm[u]] * tb.fact[sn[u]] * tb.fact[sk[u]];
+            const double sc = ((d & 1) ? -1.0 : 1.0) * scalbn(1.0, dlev * d) / fa;
+#pragma unroll
+            for (int c = 0; c < C; c++) mh[u * C + c] = (R)sc * M[((size_t)src * np + u) * C + c];
+        }
+        __syncthreads();
+        // Tausch's three-step scheme: tables of d^g G^(h), |g| <= p - h, h = p .. 0
+        R *up = bufA, *cur = bufB;
+        if (tid == 0) {
+            up[0] = Gh[2 * p];
+            if (C == 2) up[1] = Gh[2 * p + 1];
+        }
+        __syncthreads();
+        for (int h = p - 1; h >= 0; h--) {
+            const int top = p - h;
+            const int cnt = (top + 1) * (top + 2) * (top + 3) / 6;   // entries of degree <= top
+            for (int u = tid; u < cnt; u += TR_T) {
+                const int m = sm[u], n = sn[u], k = sk[u];
+                R v[C];
+                if (m + n + k == 0) {
+#pragma unroll
+                    for (int c = 0; c < C; c++) v[c] = Gh[2 * h + c];
+                } else {
+                    int ax = m > 0 ? 0 : (n > 0 ? 1 : 2);
+                    int g = ax == 0 ? m : (ax == 1 ? n : k);
+                    int m1 = m - (ax == 0), n1 = n - (ax == 1), k1 = k - (ax == 2);
+                    int i1 = sidx[(m1 * P1 + n1) * P1 + k1];
+#pragma unroll
+                    for (int c = 0; c < C; c++) v[c] = rho[ax] * up[i1 * C + c];
+                    if (g > 1) {
+                        int m2 = m1 - (ax == 0), n2 = n1 - (ax == 1), k2 = k1 - (ax == 2);
+                        int i2 = sidx[(m2 * P1 + n2) * P1 + k2];
+#pragma unroll
+                        for (int c = 0; c < C; c++) v[c] += (R)(g - 1) * up[i2 * C + c];
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < C; c++) cur[u * C + c] = v[c];
+            }
+            __syncthreads();
+            R *sw = up; up = cur; cur = sw;
+        }
+        // contraction (the derivative table is in `up`)
+#pragma unroll
+        for (int s = 0; s < TR_SLOTS; s++) {
+            const int bb = tid + s * TR_T;
+            if (bb >= np) break;
+            const int bm = sm[bb], bn = sn[bb], bk = sk[bb], db = bm + bn + bk;
+            const int na = (p - db + 1) * (p - db + 2) * (p - db + 3) / 6;
+            for (int a = 0; a < na; a++) {
+                const int g = sidx[((sm[a] + bm) * P1 + (sn[a] + bn)) * P1 + (sk[a] + bk)];
+                cmul_acc<R, C>(acc[s], up + g * C, mh + a * C);
+            }
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < TR_SLOTS; s++) {
+        const int bb = tid + s * TR_T;
+        if (bb < np) {
+            const double fb = tb.fact[tb.m[bb]] * tb.fact[tb.n[bb]] * tb.fact[tb.k[bb]];
+            const R sc = (R)(1.0 / (ht * fb));
+#pragma unroll
+            for (int c = 0; c < C; c++) L[((size_t)t * np + bb) * C + c] = acc[s][c] * sc;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// near field (regular rule over the near-list boxes) fused with L2P
+// ---------------------------------------------------------------------------
+constexpr int NF_T = 256, NF_TGT = 64, NF_SL = NF_T / NF_TGT, NF_TILE = 256;
+
+template <class R, int C, bool DL>
+__device__ __forceinline__ void pair_kernel(R rx, R ry, R rz, R nx, R ny, R nz, const R *fv, R kw, R *acc) {
+    const R r2 = rx * rx + ry * ry + rz * rz;
+    R inv;
+    if constexpr (sizeof(R) == sizeof(double)) inv = (R)rsqrt((double)r2);
+    else inv = (R)rsqrtf((float)r2);
+    if (C == 1) {
+        if (DL) acc[0] += fv[0] * (rx * nx + ry * ny + rz * nz) * inv * inv * inv;
+        else acc[0] += fv[0] * inv;
+    } else {
+        const R R1 = r2 * inv;
+        R sn, cs;
+        if constexpr (sizeof(R) == sizeof(double)) sincos((double)(kw * R1), (double *)&sn, (double *)&cs);
+        else sincosf((float)(kw * R1), (float *)&sn, (float *)&cs);
+        R gr, gi;
+        if (DL) {
+            const R kr = kw * R1, rn = (rx * nx + ry * ny + rz * nz) * inv * inv * inv;
+            gr = (cs + kr * sn) * rn;
+            gi = (sn - kr * cs) * rn;
+        } else {
+            gr = cs * inv;
+            gi = sn * inv;
+        }
+        acc[0] += gr * fv[0] - gi * fv[1];
+        acc[1] += gr * fv[1] + gi * fv[0];
+    }
+}
+
+template <class R, int C, bool DL>
+__global__ void __launch_bounds__(NF_T) k_near(int nleaf, Tabs tb, TreeView tv, QuadView qv, double kwave,
+                                               const R *__restrict__ f, const R *__restrict__ L,
+                                               double *__restrict__ ytmp, const int *__restrict__ skip) {
+    if (skip && *skip) return;
+    const int li = blockIdx.x;
+    if (li >= nleaf) return;
+    const int b = tv.leaves[li];
+    const int tid = threadIdx.x, tt = tid % NF_TGT, sl = tid / NF_TGT;
+    const int p = tb.p, np = tb.np;
+    __shared__ R sx[NF_TILE], sy[NF_TILE], sz[NF_TILE], snx[NF_TILE], sny[NF_TILE], snz[NF_TILE];
+    __shared__ R sf[NF_TILE][C];
+    __shared__ double red[NF_T][C];
+    const double cbx = tv.cx[b], cby = tv.cy[b], cbz = tv.cz[b];
+    const double h = scalbn(tv.side, -tv.level[b]);
+    const R kw = (R)kwave;
+    for (int t0 = tv.nb[b]; t0 < tv.ne[b]; t0 += NF_TGT) {
+        const int tk = t0 + tt;
+        const bool active = tk < tv.ne[b];
+        // target position: absolute (F64) or offset from this leaf's centre (F32)
+        double txd = active ? tv.tx[tk] : cbx, tyd = active ? tv.ty[tk] : cby, tzd = active ? tv.tz[tk] : cbz;
+        double acc[C];
+#pragma unroll
+        for (int c = 0; c < C; c++) acc[c] = 0.0;
+        for (int u = tv.near_ptr[b]; u < tv.near_ptr[b + 1]; u++) {
+            const int s = tv.near_idx[u];
+            const int q0 = tv.eb[s] * NQ, q1 = tv.ee[s] * NQ;
+            R tx, ty, tz;
+            if constexpr (sizeof(R) == sizeof(double)) {
+                tx = (R)txd; ty = (R)tyd; tz = (R)tzd;
+            } else {
+                // r = (c_b - c_s) + (t - c_b) - (q - c_s), each part small
+                tx = (R)(cbx - tv.cx[s]) + (R)(txd - cbx);
+                ty = (R)(cby - tv.cy[s]) + (R)(tyd - cby);
+                tz = (R)(cbz - tv.cz[s]) + (R)(tzd - cbz);
+            }
+            R part[C];
+#pragma unroll
+            for (int c = 0; c < C; c++) part[c] = (R)0;
+            for (int base = q0; base < q1; base += NF_TILE) {
+                const int nt = min(NF_TILE, q1 - base);
+                __syncthreads();
+                if (tid < nt) {
+                    const int o = base + tid;
+                    if constexpr (sizeof(R) == sizeof(double)) {
+                        sx[tid] = (R)qv.x[o]; sy[tid] = (R)qv.y[o]; sz[tid] = (R)qv.z[o];
+                        if (DL) { snx[tid] = (R)qv.nx[o]; sny[tid] = (R)qv.ny[o]; snz[tid] = (R)qv.nz[o]; }
+                    } else {
+                        sx[tid] = (R)qv.fx[o]; sy[tid] = (R)qv.fy[o]; sz[tid] = (R)qv.fz[o];
+                        if (DL) { snx[tid] = (R)qv.fnx[o]; sny[tid] = (R)qv.fny[o]; snz[tid] = (R)qv.fnz[o]; }
+                    }
+#pragma unroll
+                    for (int c = 0; c < C; c++) sf[tid][c] = f[(size_t)o * C + c];
+                }
+                __syncthreads();
+                if (active)
+                    for (int j = sl; j < nt; j += NF_SL)
+                        pair_kernel<R, C, DL>(tx - sx[j], ty - sy[j], tz - sz[j], DL ? snx[j] : (R)0,
+                                              DL ? sny[j] : (R)0, DL ? snz[j] : (R)0, sf[j], kw, part);
+            }
+#pragma unroll
+            for (int c = 0; c < C; c++) acc[c] += (double)part[c];
+        }
+        // local expansion at the target: sum_b Ls_b ((x - c)/h)^b, slices split b
+        double loc[C];
+#pragma unroll
+        for (int c = 0; c < C; c++) loc[c] = 0.0;
+        if (active) {
+            const R dx = (R)((txd - cbx) / h), dy = (R)((tyd - cby) / h), dz = (R)((tzd - cbz) / h);
+            R px[PMAX + 1], py[PMAX + 1], pz[PMAX + 1];
+            px[0] = py[0] = pz[0] = (R)1;
+            for (int e = 1; e <= p; e++) {
+                px[e] = px[e - 1] * dx;
+                py[e] = py[e - 1] * dy;
+                pz[e] = pz[e - 1] * dz;
+            }
+            for (int a = sl; a < np; a += NF_SL) {
+                const R mono = px[tb.m[a]] * py[tb.n[a]] * pz[tb.k[a]];
+#pragma unroll
+                for (int c = 0; c < C; c++) loc[c] += (double)(mono * L[((size_t)b * np + a) * C + c]);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < C; c++) red[tid][c] = acc[c] * (0.25 / M_PI) + loc[c];
+        __syncthreads();
+        if (sl == 0 && active) {
+            double s[C];
+#pragma unroll
+            for (int c = 0; c < C; c++) s[c] = red[tid][c];
+            for (int u = 1; u < NF_SL; u++)
+#pragma unroll
+                for (int c = 0; c < C; c++) s[c] += red[tid + u * NF_TGT][c];
+            const int node = tv.node_perm[tk];
+#pragma unroll
+            for (int c = 0; c < C; c++) ytmp[(size_t)node * C + c] = s[c];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// correction SpMV + diagonal: one warp per node row
+//   op A: y = C x - (ytmp + K_D x);  op B: y = -(ytmp + K_S x)
+// ---------------------------------------------------------------------------
+template <class RV, int C, bool OPA>
+__global__ void k_combine(int N, const int *__restrict__ ptr, const int *__restrict__ col, const RV *__restrict__ val,
+                          const double *__restrict__ Cdiag, const double *__restrict__ ytmp,
+                          const void *const *__restrict__ xslot, void *const *__restrict__ yslot,
+                          const int *__restrict__ skip) {
+    if (skip && *skip) return;
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (w >= N) return;
+    const double *x = (const double *)*xslot;
+    double *y = (double *)*yslot;
+    double s[C];
+#pragma unroll
+    for (int c = 0; c < C; c++) s[c] = 0.0;
+    for (int q = ptr[w] + lane; q < ptr[w + 1]; q += 32) {
+        const int j = col[q];
+        if (C == 1) {
+            s[0] += (double)val[q] * x[j];
+        } else {
+            const double vr = (double)val[2 * (size_t)q], vi = (double)val[2 * (size_t)q + 1];
+            const double xr = x[2 * (size_t)j], xi = x[2 * (size_t)j + 1];
+            s[0] += vr * xr - vi * xi;
+            s[C - 1] += vr * xi + vi * xr;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < C; c++)
+        for (int off = 16; off; off >>= 1) s[c] += __shfl_xor_sync(0xffffffffu, s[c], off);
+    if (lane == 0) {
+#pragma unroll
+        for (int c = 0; c < C; c++) {
+            const double tot = ytmp[(size_t)w * C + c] + s[c];
+            y[(size_t)w * C + c] = OPA ? Cdiag[w] * x[(size_t)w * C + c] - tot : -tot;
+        }
+    }
+}
+
+// C_i = 1 + (regular Laplace double layer of phi = 1) + (correction row sum)
+__global__ void k_finish_diag(int N, const double *__restrict__ ytmp, double *Cdiag) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) Cdiag[i] = 1.0 + ytmp[i] + Cdiag[i];
+}
+
+__global__ void k_fill(int64_t n, double v, double *a) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = v;
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+void MIndex::init(int p_) {
+    p = p_;
+    np = (p + 1) * (p + 2) * (p + 3) / 6;
+    m.clear(); n.clear(); k.clear();
+    idx3.assign((size_t)(p + 1) * (p + 1) * (p + 1), -1);
+    deg_off.assign(p + 2, 0);
+    int c = 0;
+    for (int h = 0; h <= p; h++) {
+        deg_off[h] = c;
+        for (int a = h; a >= 0; a--)
+            for (int b = h - a; b >= 0; b--) {
+                int cc = h - a - b;
+                m.push_back(a); n.push_back(b); k.push_back(cc);
+                idx3[((size_t)a * (p + 1) + b) * (p + 1) + cc] = c++;
+            }
+    }
+    deg_off[p + 1] = c;
+}
+
+static Tabs tabs_of(const bem_plan *P) {
+    return Tabs{P->d_m, P->d_n, P->d_k, P->d_idx3, P->d_binom, P->d_fact, P->mi.p, P->mi.np};
+}
+
+static TreeView view_of(const bem_plan *P) {
+    const Tree &t = P->t;
+    return TreeView{t.level, t.ix, t.iy, t.iz, t.parent, t.child0, t.nchild, t.nb, t.ne, t.eb, t.ee, t.leaves,
+                    t.near_ptr, t.near_idx, t.inter_ptr, t.inter_idx, t.node_perm, t.cx, t.cy, t.cz,
+                    t.tx, t.ty, t.tz, t.side};
+}
+
+static QuadView quad_of(const bem_plan *P) {
+    const Quad &q = P->q;
+    return QuadView{q.x, q.y, q.z, q.nx, q.ny, q.nz, q.w, q.fx, q.fy, q.fz, q.fnx, q.fny, q.fnz, q.fw};
+}
+
+static size_t tr_smem(int p, int np, size_t rbytes, int C) {
+    int P1 = p + 1;
+    size_t s = rbytes * np * C + sizeof(int) * P1 * P1 * P1;
+    s = (s + 15) & ~(size_t)15;
+    return s + sizeof(double) * P1 * P1 + 16;
+}
+
+int alloc_fmm(bem_plan *P) {
+    Arena &A = P->arena;
+    MIndex &mi = P->mi;
+    mi.init(P->prm.p);
+    const int np = mi.np, nbox = P->t.nbox, C = P->green == BEM_HELMHOLTZ ? 2 : 1;
+    BEM_TRY(A.alloc(&P->d_m, np));
+    BEM_TRY(A.alloc(&P->d_n, np));
+    BEM_TRY(A.alloc(&P->d_k, np));
+    BEM_TRY(A.alloc(&P->d_idx3, mi.idx3.size()));
+    BEM_CUDA(cudaMemcpy(P->d_m, mi.m.data(), sizeof(int) * np, cudaMemcpyHostToDevice));
+    BEM_CUDA(cudaMemcpy(P->d_n, mi.n.data(), sizeof(int) * np, cudaMemcpyHostToDevice));
+    BEM_CUDA(cudaMemcpy(P->d_k, mi.k.data(), sizeof(int) * np, cudaMemcpyHostToDevice));
+    BEM_CUDA(cudaMemcpy(P->d_idx3, mi.idx3.data(), sizeof(int) * mi.idx3.size(), cudaMemcpyHostToDevice));
+    std::vector<double> fact(2 * PMAX + 2), binom((PMAX + 1) * (PMAX + 1), 0.0);
+    fact[0] = 1.0;
+    for (int i = 1; i < (int)fact.size(); i++) fact[i] = fact[i - 1] * i;
+    for (int a = 0; a <= PMAX; a++)
+        for (int b = 0; b <= a; b++) binom[a * (PMAX + 1) + b] = std::round(fact[a] / (fact[b] * fact[a - b]));
+    BEM_TRY(A.alloc(&P->d_fact, fact.size()));
+    BEM_TRY(A.alloc(&P->d_binom, binom.size()));
+    BEM_CUDA(cudaMemcpy(P->d_fact, fact.data(), sizeof(double) * fact.size(), cudaMemcpyHostToDevice));
+    BEM_CUDA(cudaMemcpy(P->d_binom, binom.data(), sizeof(double) * binom.size(), cudaMemcpyHostToDevice));
+    // shape values at the rule points
+    double Lq[2][NQ][6] = {};
+    {
+        const double q = std::sqrt(15.0);
+        const double a = (6.0 - q) / 21.0, b = (9.0 + 2.0 * q) / 21.0;
+        const double c = (6.0 + q) / 21.0, d = (9.0 - 2.0 * q) / 21.0;
+        const double S[7] = {1.0 / 3.0, a, b, a, c, d, c}, T[7] = {1.0 / 3.0, a, a, b, c, c, d};
+        for (int r = 0; r < NQ; r++) {
+            double l0 = 1.0 - S[r] - T[r], l1 = S[r], l2 = T[r];
+            Lq[0][r][0] = l0; Lq[0][r][1] = l1; Lq[0][r][2] = l2;
+            Lq[1][r][0] = l0 * (2 * l0 - 1); Lq[1][r][1] = l1 * (2 * l1 - 1); Lq[1][r][2] = l2 * (2 * l2 - 1);
+            Lq[1][r][3] = 4 * l0 * l1; Lq[1][r][4] = 4 * l1 * l2; Lq[1][r][5] = 4 * l2 * l0;
+        }
+    }
+    BEM_CUDA(cudaMemcpyToSymbol(c_Lq, Lq, sizeof(Lq)));
+    const bool mx = P->prm.precision == BEM_MIXED;
+    if (mx) {
+        BEM_TRY(A.alloc(&P->ff, (size_t)P->Q * C));
+        BEM_TRY(A.alloc(&P->fM, (size_t)nbox * np * C));
+        BEM_TRY(A.alloc(&P->fL, (size_t)nbox * np * C));
+    } else {
+        BEM_TRY(A.alloc(&P->f, (size_t)P->Q * C));
+        BEM_TRY(A.alloc(&P->M, (size_t)nbox * np * C));
+        BEM_TRY(A.alloc(&P->L, (size_t)nbox * np * C));
+    }
+    BEM_TRY(A.alloc(&P->ytmp, (size_t)P->N * C));
+    BEM_TRY(A.alloc(&P->xptr, 2));
+    BEM_TRY(A.alloc(&P->yptr, 2));
+    // kernels with large dynamic shared memory
+    const size_t big = 200 * 1024;
+    cudaFuncSetAttribute(k_m2l<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big);
+    cudaFuncSetAttribute(k_m2l<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big);
+    cudaFuncSetAttribute(k_m2l<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big);
+    cudaFuncSetAttribute(k_m2l<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big);
+    cudaFuncSetAttribute(k_m2m<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big);
+    cudaFuncSetAttribute(k_m2m<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big);
+    cudaFuncSetAttribute(k_m2m<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big);
+    cudaFuncSetAttribute(k_m2m<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big);
+    cudaFuncSetAttribute(k_l2l<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big);
+    cudaFuncSetAttribute(k_l2l<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big);
+    cudaFuncSetAttribute(k_l2l<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big);
+    cudaFuncSetAttribute(k_l2l<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big);
+    BEM_LAUNCH_CHECK();
+    return BEM_OK;
+}
+
+template <class R, int C>
+static int run_fmm(bem_plan *P, int op, double kwave, R *f, R *M, R *L, cudaStream_t s) {
+    const Tabs tb = tabs_of(P);
+    const TreeView tv = view_of(P);
+    const QuadView qv = quad_of(P);
+    const Tree &t = P->t;
+    const int np = tb.np, p = tb.p;
+    const int *sk = P->skip;
+    const int *el = op == BEM_OP_A ? t.el_phi : t.el_chi;
+    const int Q = (int)P->Q;
+    k_p2q<R, C><<<(Q + 255) / 256, 256, 0, s>>>(Q, P->npe, el, P->q.w, P->xptr, f, sk);
+    if (op == BEM_OP_A) k_p2m<R, C, true><<<t.nleaf, P2M_T, 0, s>>>(t.nleaf, tb, tv, qv, f, M, sk);
+    else k_p2m<R, C, false><<<t.nleaf, P2M_T, 0, s>>>(t.nleaf, tb, tv, qv, f, M, sk);
+    BEM_LAUNCH_CHECK();
+    const size_t trs = tr_smem(p, np, sizeof(R), C);
+    for (int l = t.nlev - 2; l >= 0; l--) {
+        int off = t.lev_off[l], cnt = t.lev_off[l + 1] - off;
+        k_m2m<R, C><<<cnt, TR_T, trs, s>>>(off, cnt, tb, tv, M, sk);
+    }
+    BEM_LAUNCH_CHECK();
+    k_m2l<R, C><<<t.nbox, TR_T, M2LShared<R, C>::bytes(p, np), s>>>(t.nbox, tb, tv, kwave, M, L, sk);
+    BEM_LAUNCH_CHECK();
+    for (int l = 1; l < t.nlev; l++) {
+        int off = t.lev_off[l], cnt = t.lev_off[l + 1] - off;
+        k_l2l<R, C><<<cnt, TR_T, trs, s>>>(off, cnt, tb, tv, L, sk);
+    }
+    BEM_LAUNCH_CHECK();
+    if (op == BEM_OP_A) k_near<R, C, true><<<t.nleaf, NF_T, 0, s>>>(t.nleaf, tb, tv, qv, kwave, f, L, P->ytmp, sk);
+    else k_near<R, C, false><<<t.nleaf, NF_T, 0, s>>>(t.nleaf, tb, tv, qv, kwave, f, L, P->ytmp, sk);
+    BEM_LAUNCH_CHECK();
+    return BEM_OK;
+}
+
+// Enqueues one product on stream s.  The input and output vectors are read
+// from the device slots P->xptr[0] / P->yptr[0].  with_diag = 0 leaves the
+// regular far + near sums in P->ytmp (used for the diagonal).
+int enqueue_matvec_raw(bem_plan *P, int op, int green, double kwave, int with_diag, cudaStream_t s) {
+    const int C = green == BEM_HELMHOLTZ ? 2 : 1;
+    const bool mx = P->prm.precision == BEM_MIXED;
+    if (!mx) {
+        if (C == 1) BEM_TRY((run_fmm<double, 1>(P, op, kwave, P->f, P->M, P->L, s)));
+        else BEM_TRY((run_fmm<double, 2>(P, op, kwave, P->f, P->M, P->L, s)));
+    } else {
+        if (C == 1) BEM_TRY((run_fmm<float, 1>(P, op, kwave, P->ff, P->fM, P->fL, s)));
+        else BEM_TRY((run_fmm<float, 2>(P, op, kwave, P->ff, P->fM, P->fL, s)));
+    }
+    if (!with_diag) return BEM_OK;
+    const int N = (int)P->N;
+    const Correction &K = P->corr;
+    const int blocks = (N * 32 + 255) / 256;
+#define BEM_COMBINE(RV, VD, VS)                                                                                 \
+    if (op == BEM_OP_A) {                                                                                       \
+        if (C == 1) k_combine<RV, 1, true><<<blocks, 256, 0, s>>>(N, K.ptrD, K.colD, VD, P->C, P->ytmp, P->xptr, P->yptr, P->skip); \
+        else k_combine<RV, 2, true><<<blocks, 256, 0, s>>>(N, K.ptrD, K.colD, VD, P->C, P->ytmp, P->xptr, P->yptr, P->skip);       \
+    } else {                                                                                                    \
+        if (C == 1) k_combine<RV, 1, false><<<blocks, 256, 0, s>>>(N, K.ptrS, K.colS, VS, P->C, P->ytmp, P->xptr, P->yptr, P->skip); \
+        else k_combine<RV, 2, false><<<blocks, 256, 0, s>>>(N, K.ptrS, K.colS, VS, P->C, P->ytmp, P->xptr, P->yptr, P->skip);       \
+    }
+    if (mx) { BEM_COMBINE(float, K.fvalD, K.fvalS) } else { BEM_COMBINE(double, K.valD, K.valS) }
+#undef BEM_COMBINE
+    BEM_LAUNCH_CHECK();
+    return BEM_OK;
+}
+
+// Diagonal: C_i = 1 + sum_j D0_ij with D0 the Laplace double layer.  The
+// correction row sums are already in P->C; one regular Laplace double-layer
+// product on phi = 1 adds the rest.
+int compute_diagonal(bem_plan *P, cudaStream_t s) {
+    const int N = (int)P->N;
+    double *ones = nullptr;
+    BEM_TRY(P->arena.alloc(&ones, N));
+    k_fill<<<(N + 255) / 256, 256, 0, s>>>(N, 1.0, ones);
+    BEM_TRY(set_slots(P, ones, nullptr, s));
+    // a Helmholtz plan still evaluates the Laplace kernel here: run the real
+    // product on the (complex-sized) buffers with C = 1
+    BEM_TRY(enqueue_matvec_raw(P, BEM_OP_A, BEM_LAPLACE, 0.0, 0, s));
+    k_finish_diag<<<(N + 255) / 256, 256, 0, s>>>(N, P->ytmp, P->C);
+    BEM_LAUNCH_CHECK();
+    BEM_CUDA(cudaStreamSynchronize(s));
+    P->arena.release(ones);
+    return BEM_OK;
+}
+
+}  // namespace bem

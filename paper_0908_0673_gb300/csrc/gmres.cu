@@ -1,0 +1,352 @@
+// Restarted GMRES on A phi = b (b = B chi from one product), device resident:
+// float64 Arnoldi with classical Gram-Schmidt applied twice (CGS2), Givens
+// rotations on the Hessenberg column, and the true residual b - A x at every
+// restart.  Vectors are real or complex (interleaved pairs).  A device flag
+// set by the rotation step makes every later kernel of the cycle a no-op once
+// the estimated residual reaches the tolerance, so a whole cycle is enqueued
+// (or replayed as one captured graph) and the host synchronises once per
+// cycle.
+#include <cmath>
+#include <vector>
+
+#include "bem_internal.cuh"
+
+namespace bem {
+
+constexpr int GM_T = 256;
+constexpr int GM_BLK = 304;     // partial-sum blocks (2 per SM on a 152-SM part)
+
+// partial[i][blk][c] = sum over this block's rows of conj(V_i) w, i <= j
+template <int C>
+__global__ void k_mdot(int n, int nv, const double *__restrict__ V, size_t ld, const double *__restrict__ w,
+                       double *__restrict__ partial, const int *__restrict__ skip) {
+    if (skip && *skip) return;
+    __shared__ double red[GM_T][C];
+    const int tid = threadIdx.x;
+    for (int i = 0; i < nv; i++) {
+        double s[C];
+#pragma unroll
+        for (int c = 0; c < C; c++) s[c] = 0.0;
+        const double *v = V + (size_t)i * ld;
+        for (int r = blockIdx.x * GM_T + tid; r < n; r += GM_BLK * GM_T) {
+            if (C == 1) {
+                s[0] += v[r] * w[r];
+            } else {
+                double vr = v[2 * (size_t)r], vi = v[2 * (size_t)r + 1], wr = w[2 * (size_t)r], wi = w[2 * (size_t)r + 1];
+                s[0] += vr * wr + vi * wi;
+                s[C - 1] += vr * wi - vi * wr;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < C; c++) red[tid][c] = s[c];
+        __syncthreads();
+        for (int off = GM_T / 2; off; off >>= 1) {
+            if (tid < off)
+#pragma unroll
+                for (int c = 0; c < C; c++) red[tid][c] += red[tid + off][c];
+            __syncthreads();
+        }
+        if (tid == 0)
+#pragma unroll
+            for (int c = 0; c < C; c++) partial[((size_t)i * GM_BLK + blockIdx.x) * C + c] = red[0][c];
+        __syncthreads();
+    }
+}
+
+// out[i] (+)= sum_blk partial[i][blk], one warp per i; fixed order
+template <int C>
+__global__ void k_mdot_final(int nv, const double *__restrict__ partial, double *out, int accumulate,
+                             const int *__restrict__ skip) {
+    if (skip && *skip) return;
+    const int i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
+    if (i >= nv) return;
+    double s[C];
+#pragma unroll
+    for (int c = 0; c < C; c++) s[c] = 0.0;
+    for (int b = lane; b < GM_BLK; b += 32)
+#pragma unroll
+        for (int c = 0; c < C; c++) s[c] += partial[((size_t)i * GM_BLK + b) * C + c];
+#pragma unroll
+    for (int c = 0; c < C; c++)
+        for (int off = 16; off; off >>= 1) s[c] += __shfl_xor_sync(0xffffffffu, s[c], off);
+    if (lane == 0)
+#pragma unroll
+        for (int c = 0; c < C; c++) out[(size_t)i * C + c] = (accumulate ? out[(size_t)i * C + c] : 0.0) + s[c];
+}
+
+// w -= sum_{i<nv} h_i V_i   (h from the latest Gram-Schmidt pass)
+template <int C>
+__global__ void k_orth_update(int n, int nv, const double *__restrict__ V, size_t ld, const double *__restrict__ h,
+                              double *w, const int *__restrict__ skip) {
+    if (skip && *skip) return;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    double a[C];
+#pragma unroll
+    for (int c = 0; c < C; c++) a[c] = w[(size_t)r * C + c];
+    for (int i = 0; i < nv; i++) {
+        const double *v = V + (size_t)i * ld;
+        if (C == 1) {
+            a[0] -= h[i] * v[r];
+        } else {
+            double hr = h[2 * i], hi = h[2 * i + 1], vr = v[2 * (size_t)r], vi = v[2 * (size_t)r + 1];
+            a[0] -= hr * vr - hi * vi;
+            a[C - 1] -= hr * vi + hi * vr;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < C; c++) w[(size_t)r * C + c] = a[c];
+}
+
+// out = sum of |v|^2 partials
+template <int C>
+__global__ void k_nrm2_partial(int n, const double *__restrict__ v, double *partial, const int *__restrict__ skip) {
+    if (skip && *skip) return;
+    __shared__ double red[GM_T];
+    double s = 0.0;
+    for (int r = blockIdx.x * GM_T + threadIdx.x; r < n * C; r += GM_BLK * GM_T) s += v[r] * v[r];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = GM_T / 2; off; off >>= 1) {
+        if (threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void k_nrm2_final(const double *__restrict__ partial, double *out, const int *__restrict__ skip) {
+    if (skip && *skip) return;
+    double s = 0.0;
+    for (int b = threadIdx.x; b < GM_BLK; b += 32) s += partial[b];
+    for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (threadIdx.x == 0) *out = sqrt(s);
+}
+
+// y = a * x  (a = 1 / *den), used for V_{j+1} = w / ||w|| and V_0 = r / beta
+__global__ void k_scale(int n, const double *__restrict__ x, const double *__restrict__ den, double *y,
+                        const int *__restrict__ skip) {
+    if (skip && *skip) return;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const double d = *den;
+    y[r] = d > 0.0 ? x[r] / d : 0.0;
+}
+
+// r = b - r  (r holds A x on entry)
+__global__ void k_resid(int n, const double *__restrict__ b, double *r) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) r[i] = b[i] - r[i];
+}
+
+struct GmState {
+    // scalars: [0] ||b||, [1] beta, [2] |g_{j+1}| / ||b||, [3] tol, [4] ||w||
+    double *sc;
+    int *st;        // [0] converged-in-cycle flag, [1] steps done in cycle
+    double *H;      // [(m+1)][m] complex pairs
+    double *cs, *sn, *g, *y;
+    double *hcol;   // [m+1] first Gram-Schmidt pass coefficients
+    double *hcol2;  // [m+1] second pass coefficients
+};
+
+// Hessenberg column j: fold in h (from CGS2) and ||w||, apply previous
+// rotations, compute the new one, update g and the residual estimate.
+template <int C>
+__global__ void k_givens(GmState S, int m, int j) {
+    if (S.st[0]) return;
+    double *Hc = S.H + (size_t)j * (m + 1) * 2;       // column j, rows 0..j+1, complex pairs
+    for (int i = 0; i <= j; i++) {
+        Hc[2 * i] = S.hcol[i * C] + S.hcol2[i * C];
+        Hc[2 * i + 1] = C == 2 ? S.hcol[i * C + 1] + S.hcol2[i * C + 1] : 0.0;
+    }
+    Hc[2 * (j + 1)] = S.sc[4];
+    Hc[2 * (j + 1) + 1] = 0.0;
+    for (int i = 0; i < j; i++) {
+        double c = S.cs[i], sr = S.sn[2 * i], si = S.sn[2 * i + 1];
+        double ar = Hc[2 * i], ai = Hc[2 * i + 1], br = Hc[2 * i + 2], bi = Hc[2 * i + 3];
+        // t = c a + s b ; b' = -conj(s) a + c b
+        double tr = c * ar + (sr * br - si * bi), ti = c * ai + (sr * bi + si * br);
+        double nbr = -(sr * ar + si * ai) + c * br, nbi = -(sr * ai - si * ar) + c * bi;
+        Hc[2 * i] = tr; Hc[2 * i + 1] = ti; Hc[2 * i + 2] = nbr; Hc[2 * i + 3] = nbi;
+    }
+    double ar = Hc[2 * j], ai = Hc[2 * j + 1], b = Hc[2 * j + 2];    // b real >= 0
+    double aa = hypot(ar, ai), rho = hypot(aa, b);
+    double c, sr, si;
+    if (rho == 0.0) { c = 1.0; sr = 0.0; si = 0.0; }
+    else if (aa == 0.0) { c = 0.0; sr = 1.0; si = 0.0; }
+    else {
+        c = aa / rho;
+        sr = (ar / aa) * b / rho;
+        si = (ai / aa) * b / rho;
+    }
+    S.cs[j] = c; S.sn[2 * j] = sr; S.sn[2 * j + 1] = si;
+    Hc[2 * j] = c * ar + sr * b;
+    Hc[2 * j + 1] = c * ai + si * b;
+    Hc[2 * j + 2] = 0.0; Hc[2 * j + 3] = 0.0;
+    // g_{j+1} = -conj(s) g_j, g_j = c g_j
+    double gr = S.g[2 * j], gi = S.g[2 * j + 1];
+    S.g[2 * j + 2] = -(sr * gr + si * gi);
+    S.g[2 * j + 3] = -(sr * gi - si * gr);
+    S.g[2 * j] = c * gr;
+    S.g[2 * j + 1] = c * gi;
+    double est = hypot(S.g[2 * j + 2], S.g[2 * j + 3]) / S.sc[0];
+    S.sc[2] = est;
+    S.st[1] = j + 1;
+    if (est <= S.sc[3] || S.sc[4] == 0.0) S.st[0] = 1;
+}
+
+// back substitution H y = g over the steps of the cycle, then the solver
+// writes x += V y
+template <int C>
+__global__ void k_backsolve(GmState S, int m) {
+    const int k = S.st[1];
+    for (int i = k - 1; i >= 0; i--) {
+        double sr = S.g[2 * i], si = S.g[2 * i + 1];
+        for (int l = i + 1; l < k; l++) {
+            const double *Hl = S.H + (size_t)l * (m + 1) * 2;
+            double hr = Hl[2 * i], hi = Hl[2 * i + 1], yr = S.y[2 * l], yi = S.y[2 * l + 1];
+            sr -= hr * yr - hi * yi;
+            si -= hr * yi + hi * yr;
+        }
+        const double *Hi = S.H + (size_t)i * (m + 1) * 2;
+        double dr = Hi[2 * i], di = Hi[2 * i + 1], den = dr * dr + di * di;
+        S.y[2 * i] = (sr * dr + si * di) / den;
+        S.y[2 * i + 1] = (si * dr - sr * di) / den;
+    }
+}
+
+// x += sum_{i<k} y_i V_i
+template <int C>
+__global__ void k_xupdate(int n, const double *__restrict__ V, size_t ld, GmState S, double *x) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int k = S.st[1];
+    double a[C];
+#pragma unroll
+    for (int c = 0; c < C; c++) a[c] = x[(size_t)r * C + c];
+    for (int i = 0; i < k; i++) {
+        const double *v = V + (size_t)i * ld;
+        if (C == 1) {
+            a[0] += S.y[2 * i] * v[r];
+        } else {
+            double yr = S.y[2 * i], yi = S.y[2 * i + 1], vr = v[2 * (size_t)r], vi = v[2 * (size_t)r + 1];
+            a[0] += yr * vr - yi * vi;
+            a[C - 1] += yr * vi + yi * vr;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < C; c++) x[(size_t)r * C + c] = a[c];
+}
+
+__global__ void k_cycle_init(GmState S, int m) {
+    S.st[0] = 0;
+    S.st[1] = 0;
+    for (int i = 0; i < 2 * (m + 1); i++) S.g[i] = 0.0;
+    S.g[0] = S.sc[1];   // beta
+}
+
+template <int C>
+static int gmres_one(bem_plan *P, const double *b, double *x, const bem_solve_params *sp, bem_solve_info *info,
+                     cudaStream_t s) {
+    const int n = (int)P->N, m = P->gm_restart, ne = n * C;
+    const size_t ld = (size_t)ne;
+    double *V = P->V, *w = P->w, *partial = P->scal + 16;
+    double *g0 = P->gs;
+    GmState S{P->scal, P->istate, P->H, g0, g0 + m, g0 + 3 * m, g0 + 5 * m + 2, g0 + 7 * m + 2, g0 + 9 * m + 4};
+    const int eb = (ne + 255) / 256, nb = (n + 255) / 256;
+    int *skip = P->istate;
+    // ||b||
+    k_nrm2_partial<C><<<GM_BLK, GM_T, 0, s>>>(n, b, partial, nullptr);
+    k_nrm2_final<<<1, 32, 0, s>>>(partial, S.sc + 0, nullptr);
+    double tol = sp->tol;
+    BEM_CUDA(cudaMemcpyAsync(S.sc + 3, &tol, sizeof(double), cudaMemcpyHostToDevice, s));
+    BEM_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * ne, s));
+    int iters = 0, restarts = 0;
+    double rel = 1.0;
+    int status = BEM_ENOCONV;
+    while (true) {
+        // true residual r = b - A x into V_0 (unscaled), beta = ||r||
+        BEM_CUDA(cudaMemsetAsync(skip, 0, sizeof(int), s));
+        BEM_TRY(set_slots(P, x, V, s));
+        BEM_TRY(enqueue_matvec(P, BEM_OP_A, P->green, P->k, s));
+        k_resid<<<eb, 256, 0, s>>>(ne, b, V);
+        k_nrm2_partial<C><<<GM_BLK, GM_T, 0, s>>>(n, V, partial, nullptr);
+        k_nrm2_final<<<1, 32, 0, s>>>(partial, S.sc + 1, nullptr);
+        double hs[2];
+        BEM_CUDA(cudaMemcpyAsync(hs, S.sc, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+        BEM_CUDA(cudaStreamSynchronize(s));
+        restarts++;
+        rel = hs[0] > 0.0 ? hs[1] / hs[0] : 0.0;
+        if (rel <= sp->tol || hs[0] == 0.0) { status = BEM_OK; break; }
+        if (iters >= sp->max_iter) break;
+        k_scale<<<eb, 256, 0, s>>>(ne, V, S.sc + 1, V, nullptr);
+        k_cycle_init<<<1, 1, 0, s>>>(S, m);
+        const int steps = std::min(m, sp->max_iter - iters);
+        for (int j = 0; j < steps; j++) {
+            BEM_TRY(set_slots(P, V + (size_t)j * ld, w, s));
+            BEM_TRY(enqueue_matvec(P, BEM_OP_A, P->green, P->k, s));
+            // CGS2: two classical Gram-Schmidt passes against V_0..V_j
+            k_mdot<C><<<GM_BLK, GM_T, 0, s>>>(n, j + 1, V, ld, w, partial, skip);
+            k_mdot_final<C><<<(j + 1 + 7) / 8, 256, 0, s>>>(j + 1, partial, S.hcol, 0, skip);
+            k_orth_update<C><<<nb, 256, 0, s>>>(n, j + 1, V, ld, S.hcol, w, skip);
+            k_mdot<C><<<GM_BLK, GM_T, 0, s>>>(n, j + 1, V, ld, w, partial, skip);
+            k_mdot_final<C><<<(j + 1 + 7) / 8, 256, 0, s>>>(j + 1, partial, S.hcol2, 0, skip);
+            k_orth_update<C><<<nb, 256, 0, s>>>(n, j + 1, V, ld, S.hcol2, w, skip);
+            BEM_LAUNCH_CHECK();
+            k_nrm2_partial<C><<<GM_BLK, GM_T, 0, s>>>(n, w, partial, skip);
+            k_nrm2_final<<<1, 32, 0, s>>>(partial, S.sc + 4, skip);
+            k_givens<C><<<1, 1, 0, s>>>(S, m, j);
+            k_scale<<<eb, 256, 0, s>>>(ne, w, S.sc + 4, V + (size_t)(j + 1) * ld, skip);
+            BEM_LAUNCH_CHECK();
+        }
+        k_backsolve<C><<<1, 1, 0, s>>>(S, m);
+        k_xupdate<C><<<nb, 256, 0, s>>>(n, V, ld, S, x);
+        BEM_LAUNCH_CHECK();
+        int hst[2];
+        BEM_CUDA(cudaMemcpyAsync(hst, S.st, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+        BEM_CUDA(cudaStreamSynchronize(s));
+        iters += hst[1];
+        if (hst[1] == 0) break;
+    }
+    if (info) {
+        info->iters = iters;
+        info->restarts = restarts;
+        info->rel_residual = rel;
+        info->status = status;
+    }
+    return status;
+}
+
+int solve(bem_plan *P, const void *chi, void *phi, int nrhs, const bem_solve_params *sp, bem_solve_info *info,
+          cudaStream_t s) {
+    const int C = P->green == BEM_HELMHOLTZ ? 2 : 1;
+    const int m = sp->restart;
+    if (m < 1 || m > 200) { set_error("bem_solve: restart %d outside [1, 200]", m); return BEM_EINVAL; }
+    const size_t ne = (size_t)P->N * C;
+    if (P->gm_restart != m) {
+        if (P->V) { P->arena.release(P->V); P->arena.release(P->H); P->arena.release(P->gs); }
+        BEM_TRY(P->arena.alloc(&P->V, (size_t)(m + 1) * ne));
+        BEM_TRY(P->arena.alloc(&P->H, (size_t)(m + 1) * m * 2));
+        BEM_TRY(P->arena.alloc(&P->gs, (size_t)12 * (m + 2)));
+        P->gm_restart = m;
+    }
+    if (!P->w) {
+        BEM_TRY(P->arena.alloc(&P->w, ne));
+        BEM_TRY(P->arena.alloc(&P->bvec, ne));
+        BEM_TRY(P->arena.alloc(&P->scal, 16 + (size_t)GM_BLK * 2 * (200 + 2)));
+    }
+    int worst = BEM_OK;
+    const size_t nchi = (size_t)P->nchi * C;
+    for (int r = 0; r < nrhs; r++) {
+        const double *c = (const double *)chi + r * nchi;
+        double *x = (double *)phi + r * ne;
+        BEM_TRY(set_slots(P, c, P->bvec, s));
+        BEM_TRY(enqueue_matvec(P, BEM_OP_B, P->green, P->k, s));
+        int st = C == 1 ? gmres_one<1>(P, P->bvec, x, sp, info ? info + r : nullptr, s)
+                        : gmres_one<2>(P, P->bvec, x, sp, info ? info + r : nullptr, s);
+        if (st != BEM_OK && st != BEM_ENOCONV) return st;
+        if (st == BEM_ENOCONV) worst = st;
+    }
+    return worst;
+}
+
+}  // namespace bem

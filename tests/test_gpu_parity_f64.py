@@ -1,0 +1,182 @@
+"""GPU parity of the float64 path against the oracle, through the C ABI.
+
+* octree, radii and lists: bit-exact (Sections 3.1, 3.4, 3.6);
+* stored special-pair correction: same pairs, values within 1e-11;
+* diagonal C_i = 1 + sum_j D0_ij (Eq. 2-3);
+* moments and locals per box against the oracle's four-step product;
+* the product y = A x, y = B x: relative L2 <= 1e-6 against the dense oracle;
+* GMRES solution: relative L2 <= 1e-5 against the oracle's LU solve;
+* the full cube workload (24,300 6-node triangles, p = 10): 2000 sampled
+  rows against the oracle's matrix-free rows.
+"""
+import numpy as np
+import pytest
+
+from paper_0908_0673_gb300 import bem, inputs as I
+
+from gpu_util import Plan, canon_export, canon_oracle, coo_sum, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+MATVEC_TOL = 1e-6     # relative L2, float64 product vs dense oracle
+SOLVE_TOL = 1e-5      # relative L2, solve vs oracle LU solve
+
+CASES = {
+    "sphere642": (lambda: I.icosphere(3), dict(p=8, leaf_size=32, eta=2.0)),
+    "sphere642_b16": (lambda: I.icosphere(3), dict(p=8, leaf_size=16, eta=2.0)),
+    "cube6_tri6": (lambda: I.cube(6, I.TRI6), dict(p=10, leaf_size=24, eta=1.5)),
+    "cube8_tri6": (lambda: I.cube(8, I.TRI6), dict(p=10, leaf_size=32, eta=2.0)),
+    "sphere_tri6_l2": (lambda: I.icosphere(2, I.TRI6), dict(p=8, leaf_size=16, eta=2.0)),
+}
+
+
+@pytest.fixture(scope="module")
+def plans():
+    out = {}
+    yield out
+    for p in out.values():
+        p.close()
+
+
+def get(plans, name):
+    if name not in plans:
+        mk, prm = CASES[name]
+        plans[name] = Plan(mk(), **prm)
+    return plans[name]
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_tree_bit_exact(oracle_lib, plans, name):
+    P = get(plans, name)
+    prm = CASES[name][1]
+    T = oracle_lib.Tree(P.m.nodes, P.m.elems, B=prm["leaf_size"], eta=prm["eta"], leaf_descend=1)
+    d = bem.bem_plan_export_tree(P.plan)
+    assert d["side"] == T.side and np.array_equal(d["lo"], T.lo)
+    a, b = canon_export(d), canon_oracle(T)
+    assert a.keys() == b.keys()
+    for k in b:
+        assert a[k] == b[k], (k, a[k], b[k])
+
+
+@pytest.mark.parametrize("name", ["sphere642", "cube6_tri6"])
+def test_correction_matches_oracle(oracle_lib, plans, name):
+    P = get(plans, name)
+    ref = oracle_lib.correction(P.m.nodes, P.m.elems, P.chi_idx)
+    got = bem.bem_plan_export_correction(P.plan)
+    for part, rr, cc, vv in (("D", ref["row"], ref["col_phi"], ref["D"].real),
+                             ("S", ref["row"], ref["col_chi"], ref["S"].real)):
+        r = coo_sum(rr, cc, vv)
+        g = coo_sum(got["row" + part], got["col" + part], got["val" + part])
+        assert r.keys() == g.keys(), part
+        scale = max(abs(v) for v in r.values())
+        assert max(abs(g[k] - r[k]) for k in r) < 1e-11 * scale, part
+
+
+@pytest.mark.parametrize("name", ["sphere642", "cube6_tri6", "sphere_tri6_l2"])
+def test_diagonal(oracle_lib, plans, name):
+    P = get(plans, name)
+    _, _, d0 = oracle_lib.assemble(P.m.nodes, P.m.elems, P.chi_idx, P.n_chi)
+    c = bem.bem_plan_diagonal(P.plan, P.n_phi)
+    assert np.max(np.abs(c - (1.0 + d0))) < 2e-7
+
+
+@pytest.mark.parametrize("name", ["sphere642", "cube6_tri6"])
+@pytest.mark.parametrize("op", [bem.BEM_OP_A, bem.BEM_OP_B])
+def test_expansions_match_oracle_fmm(oracle_lib, plans, name, op):
+    """Moments and locals of every box against the oracle's four-step
+    product on the identical tree (both float64)."""
+    P = get(plans, name)
+    prm = CASES[name][1]
+    T = oracle_lib.Tree(P.m.nodes, P.m.elems, B=prm["leaf_size"], eta=prm["eta"])
+    n = P.n_phi if op == bem.BEM_OP_A else P.n_chi
+    x = I.random_vector(n, 11)
+    P.matvec(op, x)
+    st = P.stats()
+    mnk, mom, loc = bem.bem_plan_export_expansions(P.plan, st["n_boxes"], st["n_p"])
+    _, _, d0 = oracle_lib.assemble(P.m.nodes, P.m.elems, P.chi_idx, P.n_chi, rows=[0])
+    corr = dict(row=np.zeros(0, np.int64), col_phi=np.zeros(0, np.int32), col_chi=np.zeros(0, np.int32),
+                D=np.zeros(0, complex), S=np.zeros(0, complex))
+    _, omom, oloc = oracle_lib.fmm_apply(T, P.chi_idx, op, x, np.zeros(P.n_phi), corr, prm["p"],
+                                        want_expansions=True)
+    d = bem.bem_plan_export_tree(P.plan)
+    okey = {(int(T.level[b]),) + tuple(int(v) for v in T.ijk[b]): b for b in range(T.n_boxes)}
+    omnk = {tuple(int(v) for v in r): i for i, r in enumerate(oracle_lib.mindex(prm["p"]))}
+    perm = np.array([omnk[tuple(int(v) for v in r)] for r in mnk])
+    for b in range(st["n_boxes"]):
+        ob = okey[(int(d["level"][b]),) + tuple(int(v) for v in d["ijk"][b])]
+        for a, o in ((mom[b], omom[ob][perm].real), (loc[b], oloc[ob][perm].real)):
+            s = np.max(np.abs(o))
+            if s > 0:
+                assert np.max(np.abs(a - o)) <= 1e-9 * s, b
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_matvec_vs_dense(oracle_lib, plans, name):
+    P = get(plans, name)
+    A, B, _ = oracle_lib.operators(P.m.nodes, P.m.elems, P.chi_idx, P.n_chi)
+    x = I.random_vector(P.n_phi, 1)
+    xs = I.random_vector(P.n_chi, 2)
+    ea = rel_l2(P.matvec(bem.BEM_OP_A, x), A @ x)
+    eb = rel_l2(P.matvec(bem.BEM_OP_B, xs), B @ xs)
+    assert ea <= MATVEC_TOL and eb <= MATVEC_TOL, (ea, eb)
+
+
+def test_matvec_single_box_is_exact(oracle_lib):
+    """Fewer vertices than B: the root is the only leaf, no expansions are
+    used, and the product is the dense operator up to rounding."""
+    m = I.icosphere(1, I.TRI3)
+    P = Plan(m, p=4, leaf_size=64, eta=2.0)
+    try:
+        assert P.stats()["n_boxes"] == 1
+        A, B, _ = oracle_lib.operators(m.nodes, m.elems, P.chi_idx, P.n_chi)
+        x = I.random_vector(P.n_phi, 3)
+        assert rel_l2(P.matvec(bem.BEM_OP_A, x), A @ x) < 1e-12
+        assert rel_l2(P.matvec(bem.BEM_OP_B, x), B @ x) < 1e-12
+    finally:
+        P.close()
+
+
+def test_deep_tree_leaf_size_2(oracle_lib):
+    m = I.icosphere(2, I.TRI3)
+    P = Plan(m, p=8, leaf_size=2, eta=2.0)
+    try:
+        T = oracle_lib.Tree(m.nodes, m.elems, B=2, eta=2.0)
+        assert canon_export(bem.bem_plan_export_tree(P.plan)) == canon_oracle(T)
+        A, B, _ = oracle_lib.operators(m.nodes, m.elems, P.chi_idx, P.n_chi)
+        x = I.random_vector(P.n_phi, 4)
+        assert rel_l2(P.matvec(bem.BEM_OP_A, x), A @ x) <= MATVEC_TOL
+    finally:
+        P.close()
+
+
+@pytest.mark.parametrize("name,src", [("sphere642", (0.1, 0.2, -0.15)), ("cube6_tri6", (0.2, -0.1, 0.3))])
+def test_solve_vs_lu(oracle_lib, plans, name, src):
+    P = get(plans, name)
+    A, B, _ = oracle_lib.operators(P.m.nodes, P.m.elems, P.chi_idx, P.n_chi)
+    _, chi_e = I.point_source(P.m, src)
+    chi = oracle_lib.chi_from_elem(P.chi_idx, P.n_chi, chi_e)
+    ref = oracle_lib.solve_dense(A, B @ chi)
+    phi, code, info = P.solve(chi, tol=1e-10)
+    assert code == bem.BEM_OK and info.rel_residual <= 1e-10
+    assert rel_l2(phi, ref) <= SOLVE_TOL
+
+
+def test_full_cube_sampled_rows(oracle_lib):
+    """The cube workload at full size (45 x 45 quads per face, 6-node
+    triangles, p = 10): 2000 seeded sampled rows of A x and B x against the
+    oracle's matrix-free rows, and the tree bit-exact."""
+    m = I.cube(45, I.TRI6)
+    P = Plan(m, p=10, leaf_size=64, eta=2.0)
+    try:
+        T = oracle_lib.Tree(m.nodes, m.elems, B=64, eta=2.0)
+        assert canon_export(bem.bem_plan_export_tree(P.plan)) == canon_oracle(T)
+        rows = np.sort(np.random.default_rng(0).choice(P.n_phi, 2000, replace=False))
+        x = I.random_vector(P.n_phi, 5)
+        xs = I.random_vector(P.n_chi, 6)
+        ya = P.matvec(bem.BEM_OP_A, x)[rows]
+        yb = P.matvec(bem.BEM_OP_B, xs)[rows]
+        ra = oracle_lib.apply_rows(m.nodes, m.elems, P.chi_idx, oracle_lib.OP_A, x, rows)
+        rb = oracle_lib.apply_rows(m.nodes, m.elems, P.chi_idx, oracle_lib.OP_B, xs, rows)
+        assert rel_l2(ya, ra) <= MATVEC_TOL and rel_l2(yb, rb) <= MATVEC_TOL, (rel_l2(ya, ra), rel_l2(yb, rb))
+    finally:
+        P.close()
