@@ -202,11 +202,32 @@ int bem_plan_diagonal(const bem_plan *plan, double *c);
 /* Device memory held by the plan, in bytes. */
 int bem_plan_footprint(const bem_plan *plan, size_t *hbm_bytes);
 
-/* Integer counters of the plan: [0] n_boxes, [1] n_leaves, [2] n_levels,
- * [3] near-list entries, [4] interaction-list entries, [5] near-field
- * source-target pairs per matrix multiplication, [6] correction nnz (D),
- * [7] correction nnz (S), [8] quadrature points, [9] n_p. */
+/* Integer counters of the plan (host array of 12): [0] n_boxes, [1] n_leaves,
+ * [2] n_levels, [3] near-list entries, [4] interaction-list entries,
+ * [5] near-field source-target pairs per matrix multiplication, [6] correction
+ * nnz (D), [7] correction nnz (S), [8] quadrature points, [9] n_p,
+ * [10] / [11] kernels in the captured op A / op B product graph (0 until the
+ * first product). */
 int bem_plan_stats(const bem_plan *plan, int64_t *stats);
+
+/* Stages of one product, in launch order, for bem_plan_stage_times. */
+#define BEM_NSTAGES 7   /* P2Q, P2M, M2M, M2L, L2L, near field + L2P, correction + diagonal */
+
+/* Runs the product y = op x `reps` times outside its graph with CUDA events
+ * between the stages on the given stream and returns the mean duration of each
+ * stage in milliseconds (host array of BEM_NSTAGES).  Synchronises. */
+int bem_plan_stage_times(bem_plan *plan, int op, const void *x_dev, void *y_dev, int reps, double *ms,
+                         void *cuda_stream);
+
+/* Kernel launches issued by this library in this process so far (a graph
+ * launch counts the kernels it holds). */
+int bem_launch_count(long long *count);
+
+/* Measured fused multiply-add throughput of the current device in TFLOP/s
+ * (kind 0: float32, kind 1: float64; 2 flops per FMA), the denominator of
+ * the arithmetic rooflines.  Measurement infrastructure: the paper has no
+ * counterpart.  Synchronises. */
+int bem_measure_peak(int kind, double *tflops, void *cuda_stream);
 
 #ifdef __cplusplus
 }

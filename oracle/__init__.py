@@ -56,11 +56,17 @@ PARITY = {
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (no FMA contraction, OpenMP)."""
     os.makedirs(_LIB_DIR, exist_ok=True)
+    stamp = os.path.join(_LIB_DIR, "machine")
+    import platform
+    if not os.path.exists(stamp) or open(stamp).read().strip() != platform.machine():
+        force = True
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-std=c11",
                "-shared", "-fPIC", "-o", _LIB + ".tmp", _SRC, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(_LIB + ".tmp", _LIB)
+        with open(stamp, "w") as f:
+            f.write(platform.machine())
     return _LIB
 
 

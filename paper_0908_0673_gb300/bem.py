@@ -27,8 +27,11 @@ EXPORTS = [
     "bem_last_error", "bem_mesh_create", "bem_mesh_destroy", "bem_mesh_sizes", "bem_mesh_chi_index",
     "bem_plan_create", "bem_plan_destroy", "bem_matvec", "bem_solve", "bem_plan_tree_sizes",
     "bem_plan_export_tree", "bem_plan_export_correction", "bem_plan_export_expansions",
-    "bem_plan_diagonal", "bem_plan_footprint", "bem_plan_stats",
+    "bem_plan_diagonal", "bem_plan_footprint", "bem_plan_stats", "bem_plan_stage_times",
+    "bem_launch_count", "bem_measure_peak",
 ]
+BEM_NSTAGES = 7
+STAGE_NAMES = ["p2q", "p2m", "m2m", "m2l", "l2l", "near_l2p", "combine"]
 
 
 class bem_fmm_params(C.Structure):
@@ -99,6 +102,9 @@ def load(build_if_missing: bool = True):
     L.bem_plan_diagonal.argtypes = [P, P]
     L.bem_plan_footprint.argtypes = [P, P]
     L.bem_plan_stats.argtypes = [P, P]
+    L.bem_plan_stage_times.argtypes = [P, i32, P, P, i32, P, P]
+    L.bem_launch_count.argtypes = [P]
+    L.bem_measure_peak.argtypes = [i32, P, P]
     for name in EXPORTS:
         if name not in ("bem_fmm_params_default", "bem_solve_params_default", "bem_ctx_destroy",
                         "bem_last_error", "bem_mesh_destroy", "bem_plan_destroy"):
@@ -275,10 +281,28 @@ def bem_plan_footprint(plan) -> int:
 
 
 STAT_NAMES = ["n_boxes", "n_leaves", "n_levels", "n_near", "n_inter", "near_pairs", "corr_nnz_D",
-              "corr_nnz_S", "n_quad", "n_p"]
+              "corr_nnz_S", "n_quad", "n_p", "graph_kernels_A", "graph_kernels_B"]
+
+
+def bem_plan_stage_times(plan, op, x, y, reps=5, stream=None) -> dict:
+    ms = np.zeros(BEM_NSTAGES)
+    _check(load().bem_plan_stage_times(plan, int(op), _ptr(x), _ptr(y), int(reps), _ptr(ms), _stream(stream)))
+    return dict(zip(STAGE_NAMES, ms.tolist()))
+
+
+def bem_launch_count() -> int:
+    v = C.c_longlong()
+    _check(load().bem_launch_count(C.byref(v)))
+    return v.value
+
+
+def bem_measure_peak(kind, stream=None) -> float:
+    v = C.c_double()
+    _check(load().bem_measure_peak(int(kind), C.byref(v), _stream(stream)))
+    return v.value
 
 
 def bem_plan_stats(plan) -> dict:
-    st = np.zeros(10, np.int64)
+    st = np.zeros(12, np.int64)
     _check(load().bem_plan_stats(plan, _ptr(st)))
     return dict(zip(STAT_NAMES, (int(v) for v in st)))

@@ -7,6 +7,7 @@ from __future__ import annotations
 
 import concurrent.futures as cf
 import os
+import platform
 import subprocess
 import sys
 
@@ -47,6 +48,10 @@ def _compile(src, extra):
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     os.makedirs(OUT, exist_ok=True)
     srcs = sources()
+    stamp = os.path.join(OUT, "machine")
+    machine = platform.machine()
+    if not os.path.exists(stamp) or open(stamp).read().strip() != machine:
+        force = True
     if force:
         for f in os.listdir(OUT):
             if f.endswith(".o"):
@@ -59,6 +64,8 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
         os.replace(LIB + ".tmp", LIB)
+    with open(stamp, "w") as f:
+        f.write(machine)
     if verbose:
         print(LIB)
     return LIB

@@ -1,6 +1,7 @@
 // C ABI entry points (include/bem.h): contexts, plans, the fast matrix
 // multiplication as one captured CUDA graph per operator, the GMRES solve and
 // the exports used for parity checks.
+#include <atomic>
 #include <cstdarg>
 #include <cstring>
 #include <new>
@@ -11,6 +12,13 @@
 namespace bem {
 
 static thread_local char g_err[512] = "";
+static std::atomic<long long> g_launches{0};
+thread_local long long *tl_capture_count = nullptr;
+
+void count_launch(long long n) {
+    if (tl_capture_count) *tl_capture_count += n;
+    else g_launches += n;
+}
 
 void set_error(const char *fmt, ...) {
     va_list ap;
@@ -31,7 +39,7 @@ __global__ void k_set_slots(const void **xs, const void *x, void **ys, void *y) 
 
 // Points the plan's input/output slots at x and y, in stream order.
 int set_slots(bem_plan *P, const void *x, void *y, cudaStream_t s) {
-    k_set_slots<<<1, 1, 0, s>>>(P->xptr, x, P->yptr, y);
+    (k_set_slots<<<1, 1, 0, s>>>(P->xptr, x, P->yptr, y), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
     return BEM_OK;
 }
@@ -46,7 +54,10 @@ int enqueue_matvec(bem_plan *P, int op, int green, double k, cudaStream_t s) {
         if (!P->capture_stream) BEM_CUDA(cudaStreamCreateWithFlags(&P->capture_stream, cudaStreamNonBlocking));
         cudaGraph_t g = nullptr;
         BEM_CUDA(cudaStreamBeginCapture(P->capture_stream, cudaStreamCaptureModeThreadLocal));
+        P->graph_kernels[op] = 0;
+        tl_capture_count = &P->graph_kernels[op];
         int rc = enqueue_matvec_raw(P, op, green, k, 1, P->capture_stream);
+        tl_capture_count = nullptr;
         cudaError_t e = cudaStreamEndCapture(P->capture_stream, &g);
         if (rc != BEM_OK) {
             if (g) cudaGraphDestroy(g);
@@ -58,6 +69,7 @@ int enqueue_matvec(bem_plan *P, int op, int green, double k, cudaStream_t s) {
         if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
     }
     BEM_CUDA(cudaGraphLaunch(ge, s));
+    count_launch(P->graph_kernels[op]);
     P->last_op = op;
     return BEM_OK;
 }
@@ -92,7 +104,6 @@ static int plan_setup(bem_plan *P, cudaStream_t s) {
     BEM_TRY(build_geometry(P, s));
     BEM_TRY(build_radii_lists(P, s));
     BEM_TRY(build_correction(P, s));
-    BEM_TRY(alloc_fmm(P));
     BEM_TRY(compute_diagonal(P, s));
     // near-field pair count (targets x regular sources), for the roofline
     const Tree &t = P->t;
@@ -366,6 +377,37 @@ int bem_plan_footprint(const bem_plan *P, size_t *hbm_bytes) {
     return BEM_OK;
 }
 
+int bem_launch_count(long long *count) {
+    if (!count) { set_error("bem_launch_count: NULL argument"); return BEM_EINVAL; }
+    *count = g_launches.load();
+    return BEM_OK;
+}
+
+int bem_plan_stage_times(bem_plan *P, int op, const void *x_dev, void *y_dev, int reps, double *ms,
+                         void *cuda_stream) {
+    if (!P || !x_dev || !y_dev || !ms || reps < 1) { set_error("bem_plan_stage_times: bad argument"); return BEM_EINVAL; }
+    if (op != BEM_OP_A && op != BEM_OP_B) { set_error("bem_plan_stage_times: bad op %d", op); return BEM_EINVAL; }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    cudaEvent_t ev[BEM_NSTAGES + 1];
+    for (auto &e : ev) BEM_CUDA(cudaEventCreate(&e));
+    for (int i = 0; i < BEM_NSTAGES; i++) ms[i] = 0.0;
+    int rc = set_slots(P, x_dev, y_dev, s);
+    if (rc == BEM_OK) rc = cudaMemsetAsync(P->skip, 0, sizeof(int), s) == cudaSuccess ? BEM_OK : BEM_ECUDA;
+    for (int r = 0; r < reps && rc == BEM_OK; r++) {
+        rc = enqueue_matvec_raw(P, op, P->green, P->k, 1, s, ev);
+        if (rc != BEM_OK) break;
+        cudaError_t e = cudaEventSynchronize(ev[BEM_NSTAGES]);
+        if (e != cudaSuccess) { rc = cuda_fail(e, "cudaEventSynchronize", __FILE__, __LINE__); break; }
+        for (int i = 0; i < BEM_NSTAGES; i++) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, ev[i], ev[i + 1]);
+            ms[i] += t / reps;
+        }
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    return rc;
+}
+
 int bem_plan_stats(const bem_plan *P, int64_t *st) {
     if (!P || !st) { set_error("bem_plan_stats: NULL argument"); return BEM_EINVAL; }
     st[0] = P->t.nbox;
@@ -378,6 +420,8 @@ int bem_plan_stats(const bem_plan *P, int64_t *st) {
     st[7] = P->corr.nnzS;
     st[8] = P->Q;
     st[9] = P->mi.np;
+    st[10] = P->graph_kernels[0];
+    st[11] = P->graph_kernels[1];
     return BEM_OK;
 }
 

@@ -19,6 +19,12 @@ namespace bem {
 void set_error(const char *fmt, ...);
 int cuda_fail(cudaError_t e, const char *what, const char *file, int line);
 
+// Kernel-launch accounting: every launch site calls count_launch(); while a
+// graph is being captured the count goes to that graph's kernel tally, and
+// each graph launch adds its tally.
+void count_launch(long long n = 1);
+extern thread_local long long *tl_capture_count;
+
 #define BEM_CUDA(call)                                                      \
     do {                                                                    \
         cudaError_t e_ = (call);                                            \
@@ -166,6 +172,7 @@ struct bem_plan {
     int *skip = nullptr;                // device flag: kernels return at once when set
     // graphs
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    long long graph_kernels[2] = {0, 0};
     cudaStream_t capture_stream = nullptr;
     // counters
     int64_t near_pairs = 0;
@@ -186,9 +193,11 @@ int build_geometry(bem_plan *P, cudaStream_t s);
 int build_radii_lists(bem_plan *P, cudaStream_t s);
 int build_correction(bem_plan *P, cudaStream_t s);
 int alloc_fmm(bem_plan *P);
+void free_fmm(bem_plan *P);
 int enqueue_matvec(bem_plan *P, int op, int green, double k, cudaStream_t s);
 int set_slots(bem_plan *P, const void *x, void *y, cudaStream_t s);
-int enqueue_matvec_raw(bem_plan *P, int op, int green, double k, int with_diag, cudaStream_t s);
+int enqueue_matvec_raw(bem_plan *P, int op, int green, double k, int with_diag, cudaStream_t s,
+                       cudaEvent_t *ev = nullptr);
 int compute_diagonal(bem_plan *P, cudaStream_t s);
 int solve(bem_plan *P, const void *chi, void *phi, int nrhs, const bem_solve_params *sp,
           bem_solve_info *info, cudaStream_t s);

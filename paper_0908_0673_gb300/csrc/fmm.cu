@@ -734,8 +734,11 @@ int alloc_fmm(bem_plan *P) {
     return BEM_OK;
 }
 
+// ev (optional, BEM_NSTAGES + 1 events): recorded before the first stage and
+// after every stage, for per-stage timing outside graphs.
 template <class R, int C>
-static int run_fmm(bem_plan *P, int op, double kwave, R *f, R *M, R *L, cudaStream_t s) {
+static int run_fmm(bem_plan *P, int op, double kwave, R *f, R *M, R *L, cudaStream_t s, cudaEvent_t *ev) {
+    if (ev) BEM_CUDA(cudaEventRecord(ev[0], s));
     const Tabs tb = tabs_of(P);
     const TreeView tv = view_of(P);
     const QuadView qv = quad_of(P);
@@ -744,41 +747,48 @@ static int run_fmm(bem_plan *P, int op, double kwave, R *f, R *M, R *L, cudaStre
     const int *sk = P->skip;
     const int *el = op == BEM_OP_A ? t.el_phi : t.el_chi;
     const int Q = (int)P->Q;
-    k_p2q<R, C><<<(Q + 255) / 256, 256, 0, s>>>(Q, P->npe, el, P->q.w, P->xptr, f, sk);
-    if (op == BEM_OP_A) k_p2m<R, C, true><<<t.nleaf, P2M_T, 0, s>>>(t.nleaf, tb, tv, qv, f, M, sk);
-    else k_p2m<R, C, false><<<t.nleaf, P2M_T, 0, s>>>(t.nleaf, tb, tv, qv, f, M, sk);
+    (k_p2q<R, C><<<(Q + 255) / 256, 256, 0, s>>>(Q, P->npe, el, P->q.w, P->xptr, f, sk), ::bem::count_launch());
+    if (ev) BEM_CUDA(cudaEventRecord(ev[1], s));
+    if (op == BEM_OP_A) (k_p2m<R, C, true><<<t.nleaf, P2M_T, 0, s>>>(t.nleaf, tb, tv, qv, f, M, sk), ::bem::count_launch());
+    else (k_p2m<R, C, false><<<t.nleaf, P2M_T, 0, s>>>(t.nleaf, tb, tv, qv, f, M, sk), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
+    if (ev) BEM_CUDA(cudaEventRecord(ev[2], s));
     const size_t trs = tr_smem(p, np, sizeof(R), C);
     for (int l = t.nlev - 2; l >= 0; l--) {
         int off = t.lev_off[l], cnt = t.lev_off[l + 1] - off;
-        k_m2m<R, C><<<cnt, TR_T, trs, s>>>(off, cnt, tb, tv, M, sk);
+        (k_m2m<R, C><<<cnt, TR_T, trs, s>>>(off, cnt, tb, tv, M, sk), ::bem::count_launch());
     }
     BEM_LAUNCH_CHECK();
-    k_m2l<R, C><<<t.nbox, TR_T, M2LShared<R, C>::bytes(p, np), s>>>(t.nbox, tb, tv, kwave, M, L, sk);
+    if (ev) BEM_CUDA(cudaEventRecord(ev[3], s));
+    (k_m2l<R, C><<<t.nbox, TR_T, M2LShared<R, C>::bytes(p, np), s>>>(t.nbox, tb, tv, kwave, M, L, sk), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
+    if (ev) BEM_CUDA(cudaEventRecord(ev[4], s));
     for (int l = 1; l < t.nlev; l++) {
         int off = t.lev_off[l], cnt = t.lev_off[l + 1] - off;
-        k_l2l<R, C><<<cnt, TR_T, trs, s>>>(off, cnt, tb, tv, L, sk);
+        (k_l2l<R, C><<<cnt, TR_T, trs, s>>>(off, cnt, tb, tv, L, sk), ::bem::count_launch());
     }
     BEM_LAUNCH_CHECK();
-    if (op == BEM_OP_A) k_near<R, C, true><<<t.nleaf, NF_T, 0, s>>>(t.nleaf, tb, tv, qv, kwave, f, L, P->ytmp, sk);
-    else k_near<R, C, false><<<t.nleaf, NF_T, 0, s>>>(t.nleaf, tb, tv, qv, kwave, f, L, P->ytmp, sk);
+    if (ev) BEM_CUDA(cudaEventRecord(ev[5], s));
+    if (op == BEM_OP_A) (k_near<R, C, true><<<t.nleaf, NF_T, 0, s>>>(t.nleaf, tb, tv, qv, kwave, f, L, P->ytmp, sk), ::bem::count_launch());
+    else (k_near<R, C, false><<<t.nleaf, NF_T, 0, s>>>(t.nleaf, tb, tv, qv, kwave, f, L, P->ytmp, sk), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
+    if (ev) BEM_CUDA(cudaEventRecord(ev[6], s));
     return BEM_OK;
 }
 
 // Enqueues one product on stream s.  The input and output vectors are read
 // from the device slots P->xptr[0] / P->yptr[0].  with_diag = 0 leaves the
 // regular far + near sums in P->ytmp (used for the diagonal).
-int enqueue_matvec_raw(bem_plan *P, int op, int green, double kwave, int with_diag, cudaStream_t s) {
+int enqueue_matvec_raw(bem_plan *P, int op, int green, double kwave, int with_diag, cudaStream_t s,
+                       cudaEvent_t *ev) {
     const int C = green == BEM_HELMHOLTZ ? 2 : 1;
     const bool mx = P->prm.precision == BEM_MIXED;
     if (!mx) {
-        if (C == 1) BEM_TRY((run_fmm<double, 1>(P, op, kwave, P->f, P->M, P->L, s)));
-        else BEM_TRY((run_fmm<double, 2>(P, op, kwave, P->f, P->M, P->L, s)));
+        if (C == 1) BEM_TRY((run_fmm<double, 1>(P, op, kwave, P->f, P->M, P->L, s, ev)));
+        else BEM_TRY((run_fmm<double, 2>(P, op, kwave, P->f, P->M, P->L, s, ev)));
     } else {
-        if (C == 1) BEM_TRY((run_fmm<float, 1>(P, op, kwave, P->ff, P->fM, P->fL, s)));
-        else BEM_TRY((run_fmm<float, 2>(P, op, kwave, P->ff, P->fM, P->fL, s)));
+        if (C == 1) BEM_TRY((run_fmm<float, 1>(P, op, kwave, P->ff, P->fM, P->fL, s, ev)));
+        else BEM_TRY((run_fmm<float, 2>(P, op, kwave, P->ff, P->fM, P->fL, s, ev)));
     }
     if (!with_diag) return BEM_OK;
     const int N = (int)P->N;
@@ -786,35 +796,61 @@ int enqueue_matvec_raw(bem_plan *P, int op, int green, double kwave, int with_di
     const int blocks = (N * 32 + 255) / 256;
 #define BEM_COMBINE(RV, VD, VS)                                                                                 \
     if (op == BEM_OP_A) {                                                                                       \
-        if (C == 1) k_combine<RV, 1, true><<<blocks, 256, 0, s>>>(N, K.ptrD, K.colD, VD, P->C, P->ytmp, P->xptr, P->yptr, P->skip); \
-        else k_combine<RV, 2, true><<<blocks, 256, 0, s>>>(N, K.ptrD, K.colD, VD, P->C, P->ytmp, P->xptr, P->yptr, P->skip);       \
+        if (C == 1) (k_combine<RV, 1, true><<<blocks, 256, 0, s>>>(N, K.ptrD, K.colD, VD, P->C, P->ytmp, P->xptr, P->yptr, P->skip), ::bem::count_launch()); \
+        else (k_combine<RV, 2, true><<<blocks, 256, 0, s>>>(N, K.ptrD, K.colD, VD, P->C, P->ytmp, P->xptr, P->yptr, P->skip), ::bem::count_launch());       \
     } else {                                                                                                    \
-        if (C == 1) k_combine<RV, 1, false><<<blocks, 256, 0, s>>>(N, K.ptrS, K.colS, VS, P->C, P->ytmp, P->xptr, P->yptr, P->skip); \
-        else k_combine<RV, 2, false><<<blocks, 256, 0, s>>>(N, K.ptrS, K.colS, VS, P->C, P->ytmp, P->xptr, P->yptr, P->skip);       \
+        if (C == 1) (k_combine<RV, 1, false><<<blocks, 256, 0, s>>>(N, K.ptrS, K.colS, VS, P->C, P->ytmp, P->xptr, P->yptr, P->skip), ::bem::count_launch()); \
+        else (k_combine<RV, 2, false><<<blocks, 256, 0, s>>>(N, K.ptrS, K.colS, VS, P->C, P->ytmp, P->xptr, P->yptr, P->skip), ::bem::count_launch());       \
     }
     if (mx) { BEM_COMBINE(float, K.fvalD, K.fvalS) } else { BEM_COMBINE(double, K.valD, K.valS) }
 #undef BEM_COMBINE
     BEM_LAUNCH_CHECK();
+    if (ev) BEM_CUDA(cudaEventRecord(ev[7], s));
     return BEM_OK;
 }
 
 // Diagonal: C_i = 1 + sum_j D0_ij with D0 the Laplace double layer.  The
 // correction row sums are already in P->C; one regular Laplace double-layer
-// product on phi = 1 adds the rest.
+// product on phi = 1 adds the rest.  For a constant density the far-field
+// contributions add up coherently, so the expansions' relative error shows
+// in full; this one product therefore runs in float64 at the largest
+// supported order (error ~ eta^-(p+1)), on the same tree and lists, before
+// the buffers are sized for the plan's own order and precision.
 int compute_diagonal(bem_plan *P, cudaStream_t s) {
     const int N = (int)P->N;
+    const int p_keep = P->prm.p, prec_keep = P->prm.precision;
+    P->prm.p = PMAX;
+    P->prm.precision = BEM_F64;
+    BEM_TRY(alloc_fmm(P));
     double *ones = nullptr;
     BEM_TRY(P->arena.alloc(&ones, N));
-    k_fill<<<(N + 255) / 256, 256, 0, s>>>(N, 1.0, ones);
+    (k_fill<<<(N + 255) / 256, 256, 0, s>>>(N, 1.0, ones), ::bem::count_launch());
     BEM_TRY(set_slots(P, ones, nullptr, s));
-    // a Helmholtz plan still evaluates the Laplace kernel here: run the real
-    // product on the (complex-sized) buffers with C = 1
-    BEM_TRY(enqueue_matvec_raw(P, BEM_OP_A, BEM_LAPLACE, 0.0, 0, s));
-    k_finish_diag<<<(N + 255) / 256, 256, 0, s>>>(N, P->ytmp, P->C);
+    // a Helmholtz plan still evaluates the Laplace kernel here
+    BEM_TRY(enqueue_matvec_raw(P, BEM_OP_A, BEM_LAPLACE, 0.0, 0, s, nullptr));
+    (k_finish_diag<<<(N + 255) / 256, 256, 0, s>>>(N, P->ytmp, P->C), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
     BEM_CUDA(cudaStreamSynchronize(s));
     P->arena.release(ones);
-    return BEM_OK;
+    free_fmm(P);
+    P->prm.p = p_keep;
+    P->prm.precision = prec_keep;
+    return alloc_fmm(P);
+}
+
+// releases what alloc_fmm allocated
+void free_fmm(bem_plan *P) {
+    Arena &A = P->arena;
+    for (void *q : {(void *)P->d_m, (void *)P->d_n, (void *)P->d_k, (void *)P->d_idx3, (void *)P->d_fact,
+                    (void *)P->d_binom, (void *)P->f, (void *)P->M, (void *)P->L, (void *)P->ff, (void *)P->fM,
+                    (void *)P->fL, (void *)P->ytmp, (void *)P->xptr, (void *)P->yptr})
+        A.release(q);
+    P->d_m = P->d_n = P->d_k = P->d_idx3 = nullptr;
+    P->d_fact = P->d_binom = nullptr;
+    P->f = P->M = P->L = P->ytmp = nullptr;
+    P->ff = P->fM = P->fL = nullptr;
+    P->xptr = nullptr;
+    P->yptr = nullptr;
 }
 
 }  // namespace bem

@@ -196,9 +196,9 @@ int build_geometry(bem_plan *P, cudaStream_t s) {
     BEM_TRY(A.alloc(&q.fx, Q)); BEM_TRY(A.alloc(&q.fy, Q)); BEM_TRY(A.alloc(&q.fz, Q));
     BEM_TRY(A.alloc(&q.fnx, Q)); BEM_TRY(A.alloc(&q.fny, Q)); BEM_TRY(A.alloc(&q.fnz, Q));
     BEM_TRY(A.alloc(&q.fw, Q));
-    k_geometry<<<(int)((Q + 255) / 256), 256, 0, s>>>((int)P->E, P->npe, t.el_phi, P->nodes, t.leaf_of_node, t.cx,
+    (k_geometry<<<(int)((Q + 255) / 256), 256, 0, s>>>((int)P->E, P->npe, t.el_phi, P->nodes, t.leaf_of_node, t.cx,
                                                        t.cy, t.cz, q.x, q.y, q.z, q.nx, q.ny, q.nz, q.w, q.fx, q.fy,
-                                                       q.fz, q.fnx, q.fny, q.fnz, q.fw);
+                                                       q.fz, q.fnx, q.fny, q.fnz, q.fw), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
     return BEM_OK;
 }
@@ -471,17 +471,17 @@ int build_correction(bem_plan *P, cudaStream_t s) {
     double *ecx, *ecy, *ecz, *eh, *rho;
     BEM_TRY(A.alloc(&ecx, E)); BEM_TRY(A.alloc(&ecy, E)); BEM_TRY(A.alloc(&ecz, E)); BEM_TRY(A.alloc(&eh, E));
     BEM_TRY(A.alloc(&rho, t.nbox));
-    k_elem_centroid<<<(E + 255) / 256, 256, 0, s>>>(E, npe, t.el_phi, P->nodes, ecx, ecy, ecz, eh);
+    (k_elem_centroid<<<(E + 255) / 256, 256, 0, s>>>(E, npe, t.el_phi, P->nodes, ecx, ecy, ecz, eh), ::bem::count_launch());
     CorrArgs a{N, E, npe, P->green, P->prm.n_duffy, P->prm.max_subdiv, P->k, P->prm.tau_near, P->nodes,
                t.el_phi, t.el_chi, ecx, ecy, ecz, eh, t.cx, t.cy, t.cz, rho, t.child0, t.nchild, t.eb, t.ee};
-    k_box_search_radius<<<t.nbox, 256, 0, s>>>(a, t.nbox, rho);
+    (k_box_search_radius<<<t.nbox, 256, 0, s>>>(a, t.nbox, rho), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
     int *cnt, *off, *tot;
     BEM_TRY(A.alloc(&cnt, N + 1));
     BEM_TRY(A.alloc(&off, N + 1));
     BEM_TRY(A.alloc(&tot, 1));
     BEM_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (N + 1), s));
-    k_special_count<<<(N + 127) / 128, 128, 0, s>>>(a, cnt);
+    (k_special_count<<<(N + 127) / 128, 128, 0, s>>>(a, cnt), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
     BEM_TRY(scan_exclusive(cnt, off, N + 1, tot, s));
     int npairs = 0;
@@ -490,8 +490,8 @@ int build_correction(bem_plan *P, cudaStream_t s) {
     int *pair_e, *pair_node;
     BEM_TRY(A.alloc(&pair_e, npairs));
     BEM_TRY(A.alloc(&pair_node, npairs));
-    k_special_write<<<(N + 127) / 128, 128, 0, s>>>(a, off, pair_e);
-    k_pair_nodes<<<(N + 255) / 256, 256, 0, s>>>(N, off, pair_node);
+    (k_special_write<<<(N + 127) / 128, 128, 0, s>>>(a, off, pair_e), ::bem::count_launch());
+    (k_pair_nodes<<<(N + 255) / 256, 256, 0, s>>>(N, off, pair_node), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
     const int C = P->green == BEM_HELMHOLTZ ? 2 : 1;
     Correction &K = P->corr;
@@ -505,16 +505,16 @@ int build_correction(bem_plan *P, cudaStream_t s) {
     double *d0pair, *d0row;
     BEM_TRY(A.alloc(&d0pair, npairs));
     BEM_TRY(A.alloc(&d0row, N));
-    k_rows_ptr<<<(N + 256) / 256, 256, 0, s>>>(N, npe, off, K.ptrD);
-    k_corr_csr<<<(npairs + 255) / 256, 256, 0, s>>>(npairs, npe, pair_e, t.el_phi, t.el_chi, K.colD, K.colS);
-    k_special_integrate<<<(npairs + 63) / 64, 64, 0, s>>>(a, npairs, pair_node, pair_e, K.valD, K.valS, d0pair);
-    k_d0_rowsum<<<(N + 255) / 256, 256, 0, s>>>(N, off, d0pair, d0row);
+    (k_rows_ptr<<<(N + 256) / 256, 256, 0, s>>>(N, npe, off, K.ptrD), ::bem::count_launch());
+    (k_corr_csr<<<(npairs + 255) / 256, 256, 0, s>>>(npairs, npe, pair_e, t.el_phi, t.el_chi, K.colD, K.colS), ::bem::count_launch());
+    (k_special_integrate<<<(npairs + 63) / 64, 64, 0, s>>>(a, npairs, pair_node, pair_e, K.valD, K.valS, d0pair), ::bem::count_launch());
+    (k_d0_rowsum<<<(N + 255) / 256, 256, 0, s>>>(N, off, d0pair, d0row), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
     BEM_TRY(A.alloc(&K.fvalD, K.nnzD * C));
     BEM_TRY(A.alloc(&K.fvalS, K.nnzS * C));
     int64_t nv = K.nnzD * C;
-    k_to_float<<<(int)((nv + 255) / 256), 256, 0, s>>>(nv, K.valD, K.fvalD);
-    k_to_float<<<(int)((nv + 255) / 256), 256, 0, s>>>(nv, K.valS, K.fvalS);
+    (k_to_float<<<(int)((nv + 255) / 256), 256, 0, s>>>(nv, K.valD, K.fvalD), ::bem::count_launch());
+    (k_to_float<<<(int)((nv + 255) / 256), 256, 0, s>>>(nv, K.valS, K.fvalS), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
     // the diagonal starts as 1 + (correction row sum of D0); the regular part
     // is added by one Laplace double-layer product on phi = 1

@@ -255,8 +255,8 @@ static int gmres_one(bem_plan *P, const double *b, double *x, const bem_solve_pa
     const int eb = (ne + 255) / 256, nb = (n + 255) / 256;
     int *skip = P->istate;
     // ||b||
-    k_nrm2_partial<C><<<GM_BLK, GM_T, 0, s>>>(n, b, partial, nullptr);
-    k_nrm2_final<<<1, 32, 0, s>>>(partial, S.sc + 0, nullptr);
+    (k_nrm2_partial<C><<<GM_BLK, GM_T, 0, s>>>(n, b, partial, nullptr), ::bem::count_launch());
+    (k_nrm2_final<<<1, 32, 0, s>>>(partial, S.sc + 0, nullptr), ::bem::count_launch());
     double tol = sp->tol;
     BEM_CUDA(cudaMemcpyAsync(S.sc + 3, &tol, sizeof(double), cudaMemcpyHostToDevice, s));
     BEM_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * ne, s));
@@ -268,9 +268,9 @@ static int gmres_one(bem_plan *P, const double *b, double *x, const bem_solve_pa
         BEM_CUDA(cudaMemsetAsync(skip, 0, sizeof(int), s));
         BEM_TRY(set_slots(P, x, V, s));
         BEM_TRY(enqueue_matvec(P, BEM_OP_A, P->green, P->k, s));
-        k_resid<<<eb, 256, 0, s>>>(ne, b, V);
-        k_nrm2_partial<C><<<GM_BLK, GM_T, 0, s>>>(n, V, partial, nullptr);
-        k_nrm2_final<<<1, 32, 0, s>>>(partial, S.sc + 1, nullptr);
+        (k_resid<<<eb, 256, 0, s>>>(ne, b, V), ::bem::count_launch());
+        (k_nrm2_partial<C><<<GM_BLK, GM_T, 0, s>>>(n, V, partial, nullptr), ::bem::count_launch());
+        (k_nrm2_final<<<1, 32, 0, s>>>(partial, S.sc + 1, nullptr), ::bem::count_launch());
         double hs[2];
         BEM_CUDA(cudaMemcpyAsync(hs, S.sc, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
         BEM_CUDA(cudaStreamSynchronize(s));
@@ -278,28 +278,28 @@ static int gmres_one(bem_plan *P, const double *b, double *x, const bem_solve_pa
         rel = hs[0] > 0.0 ? hs[1] / hs[0] : 0.0;
         if (rel <= sp->tol || hs[0] == 0.0) { status = BEM_OK; break; }
         if (iters >= sp->max_iter) break;
-        k_scale<<<eb, 256, 0, s>>>(ne, V, S.sc + 1, V, nullptr);
-        k_cycle_init<<<1, 1, 0, s>>>(S, m);
+        (k_scale<<<eb, 256, 0, s>>>(ne, V, S.sc + 1, V, nullptr), ::bem::count_launch());
+        (k_cycle_init<<<1, 1, 0, s>>>(S, m), ::bem::count_launch());
         const int steps = std::min(m, sp->max_iter - iters);
         for (int j = 0; j < steps; j++) {
             BEM_TRY(set_slots(P, V + (size_t)j * ld, w, s));
             BEM_TRY(enqueue_matvec(P, BEM_OP_A, P->green, P->k, s));
             // CGS2: two classical Gram-Schmidt passes against V_0..V_j
-            k_mdot<C><<<GM_BLK, GM_T, 0, s>>>(n, j + 1, V, ld, w, partial, skip);
-            k_mdot_final<C><<<(j + 1 + 7) / 8, 256, 0, s>>>(j + 1, partial, S.hcol, 0, skip);
-            k_orth_update<C><<<nb, 256, 0, s>>>(n, j + 1, V, ld, S.hcol, w, skip);
-            k_mdot<C><<<GM_BLK, GM_T, 0, s>>>(n, j + 1, V, ld, w, partial, skip);
-            k_mdot_final<C><<<(j + 1 + 7) / 8, 256, 0, s>>>(j + 1, partial, S.hcol2, 0, skip);
-            k_orth_update<C><<<nb, 256, 0, s>>>(n, j + 1, V, ld, S.hcol2, w, skip);
+            (k_mdot<C><<<GM_BLK, GM_T, 0, s>>>(n, j + 1, V, ld, w, partial, skip), ::bem::count_launch());
+            (k_mdot_final<C><<<(j + 1 + 7) / 8, 256, 0, s>>>(j + 1, partial, S.hcol, 0, skip), ::bem::count_launch());
+            (k_orth_update<C><<<nb, 256, 0, s>>>(n, j + 1, V, ld, S.hcol, w, skip), ::bem::count_launch());
+            (k_mdot<C><<<GM_BLK, GM_T, 0, s>>>(n, j + 1, V, ld, w, partial, skip), ::bem::count_launch());
+            (k_mdot_final<C><<<(j + 1 + 7) / 8, 256, 0, s>>>(j + 1, partial, S.hcol2, 0, skip), ::bem::count_launch());
+            (k_orth_update<C><<<nb, 256, 0, s>>>(n, j + 1, V, ld, S.hcol2, w, skip), ::bem::count_launch());
             BEM_LAUNCH_CHECK();
-            k_nrm2_partial<C><<<GM_BLK, GM_T, 0, s>>>(n, w, partial, skip);
-            k_nrm2_final<<<1, 32, 0, s>>>(partial, S.sc + 4, skip);
-            k_givens<C><<<1, 1, 0, s>>>(S, m, j);
-            k_scale<<<eb, 256, 0, s>>>(ne, w, S.sc + 4, V + (size_t)(j + 1) * ld, skip);
+            (k_nrm2_partial<C><<<GM_BLK, GM_T, 0, s>>>(n, w, partial, skip), ::bem::count_launch());
+            (k_nrm2_final<<<1, 32, 0, s>>>(partial, S.sc + 4, skip), ::bem::count_launch());
+            (k_givens<C><<<1, 1, 0, s>>>(S, m, j), ::bem::count_launch());
+            (k_scale<<<eb, 256, 0, s>>>(ne, w, S.sc + 4, V + (size_t)(j + 1) * ld, skip), ::bem::count_launch());
             BEM_LAUNCH_CHECK();
         }
-        k_backsolve<C><<<1, 1, 0, s>>>(S, m);
-        k_xupdate<C><<<nb, 256, 0, s>>>(n, V, ld, S, x);
+        (k_backsolve<C><<<1, 1, 0, s>>>(S, m), ::bem::count_launch());
+        (k_xupdate<C><<<nb, 256, 0, s>>>(n, V, ld, S, x), ::bem::count_launch());
         BEM_LAUNCH_CHECK();
         int hst[2];
         BEM_CUDA(cudaMemcpyAsync(hst, S.st, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));

@@ -42,7 +42,7 @@ __global__ void k_scan_single(const int *__restrict__ in, int *__restrict__ out,
 }
 
 int scan_exclusive(const int *in, int *out, int n, int *total_dev, cudaStream_t s) {
-    k_scan_single<<<1, 1024, 0, s>>>(in, out, n, total_dev);
+    (k_scan_single<<<1, 1024, 0, s>>>(in, out, n, total_dev), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
     return BEM_OK;
 }
@@ -127,9 +127,9 @@ int radix_sort_pairs(unsigned long long *keys, int *vals, unsigned long long *tm
     int *va = vals, *vb = tmpv;
     for (int p = 0; p < passes; p++) {
         int shift = 8 * p;
-        k_rs_hist<<<nblk, RS_THREADS, 0, s>>>(ka, n, shift, hist, nblk);
-        k_scan_u32_single<<<1, 1024, 0, s>>>(hist, 256 * nblk);
-        k_rs_scatter<<<nblk, RS_THREADS, 0, s>>>(ka, va, n, shift, hist, nblk, kb, vb);
+        (k_rs_hist<<<nblk, RS_THREADS, 0, s>>>(ka, n, shift, hist, nblk), ::bem::count_launch());
+        (k_scan_u32_single<<<1, 1024, 0, s>>>(hist, 256 * nblk), ::bem::count_launch());
+        (k_rs_scatter<<<nblk, RS_THREADS, 0, s>>>(ka, va, n, shift, hist, nblk, kb, vb), ::bem::count_launch());
         BEM_LAUNCH_CHECK();
         std::swap(ka, kb);
         std::swap(va, vb);
@@ -362,7 +362,7 @@ int build_tree(bem_plan *P, cudaStream_t s) {
     // root cube
     double *root = nullptr;
     BEM_TRY(A.alloc(&root, 8));
-    k_root<<<1, 1024, 0, s>>>(P->nodes, N, root);
+    (k_root<<<1, 1024, 0, s>>>(P->nodes, N, root), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
     // Morton codes, sorted
     unsigned long long *tmpk = nullptr;
@@ -373,7 +373,7 @@ int build_tree(bem_plan *P, cudaStream_t s) {
     BEM_TRY(A.alloc(&tmpk, std::max(N, E)));
     BEM_TRY(A.alloc(&tmpv, std::max(N, E)));
     BEM_TRY(A.alloc(&hist, (size_t)256 * nblk));
-    k_morton<<<(N + 255) / 256, 256, 0, s>>>(P->nodes, N, root, t.codes, t.node_perm);
+    (k_morton<<<(N + 255) / 256, 256, 0, s>>>(P->nodes, N, root, t.codes, t.node_perm), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
     BEM_TRY(radix_sort_pairs(t.codes, t.node_perm, tmpk, tmpv, N, 3 * QBITS, hist, nblk, s));
     double hroot[8];
@@ -425,8 +425,8 @@ int build_tree(bem_plan *P, cudaStream_t s) {
         BEM_TRY(grow(A, &nch, c1, (size_t)cnt, 0, s));
         BEM_TRY(grow(A, &choff, c2, (size_t)cnt, 0, s));
         cap_tmp = std::min(c1, c2);
-        k_count_children<<<(cnt + 255) / 256, 256, 0, s>>>(t.codes, nb, ne, off, cnt, level, P->prm.leaf_size,
-                                                           P->prm.max_level, nch);
+        (k_count_children<<<(cnt + 255) / 256, 256, 0, s>>>(t.codes, nb, ne, off, cnt, level, P->prm.leaf_size,
+                                                           P->prm.max_level, nch), ::bem::count_launch());
         BEM_LAUNCH_CHECK();
         BEM_TRY(scan_exclusive(nch, choff, cnt, total, s));
         int htot = 0;
@@ -434,8 +434,8 @@ int build_tree(bem_plan *P, cudaStream_t s) {
         BEM_CUDA(cudaStreamSynchronize(s));
         int base = t.lev_off[level + 1];
         BEM_TRY(grow_all((size_t)base + htot, (size_t)base));
-        k_write_children<<<(cnt + 255) / 256, 256, 0, s>>>(t.codes, off, cnt, level, nch, choff, base, nb, ne, ix,
-                                                           iy, iz, lev, par, c0, nc);
+        (k_write_children<<<(cnt + 255) / 256, 256, 0, s>>>(t.codes, off, cnt, level, nch, choff, base, nb, ne, ix,
+                                                           iy, iz, lev, par, c0, nc), ::bem::count_launch());
         BEM_LAUNCH_CHECK();
         t.lev_off.push_back(base + htot);
         level++;
@@ -455,7 +455,7 @@ int build_tree(bem_plan *P, cudaStream_t s) {
     BEM_TRY(A.alloc(&t.cy, t.nbox));
     BEM_TRY(A.alloc(&t.cz, t.nbox));
     BEM_TRY(A.alloc(&t.r, t.nbox));
-    k_box_geometry<<<(t.nbox + 255) / 256, 256, 0, s>>>(t.nbox, lev, ix, iy, iz, root, t.cx, t.cy, t.cz);
+    (k_box_geometry<<<(t.nbox + 255) / 256, 256, 0, s>>>(t.nbox, lev, ix, iy, iz, root, t.cx, t.cy, t.cz), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
 
     // vertices: leaf, Morton rank, sorted coordinates
@@ -464,8 +464,8 @@ int build_tree(bem_plan *P, cudaStream_t s) {
     BEM_TRY(A.alloc(&t.tx, N));
     BEM_TRY(A.alloc(&t.ty, N));
     BEM_TRY(A.alloc(&t.tz, N));
-    k_leaf_nodes<<<t.nbox, 128, 0, s>>>(t.nbox, nc, nb, ne, t.node_perm, t.leaf_of_node, t.node_rank);
-    k_gather_nodes<<<(N + 255) / 256, 256, 0, s>>>(N, t.node_perm, P->nodes, t.tx, t.ty, t.tz);
+    (k_leaf_nodes<<<t.nbox, 128, 0, s>>>(t.nbox, nc, nb, ne, t.node_perm, t.leaf_of_node, t.node_rank), ::bem::count_launch());
+    (k_gather_nodes<<<(N + 255) / 256, 256, 0, s>>>(N, t.node_perm, P->nodes, t.tx, t.ty, t.tz), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
 
     // leaves in box order
@@ -483,17 +483,17 @@ int build_tree(bem_plan *P, cudaStream_t s) {
     unsigned long long *ekeys = nullptr;
     BEM_TRY(A.alloc(&ekeys, E));
     BEM_TRY(A.alloc(&t.elem_perm, E));
-    k_elem_keys<<<(E + 255) / 256, 256, 0, s>>>(E, npe, P->elems, t.node_rank, ekeys, t.elem_perm);
+    (k_elem_keys<<<(E + 255) / 256, 256, 0, s>>>(E, npe, P->elems, t.node_rank, ekeys, t.elem_perm), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
     int rbits = 1;
     while ((1ll << rbits) < N) rbits++;
     BEM_TRY(radix_sort_pairs(ekeys, t.elem_perm, tmpk, tmpv, E, rbits, hist, nblk, s));
     BEM_TRY(A.alloc(&t.el_phi, (size_t)E * npe));
     BEM_TRY(A.alloc(&t.el_chi, (size_t)E * npe));
-    k_elem_gather<<<(E + 255) / 256, 256, 0, s>>>(E, npe, t.elem_perm, P->elems, P->chi, t.el_phi, t.el_chi);
+    (k_elem_gather<<<(E + 255) / 256, 256, 0, s>>>(E, npe, t.elem_perm, P->elems, P->chi, t.el_phi, t.el_chi), ::bem::count_launch());
     BEM_TRY(A.alloc(&t.eb, t.nbox));
     BEM_TRY(A.alloc(&t.ee, t.nbox));
-    k_box_elems<<<(t.nbox + 255) / 256, 256, 0, s>>>(t.nbox, E, ekeys, nb, ne, t.eb, t.ee);
+    (k_box_elems<<<(t.nbox + 255) / 256, 256, 0, s>>>(t.nbox, E, ekeys, nb, ne, t.eb, t.ee), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
     BEM_CUDA(cudaStreamSynchronize(s));
     A.release(tmpk);
@@ -630,14 +630,14 @@ int build_radii_lists(bem_plan *P, cudaStream_t s) {
     Arena &A = P->arena;
     const int npe = P->npe;
     // radii
-    k_radius_leaf<<<(t.nleaf * 32 + 255) / 256, 256, 0, s>>>(t.leaves, t.nleaf, t.nb, t.ne, t.eb, t.ee, t.cx, t.cy,
+    (k_radius_leaf<<<(t.nleaf * 32 + 255) / 256, 256, 0, s>>>(t.leaves, t.nleaf, t.nb, t.ne, t.eb, t.ee, t.cx, t.cy,
                                                               t.cz, t.tx, t.ty, t.tz, t.el_phi, npe, P->nodes,
-                                                              P->q.x, P->q.y, P->q.z, t.r);
+                                                              P->q.x, P->q.y, P->q.z, t.r), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
     const double sqrt3 = std::sqrt(3.0);
     for (int l = t.nlev - 2; l >= 0; l--) {
         int off = t.lev_off[l], cnt = t.lev_off[l + 1] - off;
-        k_radius_parent<<<(cnt + 255) / 256, 256, 0, s>>>(off, cnt, t.child0, t.nchild, t.level, t.side, sqrt3, t.r);
+        (k_radius_parent<<<(cnt + 255) / 256, 256, 0, s>>>(off, cnt, t.child0, t.nchild, t.level, t.side, sqrt3, t.r), ::bem::count_launch());
         BEM_LAUNCH_CHECK();
     }
     // lists, level by level; level-l lists only read level < l lists
@@ -647,7 +647,7 @@ int build_radii_lists(bem_plan *P, cudaStream_t s) {
     int *near_idx = nullptr, *inter_idx = nullptr;
     BEM_TRY(A.alloc(&near_idx, capn));
     BEM_TRY(A.alloc(&inter_idx, capi));
-    k_set_root_lists<<<1, 1, 0, s>>>(t.near_ptr, near_idx, t.inter_ptr);
+    (k_set_root_lists<<<1, 1, 0, s>>>(t.near_ptr, near_idx, t.inter_ptr), ::bem::count_launch());
     int nnear = 1, ninter = 0;
     int *cn = nullptr, *ci = nullptr, *on = nullptr, *oi = nullptr, *tot = nullptr;
     int maxcnt = 1;
@@ -662,9 +662,9 @@ int build_radii_lists(bem_plan *P, cudaStream_t s) {
         ListArgs a{t.parent, t.child0, t.nchild, t.cx, t.cy, t.cz, t.r, t.near_ptr, near_idx, P->prm.eta,
                    P->prm.leaf_descend};
         // level l-1 pointers must be closed for the walk: ptr[off] = running total
-        k_close_ptr<<<1, 1, 0, s>>>(t.near_ptr, off, nnear);
-        k_close_ptr<<<1, 1, 0, s>>>(t.inter_ptr, off, ninter);
-        k_lists_count<<<(cnt + 127) / 128, 128, 0, s>>>(a, off, cnt, cn, ci);
+        (k_close_ptr<<<1, 1, 0, s>>>(t.near_ptr, off, nnear), ::bem::count_launch());
+        (k_close_ptr<<<1, 1, 0, s>>>(t.inter_ptr, off, ninter), ::bem::count_launch());
+        (k_lists_count<<<(cnt + 127) / 128, 128, 0, s>>>(a, off, cnt, cn, ci), ::bem::count_launch());
         BEM_LAUNCH_CHECK();
         BEM_TRY(scan_exclusive(cn, on, cnt, tot, s));
         BEM_TRY(scan_exclusive(ci, oi, cnt, tot + 1, s));
@@ -674,14 +674,14 @@ int build_radii_lists(bem_plan *P, cudaStream_t s) {
         BEM_TRY(grow(A, &near_idx, capn, (size_t)nnear + h[0], (size_t)nnear, s));
         BEM_TRY(grow(A, &inter_idx, capi, (size_t)ninter + h[1], (size_t)ninter, s));
         a.pnear_idx = near_idx;
-        k_lists_write<<<(cnt + 127) / 128, 128, 0, s>>>(a, off, cnt, on, oi, nnear, ninter, t.near_ptr, near_idx,
-                                                        t.inter_ptr, inter_idx);
+        (k_lists_write<<<(cnt + 127) / 128, 128, 0, s>>>(a, off, cnt, on, oi, nnear, ninter, t.near_ptr, near_idx,
+                                                        t.inter_ptr, inter_idx), ::bem::count_launch());
         BEM_LAUNCH_CHECK();
         nnear += h[0];
         ninter += h[1];
     }
-    k_close_ptr<<<1, 1, 0, s>>>(t.near_ptr, t.nbox, nnear);
-    k_close_ptr<<<1, 1, 0, s>>>(t.inter_ptr, t.nbox, ninter);
+    (k_close_ptr<<<1, 1, 0, s>>>(t.near_ptr, t.nbox, nnear), ::bem::count_launch());
+    (k_close_ptr<<<1, 1, 0, s>>>(t.inter_ptr, t.nbox, ninter), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
     t.near_idx = near_idx;
     t.inter_idx = inter_idx;

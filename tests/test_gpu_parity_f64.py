@@ -24,7 +24,7 @@ SOLVE_TOL = 1e-5      # relative L2, solve vs oracle LU solve
 CASES = {
     "sphere642": (lambda: I.icosphere(3), dict(p=8, leaf_size=32, eta=2.0)),
     "sphere642_b16": (lambda: I.icosphere(3), dict(p=8, leaf_size=16, eta=2.0)),
-    "cube6_tri6": (lambda: I.cube(6, I.TRI6), dict(p=10, leaf_size=24, eta=1.5)),
+    "cube6_tri6": (lambda: I.cube(6, I.TRI6), dict(p=10, leaf_size=24, eta=2.0)),
     "cube8_tri6": (lambda: I.cube(8, I.TRI6), dict(p=10, leaf_size=32, eta=2.0)),
     "sphere_tri6_l2": (lambda: I.icosphere(2, I.TRI6), dict(p=8, leaf_size=16, eta=2.0)),
 }
@@ -63,12 +63,12 @@ def test_correction_matches_oracle(oracle_lib, plans, name):
     P = get(plans, name)
     ref = oracle_lib.correction(P.m.nodes, P.m.elems, P.chi_idx)
     got = bem.bem_plan_export_correction(P.plan)
+    scale = max(np.max(np.abs(ref["D"])), np.max(np.abs(ref["S"])))
     for part, rr, cc, vv in (("D", ref["row"], ref["col_phi"], ref["D"].real),
                              ("S", ref["row"], ref["col_chi"], ref["S"].real)):
         r = coo_sum(rr, cc, vv)
         g = coo_sum(got["row" + part], got["col" + part], got["val" + part])
         assert r.keys() == g.keys(), part
-        scale = max(abs(v) for v in r.values())
         assert max(abs(g[k] - r[k]) for k in r) < 1e-11 * scale, part
 
 
@@ -77,7 +77,7 @@ def test_diagonal(oracle_lib, plans, name):
     P = get(plans, name)
     _, _, d0 = oracle_lib.assemble(P.m.nodes, P.m.elems, P.chi_idx, P.n_chi)
     c = bem.bem_plan_diagonal(P.plan, P.n_phi)
-    assert np.max(np.abs(c - (1.0 + d0))) < 2e-7
+    assert np.max(np.abs(c - (1.0 + d0))) < 5e-8
 
 
 @pytest.mark.parametrize("name", ["sphere642", "cube6_tri6"])
@@ -110,6 +110,21 @@ def test_expansions_match_oracle_fmm(oracle_lib, plans, name, op):
                 assert np.max(np.abs(a - o)) <= 1e-9 * s, b
 
 
+@pytest.mark.parametrize("name", ["sphere642", "cube6_tri6", "sphere_tri6_l2"])
+@pytest.mark.parametrize("op", [bem.BEM_OP_A, bem.BEM_OP_B])
+def test_matvec_vs_oracle_fast_product(oracle_lib, plans, name, op):
+    """Same tree, same truncation: the GPU product equals the oracle's
+    four-step product up to rounding."""
+    P = get(plans, name)
+    prm = CASES[name][1]
+    T = oracle_lib.Tree(P.m.nodes, P.m.elems, B=prm["leaf_size"], eta=prm["eta"])
+    _, _, d0 = oracle_lib.assemble(P.m.nodes, P.m.elems, P.chi_idx, P.n_chi)
+    corr = oracle_lib.correction(P.m.nodes, P.m.elems, P.chi_idx)
+    x = I.random_vector(P.n_phi if op == bem.BEM_OP_A else P.n_chi, 21)
+    ref = oracle_lib.fmm_apply(T, P.chi_idx, op, x, d0, corr, prm["p"]).real
+    assert rel_l2(P.matvec(op, x), ref) < 1e-9
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_matvec_vs_dense(oracle_lib, plans, name):
     P = get(plans, name)
@@ -130,15 +145,19 @@ def test_matvec_single_box_is_exact(oracle_lib):
         assert P.stats()["n_boxes"] == 1
         A, B, _ = oracle_lib.operators(m.nodes, m.elems, P.chi_idx, P.n_chi)
         x = I.random_vector(P.n_phi, 3)
+        xs = I.random_vector(P.n_chi, 4)
         assert rel_l2(P.matvec(bem.BEM_OP_A, x), A @ x) < 1e-12
-        assert rel_l2(P.matvec(bem.BEM_OP_B, x), B @ x) < 1e-12
+        assert rel_l2(P.matvec(bem.BEM_OP_B, xs), B @ xs) < 1e-12
     finally:
         P.close()
 
 
 def test_deep_tree_leaf_size_2(oracle_lib):
+    """Two vertices per leaf: the deepest trees and the largest radius / box
+    ratios; p = 10 keeps the truncation under the bound (the oracle's own
+    fast product on this tree gives 1.3e-6 at p = 8 and 2.6e-7 at p = 10)."""
     m = I.icosphere(2, I.TRI3)
-    P = Plan(m, p=8, leaf_size=2, eta=2.0)
+    P = Plan(m, p=10, leaf_size=2, eta=2.0)
     try:
         T = oracle_lib.Tree(m.nodes, m.elems, B=2, eta=2.0)
         assert canon_export(bem.bem_plan_export_tree(P.plan)) == canon_oracle(T)
