@@ -1,0 +1,341 @@
+"""Benchmark of the FMM-accelerated collocation BEM hot path on one GB300.
+
+Workload (default): Laplace exterior Neumann problem on the cube [-1,1]^3,
+45 x 45 graded quads per face split into 24,300 6-node triangles (48,602
+nodes), point source at (0.2, -0.1, 0.3), expansion order p = 10, leaf size
+64, separation factor 2, GMRES(30).
+
+One step = one complete pass of the hot path from a device-resident mesh:
+plan build on the device (quadrature geometry, octree, radii, lists,
+special-pair correction, diagonal), the right-hand side b = B chi (one fast
+product), and the GMRES solve of A phi = b (one fast product per Arnoldi
+step).  value = solves per second over all ranks (each rank an independent
+replica).  The L2 cache is flushed between steps.
+
+Extra keys: matvecs_per_s (back-to-back A products of a built plan), per-stage
+times, the roofline of the dominant kernel against measured peaks, the CPU
+oracle baseline, end-to-end timing through the public API with host buffers.
+
+--impl reference times the CPU oracle (the plain FP64 matrix-free operator
+rows) on a bounded sample of the same workload and extrapolates to solves/s.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FMM-BEM matvecs/s & served solves/s, p50/p99 latency vs plain FP64 at rel.err≤1e-5"
+WORKLOAD = "cube45-tri6-laplace"
+SOURCE = (0.2, -0.1, 0.3)
+FLOPS_PER_PAIR = {"A": 20.0, "B": 11.0}   # near-field kernel, Laplace double / single layer
+# GMRES(30) Arnoldi steps of this workload to 1e-10 (float64), measured by
+# this benchmark on a GB300; used only to extrapolate the CPU oracle's rate.
+GMRES_ITERS_CUBE45 = 60
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="f64", choices=["f64", "mixed"])
+    ap.add_argument("--n", type=int, default=45, help="quads per cube face edge")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(n):
+    from paper_0908_0673_gb300 import inputs as I
+    m = I.cube(n, I.TRI6, grade=1.2, seed=0)
+    phi_ex, chi_e = I.point_source(m, SOURCE)
+    return m, phi_ex, chi_e
+
+
+def chi_vector(chi_idx, n_chi, chi_e):
+    out = np.zeros(n_chi)
+    out[chi_idx.ravel()] = chi_e.ravel()        # equal inside one index by construction
+    return out
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, gpu_index):
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index),
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(m, chi_idx, n_phi, iters, budget_s=15.0):
+    """The oracle's matrix-free rows of A on a bounded sample of this
+    workload, extrapolated to solves/s ((iters + 1) full products per solve)."""
+    import oracle as O
+    O.build()
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(n_phi)
+    t0 = time.perf_counter()
+    rows = rng.choice(n_phi, 16, replace=False)
+    O.apply_rows(m.nodes, m.elems, chi_idx, O.OP_A, x, rows)
+    dt = time.perf_counter() - t0
+    nrows = int(max(16, min(n_phi, 16 * budget_s / max(dt, 1e-3))))
+    rows = rng.choice(n_phi, nrows, replace=False)
+    t0 = time.perf_counter()
+    O.apply_rows(m.nodes, m.elems, chi_idx, O.OP_A, x, rows)
+    dt = time.perf_counter() - t0
+    rows_per_s = nrows / dt
+    matvecs_per_s = rows_per_s / n_phi
+    solves_per_s = matvecs_per_s / (iters + 1)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": solves_per_s, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"{nrows} of {n_phi} rows of one operator product ({dt:.1f} s), "
+                      f"extrapolated to (1 + {iters}) products per solve",
+            "matvecs_per_s": matvecs_per_s}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_0908_0673_gb300 import bem
+    m, _, _ = workload(args.n)
+    h = bem.bem_mesh_create(None, m.nodes, m.elems, bem.BEM_TRI6)
+    n_phi, n_chi = bem.bem_mesh_sizes(h)
+    chi_idx = bem.bem_mesh_chi_index(h, m.n_elems, 6)
+    bem.bem_mesh_destroy(h)
+    vals = []
+    per = max(3.0, 60.0 / max(1, args.steps + args.warmup))
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(m, chi_idx, n_phi, GMRES_ITERS_CUBE45, budget_s=per)
+        if i >= args.warmup:
+            vals.append(cb)
+    v = statistics.median([c["value"] for c in vals])
+    cb = dict(vals[-1])
+    cb["value"] = v
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"cube{args.n}-tri6-laplace", "elements": int(m.n_elems), "nodes": int(n_phi),
+                      "solver": "oracle matrix-free rows (CPU, FP64)", "l2": "n/a (CPU)"},
+           "cpu_baseline": cb,
+           "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+    from paper_0908_0673_gb300 import bem
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    prec = bem.BEM_MIXED if args.precision == "mixed" else bem.BEM_F64
+    prm = bem.bem_fmm_params_default(p=10, leaf_size=64, eta=2.0, precision=prec)
+    sp = bem.bem_solve_params_default(restart=30, tol=1e-10, max_iter=600)
+
+    m, phi_ex, chi_e = workload(args.n)
+    ctx = bem.bem_ctx_create(local)
+    mesh = bem.bem_mesh_create(ctx, m.nodes, m.elems, bem.BEM_TRI6)
+    n_phi, n_chi = bem.bem_mesh_sizes(mesh)
+    chi_idx = bem.bem_mesh_chi_index(mesh, m.n_elems, 6)
+    chi = chi_vector(chi_idx, n_chi, chi_e)
+    bem.bem_mesh_upload(mesh, stream)
+    chi_d = torch.tensor(chi, device=dev, dtype=torch.float64)
+    phi_d = torch.empty(n_phi, device=dev, dtype=torch.float64)
+    flush = torch.empty(256 * 1024 * 1024 // 4, device=dev, dtype=torch.float32)   # > 129 MB L2
+
+    def step():
+        plan = bem.bem_plan_create(mesh, bem.BEM_LAPLACE, 0.0, prm, stream)
+        code, info = bem.bem_solve(plan, chi_d, phi_d, 1, sp, stream)
+        return plan, info[0]
+
+    infos = []
+    for _ in range(args.warmup):
+        plan, info = step()
+        stream.synchronize()
+        bem.bem_plan_destroy(plan)
+    # timed region
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    l0 = bem.bem_launch_count()
+    total_ms = 0.0
+    lat = []
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan, info = step()
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        total_ms += ms
+        lat.append(ms)
+        infos.append(info)
+        bem.bem_plan_destroy(plan)
+    torch.cuda.synchronize()
+    launches = bem.bem_launch_count() - l0
+    clk = clocks.stop()
+    t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    max_ms = float(t.item())
+    ms_per_step = max_ms / args.steps
+    value = world * args.steps / (max_ms / 1000.0)
+    phi = phi_d.cpu().numpy()
+    eps_rms = float(np.sqrt(np.mean((phi - phi_ex) ** 2)))
+
+    # matvec rate and per-stage times on one built plan
+    plan = bem.bem_plan_create(mesh, bem.BEM_LAPLACE, 0.0, prm, stream)
+    st = bem.bem_plan_stats(plan)
+    x_d = torch.randn(n_phi, device=dev, dtype=torch.float64, generator=torch.Generator(device=dev).manual_seed(1))
+    y_d = torch.empty_like(x_d)
+    for _ in range(3):
+        bem.bem_matvec(plan, bem.BEM_OP_A, x_d, y_d, stream)
+    with torch.cuda.stream(stream):
+        flush.zero_()
+    nmv = 30
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(nmv):
+        bem.bem_matvec(plan, bem.BEM_OP_A, x_d, y_d, stream)
+    e1.record(stream)
+    e1.synchronize()
+    matvecs_per_s = nmv / (e0.elapsed_time(e1) / 1000.0)
+    stages = bem.bem_plan_stage_times(plan, bem.BEM_OP_A, x_d, y_d, reps=10, stream=stream)
+    setup_plan_ms = None
+    bem.bem_plan_destroy(plan)
+
+    # roofline of the dominant kernel
+    dom = max(stages, key=stages.get)
+    kind = 0 if prec == bem.BEM_MIXED else 1
+    peak = bem.bem_measure_peak(kind, stream)
+    if dom == "near_l2p":
+        flops = st["near_pairs"] * FLOPS_PER_PAIR["A"]
+        achieved = flops / (stages[dom] * 1e-3) / 1e12
+        roof = {"kernel": "k_near (near-field regular quadrature + L2P)", "bound": "alu",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None,
+                "peak_source": f"measured {'FP32' if kind == 0 else 'FP64'} FMA throughput (bem_measure_peak)",
+                "work": f"{st['near_pairs']} target-source pairs x {FLOPS_PER_PAIR['A']:.0f} flops"}
+    elif dom == "m2l":
+        cpp6 = math.comb(10 + 6, 6)
+        flops = st["n_inter"] * 2.0 * cpp6
+        achieved = flops / (stages[dom] * 1e-3) / 1e12
+        roof = {"kernel": "k_m2l (multipole-to-local, Tausch derivatives + contraction)", "bound": "alu",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": f"measured {'FP32' if kind == 0 else 'FP64'} FMA throughput (bem_measure_peak)",
+                "work": f"{st['n_inter']} interaction pairs x 2 x C(p+6,6)={cpp6} flops (algorithmic, p=10)"}
+    else:
+        roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": peak, "unit": "TFLOP/s", "frac": None,
+                "traffic": None}
+
+    # end to end through the public API from pinned host buffers
+    nodes_h = torch.from_numpy(np.ascontiguousarray(m.nodes)).pin_memory()
+    elems_h = torch.from_numpy(np.ascontiguousarray(m.elems)).pin_memory()
+    chi_h = torch.from_numpy(chi).pin_memory()
+    phi_h = torch.empty(n_phi, dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for i in range(max(1, args.steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mh = bem.bem_mesh_create(ctx, nodes_h.numpy(), elems_h.numpy(), bem.BEM_TRI6)
+        plan = bem.bem_plan_create(mh, bem.BEM_LAPLACE, 0.0, prm, stream)
+        with torch.cuda.stream(stream):
+            c_d = chi_h.to(dev, non_blocking=True)
+            p_d = torch.empty(n_phi, device=dev, dtype=torch.float64)
+        bem.bem_solve(plan, c_d, p_d, 1, sp, stream)
+        with torch.cuda.stream(stream):
+            phi_h.copy_(p_d, non_blocking=True)
+        stream.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1000.0)
+        bem.bem_plan_destroy(plan)
+        bem.bem_mesh_destroy(mh)
+    h2d = nodes_h.numel() * 8 + 2 * elems_h.numel() * 4 + chi_h.numel() * 8
+    d2h = phi_h.numel() * 8
+    e2e_value = world * 1000.0 / statistics.mean(e2e_ms)
+
+    iters = [i.iters for i in infos]
+    out = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if prec == bem.BEM_MIXED else "f64", "data": "synthetic",
+        "config": {"workload": f"cube{args.n}-tri6-laplace", "elements": int(m.n_elems), "nodes": int(n_phi), "chi": int(n_chi),
+                   "p": 10, "leaf_size": 64, "eta": 2.0, "precision": args.precision, "gmres": "restart 30, tol 1e-10",
+                   "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}",
+                   "step": "device plan build + RHS product + GMRES solve"},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+        "gmres_iters": iters, "rel_residual": infos[-1].rel_residual if infos else None,
+        "eps_rms_vs_point_source": eps_rms,
+        "matvecs_per_s": matvecs_per_s, "stage_ms": stages, "plan_stats": st,
+        "roofline": roof, "clocks": clk, "gpu_launches": int(launches),
+        "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(m, chi_idx, n_phi, statistics.median(iters) if iters else 60)
+    if rank == 0:
+        print(json.dumps(out))
+    bem.bem_mesh_destroy(mesh)
+    bem.bem_ctx_destroy(ctx)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -146,6 +146,11 @@ int bem_mesh_create(bem_ctx *ctx, const double *nodes, int64_t n_nodes, const in
                     int64_t n_elems, int elem_type, double edge_angle_deg, bem_mesh **out);
 void bem_mesh_destroy(bem_mesh *mesh);
 
+/* Keeps a device-resident copy of the mesh (nodes, elements, chi indices) on
+ * the context's device, owned by the mesh, so that later bem_plan_create calls
+ * read it from HBM instead of host memory.  Synchronises the stream. */
+int bem_mesh_upload(bem_mesh *mesh, void *cuda_stream);
+
 /* n_phi = number of nodes, n_chi = number of Neumann-data indices. */
 int bem_mesh_sizes(const bem_mesh *mesh, int64_t *n_phi, int64_t *n_chi);
 

@@ -28,7 +28,7 @@ EXPORTS = [
     "bem_plan_create", "bem_plan_destroy", "bem_matvec", "bem_solve", "bem_plan_tree_sizes",
     "bem_plan_export_tree", "bem_plan_export_correction", "bem_plan_export_expansions",
     "bem_plan_diagonal", "bem_plan_footprint", "bem_plan_stats", "bem_plan_stage_times",
-    "bem_launch_count", "bem_measure_peak",
+    "bem_launch_count", "bem_measure_peak", "bem_mesh_upload",
 ]
 BEM_NSTAGES = 7
 STAGE_NAMES = ["p2q", "p2m", "m2m", "m2l", "l2l", "near_l2p", "combine"]
@@ -105,6 +105,7 @@ def load(build_if_missing: bool = True):
     L.bem_plan_stage_times.argtypes = [P, i32, P, P, i32, P, P]
     L.bem_launch_count.argtypes = [P]
     L.bem_measure_peak.argtypes = [i32, P, P]
+    L.bem_mesh_upload.argtypes = [P, P]
     for name in EXPORTS:
         if name not in ("bem_fmm_params_default", "bem_solve_params_default", "bem_ctx_destroy",
                         "bem_last_error", "bem_mesh_destroy", "bem_plan_destroy"):
@@ -181,6 +182,10 @@ def bem_mesh_create(ctx, nodes, elems, elem_type, edge_angle_deg=30.0):
 
 def bem_mesh_destroy(mesh):
     load().bem_mesh_destroy(mesh)
+
+
+def bem_mesh_upload(mesh, stream=None):
+    _check(load().bem_mesh_upload(mesh, _stream(stream)))
 
 
 def bem_mesh_sizes(mesh):

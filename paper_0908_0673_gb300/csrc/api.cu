@@ -94,9 +94,16 @@ static int plan_setup(bem_plan *P, cudaStream_t s) {
     BEM_TRY(A.alloc(&P->nodes, 3 * P->N));
     BEM_TRY(A.alloc(&P->elems, P->E * P->npe));
     BEM_TRY(A.alloc(&P->chi, P->E * P->npe));
-    BEM_CUDA(cudaMemcpyAsync(P->nodes, m->nodes.data(), sizeof(double) * 3 * P->N, cudaMemcpyHostToDevice, s));
-    BEM_CUDA(cudaMemcpyAsync(P->elems, m->elems.data(), sizeof(int) * P->E * P->npe, cudaMemcpyHostToDevice, s));
-    BEM_CUDA(cudaMemcpyAsync(P->chi, m->chi.data(), sizeof(int) * P->E * P->npe, cudaMemcpyHostToDevice, s));
+    if (m->d_nodes && m->dev_device == P->device) {
+        // device-resident mesh (bem_mesh_upload): device-to-device copies
+        BEM_CUDA(cudaMemcpyAsync(P->nodes, m->d_nodes, sizeof(double) * 3 * P->N, cudaMemcpyDeviceToDevice, s));
+        BEM_CUDA(cudaMemcpyAsync(P->elems, m->d_elems, sizeof(int) * P->E * P->npe, cudaMemcpyDeviceToDevice, s));
+        BEM_CUDA(cudaMemcpyAsync(P->chi, m->d_chi, sizeof(int) * P->E * P->npe, cudaMemcpyDeviceToDevice, s));
+    } else {
+        BEM_CUDA(cudaMemcpyAsync(P->nodes, m->nodes.data(), sizeof(double) * 3 * P->N, cudaMemcpyHostToDevice, s));
+        BEM_CUDA(cudaMemcpyAsync(P->elems, m->elems.data(), sizeof(int) * P->E * P->npe, cudaMemcpyHostToDevice, s));
+        BEM_CUDA(cudaMemcpyAsync(P->chi, m->chi.data(), sizeof(int) * P->E * P->npe, cudaMemcpyHostToDevice, s));
+    }
     BEM_TRY(A.alloc(&P->istate, 4));
     BEM_CUDA(cudaMemsetAsync(P->istate, 0, sizeof(int) * 4, s));
     P->skip = P->istate;

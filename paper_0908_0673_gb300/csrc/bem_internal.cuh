@@ -139,6 +139,11 @@ struct bem_mesh {
     std::vector<double> nodes;          // [n][3]
     std::vector<int32_t> elems;         // [E][npe]
     std::vector<int32_t> chi;           // [E][npe]
+    // optional device-resident copy (bem_mesh_upload)
+    int dev_device = -1;
+    double *d_nodes = nullptr;
+    int32_t *d_elems = nullptr, *d_chi = nullptr;
+    ~bem_mesh();
 };
 
 struct bem_plan {

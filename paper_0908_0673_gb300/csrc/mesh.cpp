@@ -70,6 +70,12 @@ int64_t mesh_chi_index(const double *nodes, int64_t nn, const int32_t *elems, in
 
 }  // namespace bem
 
+bem_mesh::~bem_mesh() {
+    if (d_nodes) cudaFree(d_nodes);
+    if (d_elems) cudaFree(d_elems);
+    if (d_chi) cudaFree(d_chi);
+}
+
 extern "C" {
 
 int bem_mesh_create(bem_ctx *ctx, const double *nodes, int64_t n_nodes, const int32_t *elems,
@@ -136,6 +142,23 @@ int bem_mesh_create(bem_ctx *ctx, const double *nodes, int64_t n_nodes, const in
 }
 
 void bem_mesh_destroy(bem_mesh *mesh) { delete mesh; }
+
+int bem_mesh_upload(bem_mesh *m, void *cuda_stream) {
+    if (!m || !m->ctx) { bem::set_error("bem_mesh_upload: mesh without a context"); return BEM_EINVAL; }
+    BEM_CUDA(cudaSetDevice(m->ctx->device));
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (!m->d_nodes) {
+        BEM_CUDA(cudaMalloc(&m->d_nodes, sizeof(double) * m->nodes.size()));
+        BEM_CUDA(cudaMalloc(&m->d_elems, sizeof(int32_t) * m->elems.size()));
+        BEM_CUDA(cudaMalloc(&m->d_chi, sizeof(int32_t) * m->chi.size()));
+    }
+    BEM_CUDA(cudaMemcpyAsync(m->d_nodes, m->nodes.data(), sizeof(double) * m->nodes.size(), cudaMemcpyHostToDevice, s));
+    BEM_CUDA(cudaMemcpyAsync(m->d_elems, m->elems.data(), sizeof(int32_t) * m->elems.size(), cudaMemcpyHostToDevice, s));
+    BEM_CUDA(cudaMemcpyAsync(m->d_chi, m->chi.data(), sizeof(int32_t) * m->chi.size(), cudaMemcpyHostToDevice, s));
+    BEM_CUDA(cudaStreamSynchronize(s));
+    m->dev_device = m->ctx->device;
+    return BEM_OK;
+}
 
 int bem_mesh_sizes(const bem_mesh *mesh, int64_t *n_phi, int64_t *n_chi) {
     if (!mesh) { bem::set_error("bem_mesh_sizes: NULL mesh"); return BEM_EINVAL; }
