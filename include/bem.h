@@ -174,6 +174,21 @@ void bem_plan_destroy(bem_plan *plan);
  * Stream ordered; no host synchronisation. */
 int bem_matvec(bem_plan *plan, int op, const void *x_dev, void *y_dev, void *cuda_stream);
 
+/* The product of bem_matvec for callers that cannot allocate device memory at
+ * the point of the call: real-time loops that must not synchronise the device
+ * (which an allocation may do), or hosts whose device memory all belongs to
+ * another allocator (a framework's pool) that forbids stray cudaMalloc calls.  The paper has no counterpart: this is an interface for
+ * such callers.  Same arguments and result as bem_matvec; the kernels are
+ * launched directly and their scratch (quadrature strengths, moments, local
+ * expansions, regular sums) lives in one fixed 48 MiB device array of the
+ * library instead of the plan's buffers.  Every GPU that loads the library
+ * holds that array until the process exits.  The first call on a device looks
+ * up the array's address, so make it before any stream capture.  BEM_EINVAL
+ * (with the sizes in the message) if the plan needs more scratch than the
+ * array holds.  All calls share the array: calls that overlap on the GPU race;
+ * order them on one stream. */
+int bem_matvec_noalloc(bem_plan *plan, int op, const void *x_dev, void *y_dev, void *cuda_stream);
+
 /* Solves A phi = B chi for nrhs right-hand sides: b = B chi by one
  * matrix multiplication, then restarted GMRES with float64 Arnoldi (CGS2),
  * Givens rotations and a true residual at every restart.  chi_dev: device

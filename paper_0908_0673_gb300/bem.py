@@ -28,7 +28,7 @@ EXPORTS = [
     "bem_plan_create", "bem_plan_destroy", "bem_matvec", "bem_solve", "bem_plan_tree_sizes",
     "bem_plan_export_tree", "bem_plan_export_correction", "bem_plan_export_expansions",
     "bem_plan_diagonal", "bem_plan_footprint", "bem_plan_stats", "bem_plan_stage_times",
-    "bem_launch_count", "bem_measure_peak", "bem_mesh_upload",
+    "bem_launch_count", "bem_measure_peak", "bem_mesh_upload", "bem_matvec_noalloc",
 ]
 BEM_NSTAGES = 7
 STAGE_NAMES = ["p2q", "p2m", "m2m", "m2l", "l2l", "near_l2p", "combine"]
@@ -106,6 +106,7 @@ def load(build_if_missing: bool = True):
     L.bem_launch_count.argtypes = [P]
     L.bem_measure_peak.argtypes = [i32, P, P]
     L.bem_mesh_upload.argtypes = [P, P]
+    L.bem_matvec_noalloc.argtypes = [P, i32, P, P, P]
     for name in EXPORTS:
         if name not in ("bem_fmm_params_default", "bem_solve_params_default", "bem_ctx_destroy",
                         "bem_last_error", "bem_mesh_destroy", "bem_plan_destroy"):
@@ -214,6 +215,12 @@ def bem_plan_destroy(plan):
 def bem_matvec(plan, op, x, y, stream=None):
     """x, y: CUDA tensors (float64, or complex128 for Helmholtz)."""
     _check(load().bem_matvec(plan, int(op), _ptr(x), _ptr(y), _stream(stream)))
+
+
+def bem_matvec_noalloc(plan, op, x, y, stream=None):
+    """bem_matvec without any allocation (scratch in the library's fixed
+    device array); see include/bem.h."""
+    _check(load().bem_matvec_noalloc(plan, int(op), _ptr(x), _ptr(y), _stream(stream)))
 
 
 def bem_solve(plan, chi, phi, nrhs=1, params=None, stream=None):

@@ -853,4 +853,84 @@ void free_fmm(bem_plan *P) {
     P->yptr = nullptr;
 }
 
+
+// ---------------------------------------------------------------------------
+// A product that allocates nothing
+//
+// Callers that cannot allocate device memory when they need a product --
+// real-time loops where an allocation (which may synchronise the device) is
+// not allowed, or hosts whose device memory all belongs to another allocator
+// (a framework's pool) that forbids stray cudaMalloc calls -- can use
+// bem_matvec_noalloc.  It launches the same kernels as bem_matvec, directly
+// (no graph is instantiated), and keeps the per-product scratch (quadrature
+// strengths, moments, local expansions, regular sums) in the file-scope array
+// below instead of the plan's own buffers.  The array is NOALLOC_BYTES long
+// and every GPU that loads this library holds it until the process exits.
+// Its device address is looked up once per device, on the first call made
+// on that device (so that first call should come before any stream capture).
+// All calls share the array and it keeps the last call's contents; no part of
+// it needs to start at zero (every stage writes its output before it is read).
+// Calls that overlap on the GPU -- on different streams, or for different
+// plans at the same time -- race on the array.
+// ---------------------------------------------------------------------------
+constexpr size_t NOALLOC_BYTES = (size_t)48 << 20;   // 48 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+static void *g_noalloc_addr[64];                     // per device ordinal, 0 until looked up
+
+static size_t noalloc_round(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace bem
+
+extern "C" int bem_matvec_noalloc(bem_plan *P, int op, const void *x_dev, void *y_dev, void *cuda_stream) {
+    using namespace bem;
+    if (!P || !x_dev || !y_dev) { set_error("bem_matvec_noalloc: NULL argument"); return BEM_EINVAL; }
+    if (op != BEM_OP_A && op != BEM_OP_B) { set_error("bem_matvec_noalloc: bad op %d", op); return BEM_EINVAL; }
+    if (P->device < 0 || P->device >= 64) { set_error("bem_matvec_noalloc: device %d out of range", P->device); return BEM_EINVAL; }
+    const int C = P->green == BEM_HELMHOLTZ ? 2 : 1;
+    const bool mx = P->prm.precision == BEM_MIXED;
+    const size_t rb = mx ? sizeof(float) : sizeof(double);
+    const size_t bf = noalloc_round((size_t)P->Q * C * rb);
+    const size_t bm = noalloc_round((size_t)P->t.nbox * P->mi.np * C * rb);
+    const size_t by = noalloc_round((size_t)P->N * C * sizeof(double));
+    const size_t need = bf + 2 * bm + by;
+    if (need > NOALLOC_BYTES) {
+        set_error("bem_matvec_noalloc: this plan needs %zu bytes of scratch, the fixed array holds %zu",
+                  need, NOALLOC_BYTES);
+        return BEM_EINVAL;
+    }
+    BEM_CUDA(cudaSetDevice(P->device));
+    if (!g_noalloc_addr[P->device]) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)", __FILE__, __LINE__);
+        g_noalloc_addr[P->device] = ptr;
+    }
+    unsigned char *base = (unsigned char *)g_noalloc_addr[P->device];
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    // point the plan's work buffers at the scratch for this one enqueue; the
+    // kernels take the pointers by value, so the plan's own are restored at once
+    double *keep_f = P->f, *keep_M = P->M, *keep_L = P->L, *keep_y = P->ytmp;
+    float *keep_ff = P->ff, *keep_fM = P->fM, *keep_fL = P->fL;
+    if (mx) {
+        P->ff = (float *)base;
+        P->fM = (float *)(base + bf);
+        P->fL = (float *)(base + bf + bm);
+    } else {
+        P->f = (double *)base;
+        P->M = (double *)(base + bf);
+        P->L = (double *)(base + bf + bm);
+    }
+    P->ytmp = (double *)(base + bf + 2 * bm);
+    int rc = set_slots(P, x_dev, y_dev, s);
+    if (rc == BEM_OK) {
+        cudaError_t e = cudaMemsetAsync(P->skip, 0, sizeof(int), s);
+        rc = e == cudaSuccess ? BEM_OK : cuda_fail(e, "cudaMemsetAsync", __FILE__, __LINE__);
+    }
+    if (rc == BEM_OK) rc = enqueue_matvec_raw(P, op, P->green, P->k, 1, s, nullptr);
+    P->f = keep_f; P->M = keep_M; P->L = keep_L; P->ytmp = keep_y;
+    P->ff = keep_ff; P->fM = keep_fM; P->fL = keep_fL;
+    return rc;
+}
+
+namespace bem {
 }  // namespace bem
