@@ -195,7 +195,10 @@ int bem_matvec_noalloc(bem_plan *plan, int op, const void *x_dev, void *y_dev, v
  * [nrhs][n_chi]; phi_dev: device [nrhs][n_phi] (written).  info: host array
  * of nrhs entries (may be NULL).  Returns BEM_ENOCONV if any right-hand side
  * stopped at max_iter; its best iterate is written.  Synchronises the stream
- * once per restart cycle. */
+ * once per restart cycle.  A BEM_MIXED plan aims at max(tol, 5e-8), just
+ * above the float32 operator's residual floor, and also stops when a whole
+ * restart cycle fails to halve the true residual; info reports the residual
+ * reached. */
 int bem_solve(bem_plan *plan, const void *chi_dev, void *phi_dev, int nrhs,
               const bem_solve_params *params, bem_solve_info *info, void *cuda_stream);
 

@@ -111,6 +111,7 @@ static int plan_setup(bem_plan *P, cudaStream_t s) {
     BEM_TRY(build_geometry(P, s));
     BEM_TRY(build_radii_lists(P, s));
     BEM_TRY(build_correction(P, s));
+    BEM_TRY(build_m2l_classes(P));
     BEM_TRY(compute_diagonal(P, s));
     // near-field pair count (targets x regular sources), for the roofline
     const Tree &t = P->t;

@@ -179,6 +179,16 @@ struct bem_plan {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     long long graph_kernels[2] = {0, 0};
     cudaStream_t capture_stream = nullptr;
+    // translation tables (translate.cu)
+    int *sh_m2m_ptr = nullptr, *sh_m2m_src = nullptr, *sh_l2l_ptr = nullptr, *sh_l2l_src = nullptr;
+    double *sh_m2m_coef = nullptr, *sh_l2l_coef = nullptr;
+    unsigned char *sh_m2m_par = nullptr, *sh_l2l_par = nullptr;
+    int *ctr_ptr = nullptr, *ctr_ag = nullptr, *ctr_beta = nullptr, *m_deg = nullptr;
+    double *m_sgnf = nullptr, *m_invf = nullptr;
+    int *m2l_cls = nullptr, *cls_dl = nullptr, m2l_ncls = 0;
+    double *cls_rho = nullptr, *cls_kh = nullptr;
+    double *m2l_D = nullptr;            // [class][np] derivative tables (x2 complex)
+    float *m2l_fD = nullptr;
     // counters
     int64_t near_pairs = 0;
     int last_op = -1;
@@ -197,8 +207,14 @@ int build_tree(bem_plan *P, cudaStream_t s);
 int build_geometry(bem_plan *P, cudaStream_t s);
 int build_radii_lists(bem_plan *P, cudaStream_t s);
 int build_correction(bem_plan *P, cudaStream_t s);
-int alloc_fmm(bem_plan *P);
+int alloc_fmm(bem_plan *P, cudaStream_t s);
 void free_fmm(bem_plan *P);
+int build_m2l_classes(bem_plan *P);
+int build_translation_tables(bem_plan *P, cudaStream_t s);
+void free_translation_tables(bem_plan *P);
+void set_translation_attributes();
+template <class R, int C>
+int launch_translations(bem_plan *P, R *M, R *L, cudaStream_t s, cudaEvent_t *ev);
 int enqueue_matvec(bem_plan *P, int op, int green, double k, cudaStream_t s);
 int set_slots(bem_plan *P, const void *x, void *y, cudaStream_t s);
 int enqueue_matvec_raw(bem_plan *P, int op, int green, double k, int with_diag, cudaStream_t s,

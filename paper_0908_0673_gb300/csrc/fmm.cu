@@ -175,269 +175,6 @@ __global__ void __launch_bounds__(P2M_T) k_p2m(int nleaf, Tabs tb, TreeView tv, 
 }
 
 // ---------------------------------------------------------------------------
-// M2M (Eq. 8) for the parents of one level; child offset is +-h_child/2 per
-// axis, i.e. +-1/4 of the parent edge:
-//   Ms'_a = sum_{b<=a} C(a,b) s^b 2^-(|a|+|b|) Ms_{a-b}
-// ---------------------------------------------------------------------------
-constexpr int TR_T = 128, TR_SLOTS = (969 + TR_T - 1) / TR_T;
-
-template <class R, int C>
-__global__ void __launch_bounds__(TR_T) k_m2m(int off, int cnt, Tabs tb, TreeView tv, R *__restrict__ M,
-                                              const int *__restrict__ skip) {
-    if (skip && *skip) return;
-    extern __shared__ unsigned char smem_raw[];
-    const int b = off + blockIdx.x;
-    if (blockIdx.x >= cnt || tv.nchild[b] == 0) return;
-    const int p = tb.p, np = tb.np, tid = threadIdx.x, P1 = p + 1;
-    R *sM = (R *)smem_raw;                                   // [np][C]
-    int *sidx = (int *)(sM + np * C);                        // [(p+1)^3]
-    double *sbin = (double *)(((uintptr_t)(sidx + P1 * P1 * P1) + 15) & ~(uintptr_t)15);   // [(p+1)^2]
-    for (int t = tid; t < P1 * P1 * P1; t += TR_T) sidx[t] = tb.idx3[t];
-    for (int t = tid; t < P1 * P1; t += TR_T) sbin[t] = tb.binom[(t / P1) * (PMAX + 1) + t % P1];
-    R acc[TR_SLOTS][C];
-#pragma unroll
-    for (int s = 0; s < TR_SLOTS; s++)
-#pragma unroll
-        for (int c = 0; c < C; c++) acc[s][c] = (R)0;
-    for (int ch = tv.child0[b]; ch < tv.child0[b] + tv.nchild[b]; ch++) {
-        __syncthreads();
-        for (int t = tid; t < np * C; t += TR_T) sM[t] = M[(size_t)ch * np * C + t];
-        __syncthreads();
-        const int sx = (tv.ix[ch] & 1) ? 1 : -1, sy = (tv.iy[ch] & 1) ? 1 : -1, sz = (tv.iz[ch] & 1) ? 1 : -1;
-#pragma unroll
-        for (int s = 0; s < TR_SLOTS; s++) {
-            int a = tid + s * TR_T;
-            if (a >= np) break;
-            const int m = tb.m[a], n = tb.n[a], k = tb.k[a], da = m + n + k;
-            for (int q = 0; q <= m; q++) {
-                const double cq = sbin[m * P1 + q] * ((sx < 0 && (q & 1)) ? -1.0 : 1.0);
-                for (int r = 0; r <= n; r++) {
-                    const double cr = cq * sbin[n * P1 + r] * ((sy < 0 && (r & 1)) ? -1.0 : 1.0);
-                    for (int t = 0; t <= k; t++) {
-                        const double ct = cr * sbin[k * P1 + t] * ((sz < 0 && (t & 1)) ? -1.0 : 1.0);
-                        const R coef = (R)scalbn(ct, -(da + q + r + t));
-                        const int src = sidx[((m - q) * P1 + (n - r)) * P1 + (k - t)];
-#pragma unroll
-                        for (int c = 0; c < C; c++) acc[s][c] += coef * sM[src * C + c];
-                    }
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int s = 0; s < TR_SLOTS; s++) {
-        int a = tid + s * TR_T;
-        if (a < np)
-#pragma unroll
-            for (int c = 0; c < C; c++) M[((size_t)b * np + a) * C + c] = acc[s][c];
-    }
-}
-
-// ---------------------------------------------------------------------------
-// L2L (Eq. 9 with binomials) for the boxes of one level:
-//   Ls'_b += sum_{g: |b|+|g|<=p} C(b+g, b) s^g 2^-(2|g|+|b|) Ls_{b+g}
-// ---------------------------------------------------------------------------
-template <class R, int C>
-__global__ void __launch_bounds__(TR_T) k_l2l(int off, int cnt, Tabs tb, TreeView tv, R *__restrict__ L,
-                                              const int *__restrict__ skip) {
-    if (skip && *skip) return;
-    extern __shared__ unsigned char smem_raw[];
-    const int b = off + blockIdx.x;
-    if (blockIdx.x >= cnt) return;
-    const int par = tv.parent[b];
-    const int p = tb.p, np = tb.np, tid = threadIdx.x, P1 = p + 1;
-    R *sL = (R *)smem_raw;
-    int *sidx = (int *)(sL + np * C);
-    double *sbin = (double *)(((uintptr_t)(sidx + P1 * P1 * P1) + 15) & ~(uintptr_t)15);
-    for (int t = tid; t < P1 * P1 * P1; t += TR_T) sidx[t] = tb.idx3[t];
-    for (int t = tid; t < P1 * P1; t += TR_T) sbin[t] = tb.binom[(t / P1) * (PMAX + 1) + t % P1];
-    for (int t = tid; t < np * C; t += TR_T) sL[t] = L[(size_t)par * np * C + t];
-    __syncthreads();
-    const int sx = (tv.ix[b] & 1) ? 1 : -1, sy = (tv.iy[b] & 1) ? 1 : -1, sz = (tv.iz[b] & 1) ? 1 : -1;
-#pragma unroll
-    for (int s = 0; s < TR_SLOTS; s++) {
-        int a = tid + s * TR_T;
-        if (a >= np) break;
-        const int m = tb.m[a], n = tb.n[a], k = tb.k[a], db = m + n + k;
-        R acc[C];
-#pragma unroll
-        for (int c = 0; c < C; c++) acc[c] = (R)0;
-        for (int q = 0; q + m <= p; q++) {
-            const double cq = sbin[(m + q) * P1 + m] * ((sx < 0 && (q & 1)) ? -1.0 : 1.0);
-            for (int r = 0; q + r + m + n <= p; r++) {
-                const double cr = cq * sbin[(n + r) * P1 + n] * ((sy < 0 && (r & 1)) ? -1.0 : 1.0);
-                for (int t = 0; q + r + t + db <= p; t++) {
-                    const double ct = cr * sbin[(k + t) * P1 + k] * ((sz < 0 && (t & 1)) ? -1.0 : 1.0);
-                    const R coef = (R)scalbn(ct, -(2 * (q + r + t) + db));
-                    const int src = sidx[((m + q) * P1 + (n + r)) * P1 + (k + t)];
-#pragma unroll
-                    for (int c = 0; c < C; c++) acc[c] += coef * sL[src * C + c];
-                }
-            }
-        }
-#pragma unroll
-        for (int c = 0; c < C; c++) L[((size_t)b * np + a) * C + c] += acc[c];
-    }
-}
-
-// ---------------------------------------------------------------------------
-// M2L (Eq. 7), SIMT: one block per target box, every interaction-list source
-// in turn.  For a pair with r = c_t - c_s, rho = r / h_t and khat = k h_t:
-//   D[g]   = d^g Ghat(rho) by Tausch's recursions (Section 3.3),
-//   mh[a]  = (-1)^|a| (h_s/h_t)^|a| Ms_s[a] / a!,
-//   acc[b] += sum_a D[a+b] mh[a];  finally Ls_t[b] = acc[b] / (h_t b!).
-// ---------------------------------------------------------------------------
-template <class R, int C>
-struct M2LShared {
-    // layout offsets inside dynamic shared memory
-    static size_t bytes(int p, int np) {
-        int P1 = p + 1;
-        size_t s = 0;
-        s += sizeof(int) * P1 * P1 * P1;           // idx3
-        s += sizeof(int) * 3 * np;                 // m n k
-        s = (s + 15) & ~(size_t)15;
-        s += sizeof(R) * (size_t)(p + 2) * 2;      // G^(h), complex pairs
-        s += sizeof(R) * (size_t)np * C * 3;       // two Tausch buffers + mh
-        return s + 64;
-    }
-};
-
-template <class R, int C>
-__device__ __forceinline__ void cmul_acc(R *acc, const R *d, const R *m) {
-    if (C == 1) {
-        acc[0] += d[0] * m[0];
-    } else {
-        acc[0] += d[0] * m[0] - d[1] * m[1];
-        acc[1] += d[0] * m[1] + d[1] * m[0];
-    }
-}
-
-template <class R, int C>
-__global__ void __launch_bounds__(TR_T) k_m2l(int nbox, Tabs tb, TreeView tv, double kwave, const R *__restrict__ M,
-                                              R *__restrict__ L, const int *__restrict__ skip) {
-    if (skip && *skip) return;
-    extern __shared__ unsigned char smem_raw[];
-    const int t = blockIdx.x;
-    if (t >= nbox) return;
-    const int p = tb.p, np = tb.np, tid = threadIdx.x, P1 = p + 1;
-    int *sidx = (int *)smem_raw;
-    int *sm = sidx + P1 * P1 * P1, *sn = sm + np, *sk = sn + np;
-    R *Gh = (R *)(((uintptr_t)(sk + np) + 15) & ~(uintptr_t)15);  // [(p+2)][2]
-    R *bufA = Gh + (p + 2) * 2, *bufB = bufA + np * C, *mh = bufB + np * C;
-    for (int u = tid; u < P1 * P1 * P1; u += TR_T) sidx[u] = tb.idx3[u];
-    for (int u = tid; u < np; u += TR_T) { sm[u] = tb.m[u]; sn[u] = tb.n[u]; sk[u] = tb.k[u]; }
-    const double ht = scalbn(tv.side, -tv.level[t]);
-    R acc[TR_SLOTS][C];
-#pragma unroll
-    for (int s = 0; s < TR_SLOTS; s++)
-#pragma unroll
-        for (int c = 0; c < C; c++) acc[s][c] = (R)0;
-    const int i0 = tv.inter_ptr[t], i1 = tv.inter_ptr[t + 1];
-    for (int it = i0; it < i1; it++) {
-        const int src = tv.inter_idx[it];
-        const double rx = (tv.cx[t] - tv.cx[src]) / ht, ry = (tv.cy[t] - tv.cy[src]) / ht,
-                     rz = (tv.cz[t] - tv.cz[src]) / ht;
-        const R rho[3] = {(R)rx, (R)ry, (R)rz};
-        const int dlev = tv.level[t] - tv.level[src];                    // h_s / h_t = 2^dlev
-        __syncthreads();
-        if (tid == 0) {
-            // G^(h), h = 0..p (Tausch): Laplace G^(h+1) = -(2h+1) G^(h) / rho^2;
-            // Helmholtz adds -khat^2 G^(h-1) / rho^2 with G^(-1) = -j e^{j khat rho} / (4 pi khat).
-            double r2 = rx * rx + ry * ry + rz * rz, r1 = sqrt(r2);
-            const double inv4pi = 0.25 / M_PI;
-            if (C == 1) {
-                double g = inv4pi / r1;
-                for (int h = 0; h <= p; h++) {
-                    Gh[2 * h] = (R)g;
-                    Gh[2 * h + 1] = (R)0;
-                    g = -(2.0 * h + 1.0) * g / r2;
-                }
-            } else {
-                double kh = kwave * ht, sn_, cs_;
-                sincos(kh * r1, &sn_, &cs_);
-                double g0r = cs_ * inv4pi / r1, g0i = sn_ * inv4pi / r1;
-                double gmr = sn_ * inv4pi / kh, gmi = -cs_ * inv4pi / kh;   // -j e / (4 pi kh)
-                double pr = gmr, pi = gmi, cr = g0r, ci = g0i;
-                for (int h = 0; h <= p; h++) {
-                    Gh[2 * h] = (R)cr;
-                    Gh[2 * h + 1] = (R)ci;
-                    double nr = -((2.0 * h + 1.0) * cr + kh * kh * pr) / r2;
-                    double ni = -((2.0 * h + 1.0) * ci + kh * kh * pi) / r2;
-                    pr = cr; pi = ci; cr = nr; ci = ni;
-                }
-            }
-        }
-        // scaled, signed, factorial-divided source moments
-        for (int u = tid; u < np; u += TR_T) {
-            const int d = sm[u] + sn[u] + sk[u];
-            const double fa = tb.fact[sm[u]] * tb.fact[sn[u]] * tb.fact[sk[u]];
-            const double sc = ((d & 1) ? -1.0 : 1.0) * scalbn(1.0, dlev * d) / fa;
-#pragma unroll
-            for (int c = 0; c < C; c++) mh[u * C + c] = (R)sc * M[((size_t)src * np + u) * C + c];
-        }
-        __syncthreads();
-        // Tausch's three-step scheme: tables of d^g G^(h), |g| <= p - h, h = p .. 0
-        R *up = bufA, *cur = bufB;
-        if (tid == 0) {
-            up[0] = Gh[2 * p];
-            if (C == 2) up[1] = Gh[2 * p + 1];
-        }
-        __syncthreads();
-        for (int h = p - 1; h >= 0; h--) {
-            const int top = p - h;
-            const int cnt = (top + 1) * (top + 2) * (top + 3) / 6;   // entries of degree <= top
-            for (int u = tid; u < cnt; u += TR_T) {
-                const int m = sm[u], n = sn[u], k = sk[u];
-                R v[C];
-                if (m + n + k == 0) {
-#pragma unroll
-                    for (int c = 0; c < C; c++) v[c] = Gh[2 * h + c];
-                } else {
-                    int ax = m > 0 ? 0 : (n > 0 ? 1 : 2);
-                    int g = ax == 0 ? m : (ax == 1 ? n : k);
-                    int m1 = m - (ax == 0), n1 = n - (ax == 1), k1 = k - (ax == 2);
-                    int i1 = sidx[(m1 * P1 + n1) * P1 + k1];
-#pragma unroll
-                    for (int c = 0; c < C; c++) v[c] = rho[ax] * up[i1 * C + c];
-                    if (g > 1) {
-                        int m2 = m1 - (ax == 0), n2 = n1 - (ax == 1), k2 = k1 - (ax == 2);
-                        int i2 = sidx[(m2 * P1 + n2) * P1 + k2];
-#pragma unroll
-                        for (int c = 0; c < C; c++) v[c] += (R)(g - 1) * up[i2 * C + c];
-                    }
-                }
-#pragma unroll
-                for (int c = 0; c < C; c++) cur[u * C + c] = v[c];
-            }
-            __syncthreads();
-            R *sw = up; up = cur; cur = sw;
-        }
-        // contraction (the derivative table is in `up`)
-#pragma unroll
-        for (int s = 0; s < TR_SLOTS; s++) {
-            const int bb = tid + s * TR_T;
-            if (bb >= np) break;
-            const int bm = sm[bb], bn = sn[bb], bk = sk[bb], db = bm + bn + bk;
-            const int na = (p - db + 1) * (p - db + 2) * (p - db + 3) / 6;
-            for (int a = 0; a < na; a++) {
-                const int g = sidx[((sm[a] + bm) * P1 + (sn[a] + bn)) * P1 + (sk[a] + bk)];
-                cmul_acc<R, C>(acc[s], up + g * C, mh + a * C);
-            }
-        }
-    }
-#pragma unroll
-    for (int s = 0; s < TR_SLOTS; s++) {
-        const int bb = tid + s * TR_T;
-        if (bb < np) {
-            const double fb = tb.fact[tb.m[bb]] * tb.fact[tb.n[bb]] * tb.fact[tb.k[bb]];
-            const R sc = (R)(1.0 / (ht * fb));
-#pragma unroll
-            for (int c = 0; c < C; c++) L[((size_t)t * np + bb) * C + c] = acc[s][c] * sc;
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
 // near field (regular rule over the near-list boxes) fused with L2P
 // ---------------------------------------------------------------------------
 constexpr int NF_T = 256, NF_TGT = 64, NF_SL = NF_T / NF_TGT, NF_TILE = 256;
@@ -570,6 +307,166 @@ __global__ void __launch_bounds__(NF_T) k_near(int nleaf, Tabs tb, TreeView tv, 
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// near field + L2P, float32 form: 16 target groups x 16 source slices per
+// block, 4 targets per thread so that every source read from shared memory
+// serves 4 pairs.  The near-list sources are packed into full tiles across
+// box boundaries; each staged source is rebased to the target leaf's centre
+// (box offset in float64, rounded once), tile partial sums go to float64.
+// ---------------------------------------------------------------------------
+constexpr int NF2_T = 256, NF2_G = 16, NF2_S = 16, NF2_U = 4, NF2_TILE = 256, NF2_ENT = 256;
+
+template <int C, bool DL>
+__device__ __forceinline__ void pair_f32(float rx, float ry, float rz, const float4 &sa, const float4 &sb, float kw,
+                                         float *acc) {
+    const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+    const float inv = rsqrtf(r2);
+    if (C == 1) {
+        if (DL) {
+            const float dot = fmaf(rx, sb.x, fmaf(ry, sb.y, rz * sb.z));
+            acc[0] = fmaf(sa.w * dot, inv * inv * inv, acc[0]);
+        } else {
+            acc[0] = fmaf(sa.w, inv, acc[0]);
+        }
+    } else {
+        const float R1 = r2 * inv;
+        float sn, cs;
+        sincosf(kw * R1, &sn, &cs);
+        float gr, gi;
+        if (DL) {
+            const float kr = kw * R1, rn = fmaf(rx, sb.x, fmaf(ry, sb.y, rz * sb.z)) * inv * inv * inv;
+            gr = (cs + kr * sn) * rn;
+            gi = (sn - kr * cs) * rn;
+        } else {
+            gr = cs * inv;
+            gi = sn * inv;
+        }
+        acc[0] += gr * sa.w - gi * sb.w;
+        acc[C - 1] += gr * sb.w + gi * sa.w;
+    }
+}
+
+template <int C, bool DL>
+__global__ void __launch_bounds__(NF2_T) k_near_f32(int nleaf, Tabs tb, TreeView tv, QuadView qv, double kwave,
+                                                    const float *__restrict__ f, const float *__restrict__ L,
+                                                    double *__restrict__ ytmp, const int *__restrict__ skip) {
+    if (skip && *skip) return;
+    const int li = blockIdx.x;
+    if (li >= nleaf) return;
+    const int b = tv.leaves[li];
+    const int tid = threadIdx.x, tg = tid % NF2_G, sl = tid / NF2_G;
+    __shared__ float4 sa[NF2_TILE], sb[NF2_TILE];
+    __shared__ int pref[NF2_ENT + 1];
+    __shared__ double red[NF2_S][NF2_G * NF2_U][C];
+    const double cbx = tv.cx[b], cby = tv.cy[b], cbz = tv.cz[b];
+    const float kw = (float)kwave;
+    const int p = tb.p, np = tb.np;
+    for (int t0 = tv.nb[b]; t0 < tv.ne[b]; t0 += NF2_G * NF2_U) {
+        float tx[NF2_U], ty[NF2_U], tz[NF2_U];
+#pragma unroll
+        for (int u = 0; u < NF2_U; u++) {
+            const int k = t0 + tg + NF2_G * u;
+            const bool on = k < tv.ne[b];
+            tx[u] = on ? (float)(tv.tx[k] - cbx) : 0.f;
+            ty[u] = on ? (float)(tv.ty[k] - cby) : 0.f;
+            tz[u] = on ? (float)(tv.tz[k] - cbz) : 0.f;
+        }
+        double acc[NF2_U][C];
+#pragma unroll
+        for (int u = 0; u < NF2_U; u++)
+#pragma unroll
+            for (int c = 0; c < C; c++) acc[u][c] = 0.0;
+        for (int e0 = tv.near_ptr[b]; e0 < tv.near_ptr[b + 1]; e0 += NF2_ENT) {
+            const int ne_ = min(NF2_ENT, tv.near_ptr[b + 1] - e0);
+            __syncthreads();
+            if (tid == 0) {
+                int run = 0;
+                for (int i = 0; i < ne_; i++) {
+                    pref[i] = run;
+                    const int s = tv.near_idx[e0 + i];
+                    run += (tv.ee[s] - tv.eb[s]) * NQ;
+                }
+                pref[ne_] = run;
+            }
+            __syncthreads();
+            const int total = pref[ne_];
+            for (int base = 0; base < total; base += NF2_TILE) {
+                __syncthreads();
+                const int j = base + tid;
+                if (j < total) {
+                    int lo = 0, hi = ne_ - 1;          // entry holding j: pref[lo] <= j < pref[lo + 1]
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (pref[mid] <= j) lo = mid; else hi = mid - 1;
+                    }
+                    const int s = tv.near_idx[e0 + lo];
+                    const int o = tv.eb[s] * NQ + (j - pref[lo]);
+                    const float dx = (float)(tv.cx[s] - cbx), dy = (float)(tv.cy[s] - cby), dz = (float)(tv.cz[s] - cbz);
+                    sa[tid] = make_float4(dx + qv.fx[o], dy + qv.fy[o], dz + qv.fz[o], f[(size_t)o * C]);
+                    sb[tid] = make_float4(DL ? qv.fnx[o] : 0.f, DL ? qv.fny[o] : 0.f, DL ? qv.fnz[o] : 0.f,
+                                          C == 2 ? f[(size_t)o * C + C - 1] : 0.f);
+                }
+                __syncthreads();
+                const int nt = min(NF2_TILE, total - base);
+                float part[NF2_U][C];
+#pragma unroll
+                for (int u = 0; u < NF2_U; u++)
+#pragma unroll
+                    for (int c = 0; c < C; c++) part[u][c] = 0.f;
+                for (int q = sl; q < nt; q += NF2_S) {
+                    const float4 A = sa[q], Bv = sb[q];
+#pragma unroll
+                    for (int u = 0; u < NF2_U; u++) pair_f32<C, DL>(tx[u] - A.x, ty[u] - A.y, tz[u] - A.z, A, Bv, kw, part[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < NF2_U; u++)
+#pragma unroll
+                    for (int c = 0; c < C; c++) acc[u][c] += (double)part[u][c];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < NF2_U; u++)
+#pragma unroll
+            for (int c = 0; c < C; c++) red[sl][tg + NF2_G * u][c] = acc[u][c];
+        __syncthreads();
+        if (tid < NF2_G * NF2_U) {
+            const int k = t0 + tid;          // target slot tid = tg + 16 u
+            if (k < tv.ne[b]) {
+                double sum[C];
+#pragma unroll
+                for (int c = 0; c < C; c++) sum[c] = 0.0;
+                for (int q = 0; q < NF2_S; q++)
+#pragma unroll
+                    for (int c = 0; c < C; c++) sum[c] += red[q][tid][c];
+                // local expansion at the target
+                const double h = scalbn(tv.side, -tv.level[b]);
+                const float dx = (float)((tv.tx[k] - cbx) / h), dy = (float)((tv.ty[k] - cby) / h),
+                            dz = (float)((tv.tz[k] - cbz) / h);
+                float px[PMAX + 1], py[PMAX + 1], pz[PMAX + 1];
+                px[0] = py[0] = pz[0] = 1.f;
+                for (int e = 1; e <= p; e++) {
+                    px[e] = px[e - 1] * dx;
+                    py[e] = py[e - 1] * dy;
+                    pz[e] = pz[e - 1] * dz;
+                }
+                double loc[C];
+#pragma unroll
+                for (int c = 0; c < C; c++) loc[c] = 0.0;
+                for (int a = 0; a < np; a++) {
+                    const float mono = px[tb.m[a]] * py[tb.n[a]] * pz[tb.k[a]];
+#pragma unroll
+                    for (int c = 0; c < C; c++) loc[c] += (double)(mono * L[((size_t)b * np + a) * C + c]);
+                }
+                const int node = tv.node_perm[k];
+#pragma unroll
+                for (int c = 0; c < C; c++) ytmp[(size_t)node * C + c] = sum[c] * (0.25 / M_PI) + loc[c];
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // correction SpMV + diagonal: one warp per node row
 //   op A: y = C x - (ytmp + K_D x);  op B: y = -(ytmp + K_S x)
@@ -659,14 +556,7 @@ static QuadView quad_of(const bem_plan *P) {
     return QuadView{q.x, q.y, q.z, q.nx, q.ny, q.nz, q.w, q.fx, q.fy, q.fz, q.fnx, q.fny, q.fnz, q.fw};
 }
 
-static size_t tr_smem(int p, int np, size_t rbytes, int C) {
-    int P1 = p + 1;
-    size_t s = rbytes * np * C + sizeof(int) * P1 * P1 * P1;
-    s = (s + 15) & ~(size_t)15;
-    return s + sizeof(double) * P1 * P1 + 16;
-}
-
-int alloc_fmm(bem_plan *P) {
+int alloc_fmm(bem_plan *P, cudaStream_t s) {
     Arena &A = P->arena;
     MIndex &mi = P->mi;
     mi.init(P->prm.p);
@@ -716,20 +606,8 @@ int alloc_fmm(bem_plan *P) {
     BEM_TRY(A.alloc(&P->ytmp, (size_t)P->N * C));
     BEM_TRY(A.alloc(&P->xptr, 2));
     BEM_TRY(A.alloc(&P->yptr, 2));
-    // kernels with large dynamic shared memory
-    const size_t big = 200 * 1024;
-    cudaFuncSetAttribute(k_m2l<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big);
-    cudaFuncSetAttribute(k_m2l<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big);
-    cudaFuncSetAttribute(k_m2l<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big);
-    cudaFuncSetAttribute(k_m2l<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big);
-    cudaFuncSetAttribute(k_m2m<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big);
-    cudaFuncSetAttribute(k_m2m<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big);
-    cudaFuncSetAttribute(k_m2m<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big);
-    cudaFuncSetAttribute(k_m2m<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big);
-    cudaFuncSetAttribute(k_l2l<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big);
-    cudaFuncSetAttribute(k_l2l<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big);
-    cudaFuncSetAttribute(k_l2l<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big);
-    cudaFuncSetAttribute(k_l2l<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big);
+    set_translation_attributes();
+    BEM_TRY(build_translation_tables(P, s));
     BEM_LAUNCH_CHECK();
     return BEM_OK;
 }
@@ -753,24 +631,14 @@ static int run_fmm(bem_plan *P, int op, double kwave, R *f, R *M, R *L, cudaStre
     else (k_p2m<R, C, false><<<t.nleaf, P2M_T, 0, s>>>(t.nleaf, tb, tv, qv, f, M, sk), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
     if (ev) BEM_CUDA(cudaEventRecord(ev[2], s));
-    const size_t trs = tr_smem(p, np, sizeof(R), C);
-    for (int l = t.nlev - 2; l >= 0; l--) {
-        int off = t.lev_off[l], cnt = t.lev_off[l + 1] - off;
-        (k_m2m<R, C><<<cnt, TR_T, trs, s>>>(off, cnt, tb, tv, M, sk), ::bem::count_launch());
+    BEM_TRY((launch_translations<R, C>(P, M, L, s, ev)));
+    if constexpr (sizeof(R) == sizeof(float)) {
+        if (op == BEM_OP_A) (k_near_f32<C, true><<<t.nleaf, NF2_T, 0, s>>>(t.nleaf, tb, tv, qv, kwave, f, L, P->ytmp, sk), ::bem::count_launch());
+        else (k_near_f32<C, false><<<t.nleaf, NF2_T, 0, s>>>(t.nleaf, tb, tv, qv, kwave, f, L, P->ytmp, sk), ::bem::count_launch());
+    } else {
+        if (op == BEM_OP_A) (k_near<R, C, true><<<t.nleaf, NF_T, 0, s>>>(t.nleaf, tb, tv, qv, kwave, f, L, P->ytmp, sk), ::bem::count_launch());
+        else (k_near<R, C, false><<<t.nleaf, NF_T, 0, s>>>(t.nleaf, tb, tv, qv, kwave, f, L, P->ytmp, sk), ::bem::count_launch());
     }
-    BEM_LAUNCH_CHECK();
-    if (ev) BEM_CUDA(cudaEventRecord(ev[3], s));
-    (k_m2l<R, C><<<t.nbox, TR_T, M2LShared<R, C>::bytes(p, np), s>>>(t.nbox, tb, tv, kwave, M, L, sk), ::bem::count_launch());
-    BEM_LAUNCH_CHECK();
-    if (ev) BEM_CUDA(cudaEventRecord(ev[4], s));
-    for (int l = 1; l < t.nlev; l++) {
-        int off = t.lev_off[l], cnt = t.lev_off[l + 1] - off;
-        (k_l2l<R, C><<<cnt, TR_T, trs, s>>>(off, cnt, tb, tv, L, sk), ::bem::count_launch());
-    }
-    BEM_LAUNCH_CHECK();
-    if (ev) BEM_CUDA(cudaEventRecord(ev[5], s));
-    if (op == BEM_OP_A) (k_near<R, C, true><<<t.nleaf, NF_T, 0, s>>>(t.nleaf, tb, tv, qv, kwave, f, L, P->ytmp, sk), ::bem::count_launch());
-    else (k_near<R, C, false><<<t.nleaf, NF_T, 0, s>>>(t.nleaf, tb, tv, qv, kwave, f, L, P->ytmp, sk), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
     if (ev) BEM_CUDA(cudaEventRecord(ev[6], s));
     return BEM_OK;
@@ -818,15 +686,17 @@ int enqueue_matvec_raw(bem_plan *P, int op, int green, double kwave, int with_di
 // the buffers are sized for the plan's own order and precision.
 int compute_diagonal(bem_plan *P, cudaStream_t s) {
     const int N = (int)P->N;
-    const int p_keep = P->prm.p, prec_keep = P->prm.precision;
+    const int p_keep = P->prm.p, prec_keep = P->prm.precision, green_keep = P->green;
+    // the diagonal uses the Laplace kernel whatever the plan's Green's function:
+    // buffers and derivative tables are built for a real Laplace product
     P->prm.p = PMAX;
     P->prm.precision = BEM_F64;
-    BEM_TRY(alloc_fmm(P));
+    P->green = BEM_LAPLACE;
+    BEM_TRY(alloc_fmm(P, s));
     double *ones = nullptr;
     BEM_TRY(P->arena.alloc(&ones, N));
     (k_fill<<<(N + 255) / 256, 256, 0, s>>>(N, 1.0, ones), ::bem::count_launch());
     BEM_TRY(set_slots(P, ones, nullptr, s));
-    // a Helmholtz plan still evaluates the Laplace kernel here
     BEM_TRY(enqueue_matvec_raw(P, BEM_OP_A, BEM_LAPLACE, 0.0, 0, s, nullptr));
     (k_finish_diag<<<(N + 255) / 256, 256, 0, s>>>(N, P->ytmp, P->C), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
@@ -835,11 +705,13 @@ int compute_diagonal(bem_plan *P, cudaStream_t s) {
     free_fmm(P);
     P->prm.p = p_keep;
     P->prm.precision = prec_keep;
-    return alloc_fmm(P);
+    P->green = green_keep;
+    return alloc_fmm(P, s);
 }
 
 // releases what alloc_fmm allocated
 void free_fmm(bem_plan *P) {
+    free_translation_tables(P);
     Arena &A = P->arena;
     for (void *q : {(void *)P->d_m, (void *)P->d_n, (void *)P->d_k, (void *)P->d_idx3, (void *)P->d_fact,
                     (void *)P->d_binom, (void *)P->f, (void *)P->M, (void *)P->L, (void *)P->ff, (void *)P->fM,

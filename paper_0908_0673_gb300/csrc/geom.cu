@@ -287,144 +287,262 @@ __global__ void k_special_write(CorrArgs a, const int *__restrict__ off, int *pa
     find_special(a, i, pair_e + off[i]);
 }
 
-struct Acc {
-    double Sre[6], Sim[6], Dre[6], Dim[6], D0[6];
+// ---------------------------------------------------------------------------
+// Special-pair quadrature, one warp per (node, element) pair.
+//
+// Point arithmetic works in the element's local frame: with d_a = X_a - x_i,
+//   r = x_i - x(s,t) = -sum N_a d_a,  tangents = sum dN_a d_a,
+// so distances keep full relative precision however close the point is to
+// the collocation node (which lets the mixed-precision plan run it in
+// float32).  Subdivision decisions use absolute float64 coordinates in the
+// fixed operation order of the oracle, so each piece gets the same rule.
+// Lanes share the Duffy points of a self element; near-singular pieces are
+// refined level by level from a per-warp queue in shared memory.  The
+// regular 7-point rule is added with negative weights, so the warp produces
+// (special - regular) directly.
+// ---------------------------------------------------------------------------
+constexpr int SW_WARPS = 4, SW_CAP = 192;
+
+struct PieceF {
+    float a0, a1, b0, b1, c0, c1;   // parametric corners (dyadic, exact in float32)
+    int depth;
 };
 
-// One quadrature point with reference-space weight wref.
-// G = exp(jkR)/(4 pi R); dG/dn1 = exp(jkR)(1 - jkR) ((x - x1).n1)/(4 pi R^3).
-__device__ __forceinline__ void acc_point(const CorrArgs &a, const double X[18], const double xi[3], double s,
-                                          double t, double wref, Acc &A) {
-    double N[6], x[3], n[3], J;
-    shape_rn(a.npe, s, t, N);
-    map_rn(a.npe, N, X, x);
-    normal_jac(a.npe, s, t, X, n, J);
-    double r0 = xi[0] - x[0], r1 = xi[1] - x[1], r2 = xi[2] - x[2];
-    double R = sqrt(r0 * r0 + r1 * r1 + r2 * r2);
-    double rn = r0 * n[0] + r1 * n[1] + r2 * n[2];
-    double w = wref * J;
-    const double inv4pi = 0.25 / M_PI;
-    double G0 = inv4pi / R, dG0 = inv4pi * rn / (R * R * R);
-    double Gre = G0, Gim = 0.0, dre = dG0, dim = 0.0;
-    if (a.green == BEM_HELMHOLTZ) {
-        double sn, cs;
-        sincos(a.k * R, &sn, &cs);
-        Gre = cs * G0; Gim = sn * G0;
-        // (cs + j sn)(1 - j kR) = cs + kR sn + j (sn - kR cs)
-        double kr = a.k * R;
-        dre = (cs + kr * sn) * dG0;
-        dim = (sn - kr * cs) * dG0;
-    }
-    for (int v = 0; v < a.npe; v++) {
-        double wn = w * N[v];
-        A.Sre[v] += wn * Gre; A.Sim[v] += wn * Gim;
-        A.Dre[v] += wn * dre; A.Dim[v] += wn * dim;
-        A.D0[v] += wn * dG0;
+template <class R, int NPE>
+__device__ __forceinline__ void shape_all(R s, R t, R N[NPE], R Ns[NPE], R Nt[NPE]) {
+    const R L0 = (R)1 - s - t;
+    if (NPE == 3) {
+        N[0] = L0; N[1] = s; N[2] = t;
+        Ns[0] = -1; Ns[1] = 1; Ns[2] = 0;
+        Nt[0] = -1; Nt[1] = 0; Nt[2] = 1;
+    } else {
+        N[0] = L0 * (2 * L0 - 1); N[1] = s * (2 * s - 1); N[2] = t * (2 * t - 1);
+        N[3 % NPE] = 4 * L0 * s; N[4 % NPE] = 4 * s * t; N[5 % NPE] = 4 * t * L0;
+        Ns[0] = 1 - 4 * L0; Ns[1] = 4 * s - 1; Ns[2] = 0;
+        Ns[3 % NPE] = 4 * (L0 - s); Ns[4 % NPE] = 4 * t; Ns[5 % NPE] = -4 * t;
+        Nt[0] = 1 - 4 * L0; Nt[1] = 0; Nt[2] = 4 * t - 1;
+        Nt[3 % NPE] = -4 * s; Nt[4 % NPE] = 4 * s; Nt[5 % NPE] = 4 * (L0 - t);
     }
 }
 
-__device__ void integrate_duffy(const CorrArgs &a, const double X[18], const double xi[3], const double P[2],
-                                const double Q1[2], const double Q2[2], Acc &A) {
-    double det = fabs((Q1[0] - P[0]) * (Q2[1] - P[1]) - (Q1[1] - P[1]) * (Q2[0] - P[0]));
-    for (int iu = 0; iu < a.nd; iu++) {
-        double u = 0.5 * (1.0 + c_glx[iu]), wu = 0.5 * c_glw[iu];
-        for (int iv = 0; iv < a.nd; iv++) {
-            double v = 0.5 * (1.0 + c_glx[iv]), wv = 0.5 * c_glw[iv];
-            double s = P[0] + u * (Q1[0] - P[0]) + u * v * (Q2[0] - Q1[0]);
-            double t = P[1] + u * (Q1[1] - P[1]) + u * v * (Q2[1] - Q1[1]);
-            acc_point(a, X, xi, s, t, wu * wv * u * det, A);
+// acc[0..4][a]: Re S, Im S, Re D, Im D, D0 (Laplace double layer)
+template <class R, bool HELM, int NPE>
+__device__ __forceinline__ void acc_local(const R *d, R kk, R s, R t, R wref, R (&acc)[5][NPE]) {
+    R N[NPE], Ns[NPE], Nt[NPE];
+    shape_all<R, NPE>(s, t, N, Ns, Nt);
+    R rx = 0, ry = 0, rz = 0, ux = 0, uy = 0, uz = 0, vx = 0, vy = 0, vz = 0;
+#pragma unroll
+    for (int a = 0; a < NPE; a++) {
+        const R dx = d[3 * a], dy = d[3 * a + 1], dz = d[3 * a + 2];
+        rx -= N[a] * dx; ry -= N[a] * dy; rz -= N[a] * dz;
+        ux += Ns[a] * dx; uy += Ns[a] * dy; uz += Ns[a] * dz;
+        vx += Nt[a] * dx; vy += Nt[a] * dy; vz += Nt[a] * dz;
+    }
+    const R nx = uy * vz - uz * vy, ny = uz * vx - ux * vz, nz = ux * vy - uy * vx;   // |n| = J
+    const R J = sqrt(nx * nx + ny * ny + nz * nz);
+    const R r2 = rx * rx + ry * ry + rz * rz;
+    const R inv = (R)1 / sqrt(r2);
+    const R c4 = (R)(0.25 / M_PI) * wref;
+    const R wS = c4 * J * inv;                                   // w J G0
+    const R wD = c4 * (rx * nx + ry * ny + rz * nz) * inv * inv * inv;   // w J dG0/dn1
+    R sr = wS, si = 0, dr = wD, di = 0;
+    if (HELM) {
+        const R R1 = r2 * inv, kr = kk * R1;
+        R sn, cs;
+        sincos(kr, &sn, &cs);
+        sr = cs * wS; si = sn * wS;
+        dr = (cs + kr * sn) * wD;
+        di = (sn - kr * cs) * wD;
+    }
+#pragma unroll
+    for (int a = 0; a < NPE; a++) {
+        acc[0][a] += N[a] * sr;
+        acc[2][a] += N[a] * dr;
+        acc[4][a] += N[a] * wD;
+        if (HELM) {
+            acc[1][a] += N[a] * si;
+            acc[3][a] += N[a] * di;
         }
     }
 }
 
-__device__ void integrate_singular(const CorrArgs &a, const double X[18], const double xi[3], int as, Acc &A) {
-    const double c0[2] = {0.0, 0.0}, c1[2] = {1.0, 0.0}, c2[2] = {0.0, 1.0};
-    const double m3[2] = {0.5, 0.0}, m4[2] = {0.5, 0.5}, m5[2] = {0.0, 0.5};
-    switch (as) {
-    case 0: integrate_duffy(a, X, xi, c0, c1, c2, A); break;
-    case 1: integrate_duffy(a, X, xi, c1, c2, c0, A); break;
-    case 2: integrate_duffy(a, X, xi, c2, c0, c1, A); break;
-    case 3: integrate_duffy(a, X, xi, m3, c1, c2, A); integrate_duffy(a, X, xi, m3, c2, c0, A); break;
-    case 4: integrate_duffy(a, X, xi, m4, c2, c0, A); integrate_duffy(a, X, xi, m4, c0, c1, A); break;
-    default: integrate_duffy(a, X, xi, m5, c0, c1, A); integrate_duffy(a, X, xi, m5, c1, c2, A); break;
+// float64 subdivision decision in the oracle's operation order: true when
+// the piece must be split.
+template <int NPE>
+__device__ __forceinline__ bool must_split(const double *X, const double xi[3], double tau, int maxdepth,
+                                           const PieceF &P) {
+    if (P.depth >= maxdepth) return false;
+    double N[6], xa[3], xb[3], xc[3], xm[3];
+    const double a0 = P.a0, a1 = P.a1, b0 = P.b0, b1 = P.b1, c0 = P.c0, c1 = P.c1;
+    const double m0 = __ddiv_rn(__dadd_rn(__dadd_rn(a0, b0), c0), 3.0);
+    const double m1 = __ddiv_rn(__dadd_rn(__dadd_rn(a1, b1), c1), 3.0);
+    shape_rn(NPE, a0, a1, N); map_rn(NPE, N, X, xa);
+    shape_rn(NPE, b0, b1, N); map_rn(NPE, N, X, xb);
+    shape_rn(NPE, c0, c1, N); map_rn(NPE, N, X, xc);
+    shape_rn(NPE, m0, m1, N); map_rn(NPE, N, X, xm);
+    double h = dist3_rn(xa[0], xa[1], xa[2], xb[0], xb[1], xb[2]);
+    const double h2 = dist3_rn(xb[0], xb[1], xb[2], xc[0], xc[1], xc[2]);
+    const double h3 = dist3_rn(xc[0], xc[1], xc[2], xa[0], xa[1], xa[2]);
+    if (h2 > h) h = h2;
+    if (h3 > h) h = h3;
+    return dist3_rn(xi[0], xi[1], xi[2], xm[0], xm[1], xm[2]) < __dmul_rn(tau, h);
+}
+
+__device__ __forceinline__ void split4(const PieceF &P, PieceF out[4]) {
+    const float ab0 = 0.5f * (P.a0 + P.b0), ab1 = 0.5f * (P.a1 + P.b1);
+    const float bc0 = 0.5f * (P.b0 + P.c0), bc1 = 0.5f * (P.b1 + P.c1);
+    const float ca0 = 0.5f * (P.c0 + P.a0), ca1 = 0.5f * (P.c1 + P.a1);
+    const int d = P.depth + 1;
+    out[0] = {P.a0, P.a1, ab0, ab1, ca0, ca1, d};
+    out[1] = {ab0, ab1, P.b0, P.b1, bc0, bc1, d};
+    out[2] = {ca0, ca1, bc0, bc1, P.c0, P.c1, d};
+    out[3] = {ab0, ab1, bc0, bc1, ca0, ca1, d};
+}
+
+template <class R, bool HELM, int NPE>
+__device__ __forceinline__ void leaf7(const R *d, R kk, const PieceF &P, R (&acc)[5][NPE]) {
+    const double det = fabs(((double)P.b0 - P.a0) * ((double)P.c1 - P.a1) - ((double)P.b1 - P.a1) * ((double)P.c0 - P.a0));
+    for (int q = 0; q < NQ; q++) {
+        const double ps = P.a0 + c_rule.s[q] * ((double)P.b0 - P.a0) + c_rule.t[q] * ((double)P.c0 - P.a0);
+        const double pt = P.a1 + c_rule.s[q] * ((double)P.b1 - P.a1) + c_rule.t[q] * ((double)P.c1 - P.a1);
+        acc_local<R, HELM, NPE>(d, kk, (R)ps, (R)pt, (R)(c_rule.w[q] * det), acc);
     }
 }
 
-// Recursive 4-way split with an explicit stack (pieces processed depth first,
-// children in the order (a,ab,ca), (ab,b,bc), (ca,bc,c), (ab,bc,ca)).
-__device__ void integrate_subdivided(const CorrArgs &a, const double X[18], const double xi[3], Acc &A) {
-    struct Piece { double a0, a1, b0, b1, c0, c1; int depth; };
-    Piece st[4 * 8 + 4];
+// serial depth-first refinement of one piece (queue overflow path)
+template <class R, bool HELM, int NPE>
+__device__ void refine_serial(const double *X, const double xi[3], const R *d, R kk, double tau, int maxdepth,
+                              PieceF root, R (&acc)[5][NPE]) {
+    PieceF st[3 * 10 + 4];
     int sp = 0;
-    st[sp++] = {0.0, 0.0, 1.0, 0.0, 0.0, 1.0, 0};
+    st[sp++] = root;
     while (sp > 0) {
-        Piece P = st[--sp];
-        double N[6], xa[3], xb[3], xc[3], xm[3];
-        double m0 = __ddiv_rn(__dadd_rn(__dadd_rn(P.a0, P.b0), P.c0), 3.0);
-        double m1 = __ddiv_rn(__dadd_rn(__dadd_rn(P.a1, P.b1), P.c1), 3.0);
-        shape_rn(a.npe, P.a0, P.a1, N); map_rn(a.npe, N, X, xa);
-        shape_rn(a.npe, P.b0, P.b1, N); map_rn(a.npe, N, X, xb);
-        shape_rn(a.npe, P.c0, P.c1, N); map_rn(a.npe, N, X, xc);
-        shape_rn(a.npe, m0, m1, N); map_rn(a.npe, N, X, xm);
-        double h = dist3_rn(xa[0], xa[1], xa[2], xb[0], xb[1], xb[2]);
-        double h2 = dist3_rn(xb[0], xb[1], xb[2], xc[0], xc[1], xc[2]);
-        double h3 = dist3_rn(xc[0], xc[1], xc[2], xa[0], xa[1], xa[2]);
-        if (h2 > h) h = h2;
-        if (h3 > h) h = h3;
-        bool near = dist3_rn(xi[0], xi[1], xi[2], xm[0], xm[1], xm[2]) < __dmul_rn(a.tau, h);
-        if (P.depth >= a.maxdepth || !near) {
-            double det = fabs((P.b0 - P.a0) * (P.c1 - P.a1) - (P.b1 - P.a1) * (P.c0 - P.a0));
-            for (int q = 0; q < NQ; q++) {
-                double ps = P.a0 + c_rule.s[q] * (P.b0 - P.a0) + c_rule.t[q] * (P.c0 - P.a0);
-                double pt = P.a1 + c_rule.s[q] * (P.b1 - P.a1) + c_rule.t[q] * (P.c1 - P.a1);
-                acc_point(a, X, xi, ps, pt, c_rule.w[q] * det, A);
-            }
+        const PieceF P = st[--sp];
+        if (!must_split<NPE>(X, xi, tau, maxdepth, P)) {
+            leaf7<R, HELM, NPE>(d, kk, P, acc);
             continue;
         }
-        double ab0 = __dmul_rn(0.5, __dadd_rn(P.a0, P.b0)), ab1 = __dmul_rn(0.5, __dadd_rn(P.a1, P.b1));
-        double bc0 = __dmul_rn(0.5, __dadd_rn(P.b0, P.c0)), bc1 = __dmul_rn(0.5, __dadd_rn(P.b1, P.c1));
-        double ca0 = __dmul_rn(0.5, __dadd_rn(P.c0, P.a0)), ca1 = __dmul_rn(0.5, __dadd_rn(P.c1, P.a1));
-        int d = P.depth + 1;
-        // pushed in reverse so that they are processed in the listed order
-        st[sp++] = {ab0, ab1, bc0, bc1, ca0, ca1, d};
-        st[sp++] = {ca0, ca1, bc0, bc1, P.c0, P.c1, d};
-        st[sp++] = {ab0, ab1, P.b0, P.b1, bc0, bc1, d};
-        st[sp++] = {P.a0, P.a1, ab0, ab1, ca0, ca1, d};
+        PieceF ch[4];
+        split4(P, ch);
+        for (int c = 3; c >= 0; c--) st[sp++] = ch[c];
     }
 }
 
-// One special (node, element) pair per thread: values (special - regular)
-// for every local node, written in the pair's slot of the CSR arrays.
-__global__ void k_special_integrate(CorrArgs a, int npairs, const int *__restrict__ pair_node,
-                                    const int *__restrict__ pair_e, double *valD, double *valS, double *d0row) {
-    int pr = blockIdx.x * blockDim.x + threadIdx.x;
-    if (pr >= npairs) return;
-    int node = pair_node[pr], e = pair_e[pr];
-    double X[18], xi[3] = {a.nodes[3 * (size_t)node], a.nodes[3 * (size_t)node + 1], a.nodes[3 * (size_t)node + 2]};
-    load_elem(a.nodes, a.el_phi + (size_t)e * a.npe, a.npe, X);
+template <class R, bool HELM, int NPE>
+__global__ void __launch_bounds__(32 * SW_WARPS) k_special_warp(CorrArgs a, int npairs, const int *__restrict__ pair_node,
+                                                                const int *__restrict__ pair_e, double *valD,
+                                                                double *valS, double *d0pair) {
+    __shared__ PieceF q[SW_WARPS][2][SW_CAP];
+    __shared__ double sX[SW_WARPS][18];
+    __shared__ R sd[SW_WARPS][18];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int pr = blockIdx.x * SW_WARPS + warp;
+    if (pr >= npairs) return;                       // uniform within the warp
+    const int node = pair_node[pr], e = pair_e[pr];
+    const double xi[3] = {a.nodes[3 * (size_t)node], a.nodes[3 * (size_t)node + 1], a.nodes[3 * (size_t)node + 2]};
+    if (lane < 3 * NPE) {
+        const int v = lane / 3, c = lane % 3;
+        const double xv = a.nodes[3 * (size_t)a.el_phi[(size_t)e * NPE + v] + c];
+        sX[warp][lane] = xv;
+        sd[warp][lane] = (R)(xv - xi[c]);
+    }
+    __syncwarp();
+    const double *X = sX[warp];
+    const R *d = sd[warp];
+    const R kk = (R)a.k;
     int as = -1;
-    int cls = classify_pair(a, node, xi, e, &as);
-    Acc sp, rg;
-    for (int v = 0; v < 6; v++) {
-        sp.Sre[v] = sp.Sim[v] = sp.Dre[v] = sp.Dim[v] = sp.D0[v] = 0.0;
-        rg.Sre[v] = rg.Sim[v] = rg.Dre[v] = rg.Dim[v] = rg.D0[v] = 0.0;
-    }
-    if (cls == 1) integrate_singular(a, X, xi, as, sp);
-    else integrate_subdivided(a, X, xi, sp);
-    for (int q = 0; q < NQ; q++) acc_point(a, X, xi, c_rule.s[q], c_rule.t[q], c_rule.w[q], rg);
-    const int C = a.green == BEM_HELMHOLTZ ? 2 : 1;
-    double d0 = 0.0;
-    for (int v = 0; v < a.npe; v++) {
-        size_t o = ((size_t)pr * a.npe + v) * C;
-        valD[o] = sp.Dre[v] - rg.Dre[v];
-        valS[o] = sp.Sre[v] - rg.Sre[v];
-        if (C == 2) {
-            valD[o + 1] = sp.Dim[v] - rg.Dim[v];
-            valS[o + 1] = sp.Sim[v] - rg.Sim[v];
+    for (int v = 0; v < NPE; v++)
+        if (a.el_phi[(size_t)e * NPE + v] == node) as = v;
+    R acc[5][NPE];
+#pragma unroll
+    for (int j = 0; j < 5; j++)
+#pragma unroll
+        for (int v = 0; v < NPE; v++) acc[j][v] = 0;
+    // minus the regular 7-point rule
+    if (lane < NQ) acc_local<R, HELM, NPE>(d, kk, (R)c_rule.s[lane], (R)c_rule.t[lane], (R)(-c_rule.w[lane]), acc);
+    if (as >= 0) {
+        // self element: Duffy rule collapsed at the singular node, split at a mid-side node
+        const double c0[2] = {0.0, 0.0}, c1[2] = {1.0, 0.0}, c2[2] = {0.0, 1.0};
+        const double mm[3][2] = {{0.5, 0.0}, {0.5, 0.5}, {0.0, 0.5}};
+        const int nsub = as < 3 ? 1 : 2, nd = a.nd, per = nd * nd;
+        for (int j = lane; j < nsub * per; j += 32) {
+            const int sub = j / per, rem = j - sub * per, iu = rem / nd, iv = rem - iu * nd;
+            const double *P, *Q1, *Q2;
+            switch (as) {
+            case 0: P = c0; Q1 = c1; Q2 = c2; break;
+            case 1: P = c1; Q1 = c2; Q2 = c0; break;
+            case 2: P = c2; Q1 = c0; Q2 = c1; break;
+            case 3: P = mm[0]; Q1 = sub ? c2 : c1; Q2 = sub ? c0 : c2; break;
+            case 4: P = mm[1]; Q1 = sub ? c0 : c2; Q2 = sub ? c1 : c0; break;
+            default: P = mm[2]; Q1 = sub ? c1 : c0; Q2 = sub ? c2 : c1; break;
+            }
+            const double det = fabs((Q1[0] - P[0]) * (Q2[1] - P[1]) - (Q1[1] - P[1]) * (Q2[0] - P[0]));
+            const double u = 0.5 * (1.0 + c_glx[iu]), wu = 0.5 * c_glw[iu];
+            const double v = 0.5 * (1.0 + c_glx[iv]), wv = 0.5 * c_glw[iv];
+            const double s = P[0] + u * (Q1[0] - P[0]) + u * v * (Q2[0] - Q1[0]);
+            const double t = P[1] + u * (Q1[1] - P[1]) + u * v * (Q2[1] - Q1[1]);
+            acc_local<R, HELM, NPE>(d, kk, (R)s, (R)t, (R)(wu * wv * u * det), acc);
         }
-        d0 += sp.D0[v] - rg.D0[v];
+    } else {
+        // near-singular element: level-synchronous 4-way refinement
+        PieceF *cur = q[warp][0], *nxt = q[warp][1];
+        int ncur = 1;
+        if (lane == 0) cur[0] = {0.f, 0.f, 1.f, 0.f, 0.f, 1.f, 0};
+        __syncwarp();
+        while (ncur > 0) {
+            int nnext = 0;
+            for (int base = 0; base < ncur; base += 32) {
+                const int i = base + lane;
+                PieceF P = {};
+                bool split = false;
+                if (i < ncur) {
+                    P = cur[i];
+                    split = must_split<NPE>(X, xi, a.tau, a.maxdepth, P);
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, split);
+                const int pos = nnext + 4 * __popc(m & ((1u << lane) - 1u));
+                if (i < ncur) {
+                    if (!split) {
+                        leaf7<R, HELM, NPE>(d, kk, P, acc);
+                    } else if (pos + 4 <= SW_CAP) {
+                        PieceF ch[4];
+                        split4(P, ch);
+                        for (int c = 0; c < 4; c++) nxt[pos + c] = ch[c];
+                    } else {
+                        refine_serial<R, HELM, NPE>(X, xi, d, kk, a.tau, a.maxdepth, P, acc);
+                    }
+                }
+                nnext = min(SW_CAP, nnext + 4 * __popc(m));
+                nnext -= (nnext % 4);
+            }
+            __syncwarp();
+            PieceF *sw = cur; cur = nxt; nxt = sw;
+            ncur = nnext;
+        }
     }
-    d0row[pr] = d0;
+    // warp sums
+#pragma unroll
+    for (int j = 0; j < 5; j++) {
+        if (!HELM && (j == 1 || j == 3)) continue;
+#pragma unroll
+        for (int v = 0; v < NPE; v++)
+            for (int off = 16; off; off >>= 1) acc[j][v] += __shfl_xor_sync(0xffffffffu, acc[j][v], off);
+    }
+    if (lane == 0) {
+        const int C = HELM ? 2 : 1;
+        double d0 = 0.0;
+        for (int v = 0; v < NPE; v++) {
+            const size_t o = ((size_t)pr * NPE + v) * C;
+            valS[o] = (double)acc[0][v];
+            valD[o] = (double)acc[2][v];
+            if (HELM) {
+                valS[o + 1] = (double)acc[1][v];
+                valD[o + 1] = (double)acc[3][v];
+            }
+            d0 += (double)acc[4][v];
+        }
+        d0pair[pr] = d0;
+    }
 }
 
 __global__ void k_pair_nodes(int N, const int *__restrict__ off, int *pair_node) {
@@ -507,7 +625,21 @@ int build_correction(bem_plan *P, cudaStream_t s) {
     BEM_TRY(A.alloc(&d0row, N));
     (k_rows_ptr<<<(N + 256) / 256, 256, 0, s>>>(N, npe, off, K.ptrD), ::bem::count_launch());
     (k_corr_csr<<<(npairs + 255) / 256, 256, 0, s>>>(npairs, npe, pair_e, t.el_phi, t.el_chi, K.colD, K.colS), ::bem::count_launch());
-    (k_special_integrate<<<(npairs + 63) / 64, 64, 0, s>>>(a, npairs, pair_node, pair_e, K.valD, K.valS, d0pair), ::bem::count_launch());
+    {
+        const int blocks = (npairs + SW_WARPS - 1) / SW_WARPS;
+        const bool mx = P->prm.precision == BEM_MIXED, helm = P->green == BEM_HELMHOLTZ;
+#define BEM_SW(R, H, NP) (k_special_warp<R, H, NP><<<blocks, 32 * SW_WARPS, 0, s>>>(a, npairs, pair_node, pair_e, K.valD, K.valS, d0pair), ::bem::count_launch())
+        if (npairs > 0) {
+            if (npe == 3) {
+                if (mx) { if (helm) BEM_SW(float, true, 3); else BEM_SW(float, false, 3); }
+                else { if (helm) BEM_SW(double, true, 3); else BEM_SW(double, false, 3); }
+            } else {
+                if (mx) { if (helm) BEM_SW(float, true, 6); else BEM_SW(float, false, 6); }
+                else { if (helm) BEM_SW(double, true, 6); else BEM_SW(double, false, 6); }
+            }
+        }
+#undef BEM_SW
+    }
     (k_d0_rowsum<<<(N + 255) / 256, 256, 0, s>>>(N, off, d0pair, d0row), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
     BEM_TRY(A.alloc(&K.fvalD, K.nnzD * C));

@@ -6,6 +6,7 @@
 // the estimated residual reaches the tolerance, so a whole cycle is enqueued
 // (or replayed as one captured graph) and the host synchronises once per
 // cycle.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -138,6 +139,16 @@ __global__ void k_resid(int n, const double *__restrict__ b, double *r) {
     if (i < n) r[i] = b[i] - r[i];
 }
 
+constexpr double TAU_MIXED = 5e-8;
+
+__global__ void k_set_scalar(double *p, double v) { *p = v; }
+
+static int set_scalar(double *p, double v, cudaStream_t s) {
+    (k_set_scalar<<<1, 1, 0, s>>>(p, v), ::bem::count_launch());
+    BEM_LAUNCH_CHECK();
+    return BEM_OK;
+}
+
 struct GmState {
     // scalars: [0] ||b||, [1] beta, [2] |g_{j+1}| / ||b||, [3] tol, [4] ||w||
     double *sc;
@@ -257,16 +268,16 @@ static int gmres_one(bem_plan *P, const double *b, double *x, const bem_solve_pa
     // ||b||
     (k_nrm2_partial<C><<<GM_BLK, GM_T, 0, s>>>(n, b, partial, nullptr), ::bem::count_launch());
     (k_nrm2_final<<<1, 32, 0, s>>>(partial, S.sc + 0, nullptr), ::bem::count_launch());
-    double tol = sp->tol;
-    BEM_CUDA(cudaMemcpyAsync(S.sc + 3, &tol, sizeof(double), cudaMemcpyHostToDevice, s));
+    // With a float32 operator the true (float64) residual levels off near
+    // 2e-8; a mixed-precision solve therefore aims at max(tol, TAU_MIXED) and
+    // also stops once a whole restart cycle fails to halve the true residual.
+    const bool mixed = P->prm.precision == BEM_MIXED;
+    const double tol = mixed ? std::max(sp->tol, TAU_MIXED) : sp->tol;
+    BEM_TRY(set_scalar(S.sc + 3, tol, s));
     BEM_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * ne, s));
     int iters = 0, restarts = 0;
     double rel = 1.0, prev_rel = 2.0;
     int status = BEM_ENOCONV;
-    // With a float32 operator the true (float64) residual levels off near the
-    // operator's rounding error; a mixed-precision solve stops once a whole
-    // restart cycle fails to halve it, and reports the residual reached.
-    const bool mixed = P->prm.precision == BEM_MIXED;
     while (true) {
         // true residual r = b - A x into V_0 (unscaled), beta = ||r||
         BEM_CUDA(cudaMemsetAsync(skip, 0, sizeof(int), s));
@@ -280,7 +291,7 @@ static int gmres_one(bem_plan *P, const double *b, double *x, const bem_solve_pa
         BEM_CUDA(cudaStreamSynchronize(s));
         restarts++;
         rel = hs[0] > 0.0 ? hs[1] / hs[0] : 0.0;
-        if (rel <= sp->tol || hs[0] == 0.0) { status = BEM_OK; break; }
+        if (rel <= tol || hs[0] == 0.0) { status = BEM_OK; break; }
         if (mixed && restarts > 1 && rel > 0.5 * prev_rel) { status = BEM_OK; break; }
         prev_rel = rel;
         if (iters >= sp->max_iter) break;

@@ -1,7 +1,8 @@
 """GPU parity of the float64 path against the oracle, through the C ABI.
 
 * octree, radii and lists: bit-exact (Sections 3.1, 3.4, 3.6);
-* stored special-pair correction: same pairs, values within 1e-11;
+* stored special-pair correction: same pairs, values within 1e-11 (relative to
+  the largest entry) plus a 1e-12 absolute floor;
 * diagonal C_i = 1 + sum_j D0_ij (Eq. 2-3);
 * moments and locals per box against the oracle's four-step product;
 * the product y = A x, y = B x: relative L2 <= 1e-6 against the dense oracle;
@@ -69,7 +70,9 @@ def test_correction_matches_oracle(oracle_lib, plans, name):
         r = coo_sum(rr, cc, vv)
         g = coo_sum(got["row" + part], got["col" + part], got["val" + part])
         assert r.keys() == g.keys(), part
-        assert max(abs(g[k] - r[k]) for k in r) < 1e-11 * scale, part
+        # 1e-12 absolute floor: on flat elements the double-layer entries are
+        # rounding noise around zero whose value depends on summation order
+        assert max(abs(g[k] - r[k]) for k in r) < 1e-11 * scale + 1e-12, part
 
 
 @pytest.mark.parametrize("name", ["sphere642", "cube6_tri6", "sphere_tri6_l2"])
