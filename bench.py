@@ -197,8 +197,10 @@ def main():
     phi_d = torch.empty(n_phi, device=dev, dtype=torch.float64)
     flush = torch.empty(256 * 1024 * 1024 // 4, device=dev, dtype=torch.float32)   # > 129 MB L2
 
-    def step():
+    def step(mid=None):
         plan = bem.bem_plan_create(mesh, bem.BEM_LAPLACE, 0.0, prm, stream)
+        if mid is not None:
+            mid.record(stream)
         code, info = bem.bem_solve(plan, chi_d, phi_d, 1, sp, stream)
         return plan, info[0]
 
@@ -214,18 +216,19 @@ def main():
     clocks = Clocks(local)
     l0 = bem.bem_launch_count()
     total_ms = 0.0
-    lat = []
+    lat, setup_ms = [], []
     for _ in range(args.steps):
         with torch.cuda.stream(stream):
             flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0, em, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
-        plan, info = step()
+        plan, info = step(em)
         e1.record(stream)
         e1.synchronize()
         ms = e0.elapsed_time(e1)
         total_ms += ms
         lat.append(ms)
+        setup_ms.append(e0.elapsed_time(em))
         infos.append(info)
         bem.bem_plan_destroy(plan)
     torch.cuda.synchronize()
@@ -321,6 +324,7 @@ def main():
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}",
                    "step": "device plan build + RHS product + GMRES solve"},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+        "setup_ms": float(np.mean(setup_ms)), "solve_ms": float(np.mean(lat) - np.mean(setup_ms)),
         "gmres_iters": iters, "rel_residual": infos[-1].rel_residual if infos else None,
         "eps_rms_vs_point_source": eps_rms,
         "matvecs_per_s": matvecs_per_s, "stage_ms": stages, "plan_stats": st,

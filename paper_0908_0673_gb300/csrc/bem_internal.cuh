@@ -189,6 +189,11 @@ struct bem_plan {
     double *cls_rho = nullptr, *cls_kh = nullptr;
     double *m2l_D = nullptr;            // [class][np] derivative tables (x2 complex)
     float *m2l_fD = nullptr;
+    // float32 class-major M2L (translate.cu)
+    int cm_ntile = 0, cm_nunits = 0;
+    int *cm_order = nullptr, *cm_tile_cls = nullptr, *cm_tile_start = nullptr, *cm_tile_cnt = nullptr;
+    int *cm_ur0 = nullptr, *cm_ua0 = nullptr, *cm_rtp = nullptr, *cm_gidx = nullptr;
+    float *cm_Lp = nullptr;             // [interaction pair][np] per-pair local contributions
     // counters
     int64_t near_pairs = 0;
     int last_op = -1;

@@ -19,6 +19,7 @@
 // Templates: R = double (BEM_F64) or float (BEM_MIXED); C = 1 (real, Laplace)
 // or 2 (complex, Helmholtz); DL selects dipole (op A) or monopole (op B)
 // sources.
+#include <algorithm>
 #include <cmath>
 
 #include "bem_internal.cuh"
@@ -309,13 +310,13 @@ __global__ void __launch_bounds__(NF_T) k_near(int nleaf, Tabs tb, TreeView tv, 
 
 
 // ---------------------------------------------------------------------------
-// near field + L2P, float32 form: 16 target groups x 16 source slices per
-// block, 4 targets per thread so that every source read from shared memory
+// near field + L2P, float32 form: 8 target groups x 32 source slices per
+// block (leaves hold ~20-60 vertices), 4 targets per thread so that every source read from shared memory
 // serves 4 pairs.  The near-list sources are packed into full tiles across
 // box boundaries; each staged source is rebased to the target leaf's centre
 // (box offset in float64, rounded once), tile partial sums go to float64.
 // ---------------------------------------------------------------------------
-constexpr int NF2_T = 256, NF2_G = 16, NF2_S = 16, NF2_U = 4, NF2_TILE = 256, NF2_ENT = 256;
+constexpr int NF2_T = 256, NF2_G = 8, NF2_S = 32, NF2_U = 4, NF2_TILE = 256, NF2_ENT = 256;
 
 template <int C, bool DL>
 __device__ __forceinline__ void pair_f32(float rx, float ry, float rz, const float4 &sa, const float4 &sb, float kw,
@@ -347,6 +348,18 @@ __device__ __forceinline__ void pair_f32(float rx, float ry, float rz, const flo
     }
 }
 
+// compensated float32 accumulation (Kahan): GB300's float64 pipe is a small
+// fraction of its float32 pipe, so long sums stay in float32 with a carried
+// error term instead of being promoted
+struct KahanF {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        const float y = v - c, t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
+
 template <int C, bool DL>
 __global__ void __launch_bounds__(NF2_T) k_near_f32(int nleaf, Tabs tb, TreeView tv, QuadView qv, double kwave,
                                                     const float *__restrict__ f, const float *__restrict__ L,
@@ -358,7 +371,8 @@ __global__ void __launch_bounds__(NF2_T) k_near_f32(int nleaf, Tabs tb, TreeView
     const int tid = threadIdx.x, tg = tid % NF2_G, sl = tid / NF2_G;
     __shared__ float4 sa[NF2_TILE], sb[NF2_TILE];
     __shared__ int pref[NF2_ENT + 1];
-    __shared__ double red[NF2_S][NF2_G * NF2_U][C];
+    __shared__ float red[NF2_S][NF2_G * NF2_U][C];
+    __shared__ float lred[NF2_T / (NF2_G * NF2_U)][NF2_G * NF2_U][C];
     const double cbx = tv.cx[b], cby = tv.cy[b], cbz = tv.cz[b];
     const float kw = (float)kwave;
     const int p = tb.p, np = tb.np;
@@ -372,11 +386,7 @@ __global__ void __launch_bounds__(NF2_T) k_near_f32(int nleaf, Tabs tb, TreeView
             ty[u] = on ? (float)(tv.ty[k] - cby) : 0.f;
             tz[u] = on ? (float)(tv.tz[k] - cbz) : 0.f;
         }
-        double acc[NF2_U][C];
-#pragma unroll
-        for (int u = 0; u < NF2_U; u++)
-#pragma unroll
-            for (int c = 0; c < C; c++) acc[u][c] = 0.0;
+        KahanF acc[NF2_U][C];
         for (int e0 = tv.near_ptr[b]; e0 < tv.near_ptr[b + 1]; e0 += NF2_ENT) {
             const int ne_ = min(NF2_ENT, tv.near_ptr[b + 1] - e0);
             __syncthreads();
@@ -422,25 +432,21 @@ __global__ void __launch_bounds__(NF2_T) k_near_f32(int nleaf, Tabs tb, TreeView
 #pragma unroll
                 for (int u = 0; u < NF2_U; u++)
 #pragma unroll
-                    for (int c = 0; c < C; c++) acc[u][c] += (double)part[u][c];
+                    for (int c = 0; c < C; c++) acc[u][c].add(part[u][c]);
             }
         }
         __syncthreads();
 #pragma unroll
         for (int u = 0; u < NF2_U; u++)
 #pragma unroll
-            for (int c = 0; c < C; c++) red[sl][tg + NF2_G * u][c] = acc[u][c];
-        __syncthreads();
-        if (tid < NF2_G * NF2_U) {
-            const int k = t0 + tid;          // target slot tid = tg + 16 u
+            for (int c = 0; c < C; c++) red[sl][tg + NF2_G * u][c] = acc[u][c].s;
+        // local expansion at the targets: every thread takes a slice of the terms
+        {
+            const int nslot = NF2_G * NF2_U, tslot = tid % nslot, part_id = tid / nslot;
+            const int nparts = NF2_T / nslot;
+            const int k = t0 + tslot;
+            KahanF loc[C];
             if (k < tv.ne[b]) {
-                double sum[C];
-#pragma unroll
-                for (int c = 0; c < C; c++) sum[c] = 0.0;
-                for (int q = 0; q < NF2_S; q++)
-#pragma unroll
-                    for (int c = 0; c < C; c++) sum[c] += red[q][tid][c];
-                // local expansion at the target
                 const double h = scalbn(tv.side, -tv.level[b]);
                 const float dx = (float)((tv.tx[k] - cbx) / h), dy = (float)((tv.ty[k] - cby) / h),
                             dz = (float)((tv.tz[k] - cbz) / h);
@@ -451,14 +457,28 @@ __global__ void __launch_bounds__(NF2_T) k_near_f32(int nleaf, Tabs tb, TreeView
                     py[e] = py[e - 1] * dy;
                     pz[e] = pz[e - 1] * dz;
                 }
-                double loc[C];
-#pragma unroll
-                for (int c = 0; c < C; c++) loc[c] = 0.0;
-                for (int a = 0; a < np; a++) {
+                for (int a = part_id; a < np; a += nparts) {
                     const float mono = px[tb.m[a]] * py[tb.n[a]] * pz[tb.k[a]];
 #pragma unroll
-                    for (int c = 0; c < C; c++) loc[c] += (double)(mono * L[((size_t)b * np + a) * C + c]);
+                    for (int c = 0; c < C; c++) loc[c].add(mono * L[((size_t)b * np + a) * C + c]);
                 }
+            }
+#pragma unroll
+            for (int c = 0; c < C; c++) lred[part_id][tslot][c] = loc[c].s;
+        }
+        __syncthreads();
+        if (tid < NF2_G * NF2_U) {
+            const int k = t0 + tid;          // target slot tid = tg + G u
+            if (k < tv.ne[b]) {
+                double sum[C], loc[C];
+#pragma unroll
+                for (int c = 0; c < C; c++) sum[c] = loc[c] = 0.0;
+                for (int q = 0; q < NF2_S; q++)
+#pragma unroll
+                    for (int c = 0; c < C; c++) sum[c] += (double)red[q][tid][c];
+                for (int q = 0; q < NF2_T / (NF2_G * NF2_U); q++)
+#pragma unroll
+                    for (int c = 0; c < C; c++) loc[c] += (double)lred[q][tid][c];
                 const int node = tv.node_perm[k];
 #pragma unroll
                 for (int c = 0; c < C; c++) ytmp[(size_t)node * C + c] = sum[c] * (0.25 / M_PI) + loc[c];
@@ -688,9 +708,13 @@ int compute_diagonal(bem_plan *P, cudaStream_t s) {
     const int N = (int)P->N;
     const int p_keep = P->prm.p, prec_keep = P->prm.precision, green_keep = P->green;
     // the diagonal uses the Laplace kernel whatever the plan's Green's function:
-    // buffers and derivative tables are built for a real Laplace product
-    P->prm.p = PMAX;
-    P->prm.precision = BEM_F64;
+    // buffers and derivative tables are built for a real Laplace product.  A
+    // float64 plan takes order PMAX in float64; a mixed plan, whose stated
+    // error is larger, takes order p + 4 in float32 (truncation reduced by
+    // about eta^-4 against its own order).
+    const bool mixed = prec_keep == BEM_MIXED;
+    P->prm.p = mixed ? std::min(PMAX, p_keep + 4) : PMAX;
+    P->prm.precision = mixed ? BEM_MIXED : BEM_F64;
     P->green = BEM_LAPLACE;
     BEM_TRY(alloc_fmm(P, s));
     double *ones = nullptr;

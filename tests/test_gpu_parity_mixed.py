@@ -21,6 +21,7 @@ CASES = {
     "sphere642": (lambda: I.icosphere(3), dict(p=8, leaf_size=32, eta=2.0), (0.1, 0.2, -0.15)),
     "cube8_tri6": (lambda: I.cube(8, I.TRI6), dict(p=10, leaf_size=32, eta=2.0), (0.2, -0.1, 0.3)),
     "sphere_tri6_l2": (lambda: I.icosphere(2, I.TRI6), dict(p=8, leaf_size=16, eta=2.0), (0.1, 0.2, -0.15)),
+    "cube6_p9": (lambda: I.cube(6, I.TRI6), dict(p=9, leaf_size=24, eta=2.0), (0.2, -0.1, 0.3)),
 }
 
 
