@@ -262,6 +262,7 @@ def main():
     e1.synchronize()
     matvecs_per_s = nmv / (e0.elapsed_time(e1) / 1000.0)
     stages = bem.bem_plan_stage_times(plan, bem.BEM_OP_A, x_d, y_d, reps=10, stream=stream)
+    setup_stages = bem.bem_plan_setup_times(plan)
     setup_plan_ms = None
     bem.bem_plan_destroy(plan)
 
@@ -327,7 +328,7 @@ def main():
         "setup_ms": float(np.mean(setup_ms)), "solve_ms": float(np.mean(lat) - np.mean(setup_ms)),
         "gmres_iters": iters, "rel_residual": infos[-1].rel_residual if infos else None,
         "eps_rms_vs_point_source": eps_rms,
-        "matvecs_per_s": matvecs_per_s, "stage_ms": stages, "plan_stats": st,
+        "matvecs_per_s": matvecs_per_s, "stage_ms": stages, "setup_stage_ms": setup_stages, "plan_stats": st,
         "roofline": roof, "clocks": clk, "gpu_launches": int(launches),
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
     }

@@ -242,6 +242,14 @@ int bem_plan_stats(const bem_plan *plan, int64_t *stats);
 int bem_plan_stage_times(bem_plan *plan, int op, const void *x_dev, void *y_dev, int reps, double *ms,
                          void *cuda_stream);
 
+/* Stages of bem_plan_create, for bem_plan_setup_times. */
+#define BEM_NSETUP 7   /* mesh upload, octree, geometry + radii + lists, special-pair correction,
+                          offset classes, diagonal + translation tables, stats */
+
+/* Wall-clock milliseconds of every set-up stage of the plan (host array of
+ * BEM_NSETUP), measured with the stream synchronised at each stage boundary. */
+int bem_plan_setup_times(const bem_plan *plan, double *ms);
+
 /* Kernel launches issued by this library in this process so far (a graph
  * launch counts the kernels it holds). */
 int bem_launch_count(long long *count);

@@ -28,8 +28,10 @@ EXPORTS = [
     "bem_plan_create", "bem_plan_destroy", "bem_matvec", "bem_solve", "bem_plan_tree_sizes",
     "bem_plan_export_tree", "bem_plan_export_correction", "bem_plan_export_expansions",
     "bem_plan_diagonal", "bem_plan_footprint", "bem_plan_stats", "bem_plan_stage_times",
-    "bem_launch_count", "bem_measure_peak", "bem_mesh_upload", "bem_matvec_noalloc",
+    "bem_launch_count", "bem_measure_peak", "bem_mesh_upload", "bem_matvec_noalloc", "bem_plan_setup_times",
 ]
+BEM_NSETUP = 7
+SETUP_NAMES = ["upload", "tree", "geometry_radii_lists", "correction", "m2l_classes", "diagonal_tables", "stats"]
 BEM_NSTAGES = 7
 STAGE_NAMES = ["p2q", "p2m", "m2m", "m2l", "l2l", "near_l2p", "combine"]
 
@@ -107,6 +109,7 @@ def load(build_if_missing: bool = True):
     L.bem_measure_peak.argtypes = [i32, P, P]
     L.bem_mesh_upload.argtypes = [P, P]
     L.bem_matvec_noalloc.argtypes = [P, i32, P, P, P]
+    L.bem_plan_setup_times.argtypes = [P, P]
     for name in EXPORTS:
         if name not in ("bem_fmm_params_default", "bem_solve_params_default", "bem_ctx_destroy",
                         "bem_last_error", "bem_mesh_destroy", "bem_plan_destroy"):
@@ -300,6 +303,12 @@ def bem_plan_stage_times(plan, op, x, y, reps=5, stream=None) -> dict:
     ms = np.zeros(BEM_NSTAGES)
     _check(load().bem_plan_stage_times(plan, int(op), _ptr(x), _ptr(y), int(reps), _ptr(ms), _stream(stream)))
     return dict(zip(STAGE_NAMES, ms.tolist()))
+
+
+def bem_plan_setup_times(plan) -> dict:
+    ms = np.zeros(BEM_NSETUP)
+    _check(load().bem_plan_setup_times(plan, _ptr(ms)))
+    return dict(zip(SETUP_NAMES, ms.tolist()))
 
 
 def bem_launch_count() -> int:

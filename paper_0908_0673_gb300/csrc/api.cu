@@ -2,6 +2,7 @@
 // multiplication as one captured CUDA graph per operator, the GMRES solve and
 // the exports used for parity checks.
 #include <atomic>
+#include <chrono>
 #include <cstdarg>
 #include <cstring>
 #include <new>
@@ -107,12 +108,27 @@ static int plan_setup(bem_plan *P, cudaStream_t s) {
     BEM_TRY(A.alloc(&P->istate, 4));
     BEM_CUDA(cudaMemsetAsync(P->istate, 0, sizeof(int) * 4, s));
     P->skip = P->istate;
+    // stage timers (wall clock, stream synchronised at every boundary)
+    auto t0 = std::chrono::steady_clock::now();
+    auto lap = [&](int i) -> int {
+        BEM_CUDA(cudaStreamSynchronize(s));
+        const auto t1 = std::chrono::steady_clock::now();
+        P->setup_ms[i] = std::chrono::duration<double, std::milli>(t1 - t0).count();
+        t0 = t1;
+        return BEM_OK;
+    };
+    BEM_TRY(lap(0));
     BEM_TRY(build_tree(P, s));
+    BEM_TRY(lap(1));
     BEM_TRY(build_geometry(P, s));
     BEM_TRY(build_radii_lists(P, s));
+    BEM_TRY(lap(2));
     BEM_TRY(build_correction(P, s));
+    BEM_TRY(lap(3));
     BEM_TRY(build_m2l_classes(P));
+    BEM_TRY(lap(4));
     BEM_TRY(compute_diagonal(P, s));
+    BEM_TRY(lap(5));
     // near-field pair count (targets x regular sources), for the roofline
     const Tree &t = P->t;
     std::vector<int> nptr(t.nbox + 1), nidx(t.n_near), nb(t.nbox), ne(t.nbox), eb(t.nbox), ee(t.nbox), lv(t.nleaf);
@@ -130,6 +146,7 @@ static int plan_setup(bem_plan *P, cudaStream_t s) {
         pairs += src * (ne[b] - nb[b]);
     }
     P->near_pairs = pairs;
+    BEM_TRY(lap(6));
     return BEM_OK;
 }
 
@@ -382,6 +399,12 @@ int bem_plan_diagonal(const bem_plan *P, double *c) {
 int bem_plan_footprint(const bem_plan *P, size_t *hbm_bytes) {
     if (!P || !hbm_bytes) { set_error("bem_plan_footprint: NULL argument"); return BEM_EINVAL; }
     *hbm_bytes = P->arena.bytes;
+    return BEM_OK;
+}
+
+int bem_plan_setup_times(const bem_plan *P, double *ms) {
+    if (!P || !ms) { set_error("bem_plan_setup_times: NULL argument"); return BEM_EINVAL; }
+    for (int i = 0; i < BEM_NSETUP; i++) ms[i] = P->setup_ms[i];
     return BEM_OK;
 }
 

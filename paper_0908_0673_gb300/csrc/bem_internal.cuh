@@ -195,6 +195,7 @@ struct bem_plan {
     int *cm_ur0 = nullptr, *cm_ua0 = nullptr, *cm_rtp = nullptr, *cm_gidx = nullptr;
     float *cm_Lp = nullptr;             // [interaction pair][np] per-pair local contributions
     // counters
+    double setup_ms[BEM_NSETUP] = {};
     int64_t near_pairs = 0;
     int last_op = -1;
     // GMRES workspace

@@ -388,6 +388,41 @@ __device__ __forceinline__ bool must_split(const double *X, const double xi[3], 
     return dist3_rn(xi[0], xi[1], xi[2], xm[0], xm[1], xm[2]) < __dmul_rn(tau, h);
 }
 
+// float32 estimate of the same decision in the element's local frame (node
+// offsets from the collocation point, df[3a..3a+2]).  Its relative error is
+// ~1e-6, so when |d - tau h| exceeds 1e-4 tau h the answer equals the float64
+// one; otherwise the exact float64 test decides.
+template <int NPE>
+__device__ __forceinline__ bool must_split_fast(const float *df, const double *X, const double xi[3], double tau,
+                                                int maxdepth, const PieceF &P) {
+    if (P.depth >= maxdepth) return false;
+    const float cs[4][2] = {{P.a0, P.a1}, {P.b0, P.b1}, {P.c0, P.c1},
+                            {(P.a0 + P.b0 + P.c0) * (1.f / 3.f), (P.a1 + P.b1 + P.c1) * (1.f / 3.f)}};
+    float x[4][3];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        float N[NPE], Ns[NPE], Nt[NPE];
+        shape_all<float, NPE>(cs[q][0], cs[q][1], N, Ns, Nt);
+        float v0 = 0.f, v1 = 0.f, v2 = 0.f;
+#pragma unroll
+        for (int a = 0; a < NPE; a++) {
+            v0 = fmaf(N[a], df[3 * a], v0);
+            v1 = fmaf(N[a], df[3 * a + 1], v1);
+            v2 = fmaf(N[a], df[3 * a + 2], v2);
+        }
+        x[q][0] = v0; x[q][1] = v1; x[q][2] = v2;
+    }
+    auto dst = [&](int i, int j) {
+        const float e0 = x[i][0] - x[j][0], e1 = x[i][1] - x[j][1], e2 = x[i][2] - x[j][2];
+        return sqrtf(e0 * e0 + e1 * e1 + e2 * e2);
+    };
+    const float h = fmaxf(dst(0, 1), fmaxf(dst(1, 2), dst(2, 0)));
+    const float d = sqrtf(x[3][0] * x[3][0] + x[3][1] * x[3][1] + x[3][2] * x[3][2]);   // |x(m) - x_i|
+    const float th = (float)tau * h, q = d - th;
+    if (fabsf(q) > 1e-4f * th) return q < 0.f;
+    return must_split<NPE>(X, xi, tau, maxdepth, P);
+}
+
 __device__ __forceinline__ void split4(const PieceF &P, PieceF out[4]) {
     const float ab0 = 0.5f * (P.a0 + P.b0), ab1 = 0.5f * (P.a1 + P.b1);
     const float bc0 = 0.5f * (P.b0 + P.c0), bc1 = 0.5f * (P.b1 + P.c1);
@@ -411,14 +446,14 @@ __device__ __forceinline__ void leaf7(const R *d, R kk, const PieceF &P, R (&acc
 
 // serial depth-first refinement of one piece (queue overflow path)
 template <class R, bool HELM, int NPE>
-__device__ void refine_serial(const double *X, const double xi[3], const R *d, R kk, double tau, int maxdepth,
-                              PieceF root, R (&acc)[5][NPE]) {
+__device__ void refine_serial(const double *X, const double xi[3], const R *d, const float *df, R kk, double tau,
+                              int maxdepth, PieceF root, R (&acc)[5][NPE]) {
     PieceF st[3 * 10 + 4];
     int sp = 0;
     st[sp++] = root;
     while (sp > 0) {
         const PieceF P = st[--sp];
-        if (!must_split<NPE>(X, xi, tau, maxdepth, P)) {
+        if (!must_split_fast<NPE>(df, X, xi, tau, maxdepth, P)) {
             leaf7<R, HELM, NPE>(d, kk, P, acc);
             continue;
         }
@@ -435,6 +470,7 @@ __global__ void __launch_bounds__(32 * SW_WARPS) k_special_warp(CorrArgs a, int 
     __shared__ PieceF q[SW_WARPS][2][SW_CAP];
     __shared__ double sX[SW_WARPS][18];
     __shared__ R sd[SW_WARPS][18];
+    __shared__ float sdf[SW_WARPS][18];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int pr = blockIdx.x * SW_WARPS + warp;
     if (pr >= npairs) return;                       // uniform within the warp
@@ -445,10 +481,12 @@ __global__ void __launch_bounds__(32 * SW_WARPS) k_special_warp(CorrArgs a, int 
         const double xv = a.nodes[3 * (size_t)a.el_phi[(size_t)e * NPE + v] + c];
         sX[warp][lane] = xv;
         sd[warp][lane] = (R)(xv - xi[c]);
+        sdf[warp][lane] = (float)(xv - xi[c]);
     }
     __syncwarp();
     const double *X = sX[warp];
     const R *d = sd[warp];
+    const float *df = sdf[warp];
     const R kk = (R)a.k;
     int as = -1;
     for (int v = 0; v < NPE; v++)
@@ -497,7 +535,7 @@ __global__ void __launch_bounds__(32 * SW_WARPS) k_special_warp(CorrArgs a, int 
                 bool split = false;
                 if (i < ncur) {
                     P = cur[i];
-                    split = must_split<NPE>(X, xi, a.tau, a.maxdepth, P);
+                    split = must_split_fast<NPE>(df, X, xi, a.tau, a.maxdepth, P);
                 }
                 const unsigned m = __ballot_sync(0xffffffffu, split);
                 const int pos = nnext + 4 * __popc(m & ((1u << lane) - 1u));
@@ -509,7 +547,7 @@ __global__ void __launch_bounds__(32 * SW_WARPS) k_special_warp(CorrArgs a, int 
                         split4(P, ch);
                         for (int c = 0; c < 4; c++) nxt[pos + c] = ch[c];
                     } else {
-                        refine_serial<R, HELM, NPE>(X, xi, d, kk, a.tau, a.maxdepth, P, acc);
+                        refine_serial<R, HELM, NPE>(X, xi, d, df, kk, a.tau, a.maxdepth, P, acc);
                     }
                 }
                 nnext = min(SW_CAP, nnext + 4 * __popc(m));

@@ -21,6 +21,7 @@
 #include <type_traits>
 #include <map>
 #include <tuple>
+#include <unordered_map>
 #include <vector>
 
 #include "bem_internal.cuh"
@@ -413,7 +414,21 @@ int build_m2l_classes(bem_plan *P) {
     BEM_CUDA(cudaMemcpy(ip.data(), t.inter_ptr, sizeof(int) * (t.nbox + 1), cudaMemcpyDeviceToHost));
     if (t.n_inter) BEM_CUDA(cudaMemcpy(ii.data(), t.inter_idx, sizeof(int) * t.n_inter, cudaMemcpyDeviceToHost));
     const bool helm = P->green == BEM_HELMHOLTZ;
-    std::map<std::tuple<int, int, long long, long long, long long>, int> id;
+    struct Key {
+        long long v[5];
+        bool operator==(const Key &o) const {
+            return v[0] == o.v[0] && v[1] == o.v[1] && v[2] == o.v[2] && v[3] == o.v[3] && v[4] == o.v[4];
+        }
+    };
+    struct KeyHash {
+        size_t operator()(const Key &k) const {
+            unsigned long long h = 1469598103934665603ull;
+            for (long long x : k.v) h = (h ^ (unsigned long long)x) * 1099511628211ull;
+            return (size_t)(h ^ (h >> 29));
+        }
+    };
+    std::unordered_map<Key, int, KeyHash> id;
+    id.reserve(1 << 16);
     std::vector<int> pair_cls(std::max<int64_t>(1, t.n_inter));
     std::vector<double> rho, kh;
     std::vector<int> dls;
@@ -425,7 +440,7 @@ int build_m2l_classes(bem_plan *P) {
                 return (long long)(2 * it_ + 1) * (1ll << e) - (long long)(2 * is_ + 1) * (1ll << (dl + e));
             };
             const long long kx = K(ix[b], ix[s]), ky = K(iy[b], iy[s]), kz = K(iz[b], iz[s]);
-            auto key = std::make_tuple(dl, helm ? lev[b] : 0, kx, ky, kz);
+            const Key key{{(long long)dl, (long long)(helm ? lev[b] : 0), kx, ky, kz}};
             auto it = id.find(key);
             int c;
             if (it == id.end()) {
