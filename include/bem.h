@@ -202,6 +202,41 @@ int bem_matvec_noalloc(bem_plan *plan, int op, const void *x_dev, void *y_dev, v
 int bem_solve(bem_plan *plan, const void *chi_dev, void *phi_dev, int nrhs,
               const bem_solve_params *params, bem_solve_info *info, void *cuda_stream);
 
+/* Concurrent solves for request serving.  The paper solves one problem at a
+ * time; a server keeps many plans resident and advances their solves together
+ * so that the device work of small problems overlaps.  A batch owns
+ * max_slots CUDA streams; each submitted solve (b = B chi, then the GMRES of
+ * bem_solve) runs on its slot's stream as a sequence of device steps, and the
+ * host only reads back a few scalars asynchronously.  Submissions may arrive
+ * at any time while other solves are in flight (continuous batching).
+ *   bem_batch_submit   starts a solve in a free slot; BEM_EBUSY if no slot is
+ *                      free or the plan already has a solve in this batch (a
+ *                      plan holds the work space of one solve).  chi_dev and
+ *                      phi_dev must stay alive until the slot is released;
+ *                      chi_dev must already hold its data (the slot streams
+ *                      do not wait on other streams), and the plan takes no
+ *                      other product or solve until the slot is released.
+ *   bem_batch_progress non-blocking: advances every solve whose pending device
+ *                      work has finished; *n_active = solves still running.
+ *   bem_batch_poll     *done = 1 when the slot's solve ended (all its device
+ *                      work, phi_dev included, is then complete); info as
+ *                      bem_solve.
+ *   bem_batch_wait     blocks until the slot ends or timeout_s passes
+ *                      (BEM_ETIMEOUT; the solve keeps running).
+ *   bem_batch_release  frees a finished slot (BEM_EBUSY while running).
+ *   bem_batch_stream   the slot's stream (cudaStream_t), e.g. to build the
+ *                      next request's plan without waiting for others. */
+typedef struct bem_batch bem_batch;
+int bem_batch_create(bem_ctx *ctx, int max_slots, bem_batch **out);
+void bem_batch_destroy(bem_batch *batch);
+int bem_batch_submit(bem_batch *batch, bem_plan *plan, const void *chi_dev, void *phi_dev,
+                     const bem_solve_params *params, int *slot);
+int bem_batch_progress(bem_batch *batch, int *n_active);
+int bem_batch_poll(bem_batch *batch, int slot, int *done, bem_solve_info *info);
+int bem_batch_wait(bem_batch *batch, int slot, double timeout_s);
+int bem_batch_release(bem_batch *batch, int slot);
+void *bem_batch_stream(bem_batch *batch, int slot);
+
 /* Tree export (see bem_tree_view).  Blocks. */
 int bem_plan_tree_sizes(const bem_plan *plan, bem_tree_view *view);
 int bem_plan_export_tree(const bem_plan *plan, bem_tree_view *view);

@@ -29,6 +29,8 @@ EXPORTS = [
     "bem_plan_export_tree", "bem_plan_export_correction", "bem_plan_export_expansions",
     "bem_plan_diagonal", "bem_plan_footprint", "bem_plan_stats", "bem_plan_stage_times",
     "bem_launch_count", "bem_measure_peak", "bem_mesh_upload", "bem_matvec_noalloc", "bem_plan_setup_times",
+    "bem_batch_create", "bem_batch_destroy", "bem_batch_submit", "bem_batch_progress", "bem_batch_poll",
+    "bem_batch_wait", "bem_batch_release", "bem_batch_stream",
 ]
 BEM_NSETUP = 7
 SETUP_NAMES = ["upload", "tree", "geometry_radii_lists", "correction", "m2l_classes", "diagonal_tables", "stats"]
@@ -110,9 +112,20 @@ def load(build_if_missing: bool = True):
     L.bem_mesh_upload.argtypes = [P, P]
     L.bem_matvec_noalloc.argtypes = [P, i32, P, P, P]
     L.bem_plan_setup_times.argtypes = [P, P]
+    L.bem_batch_create.argtypes = [P, i32, P]
+    L.bem_batch_destroy.argtypes = [P]
+    L.bem_batch_destroy.restype = None
+    L.bem_batch_submit.argtypes = [P, P, P, P, P, P]
+    L.bem_batch_progress.argtypes = [P, P]
+    L.bem_batch_poll.argtypes = [P, i32, P, P]
+    L.bem_batch_wait.argtypes = [P, i32, dbl]
+    L.bem_batch_release.argtypes = [P, i32]
+    L.bem_batch_stream.argtypes = [P, i32]
+    L.bem_batch_stream.restype = P
     for name in EXPORTS:
         if name not in ("bem_fmm_params_default", "bem_solve_params_default", "bem_ctx_destroy",
-                        "bem_last_error", "bem_mesh_destroy", "bem_plan_destroy"):
+                        "bem_last_error", "bem_mesh_destroy", "bem_plan_destroy", "bem_batch_destroy",
+                        "bem_batch_stream"):
             getattr(L, name).restype = i32
     _lib = L
     return L
@@ -233,6 +246,47 @@ def bem_solve(plan, chi, phi, nrhs=1, params=None, stream=None):
                             C.byref(params) if params is not None else None, infos, _stream(stream))
     _check(code, allow=(BEM_ENOCONV,))
     return code, list(infos)
+
+
+def bem_batch_create(ctx, max_slots):
+    h = C.c_void_p()
+    _check(load().bem_batch_create(ctx, int(max_slots), C.byref(h)))
+    return h
+
+
+def bem_batch_destroy(batch):
+    load().bem_batch_destroy(batch)
+
+
+def bem_batch_submit(batch, plan, chi, phi, params=None) -> int:
+    slot = C.c_int()
+    _check(load().bem_batch_submit(batch, plan, _ptr(chi), _ptr(phi),
+                                   C.byref(params) if params is not None else None, C.byref(slot)))
+    return slot.value
+
+
+def bem_batch_progress(batch) -> int:
+    n = C.c_int()
+    _check(load().bem_batch_progress(batch, C.byref(n)), allow=(BEM_ENOCONV,))
+    return n.value
+
+
+def bem_batch_poll(batch, slot):
+    done, info = C.c_int(), bem_solve_info()
+    _check(load().bem_batch_poll(batch, int(slot), C.byref(done), C.byref(info)))
+    return bool(done.value), info
+
+
+def bem_batch_wait(batch, slot, timeout_s=600.0):
+    _check(load().bem_batch_wait(batch, int(slot), float(timeout_s)))
+
+
+def bem_batch_release(batch, slot):
+    _check(load().bem_batch_release(batch, int(slot)))
+
+
+def bem_batch_stream(batch, slot) -> int:
+    return load().bem_batch_stream(batch, int(slot)) or 0
 
 
 def bem_plan_tree_sizes(plan) -> bem_tree_view:

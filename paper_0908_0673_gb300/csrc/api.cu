@@ -163,6 +163,7 @@ bem_plan::~bem_plan() {
     for (auto &g : graph)
         if (g) cudaGraphExecDestroy(g);
     if (cycle_graph) cudaGraphExecDestroy(cycle_graph);
+    if (hostbuf) cudaFreeHost(hostbuf);
     if (capture_stream) cudaStreamDestroy(capture_stream);
 }
 

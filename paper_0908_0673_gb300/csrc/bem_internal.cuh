@@ -201,6 +201,7 @@ struct bem_plan {
     // GMRES workspace
     double *V = nullptr, *H = nullptr, *gs = nullptr, *w = nullptr, *xk = nullptr, *bvec = nullptr;
     double *scal = nullptr;             // device scalars
+    double *hostbuf = nullptr;          // pinned read-back of GMRES scalars
     int *istate = nullptr;              // device ints: [0] converged flag, [1] steps in cycle
     int gm_restart = 0;
     cudaGraphExec_t cycle_graph = nullptr;

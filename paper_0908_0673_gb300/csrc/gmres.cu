@@ -8,6 +8,9 @@
 // cycle.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
+#include <chrono>
+#include <new>
 #include <vector>
 
 #include "bem_internal.cuh"
@@ -255,88 +258,29 @@ __global__ void k_cycle_init(GmState S, int m) {
     S.g[0] = S.sc[1];   // beta
 }
 
-template <int C>
-static int gmres_one(bem_plan *P, const double *b, double *x, const bem_solve_params *sp, bem_solve_info *info,
-                     cudaStream_t s) {
-    const int n = (int)P->N, m = P->gm_restart, ne = n * C;
-    const size_t ld = (size_t)ne;
-    double *V = P->V, *w = P->w, *partial = P->scal + 16;
-    double *g0 = P->gs;
-    GmState S{P->scal, P->istate, P->H, g0, g0 + m, g0 + 3 * m, g0 + 5 * m + 2, g0 + 7 * m + 2, g0 + 9 * m + 4};
-    const int eb = (ne + 255) / 256, nb = (n + 255) / 256;
-    int *skip = P->istate;
-    // ||b||
-    (k_nrm2_partial<C><<<GM_BLK, GM_T, 0, s>>>(n, b, partial, nullptr), ::bem::count_launch());
-    (k_nrm2_final<<<1, 32, 0, s>>>(partial, S.sc + 0, nullptr), ::bem::count_launch());
-    // With a float32 operator the true (float64) residual levels off near
-    // 2e-8; a mixed-precision solve therefore aims at max(tol, TAU_MIXED) and
-    // also stops once a whole restart cycle fails to halve the true residual.
-    const bool mixed = P->prm.precision == BEM_MIXED;
-    const double tol = mixed ? std::max(sp->tol, TAU_MIXED) : sp->tol;
-    BEM_TRY(set_scalar(S.sc + 3, tol, s));
-    BEM_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * ne, s));
-    int iters = 0, restarts = 0;
-    double rel = 1.0, prev_rel = 2.0;
-    int status = BEM_ENOCONV;
-    while (true) {
-        // true residual r = b - A x into V_0 (unscaled), beta = ||r||
-        BEM_CUDA(cudaMemsetAsync(skip, 0, sizeof(int), s));
-        BEM_TRY(set_slots(P, x, V, s));
-        BEM_TRY(enqueue_matvec(P, BEM_OP_A, P->green, P->k, s));
-        (k_resid<<<eb, 256, 0, s>>>(ne, b, V), ::bem::count_launch());
-        (k_nrm2_partial<C><<<GM_BLK, GM_T, 0, s>>>(n, V, partial, nullptr), ::bem::count_launch());
-        (k_nrm2_final<<<1, 32, 0, s>>>(partial, S.sc + 1, nullptr), ::bem::count_launch());
-        double hs[2];
-        BEM_CUDA(cudaMemcpyAsync(hs, S.sc, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
-        BEM_CUDA(cudaStreamSynchronize(s));
-        restarts++;
-        rel = hs[0] > 0.0 ? hs[1] / hs[0] : 0.0;
-        if (rel <= tol || hs[0] == 0.0) { status = BEM_OK; break; }
-        if (mixed && restarts > 1 && rel > 0.5 * prev_rel) { status = BEM_OK; break; }
-        prev_rel = rel;
-        if (iters >= sp->max_iter) break;
-        (k_scale<<<eb, 256, 0, s>>>(ne, V, S.sc + 1, V, nullptr), ::bem::count_launch());
-        (k_cycle_init<<<1, 1, 0, s>>>(S, m), ::bem::count_launch());
-        const int steps = std::min(m, sp->max_iter - iters);
-        for (int j = 0; j < steps; j++) {
-            BEM_TRY(set_slots(P, V + (size_t)j * ld, w, s));
-            BEM_TRY(enqueue_matvec(P, BEM_OP_A, P->green, P->k, s));
-            // CGS2: two classical Gram-Schmidt passes against V_0..V_j
-            (k_mdot<C><<<GM_BLK, GM_T, 0, s>>>(n, j + 1, V, ld, w, partial, skip), ::bem::count_launch());
-            (k_mdot_final<C><<<(j + 1 + 7) / 8, 256, 0, s>>>(j + 1, partial, S.hcol, 0, skip), ::bem::count_launch());
-            (k_orth_update<C><<<nb, 256, 0, s>>>(n, j + 1, V, ld, S.hcol, w, skip), ::bem::count_launch());
-            (k_mdot<C><<<GM_BLK, GM_T, 0, s>>>(n, j + 1, V, ld, w, partial, skip), ::bem::count_launch());
-            (k_mdot_final<C><<<(j + 1 + 7) / 8, 256, 0, s>>>(j + 1, partial, S.hcol2, 0, skip), ::bem::count_launch());
-            (k_orth_update<C><<<nb, 256, 0, s>>>(n, j + 1, V, ld, S.hcol2, w, skip), ::bem::count_launch());
-            BEM_LAUNCH_CHECK();
-            (k_nrm2_partial<C><<<GM_BLK, GM_T, 0, s>>>(n, w, partial, skip), ::bem::count_launch());
-            (k_nrm2_final<<<1, 32, 0, s>>>(partial, S.sc + 4, skip), ::bem::count_launch());
-            (k_givens<C><<<1, 1, 0, s>>>(S, m, j), ::bem::count_launch());
-            (k_scale<<<eb, 256, 0, s>>>(ne, w, S.sc + 4, V + (size_t)(j + 1) * ld, skip), ::bem::count_launch());
-            BEM_LAUNCH_CHECK();
-        }
-        (k_backsolve<C><<<1, 1, 0, s>>>(S, m), ::bem::count_launch());
-        (k_xupdate<C><<<nb, 256, 0, s>>>(n, V, ld, S, x), ::bem::count_launch());
-        BEM_LAUNCH_CHECK();
-        int hst[2];
-        BEM_CUDA(cudaMemcpyAsync(hst, S.st, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
-        BEM_CUDA(cudaStreamSynchronize(s));
-        iters += hst[1];
-        if (hst[1] == 0) break;
-    }
-    if (info) {
-        info->iters = iters;
-        info->restarts = restarts;
-        info->rel_residual = rel;
-        info->status = status;
-    }
-    return status;
-}
+// ---------------------------------------------------------------------------
+// The solve as a state machine.  Every transition enqueues device work on the
+// solve's own stream plus an asynchronous read-back (pinned memory) of the
+// few scalars the host decides on -- ||b||, ||r||, the steps of a cycle -- and
+// records an event.  bem_solve drives one solve to the end, waiting on each
+// event; the batch API advances many solves of different plans together,
+// querying events without blocking, so their device work overlaps.
+// ---------------------------------------------------------------------------
+struct GmSolver {
+    bem_plan *P = nullptr;
+    const double *chi = nullptr;   // Neumann data (chi index space), device
+    double *x = nullptr;           // solution, device
+    bem_solve_params sp{};
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev = nullptr;
+    int phase = 0;                 // 0 start, 1 residual in flight, 2 cycle in flight, 3 done
+    bool waiting = false;
+    int iters = 0, restarts = 0, status = BEM_ENOCONV;
+    double rel = 1.0, prev_rel = 2.0, tol = 0.0;
+};
 
-int solve(bem_plan *P, const void *chi, void *phi, int nrhs, const bem_solve_params *sp, bem_solve_info *info,
-          cudaStream_t s) {
+static int gm_workspace(bem_plan *P, int m) {
     const int C = P->green == BEM_HELMHOLTZ ? 2 : 1;
-    const int m = sp->restart;
     if (m < 1 || m > 200) { set_error("bem_solve: restart %d outside [1, 200]", m); return BEM_EINVAL; }
     const size_t ne = (size_t)P->N * C;
     if (P->gm_restart != m) {
@@ -351,19 +295,309 @@ int solve(bem_plan *P, const void *chi, void *phi, int nrhs, const bem_solve_par
         BEM_TRY(P->arena.alloc(&P->bvec, ne));
         BEM_TRY(P->arena.alloc(&P->scal, 16 + (size_t)GM_BLK * 2 * (200 + 2)));
     }
+    if (!P->hostbuf) BEM_CUDA(cudaHostAlloc((void **)&P->hostbuf, 64, cudaHostAllocDefault));
+    return BEM_OK;
+}
+
+template <int C>
+static GmState gm_state(bem_plan *P) {
+    const int m = P->gm_restart;
+    double *g0 = P->gs;
+    return GmState{P->scal, P->istate, P->H, g0, g0 + m, g0 + 3 * m, g0 + 5 * m + 2, g0 + 7 * m + 2, g0 + 9 * m + 4};
+}
+
+// true residual r = b - A x into V_0 (unscaled), beta = ||r||, read back
+template <int C>
+static int gm_enqueue_residual(GmSolver &g) {
+    bem_plan *P = g.P;
+    const int n = (int)P->N, ne = n * C, eb = (ne + 255) / 256;
+    double *V = P->V, *partial = P->scal + 16;
+    GmState S = gm_state<C>(P);
+    cudaStream_t s = g.s;
+    BEM_CUDA(cudaMemsetAsync(P->istate, 0, sizeof(int), s));
+    BEM_TRY(set_slots(P, g.x, V, s));
+    BEM_TRY(enqueue_matvec(P, BEM_OP_A, P->green, P->k, s));
+    (k_resid<<<eb, 256, 0, s>>>(ne, P->bvec, V), ::bem::count_launch());
+    (k_nrm2_partial<C><<<GM_BLK, GM_T, 0, s>>>(n, V, partial, nullptr), ::bem::count_launch());
+    (k_nrm2_final<<<1, 32, 0, s>>>(partial, S.sc + 1, nullptr), ::bem::count_launch());
+    BEM_CUDA(cudaMemcpyAsync(P->hostbuf, S.sc, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+    BEM_CUDA(cudaEventRecord(g.ev, s));
+    g.waiting = true;
+    g.phase = 1;
+    return BEM_OK;
+}
+
+// b = B chi, ||b||, tolerance, x = 0, then the first residual
+template <int C>
+static int gm_enqueue_start(GmSolver &g) {
+    bem_plan *P = g.P;
+    const int n = (int)P->N, ne = n * C;
+    double *partial = P->scal + 16;
+    GmState S = gm_state<C>(P);
+    cudaStream_t s = g.s;
+    BEM_CUDA(cudaMemsetAsync(P->istate, 0, sizeof(int), s));
+    BEM_TRY(set_slots(P, g.chi, P->bvec, s));
+    BEM_TRY(enqueue_matvec(P, BEM_OP_B, P->green, P->k, s));
+    (k_nrm2_partial<C><<<GM_BLK, GM_T, 0, s>>>(n, P->bvec, partial, nullptr), ::bem::count_launch());
+    (k_nrm2_final<<<1, 32, 0, s>>>(partial, S.sc + 0, nullptr), ::bem::count_launch());
+    // With a float32 operator the true (float64) residual levels off near
+    // 2e-8; a mixed-precision solve therefore aims at max(tol, TAU_MIXED) and
+    // also stops once a whole restart cycle fails to halve the true residual.
+    const bool mixed = P->prm.precision == BEM_MIXED;
+    g.tol = mixed ? std::max(g.sp.tol, TAU_MIXED) : g.sp.tol;
+    BEM_TRY(set_scalar(S.sc + 3, g.tol, s));
+    BEM_CUDA(cudaMemsetAsync(g.x, 0, sizeof(double) * ne, s));
+    return gm_enqueue_residual<C>(g);
+}
+
+// one restart cycle: Arnoldi (CGS2) + Givens for up to m steps, then
+// x += V y; the number of steps taken is read back
+template <int C>
+static int gm_enqueue_cycle(GmSolver &g) {
+    bem_plan *P = g.P;
+    const int n = (int)P->N, m = P->gm_restart, ne = n * C;
+    const size_t ld = (size_t)ne;
+    double *V = P->V, *w = P->w, *partial = P->scal + 16;
+    GmState S = gm_state<C>(P);
+    const int eb = (ne + 255) / 256, nb = (n + 255) / 256;
+    int *skip = P->istate;
+    cudaStream_t s = g.s;
+    (k_scale<<<eb, 256, 0, s>>>(ne, V, S.sc + 1, V, nullptr), ::bem::count_launch());
+    (k_cycle_init<<<1, 1, 0, s>>>(S, m), ::bem::count_launch());
+    const int steps = std::min(m, g.sp.max_iter - g.iters);
+    for (int j = 0; j < steps; j++) {
+        BEM_TRY(set_slots(P, V + (size_t)j * ld, w, s));
+        BEM_TRY(enqueue_matvec(P, BEM_OP_A, P->green, P->k, s));
+        // CGS2: two classical Gram-Schmidt passes against V_0..V_j
+        (k_mdot<C><<<GM_BLK, GM_T, 0, s>>>(n, j + 1, V, ld, w, partial, skip), ::bem::count_launch());
+        (k_mdot_final<C><<<(j + 1 + 7) / 8, 256, 0, s>>>(j + 1, partial, S.hcol, 0, skip), ::bem::count_launch());
+        (k_orth_update<C><<<nb, 256, 0, s>>>(n, j + 1, V, ld, S.hcol, w, skip), ::bem::count_launch());
+        (k_mdot<C><<<GM_BLK, GM_T, 0, s>>>(n, j + 1, V, ld, w, partial, skip), ::bem::count_launch());
+        (k_mdot_final<C><<<(j + 1 + 7) / 8, 256, 0, s>>>(j + 1, partial, S.hcol2, 0, skip), ::bem::count_launch());
+        (k_orth_update<C><<<nb, 256, 0, s>>>(n, j + 1, V, ld, S.hcol2, w, skip), ::bem::count_launch());
+        (k_nrm2_partial<C><<<GM_BLK, GM_T, 0, s>>>(n, w, partial, skip), ::bem::count_launch());
+        (k_nrm2_final<<<1, 32, 0, s>>>(partial, S.sc + 4, skip), ::bem::count_launch());
+        (k_givens<C><<<1, 1, 0, s>>>(S, m, j), ::bem::count_launch());
+        (k_scale<<<eb, 256, 0, s>>>(ne, w, S.sc + 4, V + (size_t)(j + 1) * ld, skip), ::bem::count_launch());
+        BEM_LAUNCH_CHECK();
+    }
+    (k_backsolve<C><<<1, 1, 0, s>>>(S, m), ::bem::count_launch());
+    (k_xupdate<C><<<nb, 256, 0, s>>>(n, V, ld, S, g.x), ::bem::count_launch());
+    BEM_LAUNCH_CHECK();
+    BEM_CUDA(cudaMemcpyAsync(P->hostbuf + 2, S.st + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BEM_CUDA(cudaEventRecord(g.ev, s));
+    g.waiting = true;
+    g.phase = 2;
+    return BEM_OK;
+}
+
+// Advances the solve as far as finished device work allows.  blocking: wait
+// for each pending event; otherwise return as soon as one is still pending.
+template <int C>
+static int gm_advance(GmSolver &g, bool blocking) {
+    while (g.phase != 3) {
+        if (g.phase == 0) {
+            BEM_TRY(gm_enqueue_start<C>(g));
+            continue;
+        }
+        if (g.waiting) {
+            cudaError_t e = blocking ? cudaEventSynchronize(g.ev) : cudaEventQuery(g.ev);
+            if (e == cudaErrorNotReady) return BEM_OK;
+            if (e != cudaSuccess) return cuda_fail(e, "GMRES event", __FILE__, __LINE__);
+            g.waiting = false;
+        }
+        const double *h = g.P->hostbuf;
+        if (g.phase == 1) {
+            g.restarts++;
+            g.rel = h[0] > 0.0 ? h[1] / h[0] : 0.0;
+            const bool mixed = g.P->prm.precision == BEM_MIXED;
+            if (g.rel <= g.tol || h[0] == 0.0 || (mixed && g.restarts > 1 && g.rel > 0.5 * g.prev_rel)) {
+                g.status = BEM_OK;
+                g.phase = 3;
+                break;
+            }
+            g.prev_rel = g.rel;
+            if (g.iters >= g.sp.max_iter) {
+                g.status = BEM_ENOCONV;
+                g.phase = 3;
+                break;
+            }
+            BEM_TRY(gm_enqueue_cycle<C>(g));
+        } else {
+            int steps;
+            memcpy(&steps, g.P->hostbuf + 2, sizeof(int));
+            g.iters += steps;
+            if (steps == 0) {
+                g.status = BEM_ENOCONV;
+                g.phase = 3;
+                break;
+            }
+            BEM_TRY(gm_enqueue_residual<C>(g));
+        }
+    }
+    return BEM_OK;
+}
+
+static int gm_init(GmSolver &g, bem_plan *P, const double *chi, double *x, const bem_solve_params *sp, cudaStream_t s) {
+    g = GmSolver{};
+    g.P = P;
+    g.chi = chi;
+    g.x = x;
+    g.sp = *sp;
+    g.s = s;
+    BEM_TRY(gm_workspace(P, sp->restart));
+    BEM_CUDA(cudaEventCreateWithFlags(&g.ev, cudaEventDisableTiming));
+    return BEM_OK;
+}
+
+static int gm_run(GmSolver &g, bool blocking) {
+    return g.P->green == BEM_HELMHOLTZ ? gm_advance<2>(g, blocking) : gm_advance<1>(g, blocking);
+}
+
+int solve(bem_plan *P, const void *chi, void *phi, int nrhs, const bem_solve_params *sp, bem_solve_info *info,
+          cudaStream_t s) {
+    const int C = P->green == BEM_HELMHOLTZ ? 2 : 1;
     int worst = BEM_OK;
-    const size_t nchi = (size_t)P->nchi * C;
+    const size_t nchi = (size_t)P->nchi * C, ne = (size_t)P->N * C;
     for (int r = 0; r < nrhs; r++) {
-        const double *c = (const double *)chi + r * nchi;
-        double *x = (double *)phi + r * ne;
-        BEM_TRY(set_slots(P, c, P->bvec, s));
-        BEM_TRY(enqueue_matvec(P, BEM_OP_B, P->green, P->k, s));
-        int st = C == 1 ? gmres_one<1>(P, P->bvec, x, sp, info ? info + r : nullptr, s)
-                        : gmres_one<2>(P, P->bvec, x, sp, info ? info + r : nullptr, s);
-        if (st != BEM_OK && st != BEM_ENOCONV) return st;
-        if (st == BEM_ENOCONV) worst = st;
+        GmSolver g;
+        BEM_TRY(gm_init(g, P, (const double *)chi + r * nchi, (double *)phi + r * ne, sp, s));
+        int rc = gm_run(g, true);
+        cudaEventDestroy(g.ev);
+        if (rc != BEM_OK) return rc;
+        if (info) info[r] = bem_solve_info{g.iters, g.restarts, g.rel, g.status};
+        if (g.status == BEM_ENOCONV) worst = BEM_ENOCONV;
     }
     return worst;
 }
 
 }  // namespace bem
+
+// ---------------------------------------------------------------------------
+// Batch of concurrent solves (each on its own stream), for request serving
+// ---------------------------------------------------------------------------
+struct bem_batch {
+    int device = 0, nslot = 0;
+    std::vector<bem::GmSolver> slot;
+    std::vector<int> used;              // 0 free, 1 active, 2 finished
+    std::vector<cudaStream_t> streams;
+    ~bem_batch() {
+        for (auto &g : slot)
+            if (g.ev) cudaEventDestroy(g.ev);
+        for (auto s : streams)
+            if (s) cudaStreamDestroy(s);
+    }
+};
+
+using namespace bem;
+
+extern "C" {
+
+int bem_batch_create(bem_ctx *ctx, int max_slots, bem_batch **out) {
+    if (!ctx || !out || max_slots < 1 || max_slots > 4096) {
+        set_error("bem_batch_create: bad argument");
+        return BEM_EINVAL;
+    }
+    *out = nullptr;
+    BEM_CUDA(cudaSetDevice(ctx->device));
+    bem_batch *b = new (std::nothrow) bem_batch;
+    if (!b) { set_error("bem_batch_create: out of host memory"); return BEM_ENOMEM; }
+    b->device = ctx->device;
+    b->nslot = max_slots;
+    b->slot.resize(max_slots);
+    b->used.assign(max_slots, 0);
+    b->streams.assign(max_slots, nullptr);
+    for (int i = 0; i < max_slots; i++) {
+        cudaError_t e = cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking);
+        if (e != cudaSuccess) { delete b; return cuda_fail(e, "cudaStreamCreate", __FILE__, __LINE__); }
+    }
+    *out = b;
+    return BEM_OK;
+}
+
+void bem_batch_destroy(bem_batch *b) {
+    if (!b) return;
+    cudaSetDevice(b->device);
+    for (auto s : b->streams)
+        if (s) cudaStreamSynchronize(s);
+    delete b;
+}
+
+int bem_batch_submit(bem_batch *b, bem_plan *P, const void *chi_dev, void *phi_dev, const bem_solve_params *params,
+                     int *slot_out) {
+    if (!b || !P || !chi_dev || !phi_dev || !slot_out) { set_error("bem_batch_submit: NULL argument"); return BEM_EINVAL; }
+    bem_solve_params sp;
+    bem_solve_params_default(&sp);
+    if (params) sp = *params;
+    int free_slot = -1;
+    for (int i = 0; i < b->nslot; i++) {
+        if (b->used[i] == 0 && free_slot < 0) free_slot = i;
+        if (b->used[i] && b->slot[i].P == P) { set_error("bem_batch_submit: the plan already has a solve in the batch"); return BEM_EBUSY; }
+    }
+    if (free_slot < 0) { set_error("bem_batch_submit: no free slot"); return BEM_EBUSY; }
+    BEM_CUDA(cudaSetDevice(b->device));
+    GmSolver &g = b->slot[free_slot];
+    if (g.ev) cudaEventDestroy(g.ev);
+    BEM_TRY(gm_init(g, P, (const double *)chi_dev, (double *)phi_dev, &sp, b->streams[free_slot]));
+    b->used[free_slot] = 1;
+    int rc = gm_run(g, false);
+    if (rc != BEM_OK) { b->used[free_slot] = 2; g.status = rc; g.phase = 3; }
+    *slot_out = free_slot;
+    return rc;
+}
+
+int bem_batch_progress(bem_batch *b, int *n_active) {
+    if (!b) { set_error("bem_batch_progress: NULL batch"); return BEM_EINVAL; }
+    BEM_CUDA(cudaSetDevice(b->device));
+    int act = 0, worst = BEM_OK;
+    for (int i = 0; i < b->nslot; i++) {
+        if (b->used[i] != 1) continue;
+        GmSolver &g = b->slot[i];
+        int rc = gm_run(g, false);
+        if (rc != BEM_OK) { g.status = rc; g.phase = 3; worst = rc; }
+        if (g.phase == 3) b->used[i] = 2;
+        else act++;
+    }
+    if (n_active) *n_active = act;
+    return worst;
+}
+
+int bem_batch_poll(bem_batch *b, int slot, int *done, bem_solve_info *info) {
+    if (!b || slot < 0 || slot >= b->nslot || !done) { set_error("bem_batch_poll: bad argument"); return BEM_EINVAL; }
+    *done = b->used[slot] == 2;
+    if (*done && info) {
+        const GmSolver &g = b->slot[slot];
+        *info = bem_solve_info{g.iters, g.restarts, g.rel, g.status};
+    }
+    return BEM_OK;
+}
+
+int bem_batch_wait(bem_batch *b, int slot, double timeout_s) {
+    if (!b || slot < 0 || slot >= b->nslot || b->used[slot] == 0) { set_error("bem_batch_wait: bad slot"); return BEM_EINVAL; }
+    const auto t0 = std::chrono::steady_clock::now();
+    while (b->used[slot] == 1) {
+        BEM_TRY(bem_batch_progress(b, nullptr));
+        if (b->used[slot] != 1) break;
+        const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el > timeout_s) { set_error("bem_batch_wait: slot %d not finished after %g s", slot, timeout_s); return BEM_ETIMEOUT; }
+        cudaEventSynchronize(b->slot[slot].ev);    // sleep until this slot's next step is done
+    }
+    return BEM_OK;
+}
+
+int bem_batch_release(bem_batch *b, int slot) {
+    if (!b || slot < 0 || slot >= b->nslot) { set_error("bem_batch_release: bad slot"); return BEM_EINVAL; }
+    if (b->used[slot] == 1) { set_error("bem_batch_release: slot %d is still running", slot); return BEM_EBUSY; }
+    BEM_CUDA(cudaSetDevice(b->device));
+    BEM_CUDA(cudaStreamSynchronize(b->streams[slot]));
+    b->used[slot] = 0;
+    b->slot[slot].P = nullptr;
+    return BEM_OK;
+}
+
+void *bem_batch_stream(bem_batch *b, int slot) {
+    if (!b || slot < 0 || slot >= b->nslot) return nullptr;
+    return (void *)b->streams[slot];
+}
+
+}  // extern "C"
