@@ -3,7 +3,8 @@
 Workload (default): Laplace exterior Neumann problem on the cube [-1,1]^3,
 45 x 45 graded quads per face split into 24,300 6-node triangles (48,602
 nodes), point source at (0.2, -0.1, 0.3), expansion order p = 10, leaf size
-64, separation factor 2, GMRES(30).
+64, separation factor 2, GMRES(30), in the mixed form (float32 near field and
+expansions, float64 Krylov); --precision f64 times the plain float64 form.
 
 One step = one complete pass of the hot path from a device-resident mesh:
 plan build on the device (quadrature geometry, octree, radii, lists,
@@ -13,8 +14,10 @@ step).  value = solves per second over all ranks (each rank an independent
 replica).  The L2 cache is flushed between steps.
 
 Extra keys: matvecs_per_s (back-to-back A products of a built plan), per-stage
-times, the roofline of the dominant kernel against measured peaks, the CPU
-oracle baseline, end-to-end timing through the public API with host buffers.
+times, the roofline of the dominant kernel against measured peaks, the plain
+float64 form on the same workload with the mixed solution's error against it
+(f64_form), a served request stream in both forms (serving), the CPU oracle
+baseline, end-to-end timing through the public API with host buffers.
 
 --impl reference times the CPU oracle (the plain FP64 matrix-free operator
 rows) on a bounded sample of the same workload and extrapolates to solves/s.
@@ -51,9 +54,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="f64", choices=["f64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["f64", "mixed"])
     ap.add_argument("--n", type=int, default=45, help="quads per cube face edge")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-f64", action="store_true", help="skip timing the plain float64 form")
+    ap.add_argument("--serve-requests", type=int, default=8, help="requests in the serving stream (0: skip)")
+    ap.add_argument("--serve-max-elems", type=int, default=20000, help="largest mesh of the serving stream")
     return ap.parse_args()
 
 
@@ -166,6 +172,113 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def time_solves(bem, torch, mesh, stream, dev, prec, chi_d, phi_d, steps, warmup, flush, world, dist):
+    """Device-timed steps (plan build + RHS product + GMRES) in one precision."""
+    prm = bem.bem_fmm_params_default(p=10, leaf_size=64, eta=2.0, precision=prec)
+    sp = bem.bem_solve_params_default(restart=30, tol=1e-10, max_iter=600)
+
+    def step(mid=None):
+        plan = bem.bem_plan_create(mesh, bem.BEM_LAPLACE, 0.0, prm, stream)
+        if mid is not None:
+            mid.record(stream)
+        code, info = bem.bem_solve(plan, chi_d, phi_d, 1, sp, stream)
+        return plan, info[0]
+
+    for _ in range(warmup):
+        plan, info = step()
+        stream.synchronize()
+        bem.bem_plan_destroy(plan)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = bem.bem_launch_count()
+    total_ms, lat, setup_ms, infos = 0.0, [], [], []
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0, em, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        plan, info = step(em)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        total_ms += ms
+        lat.append(ms)
+        setup_ms.append(e0.elapsed_time(em))
+        infos.append(info)
+        bem.bem_plan_destroy(plan)
+    torch.cuda.synchronize()
+    launches = bem.bem_launch_count() - l0
+    t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    max_ms = float(t.item())
+    return {"value": world * steps / (max_ms / 1000.0), "ms_per_step": max_ms / steps, "lat": lat,
+            "setup_ms": float(np.mean(setup_ms)), "solve_ms": float(np.mean(lat) - np.mean(setup_ms)),
+            "infos": infos, "launches": int(launches), "prm": prm, "sp": sp}
+
+
+def matvec_rate(bem, torch, mesh, stream, dev, prm, n_phi, flush):
+    """Back-to-back A products of one built plan, per-stage times, counters."""
+    plan = bem.bem_plan_create(mesh, bem.BEM_LAPLACE, 0.0, prm, stream)
+    st = bem.bem_plan_stats(plan)
+    x_d = torch.randn(n_phi, device=dev, dtype=torch.float64, generator=torch.Generator(device=dev).manual_seed(1))
+    y_d = torch.empty_like(x_d)
+    for _ in range(3):
+        bem.bem_matvec(plan, bem.BEM_OP_A, x_d, y_d, stream)
+    with torch.cuda.stream(stream):
+        flush.zero_()
+    nmv = 30
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(nmv):
+        bem.bem_matvec(plan, bem.BEM_OP_A, x_d, y_d, stream)
+    e1.record(stream)
+    e1.synchronize()
+    rate = nmv / (e0.elapsed_time(e1) / 1000.0)
+    stages = bem.bem_plan_stage_times(plan, bem.BEM_OP_A, x_d, y_d, reps=10, stream=stream)
+    setup_stages = bem.bem_plan_setup_times(plan)
+    bem.bem_plan_destroy(plan)
+    return rate, stages, setup_stages, st
+
+
+def serving(args):
+    """The same Poisson request stream twice: the mixed form with continuous
+    batching, then the plain float64 form one request at a time."""
+    from paper_0908_0673_gb300 import bem
+    from paper_0908_0673_gb300.serve import CudaEngine, Server, summarize, synthetic_stream
+    reqs = synthetic_stream(args.serve_requests, rate_per_s=200.0, elems=(1000, args.serve_max_elems),
+                            k_range=(1.0, 4.0), rhs=(1, 8), seed=0)
+    out = {"stream": {"requests": len(reqs), "arrivals": "Poisson, 200 /s, seed 0",
+                      "elements": f"log-uniform 1000-{args.serve_max_elems}, 6-node triangles",
+                      "geometry": "geodesic sphere | ellipsoid (axes U[0.5,2]) | graded cube",
+                      "green": "50% Laplace, 50% Helmholtz k U[1,4]", "rhs": "1-8 interior point sources",
+                      "total_solves": sum(len(r.rhs) for r in reqs)}}
+    phis = {}
+    for name, prec, slots, threads in (("mixed_continuous", bem.BEM_MIXED, 8, 2),
+                                       ("f64_one_at_a_time", bem.BEM_F64, 1, 1)):
+        eng = CudaEngine(precision=prec, max_slots=slots)
+        try:
+            res = Server(eng, max_inflight=slots, setup_threads=threads, keep_phi=True).run(reqs)
+        finally:
+            eng.close()
+        out[name] = summarize(res)
+        phis[name] = {r.rid: r.phi for r in res if r.phi is not None}
+    errs = []
+    for rid, ph in phis["mixed_continuous"].items():
+        ref = phis["f64_one_at_a_time"].get(rid)
+        if ref is None:
+            continue
+        for a, b in zip(ph, ref):
+            errs.append(float(np.linalg.norm(a - b) / np.linalg.norm(b)))
+    out["rel_err_vs_f64"] = {"max": max(errs) if errs else None,
+                             "within_1e-5": int(sum(e <= 1e-5 for e in errs)), "solves": len(errs)}
+    mx, f64 = out["mixed_continuous"], out["f64_one_at_a_time"]
+    out["speedup_solves_per_s"] = mx["solves_per_s"] / f64["solves_per_s"]
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -183,8 +296,6 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     prec = bem.BEM_MIXED if args.precision == "mixed" else bem.BEM_F64
-    prm = bem.bem_fmm_params_default(p=10, leaf_size=64, eta=2.0, precision=prec)
-    sp = bem.bem_solve_params_default(restart=30, tol=1e-10, max_iter=600)
 
     m, phi_ex, chi_e = workload(args.n)
     ctx = bem.bem_ctx_create(local)
@@ -197,74 +308,28 @@ def main():
     phi_d = torch.empty(n_phi, device=dev, dtype=torch.float64)
     flush = torch.empty(256 * 1024 * 1024 // 4, device=dev, dtype=torch.float32)   # > 129 MB L2
 
-    def step(mid=None):
-        plan = bem.bem_plan_create(mesh, bem.BEM_LAPLACE, 0.0, prm, stream)
-        if mid is not None:
-            mid.record(stream)
-        code, info = bem.bem_solve(plan, chi_d, phi_d, 1, sp, stream)
-        return plan, info[0]
-
-    infos = []
-    for _ in range(args.warmup):
-        plan, info = step()
-        stream.synchronize()
-        bem.bem_plan_destroy(plan)
-    # timed region
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
     clocks = Clocks(local)
-    l0 = bem.bem_launch_count()
-    total_ms = 0.0
-    lat, setup_ms = [], []
-    for _ in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.zero_()
-        e0, em, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        e0.record(stream)
-        plan, info = step(em)
-        e1.record(stream)
-        e1.synchronize()
-        ms = e0.elapsed_time(e1)
-        total_ms += ms
-        lat.append(ms)
-        setup_ms.append(e0.elapsed_time(em))
-        infos.append(info)
-        bem.bem_plan_destroy(plan)
-    torch.cuda.synchronize()
-    launches = bem.bem_launch_count() - l0
+    main_run = time_solves(bem, torch, mesh, stream, dev, prec, chi_d, phi_d, args.steps, args.warmup, flush,
+                           world, dist)
     clk = clocks.stop()
-    t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.barrier()
-    max_ms = float(t.item())
-    ms_per_step = max_ms / args.steps
-    value = world * args.steps / (max_ms / 1000.0)
     phi = phi_d.cpu().numpy()
     eps_rms = float(np.sqrt(np.mean((phi - phi_ex) ** 2)))
+    prm, sp, infos = main_run["prm"], main_run["sp"], main_run["infos"]
 
-    # matvec rate and per-stage times on one built plan
-    plan = bem.bem_plan_create(mesh, bem.BEM_LAPLACE, 0.0, prm, stream)
-    st = bem.bem_plan_stats(plan)
-    x_d = torch.randn(n_phi, device=dev, dtype=torch.float64, generator=torch.Generator(device=dev).manual_seed(1))
-    y_d = torch.empty_like(x_d)
-    for _ in range(3):
-        bem.bem_matvec(plan, bem.BEM_OP_A, x_d, y_d, stream)
-    with torch.cuda.stream(stream):
-        flush.zero_()
-    nmv = 30
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(nmv):
-        bem.bem_matvec(plan, bem.BEM_OP_A, x_d, y_d, stream)
-    e1.record(stream)
-    e1.synchronize()
-    matvecs_per_s = nmv / (e0.elapsed_time(e1) / 1000.0)
-    stages = bem.bem_plan_stage_times(plan, bem.BEM_OP_A, x_d, y_d, reps=10, stream=stream)
-    setup_stages = bem.bem_plan_setup_times(plan)
-    setup_plan_ms = None
-    bem.bem_plan_destroy(plan)
+    # the plain float64 form on the same workload, for comparison
+    other = None
+    if prec == bem.BEM_MIXED and not args.no_f64:
+        phi64_d = torch.empty_like(phi_d)
+        f = time_solves(bem, torch, mesh, stream, dev, bem.BEM_F64, chi_d, phi64_d, max(1, min(args.steps, 3)),
+                        1, flush, world, dist)
+        phi64 = phi64_d.cpu().numpy()
+        mv64 = matvec_rate(bem, torch, mesh, stream, dev, f["prm"], n_phi, flush)
+        other = {"solves_per_s": f["value"], "ms_per_step": f["ms_per_step"], "setup_ms": f["setup_ms"],
+                 "solve_ms": f["solve_ms"], "gmres_iters": [i.iters for i in f["infos"]], "matvecs_per_s": mv64[0],
+                 "stage_ms": mv64[1], "steps": max(1, min(args.steps, 3)), "warmup": 1,
+                 "rel_err_of_mixed_solution": float(np.linalg.norm(phi - phi64) / np.linalg.norm(phi64))}
+
+    matvecs_per_s, stages, setup_stages, st = matvec_rate(bem, torch, mesh, stream, dev, prm, n_phi, flush)
 
     # roofline of the dominant kernel
     dom = max(stages, key=stages.get)
@@ -316,22 +381,27 @@ def main():
     e2e_value = world * 1000.0 / statistics.mean(e2e_ms)
 
     iters = [i.iters for i in infos]
+    lat = main_run["lat"]
     out = {
-        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": main_run["value"], "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": main_run["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if prec == bem.BEM_MIXED else "f64", "data": "synthetic",
         "config": {"workload": f"cube{args.n}-tri6-laplace", "elements": int(m.n_elems), "nodes": int(n_phi), "chi": int(n_chi),
                    "p": 10, "leaf_size": 64, "eta": 2.0, "precision": args.precision, "gmres": "restart 30, tol 1e-10",
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}",
                    "step": "device plan build + RHS product + GMRES solve"},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
-        "setup_ms": float(np.mean(setup_ms)), "solve_ms": float(np.mean(lat) - np.mean(setup_ms)),
+        "setup_ms": main_run["setup_ms"], "solve_ms": main_run["solve_ms"],
         "gmres_iters": iters, "rel_residual": infos[-1].rel_residual if infos else None,
         "eps_rms_vs_point_source": eps_rms,
         "matvecs_per_s": matvecs_per_s, "stage_ms": stages, "setup_stage_ms": setup_stages, "plan_stats": st,
-        "roofline": roof, "clocks": clk, "gpu_launches": int(launches),
+        "roofline": roof, "clocks": clk, "gpu_launches": main_run["launches"],
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
     }
+    if other is not None:
+        out["f64_form"] = other
+    if rank == 0 and world == 1 and args.serve_requests > 0:
+        out["serving"] = serving(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(m, chi_idx, n_phi, statistics.median(iters) if iters else 60)
     if rank == 0:

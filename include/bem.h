@@ -260,6 +260,11 @@ int bem_plan_diagonal(const bem_plan *plan, double *c);
 /* Device memory held by the plan, in bytes. */
 int bem_plan_footprint(const bem_plan *plan, size_t *hbm_bytes);
 
+/* Most device memory the plan has held at any one time, in bytes: set-up
+ * allocates temporaries (the diagonal's higher-order product) and the first
+ * solve adds the Krylov basis, so this is what admission control must reserve. */
+int bem_plan_peak_footprint(const bem_plan *plan, size_t *hbm_bytes);
+
 /* Integer counters of the plan (host array of 12): [0] n_boxes, [1] n_leaves,
  * [2] n_levels, [3] near-list entries, [4] interaction-list entries,
  * [5] near-field source-target pairs per matrix multiplication, [6] correction

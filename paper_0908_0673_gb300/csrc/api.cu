@@ -48,7 +48,11 @@ int set_slots(bem_plan *P, const void *x, void *y, cudaStream_t s) {
 // Enqueues the full product y = A x or B x on stream s, reading the vectors
 // from the plan's device slots.  The kernel sequence is captured once per
 // operator into a CUDA graph (on a private stream, since the legacy default
-// stream cannot be captured) and replayed afterwards.
+// stream cannot be captured) and replayed afterwards.  Another host thread
+// can invalidate a capture in progress (its first launch of a kernel loads
+// the kernel, which synchronises the context); the partial graph is then
+// dropped, this product is enqueued kernel by kernel on s, and the capture
+// is tried again on the next call.
 int enqueue_matvec(bem_plan *P, int op, int green, double k, cudaStream_t s) {
     cudaGraphExec_t &ge = P->graph[op];
     if (!ge) {
@@ -60,11 +64,18 @@ int enqueue_matvec(bem_plan *P, int op, int green, double k, cudaStream_t s) {
         int rc = enqueue_matvec_raw(P, op, green, k, 1, P->capture_stream);
         tl_capture_count = nullptr;
         cudaError_t e = cudaStreamEndCapture(P->capture_stream, &g);
-        if (rc != BEM_OK) {
+        const bool invalidated = e == cudaErrorStreamCaptureInvalidated ||
+                                 (rc != BEM_OK && cudaPeekAtLastError() == cudaErrorStreamCaptureInvalidated);
+        if (rc != BEM_OK || e != cudaSuccess) {
             if (g) cudaGraphDestroy(g);
-            return rc;
+            if (!invalidated) return rc != BEM_OK ? rc : cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+            cudaGetLastError();                     // not sticky: clear it and run uncaptured
+            P->capture_retries++;
+            P->graph_kernels[op] = 0;
+            BEM_TRY(enqueue_matvec_raw(P, op, green, k, 1, s));
+            P->last_op = op;
+            return BEM_OK;
         }
-        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
         e = cudaGraphInstantiate(&ge, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
@@ -400,6 +411,12 @@ int bem_plan_diagonal(const bem_plan *P, double *c) {
 int bem_plan_footprint(const bem_plan *P, size_t *hbm_bytes) {
     if (!P || !hbm_bytes) { set_error("bem_plan_footprint: NULL argument"); return BEM_EINVAL; }
     *hbm_bytes = P->arena.bytes;
+    return BEM_OK;
+}
+
+int bem_plan_peak_footprint(const bem_plan *P, size_t *hbm_bytes) {
+    if (!P || !hbm_bytes) { set_error("bem_plan_peak_footprint: NULL argument"); return BEM_EINVAL; }
+    *hbm_bytes = P->arena.peak;
     return BEM_OK;
 }
 

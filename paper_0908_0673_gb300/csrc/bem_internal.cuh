@@ -48,6 +48,7 @@ struct Arena {
     std::vector<void *> ptrs;
     std::vector<size_t> sizes;
     size_t bytes = 0;                   // bytes currently held
+    size_t peak = 0;                    // most bytes held at any time
     template <class T>
     int alloc(T **p, size_t n) {
         *p = nullptr;
@@ -57,6 +58,7 @@ struct Arena {
         ptrs.push_back(*p);
         sizes.push_back(n * sizeof(T));
         bytes += n * sizeof(T);
+        if (bytes > peak) peak = bytes;
         return BEM_OK;
     }
     void release(void *p) {
@@ -205,6 +207,7 @@ struct bem_plan {
     int *istate = nullptr;              // device ints: [0] converged flag, [1] steps in cycle
     int gm_restart = 0;
     cudaGraphExec_t cycle_graph = nullptr;
+    int capture_retries = 0;            // captures invalidated by other host threads
     ~bem_plan();
 };
 

@@ -21,6 +21,7 @@
 // sources.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "bem_internal.cuh"
 
@@ -576,6 +577,33 @@ static QuadView quad_of(const bem_plan *P) {
     return QuadView{q.x, q.y, q.z, q.nx, q.ny, q.nz, q.w, q.fx, q.fy, q.fz, q.fnx, q.fny, q.fnz, q.fw};
 }
 
+// Shape-function values at the 7 rule points, in constant memory.  Written
+// once per device (under a lock): plans are built from several host threads
+// while kernels of other plans that read the table are running.
+static int init_shape_table(int device) {
+    static std::mutex mu;
+    static bool done[64] = {};
+    std::lock_guard<std::mutex> lock(mu);
+    if (device < 0 || device >= 64) { set_error("device %d out of range", device); return BEM_EINVAL; }
+    if (done[device]) return BEM_OK;
+    double Lq[2][NQ][6] = {};
+    {
+        const double q = std::sqrt(15.0);
+        const double a = (6.0 - q) / 21.0, b = (9.0 + 2.0 * q) / 21.0;
+        const double c = (6.0 + q) / 21.0, d = (9.0 - 2.0 * q) / 21.0;
+        const double S[7] = {1.0 / 3.0, a, b, a, c, d, c}, T[7] = {1.0 / 3.0, a, a, b, c, c, d};
+        for (int r = 0; r < NQ; r++) {
+            double l0 = 1.0 - S[r] - T[r], l1 = S[r], l2 = T[r];
+            Lq[0][r][0] = l0; Lq[0][r][1] = l1; Lq[0][r][2] = l2;
+            Lq[1][r][0] = l0 * (2 * l0 - 1); Lq[1][r][1] = l1 * (2 * l1 - 1); Lq[1][r][2] = l2 * (2 * l2 - 1);
+            Lq[1][r][3] = 4 * l0 * l1; Lq[1][r][4] = 4 * l1 * l2; Lq[1][r][5] = 4 * l2 * l0;
+        }
+    }
+    BEM_CUDA(cudaMemcpyToSymbol(c_Lq, Lq, sizeof(Lq)));
+    done[device] = true;
+    return BEM_OK;
+}
+
 int alloc_fmm(bem_plan *P, cudaStream_t s) {
     Arena &A = P->arena;
     MIndex &mi = P->mi;
@@ -598,21 +626,7 @@ int alloc_fmm(bem_plan *P, cudaStream_t s) {
     BEM_TRY(A.alloc(&P->d_binom, binom.size()));
     BEM_CUDA(cudaMemcpy(P->d_fact, fact.data(), sizeof(double) * fact.size(), cudaMemcpyHostToDevice));
     BEM_CUDA(cudaMemcpy(P->d_binom, binom.data(), sizeof(double) * binom.size(), cudaMemcpyHostToDevice));
-    // shape values at the rule points
-    double Lq[2][NQ][6] = {};
-    {
-        const double q = std::sqrt(15.0);
-        const double a = (6.0 - q) / 21.0, b = (9.0 + 2.0 * q) / 21.0;
-        const double c = (6.0 + q) / 21.0, d = (9.0 - 2.0 * q) / 21.0;
-        const double S[7] = {1.0 / 3.0, a, b, a, c, d, c}, T[7] = {1.0 / 3.0, a, a, b, c, c, d};
-        for (int r = 0; r < NQ; r++) {
-            double l0 = 1.0 - S[r] - T[r], l1 = S[r], l2 = T[r];
-            Lq[0][r][0] = l0; Lq[0][r][1] = l1; Lq[0][r][2] = l2;
-            Lq[1][r][0] = l0 * (2 * l0 - 1); Lq[1][r][1] = l1 * (2 * l1 - 1); Lq[1][r][2] = l2 * (2 * l2 - 1);
-            Lq[1][r][3] = 4 * l0 * l1; Lq[1][r][4] = 4 * l1 * l2; Lq[1][r][5] = 4 * l2 * l0;
-        }
-    }
-    BEM_CUDA(cudaMemcpyToSymbol(c_Lq, Lq, sizeof(Lq)));
+    BEM_TRY(init_shape_table(P->device));
     const bool mx = P->prm.precision == BEM_MIXED;
     if (mx) {
         BEM_TRY(A.alloc(&P->ff, (size_t)P->Q * C));

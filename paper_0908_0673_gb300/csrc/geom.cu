@@ -18,6 +18,8 @@
 #include <cmath>
 #include <vector>
 
+#include <mutex>
+
 #include "bem_internal.cuh"
 
 namespace bem {
@@ -66,7 +68,10 @@ static void gauss_legendre(int n, double *x, double *w) {
 }
 
 __constant__ Rule7 c_rule;
-__constant__ double c_glx[64], c_glw[64];
+// Gauss-Legendre nodes and weights of every order n = 1..64, order n at
+// offset n (n - 1) / 2, so that plans with different Duffy orders share them.
+constexpr int GL_MAXN = 64;
+__constant__ double c_glx[GL_MAXN * (GL_MAXN + 1) / 2], c_glw[GL_MAXN * (GL_MAXN + 1) / 2];
 
 // Shape functions in the fixed operation order that the radii and the pair
 // classification rely on.  L0 = (1 - s) - t, L1 = s, L2 = t.
@@ -176,18 +181,29 @@ __global__ void k_elem_centroid(int E, int npe, const int *__restrict__ el_phi, 
     ecx[i] = x[0]; ecy[i] = x[1]; ecz[i] = x[2]; eh[i] = m;
 }
 
+// The 7-point rule and the Gauss-Legendre tables are the same for every
+// plan: written to constant memory once per device, under a lock, because
+// plans are built from several host threads while other plans' kernels run.
+static int init_rule_tables(int device) {
+    static std::mutex mu;
+    static bool done[64] = {};
+    std::lock_guard<std::mutex> lock(mu);
+    if (device < 0 || device >= 64) { set_error("device %d out of range", device); return BEM_EINVAL; }
+    if (done[device]) return BEM_OK;
+    Rule7 r = make_rule7();
+    BEM_CUDA(cudaMemcpyToSymbol(c_rule, &r, sizeof(r)));
+    std::vector<double> gx(GL_MAXN * (GL_MAXN + 1) / 2), gw(gx.size());
+    for (int n = 1; n <= GL_MAXN; n++) gauss_legendre(n, &gx[n * (n - 1) / 2], &gw[n * (n - 1) / 2]);
+    BEM_CUDA(cudaMemcpyToSymbol(c_glx, gx.data(), sizeof(double) * gx.size()));
+    BEM_CUDA(cudaMemcpyToSymbol(c_glw, gw.data(), sizeof(double) * gw.size()));
+    done[device] = true;
+    return BEM_OK;
+}
+
 int build_geometry(bem_plan *P, cudaStream_t s) {
     Tree &t = P->t;
     Arena &A = P->arena;
-    static bool consts = false;
-    (void)consts;
-    Rule7 r = make_rule7();
-    BEM_CUDA(cudaMemcpyToSymbolAsync(c_rule, &r, sizeof(r), 0, cudaMemcpyHostToDevice, s));
-    const int nd = P->prm.n_duffy;
-    double gx[64], gw[64];
-    gauss_legendre(nd, gx, gw);
-    BEM_CUDA(cudaMemcpyToSymbolAsync(c_glx, gx, sizeof(double) * nd, 0, cudaMemcpyHostToDevice, s));
-    BEM_CUDA(cudaMemcpyToSymbolAsync(c_glw, gw, sizeof(double) * nd, 0, cudaMemcpyHostToDevice, s));
+    BEM_TRY(init_rule_tables(P->device));
     const int64_t Q = P->Q;
     Quad &q = P->q;
     BEM_TRY(A.alloc(&q.x, Q)); BEM_TRY(A.alloc(&q.y, Q)); BEM_TRY(A.alloc(&q.z, Q));
@@ -515,8 +531,9 @@ __global__ void __launch_bounds__(32 * SW_WARPS) k_special_warp(CorrArgs a, int 
             default: P = mm[2]; Q1 = sub ? c1 : c0; Q2 = sub ? c2 : c1; break;
             }
             const double det = fabs((Q1[0] - P[0]) * (Q2[1] - P[1]) - (Q1[1] - P[1]) * (Q2[0] - P[0]));
-            const double u = 0.5 * (1.0 + c_glx[iu]), wu = 0.5 * c_glw[iu];
-            const double v = 0.5 * (1.0 + c_glx[iv]), wv = 0.5 * c_glw[iv];
+            const int go = nd * (nd - 1) / 2;
+            const double u = 0.5 * (1.0 + c_glx[go + iu]), wu = 0.5 * c_glw[go + iu];
+            const double v = 0.5 * (1.0 + c_glx[go + iv]), wv = 0.5 * c_glw[go + iv];
             const double s = P[0] + u * (Q1[0] - P[0]) + u * v * (Q2[0] - Q1[0]);
             const double t = P[1] + u * (Q1[1] - P[1]) + u * v * (Q2[1] - Q1[1]);
             acc_local<R, HELM, NPE>(d, kk, (R)s, (R)t, (R)(wu * wv * u * det), acc);

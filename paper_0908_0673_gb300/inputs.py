@@ -130,6 +130,80 @@ def icosphere(level: int, elem_type: int = TRI3, radius: float = 1.0) -> Mesh:
                 {"level": level, "radius": radius})
 
 
+def geodesic(freq: int, elem_type: int = TRI6, axes=(1.0, 1.0, 1.0)) -> Mesh:
+    """Frequency-``freq`` geodesic sphere: every icosahedron face cut into
+    freq^2 triangles on a barycentric grid, points projected onto the unit
+    sphere, then scaled by the semi-axes ``axes`` (an ellipsoid unless all are
+    1).  20 freq^2 elements; 10 freq^2 + 2 nodes (tri3) or 40 freq^2 + 2
+    (tri6, whose mid-side nodes are the odd points of the grid of frequency
+    2 freq, so they lie on the surface).  Points on an icosahedron edge are
+    computed once, from the edge's lower-numbered vertex, so neighbouring faces
+    share them exactly."""
+    if freq < 1:
+        raise ValueError("freq must be >= 1")
+    V, Fc = _icosahedron()
+    F = freq * (2 if elem_type == TRI6 else 1)          # grid frequency
+    edges = {}
+    for a, b, c in Fc:
+        for u, v in ((a, b), (b, c), (c, a)):
+            edges.setdefault((min(u, v), max(u, v)), len(edges))
+    n_int = (F - 1) * (F - 2) // 2                      # interior points per face
+    base_e, base_f = 12, 12 + 30 * (F - 1)
+    pts = np.zeros((base_f + 20 * n_int, 3))
+    pts[:12] = V
+    t = np.arange(1, F)[:, None] / F
+    for (lo, hi), e in edges.items():
+        pts[base_e + e * (F - 1): base_e + (e + 1) * (F - 1)] = V[lo] + (V[hi] - V[lo]) * t
+    ii, jj = np.meshgrid(np.arange(F + 1), np.arange(F + 1), indexing="ij")
+    keep = ii + jj <= F
+    ii, jj = ii[keep], jj[keep]
+    kk = F - ii - jj
+    interior = (ii > 0) & (jj > 0) & (kk > 0)
+    gidx = np.empty((20, F + 1, F + 1), np.int64)
+    for f, (a, b, c) in enumerate(Fc):
+        w = np.stack([kk, ii, jj], 1)                    # weights of a, b, c
+        ids = np.array([a, b, c])
+        g = np.empty(len(ii), np.int64)
+        nz = (w > 0).sum(1)
+        vert = nz == 1
+        g[vert] = ids[np.argmax(w[vert], 1)]
+        edge = nz == 2
+        for r in np.nonzero(edge)[0]:
+            (p, q), = [tuple(ids[w[r] > 0])]
+            lo, hi = min(p, q), max(p, q)
+            s = w[r][ids == hi][0]                      # steps from lo toward hi
+            g[r] = base_e + edges[(lo, hi)] * (F - 1) + s - 1
+        first = base_f + f * n_int
+        g[interior] = first + np.arange(n_int)
+        pts[first: first + n_int] = (V[a] * kk[interior, None] + V[b] * ii[interior, None]
+                                     + V[c] * jj[interior, None]) / F
+        gidx[f][ii, jj] = g
+    pts /= np.linalg.norm(pts, axis=1, keepdims=True)
+    s = 2 if elem_type == TRI6 else 1
+    el = []
+    i, j = np.meshgrid(np.arange(freq), np.arange(freq), indexing="ij")
+    up = (i + j) <= freq - 1
+    dn = (i + j) <= freq - 2
+    for f in range(20):
+        G = gidx[f]
+        for msk, corners in ((up, ((0, 0), (1, 0), (0, 1))), (dn, ((1, 0), (1, 1), (0, 1)))):
+            I0, J0 = s * i[msk], s * j[msk]
+            cs = [(I0 + s * di, J0 + s * dj) for di, dj in corners]
+            cols = [G[ci, cj] for ci, cj in cs]
+            if elem_type == TRI6:
+                for p, q in ((0, 1), (1, 2), (2, 0)):
+                    cols.append(G[(cs[p][0] + cs[q][0]) // 2, (cs[p][1] + cs[q][1]) // 2])
+            el.append(np.stack(cols, 1))
+    elems = np.concatenate(el).astype(np.int32)
+    a = np.asarray(axes, dtype=np.float64)
+    nodes = pts * a
+    g = nodes[elems] / (a * a)
+    nrm = g / np.linalg.norm(g, axis=2, keepdims=True)
+    kind = "sphere" if np.all(a == 1.0) else "ellipsoid"
+    return Mesh(f"geodesic{freq}-{kind}-{'tri6' if elem_type == TRI6 else 'tri3'}", nodes, elems,
+                elem_type, nrm, {"freq": freq, "axes": a.tolist()})
+
+
 def ellipsoid(level: int, axes, elem_type: int = TRI6) -> Mesh:
     """Sphere mesh scaled by semi-axes ``axes``; mid-side nodes are placed on
     the ellipsoid by scaling the sphere-projected chord midpoints."""
