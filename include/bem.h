@@ -260,6 +260,11 @@ int bem_plan_diagonal(const bem_plan *plan, double *c);
 /* Device memory held by the plan, in bytes. */
 int bem_plan_footprint(const bem_plan *plan, size_t *hbm_bytes);
 
+/* Device-side status of the plan's kernels (blocks until the device is idle):
+ * 0, or 1 when a kernel's bounded wait on the tensor cores gave up (that
+ * kernel then stopped early and its product is incomplete). */
+int bem_plan_device_status(const bem_plan *plan, int *status);
+
 /* Most device memory the plan has held at any one time, in bytes: set-up
  * allocates temporaries (the diagonal's higher-order product) and the first
  * solve adds the Krylov basis, so this is what admission control must reserve. */

@@ -31,6 +31,7 @@ EXPORTS = [
     "bem_launch_count", "bem_measure_peak", "bem_mesh_upload", "bem_matvec_noalloc", "bem_plan_setup_times",
     "bem_batch_create", "bem_batch_destroy", "bem_batch_submit", "bem_batch_progress", "bem_batch_poll",
     "bem_batch_wait", "bem_batch_release", "bem_batch_stream", "bem_plan_peak_footprint",
+    "bem_plan_device_status",
 ]
 BEM_NSETUP = 7
 SETUP_NAMES = ["upload", "tree", "geometry_radii_lists", "correction", "m2l_classes", "diagonal_tables", "stats"]
@@ -346,6 +347,12 @@ def bem_plan_diagonal(plan, n_phi):
 def bem_plan_footprint(plan) -> int:
     v = C.c_size_t()
     _check(load().bem_plan_footprint(plan, C.byref(v)))
+    return v.value
+
+
+def bem_plan_device_status(plan) -> int:
+    v = C.c_int()
+    _check(load().bem_plan_device_status(plan, C.byref(v)))
     return v.value
 
 

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libbem.so")
-HEADERS = [os.path.join(SRC, "bem_internal.cuh"), os.path.join(os.path.dirname(HERE), "include", "bem.h")]
+HEADERS = [os.path.join(SRC, "bem_internal.cuh"), os.path.join(SRC, "tc_ptx.cuh"), os.path.join(os.path.dirname(HERE), "include", "bem.h")]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")

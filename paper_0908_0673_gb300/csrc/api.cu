@@ -119,6 +119,7 @@ static int plan_setup(bem_plan *P, cudaStream_t s) {
     BEM_TRY(A.alloc(&P->istate, 4));
     BEM_CUDA(cudaMemsetAsync(P->istate, 0, sizeof(int) * 4, s));
     P->skip = P->istate;
+    P->dev_err = P->istate + 3;
     // stage timers (wall clock, stream synchronised at every boundary)
     auto t0 = std::chrono::steady_clock::now();
     auto lap = [&](int i) -> int {
@@ -411,6 +412,14 @@ int bem_plan_diagonal(const bem_plan *P, double *c) {
 int bem_plan_footprint(const bem_plan *P, size_t *hbm_bytes) {
     if (!P || !hbm_bytes) { set_error("bem_plan_footprint: NULL argument"); return BEM_EINVAL; }
     *hbm_bytes = P->arena.bytes;
+    return BEM_OK;
+}
+
+int bem_plan_device_status(const bem_plan *P, int *status) {
+    if (!P || !status) { set_error("bem_plan_device_status: NULL argument"); return BEM_EINVAL; }
+    BEM_CUDA(cudaSetDevice(P->device));
+    BEM_CUDA(cudaDeviceSynchronize());
+    BEM_CUDA(cudaMemcpy(status, P->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
     return BEM_OK;
 }
 

@@ -84,6 +84,15 @@ struct MIndex {
     void init(int p_);
 };
 
+// Degree bands of the tensor-core M2L class matrix (m2l_tc.cu): band q holds
+// rows b0[q] .. b0[q] + n[q] - 1 (n a multiple of 16) with K extent k[q] (a
+// multiple of 8), stored from float offset off[q] of the matrix in shared memory.
+constexpr int TC_MAXG = 16;
+struct TcGroups {
+    int ng = 0, tsize = 0, ncols = 0;
+    int b0[TC_MAXG], n[TC_MAXG], k[TC_MAXG], off[TC_MAXG];
+};
+
 // Tree and plan state (everything device-resident unless named h_*).
 struct Tree {
     int nlev = 0;                       // number of levels (root = level 0)
@@ -196,6 +205,24 @@ struct bem_plan {
     int *cm_order = nullptr, *cm_tile_cls = nullptr, *cm_tile_start = nullptr, *cm_tile_cnt = nullptr;
     int *cm_ur0 = nullptr, *cm_ua0 = nullptr, *cm_rtp = nullptr, *cm_gidx = nullptr;
     float *cm_Lp = nullptr;             // [interaction pair][np] per-pair local contributions
+    // symmetry-reduced tensor-core M2L (m2l_tc.cu)
+    int sy_ncls = 0, sy_ntile = 0, sy_on = 0, sy_ldp = 0, sy_nkc = 0;
+    double *sy_rho = nullptr;           // [class][3] canonical offsets / h_t
+    int *sy_dl = nullptr;               // [class] level difference
+    int *sy_tile_cls = nullptr, *sy_tile_start = nullptr, *sy_tile_cnt = nullptr;
+    int *sy_src = nullptr, *sy_sig = nullptr, *sy_pair = nullptr;   // pairs in class order
+    int *sy_sig_u = nullptr;            // [pair] symmetry id (permutation * 8 + sign bits)
+    double *sy_D = nullptr;             // [class][np] derivative tables
+    float *sy_fD = nullptr;
+    unsigned short *sy_fwd = nullptr;   // [48][np] signed index maps (sign in bit 15)
+    int *sy_inv = nullptr;              // [48][np] signed index maps (sign in bit 31)
+    int *sy_tidx = nullptr;             // class-matrix gather table (shared-memory layout)
+    float *sy_tfac = nullptr;
+    float *sy_Lp = nullptr;             // [pair][sy_ldp] canonical-frame local contributions
+    uint4 *sy_sched = nullptr;          // MMA schedule of a tile
+    int *sy_sched_ptr = nullptr, sy_nsched = 0;
+    bem::TcGroups sy_g;
+    int *dev_err = nullptr;             // device word: set when a kernel's bounded wait gave up
     // counters
     double setup_ms[BEM_NSETUP] = {};
     int64_t near_pairs = 0;
@@ -223,6 +250,14 @@ int build_m2l_classes(bem_plan *P);
 int build_translation_tables(bem_plan *P, cudaStream_t s);
 void free_translation_tables(bem_plan *P);
 void set_translation_attributes();
+int build_m2l_sym(bem_plan *P, const std::vector<int> &pair_cls, const std::vector<long long> &kvec,
+                  const std::vector<int> &dls, const std::vector<int> &src);
+int build_tc_tables(bem_plan *P, cudaStream_t s);
+void free_tc_tables(bem_plan *P);
+int launch_m2l_tc(bem_plan *P, const float *M, float *L, cudaStream_t s);
+void set_tc_attributes();
+int launch_m2l_derivs(bem_plan *P, int ncls, const double *rho, const double *kh, double *D, float *fD,
+                      cudaStream_t s);
 template <class R, int C>
 int launch_translations(bem_plan *P, R *M, R *L, cudaStream_t s, cudaEvent_t *ev);
 int enqueue_matvec(bem_plan *P, int op, int green, double k, cudaStream_t s);

@@ -432,6 +432,7 @@ int build_m2l_classes(bem_plan *P) {
     std::vector<int> pair_cls(std::max<int64_t>(1, t.n_inter));
     std::vector<double> rho, kh;
     std::vector<int> dls;
+    std::vector<long long> kvec;        // integer offset vector of every class
     for (int b = 0; b < t.nbox; b++)
         for (int u = ip[b]; u < ip[b + 1]; u++) {
             const int s = ii[u], dl = lev[b] - lev[s], e = std::max(0, -dl);
@@ -452,6 +453,9 @@ int build_m2l_classes(bem_plan *P) {
                 rho.push_back(kz * sc);
                 kh.push_back(helm ? P->k * std::ldexp(t.side, -lev[b]) : 0.0);
                 dls.push_back(dl);
+                kvec.push_back(kx);
+                kvec.push_back(ky);
+                kvec.push_back(kz);
             } else {
                 c = it->second;
             }
@@ -496,6 +500,18 @@ int build_m2l_classes(bem_plan *P) {
         BEM_CUDA(cudaMemcpy(P->cls_kh, kh.data(), sizeof(double) * kh.size(), cudaMemcpyHostToDevice));
         BEM_CUDA(cudaMemcpy(P->cls_dl, dls.data(), sizeof(int) * dls.size(), cudaMemcpyHostToDevice));
     }
+    return build_m2l_sym(P, pair_cls, kvec, dls, ii);
+}
+
+// derivative tables of ncls offset classes (rho: [class][3]; kh: [class], Helmholtz only)
+int launch_m2l_derivs(bem_plan *P, int ncls, const double *rho, const double *kh, double *D, float *fD,
+                      cudaStream_t s) {
+    if (ncls <= 0) return BEM_OK;
+    const int p = P->mi.p, np = P->mi.np, C = P->green == BEM_HELMHOLTZ ? 2 : 1;
+    const size_t sm = sizeof(double) * (2 * (p + 2) + 4 * (size_t)np) + 64;
+    (k_m2l_tables<<<ncls, TT, sm, s>>>(ncls, p, np, C, P->d_m, P->d_n, P->d_k, P->d_idx3, rho, kh, D, fD),
+     ::bem::count_launch());
+    BEM_LAUNCH_CHECK();
     return BEM_OK;
 }
 
@@ -571,6 +587,9 @@ int build_translation_tables(bem_plan *P, cudaStream_t s) {
     BEM_TRY(up(&P->sh_l2l_coef, lcoef)); BEM_TRY(up(&P->sh_l2l_par, lpar));
     BEM_TRY(up(&P->ctr_ptr, cptr)); BEM_TRY(up(&P->ctr_ag, cag)); BEM_TRY(up(&P->ctr_beta, beta_of));
     BEM_TRY(up(&P->m_deg, deg)); BEM_TRY(up(&P->m_sgnf, sgnf)); BEM_TRY(up(&P->m_invf, invf));
+    // the tensor-core form (mixed-precision Laplace) replaces the per-class tables
+    BEM_TRY(build_tc_tables(P, s));
+    if (P->sy_on) return BEM_OK;
     // derivative tables of every offset class
     const int C = P->green == BEM_HELMHOLTZ ? 2 : 1;
     // units of the float32 class-major M2L (real kernels, one unit per thread)
@@ -607,16 +626,11 @@ int build_translation_tables(bem_plan *P, cudaStream_t s) {
     const int nc = std::max(1, P->m2l_ncls);
     BEM_TRY(A.alloc(&P->m2l_D, (size_t)nc * np * C));
     if (P->prm.precision == BEM_MIXED) BEM_TRY(A.alloc(&P->m2l_fD, (size_t)nc * np * C));
-    if (P->m2l_ncls) {
-        const size_t sm = sizeof(double) * (2 * (p + 2) + 4 * (size_t)np) + 64;
-        (k_m2l_tables<<<P->m2l_ncls, TT, sm, s>>>(P->m2l_ncls, p, np, C, P->d_m, P->d_n, P->d_k, P->d_idx3,
-                                                  P->cls_rho, P->cls_kh, P->m2l_D, P->m2l_fD), ::bem::count_launch());
-        BEM_LAUNCH_CHECK();
-    }
-    return BEM_OK;
+    return launch_m2l_derivs(P, P->m2l_ncls, P->cls_rho, P->cls_kh, P->m2l_D, P->m2l_fD, s);
 }
 
 void free_translation_tables(bem_plan *P) {
+    free_tc_tables(P);
     Arena &A = P->arena;
     for (void *q : {(void *)P->sh_m2m_ptr, (void *)P->sh_m2m_src, (void *)P->sh_m2m_coef, (void *)P->sh_m2m_par,
                     (void *)P->sh_l2l_ptr, (void *)P->sh_l2l_src, (void *)P->sh_l2l_coef, (void *)P->sh_l2l_par,
@@ -652,7 +666,9 @@ int launch_translations(bem_plan *P, R *M, R *L, cudaStream_t s, cudaEvent_t *ev
     BEM_LAUNCH_CHECK();
     if (ev) BEM_CUDA(cudaEventRecord(ev[3], s));
     const R *D = sizeof(R) == sizeof(double) ? (const R *)P->m2l_D : (const R *)P->m2l_fD;
-    if (std::is_same<R, float>::value && C == 1 && P->cm_nunits > 0) {
+    if (std::is_same<R, float>::value && C == 1 && P->sy_on) {
+        BEM_TRY(launch_m2l_tc(P, (const float *)M, (float *)L, s));
+    } else if (std::is_same<R, float>::value && C == 1 && P->cm_nunits > 0) {
         const size_t npad = ((size_t)np + CM_UA - 1) / CM_UA * CM_UA, nu = P->cm_nunits, NE = nu * CM_UR * CM_UA;
         const size_t nrt = ((size_t)np + CM_UR - 1) / CM_UR;
         const size_t sm = sizeof(int) * (NE + 2 * nu + nrt + 1 + CM_N + npad) +
@@ -702,6 +718,7 @@ void set_translation_attributes() {
     cudaFuncSetAttribute(k_m2l_tab<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_m2l_tables, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_m2l_cm, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    set_tc_attributes();
 }
 
 template int launch_translations<double, 1>(bem_plan *, double *, double *, cudaStream_t, cudaEvent_t *);

@@ -36,6 +36,7 @@ def test_mixed_matvec_and_solve(oracle_lib, name):
         xs = I.random_vector(P.n_chi, 2)
         ea = rel_l2(P.matvec(bem.BEM_OP_A, x), A @ x)
         eb = rel_l2(P.matvec(bem.BEM_OP_B, xs), B @ xs)
+        print(f"mixed {name}: product errors A {ea:.3e} B {eb:.3e}")
         assert ea <= MX_MATVEC_TOL and eb <= MX_MATVEC_TOL, (ea, eb)
         _, chi_e = I.point_source(m, src)
         chi = oracle_lib.chi_from_elem(P.chi_idx, P.n_chi, chi_e)
@@ -43,6 +44,7 @@ def test_mixed_matvec_and_solve(oracle_lib, name):
         phi, code, info = P.solve(chi, tol=1e-10)
         assert code == bem.BEM_OK
         assert rel_l2(phi, ref) <= MX_SOLVE_TOL, (rel_l2(phi, ref), info.rel_residual, info.iters)
+        assert bem.bem_plan_device_status(P.plan) == 0
     finally:
         P.close()
 

@@ -112,3 +112,29 @@ def test_m2l_converges_to_direct_sum(oracle_lib, green, k):
     for a, b in zip(errs, errs[1:]):
         assert b < a / 2.5
     assert errs[-1] < 1e-5
+
+
+@pytest.mark.parametrize("green,k", [(0, 0.0), (1, 2.0)])
+def test_derivative_symmetry_under_signed_axis_permutations(oracle_lib, green, k):
+    """The Green's functions are radial, so for r_i = s_i rhat_pi(i) the
+    derivative tensors obey D_mu(r) = prod_i s_i^mu_i D_{mu o pi^-1}(rhat):
+    the identity that lets interaction pairs share the translation matrix of
+    a canonical offset (|components| sorted in decreasing order)."""
+    import itertools
+    O = oracle_lib
+    p = 7
+    mi = O.mindex(p)
+    where = {tuple(v): i for i, v in enumerate(mi.tolist())}
+    rng = np.random.default_rng(5)
+    for _ in range(3):
+        rhat = np.sort(np.abs(rng.uniform(1.0, 3.0, 3)))[::-1]
+        Dc = O.green_derivs(p, rhat, green, k)
+        for pi in itertools.permutations(range(3)):
+            pinv = [pi.index(j) for j in range(3)]
+            for s in itertools.product((1, -1), repeat=3):
+                r = np.array([s[i] * rhat[pi[i]] for i in range(3)])
+                D = O.green_derivs(p, r, green, k)
+                for a, mu in enumerate(mi.tolist()):
+                    g = tuple(mu[pinv[j]] for j in range(3))
+                    sign = np.prod([s[i] ** mu[i] for i in range(3)])
+                    assert abs(D[a] - sign * Dc[where[g]]) <= 1e-12 * (abs(D[a]) + 1e-300) + 1e-300
