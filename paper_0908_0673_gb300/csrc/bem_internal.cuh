@@ -191,9 +191,6 @@ struct bem_plan {
     long long graph_kernels[2] = {0, 0};
     cudaStream_t capture_stream = nullptr;
     // translation tables (translate.cu)
-    int *sh_m2m_ptr = nullptr, *sh_m2m_src = nullptr, *sh_l2l_ptr = nullptr, *sh_l2l_src = nullptr;
-    double *sh_m2m_coef = nullptr, *sh_l2l_coef = nullptr;
-    unsigned char *sh_m2m_par = nullptr, *sh_l2l_par = nullptr;
     int *ctr_ptr = nullptr, *ctr_ag = nullptr, *ctr_beta = nullptr, *m_deg = nullptr;
     double *m_sgnf = nullptr, *m_invf = nullptr;
     int *m2l_cls = nullptr, *cls_dl = nullptr, m2l_ncls = 0;

@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(P2M_T) k_p2m(int nleaf, Tabs tb, TreeView tv, 
     if (li >= nleaf) return;
     const int b = tv.leaves[li];
     const int p = tb.p, np = tb.np, tid = threadIdx.x;
-    __shared__ R pw[3][PMAX + 1][P2M_B];
+    __shared__ R pw[3][P2M_B][PMAX + 1];             // [axis][point][power]: lanes with distinct powers hit distinct banks
     __shared__ R sf[P2M_B][C];
     __shared__ R sn[3][P2M_B];
     const double h = scalbn(tv.side, -tv.level[b]);
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(P2M_T) k_p2m(int nleaf, Tabs tb, TreeView tv, 
             }
             R v = (R)1;
             for (int e = 0; e <= p; e++) {
-                pw[ax][e][pt] = v;
+                pw[ax][pt][e] = v;
                 v *= d;
             }
         } else if (tid < 3 * P2M_B + P2M_B) {
@@ -154,12 +154,12 @@ __global__ void __launch_bounds__(P2M_T) k_p2m(int nleaf, Tabs tb, TreeView tv, 
                 const int m = am[s], n = an[s], k = ak[s];
                 R val;
                 if (!DL) {
-                    val = pw[0][m][pt] * pw[1][n][pt] * pw[2][k][pt];
+                    val = pw[0][pt][m] * pw[1][pt][n] * pw[2][pt][k];
                 } else {
                     val = (R)0;
-                    if (m) val += (R)m * sn[0][pt] * pw[0][m - 1][pt] * pw[1][n][pt] * pw[2][k][pt];
-                    if (n) val += (R)n * sn[1][pt] * pw[0][m][pt] * pw[1][n - 1][pt] * pw[2][k][pt];
-                    if (k) val += (R)k * sn[2][pt] * pw[0][m][pt] * pw[1][n][pt] * pw[2][k - 1][pt];
+                    if (m) val += (R)m * sn[0][pt] * pw[0][pt][m - 1] * pw[1][pt][n] * pw[2][pt][k];
+                    if (n) val += (R)n * sn[1][pt] * pw[0][pt][m] * pw[1][pt][n - 1] * pw[2][pt][k];
+                    if (k) val += (R)k * sn[2][pt] * pw[0][pt][m] * pw[1][pt][n] * pw[2][pt][k - 1];
                     val *= hinv;
                 }
 #pragma unroll
@@ -311,13 +311,18 @@ __global__ void __launch_bounds__(NF_T) k_near(int nleaf, Tabs tb, TreeView tv, 
 
 
 // ---------------------------------------------------------------------------
-// near field + L2P, float32 form: 8 target groups x 32 source slices per
-// block (leaves hold ~20-60 vertices), 4 targets per thread so that every source read from shared memory
-// serves 4 pairs.  The near-list sources are packed into full tiles across
-// box boundaries; each staged source is rebased to the target leaf's centre
-// (box offset in float64, rounded once), tile partial sums go to float64.
+// near field + L2P, float32 form.  A block takes one leaf and up to SLOTS of
+// its targets per pass: G = ceil(targets / U) target groups x (256 / G)
+// source slices, each thread holding U targets (8 real, 4 complex) so that
+// every source read from shared memory serves U pairs.  The near-list
+// sources are packed into full tiles across box boundaries; each staged
+// source is rebased to the target leaf's centre (box offset in float64,
+// rounded once).  For the real double layer the strength is folded into the
+// staged normal, so a pair costs 3 subtractions, two 3-term dot products, one
+// reciprocal square root and three multiplies.  Tile partial sums are added
+// with compensation, slices and the local expansion combine in float64.
 // ---------------------------------------------------------------------------
-constexpr int NF2_T = 256, NF2_G = 8, NF2_S = 32, NF2_U = 4, NF2_TILE = 256, NF2_ENT = 256;
+constexpr int NF2_T = 256, NF2_TILE = 1024, NF2_ENT = 256;
 
 template <int C, bool DL>
 __device__ __forceinline__ void pair_f32(float rx, float ry, float rz, const float4 &sa, const float4 &sb, float kw,
@@ -325,9 +330,9 @@ __device__ __forceinline__ void pair_f32(float rx, float ry, float rz, const flo
     const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
     const float inv = rsqrtf(r2);
     if (C == 1) {
-        if (DL) {
+        if (DL) {   // sb = strength * normal
             const float dot = fmaf(rx, sb.x, fmaf(ry, sb.y, rz * sb.z));
-            acc[0] = fmaf(sa.w * dot, inv * inv * inv, acc[0]);
+            acc[0] = fmaf(dot * inv, inv * inv, acc[0]);
         } else {
             acc[0] = fmaf(sa.w, inv, acc[0]);
         }
@@ -365,47 +370,67 @@ template <int C, bool DL>
 __global__ void __launch_bounds__(NF2_T) k_near_f32(int nleaf, Tabs tb, TreeView tv, QuadView qv, double kwave,
                                                     const float *__restrict__ f, const float *__restrict__ L,
                                                     double *__restrict__ ytmp, const int *__restrict__ skip) {
+    constexpr int U = C == 1 ? 8 : 4;                 // targets per thread
+    constexpr int SLOTS = 8 * U;                      // targets per pass (at most 8 groups)
+    constexpr int LP = NF2_T / SLOTS;                 // threads per target in the local expansion
     if (skip && *skip) return;
     const int li = blockIdx.x;
     if (li >= nleaf) return;
     const int b = tv.leaves[li];
-    const int tid = threadIdx.x, tg = tid % NF2_G, sl = tid / NF2_G;
-    __shared__ float4 sa[NF2_TILE], sb[NF2_TILE];
+    const int tid = threadIdx.x, lane = tid & 31;
+    extern __shared__ float4 near_tile[];             // [2][NF2_TILE] staged sources
+    float4 *sa = near_tile, *sb = near_tile + NF2_TILE;
     __shared__ int pref[NF2_ENT + 1];
-    __shared__ float red[NF2_S][NF2_G * NF2_U][C];
-    __shared__ float lred[NF2_T / (NF2_G * NF2_U)][NF2_G * NF2_U][C];
+    __shared__ float red[NF2_T * U * C];              // [slice][slot] partial sums
+    __shared__ float lred[NF2_T * C];                 // [part][slot] local-expansion partial sums
+    __shared__ float spow[SLOTS][3][PMAX + 1];        // powers of the targets' scaled offsets
     const double cbx = tv.cx[b], cby = tv.cy[b], cbz = tv.cz[b];
     const float kw = (float)kwave;
     const int p = tb.p, np = tb.np;
-    for (int t0 = tv.nb[b]; t0 < tv.ne[b]; t0 += NF2_G * NF2_U) {
-        float tx[NF2_U], ty[NF2_U], tz[NF2_U];
+    const int tb0 = tv.nb[b], te0 = tv.ne[b];
+    for (int t0 = tb0; t0 < te0; t0 += SLOTS) {
+        const int nt = min(SLOTS, te0 - t0);
+        const int G = (nt + U - 1) / U, S = NF2_T / G, tg = tid % G, sl = tid / G;
+        const bool worker = sl < S;
+        float tx[U], ty[U], tz[U];
 #pragma unroll
-        for (int u = 0; u < NF2_U; u++) {
-            const int k = t0 + tg + NF2_G * u;
-            const bool on = k < tv.ne[b];
+        for (int u = 0; u < U; u++) {
+            const int k = t0 + tg + G * u;
+            const bool on = k < te0;
             tx[u] = on ? (float)(tv.tx[k] - cbx) : 0.f;
             ty[u] = on ? (float)(tv.ty[k] - cby) : 0.f;
-            tz[u] = on ? (float)(tv.tz[k] - cbz) : 0.f;
+            tz[u] = on ? (float)(tv.tz[k] - cbz) : 1.f;
         }
-        KahanF acc[NF2_U][C];
+        KahanF acc[U][C];
         for (int e0 = tv.near_ptr[b]; e0 < tv.near_ptr[b + 1]; e0 += NF2_ENT) {
             const int ne_ = min(NF2_ENT, tv.near_ptr[b + 1] - e0);
             __syncthreads();
-            if (tid == 0) {
-                int run = 0;
-                for (int i = 0; i < ne_; i++) {
-                    pref[i] = run;
-                    const int s = tv.near_idx[e0 + i];
-                    run += (tv.ee[s] - tv.eb[s]) * NQ;
+            if (tid < 32) {                           // quadrature-point offsets of the entries (warp scan)
+                int carry = 0;
+                for (int i0 = 0; i0 < ne_; i0 += 32) {
+                    const int i = i0 + lane;
+                    int x = 0;
+                    if (i < ne_) {
+                        const int s = tv.near_idx[e0 + i];
+                        x = (tv.ee[s] - tv.eb[s]) * NQ;
+                    }
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(0xffffffffu, x, o);
+                        if (lane >= o) x += y;
+                    }
+                    if (i < ne_) pref[i + 1] = carry + x;
+                    carry += __shfl_sync(0xffffffffu, x, 31);
                 }
-                pref[ne_] = run;
+                if (lane == 0) pref[0] = 0;
             }
             __syncthreads();
             const int total = pref[ne_];
             for (int base = 0; base < total; base += NF2_TILE) {
                 __syncthreads();
-                const int j = base + tid;
-                if (j < total) {
+                for (int jj = tid; jj < NF2_TILE; jj += NF2_T) {
+                    const int j = base + jj;
+                    if (j >= total) break;
                     int lo = 0, hi = ne_ - 1;          // entry holding j: pref[lo] <= j < pref[lo + 1]
                     while (lo < hi) {
                         const int mid = (lo + hi + 1) >> 1;
@@ -414,77 +439,90 @@ __global__ void __launch_bounds__(NF2_T) k_near_f32(int nleaf, Tabs tb, TreeView
                     const int s = tv.near_idx[e0 + lo];
                     const int o = tv.eb[s] * NQ + (j - pref[lo]);
                     const float dx = (float)(tv.cx[s] - cbx), dy = (float)(tv.cy[s] - cby), dz = (float)(tv.cz[s] - cbz);
-                    sa[tid] = make_float4(dx + qv.fx[o], dy + qv.fy[o], dz + qv.fz[o], f[(size_t)o * C]);
-                    sb[tid] = make_float4(DL ? qv.fnx[o] : 0.f, DL ? qv.fny[o] : 0.f, DL ? qv.fnz[o] : 0.f,
-                                          C == 2 ? f[(size_t)o * C + C - 1] : 0.f);
+                    const float4 xa = make_float4(dx + qv.fx[o], dy + qv.fy[o], dz + qv.fz[o], 0.f);
+                    if (C == 1 && DL) {
+                        const float fo = f[o];
+                        sa[jj] = xa;
+                        sb[jj] = make_float4(fo * qv.fnx[o], fo * qv.fny[o], fo * qv.fnz[o], 0.f);
+                    } else {
+                        sa[jj] = make_float4(xa.x, xa.y, xa.z, f[(size_t)o * C]);
+                        sb[jj] = make_float4(DL ? qv.fnx[o] : 0.f, DL ? qv.fny[o] : 0.f, DL ? qv.fnz[o] : 0.f,
+                                             C == 2 ? f[(size_t)o * C + C - 1] : 0.f);
+                    }
                 }
                 __syncthreads();
-                const int nt = min(NF2_TILE, total - base);
-                float part[NF2_U][C];
+                const int nq = min(NF2_TILE, total - base);
+                float part[U][C];
 #pragma unroll
-                for (int u = 0; u < NF2_U; u++)
+                for (int u = 0; u < U; u++)
 #pragma unroll
                     for (int c = 0; c < C; c++) part[u][c] = 0.f;
-                for (int q = sl; q < nt; q += NF2_S) {
-                    const float4 A = sa[q], Bv = sb[q];
+                if (worker)
+                    for (int q = sl; q < nq; q += S) {
+                        const float4 A = sa[q], Bv = sb[q];
 #pragma unroll
-                    for (int u = 0; u < NF2_U; u++) pair_f32<C, DL>(tx[u] - A.x, ty[u] - A.y, tz[u] - A.z, A, Bv, kw, part[u]);
-                }
+                        for (int u = 0; u < U; u++)
+                            pair_f32<C, DL>(tx[u] - A.x, ty[u] - A.y, tz[u] - A.z, A, Bv, kw, part[u]);
+                    }
 #pragma unroll
-                for (int u = 0; u < NF2_U; u++)
+                for (int u = 0; u < U; u++)
 #pragma unroll
                     for (int c = 0; c < C; c++) acc[u][c].add(part[u][c]);
             }
         }
         __syncthreads();
+        if (worker)
 #pragma unroll
-        for (int u = 0; u < NF2_U; u++)
+            for (int u = 0; u < U; u++)
 #pragma unroll
-            for (int c = 0; c < C; c++) red[sl][tg + NF2_G * u][c] = acc[u][c].s;
-        // local expansion at the targets: every thread takes a slice of the terms
+                for (int c = 0; c < C; c++) red[((size_t)sl * G * U + tg + G * u) * C + c] = acc[u][c].s;
+        // local expansion at the targets: powers of the scaled offsets, then
+        // LP threads per target each take every LP-th term
+        const double h = scalbn(tv.side, -tv.level[b]);
+        if (tid < nt) {
+            const int k = t0 + tid;
+            const float dx = (float)((tv.tx[k] - cbx) / h), dy = (float)((tv.ty[k] - cby) / h),
+                        dz = (float)((tv.tz[k] - cbz) / h);
+            float qx = 1.f, qy = 1.f, qz = 1.f;
+            for (int e = 0; e <= p; e++) {
+                spow[tid][0][e] = qx;
+                spow[tid][1][e] = qy;
+                spow[tid][2][e] = qz;
+                qx *= dx;
+                qy *= dy;
+                qz *= dz;
+            }
+        }
+        __syncthreads();
         {
-            const int nslot = NF2_G * NF2_U, tslot = tid % nslot, part_id = tid / nslot;
-            const int nparts = NF2_T / nslot;
-            const int k = t0 + tslot;
+            const int slot = tid % SLOTS, part_id = tid / SLOTS;
             KahanF loc[C];
-            if (k < tv.ne[b]) {
-                const double h = scalbn(tv.side, -tv.level[b]);
-                const float dx = (float)((tv.tx[k] - cbx) / h), dy = (float)((tv.ty[k] - cby) / h),
-                            dz = (float)((tv.tz[k] - cbz) / h);
-                float px[PMAX + 1], py[PMAX + 1], pz[PMAX + 1];
-                px[0] = py[0] = pz[0] = 1.f;
-                for (int e = 1; e <= p; e++) {
-                    px[e] = px[e - 1] * dx;
-                    py[e] = py[e - 1] * dy;
-                    pz[e] = pz[e - 1] * dz;
-                }
-                for (int a = part_id; a < np; a += nparts) {
-                    const float mono = px[tb.m[a]] * py[tb.n[a]] * pz[tb.k[a]];
+            if (slot < nt)
+                for (int a = part_id; a < np; a += LP) {
+                    const float mono = spow[slot][0][tb.m[a]] * spow[slot][1][tb.n[a]] * spow[slot][2][tb.k[a]];
 #pragma unroll
                     for (int c = 0; c < C; c++) loc[c].add(mono * L[((size_t)b * np + a) * C + c]);
                 }
-            }
 #pragma unroll
-            for (int c = 0; c < C; c++) lred[part_id][tslot][c] = loc[c].s;
+            for (int c = 0; c < C; c++) lred[(part_id * SLOTS + slot) * C + c] = loc[c].s;
         }
         __syncthreads();
-        if (tid < NF2_G * NF2_U) {
-            const int k = t0 + tid;          // target slot tid = tg + G u
-            if (k < tv.ne[b]) {
-                double sum[C], loc[C];
+        if (tid < nt) {
+            // target t0 + tid sits in slot tid = tg + G u of every slice
+            double sum[C], loc[C];
 #pragma unroll
-                for (int c = 0; c < C; c++) sum[c] = loc[c] = 0.0;
-                for (int q = 0; q < NF2_S; q++)
+            for (int c = 0; c < C; c++) sum[c] = loc[c] = 0.0;
+            for (int q = 0; q < S; q++)
 #pragma unroll
-                    for (int c = 0; c < C; c++) sum[c] += (double)red[q][tid][c];
-                for (int q = 0; q < NF2_T / (NF2_G * NF2_U); q++)
+                for (int c = 0; c < C; c++) sum[c] += (double)red[((size_t)q * G * U + tid) * C + c];
+            for (int q = 0; q < LP; q++)
 #pragma unroll
-                    for (int c = 0; c < C; c++) loc[c] += (double)lred[q][tid][c];
-                const int node = tv.node_perm[k];
+                for (int c = 0; c < C; c++) loc[c] += (double)lred[(q * SLOTS + tid) * C + c];
+            const int node = tv.node_perm[t0 + tid];
 #pragma unroll
-                for (int c = 0; c < C; c++) ytmp[(size_t)node * C + c] = sum[c] * (0.25 / M_PI) + loc[c];
-            }
+            for (int c = 0; c < C; c++) ytmp[(size_t)node * C + c] = sum[c] * (0.25 / M_PI) + loc[c];
         }
+        __syncthreads();
     }
 }
 
@@ -604,6 +642,16 @@ static int init_shape_table(int device) {
     return BEM_OK;
 }
 
+// the float32 near-field kernels stage their source tile in dynamic shared
+// memory above the 48 KB default (set outside any graph capture)
+static void set_near_attributes() {
+    const int big = 100 * 1024;
+    cudaFuncSetAttribute(k_near_f32<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_near_f32<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_near_f32<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_near_f32<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+}
+
 int alloc_fmm(bem_plan *P, cudaStream_t s) {
     Arena &A = P->arena;
     MIndex &mi = P->mi;
@@ -641,6 +689,7 @@ int alloc_fmm(bem_plan *P, cudaStream_t s) {
     BEM_TRY(A.alloc(&P->xptr, 2));
     BEM_TRY(A.alloc(&P->yptr, 2));
     set_translation_attributes();
+    set_near_attributes();
     BEM_TRY(build_translation_tables(P, s));
     BEM_LAUNCH_CHECK();
     return BEM_OK;
@@ -667,8 +716,9 @@ static int run_fmm(bem_plan *P, int op, double kwave, R *f, R *M, R *L, cudaStre
     if (ev) BEM_CUDA(cudaEventRecord(ev[2], s));
     BEM_TRY((launch_translations<R, C>(P, M, L, s, ev)));
     if constexpr (sizeof(R) == sizeof(float)) {
-        if (op == BEM_OP_A) (k_near_f32<C, true><<<t.nleaf, NF2_T, 0, s>>>(t.nleaf, tb, tv, qv, kwave, f, L, P->ytmp, sk), ::bem::count_launch());
-        else (k_near_f32<C, false><<<t.nleaf, NF2_T, 0, s>>>(t.nleaf, tb, tv, qv, kwave, f, L, P->ytmp, sk), ::bem::count_launch());
+        constexpr size_t tile_sm = 2 * NF2_TILE * sizeof(float4);
+        if (op == BEM_OP_A) (k_near_f32<C, true><<<t.nleaf, NF2_T, tile_sm, s>>>(t.nleaf, tb, tv, qv, kwave, f, L, P->ytmp, sk), ::bem::count_launch());
+        else (k_near_f32<C, false><<<t.nleaf, NF2_T, tile_sm, s>>>(t.nleaf, tb, tv, qv, kwave, f, L, P->ytmp, sk), ::bem::count_launch());
     } else {
         if (op == BEM_OP_A) (k_near<R, C, true><<<t.nleaf, NF_T, 0, s>>>(t.nleaf, tb, tv, qv, kwave, f, L, P->ytmp, sk), ::bem::count_launch());
         else (k_near<R, C, false><<<t.nleaf, NF_T, 0, s>>>(t.nleaf, tb, tv, qv, kwave, f, L, P->ytmp, sk), ::bem::count_launch());

@@ -240,12 +240,27 @@ __global__ void __launch_bounds__(TC_T, 1) k_m2l_tc(const __grid_constant__ TcAr
                 if (k > 0 && !__all_sync(0xffffffffu, wait_or_abort(tfull, (uint32_t)((k - 1) & 1), sAbort))) break;
                 const int dl = a.dl[cls];
                 const float *Dc = a.fD + (size_t)cls * np;
-                for (int e = pt; e < G.tsize; e += 384) {
-                    const int gi = __ldg(a.tidx + e);
-                    const float v = gi >= 0 ? ldexpf(__ldg(Dc + (gi & 0xffff)) * __ldg(a.tfac + e), dl * (gi >> 16)) : 0.f;
-                    const float hi = tc::to_tf32(v);
-                    sTh[e] = hi;
-                    sTl[e] = tc::to_tf32(v - hi);
+                for (int e0 = pt; e0 < G.tsize; e0 += 4 * 384) {
+                    int gi[4];
+                    float fc[4], dv[4];
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        const int e = e0 + q * 384;
+                        gi[q] = e < G.tsize ? __ldg(a.tidx + e) : -1;
+                        fc[q] = e < G.tsize ? __ldg(a.tfac + e) : 0.f;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; q++) dv[q] = gi[q] >= 0 ? __ldg(Dc + (gi[q] & 0xffff)) : 0.f;
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        const int e = e0 + q * 384;
+                        if (e < G.tsize) {
+                            const float v = gi[q] >= 0 ? ldexpf(dv[q] * fc[q], dl * (gi[q] >> 16)) : 0.f;
+                            const float hi = tc::to_tf32(v);
+                            sTh[e] = hi;
+                            sTl[e] = tc::to_tf32(v - hi);
+                        }
+                    }
                 }
                 prev_cls = cls;
             }
@@ -305,25 +320,45 @@ __global__ void __launch_bounds__(TC_T, 1) k_m2l_tc(const __grid_constant__ TcAr
 }
 
 // L_t[b] = (1 / h_t) sum over t's interaction list, in list order, of
-// sign * Lhat_u[b o pi_u^-1]
-__global__ void k_m2l_gather_sym(int nbox, const int *__restrict__ level, double side,
-                                 const int *__restrict__ inter_ptr, int np, int ldp, const int *__restrict__ sig_u,
-                                 const int *__restrict__ inv, const float *__restrict__ Lp, float *__restrict__ L,
-                                 const int *__restrict__ skip) {
+// sign * Lhat_u[b o pi_u^-1]; one thread per row b, eight rows of Lhat in flight
+constexpr int GA_LIST = 512;            // list entries staged per pass
+__global__ void __launch_bounds__(512) k_m2l_gather_sym(int nbox, const int *__restrict__ level, double side,
+                                                        const int *__restrict__ inter_ptr, int np, int ldp,
+                                                        const int *__restrict__ sig_u, const int *__restrict__ inv,
+                                                        const float *__restrict__ Lp, float *__restrict__ L,
+                                                        const int *__restrict__ skip) {
     if (skip && *skip) return;
-    const int t = blockIdx.x;
+    __shared__ int sOff[GA_LIST];          // sig * np of every staged pair
+    const int t = blockIdx.x, b = threadIdx.x;
     if (t >= nbox) return;
     const float sc = (float)(1.0 / scalbn(side, -level[t]));
     const int u0 = inter_ptr[t], u1 = inter_ptr[t + 1];
-    for (int b = threadIdx.x; b < np; b += blockDim.x) {
-        float sum = 0.f;
-        for (int u = u0; u < u1; u++) {
-            const int f = __ldg(inv + (size_t)sig_u[u] * np + b);
-            const float v = Lp[(size_t)u * ldp + (f & 0x7fffffff)];
-            sum += f < 0 ? -v : v;
+    float sum = 0.f;
+    for (int base = u0; base < u1; base += GA_LIST) {
+        const int n = min(GA_LIST, u1 - base);
+        __syncthreads();
+        for (int i = b; i < n; i += blockDim.x) sOff[i] = sig_u[base + i] * np;
+        __syncthreads();
+        if (b < np) {
+            int i = 0;
+            for (; i + 8 <= n; i += 8) {
+                int f[8];
+                float v[8];
+#pragma unroll
+                for (int q = 0; q < 8; q++) f[q] = __ldg(inv + sOff[i + q] + b);
+#pragma unroll
+                for (int q = 0; q < 8; q++) v[q] = Lp[(size_t)(base + i + q) * ldp + (f[q] & 0x7fffffff)];
+#pragma unroll
+                for (int q = 0; q < 8; q++) sum += f[q] < 0 ? -v[q] : v[q];
+            }
+            for (; i < n; i++) {
+                const int f = __ldg(inv + sOff[i] + b);
+                const float v = Lp[(size_t)(base + i) * ldp + (f & 0x7fffffff)];
+                sum += f < 0 ? -v : v;
+            }
         }
-        L[(size_t)t * np + b] = sum * sc;
     }
+    if (b < np) L[(size_t)t * np + b] = sum * sc;
 }
 
 }  // namespace
@@ -592,7 +627,7 @@ int launch_m2l_tc(bem_plan *P, const float *M, float *L, cudaStream_t s) {
     const size_t sm = tc_smem_bytes(a.g, a.ldp);
     const int grid = std::min(P->sy_ntile, std::max(1, P->sm_count));
     if (P->sy_ntile > 0) (k_m2l_tc<<<grid, TC_T, sm, s>>>(a), ::bem::count_launch());
-    (k_m2l_gather_sym<<<t.nbox, 128, 0, s>>>(t.nbox, t.level, t.side, t.inter_ptr, a.np, a.ldp, P->sy_sig_u,
+    (k_m2l_gather_sym<<<t.nbox, a.ldp, 0, s>>>(t.nbox, t.level, t.side, t.inter_ptr, a.np, a.ldp, P->sy_sig_u,
                                              P->sy_inv, P->sy_Lp, L, P->skip),
      ::bem::count_launch());
     BEM_LAUNCH_CHECK();

@@ -1,4 +1,4 @@
-// Translation operators of the fast method with precomputed tables:
+// Translation operators of the fast method:
 //
 //   M2M  coefficient shift (Eq. 8):  Ms'_a = sum_{b<=a} C(a,b) s^b 2^-(|a|+|b|) Ms_{a-b}
 //   L2L  expansion shift (Eq. 9):    Ls'_b += sum_g C(b+g,b) s^g 2^-(2|g|+|b|) Ls_{b+g}
@@ -6,9 +6,8 @@
 //
 // Moments / locals are scaled by the box edge (Ms = I / h^|a|, Ls = F h^|b|),
 // so a child's offset from its parent is +-1/4 of the parent edge per axis and
-// every shift coefficient is a binomial times a power of two; the octant only
-// flips signs.  The coefficient lists (source index, coefficient, parity of
-// the shift exponent per axis) are built once per expansion order.
+// every shift coefficient is a product of per-axis binomials and powers of
+// two; the octant only flips signs.
 //
 // M2L: the derivatives D[g] = d^g Ghat(rho) (Tausch's recursions, Section
 // 3.3) depend only on rho = (c_t - c_s) / h_t, the level difference and, for
@@ -38,77 +37,144 @@ __device__ __forceinline__ void cmac(R *acc, R cf, const R *v) {
 }
 
 // ---------------------------------------------------------------------------
-// M2M for the parents of one level: one block per parent, all children staged
+// Shifts as three one-dimensional passes.  With box-scaled expansions every
+// shift coefficient is a product of per-axis factors,
+//   M2M  M'_a = 2^-|a| sum_{g <= a} prod_i binom(a_i, g_i) 2^-g_i s_i^g_i  M_{a-g},
+//   L2L  L'_b = 2^-|b| sum_{|b|+|g| <= p} prod_i binom(b_i+g_i, b_i) 4^-g_i s_i^g_i  L_{b+g},
+// (s_i = -1 where the child lies on the low side of axis i), so each shift is
+// done axis by axis: an output of one pass sums at most p + 1 terms, and the
+// degree bound |.| <= p carries through the passes unchanged.  Multi-index
+// table and per-axis factors sit in shared memory.  M2M: every child of the
+// parent at once, children then added in a fixed order; L2L: one child per
+// block.  Deterministic.
 // ---------------------------------------------------------------------------
-template <class R, int C>
-__global__ void __launch_bounds__(TT) k_m2m_tab(int off, int cnt, const int *__restrict__ child0,
-                                                const int *__restrict__ nchild, const int *__restrict__ ix,
-                                                const int *__restrict__ iy, const int *__restrict__ iz, int np,
-                                                const int *__restrict__ ptr, const int *__restrict__ src,
-                                                const double *__restrict__ coef, const unsigned char *__restrict__ par,
-                                                R *__restrict__ M, const int *__restrict__ skip) {
-    if (skip && *skip) return;
-    extern __shared__ unsigned char smem_raw[];
-    R *sM = (R *)smem_raw;                       // [8][np][C]
-    __shared__ int smask[8];
-    const int b = off + blockIdx.x;
-    if (blockIdx.x >= cnt) return;
-    const int nch = nchild[b];
-    if (nch == 0) return;
-    const int c0 = child0[b], tid = threadIdx.x;
-    for (int j = 0; j < nch; j++)
-        for (int t = tid; t < np * C; t += TT) sM[j * np * C + t] = M[(size_t)(c0 + j) * np * C + t];
-    if (tid < nch) {
-        const int c = c0 + tid;
-        // a child on the low side of an axis has offset -1/4 of the parent edge
-        smask[tid] = ((ix[c] & 1) ? 0 : 1) | ((iy[c] & 1) ? 0 : 2) | ((iz[c] & 1) ? 0 : 4);
-    }
-    __syncthreads();
-    for (int a = tid; a < np; a += TT) {
-        R acc[C];
-#pragma unroll
-        for (int c = 0; c < C; c++) acc[c] = (R)0;
-        for (int k = ptr[a]; k < ptr[a + 1]; k++) {
-            const R cf = (R)coef[k];
-            const int sidx = src[k], pr = par[k];
-            for (int j = 0; j < nch; j++) {
-                const R sg = (__popc(pr & smask[j]) & 1) ? -cf : cf;
-                cmac<R, C>(acc, sg, sM + (j * np + sidx) * C);
-            }
-        }
-#pragma unroll
-        for (int c = 0; c < C; c++) M[((size_t)b * np + a) * C + c] = acc[c];
+constexpr int MM_T = 512;
+
+template <class R>
+__device__ __forceinline__ void shift_tables(int p, const int *__restrict__ idx3, const double *__restrict__ binom,
+                                             bool m2m, short *sIdx, R *sG) {
+    const int P1 = p + 1;
+    for (int i = threadIdx.x; i < P1 * P1 * P1; i += blockDim.x) sIdx[i] = (short)idx3[i];
+    for (int i = threadIdx.x; i < P1 * P1; i += blockDim.x) {
+        const int a = i / P1, g = i - a * P1;
+        // M2M: binom(a, g) 2^-g (g <= a);  L2L: binom(a + g, a) 4^-g (a + g <= p)
+        double v = 0.0;
+        if (m2m && g <= a) v = ldexp(binom[a * (PMAX + 1) + g], -g);
+        if (!m2m && a + g <= p) v = ldexp(binom[(a + g) * (PMAX + 1) + a], -2 * g);
+        sG[i] = (R)v;
     }
 }
 
-// ---------------------------------------------------------------------------
-// L2L for the boxes of one level: one block per child, parent staged
-// ---------------------------------------------------------------------------
-template <class R, int C>
-__global__ void __launch_bounds__(TT) k_l2l_tab(int off, int cnt, const int *__restrict__ parent,
-                                                const int *__restrict__ ix, const int *__restrict__ iy,
-                                                const int *__restrict__ iz, int np, const int *__restrict__ ptr,
-                                                const int *__restrict__ src, const double *__restrict__ coef,
-                                                const unsigned char *__restrict__ par, R *__restrict__ L,
-                                                const int *__restrict__ skip) {
-    if (skip && *skip) return;
-    extern __shared__ unsigned char smem_raw[];
-    R *sL = (R *)smem_raw;
-    if (blockIdx.x >= cnt) return;
-    const int b = off + blockIdx.x, pa = parent[b], tid = threadIdx.x;
-    for (int t = tid; t < np * C; t += TT) sL[t] = L[(size_t)pa * np * C + t];
-    const int mask = ((ix[b] & 1) ? 0 : 1) | ((iy[b] & 1) ? 0 : 2) | ((iz[b] & 1) ? 0 : 4);
-    __syncthreads();
-    for (int a = tid; a < np; a += TT) {
+// one axis pass over nv vectors: out[v][a] = sum_g G[a_ax][g] s_v^g in[v][a -/+ g e_ax]
+template <class R, int C, bool DOWN>
+__device__ __forceinline__ void shift_pass(int ax, int nv, int p, int np, const int *__restrict__ tm,
+                                           const int *__restrict__ tn, const int *__restrict__ tk, const short *sIdx,
+                                           const R *sG, const int *smask, const R *in, R *out) {
+    const int P1 = p + 1;
+    for (int t = threadIdx.x; t < nv * np; t += blockDim.x) {
+        const int v = t / np, a = t - v * np;
+        int c3[3] = {tm[a], tn[a], tk[a]};
+        const int e = c3[ax], rest = p - (c3[0] + c3[1] + c3[2]);
+        const R sg = (smask[v] >> ax) & 1 ? (R)-1 : (R)1;
+        const R *iv = in + (size_t)v * np * C;
         R acc[C];
 #pragma unroll
         for (int c = 0; c < C; c++) acc[c] = (R)0;
-        for (int k = ptr[a]; k < ptr[a + 1]; k++) {
-            const R cf = (R)coef[k];
-            cmac<R, C>(acc, (__popc(par[k] & mask) & 1) ? -cf : cf, sL + src[k] * C);
+        R gs = (R)1;
+        const int ng = DOWN ? e : rest;          // M2M: g <= a_ax;  L2L: |a| + g <= p
+        for (int g = 0; g <= ng; g++, gs *= sg) {
+            c3[ax] = DOWN ? e - g : e + g;
+            const int src = sIdx[(c3[0] * P1 + c3[1]) * P1 + c3[2]];
+            cmac<R, C>(acc, gs * sG[e * P1 + g], iv + src * C);
         }
 #pragma unroll
-        for (int c = 0; c < C; c++) L[((size_t)b * np + a) * C + c] += acc[c];
+        for (int c = 0; c < C; c++) out[((size_t)v * np + a) * C + c] = acc[c];
+    }
+}
+
+template <class R, int C>
+__global__ void __launch_bounds__(MM_T) k_m2m_sep(int off, int cnt, const int *__restrict__ child0,
+                                                  const int *__restrict__ nchild, const int *__restrict__ ix,
+                                                  const int *__restrict__ iy, const int *__restrict__ iz, int p, int np,
+                                                  int grp, const int *__restrict__ tm, const int *__restrict__ tn,
+                                                  const int *__restrict__ tk, const int *__restrict__ idx3,
+                                                  const double *__restrict__ binom, R *__restrict__ M,
+                                                  const int *__restrict__ skip) {
+    if (skip && *skip) return;
+    extern __shared__ unsigned char smem_raw[];
+    const int P1 = p + 1;
+    R *sA = (R *)smem_raw;                                  // [grp][np][C]
+    R *sB = sA + (size_t)grp * np * C;                       // [grp][np][C]
+    R *sS = sB + (size_t)grp * np * C;                       // [np][C] sum over children
+    R *sG = sS + (size_t)np * C;                             // [P1][P1]
+    short *sIdx = (short *)(sG + P1 * P1);                   // [P1^3]
+    __shared__ int smask[8];
+    if (blockIdx.x >= cnt) return;
+    const int b = off + blockIdx.x, nch = nchild[b];
+    if (nch == 0) return;
+    const int c0 = child0[b], tid = threadIdx.x;
+    shift_tables<R>(p, idx3, binom, true, sIdx, sG);
+    for (int g0 = 0; g0 < nch; g0 += grp) {
+        const int ng = min(grp, nch - g0);
+        __syncthreads();
+        for (int t = tid; t < ng * np * C; t += MM_T) sA[t] = M[(size_t)(c0 + g0) * np * C + t];   // consecutive
+        // a child on the low side of an axis has offset -1/4 of the parent edge
+        if (tid < ng) {
+            const int c = c0 + g0 + tid;
+            smask[tid] = ((ix[c] & 1) ? 0 : 1) | ((iy[c] & 1) ? 0 : 2) | ((iz[c] & 1) ? 0 : 4);
+        }
+        __syncthreads();
+        shift_pass<R, C, true>(0, ng, p, np, tm, tn, tk, sIdx, sG, smask, sA, sB);
+        __syncthreads();
+        shift_pass<R, C, true>(1, ng, p, np, tm, tn, tk, sIdx, sG, smask, sB, sA);
+        __syncthreads();
+        shift_pass<R, C, true>(2, ng, p, np, tm, tn, tk, sIdx, sG, smask, sA, sB);
+        __syncthreads();
+        for (int t = tid; t < np * C; t += MM_T) {
+            R sum = g0 == 0 ? (R)0 : sS[t];
+            for (int j = 0; j < ng; j++) sum += sB[(size_t)j * np * C + t];
+            sS[t] = sum;
+        }
+    }
+    __syncthreads();
+    for (int a = tid; a < np; a += MM_T) {
+        const R sc = (R)ldexp(1.0, -(tm[a] + tn[a] + tk[a]));
+#pragma unroll
+        for (int c = 0; c < C; c++) M[((size_t)b * np + a) * C + c] = sS[(size_t)a * C + c] * sc;
+    }
+}
+
+template <class R, int C>
+__global__ void __launch_bounds__(MM_T) k_l2l_sep(int off, int cnt, const int *__restrict__ parent,
+                                                  const int *__restrict__ ix, const int *__restrict__ iy,
+                                                  const int *__restrict__ iz, int p, int np, const int *__restrict__ tm,
+                                                  const int *__restrict__ tn, const int *__restrict__ tk,
+                                                  const int *__restrict__ idx3, const double *__restrict__ binom,
+                                                  R *__restrict__ L, const int *__restrict__ skip) {
+    if (skip && *skip) return;
+    extern __shared__ unsigned char smem_raw[];
+    const int P1 = p + 1;
+    R *sA = (R *)smem_raw;                                  // [np][C]
+    R *sB = sA + (size_t)np * C;                             // [np][C]
+    R *sG = sB + (size_t)np * C;                             // [P1][P1]
+    short *sIdx = (short *)(sG + P1 * P1);                   // [P1^3]
+    __shared__ int smask[1];
+    if (blockIdx.x >= cnt) return;
+    const int b = off + blockIdx.x, pa = parent[b], tid = threadIdx.x;
+    for (int t = tid; t < np * C; t += MM_T) sA[t] = L[(size_t)pa * np * C + t];
+    shift_tables<R>(p, idx3, binom, false, sIdx, sG);
+    if (tid == 0) smask[0] = ((ix[b] & 1) ? 0 : 1) | ((iy[b] & 1) ? 0 : 2) | ((iz[b] & 1) ? 0 : 4);
+    __syncthreads();
+    shift_pass<R, C, false>(2, 1, p, np, tm, tn, tk, sIdx, sG, smask, sA, sB);
+    __syncthreads();
+    shift_pass<R, C, false>(1, 1, p, np, tm, tn, tk, sIdx, sG, smask, sB, sA);
+    __syncthreads();
+    shift_pass<R, C, false>(0, 1, p, np, tm, tn, tk, sIdx, sG, smask, sA, sB);
+    __syncthreads();
+    for (int a = tid; a < np; a += MM_T) {
+        const R sc = (R)ldexp(1.0, -(tm[a] + tn[a] + tk[a]));
+#pragma unroll
+        for (int c = 0; c < C; c++) L[((size_t)b * np + a) * C + c] += sB[(size_t)a * C + c] * sc;
     }
 }
 
@@ -414,25 +480,37 @@ int build_m2l_classes(bem_plan *P) {
     BEM_CUDA(cudaMemcpy(ip.data(), t.inter_ptr, sizeof(int) * (t.nbox + 1), cudaMemcpyDeviceToHost));
     if (t.n_inter) BEM_CUDA(cudaMemcpy(ii.data(), t.inter_idx, sizeof(int) * t.n_inter, cudaMemcpyDeviceToHost));
     const bool helm = P->green == BEM_HELMHOLTZ;
-    struct Key {
-        long long v[5];
-        bool operator==(const Key &o) const {
-            return v[0] == o.v[0] && v[1] == o.v[1] && v[2] == o.v[2] && v[3] == o.v[3] && v[4] == o.v[4];
-        }
-    };
-    struct KeyHash {
-        size_t operator()(const Key &k) const {
-            unsigned long long h = 1469598103934665603ull;
-            for (long long x : k.v) h = (h ^ (unsigned long long)x) * 1099511628211ull;
-            return (size_t)(h ^ (h >> 29));
-        }
-    };
-    std::unordered_map<Key, int, KeyHash> id;
-    id.reserve(1 << 16);
+    // Class key: (dl, level for Helmholtz, K).  Offsets of interacting boxes
+    // are small integers, so the key packs into 64 bits (17 bits per K
+    // component, biased) and goes into a flat open-addressing table; a key
+    // that does not fit the packing uses an ordered map.
+    const int KB = 17;
+    const long long KMAX = (1ll << (KB - 1)) - 1;
+    std::vector<unsigned long long> tkey;
+    std::vector<int> tval;
+    size_t tmask = 1;
+    while (tmask < 2 * (size_t)t.n_inter + 1024) tmask <<= 1;     // more slots than keys: probing ends
+    tkey.assign(tmask, 0ull);
+    tval.assign(tmask, -1);
+    tmask -= 1;
+    std::map<std::tuple<int, int, long long, long long, long long>, int> wide;
     std::vector<int> pair_cls(std::max<int64_t>(1, t.n_inter));
     std::vector<double> rho, kh;
     std::vector<int> dls;
     std::vector<long long> kvec;        // integer offset vector of every class
+    auto new_class = [&](int b, int dl, int e, long long kx, long long ky, long long kz) {
+        const int c = (int)dls.size();
+        const double sc = std::ldexp(1.0, -(e + 1));
+        rho.push_back(kx * sc);
+        rho.push_back(ky * sc);
+        rho.push_back(kz * sc);
+        kh.push_back(helm ? P->k * std::ldexp(t.side, -lev[b]) : 0.0);
+        dls.push_back(dl);
+        kvec.push_back(kx);
+        kvec.push_back(ky);
+        kvec.push_back(kz);
+        return c;
+    };
     for (int b = 0; b < t.nbox; b++)
         for (int u = ip[b]; u < ip[b + 1]; u++) {
             const int s = ii[u], dl = lev[b] - lev[s], e = std::max(0, -dl);
@@ -441,22 +519,24 @@ int build_m2l_classes(bem_plan *P) {
                 return (long long)(2 * it_ + 1) * (1ll << e) - (long long)(2 * is_ + 1) * (1ll << (dl + e));
             };
             const long long kx = K(ix[b], ix[s]), ky = K(iy[b], iy[s]), kz = K(iz[b], iz[s]);
-            const Key key{{(long long)dl, (long long)(helm ? lev[b] : 0), kx, ky, kz}};
-            auto it = id.find(key);
+            const int lv = helm ? lev[b] : 0;
             int c;
-            if (it == id.end()) {
-                c = (int)dls.size();
-                id.emplace(key, c);
-                const double sc = std::ldexp(1.0, -(e + 1));
-                rho.push_back(kx * sc);
-                rho.push_back(ky * sc);
-                rho.push_back(kz * sc);
-                kh.push_back(helm ? P->k * std::ldexp(t.side, -lev[b]) : 0.0);
-                dls.push_back(dl);
-                kvec.push_back(kx);
-                kvec.push_back(ky);
-                kvec.push_back(kz);
+            if (std::llabs(kx) <= KMAX && std::llabs(ky) <= KMAX && std::llabs(kz) <= KMAX && dl > -64 && dl < 64) {
+                const unsigned long long key =
+                    1ull + (((unsigned long long)(kx + KMAX)) | ((unsigned long long)(ky + KMAX) << KB) |
+                            ((unsigned long long)(kz + KMAX) << (2 * KB)) |
+                            ((unsigned long long)(dl + 64) << (3 * KB)) | ((unsigned long long)lv << (3 * KB + 7)));
+                size_t h = (size_t)((key * 0x9E3779B97F4A7C15ull) >> 20) & tmask;
+                while (tkey[h] != 0ull && tkey[h] != key) h = (h + 1) & tmask;
+                if (tkey[h] == 0ull) {
+                    tkey[h] = key;
+                    tval[h] = new_class(b, dl, e, kx, ky, kz);
+                }
+                c = tval[h];
             } else {
+                auto wk = std::make_tuple(dl, lv, kx, ky, kz);
+                auto it = wide.find(wk);
+                if (it == wide.end()) it = wide.emplace(wk, new_class(b, dl, e, kx, ky, kz)).first;
                 c = it->second;
             }
             pair_cls[u] = c;
@@ -524,29 +604,6 @@ int build_translation_tables(bem_plan *P, cudaStream_t s) {
     std::vector<double> fact(2 * PMAX + 2);
     fact[0] = 1.0;
     for (int i = 1; i < (int)fact.size(); i++) fact[i] = fact[i - 1] * i;
-    auto binom = [&](int a, int b) { return std::round(fact[a] / (fact[b] * fact[a - b])); };
-    std::vector<int> mptr(np + 1, 0), msrc, lptr(np + 1, 0), lsrc;
-    std::vector<double> mcoef, lcoef;
-    std::vector<unsigned char> mpar, lpar;
-    for (int a = 0; a < np; a++) {
-        const int m = mi.m[a], n = mi.n[a], k = mi.k[a], da = m + n + k;
-        for (int q = 0; q <= m; q++)
-            for (int r = 0; r <= n; r++)
-                for (int t = 0; t <= k; t++) {
-                    msrc.push_back(idx(m - q, n - r, k - t));
-                    mcoef.push_back(std::ldexp(binom(m, q) * binom(n, r) * binom(k, t), -(da + q + r + t)));
-                    mpar.push_back((unsigned char)((q & 1) | ((r & 1) << 1) | ((t & 1) << 2)));
-                }
-        mptr[a + 1] = (int)msrc.size();
-        for (int q = 0; q + da <= p; q++)
-            for (int r = 0; q + r + da <= p; r++)
-                for (int t = 0; q + r + t + da <= p; t++) {
-                    lsrc.push_back(idx(m + q, n + r, k + t));
-                    lcoef.push_back(std::ldexp(binom(m + q, m) * binom(n + r, n) * binom(k + t, k), -(2 * (q + r + t) + da)));
-                    lpar.push_back((unsigned char)((q & 1) | ((r & 1) << 1) | ((t & 1) << 2)));
-                }
-        lptr[a + 1] = (int)lsrc.size();
-    }
     // contraction lists: for every b, the (a, a+b) pairs with |a| + |b| <= p
     std::vector<int> cptr(np + 1, 0), cag, deg(np);
     std::vector<double> sgnf(np), invf(np);
@@ -581,10 +638,6 @@ int build_translation_tables(bem_plan *P, cudaStream_t s) {
         BEM_CUDA(cudaMemcpy(*d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice));
         return BEM_OK;
     };
-    BEM_TRY(up(&P->sh_m2m_ptr, mptr)); BEM_TRY(up(&P->sh_m2m_src, msrc));
-    BEM_TRY(up(&P->sh_m2m_coef, mcoef)); BEM_TRY(up(&P->sh_m2m_par, mpar));
-    BEM_TRY(up(&P->sh_l2l_ptr, lptr)); BEM_TRY(up(&P->sh_l2l_src, lsrc));
-    BEM_TRY(up(&P->sh_l2l_coef, lcoef)); BEM_TRY(up(&P->sh_l2l_par, lpar));
     BEM_TRY(up(&P->ctr_ptr, cptr)); BEM_TRY(up(&P->ctr_ag, cag)); BEM_TRY(up(&P->ctr_beta, beta_of));
     BEM_TRY(up(&P->m_deg, deg)); BEM_TRY(up(&P->m_sgnf, sgnf)); BEM_TRY(up(&P->m_invf, invf));
     // the tensor-core form (mixed-precision Laplace) replaces the per-class tables
@@ -632,18 +685,13 @@ int build_translation_tables(bem_plan *P, cudaStream_t s) {
 void free_translation_tables(bem_plan *P) {
     free_tc_tables(P);
     Arena &A = P->arena;
-    for (void *q : {(void *)P->sh_m2m_ptr, (void *)P->sh_m2m_src, (void *)P->sh_m2m_coef, (void *)P->sh_m2m_par,
-                    (void *)P->sh_l2l_ptr, (void *)P->sh_l2l_src, (void *)P->sh_l2l_coef, (void *)P->sh_l2l_par,
-                    (void *)P->ctr_ptr, (void *)P->ctr_ag, (void *)P->ctr_beta, (void *)P->m_deg, (void *)P->m_sgnf,
+    for (void *q : {(void *)P->ctr_ptr, (void *)P->ctr_ag, (void *)P->ctr_beta, (void *)P->m_deg, (void *)P->m_sgnf,
                     (void *)P->m_invf, (void *)P->m2l_D, (void *)P->m2l_fD, (void *)P->cm_ur0, (void *)P->cm_ua0,
                     (void *)P->cm_rtp, (void *)P->cm_gidx, (void *)P->cm_Lp})
         A.release(q);
     P->cm_ur0 = P->cm_ua0 = P->cm_rtp = P->cm_gidx = nullptr;
     P->cm_Lp = nullptr;
     P->cm_nunits = 0;
-    P->sh_m2m_ptr = P->sh_m2m_src = P->sh_l2l_ptr = P->sh_l2l_src = nullptr;
-    P->sh_m2m_coef = P->sh_l2l_coef = nullptr;
-    P->sh_m2m_par = P->sh_l2l_par = nullptr;
     P->ctr_ptr = P->ctr_ag = P->ctr_beta = P->m_deg = nullptr;
     P->m_sgnf = P->m_invf = P->m2l_D = nullptr;
     P->m2l_fD = nullptr;
@@ -657,11 +705,16 @@ int launch_translations(bem_plan *P, R *M, R *L, cudaStream_t s, cudaEvent_t *ev
     const Tree &t = P->t;
     const int np = P->mi.np;
     const int *sk = P->skip;
+    const int P1 = P->mi.p + 1;
+    const size_t tab_sm = sizeof(R) * P1 * P1 + sizeof(short) * P1 * P1 * P1 + 16;
+    int grp = 8;                                 // children shifted together (shared memory permitting)
+    while (grp > 1 && sizeof(R) * (2 * grp + 1) * np * C + tab_sm > 220 * 1024) grp /= 2;
+    const size_t m2m_sm = sizeof(R) * (2 * grp + 1) * np * C + tab_sm;
     for (int l = t.nlev - 2; l >= 0; l--) {
         const int off = t.lev_off[l], cnt = t.lev_off[l + 1] - off;
-        (k_m2m_tab<R, C><<<cnt, TT, sizeof(R) * 8 * np * C, s>>>(off, cnt, t.child0, t.nchild, t.ix, t.iy, t.iz, np,
-                                                                 P->sh_m2m_ptr, P->sh_m2m_src, P->sh_m2m_coef,
-                                                                 P->sh_m2m_par, M, sk), ::bem::count_launch());
+        (k_m2m_sep<R, C><<<cnt, MM_T, m2m_sm, s>>>(off, cnt, t.child0, t.nchild, t.ix, t.iy, t.iz, P->mi.p, np, grp,
+                                                   P->d_m, P->d_n, P->d_k, P->d_idx3, P->d_binom, M, sk),
+         ::bem::count_launch());
     }
     BEM_LAUNCH_CHECK();
     if (ev) BEM_CUDA(cudaEventRecord(ev[3], s));
@@ -692,8 +745,9 @@ int launch_translations(bem_plan *P, R *M, R *L, cudaStream_t s, cudaEvent_t *ev
     if (ev) BEM_CUDA(cudaEventRecord(ev[4], s));
     for (int l = 1; l < t.nlev; l++) {
         const int off = t.lev_off[l], cnt = t.lev_off[l + 1] - off;
-        (k_l2l_tab<R, C><<<cnt, TT, sizeof(R) * np * C, s>>>(off, cnt, t.parent, t.ix, t.iy, t.iz, np, P->sh_l2l_ptr,
-                                                             P->sh_l2l_src, P->sh_l2l_coef, P->sh_l2l_par, L, sk),
+        (k_l2l_sep<R, C><<<cnt, MM_T, sizeof(R) * 2 * np * C + tab_sm, s>>>(off, cnt, t.parent, t.ix, t.iy, t.iz,
+                                                                       P->mi.p, np, P->d_m, P->d_n, P->d_k, P->d_idx3,
+                                                                       P->d_binom, L, sk),
          ::bem::count_launch());
     }
     BEM_LAUNCH_CHECK();
@@ -704,19 +758,19 @@ int launch_translations(bem_plan *P, R *M, R *L, cudaStream_t s, cudaEvent_t *ev
 // large dynamic shared memory for every instantiation (outside any capture)
 void set_translation_attributes() {
     const int big = 220 * 1024;
-    cudaFuncSetAttribute(k_m2m_tab<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_m2m_tab<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_m2m_tab<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_m2m_tab<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_l2l_tab<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_l2l_tab<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_l2l_tab<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_l2l_tab<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_m2l_tab<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_m2l_tab<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_m2l_tab<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_m2l_tab<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_m2l_tables, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_m2m_sep<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_m2m_sep<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_m2m_sep<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_m2m_sep<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_l2l_sep<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_l2l_sep<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_l2l_sep<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_l2l_sep<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_m2l_cm, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     set_tc_attributes();
 }
