@@ -1,0 +1,60 @@
+"""Helmholtz plane-wave scattering from the unit sphere at full size: level-6
+icosphere, 81,920 six-node triangles, 163,842 nodes, rigid (Neumann) surface,
+incidence along +z.  Too large for the dense oracle, so:
+
+* the fast product (float64 and mixed) is compared with the oracle's
+  matrix-free rows of A on a random sample of rows;
+* the float64 solution is compared with the Mie series (discretisation error);
+* the mixed solution is compared with the float64 one (1e-5).
+
+ka = 2 runs at p = 10.  At ka = 8 the boxes of the coarse interaction levels
+are several wavelengths across relative to the expansion's radius of
+convergence and a fixed order p = 10 misses the product bar (error ~2e-4), so
+that case runs at p = 16.
+"""
+import numpy as np
+import pytest
+
+from paper_0908_0673_gb300 import bem, inputs as I
+
+from gpu_util import Plan, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+F64_PRODUCT_TOL = 1e-6
+MX_PRODUCT_TOL = 2e-6
+MIE_TOL = 1e-4
+MX_VS_F64_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def sphere6():
+    return I.icosphere(6, I.TRI6)
+
+
+@pytest.mark.parametrize("ka,p", [(2.0, 10), (8.0, 16)])
+def test_sphere_plane_wave_at_scale(oracle_lib, sphere6, ka, p):
+    m = sphere6
+    rng = np.random.default_rng(int(ka))
+    out = {}
+    for prec in (bem.BEM_F64, bem.BEM_MIXED):
+        P = Plan(m, bem.BEM_HELMHOLTZ, ka, p=p, leaf_size=64, eta=2.0, precision=prec)
+        try:
+            rows = np.sort(rng.choice(P.n_phi, 48, replace=False))
+            x = I.random_vector(P.n_phi, 1, complex_=True)
+            y = P.matvec(bem.BEM_OP_A, x)
+            ref = oracle_lib.apply_rows(m.nodes, m.elems, P.chi_idx, oracle_lib.OP_A, x, rows, oracle_lib.HELMHOLTZ, ka)
+            err = rel_l2(y[rows], ref)
+            chi = oracle_lib.chi_from_elem(P.chi_idx, P.n_chi, I.plane_wave_rigid(m, ka))
+            phi, code, info = P.solve(chi, tol=1e-10, max_iter=600)
+            assert code == bem.BEM_OK
+            assert bem.bem_plan_device_status(P.plan) == 0
+            out[prec] = (err, phi)
+            print(f"ka={ka} p={p} precision={prec}: product {err:.2e}, iters {info.iters}")
+        finally:
+            P.close()
+    assert out[bem.BEM_F64][0] <= F64_PRODUCT_TOL
+    assert out[bem.BEM_MIXED][0] <= MX_PRODUCT_TOL
+    mie = oracle_lib.mie_rigid_sphere_scattered(ka, m.nodes[:, 2])
+    assert rel_l2(out[bem.BEM_F64][1], mie) <= MIE_TOL
+    assert rel_l2(out[bem.BEM_MIXED][1], out[bem.BEM_F64][1]) <= MX_VS_F64_TOL
