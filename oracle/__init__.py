@@ -103,6 +103,7 @@ def lib():
         L.or_l2l.argtypes = [i32, P, P, P, P]
         L.or_l2p.argtypes = [i32, P, i64, P, P, P]
         L.or_fmm_apply.argtypes = [P, P, P, P, i32, dbl, i32, i32, P, P, P, P, P, i64, P, P, P]
+        L.or_field.argtypes = [P, i64, P, i64, i32, P, i32, dbl, dbl, i32, P, P, i64, P, P]
         L.or_rule7.argtypes = [P, P, P]
         L.or_shape.argtypes = [i32, dbl, dbl, P, P, P]
         _lib = L
@@ -211,6 +212,19 @@ def apply_rows(nodes, elems, chi_idx, op, x, rows=None, green=LAPLACE, k=0.0, st
                         _p(st.glx), _p(st.glw), st.n_duffy, st.tau, st.maxdepth,
                         op, _p(xc), _p(r), nr, _p(y))
     return y.real.copy() if (green == LAPLACE and not np.iscomplexobj(x)) else y
+
+
+def field(nodes, elems, chi_idx, phi, chi, pts, green=LAPLACE, k=0.0, st=DEFAULT):
+    """u(x) = D phi - S chi at points off the surface (the exterior
+    representation; zero inside the body), plain quadrature over every element."""
+    nodes, elems, chi_idx = _c(nodes, np.float64), _c(elems, np.int32), _c(chi_idx, np.int32)
+    pts = _c(pts, np.float64).reshape(-1, 3)
+    ph, ch = _c(phi, np.complex128), _c(chi, np.complex128)
+    u = np.zeros(pts.shape[0], np.complex128)
+    lib().or_field(_p(nodes), nodes.shape[0], _p(elems), elems.shape[0], elems.shape[1], _p(chi_idx), green,
+                   float(k), st.tau, st.maxdepth, _p(ph), _p(ch), pts.shape[0], _p(pts), _p(u))
+    real = green == LAPLACE and not (np.iscomplexobj(phi) or np.iscomplexobj(chi))
+    return u.real.copy() if real else u
 
 
 def correction(nodes, elems, chi_idx, green=LAPLACE, k=0.0, st=DEFAULT):
@@ -431,6 +445,25 @@ def mie_rigid_sphere_total(ka: float, cos_theta, nmax=None):
     for n in range(nmax + 1):
         dh = spherical_jn(n, ka, derivative=True) + 1j * spherical_yn(n, ka, derivative=True)
         out += (2 * n + 1) * (1j ** n) * (1j / (ka * ka * dh)) * eval_legendre(n, ct)
+    return out
+
+
+def mie_rigid_sphere_field(k: float, a: float, r, cos_theta, nmax=None):
+    """Scattered potential outside a rigid sphere of radius a under exp(jkz)
+    incidence: sum_n (2n+1) j^n (-j_n'(ka) / h_n'(ka)) h_n(kr) P_n(cos theta),
+    h_n = j_n + j y_n (outgoing for the time factor exp(-j omega t))."""
+    from scipy.special import eval_legendre, spherical_jn, spherical_yn
+    ka = k * a
+    if nmax is None:
+        nmax = int(ka + 30)
+    r = np.asarray(r, dtype=np.float64)
+    ct = np.asarray(cos_theta, dtype=np.float64)
+    out = np.zeros(np.broadcast(r, ct).shape, np.complex128)
+    for n in range(nmax + 1):
+        dh = spherical_jn(n, ka, derivative=True) + 1j * spherical_yn(n, ka, derivative=True)
+        an = -spherical_jn(n, ka, derivative=True) / dh
+        hn = spherical_jn(n, k * r) + 1j * spherical_yn(n, k * r)
+        out += (2 * n + 1) * (1j ** n) * an * hn * eval_legendre(n, ct)
     return out
 
 

@@ -393,6 +393,43 @@ int or_apply_rows(const double *nodes, int64_t nn, const int32_t *elems, int64_t
     return 0;
 }
 
+/* Field of known surface data off the surface: the representation of Eq. 1
+ * with C(x) = 1 outside the body and C(x) = 0 inside (Section 2.2, the field
+ * evaluated from phi and its normal derivative chi),
+ *   u(x) = sum_e sum_a [ phi_a int L_a dG/dn1 dS  -  chi_a int L_a G dS ],
+ * each element integrated with the 7-point rule, or with the parametric
+ * subdivision where |x - centroid| < tau h_e (as for near-singular pairs).
+ * x must not lie on the surface.  phi: [n_nodes], chi: [n_chi], complex. */
+int or_field(const double *nodes, int64_t nn, const int32_t *elems, int64_t ne, int npe,
+             const int32_t *chi_idx, int green, double k, double tau, int maxdepth,
+             const cplx *phi, const cplx *chi, int64_t npts, const double *pts, cplx *u)
+{
+    problem_t P = {nodes, nn, elems, ne, npe, green, k, NULL, NULL, 0, tau, maxdepth};
+    #pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t i = 0; i < npts; i++) {
+        cplx acc = 0.0;
+        for (int64_t e = 0; e < ne; e++) {
+            double X[18];
+            gather_elem(&P, e, X);
+            acc_t A;
+            memset(&A, 0, sizeof(A));
+            A.X = X; A.npe = npe; A.xi = pts + 3 * i; A.green = green; A.k = k;
+            int a_sing = -1;
+            /* index -1 matches no element node: regular or near-singular only */
+            if (classify(A.xi, -1, elems + e * npe, X, npe, tau, &a_sing) == 0) {
+                integrate_regular(&A);
+            } else {
+                double c0[2] = {0.0, 0.0}, c1[2] = {1.0, 0.0}, c2[2] = {0.0, 1.0};
+                integrate_subdivided(&A, c0, c1, c2, 0, tau, maxdepth);
+            }
+            for (int a = 0; a < npe; a++)
+                acc += A.D[a] * phi[elems[e * npe + a]] - A.S[a] * chi[chi_idx[e * npe + a]];
+        }
+        u[i] = acc;
+    }
+    return 0;
+}
+
 /* The correction the fast method adds to its regular-rule sums: for every
  * special pair (class 1 or 2) and local node a, (special - regular) integral,
  * as COO triplets.  Returns the number of triplets written (npe per pair), or
