@@ -202,6 +202,21 @@ int bem_matvec_noalloc(bem_plan *plan, int op, const void *x_dev, void *y_dev, v
 int bem_solve(bem_plan *plan, const void *chi_dev, void *phi_dev, int nrhs,
               const bem_solve_params *params, bem_solve_info *info, void *cuda_stream);
 
+/* Field of the surface data at points off the surface (Section 2.2,
+ * accelerated field evaluation): u(x) = integral over S of
+ * (phi dG/dn1 - G chi) dS, the representation of Eq. 1 with C(x) = 1 outside
+ * the body (and 0 inside).  Tree descent from the root for every point: a box
+ * whose centre is farther than eta r_C contributes its multipole expansion,
+ * a nearer leaf is integrated directly (7-point rule, subdivided within
+ * tau h_e of an element).  phi_dev [n_phi], chi_dev [n_chi] as for
+ * bem_solve; pts_dev device f64 [npts][3]; u_dev device [npts] (complex
+ * pairs for Helmholtz).  Points on the surface are not supported.  Stream
+ * ordered; uses the plan's product work space (no product may run on the
+ * plan at the same time).  A descent deeper than the kernel's stack sets
+ * bem_plan_device_status to 2. */
+int bem_field(bem_plan *plan, const void *phi_dev, const void *chi_dev, int64_t npts, const double *pts_dev,
+              void *u_dev, void *cuda_stream);
+
 /* Concurrent solves for request serving.  The paper solves one problem at a
  * time; a server keeps many plans resident and advances their solves together
  * so that the device work of small problems overlaps.  A batch owns
@@ -262,7 +277,8 @@ int bem_plan_footprint(const bem_plan *plan, size_t *hbm_bytes);
 
 /* Device-side status of the plan's kernels (blocks until the device is idle):
  * 0, or 1 when a kernel's bounded wait on the tensor cores gave up (that
- * kernel then stopped early and its product is incomplete). */
+ * kernel then stopped early and its product is incomplete), or 2 when a field
+ * evaluation's descent stack was full (a branch was skipped). */
 int bem_plan_device_status(const bem_plan *plan, int *status);
 
 /* Most device memory the plan has held at any one time, in bytes: set-up

@@ -31,7 +31,7 @@ EXPORTS = [
     "bem_launch_count", "bem_measure_peak", "bem_mesh_upload", "bem_matvec_noalloc", "bem_plan_setup_times",
     "bem_batch_create", "bem_batch_destroy", "bem_batch_submit", "bem_batch_progress", "bem_batch_poll",
     "bem_batch_wait", "bem_batch_release", "bem_batch_stream", "bem_plan_peak_footprint",
-    "bem_plan_device_status",
+    "bem_plan_device_status", "bem_field",
 ]
 BEM_NSETUP = 7
 SETUP_NAMES = ["upload", "tree", "geometry_radii_lists", "correction", "m2l_classes", "diagonal_tables", "stats"]
@@ -247,6 +247,12 @@ def bem_solve(plan, chi, phi, nrhs=1, params=None, stream=None):
                             C.byref(params) if params is not None else None, infos, _stream(stream))
     _check(code, allow=(BEM_ENOCONV,))
     return code, list(infos)
+
+
+def bem_field(plan, phi, chi, pts, u, stream=None):
+    """Field of the surface data at points off the surface (see include/bem.h).
+    phi, chi, pts ([npts, 3] float64), u: CUDA tensors."""
+    _check(load().bem_field(plan, _ptr(phi), _ptr(chi), int(pts.shape[0]), _ptr(pts), _ptr(u), _stream(stream)))
 
 
 def bem_batch_create(ctx, max_slots):

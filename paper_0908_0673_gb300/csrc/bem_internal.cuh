@@ -257,6 +257,9 @@ int launch_m2l_derivs(bem_plan *P, int ncls, const double *rho, const double *kh
                       cudaStream_t s);
 template <class R, int C>
 int launch_translations(bem_plan *P, R *M, R *L, cudaStream_t s, cudaEvent_t *ev);
+template <class R, int C>
+int launch_m2m(bem_plan *P, R *M, cudaStream_t s);
+int field_moments(bem_plan *P, const void *phi, const void *chi, cudaStream_t s);
 int enqueue_matvec(bem_plan *P, int op, int green, double k, cudaStream_t s);
 int set_slots(bem_plan *P, const void *x, void *y, cudaStream_t s);
 int enqueue_matvec_raw(bem_plan *P, int op, int green, double k, int with_diag, cudaStream_t s,

@@ -728,6 +728,43 @@ static int run_fmm(bem_plan *P, int op, double kwave, R *f, R *M, R *L, cudaStre
     return BEM_OK;
 }
 
+// Moments for the field evaluation: double-layer moments of phi minus
+// single-layer moments of chi at the leaves (the local buffer serves as
+// scratch), then shifted up the tree.
+template <class R>
+__global__ void k_sub_moments(size_t n, R *__restrict__ M, const R *__restrict__ B) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) M[i] -= B[i];
+}
+
+template <class R, int C>
+static int field_moments_t(bem_plan *P, const void *phi, const void *chi, R *f, R *M, R *Bm, cudaStream_t s) {
+    const Tabs tb = tabs_of(P);
+    const TreeView tv = view_of(P);
+    const QuadView qv = quad_of(P);
+    const Tree &t = P->t;
+    const int Q = (int)P->Q;
+    const int *sk = P->skip;
+    BEM_TRY(set_slots(P, phi, nullptr, s));
+    (k_p2q<R, C><<<(Q + 255) / 256, 256, 0, s>>>(Q, P->npe, t.el_phi, P->q.w, P->xptr, f, sk), ::bem::count_launch());
+    (k_p2m<R, C, true><<<t.nleaf, P2M_T, 0, s>>>(t.nleaf, tb, tv, qv, f, M, sk), ::bem::count_launch());
+    BEM_TRY(set_slots(P, chi, nullptr, s));
+    (k_p2q<R, C><<<(Q + 255) / 256, 256, 0, s>>>(Q, P->npe, t.el_chi, P->q.w, P->xptr, f, sk), ::bem::count_launch());
+    (k_p2m<R, C, false><<<t.nleaf, P2M_T, 0, s>>>(t.nleaf, tb, tv, qv, f, Bm, sk), ::bem::count_launch());
+    const size_t n = (size_t)t.nbox * P->mi.np * C;
+    (k_sub_moments<R><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, M, Bm), ::bem::count_launch());
+    BEM_LAUNCH_CHECK();
+    return launch_m2m<R, C>(P, M, s);
+}
+
+int field_moments(bem_plan *P, const void *phi, const void *chi, cudaStream_t s) {
+    const bool mx = P->prm.precision == BEM_MIXED, helm = P->green == BEM_HELMHOLTZ;
+    if (mx) return helm ? field_moments_t<float, 2>(P, phi, chi, P->ff, P->fM, P->fL, s)
+                        : field_moments_t<float, 1>(P, phi, chi, P->ff, P->fM, P->fL, s);
+    return helm ? field_moments_t<double, 2>(P, phi, chi, P->f, P->M, P->L, s)
+                : field_moments_t<double, 1>(P, phi, chi, P->f, P->M, P->L, s);
+}
+
 // Enqueues one product on stream s.  The input and output vectors are read
 // from the device slots P->xptr[0] / P->yptr[0].  with_diag = 0 leaves the
 // regular far + near sums in P->ytmp (used for the diagonal).

@@ -700,8 +700,9 @@ void free_translation_tables(bem_plan *P) {
 // ---------------------------------------------------------------------------
 // host: launchers
 // ---------------------------------------------------------------------------
+// upward pass: moments of every parent from its children, level by level
 template <class R, int C>
-int launch_translations(bem_plan *P, R *M, R *L, cudaStream_t s, cudaEvent_t *ev) {
+int launch_m2m(bem_plan *P, R *M, cudaStream_t s) {
     const Tree &t = P->t;
     const int np = P->mi.np;
     const int *sk = P->skip;
@@ -716,6 +717,18 @@ int launch_translations(bem_plan *P, R *M, R *L, cudaStream_t s, cudaEvent_t *ev
                                                    P->d_m, P->d_n, P->d_k, P->d_idx3, P->d_binom, M, sk),
          ::bem::count_launch());
     }
+    BEM_LAUNCH_CHECK();
+    return BEM_OK;
+}
+
+template <class R, int C>
+int launch_translations(bem_plan *P, R *M, R *L, cudaStream_t s, cudaEvent_t *ev) {
+    const Tree &t = P->t;
+    const int np = P->mi.np;
+    const int *sk = P->skip;
+    const int P1 = P->mi.p + 1;
+    const size_t tab_sm = sizeof(R) * P1 * P1 + sizeof(short) * P1 * P1 * P1 + 16;
+    BEM_TRY((launch_m2m<R, C>(P, M, s)));
     BEM_LAUNCH_CHECK();
     if (ev) BEM_CUDA(cudaEventRecord(ev[3], s));
     const R *D = sizeof(R) == sizeof(double) ? (const R *)P->m2l_D : (const R *)P->m2l_fD;
@@ -775,6 +788,10 @@ void set_translation_attributes() {
     set_tc_attributes();
 }
 
+template int launch_m2m<double, 1>(bem_plan *, double *, cudaStream_t);
+template int launch_m2m<double, 2>(bem_plan *, double *, cudaStream_t);
+template int launch_m2m<float, 1>(bem_plan *, float *, cudaStream_t);
+template int launch_m2m<float, 2>(bem_plan *, float *, cudaStream_t);
 template int launch_translations<double, 1>(bem_plan *, double *, double *, cudaStream_t, cudaEvent_t *);
 template int launch_translations<double, 2>(bem_plan *, double *, double *, cudaStream_t, cudaEvent_t *);
 template int launch_translations<float, 1>(bem_plan *, float *, float *, cudaStream_t, cudaEvent_t *);
