@@ -252,6 +252,28 @@ int bem_batch_wait(bem_batch *batch, int slot, double timeout_s);
 int bem_batch_release(bem_batch *batch, int slot);
 void *bem_batch_stream(bem_batch *batch, int slot);
 
+/* Group solves: many plans -- meshes of uneven size, either Green's function,
+ * either precision -- solved together in lock step.  Every member's restart
+ * cycle (the Arnoldi steps with their fast products, the update and the true
+ * residual) is captured once into one CUDA graph with the members as parallel
+ * branches, so each cycle of the whole group is a single graph launch; a
+ * member that has converged is halted and its branch returns at once.  The
+ * iterations, stopping rules and results are those of bem_solve.
+ *   bem_group_create  plans: host array of nplans distinct plans (the group
+ *                     keeps the pointers; destroy the group before them).
+ *   bem_group_solve   chis / phis: host arrays of nplans device pointers
+ *                     (chi_dev / phi_dev of bem_solve; a NULL pair leaves the
+ *                     member out of this solve); info: host [nplans];
+ *                     launches (optional): kernels launched.  Blocks until
+ *                     every member has ended; BEM_ENOCONV if one did not
+ *                     converge.  The graphs are captured on the first call
+ *                     and again whenever restart or tol change. */
+typedef struct bem_group bem_group;
+int bem_group_create(bem_ctx *ctx, bem_plan *const *plans, int nplans, bem_group **out);
+void bem_group_destroy(bem_group *group);
+int bem_group_solve(bem_group *group, const void *const *chis, void *const *phis, const bem_solve_params *params,
+                    bem_solve_info *info, long long *launches);
+
 /* Tree export (see bem_tree_view).  Blocks. */
 int bem_plan_tree_sizes(const bem_plan *plan, bem_tree_view *view);
 int bem_plan_export_tree(const bem_plan *plan, bem_tree_view *view);

@@ -31,7 +31,7 @@ EXPORTS = [
     "bem_launch_count", "bem_measure_peak", "bem_mesh_upload", "bem_matvec_noalloc", "bem_plan_setup_times",
     "bem_batch_create", "bem_batch_destroy", "bem_batch_submit", "bem_batch_progress", "bem_batch_poll",
     "bem_batch_wait", "bem_batch_release", "bem_batch_stream", "bem_plan_peak_footprint",
-    "bem_plan_device_status", "bem_field",
+    "bem_plan_device_status", "bem_field", "bem_group_create", "bem_group_destroy", "bem_group_solve",
 ]
 BEM_NSETUP = 7
 SETUP_NAMES = ["upload", "tree", "geometry_radii_lists", "correction", "m2l_classes", "diagonal_tables", "stats"]
@@ -126,7 +126,7 @@ def load(build_if_missing: bool = True):
     for name in EXPORTS:
         if name not in ("bem_fmm_params_default", "bem_solve_params_default", "bem_ctx_destroy",
                         "bem_last_error", "bem_mesh_destroy", "bem_plan_destroy", "bem_batch_destroy",
-                        "bem_batch_stream"):
+                        "bem_batch_stream", "bem_group_destroy"):
             getattr(L, name).restype = i32
     _lib = L
     return L
@@ -253,6 +253,30 @@ def bem_field(plan, phi, chi, pts, u, stream=None):
     """Field of the surface data at points off the surface (see include/bem.h).
     phi, chi, pts ([npts, 3] float64), u: CUDA tensors."""
     _check(load().bem_field(plan, _ptr(phi), _ptr(chi), int(pts.shape[0]), _ptr(pts), _ptr(u), _stream(stream)))
+
+
+def bem_group_create(ctx, plans):
+    arr = (C.c_void_p * len(plans))(*[C.c_void_p(p.value if hasattr(p, "value") else p) for p in plans])
+    h = C.c_void_p()
+    _check(load().bem_group_create(ctx, arr, len(plans), C.byref(h)))
+    return h
+
+
+def bem_group_destroy(group):
+    load().bem_group_destroy(group)
+
+
+def bem_group_solve(group, chis, phis, params=None):
+    """chis, phis: lists of CUDA tensors (or None to leave a member out).
+    Returns (code, [bem_solve_info], kernels launched)."""
+    n = len(chis)
+    ca = (C.c_void_p * n)(*[C.c_void_p(_ptr(c).value if c is not None else None) for c in chis])
+    pa = (C.c_void_p * n)(*[C.c_void_p(_ptr(p).value if p is not None else None) for p in phis])
+    infos = (bem_solve_info * n)()
+    nl = C.c_longlong()
+    code = load().bem_group_solve(group, ca, pa, C.byref(params) if params is not None else None, infos, C.byref(nl))
+    _check(code, allow=(BEM_ENOCONV,))
+    return code, list(infos), nl.value
 
 
 def bem_batch_create(ctx, max_slots):

@@ -228,6 +228,7 @@ struct bem_plan {
     double *V = nullptr, *H = nullptr, *gs = nullptr, *w = nullptr, *xk = nullptr, *bvec = nullptr;
     double *scal = nullptr;             // device scalars
     double *hostbuf = nullptr;          // pinned read-back of GMRES scalars
+    void **gm_slot = nullptr;           // device pointer slots of the current solve: [0] chi, [1] x
     int *istate = nullptr;              // device ints: [0] converged flag, [1] steps in cycle
     int gm_restart = 0;
     cudaGraphExec_t cycle_graph = nullptr;

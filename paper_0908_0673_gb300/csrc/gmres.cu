@@ -137,10 +137,15 @@ __global__ void k_scale(int n, const double *__restrict__ x, const double *__res
 }
 
 // r = b - r  (r holds A x on entry)
-__global__ void k_resid(int n, const double *__restrict__ b, double *r) {
+__global__ void k_resid(int n, const double *__restrict__ b, double *r, const int *__restrict__ skip) {
+    if (skip && *skip) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) r[i] = b[i] - r[i];
 }
+
+// istate: [0] skip (set inside a cycle once converged), [1] steps of the
+// cycle, [2] halt (the solve has ended: every kernel of the solve returns)
+__global__ void k_arm(int *st) { st[0] = st[2]; }
 
 constexpr double TAU_MIXED = 5e-8;
 
@@ -212,6 +217,7 @@ __global__ void k_givens(GmState S, int m, int j) {
 // writes x += V y
 template <int C>
 __global__ void k_backsolve(GmState S, int m) {
+    if (S.st[2]) return;
     const int k = S.st[1];
     for (int i = k - 1; i >= 0; i--) {
         double sr = S.g[2 * i], si = S.g[2 * i + 1];
@@ -230,9 +236,11 @@ __global__ void k_backsolve(GmState S, int m) {
 
 // x += sum_{i<k} y_i V_i
 template <int C>
-__global__ void k_xupdate(int n, const double *__restrict__ V, size_t ld, GmState S, double *x) {
+__global__ void k_xupdate(int n, const double *__restrict__ V, size_t ld, GmState S, double *const *xslot) {
+    if (S.st[2]) return;
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
+    double *x = *xslot;
     const int k = S.st[1];
     double a[C];
 #pragma unroll
@@ -252,10 +260,32 @@ __global__ void k_xupdate(int n, const double *__restrict__ V, size_t ld, GmStat
 }
 
 __global__ void k_cycle_init(GmState S, int m) {
-    S.st[0] = 0;
+    S.st[0] = S.st[2];
     S.st[1] = 0;
+    if (S.st[2]) return;
     for (int i = 0; i < 2 * (m + 1); i++) S.g[i] = 0.0;
     S.g[0] = S.sc[1];   // beta
+}
+
+// pointer slots of a solve: [0] chi (Neumann data), [1] x (the solution)
+__global__ void k_set_ptrs(void **slot, const void *chi, void *x) {
+    slot[0] = (void *)chi;
+    slot[1] = x;
+}
+__global__ void k_set_ptrs_tab(void **slot, const void *const *chi_tab, void *const *x_tab, int i) {
+    slot[0] = (void *)chi_tab[i];
+    slot[1] = x_tab[i];
+}
+// product input / output slots from a solve slot
+__global__ void k_slot_io(const void **xptr, void **yptr, void *const *src, void *y) {
+    xptr[0] = *src;
+    yptr[0] = y;
+}
+__global__ void k_zero_slot(void *const *slot, size_t n, const int *__restrict__ skip) {
+    if (skip && *skip) return;
+    double *x = (double *)*slot;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        x[i] = 0.0;
 }
 
 // ---------------------------------------------------------------------------
@@ -264,7 +294,10 @@ __global__ void k_cycle_init(GmState S, int m) {
 // few scalars the host decides on -- ||b||, ||r||, the steps of a cycle -- and
 // records an event.  bem_solve drives one solve to the end, waiting on each
 // event; the batch API advances many solves of different plans together,
-// querying events without blocking, so their device work overlaps.
+// querying events without blocking, so their device work overlaps.  The
+// device work of each transition (start, true residual, restart cycle) is a
+// fixed kernel sequence that reads x and chi through the solve's pointer
+// slots, so a group of plans can also capture it once into one graph.
 // ---------------------------------------------------------------------------
 struct GmSolver {
     bem_plan *P = nullptr;
@@ -294,6 +327,7 @@ static int gm_workspace(bem_plan *P, int m) {
         BEM_TRY(P->arena.alloc(&P->w, ne));
         BEM_TRY(P->arena.alloc(&P->bvec, ne));
         BEM_TRY(P->arena.alloc(&P->scal, 16 + (size_t)GM_BLK * 2 * (200 + 2)));
+        BEM_TRY(P->arena.alloc(&P->gm_slot, 2));
     }
     if (!P->hostbuf) BEM_CUDA(cudaHostAlloc((void **)&P->hostbuf, 64, cudaHostAllocDefault));
     return BEM_OK;
@@ -306,68 +340,63 @@ static GmState gm_state(bem_plan *P) {
     return GmState{P->scal, P->istate, P->H, g0, g0 + m, g0 + 3 * m, g0 + 5 * m + 2, g0 + 7 * m + 2, g0 + 9 * m + 4};
 }
 
-// true residual r = b - A x into V_0 (unscaled), beta = ||r||, read back
+// the product inside a solve: a replay of the plan's graph, or (inside a
+// group capture) its kernels
+static int gm_product(bem_plan *P, int op, cudaStream_t s, bool raw) {
+    if (raw) return enqueue_matvec_raw(P, op, P->green, P->k, 1, s);
+    return enqueue_matvec(P, op, P->green, P->k, s);
+}
+
+// b = B chi, ||b||, tolerance, x = 0
 template <int C>
-static int gm_enqueue_residual(GmSolver &g) {
-    bem_plan *P = g.P;
-    const int n = (int)P->N, ne = n * C, eb = (ne + 255) / 256;
-    double *V = P->V, *partial = P->scal + 16;
+static int gm_k_start(bem_plan *P, double tol, cudaStream_t s, bool raw) {
+    const int n = (int)P->N;
+    double *partial = P->scal + 16;
     GmState S = gm_state<C>(P);
-    cudaStream_t s = g.s;
-    BEM_CUDA(cudaMemsetAsync(P->istate, 0, sizeof(int), s));
-    BEM_TRY(set_slots(P, g.x, V, s));
-    BEM_TRY(enqueue_matvec(P, BEM_OP_A, P->green, P->k, s));
-    (k_resid<<<eb, 256, 0, s>>>(ne, P->bvec, V), ::bem::count_launch());
-    (k_nrm2_partial<C><<<GM_BLK, GM_T, 0, s>>>(n, V, partial, nullptr), ::bem::count_launch());
-    (k_nrm2_final<<<1, 32, 0, s>>>(partial, S.sc + 1, nullptr), ::bem::count_launch());
-    BEM_CUDA(cudaMemcpyAsync(P->hostbuf, S.sc, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
-    BEM_CUDA(cudaEventRecord(g.ev, s));
-    g.waiting = true;
-    g.phase = 1;
+    int *skip = P->istate;
+    (k_arm<<<1, 1, 0, s>>>(P->istate), ::bem::count_launch());
+    (k_slot_io<<<1, 1, 0, s>>>(P->xptr, P->yptr, (void *const *)P->gm_slot, P->bvec), ::bem::count_launch());
+    BEM_TRY(gm_product(P, BEM_OP_B, s, raw));
+    (k_nrm2_partial<C><<<GM_BLK, GM_T, 0, s>>>(n, P->bvec, partial, skip), ::bem::count_launch());
+    (k_nrm2_final<<<1, 32, 0, s>>>(partial, S.sc + 0, skip), ::bem::count_launch());
+    BEM_TRY(set_scalar(S.sc + 3, tol, s));
+    (k_zero_slot<<<GM_BLK, 256, 0, s>>>((void *const *)P->gm_slot + 1, (size_t)n * C, skip), ::bem::count_launch());
+    BEM_LAUNCH_CHECK();
     return BEM_OK;
 }
 
-// b = B chi, ||b||, tolerance, x = 0, then the first residual
+// true residual r = b - A x into V_0 (unscaled), beta = ||r||
 template <int C>
-static int gm_enqueue_start(GmSolver &g) {
-    bem_plan *P = g.P;
-    const int n = (int)P->N, ne = n * C;
-    double *partial = P->scal + 16;
+static int gm_k_residual(bem_plan *P, cudaStream_t s, bool raw) {
+    const int n = (int)P->N, ne = n * C, eb = (ne + 255) / 256;
+    double *V = P->V, *partial = P->scal + 16;
     GmState S = gm_state<C>(P);
-    cudaStream_t s = g.s;
-    BEM_CUDA(cudaMemsetAsync(P->istate, 0, sizeof(int), s));
-    BEM_TRY(set_slots(P, g.chi, P->bvec, s));
-    BEM_TRY(enqueue_matvec(P, BEM_OP_B, P->green, P->k, s));
-    (k_nrm2_partial<C><<<GM_BLK, GM_T, 0, s>>>(n, P->bvec, partial, nullptr), ::bem::count_launch());
-    (k_nrm2_final<<<1, 32, 0, s>>>(partial, S.sc + 0, nullptr), ::bem::count_launch());
-    // With a float32 operator the true (float64) residual levels off near
-    // 2e-8; a mixed-precision solve therefore aims at max(tol, TAU_MIXED) and
-    // also stops once a whole restart cycle fails to halve the true residual.
-    const bool mixed = P->prm.precision == BEM_MIXED;
-    g.tol = mixed ? std::max(g.sp.tol, TAU_MIXED) : g.sp.tol;
-    BEM_TRY(set_scalar(S.sc + 3, g.tol, s));
-    BEM_CUDA(cudaMemsetAsync(g.x, 0, sizeof(double) * ne, s));
-    return gm_enqueue_residual<C>(g);
+    int *skip = P->istate;
+    (k_arm<<<1, 1, 0, s>>>(P->istate), ::bem::count_launch());
+    (k_slot_io<<<1, 1, 0, s>>>(P->xptr, P->yptr, (void *const *)P->gm_slot + 1, V), ::bem::count_launch());
+    BEM_TRY(gm_product(P, BEM_OP_A, s, raw));
+    (k_resid<<<eb, 256, 0, s>>>(ne, P->bvec, V, skip), ::bem::count_launch());
+    (k_nrm2_partial<C><<<GM_BLK, GM_T, 0, s>>>(n, V, partial, skip), ::bem::count_launch());
+    (k_nrm2_final<<<1, 32, 0, s>>>(partial, S.sc + 1, skip), ::bem::count_launch());
+    BEM_LAUNCH_CHECK();
+    return BEM_OK;
 }
 
-// one restart cycle: Arnoldi (CGS2) + Givens for up to m steps, then
-// x += V y; the number of steps taken is read back
+// one restart cycle: Arnoldi (CGS2) + Givens for up to `steps` steps, then
+// x += V y
 template <int C>
-static int gm_enqueue_cycle(GmSolver &g) {
-    bem_plan *P = g.P;
+static int gm_k_cycle(bem_plan *P, int steps, cudaStream_t s, bool raw) {
     const int n = (int)P->N, m = P->gm_restart, ne = n * C;
     const size_t ld = (size_t)ne;
     double *V = P->V, *w = P->w, *partial = P->scal + 16;
     GmState S = gm_state<C>(P);
     const int eb = (ne + 255) / 256, nb = (n + 255) / 256;
     int *skip = P->istate;
-    cudaStream_t s = g.s;
-    (k_scale<<<eb, 256, 0, s>>>(ne, V, S.sc + 1, V, nullptr), ::bem::count_launch());
+    (k_scale<<<eb, 256, 0, s>>>(ne, V, S.sc + 1, V, skip), ::bem::count_launch());
     (k_cycle_init<<<1, 1, 0, s>>>(S, m), ::bem::count_launch());
-    const int steps = std::min(m, g.sp.max_iter - g.iters);
     for (int j = 0; j < steps; j++) {
         BEM_TRY(set_slots(P, V + (size_t)j * ld, w, s));
-        BEM_TRY(enqueue_matvec(P, BEM_OP_A, P->green, P->k, s));
+        BEM_TRY(gm_product(P, BEM_OP_A, s, raw));
         // CGS2: two classical Gram-Schmidt passes against V_0..V_j
         (k_mdot<C><<<GM_BLK, GM_T, 0, s>>>(n, j + 1, V, ld, w, partial, skip), ::bem::count_launch());
         (k_mdot_final<C><<<(j + 1 + 7) / 8, 256, 0, s>>>(j + 1, partial, S.hcol, 0, skip), ::bem::count_launch());
@@ -382,10 +411,64 @@ static int gm_enqueue_cycle(GmSolver &g) {
         BEM_LAUNCH_CHECK();
     }
     (k_backsolve<C><<<1, 1, 0, s>>>(S, m), ::bem::count_launch());
-    (k_xupdate<C><<<nb, 256, 0, s>>>(n, V, ld, S, g.x), ::bem::count_launch());
+    (k_xupdate<C><<<nb, 256, 0, s>>>(n, V, ld, S, (double *const *)P->gm_slot + 1), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
-    BEM_CUDA(cudaMemcpyAsync(P->hostbuf + 2, S.st + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
-    BEM_CUDA(cudaEventRecord(g.ev, s));
+    return BEM_OK;
+}
+
+static double gm_tol(const bem_plan *P, double tol) {
+    // With a float32 operator the true (float64) residual levels off near
+    // 2e-8; a mixed-precision solve therefore aims at max(tol, TAU_MIXED) and
+    // also stops once a whole restart cycle fails to halve the true residual.
+    return P->prm.precision == BEM_MIXED ? std::max(tol, TAU_MIXED) : tol;
+}
+
+// host decision after a true residual: returns true when the solve has ended
+static bool gm_after_residual(GmSolver &g, double bnorm, double beta) {
+    g.restarts++;
+    g.rel = bnorm > 0.0 ? beta / bnorm : 0.0;
+    const bool mixed = g.P->prm.precision == BEM_MIXED;
+    if (g.rel <= g.tol || bnorm == 0.0 || (mixed && g.restarts > 1 && g.rel > 0.5 * g.prev_rel)) {
+        g.status = BEM_OK;
+        return true;
+    }
+    g.prev_rel = g.rel;
+    if (g.iters >= g.sp.max_iter) {
+        g.status = BEM_ENOCONV;
+        return true;
+    }
+    return false;
+}
+
+template <int C>
+static int gm_enqueue_residual(GmSolver &g) {
+    bem_plan *P = g.P;
+    GmState S = gm_state<C>(P);
+    BEM_TRY(gm_k_residual<C>(P, g.s, false));
+    BEM_CUDA(cudaMemcpyAsync(P->hostbuf, S.sc, sizeof(double) * 2, cudaMemcpyDeviceToHost, g.s));
+    BEM_CUDA(cudaEventRecord(g.ev, g.s));
+    g.waiting = true;
+    g.phase = 1;
+    return BEM_OK;
+}
+
+template <int C>
+static int gm_enqueue_start(GmSolver &g) {
+    bem_plan *P = g.P;
+    g.tol = gm_tol(P, g.sp.tol);
+    BEM_CUDA(cudaMemsetAsync(P->istate, 0, sizeof(int) * 3, g.s));
+    (k_set_ptrs<<<1, 1, 0, g.s>>>((void **)P->gm_slot, g.chi, g.x), ::bem::count_launch());
+    BEM_TRY(gm_k_start<C>(P, g.tol, g.s, false));
+    return gm_enqueue_residual<C>(g);
+}
+
+template <int C>
+static int gm_enqueue_cycle(GmSolver &g) {
+    bem_plan *P = g.P;
+    GmState S = gm_state<C>(P);
+    BEM_TRY(gm_k_cycle<C>(P, std::min(P->gm_restart, g.sp.max_iter - g.iters), g.s, false));
+    BEM_CUDA(cudaMemcpyAsync(P->hostbuf + 2, S.st + 1, sizeof(int), cudaMemcpyDeviceToHost, g.s));
+    BEM_CUDA(cudaEventRecord(g.ev, g.s));
     g.waiting = true;
     g.phase = 2;
     return BEM_OK;
@@ -408,17 +491,7 @@ static int gm_advance(GmSolver &g, bool blocking) {
         }
         const double *h = g.P->hostbuf;
         if (g.phase == 1) {
-            g.restarts++;
-            g.rel = h[0] > 0.0 ? h[1] / h[0] : 0.0;
-            const bool mixed = g.P->prm.precision == BEM_MIXED;
-            if (g.rel <= g.tol || h[0] == 0.0 || (mixed && g.restarts > 1 && g.rel > 0.5 * g.prev_rel)) {
-                g.status = BEM_OK;
-                g.phase = 3;
-                break;
-            }
-            g.prev_rel = g.rel;
-            if (g.iters >= g.sp.max_iter) {
-                g.status = BEM_ENOCONV;
+            if (gm_after_residual(g, h[0], h[1])) {
                 g.phase = 3;
                 break;
             }
@@ -469,6 +542,97 @@ int solve(bem_plan *P, const void *chi, void *phi, int nrhs, const bem_solve_par
         if (g.status == BEM_ENOCONV) worst = BEM_ENOCONV;
     }
     return worst;
+}
+
+// ---------------------------------------------------------------------------
+// Group solves: many plans (meshes of any size, either Green's function,
+// either precision) advanced in lock step, every restart cycle of every
+// member one launch of a single captured graph (members are parallel
+// branches; a member that has ended is halted and its branch returns at once).
+// ---------------------------------------------------------------------------
+__global__ void k_apply_halt(int n, int *const *ist, const int *__restrict__ halt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) ist[i][0] = ist[i][2] = halt[i];
+}
+__global__ void k_gather_read(int n, double *const *sc, int *const *ist, double *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[3 * i] = sc[i][0];
+    out[3 * i + 1] = sc[i][1];
+    out[3 * i + 2] = (double)ist[i][1];
+}
+
+}  // namespace bem
+
+struct bem_group {
+    int device = 0, n = 0, m = 0;
+    double tol = -1.0;
+    std::vector<bem_plan *> plans;
+    std::vector<cudaStream_t> st;
+    std::vector<cudaEvent_t> ev;
+    cudaStream_t s0 = nullptr;
+    cudaEvent_t e0 = nullptr;
+    cudaGraphExec_t gstart = nullptr, gcycle = nullptr;
+    long long kstart = 0, kcycle = 0;   // kernels per graph launch
+    std::vector<const void *> captured; // members' Krylov bases the graphs were captured with
+    bem::Arena arena;
+    const void **d_chi = nullptr;
+    void **d_x = nullptr;
+    int *d_halt = nullptr;
+    int **d_ist = nullptr;
+    double **d_sc = nullptr;
+    double *d_read = nullptr;
+    void *h_pin = nullptr;              // pinned: chi ptrs, x ptrs, halt, read-back
+    ~bem_group() {
+        if (gstart) cudaGraphExecDestroy(gstart);
+        if (gcycle) cudaGraphExecDestroy(gcycle);
+        for (auto e : ev) if (e) cudaEventDestroy(e);
+        for (auto s : st) if (s) cudaStreamDestroy(s);
+        if (e0) cudaEventDestroy(e0);
+        if (s0) cudaStreamDestroy(s0);
+        if (h_pin) cudaFreeHost(h_pin);
+    }
+};
+
+namespace bem {
+
+// Captures one graph: (apply halts) -> per member on its stream
+// [pointer slots, body] -> gather of (||b||, beta, steps) of every member.
+template <class Body>
+static int group_capture(bem_group *G, cudaGraphExec_t *out, long long *kernels, Body body) {
+    if (*out) { cudaGraphExecDestroy(*out); *out = nullptr; }
+    cudaGraph_t gr = nullptr;
+    BEM_CUDA(cudaStreamBeginCapture(G->s0, cudaStreamCaptureModeThreadLocal));
+    long long count = 0;
+    tl_capture_count = &count;
+    int rc = BEM_OK;
+    (k_apply_halt<<<(G->n + 127) / 128, 128, 0, G->s0>>>(G->n, G->d_ist, G->d_halt), ::bem::count_launch());
+    if (cudaEventRecord(G->e0, G->s0) != cudaSuccess) rc = BEM_ECUDA;
+    for (int i = 0; i < G->n && rc == BEM_OK; i++) {
+        bem_plan *P = G->plans[i];
+        cudaStream_t s = G->st[i];
+        if (cudaStreamWaitEvent(s, G->e0, 0) != cudaSuccess) { rc = BEM_ECUDA; break; }
+        (k_set_ptrs_tab<<<1, 1, 0, s>>>((void **)P->gm_slot, G->d_chi, G->d_x, i), ::bem::count_launch());
+        rc = body(P, s);
+        if (rc == BEM_OK && (cudaEventRecord(G->ev[i], s) != cudaSuccess || cudaStreamWaitEvent(G->s0, G->ev[i], 0) != cudaSuccess))
+            rc = BEM_ECUDA;
+    }
+    if (rc == BEM_OK)
+        (k_gather_read<<<(G->n + 127) / 128, 128, 0, G->s0>>>(G->n, G->d_sc, G->d_ist, G->d_read), ::bem::count_launch());
+    tl_capture_count = nullptr;
+    cudaError_t e = cudaStreamEndCapture(G->s0, &gr);
+    if (rc != BEM_OK || e != cudaSuccess) {
+        if (gr) cudaGraphDestroy(gr);
+        cudaGetLastError();
+        if (rc == BEM_OK) rc = cuda_fail(e, "group capture", __FILE__, __LINE__);
+        else set_error("group capture failed");
+        return rc;
+    }
+    e = cudaGraphInstantiate(out, gr, 0);
+    cudaGraphDestroy(gr);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
+    *kernels = count;
+    return BEM_OK;
 }
 
 }  // namespace bem
@@ -598,6 +762,164 @@ int bem_batch_release(bem_batch *b, int slot) {
 void *bem_batch_stream(bem_batch *b, int slot) {
     if (!b || slot < 0 || slot >= b->nslot) return nullptr;
     return (void *)b->streams[slot];
+}
+
+
+int bem_group_create(bem_ctx *ctx, bem_plan *const *plans, int nplans, bem_group **out) {
+    if (!ctx || !plans || !out || nplans < 1 || nplans > 65536) { set_error("bem_group_create: bad argument"); return BEM_EINVAL; }
+    *out = nullptr;
+    for (int i = 0; i < nplans; i++) {
+        if (!plans[i]) { set_error("bem_group_create: plan %d is NULL", i); return BEM_EINVAL; }
+        for (int j = 0; j < i; j++)
+            if (plans[j] == plans[i]) { set_error("bem_group_create: plan %d appears twice", i); return BEM_EINVAL; }
+    }
+    BEM_CUDA(cudaSetDevice(ctx->device));
+    bem_group *G = new (std::nothrow) bem_group;
+    if (!G) { set_error("bem_group_create: out of host memory"); return BEM_ENOMEM; }
+    G->device = ctx->device;
+    G->n = nplans;
+    G->plans.assign(plans, plans + nplans);
+    G->st.assign(nplans, nullptr);
+    G->ev.assign(nplans, nullptr);
+    auto fail = [&](cudaError_t e, const char *what) { delete G; return cuda_fail(e, what, __FILE__, __LINE__); };
+    cudaError_t e = cudaStreamCreateWithFlags(&G->s0, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&G->e0, cudaEventDisableTiming);
+    for (int i = 0; i < nplans && e == cudaSuccess; i++) {
+        e = cudaStreamCreateWithFlags(&G->st[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&G->ev[i], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return fail(e, "bem_group_create");
+    int rc = G->arena.alloc(&G->d_chi, nplans);
+    if (rc == BEM_OK) rc = G->arena.alloc(&G->d_x, nplans);
+    if (rc == BEM_OK) rc = G->arena.alloc(&G->d_halt, nplans);
+    if (rc == BEM_OK) rc = G->arena.alloc(&G->d_ist, nplans);
+    if (rc == BEM_OK) rc = G->arena.alloc(&G->d_sc, nplans);
+    if (rc == BEM_OK) rc = G->arena.alloc(&G->d_read, 3 * (size_t)nplans);
+    if (rc != BEM_OK) { delete G; return rc; }
+    const size_t pin = sizeof(void *) * 2 * nplans + sizeof(int) * nplans + sizeof(double) * 3 * nplans + 64;
+    e = cudaHostAlloc(&G->h_pin, pin, cudaHostAllocDefault);
+    if (e != cudaSuccess) return fail(e, "cudaHostAlloc");
+    *out = G;
+    return BEM_OK;
+}
+
+void bem_group_destroy(bem_group *G) {
+    if (!G) return;
+    cudaSetDevice(G->device);
+    cudaStreamSynchronize(G->s0);
+    delete G;
+}
+
+int bem_group_solve(bem_group *G, const void *const *chis, void *const *phis, const bem_solve_params *params,
+                    bem_solve_info *info, long long *launches) {
+    if (!G || !chis || !phis) { set_error("bem_group_solve: NULL argument"); return BEM_EINVAL; }
+    bem_solve_params sp;
+    bem_solve_params_default(&sp);
+    if (params) sp = *params;
+    if (!(sp.tol > 0.0) || sp.max_iter < 1) { set_error("bem_group_solve: tol must be > 0 and max_iter >= 1"); return BEM_EINVAL; }
+    BEM_CUDA(cudaSetDevice(G->device));
+    const int n = G->n;
+    const void **h_chi = (const void **)G->h_pin;
+    void **h_x = (void **)(h_chi + n);
+    int *h_halt = (int *)(h_x + n);
+    double *h_read = (double *)(((uintptr_t)(h_halt + n) + 15) & ~(uintptr_t)15);
+    std::vector<GmSolver> gs(n);
+    std::vector<int> ist_ok(n);
+    std::vector<int *> ist(n);
+    std::vector<double *> sc(n);
+    for (int i = 0; i < n; i++) {
+        bem_plan *P = G->plans[i];
+        gs[i] = GmSolver{};
+        gs[i].P = P;
+        gs[i].sp = sp;
+        gs[i].chi = (const double *)chis[i];
+        gs[i].x = (double *)phis[i];
+        gs[i].tol = gm_tol(P, sp.tol);
+        BEM_TRY(gm_workspace(P, sp.restart));
+        ist[i] = P->istate;
+        sc[i] = P->scal;
+        h_chi[i] = chis[i];
+        h_x[i] = phis[i];
+        h_halt[i] = chis[i] && phis[i] ? 0 : 1;          // a member without data sits this solve out
+        gs[i].phase = h_halt[i] ? 3 : 0;
+        gs[i].status = BEM_OK;
+    }
+    cudaStream_t s0 = G->s0;
+    BEM_CUDA(cudaMemcpyAsync(G->d_ist, ist.data(), sizeof(int *) * n, cudaMemcpyHostToDevice, s0));
+    BEM_CUDA(cudaMemcpyAsync(G->d_sc, sc.data(), sizeof(double *) * n, cudaMemcpyHostToDevice, s0));
+    BEM_CUDA(cudaMemcpyAsync(G->d_chi, h_chi, sizeof(void *) * n, cudaMemcpyHostToDevice, s0));
+    BEM_CUDA(cudaMemcpyAsync(G->d_x, h_x, sizeof(void *) * n, cudaMemcpyHostToDevice, s0));
+    BEM_CUDA(cudaMemcpyAsync(G->d_halt, h_halt, sizeof(int) * n, cudaMemcpyHostToDevice, s0));
+    BEM_CUDA(cudaStreamSynchronize(s0));   // tables in place (the pinned copies are rewritten below)
+    // graphs are captured once per (restart, tolerance) and read pointers from the tables
+    std::vector<const void *> bases(n);
+    for (int i = 0; i < n; i++) bases[i] = G->plans[i]->V;
+    if (!G->gstart || !G->gcycle || G->m != sp.restart || G->tol != sp.tol || G->captured != bases) {
+        for (int i = 0; i < n; i++)
+            BEM_CUDA(cudaMemsetAsync(G->plans[i]->istate, 0, sizeof(int) * 3, s0));
+        BEM_CUDA(cudaStreamSynchronize(s0));
+        BEM_TRY(group_capture(G, &G->gstart, &G->kstart, [&](bem_plan *P, cudaStream_t s) -> int {
+            const double tol = gm_tol(P, sp.tol);
+            if (P->green == BEM_HELMHOLTZ) {
+                BEM_TRY(gm_k_start<2>(P, tol, s, true));
+                return gm_k_residual<2>(P, s, true);
+            }
+            BEM_TRY(gm_k_start<1>(P, tol, s, true));
+            return gm_k_residual<1>(P, s, true);
+        }));
+        BEM_TRY(group_capture(G, &G->gcycle, &G->kcycle, [&](bem_plan *P, cudaStream_t s) -> int {
+            if (P->green == BEM_HELMHOLTZ) {
+                BEM_TRY(gm_k_cycle<2>(P, P->gm_restart, s, true));
+                return gm_k_residual<2>(P, s, true);
+            }
+            BEM_TRY(gm_k_cycle<1>(P, P->gm_restart, s, true));
+            return gm_k_residual<1>(P, s, true);
+        }));
+        G->m = sp.restart;
+        G->tol = sp.tol;
+        G->captured = bases;
+    }
+    long long nlaunch = 0;
+    auto launch = [&](cudaGraphExec_t ge, long long k) -> int {
+        BEM_CUDA(cudaMemcpyAsync(G->d_halt, h_halt, sizeof(int) * n, cudaMemcpyHostToDevice, s0));
+        BEM_CUDA(cudaGraphLaunch(ge, s0));
+        count_launch(k);
+        nlaunch += k;
+        BEM_CUDA(cudaMemcpyAsync(h_read, G->d_read, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s0));
+        BEM_CUDA(cudaStreamSynchronize(s0));
+        return BEM_OK;
+    };
+    BEM_TRY(launch(G->gstart, G->kstart));
+    int active = 0;
+    for (int i = 0; i < n; i++) {
+        if (gs[i].phase == 3) continue;
+        if (gm_after_residual(gs[i], h_read[3 * i], h_read[3 * i + 1])) { gs[i].phase = 3; h_halt[i] = 1; }
+        else active++;
+    }
+    while (active > 0) {
+        BEM_TRY(launch(G->gcycle, G->kcycle));
+        active = 0;
+        for (int i = 0; i < n; i++) {
+            if (gs[i].phase == 3) continue;
+            const int steps = (int)h_read[3 * i + 2];
+            gs[i].iters += steps;
+            if (steps == 0) {
+                gs[i].status = BEM_ENOCONV;
+                gs[i].phase = 3;
+            } else if (gm_after_residual(gs[i], h_read[3 * i], h_read[3 * i + 1])) {
+                gs[i].phase = 3;
+            }
+            if (gs[i].phase == 3) h_halt[i] = 1;
+            else active++;
+        }
+    }
+    int worst = BEM_OK;
+    for (int i = 0; i < n; i++) {
+        if (info) info[i] = bem_solve_info{gs[i].iters, gs[i].restarts, gs[i].rel, gs[i].status};
+        if (gs[i].status == BEM_ENOCONV) worst = BEM_ENOCONV;
+    }
+    if (launches) *launches = nlaunch;
+    return worst;
 }
 
 }  // extern "C"
