@@ -2,9 +2,10 @@
 
 Workload (default): Laplace exterior Neumann problem on the cube [-1,1]^3,
 45 x 45 graded quads per face split into 24,300 6-node triangles (48,602
-nodes), point source at (0.2, -0.1, 0.3), expansion order p = 10, leaf size
-64, separation factor 2, GMRES(30), in the mixed form (float32 near field and
-expansions, float64 Krylov); --precision f64 times the plain float64 form.
+nodes), point source at (0.2, -0.1, 0.3), expansion order p = 10, separation
+factor 2, leaf size from the autotuner's table for this size class, GMRES(30),
+in the mixed form (float32 near field and expansions, float64 Krylov);
+--precision f64 times the plain float64 form.
 
 One step = one complete pass of the hot path from a device-resident mesh:
 plan build on the device (quadrature geometry, octree, radii, lists,
@@ -58,6 +59,7 @@ def parse():
     ap.add_argument("--n", type=int, default=45, help="quads per cube face edge")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-f64", action="store_true", help="skip timing the plain float64 form")
+    ap.add_argument("--leaf", type=int, default=0, help="leaf size (0: the autotuner's choice)")
     ap.add_argument("--serve-requests", type=int, default=8, help="requests in the serving stream (0: skip)")
     ap.add_argument("--serve-max-elems", type=int, default=20000, help="largest mesh of the serving stream")
     return ap.parse_args()
@@ -172,9 +174,9 @@ def run_reference(args):
     print(json.dumps(out))
 
 
-def time_solves(bem, torch, mesh, stream, dev, prec, chi_d, phi_d, steps, warmup, flush, world, dist):
+def time_solves(bem, torch, mesh, stream, dev, prec, chi_d, phi_d, steps, warmup, flush, world, dist, leaf):
     """Device-timed steps (plan build + RHS product + GMRES) in one precision."""
-    prm = bem.bem_fmm_params_default(p=10, leaf_size=64, eta=2.0, precision=prec)
+    prm = bem.bem_fmm_params_default(p=10, leaf_size=leaf, eta=2.0, precision=prec)
     sp = bem.bem_solve_params_default(restart=30, tol=1e-10, max_iter=600)
 
     def step(mid=None):
@@ -308,9 +310,12 @@ def main():
     phi_d = torch.empty(n_phi, device=dev, dtype=torch.float64)
     flush = torch.empty(256 * 1024 * 1024 // 4, device=dev, dtype=torch.float32)   # > 129 MB L2
 
+    from paper_0908_0673_gb300 import tune
+    leaf = args.leaf or tune.choose(int(m.n_elems), bem.BEM_LAPLACE, prec)["leaf_size"]
+    leaf64 = args.leaf or tune.choose(int(m.n_elems), bem.BEM_LAPLACE, bem.BEM_F64)["leaf_size"]
     clocks = Clocks(local)
     main_run = time_solves(bem, torch, mesh, stream, dev, prec, chi_d, phi_d, args.steps, args.warmup, flush,
-                           world, dist)
+                           world, dist, leaf)
     clk = clocks.stop()
     phi = phi_d.cpu().numpy()
     eps_rms = float(np.sqrt(np.mean((phi - phi_ex) ** 2)))
@@ -321,12 +326,12 @@ def main():
     if prec == bem.BEM_MIXED and not args.no_f64:
         phi64_d = torch.empty_like(phi_d)
         f = time_solves(bem, torch, mesh, stream, dev, bem.BEM_F64, chi_d, phi64_d, max(1, min(args.steps, 3)),
-                        1, flush, world, dist)
+                        1, flush, world, dist, leaf64)
         phi64 = phi64_d.cpu().numpy()
         mv64 = matvec_rate(bem, torch, mesh, stream, dev, f["prm"], n_phi, flush)
         other = {"solves_per_s": f["value"], "ms_per_step": f["ms_per_step"], "setup_ms": f["setup_ms"],
                  "solve_ms": f["solve_ms"], "gmres_iters": [i.iters for i in f["infos"]], "matvecs_per_s": mv64[0],
-                 "stage_ms": mv64[1], "steps": max(1, min(args.steps, 3)), "warmup": 1,
+                 "stage_ms": mv64[1], "steps": max(1, min(args.steps, 3)), "warmup": 1, "leaf_size": leaf64,
                  "rel_err_of_mixed_solution": float(np.linalg.norm(phi - phi64) / np.linalg.norm(phi64))}
 
     matvecs_per_s, stages, setup_stages, st = matvec_rate(bem, torch, mesh, stream, dev, prm, n_phi, flush)
@@ -387,7 +392,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": main_run["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if prec == bem.BEM_MIXED else "f64", "data": "synthetic",
         "config": {"workload": f"cube{args.n}-tri6-laplace", "elements": int(m.n_elems), "nodes": int(n_phi), "chi": int(n_chi),
-                   "p": 10, "leaf_size": 64, "eta": 2.0, "precision": args.precision, "gmres": "restart 30, tol 1e-10",
+                   "p": 10, "leaf_size": leaf, "leaf_size_source": "argument" if args.leaf else "autotuner table",
+                   "eta": 2.0, "precision": args.precision, "gmres": "restart 30, tol 1e-10",
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}",
                    "step": "device plan build + RHS product + GMRES solve"},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},

@@ -35,6 +35,7 @@ import numpy as np
 
 from . import bem
 from . import inputs as I
+from . import tune
 
 
 # ----------------------------------------------------------------------------
@@ -87,7 +88,7 @@ class EngineError(RuntimeError):
 # ----------------------------------------------------------------------------
 
 # Peak device bytes per geometric node of a plan with the default parameters
-# (p = 10, leaf size 64, eta = 2, Duffy order 12, tau = 2) and a GMRES(30)
+# (p = 10, leaf sizes 32-128, eta = 2, Duffy order 12, tau = 2) and a GMRES(30)
 # basis, by (Green's function, precision).  The correction matrix dominates
 # (a few hundred entries per row for each of D and S); then the translation
 # tables, the diagonal's higher-order temporaries and the Krylov basis.  The
@@ -131,9 +132,7 @@ class CudaEngine:
         self.max_slots = max_slots
         self.ctx = bem.bem_ctx_create(device)
         self.batch = bem.bem_batch_create(self.ctx, max_slots)
-        self.fmm = dict(p=10, leaf_size=64, eta=2.0)
-        self.fmm.update(fmm or {})
-        self.fmm["precision"] = precision
+        self.fmm = dict(fmm or {})          # fixed parameters; the rest per mesh from the autotuner's table
         self.solve = dict(restart=30, tol=1e-10, max_iter=600)
         self.solve.update(solve or {})
         self.sp = bem.bem_solve_params_default(**self.solve)
@@ -180,7 +179,10 @@ class CudaEngine:
             n_phi, n_chi = bem.bem_mesh_sizes(mesh)
             idx = bem.bem_mesh_chi_index(mesh, m.n_elems, m.npe)
             s = self._stream()
-            plan = bem.bem_plan_create(mesh, req.green, req.k, bem.bem_fmm_params_default(**self.fmm), s)
+            prm = tune.choose(m.n_elems, req.green, self.precision)
+            prm.update(self.fmm)
+            prm["precision"] = self.precision
+            plan = bem.bem_plan_create(mesh, req.green, req.k, bem.bem_fmm_params_default(**prm), s)
             cplx = req.green == bem.BEM_HELMHOLTZ
             dt = t.complex128 if cplx else t.float64
             chi = np.zeros((len(req.rhs), n_chi), np.complex128 if cplx else np.float64)

@@ -7,7 +7,7 @@ plan's measured peak footprint."""
 import numpy as np
 import pytest
 
-from paper_0908_0673_gb300 import bem, inputs as I
+from paper_0908_0673_gb300 import bem, inputs as I, tune
 from paper_0908_0673_gb300.serve import CudaEngine, Server, estimate_peak_footprint, summarize, synthetic_stream
 
 from gpu_util import rel_l2
@@ -22,7 +22,7 @@ def _alone(req, precision):
     n_phi, n_chi = bem.bem_mesh_sizes(mesh)
     idx = bem.bem_mesh_chi_index(mesh, req.mesh.n_elems, req.mesh.npe)
     plan = bem.bem_plan_create(mesh, req.green, req.k,
-                               bem.bem_fmm_params_default(p=10, leaf_size=64, eta=2.0, precision=precision))
+                               bem.bem_fmm_params_default(**tune.choose(req.mesh.n_elems, req.green, precision)))
     try:
         cplx = req.green == bem.BEM_HELMHOLTZ
         out = []
