@@ -17,7 +17,8 @@ replica).  The L2 cache is flushed between steps.
 Extra keys: matvecs_per_s (back-to-back A products of a built plan), per-stage
 times, the roofline of the dominant kernel against measured peaks, the plain
 float64 form on the same workload with the mixed solution's error against it
-(f64_form), a served request stream in both forms (serving), the CPU oracle
+(f64_form), a served request stream in both forms (serving), batched
+instances solved as one group against one at a time (grouped), the CPU oracle
 baseline, end-to-end timing through the public API with host buffers.
 
 --impl reference times the CPU oracle (the plain FP64 matrix-free operator
@@ -60,6 +61,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-f64", action="store_true", help="skip timing the plain float64 form")
     ap.add_argument("--leaf", type=int, default=0, help="leaf size (0: the autotuner's choice)")
+    ap.add_argument("--group", type=int, default=12, help="instances solved as one group (0: skip)")
+    ap.add_argument("--group-min-elems", type=int, default=2000)
+    ap.add_argument("--group-max-elems", type=int, default=10000)
+    ap.add_argument("--group-max-rhs", type=int, default=3)
     ap.add_argument("--serve-requests", type=int, default=8, help="requests in the serving stream (0: skip)")
     ap.add_argument("--serve-max-elems", type=int, default=20000, help="largest mesh of the serving stream")
     return ap.parse_args()
@@ -281,6 +286,124 @@ def serving(args):
     return out
 
 
+def grouped(args):
+    """Batched instances (meshes of uneven size, Laplace and Helmholtz, several
+    right-hand sides each) in the mixed form: plans built, then every
+    right-hand-side round solved as one group (one graph launch per restart
+    cycle for all members), against the same solves one at a time; each
+    solution checked against the instance's own float64 solution."""
+    import torch
+    from paper_0908_0673_gb300 import bem, tune
+    from paper_0908_0673_gb300 import inputs as I
+    rng = np.random.default_rng(0)
+    n_inst = args.group
+    insts = []
+    for i in range(n_inst):
+        E = rng.uniform(args.group_min_elems, args.group_max_elems)
+        kind = int(rng.integers(0, 3))
+        if kind == 2:
+            m = I.cube(max(2, int(round(math.sqrt(E / 12.0)))), I.TRI6, seed=i)
+            rmax = 0.3
+        else:
+            axes = (1.0, 1.0, 1.0) if kind == 0 else tuple(rng.uniform(0.5, 2.0, 3))
+            m = I.geodesic(max(2, int(round(math.sqrt(E / 20.0)))), I.TRI6, axes=axes)
+            rmax = 0.3 * min(axes)
+        helm = rng.uniform() < 0.5
+        k = float(rng.uniform(1.0, 4.0)) if helm else 0.0
+        nr = int(rng.integers(1, args.group_max_rhs + 1))
+        srcs = []
+        for _ in range(nr):
+            d = rng.standard_normal(3)
+            srcs.append(d / np.linalg.norm(d) * rmax * rng.uniform() ** (1.0 / 3.0))
+        insts.append((m, bem.BEM_HELMHOLTZ if helm else bem.BEM_LAPLACE, k, srcs))
+    ctx = bem.bem_ctx_create(0)
+    sp = bem.bem_solve_params_default(restart=30, tol=1e-10, max_iter=600)
+
+    def build(prec):
+        # the float64 references share the mixed form's tree (same leaf size),
+        # so that they differ in precision only
+        out = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for m, green, k, srcs in insts:
+            mh = bem.bem_mesh_create(ctx, m.nodes, m.elems, m.elem_type)
+            n_phi, n_chi = bem.bem_mesh_sizes(mh)
+            idx = bem.bem_mesh_chi_index(mh, m.n_elems, m.npe)
+            prm = tune.choose(m.n_elems, green, bem.BEM_MIXED)
+            prm["precision"] = prec
+            plan = bem.bem_plan_create(mh, green, k, bem.bem_fmm_params_default(**prm))
+            cplx = green == bem.BEM_HELMHOLTZ
+            chis = []
+            for x in srcs:
+                ce = I.helmholtz_point_source(m, x, k)[1] if cplx else I.point_source(m, x)[1]
+                c = np.zeros(n_chi, np.complex128 if cplx else np.float64)
+                c[idx.ravel()] = np.asarray(ce).ravel()
+                chis.append(torch.tensor(c, device="cuda"))
+            out.append((mh, plan, n_phi, chis))
+        torch.cuda.synchronize()
+        return out, time.perf_counter() - t0
+
+    mx, t_build = build(bem.BEM_MIXED)
+    nrhs_max = max(len(s[3]) for s in insts)
+    total = sum(len(s[3]) for s in insts)
+    group = bem.bem_group_create(ctx, [pl for _, pl, _, _ in mx])
+    phis_g = [[torch.empty(npp, device="cuda", dtype=ch[0].dtype) for _ in ch] for _, _, npp, ch in mx]
+    # first call captures the graphs: time it apart from the solves
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    bem.bem_group_solve(group, [ch[0] for *_, ch in mx], [p[0] for p in phis_g], sp)
+    torch.cuda.synchronize()
+    t_first = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    iters, launches = [], 0
+    for r in range(nrhs_max):
+        chis = [ch[r] if r < len(ch) else None for *_, ch in mx]
+        outs = [p[r] if r < len(p) else None for p in phis_g]
+        code, infos, nl = bem.bem_group_solve(group, chis, outs, sp)
+        launches += nl
+        iters += [inf.iters for inf, c in zip(infos, chis) if c is not None]
+    torch.cuda.synchronize()
+    t_group = time.perf_counter() - t0
+    # the same solves one at a time
+    t0 = time.perf_counter()
+    for (mh, pl, npp, ch) in mx:
+        for c in ch:
+            out = torch.empty(npp, device="cuda", dtype=c.dtype)
+            bem.bem_solve(pl, c, out, 1, sp)
+    torch.cuda.synchronize()
+    t_single = time.perf_counter() - t0
+    bem.bem_group_destroy(group)
+    # float64 references, one at a time (not timed)
+    errs, worst = [], []
+    f64, _ = build(bem.BEM_F64)
+    for i, ((mh, pl, npp, ch), g) in enumerate(zip(f64, phis_g)):
+        for c, pg in zip(ch, g):
+            out = torch.empty(npp, device="cuda", dtype=c.dtype)
+            bem.bem_solve(pl, c, out, 1, sp)
+            a, b = pg.cpu().numpy(), out.cpu().numpy()
+            errs.append(float(np.linalg.norm(a - b) / np.linalg.norm(b)))
+            m, green, k, _s = insts[i]
+            worst.append((errs[-1], {"instance": i, "mesh": m.name, "elements": int(m.n_elems),
+                                     "green": "helmholtz" if green == bem.BEM_HELMHOLTZ else "laplace", "k": k,
+                                     "rel_err": errs[-1]}))
+    worst = [w for _, w in sorted(worst, key=lambda t: -t[0])[:4]]
+    for lst in (mx, f64):
+        for mh, pl, _, _ in lst:
+            bem.bem_plan_destroy(pl)
+            bem.bem_mesh_destroy(mh)
+    bem.bem_ctx_destroy(ctx)
+    return {"instances": n_inst, "elements": f"uniform {args.group_min_elems}-{args.group_max_elems}, 6-node triangles",
+            "geometry": "geodesic sphere | ellipsoid (axes U[0.5,2]) | graded cube", "green": "50% Laplace, 50% Helmholtz k U[1,4]",
+            "rhs": f"1-{args.group_max_rhs} interior point sources", "total_solves": total,
+            "total_elements": int(sum(s[0].n_elems for s in insts)),
+            "build_s": t_build, "first_call_with_capture_s": t_first,
+            "group": {"solves_per_s": total / t_group, "seconds": t_group, "graph_kernels": int(launches)},
+            "one_at_a_time": {"solves_per_s": total / t_single, "seconds": t_single},
+            "speedup": t_single / t_group, "gmres_iters_mean": float(np.mean(iters)),
+            "rel_err_vs_own_f64": {"max": max(errs), "within_1e-5": int(sum(e <= 1e-5 for e in errs)), "solves": len(errs),
+                                   "worst": worst}}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -408,6 +531,8 @@ def main():
         out["f64_form"] = other
     if rank == 0 and world == 1 and args.serve_requests > 0:
         out["serving"] = serving(args)
+    if rank == 0 and world == 1 and args.group > 0:
+        out["grouped"] = grouped(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(m, chi_idx, n_phi, statistics.median(iters) if iters else 60)
     if rank == 0:
