@@ -45,6 +45,38 @@ METRIC = "FMM-BEM matvecs/s & served solves/s, p50/p99 latency vs plain FP64 at 
 WORKLOAD = "cube45-tri6-laplace"
 SOURCE = (0.2, -0.1, 0.3)
 FLOPS_PER_PAIR = {"A": 20.0, "B": 11.0}   # near-field kernel, Laplace double / single layer
+# DRAM bytes (read + write) per launch of the dominant kernels, from one ncu
+# capture of this workload (the command is in profiles/); reported while the
+# kernel's source file is unchanged, null otherwise.
+NCU_TRAFFIC = {
+    "near_l2p": {"bytes": 7447552, "source": "paper_0908_0673_gb300/csrc/fmm.cu", "sha256": "055f25b35203c30b025c2c2a51d09f40cf522c78d9a42c50ddc314feb4f009e1"},
+    "m2l": {"bytes": 3138304 + 66804224, "source": "paper_0908_0673_gb300/csrc/m2l_tc.cu", "sha256": "bcf53837cff02e76d6944217047105f3c8b102d51405b24253b15155c3ea3a78"},
+}
+
+
+def tc_issued_macs(p):
+    """MACs the tensor-core M2L issues per interaction pair and split term:
+    rows in 16-row bands, each band's K extent the columns its lowest-degree
+    row needs (the kernel's tiling of the |a| + |b| <= p triangle)."""
+    deg = [d for d in range(p + 1) for _ in range((d + 1) * (d + 2) // 2)]
+    cum = lambda d: d * (d + 1) * (d + 2) // 6 if d > 0 else 0
+    ncols = (len(deg) + 15) // 16 * 16
+    total = 0
+    for b0 in range(0, ncols, 16):
+        K = max([8] + [cum(p - deg[b] + 1) for b in range(b0, min(b0 + 16, len(deg)))])
+        total += 16 * ((K + 7) // 8 * 8)
+    return total
+
+
+def ncu_traffic(stage):
+    import hashlib
+    rec = NCU_TRAFFIC.get(stage)
+    if rec is None:
+        return None
+    with open(os.path.join(ROOT, rec["source"]), "rb") as f:
+        return rec["bytes"] if hashlib.sha256(f.read()).hexdigest() == rec["sha256"] else None
+
+
 # GMRES(30) Arnoldi steps of this workload to 1e-10 (float64), measured by
 # this benchmark on a GB300; used only to extrapolate the CPU oracle's rate.
 GMRES_ITERS_CUBE45 = 60
@@ -466,9 +498,10 @@ def main():
     if dom == "near_l2p":
         flops = st["near_pairs"] * FLOPS_PER_PAIR["A"]
         achieved = flops / (stages[dom] * 1e-3) / 1e12
-        roof = {"kernel": "k_near (near-field regular quadrature + L2P)", "bound": "alu",
+        roof = {"kernel": "k_near_f32 (near-field regular quadrature + L2P)" if kind == 0 else
+                "k_near (near-field regular quadrature + L2P)", "bound": "alu",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None,
+                "traffic": ncu_traffic("near_l2p") if kind == 0 else None, "traffic_unit": "bytes per launch",
                 "peak_source": f"measured {'FP32' if kind == 0 else 'FP64'} FMA throughput (bem_measure_peak)",
                 "work": f"{st['near_pairs']} target-source pairs x {FLOPS_PER_PAIR['A']:.0f} flops"}
     elif dom == "m2l":
@@ -482,6 +515,22 @@ def main():
     else:
         roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": peak, "unit": "TFLOP/s", "frac": None,
                 "traffic": None}
+
+    m2l_tensor = None
+    if prec == bem.BEM_MIXED:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops": 1900.0}
+        tf32 = 0.5 * peaks["bf16_tflops"]
+        t = stages["m2l"] * 1e-3
+        alg = st["n_inter"] * 2.0 * math.comb(10 + 6, 6) / t / 1e12
+        issued = st["n_inter"] * 3 * 2.0 * tc_issued_macs(10) / t / 1e12
+        m2l_tensor = {"kernel": "k_m2l_tc + k_m2l_gather_sym (tcgen05 kind::tf32, hi/lo split, 3 products)",
+                      "bound": "tensor", "unit": "TFLOP/s", "peak": tf32,
+                      "peak_source": "TF32 = 0.5 x measured BF16 (MEASURED_PEAKS.json, nominal ratio)",
+                      "achieved_algorithmic": alg, "frac_algorithmic": alg / tf32,
+                      "achieved_issued": issued, "frac_issued": issued / tf32,
+                      "stage_ms": stages["m2l"], "traffic": ncu_traffic("m2l"), "traffic_unit": "bytes per launch",
+                      "work": f"{st['n_inter']} pairs x 2 x C(16,6) algorithmic; x 3 x {tc_issued_macs(10)} MACs issued"}
 
     # end to end through the public API from pinned host buffers
     nodes_h = torch.from_numpy(np.ascontiguousarray(m.nodes)).pin_memory()
@@ -524,7 +573,7 @@ def main():
         "gmres_iters": iters, "rel_residual": infos[-1].rel_residual if infos else None,
         "eps_rms_vs_point_source": eps_rms,
         "matvecs_per_s": matvecs_per_s, "stage_ms": stages, "setup_stage_ms": setup_stages, "plan_stats": st,
-        "roofline": roof, "clocks": clk, "gpu_launches": main_run["launches"],
+        "roofline": roof, "m2l_tensor": m2l_tensor, "clocks": clk, "gpu_launches": main_run["launches"],
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
     }
     if other is not None:
