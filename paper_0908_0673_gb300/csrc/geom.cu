@@ -72,6 +72,10 @@ __constant__ Rule7 c_rule;
 // offset n (n - 1) / 2, so that plans with different Duffy orders share them.
 constexpr int GL_MAXN = 64;
 __constant__ double c_glx[GL_MAXN * (GL_MAXN + 1) / 2], c_glw[GL_MAXN * (GL_MAXN + 1) / 2];
+// float32 copies for the mixed-precision special-pair quadrature: the 7-point
+// rule (s, t, w) and the Gauss-Legendre nodes and weights mapped to [0, 1]
+__constant__ float c_rulef[3][7];
+__constant__ float2 c_gl01f[GL_MAXN * (GL_MAXN + 1) / 2];
 
 // Shape functions in the fixed operation order that the radii and the pair
 // classification rely on.  L0 = (1 - s) - t, L1 = s, L2 = t.
@@ -164,8 +168,13 @@ __global__ void k_geometry(int E, int npe, const int *__restrict__ el_phi, const
     fw[o] = (float)w;
 }
 
-__global__ void k_elem_centroid(int E, int npe, const int *__restrict__ el_phi, const double *__restrict__ nodes,
-                                double *ecx, double *ecy, double *ecz, double *eh) {
+// Also writes a float32 bound per element for the pair search: the centroid
+// image and a radius R_e >= max(tau h_e, max_a |X_a - c_e|), so a node
+// farther than R_e (plus the float32 rounding margin) is neither a node of
+// the element nor near-singular to it.
+__global__ void k_elem_centroid(int E, int npe, double tau, const int *__restrict__ el_phi,
+                                const double *__restrict__ nodes, double *ecx, double *ecy, double *ecz, double *eh,
+                                float4 *ebnd) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= E) return;
     double X[18], N[6], x[3];
@@ -179,6 +188,9 @@ __global__ void k_elem_centroid(int E, int npe, const int *__restrict__ el_phi, 
     if (h12 > m) m = h12;
     if (h20 > m) m = h20;
     ecx[i] = x[0]; ecy[i] = x[1]; ecz[i] = x[2]; eh[i] = m;
+    double rb = tau * m;
+    for (int v = 0; v < npe; v++) rb = fmax(rb, dist3_rn(X[3 * v], X[3 * v + 1], X[3 * v + 2], x[0], x[1], x[2]));
+    ebnd[i] = make_float4((float)x[0], (float)x[1], (float)x[2], (float)(rb * (1.0 + 1e-6)));
 }
 
 // The 7-point rule and the Gauss-Legendre tables are the same for every
@@ -196,6 +208,12 @@ static int init_rule_tables(int device) {
     for (int n = 1; n <= GL_MAXN; n++) gauss_legendre(n, &gx[n * (n - 1) / 2], &gw[n * (n - 1) / 2]);
     BEM_CUDA(cudaMemcpyToSymbol(c_glx, gx.data(), sizeof(double) * gx.size()));
     BEM_CUDA(cudaMemcpyToSymbol(c_glw, gw.data(), sizeof(double) * gw.size()));
+    float rf[3][7];
+    for (int q = 0; q < 7; q++) { rf[0][q] = (float)r.s[q]; rf[1][q] = (float)r.t[q]; rf[2][q] = (float)r.w[q]; }
+    BEM_CUDA(cudaMemcpyToSymbol(c_rulef, rf, sizeof(rf)));
+    std::vector<float2> g01(gx.size());
+    for (size_t i = 0; i < gx.size(); i++) g01[i] = make_float2((float)(0.5 * (1.0 + gx[i])), (float)(0.5 * gw[i]));
+    BEM_CUDA(cudaMemcpyToSymbol(c_gl01f, g01.data(), sizeof(float2) * g01.size()));
     done[device] = true;
     return BEM_OK;
 }
@@ -228,33 +246,31 @@ struct CorrArgs {
     const double *nodes;
     const int *el_phi, *el_chi;
     const double *ecx, *ecy, *ecz, *eh;   // per element centroid image and size
+    const float4 *ebnd;                   // per element float32 search bound (centroid, R_e)
     const double *bcx, *bcy, *bcz, *brho; // per box centre and search radius
     const int *child0, *nchild, *eb, *ee;
 };
 
 // Per box: radius of a ball around the centre that holds every point a
 // special pair can involve: max over the subtree's elements of
-// max(|c_e - c| + tau h_e, max_a |X_a - c|), inflated by 1e-12.
-__global__ void k_box_search_radius(CorrArgs a, int nbox, double *rho) {
-    int b = blockIdx.x;
-    if (b >= nbox) return;
-    double m = 0.0;
-    for (int i = a.eb[b] + threadIdx.x; i < a.ee[b]; i += blockDim.x) {
-        double d = dist3_rn(a.ecx[i], a.ecy[i], a.ecz[i], a.bcx[b], a.bcy[b], a.bcz[b]) + a.tau * a.eh[i];
+// max(|c_e - c| + tau h_e, max_a |X_a - c|), inflated by 1e-12.  One thread
+// per element walks from its owner leaf (the leaf of its node 0) to the root
+// and raises each box's radius by an integer atomic max on the bits of the
+// non-negative double (rho starts at zero).
+__global__ void k_elem_search_radius(CorrArgs a, const int *__restrict__ leaf_of_node, const int *__restrict__ parent,
+                                     unsigned long long *rho_bits) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= a.E) return;
+    const int *el = a.el_phi + (size_t)e * a.npe;
+    const double te = a.tau * a.eh[e];
+    for (int b = leaf_of_node[el[0]]; b >= 0; b = b ? parent[b] : -1) {
+        double d = dist3_rn(a.ecx[e], a.ecy[e], a.ecz[e], a.bcx[b], a.bcy[b], a.bcz[b]) + te;
         for (int v = 0; v < a.npe; v++) {
-            const double *p = a.nodes + 3 * (size_t)a.el_phi[(size_t)i * a.npe + v];
+            const double *p = a.nodes + 3 * (size_t)el[v];
             d = fmax(d, dist3_rn(p[0], p[1], p[2], a.bcx[b], a.bcy[b], a.bcz[b]));
         }
-        m = fmax(m, d);
+        atomicMax(rho_bits + b, (unsigned long long)__double_as_longlong(d * (1.0 + 1e-12)));
     }
-    __shared__ double red[256];
-    red[threadIdx.x] = m;
-    __syncthreads();
-    for (int off = blockDim.x / 2; off; off >>= 1) {
-        if (threadIdx.x < off) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + off]);
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) rho[b] = red[0] * (1.0 + 1e-12);
 }
 
 // 0 regular, 1 singular (*a_sing = local node), 2 near-singular
@@ -270,6 +286,8 @@ __device__ __forceinline__ int classify_pair(const CorrArgs &a, int node, const 
 // ball holds the node; writes special (element, kind) pairs when `out`.
 __device__ int find_special(const CorrArgs &a, int node, int *out_e) {
     double xi[3] = {a.nodes[3 * (size_t)node], a.nodes[3 * (size_t)node + 1], a.nodes[3 * (size_t)node + 2]};
+    const float xf[3] = {(float)xi[0], (float)xi[1], (float)xi[2]};
+    const float ax = fabsf(xf[0]) + fabsf(xf[1]) + fabsf(xf[2]);
     int stack[8 * 24], sp = 0, cnt = 0;
     stack[sp++] = 0;
     while (sp > 0) {
@@ -281,6 +299,12 @@ __device__ int find_special(const CorrArgs &a, int node, int *out_e) {
             continue;
         }
         for (int e = a.eb[b]; e < a.ee[b]; e++) {
+            // float32 rejection of elements that are certainly regular (the
+            // margin covers the rounding of both positions), then the exact test
+            const float4 c = a.ebnd[e];
+            const float dx = xf[0] - c.x, dy = xf[1] - c.y, dz = xf[2] - c.z;
+            const float lim = c.w + 1e-5f * (ax + fabsf(c.x) + fabsf(c.y) + fabsf(c.z) + c.w);
+            if (dx * dx + dy * dy + dz * dz > lim * lim) continue;
             int as;
             if (classify_pair(a, node, xi, e, &as)) {
                 if (out_e) out_e[cnt] = e;
@@ -310,19 +334,48 @@ __global__ void k_special_write(CorrArgs a, const int *__restrict__ off, int *pa
 //   r = x_i - x(s,t) = -sum N_a d_a,  tangents = sum dN_a d_a,
 // so distances keep full relative precision however close the point is to
 // the collocation node (which lets the mixed-precision plan run it in
-// float32).  Subdivision decisions use absolute float64 coordinates in the
-// fixed operation order of the oracle, so each piece gets the same rule.
-// Lanes share the Duffy points of a self element; near-singular pieces are
-// refined level by level from a per-warp queue in shared memory.  The
-// regular 7-point rule is added with negative weights, so the warp produces
-// (special - regular) directly.
+// float32).  At a Duffy point (s,t) = P + delta of a self element, P the
+// parametric position of the node, the shape values are taken as
+//   N_a(P + delta) = [a = a_sing] + (grad N_a(P) + grad N_a(P + delta)) . delta / 2,
+// which is exact for shape functions of degree two or less and keeps the
+// small N_a next to the node at full relative precision as well.
+//
+// Per pair the warp works in three steps.  Quadrature points are written to
+// a per-warp ring in shared memory: the regular 7-point rule with negative
+// weights first, then the 7 points of every leaf piece of the subdivision.
+// Every 32 pending points are evaluated, one per lane.  Finally the lanes'
+// partial sums are reduced by a transposing butterfly that leaves value l
+// of the pair on lane l for the store.  Subdivision decisions use a float32
+// estimate with a margin and fall back to the float64 test in the oracle's
+// operation order, so each piece gets the same rule on both sides; pieces
+// are refined level by level from a per-warp queue.  Self elements take
+// their Duffy points by index, all lanes at once.  Points go to lanes in a
+// fixed order, so the stored values are the same on every run.
 // ---------------------------------------------------------------------------
-constexpr int SW_WARPS = 4, SW_CAP = 192;
+constexpr int SP_WARPS = 4;        // warps per block
+constexpr int SP_QCAP = 128;       // pieces per level buffer and warp
+constexpr int SP_RING = 256;       // pending points per warp: a power of two >= 31 + 7 * 32
+constexpr float SP_UNIT = 1024.f;  // piece corners are multiples of 2^-10 (max_subdiv <= 10)
 
 struct PieceF {
     float a0, a1, b0, b1, c0, c1;   // parametric corners (dyadic, exact in float32)
     int depth;
 };
+
+// values a pair stores (2 NPE C + 1), rounded up to 16 or 32 lanes
+__host__ __device__ constexpr int sp_nvp(bool helm, int npe) { return 2 * npe * (helm ? 2 : 1) + 1 <= 16 ? 16 : 32; }
+
+// a queued piece: corners in units of 2^-10, two to a word, then the depth
+__device__ __forceinline__ uint4 pack_piece(const PieceF &P) {
+    auto u = [](float x) { return (unsigned)(x * SP_UNIT); };
+    return make_uint4(u(P.a0) | u(P.a1) << 16, u(P.b0) | u(P.b1) << 16, u(P.c0) | u(P.c1) << 16, (unsigned)P.depth);
+}
+
+__device__ __forceinline__ PieceF unpack_piece(uint4 q) {
+    const float k = 1.f / SP_UNIT;
+    return {(q.x & 0xffffu) * k, (q.x >> 16) * k, (q.y & 0xffffu) * k, (q.y >> 16) * k,
+            (q.z & 0xffffu) * k, (q.z >> 16) * k, (int)q.w};
+}
 
 template <class R, int NPE>
 __device__ __forceinline__ void shape_all(R s, R t, R N[NPE], R Ns[NPE], R Nt[NPE]) {
@@ -341,11 +394,31 @@ __device__ __forceinline__ void shape_all(R s, R t, R N[NPE], R Ns[NPE], R Nt[NP
     }
 }
 
-// acc[0..4][a]: Re S, Im S, Re D, Im D, D0 (Laplace double layer)
+// rule tables in the working precision
+template <class R> __device__ __forceinline__ R rule_s(int q);
+template <class R> __device__ __forceinline__ R rule_t(int q);
+template <class R> __device__ __forceinline__ R rule_w(int q);
+template <> __device__ __forceinline__ float rule_s<float>(int q) { return c_rulef[0][q]; }
+template <> __device__ __forceinline__ float rule_t<float>(int q) { return c_rulef[1][q]; }
+template <> __device__ __forceinline__ float rule_w<float>(int q) { return c_rulef[2][q]; }
+template <> __device__ __forceinline__ double rule_s<double>(int q) { return c_rule.s[q]; }
+template <> __device__ __forceinline__ double rule_t<double>(int q) { return c_rule.t[q]; }
+template <> __device__ __forceinline__ double rule_w<double>(int q) { return c_rule.w[q]; }
+// Gauss-Legendre node and weight mapped to [0, 1]
+template <class R> __device__ __forceinline__ void gl01(int i, R &u, R &wu);
+template <> __device__ __forceinline__ void gl01<float>(int i, float &u, float &wu) { u = c_gl01f[i].x; wu = c_gl01f[i].y; }
+template <> __device__ __forceinline__ void gl01<double>(int i, double &u, double &wu) {
+    u = 0.5 * (1.0 + c_glx[i]);
+    wu = 0.5 * c_glw[i];
+}
+
+// The values a pair stores, per lane partial sums: S at a*C + c, D at
+// NPE*C + a*C + c (c = 0 real, 1 imaginary), the Laplace double layer of a
+// constant density (D0 row sum) at 2*NPE*C.
 template <class R, bool HELM, int NPE>
-__device__ __forceinline__ void acc_local(const R *d, R kk, R s, R t, R wref, R (&acc)[5][NPE]) {
-    R N[NPE], Ns[NPE], Nt[NPE];
-    shape_all<R, NPE>(s, t, N, Ns, Nt);
+__device__ __forceinline__ void point_acc(const R *d, R kk, const R (&N)[NPE], const R (&Ns)[NPE], const R (&Nt)[NPE],
+                                          R wref, R (&v)[sp_nvp(HELM, NPE)]) {
+    constexpr int C = HELM ? 2 : 1;
     R rx = 0, ry = 0, rz = 0, ux = 0, uy = 0, uz = 0, vx = 0, vy = 0, vz = 0;
 #pragma unroll
     for (int a = 0; a < NPE; a++) {
@@ -359,11 +432,11 @@ __device__ __forceinline__ void acc_local(const R *d, R kk, R s, R t, R wref, R 
     const R r2 = rx * rx + ry * ry + rz * rz;
     const R inv = (R)1 / sqrt(r2);
     const R c4 = (R)(0.25 / M_PI) * wref;
-    const R wS = c4 * J * inv;                                   // w J G0
+    const R wS = c4 * J * inv;                                           // w J G0
     const R wD = c4 * (rx * nx + ry * ny + rz * nz) * inv * inv * inv;   // w J dG0/dn1
     R sr = wS, si = 0, dr = wD, di = 0;
     if (HELM) {
-        const R R1 = r2 * inv, kr = kk * R1;
+        const R kr = kk * (r2 * inv);
         R sn, cs;
         sincos(kr, &sn, &cs);
         sr = cs * wS; si = sn * wS;
@@ -372,20 +445,38 @@ __device__ __forceinline__ void acc_local(const R *d, R kk, R s, R t, R wref, R 
     }
 #pragma unroll
     for (int a = 0; a < NPE; a++) {
-        acc[0][a] += N[a] * sr;
-        acc[2][a] += N[a] * dr;
-        acc[4][a] += N[a] * wD;
+        v[a * C] += N[a] * sr;
+        v[NPE * C + a * C] += N[a] * dr;
         if (HELM) {
-            acc[1][a] += N[a] * si;
-            acc[3][a] += N[a] * di;
+            v[a * C + 1] += N[a] * si;
+            v[NPE * C + a * C + 1] += N[a] * di;
         }
     }
+    v[2 * NPE * C] += wD;
+}
+
+template <class R, bool HELM, int NPE>
+__device__ __forceinline__ void eval_st(const R *d, R kk, R s, R t, R w, R (&v)[sp_nvp(HELM, NPE)]) {
+    R N[NPE], Ns[NPE], Nt[NPE];
+    shape_all<R, NPE>(s, t, N, Ns, Nt);
+    point_acc<R, HELM, NPE>(d, kk, N, Ns, Nt, w, v);
+}
+
+// q-th point of the 7-point rule on a piece, with its weight
+template <class R>
+__device__ __forceinline__ void leaf_point(const PieceF &P, int q, R &s, R &t, R &w) {
+    const R e0 = (R)P.b0 - (R)P.a0, e1 = (R)P.b1 - (R)P.a1, f0 = (R)P.c0 - (R)P.a0, f1 = (R)P.c1 - (R)P.a1;
+    const R det = fabs(e0 * f1 - e1 * f0);   // exact: products of dyadic numbers
+    const R rs = rule_s<R>(q), rt = rule_t<R>(q);
+    s = (R)P.a0 + rs * e0 + rt * f0;
+    t = (R)P.a1 + rs * e1 + rt * f1;
+    w = rule_w<R>(q) * det;
 }
 
 // float64 subdivision decision in the oracle's operation order: true when
 // the piece must be split.
 template <int NPE>
-__device__ __forceinline__ bool must_split(const double *X, const double xi[3], double tau, int maxdepth,
+__device__ __noinline__ bool must_split(const double *X, const double xi[3], double tau, int maxdepth,
                                            const PieceF &P) {
     if (P.depth >= maxdepth) return false;
     double N[6], xa[3], xb[3], xc[3], xm[3];
@@ -450,27 +541,21 @@ __device__ __forceinline__ void split4(const PieceF &P, PieceF out[4]) {
     out[3] = {ab0, ab1, bc0, bc1, ca0, ca1, d};
 }
 
-template <class R, bool HELM, int NPE>
-__device__ __forceinline__ void leaf7(const R *d, R kk, const PieceF &P, R (&acc)[5][NPE]) {
-    const double det = fabs(((double)P.b0 - P.a0) * ((double)P.c1 - P.a1) - ((double)P.b1 - P.a1) * ((double)P.c0 - P.a0));
-    for (int q = 0; q < NQ; q++) {
-        const double ps = P.a0 + c_rule.s[q] * ((double)P.b0 - P.a0) + c_rule.t[q] * ((double)P.c0 - P.a0);
-        const double pt = P.a1 + c_rule.s[q] * ((double)P.b1 - P.a1) + c_rule.t[q] * ((double)P.c1 - P.a1);
-        acc_local<R, HELM, NPE>(d, kk, (R)ps, (R)pt, (R)(c_rule.w[q] * det), acc);
-    }
-}
-
-// serial depth-first refinement of one piece (queue overflow path)
+// serial depth-first refinement of one piece on one lane (queue overflow path)
 template <class R, bool HELM, int NPE>
 __device__ void refine_serial(const double *X, const double xi[3], const R *d, const float *df, R kk, double tau,
-                              int maxdepth, PieceF root, R (&acc)[5][NPE]) {
+                              int maxdepth, PieceF root, R (&v)[sp_nvp(HELM, NPE)]) {
     PieceF st[3 * 10 + 4];
     int sp = 0;
     st[sp++] = root;
     while (sp > 0) {
         const PieceF P = st[--sp];
         if (!must_split_fast<NPE>(df, X, xi, tau, maxdepth, P)) {
-            leaf7<R, HELM, NPE>(d, kk, P, acc);
+            for (int q = 0; q < NQ; q++) {
+                R s, t, w;
+                leaf_point<R>(P, q, s, t, w);
+                eval_st<R, HELM, NPE>(d, kk, s, t, w, v);
+            }
             continue;
         }
         PieceF ch[4];
@@ -480,123 +565,157 @@ __device__ void refine_serial(const double *X, const double xi[3], const R *d, c
 }
 
 template <class R, bool HELM, int NPE>
-__global__ void __launch_bounds__(32 * SW_WARPS) k_special_warp(CorrArgs a, int npairs, const int *__restrict__ pair_node,
+__global__ void __launch_bounds__(32 * SP_WARPS, 4) k_special_pair(CorrArgs a, int npairs, const int *__restrict__ pair_node,
                                                                 const int *__restrict__ pair_e, double *valD,
                                                                 double *valS, double *d0pair) {
-    __shared__ PieceF q[SW_WARPS][2][SW_CAP];
-    __shared__ double sX[SW_WARPS][18];
-    __shared__ R sd[SW_WARPS][18];
-    __shared__ float sdf[SW_WARPS][18];
+    constexpr int C = HELM ? 2 : 1;
+    constexpr unsigned FULL = 0xffffffffu;
+    __shared__ uint4 qbuf[SP_WARPS][2][SP_QCAP];
+    __shared__ R ring[SP_WARPS][3][SP_RING];
+    __shared__ double sX[SP_WARPS][18];
+    __shared__ R sd[SP_WARPS][18];
+    __shared__ float sdf[SP_WARPS][18];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int pr = blockIdx.x * SW_WARPS + warp;
-    if (pr >= npairs) return;                       // uniform within the warp
-    const int node = pair_node[pr], e = pair_e[pr];
-    const double xi[3] = {a.nodes[3 * (size_t)node], a.nodes[3 * (size_t)node + 1], a.nodes[3 * (size_t)node + 2]};
-    if (lane < 3 * NPE) {
-        const int v = lane / 3, c = lane % 3;
-        const double xv = a.nodes[3 * (size_t)a.el_phi[(size_t)e * NPE + v] + c];
-        sX[warp][lane] = xv;
-        sd[warp][lane] = (R)(xv - xi[c]);
-        sdf[warp][lane] = (float)(xv - xi[c]);
-    }
-    __syncwarp();
+    const unsigned lt = (1u << lane) - 1u;
+    R *rs = ring[warp][0], *rt = ring[warp][1], *rw = ring[warp][2];
     const double *X = sX[warp];
     const R *d = sd[warp];
     const float *df = sdf[warp];
     const R kk = (R)a.k;
-    int as = -1;
-    for (int v = 0; v < NPE; v++)
-        if (a.el_phi[(size_t)e * NPE + v] == node) as = v;
-    R acc[5][NPE];
-#pragma unroll
-    for (int j = 0; j < 5; j++)
-#pragma unroll
-        for (int v = 0; v < NPE; v++) acc[j][v] = 0;
-    // minus the regular 7-point rule
-    if (lane < NQ) acc_local<R, HELM, NPE>(d, kk, (R)c_rule.s[lane], (R)c_rule.t[lane], (R)(-c_rule.w[lane]), acc);
-    if (as >= 0) {
-        // self element: Duffy rule collapsed at the singular node, split at a mid-side node
-        const double c0[2] = {0.0, 0.0}, c1[2] = {1.0, 0.0}, c2[2] = {0.0, 1.0};
-        const double mm[3][2] = {{0.5, 0.0}, {0.5, 0.5}, {0.0, 0.5}};
-        const int nsub = as < 3 ? 1 : 2, nd = a.nd, per = nd * nd;
-        for (int j = lane; j < nsub * per; j += 32) {
-            const int sub = j / per, rem = j - sub * per, iu = rem / nd, iv = rem - iu * nd;
-            const double *P, *Q1, *Q2;
-            switch (as) {
-            case 0: P = c0; Q1 = c1; Q2 = c2; break;
-            case 1: P = c1; Q1 = c2; Q2 = c0; break;
-            case 2: P = c2; Q1 = c0; Q2 = c1; break;
-            case 3: P = mm[0]; Q1 = sub ? c2 : c1; Q2 = sub ? c0 : c2; break;
-            case 4: P = mm[1]; Q1 = sub ? c0 : c2; Q2 = sub ? c1 : c0; break;
-            default: P = mm[2]; Q1 = sub ? c1 : c0; Q2 = sub ? c2 : c1; break;
-            }
-            const double det = fabs((Q1[0] - P[0]) * (Q2[1] - P[1]) - (Q1[1] - P[1]) * (Q2[0] - P[0]));
-            const int go = nd * (nd - 1) / 2;
-            const double u = 0.5 * (1.0 + c_glx[go + iu]), wu = 0.5 * c_glw[go + iu];
-            const double v = 0.5 * (1.0 + c_glx[go + iv]), wv = 0.5 * c_glw[go + iv];
-            const double s = P[0] + u * (Q1[0] - P[0]) + u * v * (Q2[0] - Q1[0]);
-            const double t = P[1] + u * (Q1[1] - P[1]) + u * v * (Q2[1] - Q1[1]);
-            acc_local<R, HELM, NPE>(d, kk, (R)s, (R)t, (R)(wu * wv * u * det), acc);
+    for (int pr = blockIdx.x * SP_WARPS + warp; pr < npairs; pr += gridDim.x * SP_WARPS) {
+        const int node = pair_node[pr], e = pair_e[pr];
+        const double xi[3] = {a.nodes[3 * (size_t)node], a.nodes[3 * (size_t)node + 1], a.nodes[3 * (size_t)node + 2]};
+        __syncwarp();                                   // the previous pair's reads of the tables are done
+        int vid = -1;
+        if (lane < 3 * NPE) {
+            const int c = lane % 3;
+            vid = a.el_phi[(size_t)e * NPE + lane / 3];
+            const double xv = a.nodes[3 * (size_t)vid + c];
+            sX[warp][lane] = xv;
+            sd[warp][lane] = (R)(xv - xi[c]);
+            sdf[warp][lane] = (float)(xv - xi[c]);
         }
-    } else {
-        // near-singular element: level-synchronous 4-way refinement
-        PieceF *cur = q[warp][0], *nxt = q[warp][1];
-        int ncur = 1;
-        if (lane == 0) cur[0] = {0.f, 0.f, 1.f, 0.f, 0.f, 1.f, 0};
+        const unsigned sing = __ballot_sync(FULL, vid == node && lane % 3 == 0);
+        const int as = sing ? (__ffs(sing) - 1) / 3 : -1;
         __syncwarp();
-        while (ncur > 0) {
-            int nnext = 0;
-            for (int base = 0; base < ncur; base += 32) {
-                const int i = base + lane;
-                PieceF P = {};
-                bool split = false;
-                if (i < ncur) {
-                    P = cur[i];
-                    split = must_split_fast<NPE>(df, X, xi, a.tau, a.maxdepth, P);
+        constexpr int NVP = sp_nvp(HELM, NPE);
+        R v[NVP];
+#pragma unroll
+        for (int i = 0; i < NVP; i++) v[i] = 0;
+        if (as >= 0) {
+            // self element: Duffy rule collapsed at the node (split at a mid-side
+            // node), then the regular rule subtracted, all by point index
+            const R p0 = as == 1 || as == 3 || as == 4 ? (R)(as == 1 ? 1 : 0.5) : (R)0;
+            const R p1 = as == 2 || as == 4 || as == 5 ? (R)(as == 2 ? 1 : 0.5) : (R)0;
+            R NP[NPE], NsP[NPE], NtP[NPE];
+            shape_all<R, NPE>(p0, p1, NP, NsP, NtP);
+            const int nsub = as < 3 ? 1 : 2, nd = a.nd, per = nd * nd, go = nd * (nd - 1) / 2;
+            const int nduffy = nsub * per;
+            for (int j = lane; j < nduffy + NQ; j += 32) {
+                if (j >= nduffy) {
+                    const int q = j - nduffy;
+                    eval_st<R, HELM, NPE>(d, kk, rule_s<R>(q), rule_t<R>(q), -rule_w<R>(q), v);
+                    continue;
                 }
-                const unsigned m = __ballot_sync(0xffffffffu, split);
-                const int pos = nnext + 4 * __popc(m & ((1u << lane) - 1u));
-                if (i < ncur) {
-                    if (!split) {
-                        leaf7<R, HELM, NPE>(d, kk, P, acc);
-                    } else if (pos + 4 <= SW_CAP) {
-                        PieceF ch[4];
-                        split4(P, ch);
-                        for (int c = 0; c < 4; c++) nxt[pos + c] = ch[c];
-                    } else {
-                        refine_serial<R, HELM, NPE>(X, xi, d, df, kk, a.tau, a.maxdepth, P, acc);
-                    }
-                }
-                nnext = min(SW_CAP, nnext + 4 * __popc(m));
-                nnext -= (nnext % 4);
+                const int sub = j / per, rem = j - sub * per, iu = rem / nd, iv = rem - iu * nd;
+                // the sub-triangle (P, Q1, Q2): Q1, Q2 the corners (r+1) mod 3 and
+                // (r+2) mod 3 of the reference triangle, corners 0 (0,0), 1 (1,0), 2 (0,1)
+                const int r = as < 3 ? as : (as - 3 + sub) % 3, k1 = (r + 1) % 3, k2 = (r + 2) % 3;
+                const R q10 = (R)(k1 == 1), q11 = (R)(k1 == 2), q20 = (R)(k2 == 1), q21 = (R)(k2 == 2);
+                const R det = fabs((q10 - p0) * (q21 - p1) - (q11 - p1) * (q20 - p0));
+                R u, wu, w2, wv;
+                gl01<R>(go + iu, u, wu);
+                gl01<R>(go + iv, w2, wv);
+                const R uv = u * w2;
+                const R ds = u * (q10 - p0) + uv * (q20 - q10);
+                const R dt = u * (q11 - p1) + uv * (q21 - q11);
+                R N[NPE], Ns[NPE], Nt[NPE];
+                shape_all<R, NPE>(p0 + ds, p1 + dt, N, Ns, Nt);
+#pragma unroll
+                for (int b = 0; b < NPE; b++)
+                    N[b] = (b == as ? (R)1 : (R)0) + (R)0.5 * ((NsP[b] + Ns[b]) * ds + (NtP[b] + Nt[b]) * dt);
+                point_acc<R, HELM, NPE>(d, kk, N, Ns, Nt, wu * wv * u * det, v);
             }
+        } else {
+            // near-singular element: the regular rule with negative weights,
+            // then the leaf pieces of a level-synchronous 4-way refinement
+            if (lane < NQ) { rs[lane] = rule_s<R>(lane); rt[lane] = rule_t<R>(lane); rw[lane] = -rule_w<R>(lane); }
+            int head = 0, tail = NQ;
+            uint4 *cur = qbuf[warp][0], *nxt = qbuf[warp][1];
+            int ncur = 1;
+            if (lane == 0) cur[0] = pack_piece(PieceF{0.f, 0.f, 1.f, 0.f, 0.f, 1.f, 0});
             __syncwarp();
-            PieceF *sw = cur; cur = nxt; nxt = sw;
-            ncur = nnext;
-        }
-    }
-    // warp sums
+            while (ncur > 0) {
+                int nnext = 0;
+                for (int base = 0; base < ncur; base += 32) {
+                    const int i = base + lane;
+                    PieceF P = {};
+                    bool split = false, leaf = false;
+                    if (i < ncur) {
+                        P = unpack_piece(cur[i]);
+                        split = must_split_fast<NPE>(df, X, xi, a.tau, a.maxdepth, P);
+                        leaf = !split;
+                    }
+                    const unsigned ms = __ballot_sync(FULL, split), ml = __ballot_sync(FULL, leaf);
+                    if (split) {
+                        const int pos = nnext + 4 * __popc(ms & lt);
+                        if (pos + 4 <= SP_QCAP) {
+                            PieceF ch[4];
+                            split4(P, ch);
 #pragma unroll
-    for (int j = 0; j < 5; j++) {
-        if (!HELM && (j == 1 || j == 3)) continue;
+                            for (int c = 0; c < 4; c++) nxt[pos + c] = pack_piece(ch[c]);
+                        } else {
+                            refine_serial<R, HELM, NPE>(X, xi, d, df, kk, a.tau, a.maxdepth, P, v);
+                        }
+                    }
+                    if (leaf) {
+                        const int p0 = tail + NQ * __popc(ml & lt);
 #pragma unroll
-        for (int v = 0; v < NPE; v++)
-            for (int off = 16; off; off >>= 1) acc[j][v] += __shfl_xor_sync(0xffffffffu, acc[j][v], off);
-    }
-    if (lane == 0) {
-        const int C = HELM ? 2 : 1;
-        double d0 = 0.0;
-        for (int v = 0; v < NPE; v++) {
-            const size_t o = ((size_t)pr * NPE + v) * C;
-            valS[o] = (double)acc[0][v];
-            valD[o] = (double)acc[2][v];
-            if (HELM) {
-                valS[o + 1] = (double)acc[1][v];
-                valD[o + 1] = (double)acc[3][v];
+                        for (int q = 0; q < NQ; q++) {
+                            R s, t, w;
+                            leaf_point<R>(P, q, s, t, w);
+                            const int k = (p0 + q) & (SP_RING - 1);
+                            rs[k] = s; rt[k] = t; rw[k] = w;
+                        }
+                    }
+                    tail += NQ * __popc(ml);
+                    nnext = min(SP_QCAP, nnext + 4 * __popc(ms));
+                    nnext -= nnext % 4;
+                    __syncwarp();
+                    for (; tail - head >= 32; head += 32) {
+                        const int k = (head + lane) & (SP_RING - 1);
+                        eval_st<R, HELM, NPE>(d, kk, rs[k], rt[k], rw[k], v);
+                    }
+                    __syncwarp();                       // ring reads done before the next writes
+                }
+                uint4 *sw = cur; cur = nxt; nxt = sw;
+                ncur = nnext;
             }
-            d0 += (double)acc[4][v];
+            if (head + lane < tail) {
+                const int k = (head + lane) & (SP_RING - 1);
+                eval_st<R, HELM, NPE>(d, kk, rs[k], rt[k], rw[k], v);
+            }
         }
-        d0pair[pr] = d0;
+        // transposing butterfly: after the step of width k a lane keeps the
+        // half of its values selected by bit k of its index, so value l of
+        // the pair ends on lane l (with 16 values, a plain step across the
+        // half-warps comes first and lanes l and l + 16 both hold value l)
+        if (NVP == 16) {
+#pragma unroll
+            for (int i = 0; i < NVP; i++) v[i] += __shfl_xor_sync(FULL, v[i], 16);
+        }
+#pragma unroll
+        for (int k = NVP / 2; k >= 1; k >>= 1) {
+            const bool up = (lane & k) != 0;
+#pragma unroll
+            for (int i = 0; i < k; i++) {
+                const R lo = v[i], hi = v[i + k];
+                v[i] = (up ? hi : lo) + __shfl_xor_sync(FULL, up ? lo : hi, k);
+            }
+        }
+        if (lane < NPE * C) valS[(size_t)pr * NPE * C + lane] = (double)v[0];
+        else if (lane < 2 * NPE * C) valD[(size_t)pr * NPE * C + lane - NPE * C] = (double)v[0];
+        else if (lane == 2 * NPE * C) d0pair[pr] = (double)v[0];
     }
 }
 
@@ -643,11 +762,16 @@ int build_correction(bem_plan *P, cudaStream_t s) {
     const int N = (int)P->N, E = (int)P->E, npe = P->npe;
     double *ecx, *ecy, *ecz, *eh, *rho;
     BEM_TRY(A.alloc(&ecx, E)); BEM_TRY(A.alloc(&ecy, E)); BEM_TRY(A.alloc(&ecz, E)); BEM_TRY(A.alloc(&eh, E));
+    float4 *ebnd;
+    BEM_TRY(A.alloc(&ebnd, E));
     BEM_TRY(A.alloc(&rho, t.nbox));
-    (k_elem_centroid<<<(E + 255) / 256, 256, 0, s>>>(E, npe, t.el_phi, P->nodes, ecx, ecy, ecz, eh), ::bem::count_launch());
+    (k_elem_centroid<<<(E + 255) / 256, 256, 0, s>>>(E, npe, P->prm.tau_near, t.el_phi, P->nodes, ecx, ecy, ecz, eh, ebnd),
+     ::bem::count_launch());
     CorrArgs a{N, E, npe, P->green, P->prm.n_duffy, P->prm.max_subdiv, P->k, P->prm.tau_near, P->nodes,
-               t.el_phi, t.el_chi, ecx, ecy, ecz, eh, t.cx, t.cy, t.cz, rho, t.child0, t.nchild, t.eb, t.ee};
-    (k_box_search_radius<<<t.nbox, 256, 0, s>>>(a, t.nbox, rho), ::bem::count_launch());
+               t.el_phi, t.el_chi, ecx, ecy, ecz, eh, ebnd, t.cx, t.cy, t.cz, rho, t.child0, t.nchild, t.eb, t.ee};
+    BEM_CUDA(cudaMemsetAsync(rho, 0, sizeof(double) * t.nbox, s));
+    (k_elem_search_radius<<<(E + 255) / 256, 256, 0, s>>>(a, t.leaf_of_node, t.parent, (unsigned long long *)rho),
+     ::bem::count_launch());
     BEM_LAUNCH_CHECK();
     int *cnt, *off, *tot;
     BEM_TRY(A.alloc(&cnt, N + 1));
@@ -681,9 +805,16 @@ int build_correction(bem_plan *P, cudaStream_t s) {
     (k_rows_ptr<<<(N + 256) / 256, 256, 0, s>>>(N, npe, off, K.ptrD), ::bem::count_launch());
     (k_corr_csr<<<(npairs + 255) / 256, 256, 0, s>>>(npairs, npe, pair_e, t.el_phi, t.el_chi, K.colD, K.colS), ::bem::count_launch());
     {
-        const int blocks = (npairs + SW_WARPS - 1) / SW_WARPS;
         const bool mx = P->prm.precision == BEM_MIXED, helm = P->green == BEM_HELMHOLTZ;
-#define BEM_SW(R, H, NP) (k_special_warp<R, H, NP><<<blocks, 32 * SW_WARPS, 0, s>>>(a, npairs, pair_node, pair_e, K.valD, K.valS, d0pair), ::bem::count_launch())
+        // a grid-stride loop over pairs: as many blocks as fit on the device at once
+        auto grid_of = [&](const void *fn) {
+            int per_sm = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * SP_WARPS, 0) != cudaSuccess || per_sm < 1)
+                per_sm = 1;
+            const long long want = ((long long)npairs + SP_WARPS - 1) / SP_WARPS;
+            return (int)std::max(1LL, std::min(want, (long long)per_sm * std::max(1, P->sm_count)));
+        };
+#define BEM_SW(R, H, NP) (k_special_pair<R, H, NP><<<grid_of((const void *)k_special_pair<R, H, NP>), 32 * SP_WARPS, 0, s>>>(a, npairs, pair_node, pair_e, K.valD, K.valS, d0pair), ::bem::count_launch())
         if (npairs > 0) {
             if (npe == 3) {
                 if (mx) { if (helm) BEM_SW(float, true, 3); else BEM_SW(float, false, 3); }
@@ -708,7 +839,7 @@ int build_correction(bem_plan *P, cudaStream_t s) {
     P->C = d0row;
     BEM_CUDA(cudaStreamSynchronize(s));
     A.release(cnt); A.release(tot); A.release(pair_node); A.release(d0pair);
-    A.release(ecx); A.release(ecy); A.release(ecz); A.release(eh); A.release(rho); A.release(off);
+    A.release(ecx); A.release(ecy); A.release(ecz); A.release(eh); A.release(ebnd); A.release(rho); A.release(off);
     A.release(pair_e);
     return BEM_OK;
 }
