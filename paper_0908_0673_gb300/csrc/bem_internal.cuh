@@ -190,32 +190,28 @@ struct bem_plan {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     long long graph_kernels[2] = {0, 0};
     cudaStream_t capture_stream = nullptr;
-    // translation tables (translate.cu)
-    int *ctr_ptr = nullptr, *ctr_ag = nullptr, *ctr_beta = nullptr, *m_deg = nullptr;
-    double *m_sgnf = nullptr, *m_invf = nullptr;
-    int *m2l_cls = nullptr, *cls_dl = nullptr, m2l_ncls = 0;
-    double *cls_rho = nullptr, *cls_kh = nullptr;
-    double *m2l_D = nullptr;            // [class][np] derivative tables (x2 complex)
-    float *m2l_fD = nullptr;
-    // float32 class-major M2L (translate.cu)
-    int cm_ntile = 0, cm_nunits = 0;
-    int *cm_order = nullptr, *cm_tile_cls = nullptr, *cm_tile_start = nullptr, *cm_tile_cnt = nullptr;
-    int *cm_ur0 = nullptr, *cm_ua0 = nullptr, *cm_rtp = nullptr, *cm_gidx = nullptr;
-    float *cm_Lp = nullptr;             // [interaction pair][np] per-pair local contributions
-    // symmetry-reduced tensor-core M2L (m2l_tc.cu)
-    int sy_ncls = 0, sy_ntile = 0, sy_on = 0, sy_ldp = 0, sy_nkc = 0;
+    // M2L on canonical offset classes (m2l_tc.cu: tensor-core form and tables;
+    // m2l_simt.cu: SIMT form)
+    int sy_ncls = 0, sy_ntile = 0, sy_ldp = 0, sy_nkc = 0;
+    int sy_ready = 0;                   // order-dependent tables built for the current order
+    int sy_tc = 0;                      // the tensor-core form runs (mixed-precision Laplace)
     double *sy_rho = nullptr;           // [class][3] canonical offsets / h_t
+    double *sy_kh = nullptr;            // [class] k h_t (Helmholtz)
     int *sy_dl = nullptr;               // [class] level difference
     int *sy_tile_cls = nullptr, *sy_tile_start = nullptr, *sy_tile_cnt = nullptr;
     int *sy_src = nullptr, *sy_sig = nullptr, *sy_pair = nullptr;   // pairs in class order
     int *sy_sig_u = nullptr;            // [pair] symmetry id (permutation * 8 + sign bits)
-    double *sy_D = nullptr;             // [class][np] derivative tables
+    std::vector<int> sy_hcls, sy_hsig, sy_hsrc, sy_hip;   // host: per pair class, symmetry, source; list offsets
+    std::vector<int> sy_bt, sy_bb, sy_bu;                 // host: per run, first tile, target and pair (size runs + 1)
+    double *sy_D = nullptr;             // [class][np][C] derivative tables
     float *sy_fD = nullptr;
     unsigned short *sy_fwd = nullptr;   // [48][np] signed index maps (sign in bit 15)
     int *sy_inv = nullptr;              // [48][np] signed index maps (sign in bit 31)
+    int *sy_mexp = nullptr;             // [np] exponents m | n << 8 | k << 16 | degree << 24
+    double *sy_invf = nullptr;          // [np] 1 / a!
     int *sy_tidx = nullptr;             // class-matrix gather table (shared-memory layout)
     float *sy_tfac = nullptr;
-    float *sy_Lp = nullptr;             // [pair][sy_ldp] canonical-frame local contributions
+    void *sy_Lp = nullptr;              // [pair][sy_ldp][C] canonical-frame local contributions
     uint4 *sy_sched = nullptr;          // MMA schedule of a tile
     int *sy_sched_ptr = nullptr, sy_nsched = 0;
     bem::TcGroups sy_g;
@@ -249,11 +245,16 @@ int build_translation_tables(bem_plan *P, cudaStream_t s);
 void free_translation_tables(bem_plan *P);
 void set_translation_attributes();
 int build_m2l_sym(bem_plan *P, const std::vector<int> &pair_cls, const std::vector<long long> &kvec,
-                  const std::vector<int> &dls, const std::vector<int> &src);
-int build_tc_tables(bem_plan *P, cudaStream_t s);
-void free_tc_tables(bem_plan *P);
+                  const std::vector<int> &dls, const std::vector<int> &levs, const std::vector<int> &src,
+                  const std::vector<int> &ip);
+int build_sym_tables(bem_plan *P, cudaStream_t s);
+void free_sym_tables(bem_plan *P);
 int launch_m2l_tc(bem_plan *P, const float *M, float *L, cudaStream_t s);
 void set_tc_attributes();
+template <class R, int C>
+int launch_m2l_sy(bem_plan *P, const R *M, R *L, cudaStream_t s);
+size_t sy_simt_smem_bytes(int prec_float, int C, int np, int p);
+void set_sy_attributes();
 int launch_m2l_derivs(bem_plan *P, int ncls, const double *rho, const double *kh, double *D, float *fD,
                       cudaStream_t s);
 template <class R, int C>

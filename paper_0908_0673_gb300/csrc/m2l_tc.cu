@@ -57,8 +57,8 @@ struct TcArgs {
     const float *tfac, *fD, *M;
     const uint4 *sched;                 // MMA schedule: {T offset, sbo, idesc, dcol | ks << 16 | acc << 31}
     const int *sched_ptr;               // [nkc + 1] schedule entries of each chunk
-    float *Lp;
-    int ldp;
+    float *Lp;                          // rows of this run's pairs, row u - u0
+    int ldp, u0;
     int *err;
     const int *skip;
 };
@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(TC_T, 1) k_m2l_tc(const __grid_constant__ TcAr
                 float v[32];
                 tc::tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * c), v);
                 if (u >= 0) {
-                    float4 *dst = (float4 *)(a.Lp + (size_t)u * a.ldp + 32 * c);
+                    float4 *dst = (float4 *)(a.Lp + (size_t)(u - a.u0) * a.ldp + 32 * c);
 #pragma unroll
                     for (int i = 0; i < 8; i++) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
                 }
@@ -322,14 +322,14 @@ __global__ void __launch_bounds__(TC_T, 1) k_m2l_tc(const __grid_constant__ TcAr
 // L_t[b] = (1 / h_t) sum over t's interaction list, in list order, of
 // sign * Lhat_u[b o pi_u^-1]; one thread per row b, eight rows of Lhat in flight
 constexpr int GA_LIST = 512;            // list entries staged per pass
-__global__ void __launch_bounds__(512) k_m2l_gather_sym(int nbox, const int *__restrict__ level, double side,
-                                                        const int *__restrict__ inter_ptr, int np, int ldp,
+__global__ void __launch_bounds__(512) k_m2l_gather_sym(int t0, int nbox, const int *__restrict__ level, double side,
+                                                        const int *__restrict__ inter_ptr, int u0r, int np, int ldp,
                                                         const int *__restrict__ sig_u, const int *__restrict__ inv,
                                                         const float *__restrict__ Lp, float *__restrict__ L,
                                                         const int *__restrict__ skip) {
     if (skip && *skip) return;
     __shared__ int sOff[GA_LIST];          // sig * np of every staged pair
-    const int t = blockIdx.x, b = threadIdx.x;
+    const int t = t0 + blockIdx.x, b = threadIdx.x;
     if (t >= nbox) return;
     const float sc = (float)(1.0 / scalbn(side, -level[t]));
     const int u0 = inter_ptr[t], u1 = inter_ptr[t + 1];
@@ -347,13 +347,13 @@ __global__ void __launch_bounds__(512) k_m2l_gather_sym(int nbox, const int *__r
 #pragma unroll
                 for (int q = 0; q < 8; q++) f[q] = __ldg(inv + sOff[i + q] + b);
 #pragma unroll
-                for (int q = 0; q < 8; q++) v[q] = Lp[(size_t)(base + i + q) * ldp + (f[q] & 0x7fffffff)];
+                for (int q = 0; q < 8; q++) v[q] = Lp[(size_t)(base + i + q - u0r) * ldp + (f[q] & 0x7fffffff)];
 #pragma unroll
                 for (int q = 0; q < 8; q++) sum += f[q] < 0 ? -v[q] : v[q];
             }
             for (; i < n; i++) {
                 const int f = __ldg(inv + sOff[i] + b);
-                const float v = Lp[(size_t)(base + i) * ldp + (f & 0x7fffffff)];
+                const float v = Lp[(size_t)(base + i - u0r) * ldp + (f & 0x7fffffff)];
                 sum += f < 0 ? -v : v;
             }
         }
@@ -368,14 +368,17 @@ __global__ void __launch_bounds__(512) k_m2l_gather_sym(int nbox, const int *__r
 // the exact offset classes (integer offset vector, level difference)
 // ---------------------------------------------------------------------------
 int build_m2l_sym(bem_plan *P, const std::vector<int> &pair_cls, const std::vector<long long> &kvec,
-                  const std::vector<int> &dls, const std::vector<int> &src) {
+                  const std::vector<int> &dls, const std::vector<int> &levs, const std::vector<int> &src,
+                  const std::vector<int> &ip) {
     const int64_t npair = P->t.n_inter;
     const int nfull = (int)dls.size();
     // every exact offset class maps to one canonical class and one symmetry
+    // key: level difference, target level (Helmholtz: the derivatives depend
+    // on k h_t; zero for Laplace), sorted absolute offset components
     struct Key {
-        long long v[4];
+        long long v[5];
         bool operator<(const Key &o) const {
-            for (int i = 0; i < 4; i++)
+            for (int i = 0; i < 5; i++)
                 if (v[i] != o.v[i]) return v[i] < o.v[i];
             return false;
         }
@@ -391,51 +394,41 @@ int build_m2l_sym(bem_plan *P, const std::vector<int> &pair_cls, const std::vect
         int q = 0;
         while (!(PERMS[q][0] == pi[0] && PERMS[q][1] == pi[1] && PERMS[q][2] == pi[2])) q++;
         fsig[c] = q * 8 + ((K[0] < 0 ? 1 : 0) | (K[1] < 0 ? 2 : 0) | (K[2] < 0 ? 4 : 0));
-        fkey[c] = Key{{(long long)dls[c], std::llabs(K[order[0]]), std::llabs(K[order[1]]), std::llabs(K[order[2]])}};
+        fkey[c] = Key{{(long long)dls[c], (long long)levs[c], std::llabs(K[order[0]]), std::llabs(K[order[1]]),
+                       std::llabs(K[order[2]])}};
     }
     std::vector<int> fidx(nfull);
     for (int c = 0; c < nfull; c++) fidx[c] = c;
     std::sort(fidx.begin(), fidx.end(), [&](int x, int y) { return fkey[x] < fkey[y] || (!(fkey[y] < fkey[x]) && x < y); });
     std::vector<int> fcan(nfull), dlc;
-    std::vector<double> rho;
+    std::vector<double> rho, khc;
+    const bool helm = P->green == BEM_HELMHOLTZ;
     int nc = 0;
     for (int i = 0; i < nfull; i++) {
         const Key &k = fkey[fidx[i]];
         if (i == 0 || fkey[fidx[i - 1]] < k) {
             const int dl = (int)k.v[0], e = std::max(0, -dl);
             const double sc = std::ldexp(1.0, -(e + 1));
-            rho.push_back(k.v[1] * sc);
             rho.push_back(k.v[2] * sc);
             rho.push_back(k.v[3] * sc);
+            rho.push_back(k.v[4] * sc);
+            khc.push_back(helm ? P->k * std::ldexp(P->t.side, -(int)k.v[1]) : 0.0);
             dlc.push_back(dl);
             nc++;
         }
         fcan[fidx[i]] = nc - 1;
     }
-    // pairs sorted by canonical class (counting sort, stable in pair order)
-    std::vector<int> start(nc + 1, 0), sig_u(std::max<int64_t>(1, npair), 0);
+    // per pair (list order): canonical class, symmetry, source box; the tiles
+    // are cut per order (build_sym_tables), when the row size is known
+    P->sy_hcls.assign(npair, 0);
+    P->sy_hsig.assign(npair, 0);
+    P->sy_hsrc.assign(src.begin(), src.begin() + npair);
+    P->sy_hip = ip;
     for (int64_t u = 0; u < npair; u++) {
-        start[fcan[pair_cls[u]] + 1]++;
-        sig_u[u] = fsig[pair_cls[u]];
+        P->sy_hcls[u] = fcan[pair_cls[u]];
+        P->sy_hsig[u] = fsig[pair_cls[u]];
     }
-    for (int c = 0; c < nc; c++) start[c + 1] += start[c];
-    std::vector<int> fill(start.begin(), start.end() - 1), psrc(std::max<int64_t>(1, npair)),
-        psig(std::max<int64_t>(1, npair)), pu(std::max<int64_t>(1, npair));
-    for (int64_t u = 0; u < npair; u++) {
-        const int i = fill[fcan[pair_cls[u]]]++;
-        psrc[i] = src[u];
-        psig[i] = sig_u[u];
-        pu[i] = (int)u;
-    }
-    std::vector<int> tcls, tst, tcnt;
-    for (int c = 0; c < nc; c++)
-        for (int k = start[c]; k < start[c + 1]; k += TC_M) {
-            tcls.push_back(c);
-            tst.push_back(k);
-            tcnt.push_back(std::min(TC_M, start[c + 1] - k));
-        }
     P->sy_ncls = nc;
-    P->sy_ntile = (int)tcls.size();
     Arena &A = P->arena;
     auto up = [&](auto **d, const auto &h) -> int {
         using T = std::decay_t<decltype(h[0])>;
@@ -444,14 +437,73 @@ int build_m2l_sym(bem_plan *P, const std::vector<int> &pair_cls, const std::vect
         return BEM_OK;
     };
     BEM_TRY(up(&P->sy_rho, rho));
+    BEM_TRY(up(&P->sy_kh, khc));
     BEM_TRY(up(&P->sy_dl, dlc));
+    BEM_TRY(up(&P->sy_sig_u, P->sy_hsig));
+    return BEM_OK;
+}
+
+// Batches and tiles for rows of row_bytes: the targets are cut into runs whose
+// interaction lists hold at most SY_LP_BYTES of rows together (a run holds at
+// least one whole list), and within a run the pairs are sorted by canonical
+// class (counting sort, stable in list order) and cut into tiles of up to
+// 128 pairs of one class.  Each run's rows are computed into the same buffer
+// and gathered before the next run starts, so the buffer is bounded however
+// large the mesh, and every target's sum keeps its list order.
+constexpr size_t SY_LP_BYTES = (size_t)128 << 20;
+
+static int build_sym_tiles(bem_plan *P, size_t row_bytes, int64_t &max_rows) {
+    const int nbox = P->t.nbox, nc = P->sy_ncls;
+    const std::vector<int> &ip = P->sy_hip;
+    const int64_t npair = P->t.n_inter;
+    int64_t longest = 0;
+    for (int b = 0; b < nbox; b++) longest = std::max<int64_t>(longest, ip[b + 1] - ip[b]);
+    const int64_t cap = std::max<int64_t>(std::max<int64_t>(1, longest), (int64_t)(SY_LP_BYTES / row_bytes));
+    std::vector<int> psrc(std::max<int64_t>(1, npair)), psig(std::max<int64_t>(1, npair)),
+        pu(std::max<int64_t>(1, npair)), tcls, tst, tcnt, cnt(nc + 1);
+    P->sy_bt.assign(1, 0);
+    P->sy_bb.assign(1, 0);
+    P->sy_bu.assign(1, 0);
+    max_rows = 0;
+    for (int t0 = 0; t0 < nbox;) {
+        int t1 = t0 + 1;
+        while (t1 < nbox && ip[t1 + 1] - ip[t0] <= cap) t1++;
+        const int u0 = ip[t0], u1 = ip[t1];
+        std::fill(cnt.begin(), cnt.end(), 0);
+        for (int u = u0; u < u1; u++) cnt[P->sy_hcls[u] + 1]++;
+        for (int c = 0; c < nc; c++) cnt[c + 1] += cnt[c];
+        for (int c = 0; c < nc; c++)
+            for (int k = cnt[c]; k < cnt[c + 1]; k += TC_M) {
+                tcls.push_back(c);
+                tst.push_back(u0 + k);
+                tcnt.push_back(std::min(TC_M, cnt[c + 1] - k));
+            }
+        for (int u = u0; u < u1; u++) {
+            const int i = u0 + cnt[P->sy_hcls[u]]++;
+            psrc[i] = P->sy_hsrc[u];
+            psig[i] = P->sy_hsig[u];
+            pu[i] = u;
+        }
+        P->sy_bt.push_back((int)tcls.size());
+        P->sy_bb.push_back(t1);
+        P->sy_bu.push_back(u1);
+        max_rows = std::max<int64_t>(max_rows, u1 - u0);
+        t0 = t1;
+    }
+    P->sy_ntile = (int)tcls.size();
+    Arena &A = P->arena;
+    auto up = [&](auto **d, const auto &h) -> int {
+        using T = std::decay_t<decltype(h[0])>;
+        BEM_TRY(A.alloc((T **)d, std::max<size_t>(1, h.size())));
+        if (!h.empty()) BEM_CUDA(cudaMemcpy(*d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice));
+        return BEM_OK;
+    };
     BEM_TRY(up(&P->sy_tile_cls, tcls));
     BEM_TRY(up(&P->sy_tile_start, tst));
     BEM_TRY(up(&P->sy_tile_cnt, tcnt));
     BEM_TRY(up(&P->sy_src, psrc));
     BEM_TRY(up(&P->sy_sig, psig));
     BEM_TRY(up(&P->sy_pair, pu));
-    BEM_TRY(up(&P->sy_sig_u, sig_u));
     return BEM_OK;
 }
 
@@ -461,22 +513,17 @@ int build_m2l_sym(bem_plan *P, const std::vector<int> &pair_cls, const std::vect
 // ---------------------------------------------------------------------------
 size_t tc_smem_bytes(const TcGroups &g, int ldp) { return tc_layout(g, ldp).total; }
 
-int build_tc_tables(bem_plan *P, cudaStream_t s) {
-    P->sy_on = 0;
-    const MIndex &mi = P->mi;
-    const int p = mi.p, np = mi.np, P1 = p + 1;
-    if (P->green != BEM_LAPLACE || P->prm.precision != BEM_MIXED || P->sy_ncls == 0 || P->t.n_inter == 0)
-        return BEM_OK;
-    auto idx = [&](int m, int n, int k) { return mi.idx3[((size_t)m * P1 + n) * P1 + k]; };
-    std::vector<int> deg(np);
-    std::vector<double> fact(2 * PMAX + 2);
-    fact[0] = 1.0;
-    for (int i = 1; i < (int)fact.size(); i++) fact[i] = fact[i - 1] * i;
-    for (int a = 0; a < np; a++) deg[a] = mi.m[a] + mi.n[a] + mi.k[a];
+// The TC tables of the current order, when the tensor-core form applies:
+// degree bands of the class matrix, its gather table in shared-memory layout
+// order, the MMA schedule.  Returns false (nothing allocated) when the order
+// does not fit the fixed band table, the schedule or shared memory.
+static bool tc_plan(const MIndex &mi, const std::vector<int> &deg, TcGroups &g, int &ldp, int &nkc,
+                    std::vector<uint4> &sched, std::vector<int> &sptr) {
+    const int p = mi.p, np = mi.np;
     // degree bands of rows b: K extent = columns a with |a| <= p - |b|, i.e.
     // the count of multi-indices of degree <= p - |b|
     auto cum = [](int d) { return d <= 0 ? 0 : d * (d + 1) * (d + 2) / 6; };
-    TcGroups g{};
+    g = TcGroups{};
     const int ncols = (np + 15) / 16 * 16;
     std::vector<int> bk;
     for (int b0 = 0; b0 < ncols; b0 += 16) {
@@ -488,7 +535,7 @@ int build_tc_tables(bem_plan *P, cudaStream_t s) {
     for (size_t i = 0; i < bk.size();) {
         size_t j = i;
         while (j < bk.size() && bk[j] == bk[i] && (int)(j - i + 1) * 16 <= 256) j++;
-        if (g.ng >= TC_MAXG) return BEM_OK;       // does not fit the fixed group table
+        if (g.ng >= TC_MAXG) return false;        // does not fit the fixed group table
         g.b0[g.ng] = (int)i * 16;
         g.n[g.ng] = (int)(j - i) * 16;
         g.k[g.ng] = bk[i];
@@ -500,14 +547,14 @@ int build_tc_tables(bem_plan *P, cudaStream_t s) {
         g.off[q] = g.tsize;
         g.tsize += g.n[q] * g.k[q];
     }
-    const int ldp = (ncols + 31) / 32 * 32;          // TMEM columns read back, 32 at a time
+    ldp = (ncols + 31) / 32 * 32;                 // TMEM columns read back, 32 at a time
     g.ncols = ldp;
     const int kmax = (g.k[0] + TC_KC - 1) / TC_KC * TC_KC;
-    const int nkc = kmax / TC_KC;
+    nkc = kmax / TC_KC;
     // MMA schedule: per chunk, every band whose K extent reaches into it,
     // 8 columns (one tf32 MMA) at a time
-    std::vector<uint4> sched;
-    std::vector<int> sptr(nkc + 1, 0);
+    sched.clear();
+    sptr.assign(nkc + 1, 0);
     for (int kc = 0; kc < nkc; kc++) {
         sptr[kc] = (int)sched.size();
         for (int q = 0; q < g.ng; q++) {
@@ -521,25 +568,33 @@ int build_tc_tables(bem_plan *P, cudaStream_t s) {
         }
     }
     sptr[nkc] = (int)sched.size();
-    if ((int)sched.size() > TC_MAXE) return BEM_OK;
-    if (tc_smem_bytes(g, ldp) > (size_t)TC_SMEM_MAX || ldp > 512) return BEM_OK;   // the SIMT form runs
-    // class-matrix gather table in shared-memory layout order
-    std::vector<int> tidx(g.tsize, -1);
-    std::vector<float> tfac(g.tsize, 0.f);
-    for (int q = 0; q < g.ng; q++)
-        for (int bl = 0; bl < g.n[q]; bl++)
-            for (int al = 0; al < g.k[q]; al++) {
-                const int b = g.b0[q] + bl, e = g.off[q] + (bl >> 3) * (g.k[q] / 4) * 32 + (al >> 2) * 32 +
-                                                (bl & 7) * 4 + (al & 3);
-                if (b < np && al < np && deg[b] + deg[al] <= p) {
-                    tidx[e] = idx(mi.m[al] + mi.m[b], mi.n[al] + mi.n[b], mi.k[al] + mi.k[b]) | (deg[al] << 16);
-                    const double fa = fact[mi.m[al]] * fact[mi.n[al]] * fact[mi.k[al]];
-                    const double fb = fact[mi.m[b]] * fact[mi.n[b]] * fact[mi.k[b]];
-                    tfac[e] = (float)(((deg[al] & 1) ? -1.0 : 1.0) / (fa * fb));
-                }
-            }
+    if ((int)sched.size() > TC_MAXE) return false;
+    return tc_smem_bytes(g, ldp) <= (size_t)TC_SMEM_MAX && ldp <= 512;
+}
+
+// Order-dependent tables of the M2L on canonical classes: symmetry maps,
+// exponent and factorial tables, derivative tables of the canonical classes,
+// the per-pair row buffer, and the tensor-core tables when that form applies
+// (mixed-precision Laplace at an order whose tables fit); else the SIMT form runs.
+int build_sym_tables(bem_plan *P, cudaStream_t s) {
+    P->sy_tc = 0;
+    P->sy_ready = 0;
+    const MIndex &mi = P->mi;
+    const int p = mi.p, np = mi.np, P1 = p + 1;
+    const int C = P->green == BEM_HELMHOLTZ ? 2 : 1;
+    const bool mx = P->prm.precision == BEM_MIXED;
+    auto idx = [&](int m, int n, int k) { return mi.idx3[((size_t)m * P1 + n) * P1 + k]; };
+    std::vector<int> deg(np), mexp(np);
+    std::vector<double> fact(2 * PMAX + 2), invf(np);
+    fact[0] = 1.0;
+    for (int i = 1; i < (int)fact.size(); i++) fact[i] = fact[i - 1] * i;
+    for (int a = 0; a < np; a++) {
+        deg[a] = mi.m[a] + mi.n[a] + mi.k[a];
+        mexp[a] = mi.m[a] | (mi.n[a] << 8) | (mi.k[a] << 16) | (deg[a] << 24);
+        invf[a] = 1.0 / (fact[mi.m[a]] * fact[mi.n[a]] * fact[mi.k[a]]);
+    }
     // symmetry maps: fwd[sig][ahat] = a = ahat o pi (with sign_s(a)),
-    // inv[sig][b] = bhat = b o pi^-1 (with sign_s(b)); sign in bit 31
+    // inv[sig][b] = bhat = b o pi^-1 (with sign_s(b)); sign in bit 15 / 31
     std::vector<unsigned short> fwd(48 * (size_t)np);
     std::vector<int> inv(48 * (size_t)np);
     for (int q = 0; q < 6; q++)
@@ -566,36 +621,76 @@ int build_tc_tables(bem_plan *P, cudaStream_t s) {
         if (!h.empty()) BEM_CUDA(cudaMemcpy(*d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice));
         return BEM_OK;
     };
-    BEM_TRY(up(&P->sy_tidx, tidx));
-    BEM_TRY(up(&P->sy_tfac, tfac));
     BEM_TRY(up(&P->sy_fwd, fwd));
-    BEM_TRY(up(&P->sy_sched, sched));
-    BEM_TRY(up(&P->sy_sched_ptr, sptr));
     BEM_TRY(up(&P->sy_inv, inv));
-    BEM_TRY(A.alloc(&P->sy_D, (size_t)P->sy_ncls * np));
-    BEM_TRY(A.alloc(&P->sy_fD, (size_t)P->sy_ncls * np));
-    BEM_TRY(A.alloc(&P->sy_Lp, (size_t)P->t.n_inter * ldp));
-    BEM_TRY(launch_m2l_derivs(P, P->sy_ncls, P->sy_rho, nullptr, P->sy_D, P->sy_fD, s));
-    P->sy_g = g;
+    BEM_TRY(up(&P->sy_mexp, mexp));
+    BEM_TRY(up(&P->sy_invf, invf));
+    const int ncls = P->sy_ncls;
+    BEM_TRY(A.alloc(&P->sy_D, std::max<size_t>(1, (size_t)ncls * np * C)));
+    if (mx) BEM_TRY(A.alloc(&P->sy_fD, std::max<size_t>(1, (size_t)ncls * np * C)));
+    BEM_TRY(launch_m2l_derivs(P, ncls, P->sy_rho, C == 2 ? P->sy_kh : nullptr, P->sy_D, mx ? P->sy_fD : nullptr, s));
+    TcGroups g{};
+    int ldp = 0, nkc = 0;
+    std::vector<uint4> sched;
+    std::vector<int> sptr;
+    const bool tc = C == 1 && mx && ncls > 0 && tc_plan(mi, deg, g, ldp, nkc, sched, sptr);
+    if (tc) {
+        // class-matrix gather table in shared-memory layout order
+        std::vector<int> tidx(g.tsize, -1);
+        std::vector<float> tfac(g.tsize, 0.f);
+        for (int q = 0; q < g.ng; q++)
+            for (int bl = 0; bl < g.n[q]; bl++)
+                for (int al = 0; al < g.k[q]; al++) {
+                    const int b = g.b0[q] + bl, e = g.off[q] + (bl >> 3) * (g.k[q] / 4) * 32 + (al >> 2) * 32 +
+                                                    (bl & 7) * 4 + (al & 3);
+                    if (b < np && al < np && deg[b] + deg[al] <= p) {
+                        tidx[e] = idx(mi.m[al] + mi.m[b], mi.n[al] + mi.n[b], mi.k[al] + mi.k[b]) | (deg[al] << 16);
+                        tfac[e] = (float)(((deg[al] & 1) ? -1.0 : 1.0) * invf[al] * invf[b]);
+                    }
+                }
+        BEM_TRY(up(&P->sy_tidx, tidx));
+        BEM_TRY(up(&P->sy_tfac, tfac));
+        BEM_TRY(up(&P->sy_sched, sched));
+        BEM_TRY(up(&P->sy_sched_ptr, sptr));
+        P->sy_g = g;
+        P->sy_nkc = nkc;
+        P->sy_nsched = (int)sched.size();
+    } else {
+        ldp = (np + 3) / 4 * 4;
+        if (sy_simt_smem_bytes(mx, C, np, p) > (size_t)200 * 1024) {
+            set_error("M2L: order %d needs more shared memory than a block has", p);
+            return BEM_EINVAL;
+        }
+    }
+    int64_t max_rows = 0;
+    BEM_TRY(build_sym_tiles(P, (size_t)ldp * C * (mx ? sizeof(float) : sizeof(double)), max_rows));
+    const size_t nLp = std::max<size_t>(1, (size_t)max_rows * ldp * C);
+    if (mx) BEM_TRY(A.alloc((float **)&P->sy_Lp, nLp));
+    else BEM_TRY(A.alloc((double **)&P->sy_Lp, nLp));
     P->sy_ldp = ldp;
-    P->sy_nkc = nkc;
-    P->sy_nsched = (int)sched.size();
-    P->sy_on = 1;
+    P->sy_tc = tc ? 1 : 0;
+    P->sy_ready = 1;
     return BEM_OK;
 }
 
-void free_tc_tables(bem_plan *P) {
+void free_sym_tables(bem_plan *P) {
     Arena &A = P->arena;
     for (void *q : {(void *)P->sy_tidx, (void *)P->sy_tfac, (void *)P->sy_fwd, (void *)P->sy_inv, (void *)P->sy_D,
-                    (void *)P->sy_fD, (void *)P->sy_Lp, (void *)P->sy_sched, (void *)P->sy_sched_ptr})
+                    (void *)P->sy_fD, (void *)P->sy_Lp, (void *)P->sy_sched, (void *)P->sy_sched_ptr,
+                    (void *)P->sy_mexp, (void *)P->sy_invf, (void *)P->sy_tile_cls, (void *)P->sy_tile_start,
+                    (void *)P->sy_tile_cnt, (void *)P->sy_src, (void *)P->sy_sig, (void *)P->sy_pair})
         A.release(q);
-    P->sy_tidx = P->sy_inv = nullptr;
+    P->sy_tile_cls = P->sy_tile_start = P->sy_tile_cnt = P->sy_src = P->sy_sig = P->sy_pair = nullptr;
+    P->sy_ntile = 0;
+    P->sy_tidx = P->sy_inv = P->sy_mexp = nullptr;
     P->sy_fwd = nullptr;
     P->sy_sched = nullptr;
     P->sy_sched_ptr = nullptr;
-    P->sy_tfac = P->sy_fD = P->sy_Lp = nullptr;
-    P->sy_D = nullptr;
-    P->sy_on = 0;
+    P->sy_tfac = P->sy_fD = nullptr;
+    P->sy_Lp = nullptr;
+    P->sy_D = P->sy_invf = nullptr;
+    P->sy_tc = 0;
+    P->sy_ready = 0;
 }
 
 int launch_m2l_tc(bem_plan *P, const float *M, float *L, cudaStream_t s) {
@@ -603,14 +698,10 @@ int launch_m2l_tc(bem_plan *P, const float *M, float *L, cudaStream_t s) {
     TcArgs a{};
     a.g = P->sy_g;
     a.np = P->mi.np;
-    a.ntile = P->sy_ntile;
     a.nkc = P->sy_nkc;
     a.nsched = P->sy_nsched;
     a.sched = P->sy_sched;
     a.sched_ptr = P->sy_sched_ptr;
-    a.tile_cls = P->sy_tile_cls;
-    a.tile_start = P->sy_tile_start;
-    a.tile_cnt = P->sy_tile_cnt;
     a.src = P->sy_src;
     a.sig = P->sy_sig;
     a.pair = P->sy_pair;
@@ -620,16 +711,25 @@ int launch_m2l_tc(bem_plan *P, const float *M, float *L, cudaStream_t s) {
     a.tfac = P->sy_tfac;
     a.fD = P->sy_fD;
     a.M = M;
-    a.Lp = P->sy_Lp;
+    a.Lp = (float *)P->sy_Lp;
     a.ldp = P->sy_ldp;
     a.err = P->dev_err;
     a.skip = P->skip;
     const size_t sm = tc_smem_bytes(a.g, a.ldp);
-    const int grid = std::min(P->sy_ntile, std::max(1, P->sm_count));
-    if (P->sy_ntile > 0) (k_m2l_tc<<<grid, TC_T, sm, s>>>(a), ::bem::count_launch());
-    (k_m2l_gather_sym<<<t.nbox, a.ldp, 0, s>>>(t.nbox, t.level, t.side, t.inter_ptr, a.np, a.ldp, P->sy_sig_u,
-                                             P->sy_inv, P->sy_Lp, L, P->skip),
-     ::bem::count_launch());
+    // one run of targets at a time: its tiles, then the gather of its targets
+    for (size_t r = 0; r + 1 < P->sy_bt.size(); r++) {
+        const int bt0 = P->sy_bt[r], nt = P->sy_bt[r + 1] - bt0, tg0 = P->sy_bb[r], ntg = P->sy_bb[r + 1] - tg0;
+        a.ntile = nt;
+        a.tile_cls = P->sy_tile_cls + bt0;
+        a.tile_start = P->sy_tile_start + bt0;
+        a.tile_cnt = P->sy_tile_cnt + bt0;
+        a.u0 = P->sy_bu[r];
+        if (nt > 0) (k_m2l_tc<<<std::min(nt, std::max(1, P->sm_count)), TC_T, sm, s>>>(a), ::bem::count_launch());
+        if (ntg > 0)
+            (k_m2l_gather_sym<<<ntg, a.ldp, 0, s>>>(tg0, t.nbox, t.level, t.side, t.inter_ptr, a.u0, a.np, a.ldp,
+                                                    P->sy_sig_u, P->sy_inv, (const float *)P->sy_Lp, L, P->skip),
+             ::bem::count_launch());
+    }
     BEM_LAUNCH_CHECK();
     return BEM_OK;
 }

@@ -92,16 +92,18 @@ class EngineError(RuntimeError):
 # basis, by (Green's function, precision).  The correction matrix dominates
 # (a few hundred entries per row for each of D and S); then the translation
 # tables, the diagonal's higher-order temporaries and the Krylov basis.  The
-# values bound the measured peaks (8-25 kB per node on spheres, ellipsoids and
+# values bound the measured peaks (9-28 kB per node on spheres, ellipsoids and
 # graded cubes of 1k-18k quadratic elements) with a margin; the GPU tests
-# check the bound.
+# check the bound.  The fixed part holds the M2L row buffer, which is capped
+# at 128 MiB whatever the mesh (its rows are computed and gathered in runs of
+# targets), and 64 MiB of small tables.
 _BYTES_PER_NODE = {
     (bem.BEM_LAPLACE, bem.BEM_F64): 28_000,
     (bem.BEM_LAPLACE, bem.BEM_MIXED): 28_000,
     (bem.BEM_HELMHOLTZ, bem.BEM_F64): 36_000,
     (bem.BEM_HELMHOLTZ, bem.BEM_MIXED): 36_000,
 }
-_BYTES_FIXED = 64 << 20
+_BYTES_FIXED = (64 + 128) << 20
 
 
 def estimate_peak_footprint(n_nodes: int, green: int, precision: int) -> int:
