@@ -134,6 +134,7 @@ static int plan_setup(bem_plan *P, cudaStream_t s) {
     BEM_TRY(lap(1));
     BEM_TRY(build_geometry(P, s));
     BEM_TRY(build_radii_lists(P, s));
+    BEM_TRY(build_near_items(P));
     BEM_TRY(lap(2));
     BEM_TRY(build_correction(P, s));
     BEM_TRY(lap(3));
@@ -141,23 +142,6 @@ static int plan_setup(bem_plan *P, cudaStream_t s) {
     BEM_TRY(lap(4));
     BEM_TRY(compute_diagonal(P, s));
     BEM_TRY(lap(5));
-    // near-field pair count (targets x regular sources), for the roofline
-    const Tree &t = P->t;
-    std::vector<int> nptr(t.nbox + 1), nidx(t.n_near), nb(t.nbox), ne(t.nbox), eb(t.nbox), ee(t.nbox), lv(t.nleaf);
-    BEM_CUDA(cudaMemcpy(nptr.data(), t.near_ptr, sizeof(int) * (t.nbox + 1), cudaMemcpyDeviceToHost));
-    BEM_CUDA(cudaMemcpy(nidx.data(), t.near_idx, sizeof(int) * t.n_near, cudaMemcpyDeviceToHost));
-    BEM_CUDA(cudaMemcpy(nb.data(), t.nb, sizeof(int) * t.nbox, cudaMemcpyDeviceToHost));
-    BEM_CUDA(cudaMemcpy(ne.data(), t.ne, sizeof(int) * t.nbox, cudaMemcpyDeviceToHost));
-    BEM_CUDA(cudaMemcpy(eb.data(), t.eb, sizeof(int) * t.nbox, cudaMemcpyDeviceToHost));
-    BEM_CUDA(cudaMemcpy(ee.data(), t.ee, sizeof(int) * t.nbox, cudaMemcpyDeviceToHost));
-    BEM_CUDA(cudaMemcpy(lv.data(), t.leaves, sizeof(int) * t.nleaf, cudaMemcpyDeviceToHost));
-    int64_t pairs = 0;
-    for (int b : lv) {
-        int64_t src = 0;
-        for (int u = nptr[b]; u < nptr[b + 1]; u++) src += (int64_t)(ee[nidx[u]] - eb[nidx[u]]) * NQ;
-        pairs += src * (ne[b] - nb[b]);
-    }
-    P->near_pairs = pairs;
     BEM_TRY(lap(6));
     return BEM_OK;
 }

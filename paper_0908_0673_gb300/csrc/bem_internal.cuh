@@ -219,6 +219,8 @@ struct bem_plan {
     // counters
     double setup_ms[BEM_NSETUP] = {};
     int64_t near_pairs = 0;
+    int2 *near_items[2] = {nullptr, nullptr};   // float32 near-field work items, 64- and 32-target passes
+    int near_nitems[2] = {0, 0};
     int last_op = -1;
     // GMRES workspace
     double *V = nullptr, *H = nullptr, *gs = nullptr, *w = nullptr, *xk = nullptr, *bvec = nullptr;
@@ -262,6 +264,7 @@ int launch_translations(bem_plan *P, R *M, R *L, cudaStream_t s, cudaEvent_t *ev
 template <class R, int C>
 int launch_m2m(bem_plan *P, R *M, cudaStream_t s);
 int field_moments(bem_plan *P, const void *phi, const void *chi, cudaStream_t s);
+int build_near_items(bem_plan *P);
 int enqueue_matvec(bem_plan *P, int op, int green, double k, cudaStream_t s);
 int set_slots(bem_plan *P, const void *x, void *y, cudaStream_t s);
 int enqueue_matvec_raw(bem_plan *P, int op, int green, double k, int with_diag, cudaStream_t s,

@@ -323,12 +323,71 @@ __global__ void __launch_bounds__(NF_T) k_near(int nleaf, Tabs tb, TreeView tv, 
 // with compensation, slices and the local expansion combine in float64.
 // ---------------------------------------------------------------------------
 constexpr int NF2_T = 256, NF2_TILE = 1024, NF2_ENT = 256;
+__host__ __device__ constexpr int nf2_u(int C) { return C == 1 ? 8 : 4; }
+// sources per staged round: 3 float4 each in the packed real form, 2 complex
+__host__ __device__ constexpr int nf2_tile(int C) { return C == 1 ? 640 : NF2_TILE; }
+
+// Work items of the float32 near field: one per (leaf, pass of up to 8 U
+// targets), ordered by decreasing pair count (targets x near sources, ties in
+// leaf order), so the largest blocks start first and the last wave is made of
+// the smallest.  Each target is summed by one block whatever the order.
+int build_near_items(bem_plan *P) {
+    const Tree &t = P->t;
+    std::vector<int> nptr(t.nbox + 1), nidx(std::max<int64_t>(1, t.n_near)), nb(t.nbox), ne(t.nbox), eb(t.nbox),
+        ee(t.nbox), lv(t.nleaf);
+    BEM_CUDA(cudaMemcpy(nptr.data(), t.near_ptr, sizeof(int) * (t.nbox + 1), cudaMemcpyDeviceToHost));
+    if (t.n_near) BEM_CUDA(cudaMemcpy(nidx.data(), t.near_idx, sizeof(int) * t.n_near, cudaMemcpyDeviceToHost));
+    BEM_CUDA(cudaMemcpy(nb.data(), t.nb, sizeof(int) * t.nbox, cudaMemcpyDeviceToHost));
+    BEM_CUDA(cudaMemcpy(ne.data(), t.ne, sizeof(int) * t.nbox, cudaMemcpyDeviceToHost));
+    BEM_CUDA(cudaMemcpy(eb.data(), t.eb, sizeof(int) * t.nbox, cudaMemcpyDeviceToHost));
+    BEM_CUDA(cudaMemcpy(ee.data(), t.ee, sizeof(int) * t.nbox, cudaMemcpyDeviceToHost));
+    BEM_CUDA(cudaMemcpy(lv.data(), t.leaves, sizeof(int) * t.nleaf, cudaMemcpyDeviceToHost));
+    int64_t pairs = 0;
+    std::vector<int64_t> src(t.nleaf);
+    for (int li = 0; li < t.nleaf; li++) {
+        const int b = lv[li];
+        int64_t n = 0;
+        for (int u = nptr[b]; u < nptr[b + 1]; u++) n += (int64_t)(ee[nidx[u]] - eb[nidx[u]]) * NQ;
+        src[li] = n;
+        pairs += n * (ne[b] - nb[b]);
+    }
+    P->near_pairs = pairs;
+    for (int v = 0; v < 2; v++) {
+        const int slots = 8 * nf2_u(v + 1);
+        std::vector<int2> items;
+        std::vector<int64_t> cost;
+        for (int li = 0; li < t.nleaf; li++) {
+            const int b = lv[li];
+            for (int t0 = nb[b]; t0 < ne[b]; t0 += slots) {
+                items.push_back(make_int2(li, t0));
+                cost.push_back((int64_t)std::min(slots, ne[b] - t0) * src[li]);
+            }
+        }
+        std::vector<int> ord(items.size());
+        for (size_t i = 0; i < ord.size(); i++) ord[i] = (int)i;
+        std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+        std::vector<int2> sorted(std::max<size_t>(1, items.size()));
+        for (size_t i = 0; i < ord.size(); i++) sorted[i] = items[ord[i]];
+        BEM_TRY(P->arena.alloc(&P->near_items[v], sorted.size()));
+        BEM_CUDA(cudaMemcpy(P->near_items[v], sorted.data(), sizeof(int2) * sorted.size(), cudaMemcpyHostToDevice));
+        P->near_nitems[v] = (int)items.size();
+    }
+    return BEM_OK;
+}
+
+// 1 / sqrt(x) as the single hardware approximation (flush-to-zero form: the
+// squared distances of near-field pairs are never subnormal)
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 template <int C, bool DL>
 __device__ __forceinline__ void pair_f32(float rx, float ry, float rz, const float4 &sa, const float4 &sb, float kw,
                                          float *acc) {
     const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-    const float inv = rsqrtf(r2);
+    const float inv = rsqrt_ftz(r2);
     if (C == 1) {
         if (DL) {   // sb = strength * normal
             const float dot = fmaf(rx, sb.x, fmaf(ry, sb.y, rz * sb.z));
@@ -366,163 +425,267 @@ struct KahanF {
     }
 };
 
+// shared memory of the float32 near field beyond its static part: the staged
+// sources (sa, sb) and the per-thread compensated sums
+__host__ __device__ constexpr size_t nf2_dyn_bytes(int C) {
+    return 2 * NF2_TILE * sizeof(float4) + 2 * (size_t)nf2_u(C) * C * NF2_T * sizeof(float);
+}
+
 template <int C, bool DL>
-__global__ void __launch_bounds__(NF2_T) k_near_f32(int nleaf, Tabs tb, TreeView tv, QuadView qv, double kwave,
-                                                    const float *__restrict__ f, const float *__restrict__ L,
-                                                    double *__restrict__ ytmp, const int *__restrict__ skip) {
-    constexpr int U = C == 1 ? 8 : 4;                 // targets per thread
+__global__ void __launch_bounds__(NF2_T, 4) k_near_f32(int nitem, const int2 *__restrict__ items, Tabs tb, TreeView tv,
+                                                       QuadView qv, double kwave, const float *__restrict__ f,
+                                                       const float *__restrict__ L, double *__restrict__ ytmp,
+                                                       const int *__restrict__ skip) {
+    constexpr int U = nf2_u(C);                       // targets per thread
     constexpr int SLOTS = 8 * U;                      // targets per pass (at most 8 groups)
     constexpr int LP = NF2_T / SLOTS;                 // threads per target in the local expansion
+    constexpr int UC = U * C;
+    constexpr int TILE = nf2_tile(C);                 // sources staged per round
     if (skip && *skip) return;
-    const int li = blockIdx.x;
-    if (li >= nleaf) return;
-    const int b = tv.leaves[li];
+    if ((int)blockIdx.x >= nitem) return;
+    const int2 item = items[blockIdx.x];              // (leaf, first target of the pass)
+    const int b = tv.leaves[item.x];
     const int tid = threadIdx.x, lane = tid & 31;
-    extern __shared__ float4 near_tile[];             // [2][NF2_TILE] staged sources
-    float4 *sa = near_tile, *sb = near_tile + NF2_TILE;
+    // The staged-source region is reused once the sources are done: slice
+    // sums, local-expansion partials and the targets' powers (23 KB at most).
+    extern __shared__ float4 near_tile[];
+    float4 *sa = near_tile, *sb = near_tile + NF2_TILE;                 // C = 2: position | Re f, normal | Im f
+    float4 *s0 = near_tile, *s1 = s0 + TILE, *s2 = s1 + TILE;           // C = 1: packed (see the staging)
+    float *ks = (float *)(near_tile + 2 * NF2_TILE);  // [UC][NF2_T] compensated sums
+    float *kc = ks + UC * NF2_T;                      // [UC][NF2_T] their carries
+    float *red = (float *)near_tile;                  // [slice][slot][C]
+    float *lred = red + NF2_T * UC;                   // [part][slot][C]
+    float *spow = lred + NF2_T * C;                   // [slot][3][PMAX + 1]
     __shared__ int pref[NF2_ENT + 1];
-    __shared__ float red[NF2_T * U * C];              // [slice][slot] partial sums
-    __shared__ float lred[NF2_T * C];                 // [part][slot] local-expansion partial sums
-    __shared__ float spow[SLOTS][3][PMAX + 1];        // powers of the targets' scaled offsets
+    __shared__ int ebase[NF2_ENT];                    // first quadrature point of each entry's box
+    __shared__ float eoff[NF2_ENT][3];                // entry box centre - target leaf centre
+    __shared__ float toff[SLOTS][3];                  // target - target leaf centre
     const double cbx = tv.cx[b], cby = tv.cy[b], cbz = tv.cz[b];
     const float kw = (float)kwave;
     const int p = tb.p, np = tb.np;
-    const int tb0 = tv.nb[b], te0 = tv.ne[b];
-    for (int t0 = tb0; t0 < te0; t0 += SLOTS) {
-        const int nt = min(SLOTS, te0 - t0);
-        const int G = (nt + U - 1) / U, S = NF2_T / G, tg = tid % G, sl = tid / G;
-        const bool worker = sl < S;
-        float tx[U], ty[U], tz[U];
+    const int t0 = item.y, nt = min(SLOTS, tv.ne[b] - t0);
+    const int G = (nt + U - 1) / U, S = NF2_T / G, tg = tid % G, sl = tid / G;
+    const bool worker = sl < S;
+    if (tid < SLOTS) {
+        const int k = t0 + tid;
+        const bool on = tid < nt;
+        toff[tid][0] = on ? (float)(tv.tx[k] - cbx) : 0.f;
+        toff[tid][1] = on ? (float)(tv.ty[k] - cby) : 0.f;
+        toff[tid][2] = on ? (float)(tv.tz[k] - cbz) : 1.f;   // off targets stay away from every source
+    }
+    for (int i = tid; i < 2 * UC * NF2_T; i += NF2_T) ks[i] = 0.f;
+    __syncthreads();
+    float tx[U], ty[U], tz[U];
 #pragma unroll
-        for (int u = 0; u < U; u++) {
-            const int k = t0 + tg + G * u;
-            const bool on = k < te0;
-            tx[u] = on ? (float)(tv.tx[k] - cbx) : 0.f;
-            ty[u] = on ? (float)(tv.ty[k] - cby) : 0.f;
-            tz[u] = on ? (float)(tv.tz[k] - cbz) : 1.f;
-        }
-        KahanF acc[U][C];
-        for (int e0 = tv.near_ptr[b]; e0 < tv.near_ptr[b + 1]; e0 += NF2_ENT) {
-            const int ne_ = min(NF2_ENT, tv.near_ptr[b + 1] - e0);
-            __syncthreads();
-            if (tid < 32) {                           // quadrature-point offsets of the entries (warp scan)
-                int carry = 0;
-                for (int i0 = 0; i0 < ne_; i0 += 32) {
-                    const int i = i0 + lane;
-                    int x = 0;
-                    if (i < ne_) {
-                        const int s = tv.near_idx[e0 + i];
-                        x = (tv.ee[s] - tv.eb[s]) * NQ;
-                    }
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int y = __shfl_up_sync(0xffffffffu, x, o);
-                        if (lane >= o) x += y;
-                    }
-                    if (i < ne_) pref[i + 1] = carry + x;
-                    carry += __shfl_sync(0xffffffffu, x, 31);
+    for (int u = 0; u < U; u++) {
+        const int slot = tg + G * u;                 // < G U <= SLOTS
+        tx[u] = toff[slot][0];
+        ty[u] = toff[slot][1];
+        tz[u] = toff[slot][2];
+    }
+    for (int e0 = tv.near_ptr[b]; e0 < tv.near_ptr[b + 1]; e0 += NF2_ENT) {
+        const int ne_ = min(NF2_ENT, tv.near_ptr[b + 1] - e0);
+        __syncthreads();
+        if (tid < 32) {                               // quadrature-point offsets of the entries (warp scan)
+            int carry = 0;
+            for (int i0 = 0; i0 < ne_; i0 += 32) {
+                const int i = i0 + lane;
+                int x = 0;
+                if (i < ne_) {
+                    const int s = tv.near_idx[e0 + i];
+                    x = (tv.ee[s] - tv.eb[s]) * NQ;
+                    ebase[i] = tv.eb[s] * NQ;
+                    eoff[i][0] = (float)(tv.cx[s] - cbx);
+                    eoff[i][1] = (float)(tv.cy[s] - cby);
+                    eoff[i][2] = (float)(tv.cz[s] - cbz);
                 }
-                if (lane == 0) pref[0] = 0;
-            }
-            __syncthreads();
-            const int total = pref[ne_];
-            for (int base = 0; base < total; base += NF2_TILE) {
-                __syncthreads();
-                for (int jj = tid; jj < NF2_TILE; jj += NF2_T) {
-                    const int j = base + jj;
-                    if (j >= total) break;
-                    int lo = 0, hi = ne_ - 1;          // entry holding j: pref[lo] <= j < pref[lo + 1]
-                    while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if (pref[mid] <= j) lo = mid; else hi = mid - 1;
-                    }
-                    const int s = tv.near_idx[e0 + lo];
-                    const int o = tv.eb[s] * NQ + (j - pref[lo]);
-                    const float dx = (float)(tv.cx[s] - cbx), dy = (float)(tv.cy[s] - cby), dz = (float)(tv.cz[s] - cbz);
-                    const float4 xa = make_float4(dx + qv.fx[o], dy + qv.fy[o], dz + qv.fz[o], 0.f);
-                    if (C == 1 && DL) {
-                        const float fo = f[o];
-                        sa[jj] = xa;
-                        sb[jj] = make_float4(fo * qv.fnx[o], fo * qv.fny[o], fo * qv.fnz[o], 0.f);
-                    } else {
-                        sa[jj] = make_float4(xa.x, xa.y, xa.z, f[(size_t)o * C]);
-                        sb[jj] = make_float4(DL ? qv.fnx[o] : 0.f, DL ? qv.fny[o] : 0.f, DL ? qv.fnz[o] : 0.f,
-                                             C == 2 ? f[(size_t)o * C + C - 1] : 0.f);
-                    }
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= o) x += y;
                 }
-                __syncthreads();
-                const int nq = min(NF2_TILE, total - base);
-                float part[U][C];
-#pragma unroll
-                for (int u = 0; u < U; u++)
-#pragma unroll
-                    for (int c = 0; c < C; c++) part[u][c] = 0.f;
-                if (worker)
-                    for (int q = sl; q < nq; q += S) {
-                        const float4 A = sa[q], Bv = sb[q];
-#pragma unroll
-                        for (int u = 0; u < U; u++)
-                            pair_f32<C, DL>(tx[u] - A.x, ty[u] - A.y, tz[u] - A.z, A, Bv, kw, part[u]);
-                    }
-#pragma unroll
-                for (int u = 0; u < U; u++)
-#pragma unroll
-                    for (int c = 0; c < C; c++) acc[u][c].add(part[u][c]);
+                if (i < ne_) pref[i + 1] = carry + x;
+                carry += __shfl_sync(0xffffffffu, x, 31);
             }
+            if (lane == 0) pref[0] = 0;
         }
         __syncthreads();
-        if (worker)
+        const int total = pref[ne_];
+        for (int base = 0; base < total; base += TILE) {
+            __syncthreads();
+            int lo = 0;                               // entry holding j: pref[lo] <= j < pref[lo + 1]
+            if (base + tid < total) {
+                int hi = ne_ - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (pref[mid] <= base + tid) lo = mid; else hi = mid - 1;
+                }
+            }
+            for (int jj = tid; jj < TILE; jj += NF2_T) {
+                const int j = base + jj;
+                if (j >= total) break;
+                while (pref[lo + 1] <= j) lo++;       // j grows with jj: the entry only moves forward
+                const int o = ebase[lo] + (j - pref[lo]);
+                const float4 xa = make_float4(eoff[lo][0] + qv.fx[o], eoff[lo][1] + qv.fy[o], eoff[lo][2] + qv.fz[o], 0.f);
+                if constexpr (C == 1) {
+                    // packed layout: each value twice, for the two targets of a float2
+                    // operation; positions negated so that r = t + (-a)
+                    const float fo = f[o];
+                    s0[jj] = make_float4(-xa.x, -xa.x, -xa.y, -xa.y);
+                    if (DL) {
+                        const float nx = fo * qv.fnx[o], ny = fo * qv.fny[o], nz = fo * qv.fnz[o];
+                        s1[jj] = make_float4(-xa.z, -xa.z, nx, nx);
+                        s2[jj] = make_float4(ny, ny, nz, nz);
+                    } else {
+                        s1[jj] = make_float4(-xa.z, -xa.z, fo, fo);
+                    }
+                } else {
+                    sa[jj] = make_float4(xa.x, xa.y, xa.z, f[(size_t)o * C]);
+                    sb[jj] = make_float4(DL ? qv.fnx[o] : 0.f, DL ? qv.fny[o] : 0.f, DL ? qv.fnz[o] : 0.f,
+                                         C == 2 ? f[(size_t)o * C + C - 1] : 0.f);
+                }
+            }
+            __syncthreads();
+            const int nq = min(TILE, total - base);
+            float part[U][C];
 #pragma unroll
             for (int u = 0; u < U; u++)
 #pragma unroll
-                for (int c = 0; c < C; c++) red[((size_t)sl * G * U + tg + G * u) * C + c] = acc[u][c].s;
-        // local expansion at the targets: powers of the scaled offsets, then
-        // LP threads per target each take every LP-th term
-        const double h = scalbn(tv.side, -tv.level[b]);
-        if (tid < nt) {
-            const int k = t0 + tid;
-            const float dx = (float)((tv.tx[k] - cbx) / h), dy = (float)((tv.ty[k] - cby) / h),
-                        dz = (float)((tv.tz[k] - cbz) / h);
-            float qx = 1.f, qy = 1.f, qz = 1.f;
-            for (int e = 0; e <= p; e++) {
-                spow[tid][0][e] = qx;
-                spow[tid][1][e] = qy;
-                spow[tid][2][e] = qz;
-                qx *= dx;
-                qy *= dy;
-                qz *= dz;
-            }
-        }
-        __syncthreads();
-        {
-            const int slot = tid % SLOTS, part_id = tid / SLOTS;
-            KahanF loc[C];
-            if (slot < nt)
-                for (int a = part_id; a < np; a += LP) {
-                    const float mono = spow[slot][0][tb.m[a]] * spow[slot][1][tb.n[a]] * spow[slot][2][tb.k[a]];
+                for (int c = 0; c < C; c++) part[u][c] = 0.f;
+            if constexpr (C == 1) {
+                // two targets per packed float32 operation (__fadd2 / __fmul2 / __ffma2):
+                // half the issue slots of the scalar form, same roundings in the same order
+                float2 t2x[U / 2], t2y[U / 2], t2z[U / 2], p2[U / 2];
 #pragma unroll
-                    for (int c = 0; c < C; c++) loc[c].add(mono * L[((size_t)b * np + a) * C + c]);
+                for (int v = 0; v < U / 2; v++) {
+                    t2x[v] = make_float2(tx[2 * v], tx[2 * v + 1]);
+                    t2y[v] = make_float2(ty[2 * v], ty[2 * v + 1]);
+                    t2z[v] = make_float2(tz[2 * v], tz[2 * v + 1]);
+                    p2[v] = make_float2(0.f, 0.f);
+                }
+                auto source = [&](int q) {
+                    const float4 a0 = s0[q], a1 = s1[q];
+                    const float2 mx = make_float2(a0.x, a0.y), my = make_float2(a0.z, a0.w), mz = make_float2(a1.x, a1.y);
+                    float2 nx, ny, nz;
+                    if (DL) {
+                        const float4 a2 = s2[q];
+                        nx = make_float2(a1.z, a1.w);
+                        ny = make_float2(a2.x, a2.y);
+                        nz = make_float2(a2.z, a2.w);
+                    }
+#pragma unroll
+                    for (int v = 0; v < U / 2; v++) {
+                        const float2 rx = __fadd2_rn(t2x[v], mx), ry = __fadd2_rn(t2y[v], my), rz = __fadd2_rn(t2z[v], mz);
+                        float2 r2 = __fmul2_rn(rz, rz);
+                        r2 = __ffma2_rn(ry, ry, r2);
+                        r2 = __ffma2_rn(rx, rx, r2);
+                        const float2 inv = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
+                        if (DL) {
+                            float2 dot = __fmul2_rn(rz, nz);
+                            dot = __ffma2_rn(ry, ny, dot);
+                            dot = __ffma2_rn(rx, nx, dot);
+                            p2[v] = __ffma2_rn(__fmul2_rn(dot, inv), __fmul2_rn(inv, inv), p2[v]);
+                        } else {
+                            p2[v] = __ffma2_rn(make_float2(a1.z, a1.w), inv, p2[v]);
+                        }
+                    }
+                };
+                if (worker) {
+                    int q = sl;
+                    for (; q + S < nq; q += 2 * S) {
+                        source(q);
+                        source(q + S);
+                    }
+                    if (q < nq) source(q);
                 }
 #pragma unroll
-            for (int c = 0; c < C; c++) lred[(part_id * SLOTS + slot) * C + c] = loc[c].s;
+                for (int v = 0; v < U / 2; v++) {
+                    part[2 * v][0] = p2[v].x;
+                    part[2 * v + 1][0] = p2[v].y;
+                }
+            } else if (worker) {
+                // two sources per iteration (fewer loop instructions, more independent work)
+                const float4 *pa = sa + sl, *pb = sb + sl;
+                int q = sl;
+                for (; q + S < nq; q += 2 * S, pa += 2 * S, pb += 2 * S) {
+                    const float4 A0 = pa[0], B0 = pb[0], A1 = pa[S], B1 = pb[S];
+#pragma unroll
+                    for (int u = 0; u < U; u++) {
+                        pair_f32<C, DL>(tx[u] - A0.x, ty[u] - A0.y, tz[u] - A0.z, A0, B0, kw, part[u]);
+                        pair_f32<C, DL>(tx[u] - A1.x, ty[u] - A1.y, tz[u] - A1.z, A1, B1, kw, part[u]);
+                    }
+                }
+                if (q < nq) {
+                    const float4 A = pa[0], Bv = pb[0];
+#pragma unroll
+                    for (int u = 0; u < U; u++)
+                        pair_f32<C, DL>(tx[u] - A.x, ty[u] - A.y, tz[u] - A.z, A, Bv, kw, part[u]);
+                }
+            }
+            // tile partials into the compensated sums (Kahan), kept in shared memory
+#pragma unroll
+            for (int u = 0; u < U; u++)
+#pragma unroll
+                for (int c = 0; c < C; c++) {
+                    const int i = (u * C + c) * NF2_T + tid;
+                    const float s = ks[i], y = part[u][c] - kc[i], t = s + y;
+                    kc[i] = (t - s) - y;
+                    ks[i] = t;
+                }
         }
-        __syncthreads();
-        if (tid < nt) {
-            // target t0 + tid sits in slot tid = tg + G u of every slice
-            double sum[C], loc[C];
+    }
+    __syncthreads();                                  // sources done: their region is reused below
+    if (worker)
 #pragma unroll
-            for (int c = 0; c < C; c++) sum[c] = loc[c] = 0.0;
-            for (int q = 0; q < S; q++)
+        for (int u = 0; u < U; u++)
 #pragma unroll
-                for (int c = 0; c < C; c++) sum[c] += (double)red[((size_t)q * G * U + tid) * C + c];
-            for (int q = 0; q < LP; q++)
-#pragma unroll
-                for (int c = 0; c < C; c++) loc[c] += (double)lred[(q * SLOTS + tid) * C + c];
-            const int node = tv.node_perm[t0 + tid];
-#pragma unroll
-            for (int c = 0; c < C; c++) ytmp[(size_t)node * C + c] = sum[c] * (0.25 / M_PI) + loc[c];
+            for (int c = 0; c < C; c++) red[((size_t)sl * G * U + tg + G * u) * C + c] = ks[(u * C + c) * NF2_T + tid];
+    // local expansion at the targets: powers of the scaled offsets, then
+    // LP threads per target each take every LP-th term
+    if (tid < nt) {
+        const int k = t0 + tid;
+        const double ih = scalbn(1.0 / tv.side, tv.level[b]);   // 1 / h of the leaf
+        const float dx = (float)((tv.tx[k] - cbx) * ih), dy = (float)((tv.ty[k] - cby) * ih),
+                    dz = (float)((tv.tz[k] - cbz) * ih);
+        float qx = 1.f, qy = 1.f, qz = 1.f;
+        float *sp = spow + (size_t)tid * 3 * (PMAX + 1);
+        for (int e = 0; e <= p; e++) {
+            sp[e] = qx;
+            sp[PMAX + 1 + e] = qy;
+            sp[2 * (PMAX + 1) + e] = qz;
+            qx *= dx;
+            qy *= dy;
+            qz *= dz;
         }
-        __syncthreads();
+    }
+    __syncthreads();
+    {
+        const int slot = tid % SLOTS, part_id = tid / SLOTS;
+        KahanF loc[C];
+        if (slot < nt) {
+            const float *sp = spow + (size_t)slot * 3 * (PMAX + 1);
+            for (int a = part_id; a < np; a += LP) {
+                const float mono = sp[tb.m[a]] * sp[PMAX + 1 + tb.n[a]] * sp[2 * (PMAX + 1) + tb.k[a]];
+#pragma unroll
+                for (int c = 0; c < C; c++) loc[c].add(mono * L[((size_t)b * np + a) * C + c]);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < C; c++) lred[(part_id * SLOTS + slot) * C + c] = loc[c].s;
+    }
+    __syncthreads();
+    if (tid < nt) {
+        // target t0 + tid sits in slot tid = tg + G u of every slice
+        KahanF sum[C], loc[C];
+        for (int q = 0; q < S; q++)
+#pragma unroll
+            for (int c = 0; c < C; c++) sum[c].add(red[((size_t)q * G * U + tid) * C + c]);
+        for (int q = 0; q < LP; q++)
+#pragma unroll
+            for (int c = 0; c < C; c++) loc[c].add(lred[(q * SLOTS + tid) * C + c]);
+        const int node = tv.node_perm[t0 + tid];
+#pragma unroll
+        for (int c = 0; c < C; c++) ytmp[(size_t)node * C + c] = (double)sum[c].s * (0.25 / M_PI) + (double)loc[c].s;
     }
 }
 
@@ -716,9 +879,13 @@ static int run_fmm(bem_plan *P, int op, double kwave, R *f, R *M, R *L, cudaStre
     if (ev) BEM_CUDA(cudaEventRecord(ev[2], s));
     BEM_TRY((launch_translations<R, C>(P, M, L, s, ev)));
     if constexpr (sizeof(R) == sizeof(float)) {
-        constexpr size_t tile_sm = 2 * NF2_TILE * sizeof(float4);
-        if (op == BEM_OP_A) (k_near_f32<C, true><<<t.nleaf, NF2_T, tile_sm, s>>>(t.nleaf, tb, tv, qv, kwave, f, L, P->ytmp, sk), ::bem::count_launch());
-        else (k_near_f32<C, false><<<t.nleaf, NF2_T, tile_sm, s>>>(t.nleaf, tb, tv, qv, kwave, f, L, P->ytmp, sk), ::bem::count_launch());
+        constexpr size_t tile_sm = nf2_dyn_bytes(C);
+        const int ni = P->near_nitems[C - 1];
+        const int2 *it = P->near_items[C - 1];
+        if (ni > 0) {
+            if (op == BEM_OP_A) (k_near_f32<C, true><<<ni, NF2_T, tile_sm, s>>>(ni, it, tb, tv, qv, kwave, f, L, P->ytmp, sk), ::bem::count_launch());
+            else (k_near_f32<C, false><<<ni, NF2_T, tile_sm, s>>>(ni, it, tb, tv, qv, kwave, f, L, P->ytmp, sk), ::bem::count_launch());
+        }
     } else {
         if (op == BEM_OP_A) (k_near<R, C, true><<<t.nleaf, NF_T, 0, s>>>(t.nleaf, tb, tv, qv, kwave, f, L, P->ytmp, sk), ::bem::count_launch());
         else (k_near<R, C, false><<<t.nleaf, NF_T, 0, s>>>(t.nleaf, tb, tv, qv, kwave, f, L, P->ytmp, sk), ::bem::count_launch());

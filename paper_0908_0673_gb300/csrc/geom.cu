@@ -353,7 +353,7 @@ __global__ void k_special_write(CorrArgs a, const int *__restrict__ off, int *pa
 // fixed order, so the stored values are the same on every run.
 // ---------------------------------------------------------------------------
 constexpr int SP_WARPS = 4;        // warps per block
-constexpr int SP_QCAP = 128;       // pieces per level buffer and warp
+constexpr int SP_QCAP = 64;        // pieces per level buffer and warp (float32; half for float64)
 constexpr int SP_RING = 256;       // pending points per warp: a power of two >= 31 + 7 * 32
 constexpr float SP_UNIT = 1024.f;  // piece corners are multiples of 2^-10 (max_subdiv <= 10)
 
@@ -530,6 +530,47 @@ __device__ __forceinline__ bool must_split_fast(const float *df, const double *X
     return must_split<NPE>(X, xi, tau, maxdepth, P);
 }
 
+// A queued piece with the images of its corners in the element's local frame
+// (node offsets from the collocation point), so that a decision maps only the
+// centroid and a split only the three edge midpoints.
+struct __align__(16) QPiece {
+    uint4 piece;                    // pack_piece
+    float4 A, B, Cc;                // corner images (w unused)
+};
+
+template <int NPE>
+__device__ __forceinline__ float4 map_f(const float *df, float s, float t) {
+    float N[NPE], Ns[NPE], Nt[NPE];
+    shape_all<float, NPE>(s, t, N, Ns, Nt);
+    float v0 = 0.f, v1 = 0.f, v2 = 0.f;
+#pragma unroll
+    for (int a = 0; a < NPE; a++) {
+        v0 = fmaf(N[a], df[3 * a], v0);
+        v1 = fmaf(N[a], df[3 * a + 1], v1);
+        v2 = fmaf(N[a], df[3 * a + 2], v2);
+    }
+    return make_float4(v0, v1, v2, 0.f);
+}
+
+__device__ __forceinline__ float dist2f(float4 p, float4 q) {
+    const float e0 = p.x - q.x, e1 = p.y - q.y, e2 = p.z - q.z;
+    return e0 * e0 + e1 * e1 + e2 * e2;
+}
+
+// The subdivision decision from the corner images: |x(m) - x_i|^2 against
+// tau^2 h^2 in float32 (relative error ~2e-6), decided there when the two
+// differ by more than 2e-4 tau^2 h^2, else by the exact float64 test.
+template <int NPE>
+__device__ __forceinline__ bool split_test(const float *df, const QPiece &Q, const PieceF &P, const double *X,
+                                           const double xi[3], float tau2, double tau, int maxdepth) {
+    if (P.depth >= maxdepth) return false;
+    const float4 m = map_f<NPE>(df, (P.a0 + P.b0 + P.c0) * (1.f / 3.f), (P.a1 + P.b1 + P.c1) * (1.f / 3.f));
+    const float h2 = fmaxf(dist2f(Q.A, Q.B), fmaxf(dist2f(Q.B, Q.Cc), dist2f(Q.Cc, Q.A)));
+    const float th = tau2 * h2, q = m.x * m.x + m.y * m.y + m.z * m.z - th;
+    if (fabsf(q) > 2e-4f * th) return q < 0.f;
+    return must_split<NPE>(X, xi, tau, maxdepth, P);
+}
+
 __device__ __forceinline__ void split4(const PieceF &P, PieceF out[4]) {
     const float ab0 = 0.5f * (P.a0 + P.b0), ab1 = 0.5f * (P.a1 + P.b1);
     const float bc0 = 0.5f * (P.b0 + P.c0), bc1 = 0.5f * (P.b1 + P.c1);
@@ -570,7 +611,8 @@ __global__ void __launch_bounds__(32 * SP_WARPS, 4) k_special_pair(CorrArgs a, i
                                                                 double *valS, double *d0pair) {
     constexpr int C = HELM ? 2 : 1;
     constexpr unsigned FULL = 0xffffffffu;
-    __shared__ uint4 qbuf[SP_WARPS][2][SP_QCAP];
+    constexpr int QCAP = sizeof(R) == 4 ? SP_QCAP : SP_QCAP / 2;   // static shared memory stays under 48 KB
+    __shared__ QPiece qbuf[SP_WARPS][2][QCAP];
     __shared__ R ring[SP_WARPS][3][SP_RING];
     __shared__ double sX[SP_WARPS][18];
     __shared__ R sd[SP_WARPS][18];
@@ -582,6 +624,7 @@ __global__ void __launch_bounds__(32 * SP_WARPS, 4) k_special_pair(CorrArgs a, i
     const R *d = sd[warp];
     const float *df = sdf[warp];
     const R kk = (R)a.k;
+    const float tau2 = (float)(a.tau * a.tau);
     for (int pr = blockIdx.x * SP_WARPS + warp; pr < npairs; pr += gridDim.x * SP_WARPS) {
         const int node = pair_node[pr], e = pair_e[pr];
         const double xi[3] = {a.nodes[3 * (size_t)node], a.nodes[3 * (size_t)node + 1], a.nodes[3 * (size_t)node + 2]};
@@ -641,29 +684,63 @@ __global__ void __launch_bounds__(32 * SP_WARPS, 4) k_special_pair(CorrArgs a, i
             // then the leaf pieces of a level-synchronous 4-way refinement
             if (lane < NQ) { rs[lane] = rule_s<R>(lane); rt[lane] = rule_t<R>(lane); rw[lane] = -rule_w<R>(lane); }
             int head = 0, tail = NQ;
-            uint4 *cur = qbuf[warp][0], *nxt = qbuf[warp][1];
-            int ncur = 1;
-            if (lane == 0) cur[0] = pack_piece(PieceF{0.f, 0.f, 1.f, 0.f, 0.f, 1.f, 0});
+            QPiece *cur = qbuf[warp][0], *nxt = qbuf[warp][1];
+            int ncur = 0;
+            auto img = [&](int v) { return make_float4(df[3 * v], df[3 * v + 1], df[3 * v + 2], 0.f); };
+            if (a.maxdepth > 0) {
+                // the pair was selected by the root's own test, so the root
+                // splits: its four children, corner images from the nodes
+                if (lane < 4) {
+                    const float4 v0 = img(0), v1 = img(1), v2 = img(2);
+                    float4 m01, m12, m20;
+                    if (NPE == 6) {
+                        m01 = img(3 % NPE); m12 = img(4 % NPE); m20 = img(5 % NPE);
+                    } else {
+                        m01 = map_f<NPE>(df, 0.5f, 0.f); m12 = map_f<NPE>(df, 0.5f, 0.5f); m20 = map_f<NPE>(df, 0.f, 0.5f);
+                    }
+                    PieceF ch[4];
+                    split4(PieceF{0.f, 0.f, 1.f, 0.f, 0.f, 1.f, 0}, ch);
+                    QPiece Q;
+                    Q.piece = pack_piece(ch[lane]);
+                    Q.A = lane == 0 ? v0 : lane == 2 ? m20 : m01;
+                    Q.B = lane == 0 ? m01 : lane == 1 ? v1 : m12;
+                    Q.Cc = lane == 0 ? m20 : lane == 1 ? m12 : lane == 2 ? v2 : m20;
+                    cur[lane] = Q;
+                }
+                ncur = 4;
+            } else if (lane < NQ) {
+                // no subdivision: the special rule is the regular rule
+                rs[NQ + lane] = rule_s<R>(lane); rt[NQ + lane] = rule_t<R>(lane); rw[NQ + lane] = rule_w<R>(lane);
+            }
+            if (a.maxdepth <= 0) tail = 2 * NQ;
             __syncwarp();
             while (ncur > 0) {
                 int nnext = 0;
                 for (int base = 0; base < ncur; base += 32) {
                     const int i = base + lane;
                     PieceF P = {};
+                    QPiece Q;
                     bool split = false, leaf = false;
                     if (i < ncur) {
-                        P = unpack_piece(cur[i]);
-                        split = must_split_fast<NPE>(df, X, xi, a.tau, a.maxdepth, P);
+                        Q = cur[i];
+                        P = unpack_piece(Q.piece);
+                        split = split_test<NPE>(df, Q, P, X, xi, tau2, a.tau, a.maxdepth);
                         leaf = !split;
                     }
                     const unsigned ms = __ballot_sync(FULL, split), ml = __ballot_sync(FULL, leaf);
                     if (split) {
                         const int pos = nnext + 4 * __popc(ms & lt);
-                        if (pos + 4 <= SP_QCAP) {
+                        if (pos + 4 <= QCAP) {
                             PieceF ch[4];
                             split4(P, ch);
-#pragma unroll
-                            for (int c = 0; c < 4; c++) nxt[pos + c] = pack_piece(ch[c]);
+                            const float4 mab = map_f<NPE>(df, ch[0].b0, ch[0].b1);   // (a + b) / 2
+                            const float4 mca = map_f<NPE>(df, ch[0].c0, ch[0].c1);   // (c + a) / 2
+                            const float4 mbc = map_f<NPE>(df, ch[1].c0, ch[1].c1);   // (b + c) / 2
+                            QPiece *o = nxt + pos;
+                            o[0].piece = pack_piece(ch[0]); o[0].A = Q.A; o[0].B = mab; o[0].Cc = mca;
+                            o[1].piece = pack_piece(ch[1]); o[1].A = mab; o[1].B = Q.B; o[1].Cc = mbc;
+                            o[2].piece = pack_piece(ch[2]); o[2].A = mca; o[2].B = mbc; o[2].Cc = Q.Cc;
+                            o[3].piece = pack_piece(ch[3]); o[3].A = mab; o[3].B = mbc; o[3].Cc = mca;
                         } else {
                             refine_serial<R, HELM, NPE>(X, xi, d, df, kk, a.tau, a.maxdepth, P, v);
                         }
@@ -679,7 +756,7 @@ __global__ void __launch_bounds__(32 * SP_WARPS, 4) k_special_pair(CorrArgs a, i
                         }
                     }
                     tail += NQ * __popc(ml);
-                    nnext = min(SP_QCAP, nnext + 4 * __popc(ms));
+                    nnext = min(QCAP, nnext + 4 * __popc(ms));
                     nnext -= nnext % 4;
                     __syncwarp();
                     for (; tail - head >= 32; head += 32) {
@@ -688,12 +765,12 @@ __global__ void __launch_bounds__(32 * SP_WARPS, 4) k_special_pair(CorrArgs a, i
                     }
                     __syncwarp();                       // ring reads done before the next writes
                 }
-                uint4 *sw = cur; cur = nxt; nxt = sw;
+                QPiece *sw = cur; cur = nxt; nxt = sw;
                 ncur = nnext;
             }
-            if (head + lane < tail) {
+            for (; tail - head > 0; head += 32) {
                 const int k = (head + lane) & (SP_RING - 1);
-                eval_st<R, HELM, NPE>(d, kk, rs[k], rt[k], rw[k], v);
+                if (head + lane < tail) eval_st<R, HELM, NPE>(d, kk, rs[k], rt[k], rw[k], v);
             }
         }
         // transposing butterfly: after the step of width k a lane keeps the
