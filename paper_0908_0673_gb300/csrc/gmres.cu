@@ -306,8 +306,13 @@ struct GmSolver {
     bem_solve_params sp{};
     cudaStream_t s = nullptr;
     cudaEvent_t ev = nullptr;
-    int phase = 0;                 // 0 start, 1 residual in flight, 2 cycle in flight, 3 done
+    int phase = 0;                 // 0 start, 1 residual in flight, 2 cycle steps, 3 done, 4 cycle end in flight
     bool waiting = false;
+    // cycle steps go out in chunks, at most two in flight; each chunk reports
+    // the device's converged flag, and once one has, no further chunk is sent
+    cudaEvent_t evc[2] = {nullptr, nullptr};
+    int cyc_steps = 0, j_next = 0, nfly = 0, chunk_seq = 0;
+    bool stop = false;
     int iters = 0, restarts = 0, status = BEM_ENOCONV;
     double rel = 1.0, prev_rel = 2.0, tol = 0.0;
 };
@@ -383,37 +388,59 @@ static int gm_k_residual(bem_plan *P, cudaStream_t s, bool raw) {
 }
 
 // one restart cycle: Arnoldi (CGS2) + Givens for up to `steps` steps, then
-// x += V y
+// x += V y.  Begin, one step, end: the solver enqueues steps in chunks, the
+// captured group graphs the whole cycle.
 template <int C>
-static int gm_k_cycle(bem_plan *P, int steps, cudaStream_t s, bool raw) {
+static int gm_k_cycle_begin(bem_plan *P, cudaStream_t s) {
+    const int ne = (int)P->N * C, eb = (ne + 255) / 256;
+    GmState S = gm_state<C>(P);
+    (k_scale<<<eb, 256, 0, s>>>(ne, P->V, S.sc + 1, P->V, P->istate), ::bem::count_launch());
+    (k_cycle_init<<<1, 1, 0, s>>>(S, P->gm_restart), ::bem::count_launch());
+    BEM_LAUNCH_CHECK();
+    return BEM_OK;
+}
+
+template <int C>
+static int gm_k_step(bem_plan *P, int j, cudaStream_t s, bool raw) {
     const int n = (int)P->N, m = P->gm_restart, ne = n * C;
     const size_t ld = (size_t)ne;
     double *V = P->V, *w = P->w, *partial = P->scal + 16;
     GmState S = gm_state<C>(P);
     const int eb = (ne + 255) / 256, nb = (n + 255) / 256;
     int *skip = P->istate;
-    (k_scale<<<eb, 256, 0, s>>>(ne, V, S.sc + 1, V, skip), ::bem::count_launch());
-    (k_cycle_init<<<1, 1, 0, s>>>(S, m), ::bem::count_launch());
-    for (int j = 0; j < steps; j++) {
-        BEM_TRY(set_slots(P, V + (size_t)j * ld, w, s));
-        BEM_TRY(gm_product(P, BEM_OP_A, s, raw));
-        // CGS2: two classical Gram-Schmidt passes against V_0..V_j
-        (k_mdot<C><<<GM_BLK, GM_T, 0, s>>>(n, j + 1, V, ld, w, partial, skip), ::bem::count_launch());
-        (k_mdot_final<C><<<(j + 1 + 7) / 8, 256, 0, s>>>(j + 1, partial, S.hcol, 0, skip), ::bem::count_launch());
-        (k_orth_update<C><<<nb, 256, 0, s>>>(n, j + 1, V, ld, S.hcol, w, skip), ::bem::count_launch());
-        (k_mdot<C><<<GM_BLK, GM_T, 0, s>>>(n, j + 1, V, ld, w, partial, skip), ::bem::count_launch());
-        (k_mdot_final<C><<<(j + 1 + 7) / 8, 256, 0, s>>>(j + 1, partial, S.hcol2, 0, skip), ::bem::count_launch());
-        (k_orth_update<C><<<nb, 256, 0, s>>>(n, j + 1, V, ld, S.hcol2, w, skip), ::bem::count_launch());
-        (k_nrm2_partial<C><<<GM_BLK, GM_T, 0, s>>>(n, w, partial, skip), ::bem::count_launch());
-        (k_nrm2_final<<<1, 32, 0, s>>>(partial, S.sc + 4, skip), ::bem::count_launch());
-        (k_givens<C><<<1, 1, 0, s>>>(S, m, j), ::bem::count_launch());
-        (k_scale<<<eb, 256, 0, s>>>(ne, w, S.sc + 4, V + (size_t)(j + 1) * ld, skip), ::bem::count_launch());
-        BEM_LAUNCH_CHECK();
-    }
-    (k_backsolve<C><<<1, 1, 0, s>>>(S, m), ::bem::count_launch());
-    (k_xupdate<C><<<nb, 256, 0, s>>>(n, V, ld, S, (double *const *)P->gm_slot + 1), ::bem::count_launch());
+    BEM_TRY(set_slots(P, V + (size_t)j * ld, w, s));
+    BEM_TRY(gm_product(P, BEM_OP_A, s, raw));
+    // CGS2: two classical Gram-Schmidt passes against V_0..V_j
+    (k_mdot<C><<<GM_BLK, GM_T, 0, s>>>(n, j + 1, V, ld, w, partial, skip), ::bem::count_launch());
+    (k_mdot_final<C><<<(j + 1 + 7) / 8, 256, 0, s>>>(j + 1, partial, S.hcol, 0, skip), ::bem::count_launch());
+    (k_orth_update<C><<<nb, 256, 0, s>>>(n, j + 1, V, ld, S.hcol, w, skip), ::bem::count_launch());
+    (k_mdot<C><<<GM_BLK, GM_T, 0, s>>>(n, j + 1, V, ld, w, partial, skip), ::bem::count_launch());
+    (k_mdot_final<C><<<(j + 1 + 7) / 8, 256, 0, s>>>(j + 1, partial, S.hcol2, 0, skip), ::bem::count_launch());
+    (k_orth_update<C><<<nb, 256, 0, s>>>(n, j + 1, V, ld, S.hcol2, w, skip), ::bem::count_launch());
+    (k_nrm2_partial<C><<<GM_BLK, GM_T, 0, s>>>(n, w, partial, skip), ::bem::count_launch());
+    (k_nrm2_final<<<1, 32, 0, s>>>(partial, S.sc + 4, skip), ::bem::count_launch());
+    (k_givens<C><<<1, 1, 0, s>>>(S, m, j), ::bem::count_launch());
+    (k_scale<<<eb, 256, 0, s>>>(ne, w, S.sc + 4, V + (size_t)(j + 1) * ld, skip), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
     return BEM_OK;
+}
+
+template <int C>
+static int gm_k_cycle_end(bem_plan *P, cudaStream_t s) {
+    const int n = (int)P->N;
+    GmState S = gm_state<C>(P);
+    (k_backsolve<C><<<1, 1, 0, s>>>(S, P->gm_restart), ::bem::count_launch());
+    (k_xupdate<C><<<(n + 255) / 256, 256, 0, s>>>(n, P->V, (size_t)n * C, S, (double *const *)P->gm_slot + 1),
+     ::bem::count_launch());
+    BEM_LAUNCH_CHECK();
+    return BEM_OK;
+}
+
+template <int C>
+static int gm_k_cycle(bem_plan *P, int steps, cudaStream_t s, bool raw) {
+    BEM_TRY(gm_k_cycle_begin<C>(P, s));
+    for (int j = 0; j < steps; j++) BEM_TRY(gm_k_step<C>(P, j, s, raw));
+    return gm_k_cycle_end<C>(P, s);
 }
 
 static double gm_tol(const bem_plan *P, double tol) {
@@ -452,25 +479,71 @@ static int gm_enqueue_residual(GmSolver &g) {
     return BEM_OK;
 }
 
+// The first residual of a solve: x = 0, so r = b and beta = ||b|| (the
+// product of the zero vector is exactly zero and is not formed).
 template <int C>
 static int gm_enqueue_start(GmSolver &g) {
     bem_plan *P = g.P;
+    GmState S = gm_state<C>(P);
     g.tol = gm_tol(P, g.sp.tol);
     BEM_CUDA(cudaMemsetAsync(P->istate, 0, sizeof(int) * 3, g.s));
     (k_set_ptrs<<<1, 1, 0, g.s>>>((void **)P->gm_slot, g.chi, g.x), ::bem::count_launch());
     BEM_TRY(gm_k_start<C>(P, g.tol, g.s, false));
-    return gm_enqueue_residual<C>(g);
+    BEM_CUDA(cudaMemcpyAsync(P->V, P->bvec, sizeof(double) * (size_t)P->N * C, cudaMemcpyDeviceToDevice, g.s));
+    BEM_CUDA(cudaMemcpyAsync(S.sc + 1, S.sc, sizeof(double), cudaMemcpyDeviceToDevice, g.s));
+    BEM_CUDA(cudaMemcpyAsync(P->hostbuf, S.sc, sizeof(double) * 2, cudaMemcpyDeviceToHost, g.s));
+    BEM_CUDA(cudaEventRecord(g.ev, g.s));
+    g.waiting = true;
+    g.phase = 1;
+    return BEM_OK;
 }
+
+constexpr int GM_CHUNK = 4;         // Arnoldi steps per chunk
 
 template <int C>
 static int gm_enqueue_cycle(GmSolver &g) {
+    BEM_TRY(gm_k_cycle_begin<C>(g.P, g.s));
+    g.cyc_steps = std::min(g.P->gm_restart, g.sp.max_iter - g.iters);
+    g.j_next = g.nfly = g.chunk_seq = 0;
+    g.stop = false;
+    g.waiting = false;
+    g.phase = 2;
+    return BEM_OK;
+}
+
+// Sends chunks of cycle steps (at most two in flight) and reads their
+// converged flags; once every chunk has finished, the cycle's end.  Returns
+// with phase 2 when a chunk is pending and the call does not block.
+template <int C>
+static int gm_cycle_steps(GmSolver &g, bool blocking) {
     bem_plan *P = g.P;
     GmState S = gm_state<C>(P);
-    BEM_TRY(gm_k_cycle<C>(P, std::min(P->gm_restart, g.sp.max_iter - g.iters), g.s, false));
+    for (;;) {
+        if (!g.stop && g.j_next < g.cyc_steps && g.nfly < 2) {
+            const int j1 = std::min(g.cyc_steps, g.j_next + GM_CHUNK), k = (g.chunk_seq + g.nfly) & 1;
+            for (int j = g.j_next; j < j1; j++) BEM_TRY(gm_k_step<C>(P, j, g.s, false));
+            BEM_CUDA(cudaMemcpyAsync(P->hostbuf + 4 + k, S.st, sizeof(int), cudaMemcpyDeviceToHost, g.s));
+            BEM_CUDA(cudaEventRecord(g.evc[k], g.s));
+            g.j_next = j1;
+            g.nfly++;
+            continue;
+        }
+        if (g.nfly == 0) break;
+        const int k = g.chunk_seq & 1;             // the oldest chunk in flight
+        cudaError_t e = blocking ? cudaEventSynchronize(g.evc[k]) : cudaEventQuery(g.evc[k]);
+        if (e == cudaErrorNotReady) return BEM_OK;
+        if (e != cudaSuccess) return cuda_fail(e, "GMRES chunk event", __FILE__, __LINE__);
+        int conv;
+        memcpy(&conv, P->hostbuf + 4 + k, sizeof(int));
+        g.nfly--;
+        g.chunk_seq++;
+        if (conv) g.stop = true;
+    }
+    BEM_TRY(gm_k_cycle_end<C>(P, g.s));
     BEM_CUDA(cudaMemcpyAsync(P->hostbuf + 2, S.st + 1, sizeof(int), cudaMemcpyDeviceToHost, g.s));
     BEM_CUDA(cudaEventRecord(g.ev, g.s));
     g.waiting = true;
-    g.phase = 2;
+    g.phase = 4;
     return BEM_OK;
 }
 
@@ -481,6 +554,11 @@ static int gm_advance(GmSolver &g, bool blocking) {
     while (g.phase != 3) {
         if (g.phase == 0) {
             BEM_TRY(gm_enqueue_start<C>(g));
+            continue;
+        }
+        if (g.phase == 2) {
+            BEM_TRY(gm_cycle_steps<C>(g, blocking));
+            if (g.phase == 2) return BEM_OK;          // a chunk is still running
             continue;
         }
         if (g.waiting) {
@@ -511,6 +589,18 @@ static int gm_advance(GmSolver &g, bool blocking) {
     return BEM_OK;
 }
 
+// the event a solver is waiting for (the oldest chunk while steps are out)
+static cudaEvent_t gm_pending_event(const GmSolver &g) {
+    return g.phase == 2 && g.nfly > 0 ? g.evc[g.chunk_seq & 1] : g.ev;
+}
+
+static void gm_release(GmSolver &g) {
+    if (g.ev) cudaEventDestroy(g.ev);
+    for (auto &e : g.evc)
+        if (e) cudaEventDestroy(e);
+    g.ev = g.evc[0] = g.evc[1] = nullptr;
+}
+
 static int gm_init(GmSolver &g, bem_plan *P, const double *chi, double *x, const bem_solve_params *sp, cudaStream_t s) {
     g = GmSolver{};
     g.P = P;
@@ -520,6 +610,7 @@ static int gm_init(GmSolver &g, bem_plan *P, const double *chi, double *x, const
     g.s = s;
     BEM_TRY(gm_workspace(P, sp->restart));
     BEM_CUDA(cudaEventCreateWithFlags(&g.ev, cudaEventDisableTiming));
+    for (auto &e : g.evc) BEM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     return BEM_OK;
 }
 
@@ -536,7 +627,7 @@ int solve(bem_plan *P, const void *chi, void *phi, int nrhs, const bem_solve_par
         GmSolver g;
         BEM_TRY(gm_init(g, P, (const double *)chi + r * nchi, (double *)phi + r * ne, sp, s));
         int rc = gm_run(g, true);
-        cudaEventDestroy(g.ev);
+        gm_release(g);
         if (rc != BEM_OK) return rc;
         if (info) info[r] = bem_solve_info{g.iters, g.restarts, g.rel, g.status};
         if (g.status == BEM_ENOCONV) worst = BEM_ENOCONV;
@@ -646,8 +737,7 @@ struct bem_batch {
     std::vector<int> used;              // 0 free, 1 active, 2 finished
     std::vector<cudaStream_t> streams;
     ~bem_batch() {
-        for (auto &g : slot)
-            if (g.ev) cudaEventDestroy(g.ev);
+        for (auto &g : slot) bem::gm_release(g);
         for (auto s : streams)
             if (s) cudaStreamDestroy(s);
     }
@@ -701,7 +791,7 @@ int bem_batch_submit(bem_batch *b, bem_plan *P, const void *chi_dev, void *phi_d
     if (free_slot < 0) { set_error("bem_batch_submit: no free slot"); return BEM_EBUSY; }
     BEM_CUDA(cudaSetDevice(b->device));
     GmSolver &g = b->slot[free_slot];
-    if (g.ev) cudaEventDestroy(g.ev);
+    gm_release(g);
     BEM_TRY(gm_init(g, P, (const double *)chi_dev, (double *)phi_dev, &sp, b->streams[free_slot]));
     b->used[free_slot] = 1;
     int rc = gm_run(g, false);
@@ -744,7 +834,7 @@ int bem_batch_wait(bem_batch *b, int slot, double timeout_s) {
         if (b->used[slot] != 1) break;
         const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         if (el > timeout_s) { set_error("bem_batch_wait: slot %d not finished after %g s", slot, timeout_s); return BEM_ETIMEOUT; }
-        cudaEventSynchronize(b->slot[slot].ev);    // sleep until this slot's next step is done
+        cudaEventSynchronize(gm_pending_event(b->slot[slot]));   // sleep until this slot's next step is done
     }
     return BEM_OK;
 }
