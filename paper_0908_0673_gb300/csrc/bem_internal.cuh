@@ -105,6 +105,7 @@ struct Tree {
     int *nb = nullptr, *ne = nullptr;   // node range in Morton order
     int *eb = nullptr, *ee = nullptr;   // element range in owner order
     double *cx = nullptr, *cy = nullptr, *cz = nullptr, *r = nullptr;
+    float4 *fbox = nullptr;             // float32 centre and radius of each box (search filters)
     int *leaves = nullptr;              // box ids of the leaves
     int *near_ptr = nullptr, *near_idx = nullptr;
     int *inter_ptr = nullptr, *inter_idx = nullptr;

@@ -247,6 +247,8 @@ struct CorrArgs {
     const int *el_phi, *el_chi;
     const double *ecx, *ecy, *ecz, *eh;   // per element centroid image and size
     const float4 *ebnd;                   // per element float32 search bound (centroid, R_e)
+    const float4 *fbox;                   // per box float32 centre (x, y, z)
+    const float *frho;                    // per box float32 search radius, rounded up
     const double *bcx, *bcy, *bcz, *brho; // per box centre and search radius
     const int *child0, *nchild, *eb, *ee;
 };
@@ -273,6 +275,11 @@ __global__ void k_elem_search_radius(CorrArgs a, const int *__restrict__ leaf_of
     }
 }
 
+__global__ void k_rho_float(int nbox, const double *__restrict__ rho, float *frho) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nbox) frho[b] = (float)(rho[b] * (1.0 + 1e-6));
+}
+
 // 0 regular, 1 singular (*a_sing = local node), 2 near-singular
 __device__ __forceinline__ int classify_pair(const CorrArgs &a, int node, const double xi[3], int e, int *a_sing) {
     const int *el = a.el_phi + (size_t)e * a.npe;
@@ -282,49 +289,80 @@ __device__ __forceinline__ int classify_pair(const CorrArgs &a, int node, const 
     return d < __dmul_rn(a.tau, a.eh[e]) ? 2 : 0;
 }
 
-// Visits, for collocation node `node`, every element of a leaf whose search
-// ball holds the node; writes special (element, kind) pairs when `out`.
-__device__ int find_special(const CorrArgs &a, int node, int *out_e) {
-    double xi[3] = {a.nodes[3 * (size_t)node], a.nodes[3 * (size_t)node + 1], a.nodes[3 * (size_t)node + 2]};
+// One warp per collocation node: walks the box tree (children tested by the
+// lanes in parallel, passing children pushed in reverse so that they are
+// visited in order) and, in every leaf reached, tests the leaf's elements 32
+// at a time; special (element) pairs are counted, or written in leaf order
+// and element order within a leaf when `out_e` is given.  A float32 test with
+// an inflated radius filters boxes (visiting a box the exact test would skip
+// only adds candidates); elements pass a float32 rejection and then the
+// exact float64 classification.
+constexpr int SS_WARPS = 4, SS_STACK = 8 * 24;
+
+__device__ __forceinline__ bool box_may_hold(const CorrArgs &a, int b, const float xf[3], float ax) {
+    const float4 c = a.fbox[b];
+    const float dx = xf[0] - c.x, dy = xf[1] - c.y, dz = xf[2] - c.z, rh = a.frho[b];
+    const float lim = rh + 1e-5f * (ax + fabsf(c.x) + fabsf(c.y) + fabsf(c.z) + rh);
+    return dx * dx + dy * dy + dz * dz <= lim * lim;
+}
+
+__device__ int find_special_warp(const CorrArgs &a, int node, int *out_e, int *stack) {
+    const int lane = threadIdx.x & 31;
+    const unsigned FULL = 0xffffffffu, lt = (1u << lane) - 1u;
+    const double xi[3] = {a.nodes[3 * (size_t)node], a.nodes[3 * (size_t)node + 1], a.nodes[3 * (size_t)node + 2]};
     const float xf[3] = {(float)xi[0], (float)xi[1], (float)xi[2]};
     const float ax = fabsf(xf[0]) + fabsf(xf[1]) + fabsf(xf[2]);
-    int stack[8 * 24], sp = 0, cnt = 0;
-    stack[sp++] = 0;
+    int sp = 0, cnt = 0;
+    if (lane == 0) stack[0] = 0;
+    sp = 1;
+    __syncwarp();
     while (sp > 0) {
-        int b = stack[--sp];
-        double d = dist3_rn(xi[0], xi[1], xi[2], a.bcx[b], a.bcy[b], a.bcz[b]);
-        if (d > a.brho[b]) continue;
-        if (a.nchild[b] != 0) {
-            for (int c = a.child0[b] + a.nchild[b] - 1; c >= a.child0[b]; c--) stack[sp++] = c;
+        const int b = stack[--sp];
+        __syncwarp();
+        const int nc = a.nchild[b];
+        if (nc != 0) {
+            const int c0 = a.child0[b];
+            const unsigned m = __ballot_sync(FULL, lane < nc && box_may_hold(a, c0 + lane, xf, ax));
+            const int k = __popc(m);
+            // passing children in reverse order: lane holding child c writes at sp + (passing children after c)
+            if (lane < nc && ((m >> lane) & 1u)) stack[sp + __popc(m >> (lane + 1))] = c0 + lane;
+            sp += k;
+            __syncwarp();
             continue;
         }
-        for (int e = a.eb[b]; e < a.ee[b]; e++) {
-            // float32 rejection of elements that are certainly regular (the
-            // margin covers the rounding of both positions), then the exact test
-            const float4 c = a.ebnd[e];
-            const float dx = xf[0] - c.x, dy = xf[1] - c.y, dz = xf[2] - c.z;
-            const float lim = c.w + 1e-5f * (ax + fabsf(c.x) + fabsf(c.y) + fabsf(c.z) + c.w);
-            if (dx * dx + dy * dy + dz * dz > lim * lim) continue;
-            int as;
-            if (classify_pair(a, node, xi, e, &as)) {
-                if (out_e) out_e[cnt] = e;
-                cnt++;
+        for (int base = a.eb[b]; base < a.ee[b]; base += 32) {
+            const int e = base + lane;
+            bool hit = false;
+            if (e < a.ee[b]) {
+                const float4 c = a.ebnd[e];
+                const float dx = xf[0] - c.x, dy = xf[1] - c.y, dz = xf[2] - c.z;
+                const float lim = c.w + 1e-5f * (ax + fabsf(c.x) + fabsf(c.y) + fabsf(c.z) + c.w);
+                if (dx * dx + dy * dy + dz * dz <= lim * lim) {
+                    int as;
+                    hit = classify_pair(a, node, xi, e, &as) != 0;
+                }
             }
+            const unsigned m = __ballot_sync(FULL, hit);
+            if (out_e && hit) out_e[cnt + __popc(m & lt)] = e;
+            cnt += __popc(m);
         }
     }
     return cnt;
 }
 
-__global__ void k_special_count(CorrArgs a, int *cnt) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.N) return;
-    cnt[i] = find_special(a, i, nullptr);
+__global__ void __launch_bounds__(32 * SS_WARPS) k_special_count(CorrArgs a, int *cnt) {
+    __shared__ int stack[SS_WARPS][SS_STACK];
+    const int w = threadIdx.x >> 5, i = blockIdx.x * SS_WARPS + w;
+    if (i >= a.N) return;                              // uniform within the warp
+    const int c = find_special_warp(a, i, nullptr, stack[w]);
+    if ((threadIdx.x & 31) == 0) cnt[i] = c;
 }
 
-__global__ void k_special_write(CorrArgs a, const int *__restrict__ off, int *pair_e) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(32 * SS_WARPS) k_special_write(CorrArgs a, const int *__restrict__ off, int *pair_e) {
+    __shared__ int stack[SS_WARPS][SS_STACK];
+    const int w = threadIdx.x >> 5, i = blockIdx.x * SS_WARPS + w;
     if (i >= a.N) return;
-    find_special(a, i, pair_e + off[i]);
+    find_special_warp(a, i, pair_e + off[i], stack[w]);
 }
 
 // ---------------------------------------------------------------------------
@@ -840,22 +878,26 @@ int build_correction(bem_plan *P, cudaStream_t s) {
     double *ecx, *ecy, *ecz, *eh, *rho;
     BEM_TRY(A.alloc(&ecx, E)); BEM_TRY(A.alloc(&ecy, E)); BEM_TRY(A.alloc(&ecz, E)); BEM_TRY(A.alloc(&eh, E));
     float4 *ebnd;
+    float *frho;
     BEM_TRY(A.alloc(&ebnd, E));
+    BEM_TRY(A.alloc(&frho, t.nbox));
     BEM_TRY(A.alloc(&rho, t.nbox));
     (k_elem_centroid<<<(E + 255) / 256, 256, 0, s>>>(E, npe, P->prm.tau_near, t.el_phi, P->nodes, ecx, ecy, ecz, eh, ebnd),
      ::bem::count_launch());
     CorrArgs a{N, E, npe, P->green, P->prm.n_duffy, P->prm.max_subdiv, P->k, P->prm.tau_near, P->nodes,
-               t.el_phi, t.el_chi, ecx, ecy, ecz, eh, ebnd, t.cx, t.cy, t.cz, rho, t.child0, t.nchild, t.eb, t.ee};
+               t.el_phi, t.el_chi, ecx, ecy, ecz, eh, ebnd, t.fbox, frho, t.cx, t.cy, t.cz, rho, t.child0, t.nchild,
+               t.eb, t.ee};
     BEM_CUDA(cudaMemsetAsync(rho, 0, sizeof(double) * t.nbox, s));
     (k_elem_search_radius<<<(E + 255) / 256, 256, 0, s>>>(a, t.leaf_of_node, t.parent, (unsigned long long *)rho),
      ::bem::count_launch());
+    (k_rho_float<<<(t.nbox + 255) / 256, 256, 0, s>>>(t.nbox, rho, frho), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
     int *cnt, *off, *tot;
     BEM_TRY(A.alloc(&cnt, N + 1));
     BEM_TRY(A.alloc(&off, N + 1));
     BEM_TRY(A.alloc(&tot, 1));
     BEM_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (N + 1), s));
-    (k_special_count<<<(N + 127) / 128, 128, 0, s>>>(a, cnt), ::bem::count_launch());
+    (k_special_count<<<(N + SS_WARPS - 1) / SS_WARPS, 32 * SS_WARPS, 0, s>>>(a, cnt), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
     BEM_TRY(scan_exclusive(cnt, off, N + 1, tot, s));
     int npairs = 0;
@@ -864,7 +906,7 @@ int build_correction(bem_plan *P, cudaStream_t s) {
     int *pair_e, *pair_node;
     BEM_TRY(A.alloc(&pair_e, npairs));
     BEM_TRY(A.alloc(&pair_node, npairs));
-    (k_special_write<<<(N + 127) / 128, 128, 0, s>>>(a, off, pair_e), ::bem::count_launch());
+    (k_special_write<<<(N + SS_WARPS - 1) / SS_WARPS, 32 * SS_WARPS, 0, s>>>(a, off, pair_e), ::bem::count_launch());
     (k_pair_nodes<<<(N + 255) / 256, 256, 0, s>>>(N, off, pair_node), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
     const int C = P->green == BEM_HELMHOLTZ ? 2 : 1;
@@ -916,7 +958,7 @@ int build_correction(bem_plan *P, cudaStream_t s) {
     P->C = d0row;
     BEM_CUDA(cudaStreamSynchronize(s));
     A.release(cnt); A.release(tot); A.release(pair_node); A.release(d0pair);
-    A.release(ecx); A.release(ecy); A.release(ecz); A.release(eh); A.release(ebnd); A.release(rho); A.release(off);
+    A.release(ecx); A.release(ecy); A.release(ecz); A.release(eh); A.release(ebnd); A.release(frho); A.release(rho); A.release(off);
     A.release(pair_e);
     return BEM_OK;
 }

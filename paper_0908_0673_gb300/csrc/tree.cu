@@ -559,11 +559,29 @@ struct ListArgs {
     const int *pnear_ptr, *pnear_idx;   // lists of the previous levels
     double eta;
     int leaf_descend;
+    const float4 *fbox;                 // float32 centres and radii
 };
 
+// |c_b - c_n| > eta (r_b + r_n), exactly as in float64 (the oracle's
+// operation order).  A float32 estimate decides when it clears the threshold
+// by more than its rounding error can move it (1e-5 of the magnitudes
+// involved); the float64 test decides the rest.
 __device__ __forceinline__ bool separated(const ListArgs &a, int b, int n) {
+    const float4 B = a.fbox[b], Nb = a.fbox[n];
+    const float dx = B.x - Nb.x, dy = B.y - Nb.y, dz = B.z - Nb.z;
+    const float d2 = dx * dx + dy * dy + dz * dz;
+    const float T = (float)a.eta * (B.w + Nb.w);
+    const float m = 1e-5f * (T + fabsf(B.x) + fabsf(B.y) + fabsf(B.z) + fabsf(Nb.x) + fabsf(Nb.y) + fabsf(Nb.z));
+    if (d2 > (T + m) * (T + m)) return true;
+    if (T > m && d2 < (T - m) * (T - m)) return false;
     double d = dist3_rn(a.cx[b], a.cy[b], a.cz[b], a.cx[n], a.cy[n], a.cz[n]);
     return d > __dmul_rn(a.eta, __dadd_rn(a.r[b], a.r[n]));
+}
+
+__global__ void k_box_floats(int nbox, const double *__restrict__ cx, const double *__restrict__ cy,
+                             const double *__restrict__ cz, const double *__restrict__ r, float4 *fbox) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nbox) fbox[b] = make_float4((float)cx[b], (float)cy[b], (float)cz[b], (float)r[b]);
 }
 
 // Walks the parent's near list for box b; when `write`, stores the entries.
@@ -640,6 +658,8 @@ int build_radii_lists(bem_plan *P, cudaStream_t s) {
         (k_radius_parent<<<(cnt + 255) / 256, 256, 0, s>>>(off, cnt, t.child0, t.nchild, t.level, t.side, sqrt3, t.r), ::bem::count_launch());
         BEM_LAUNCH_CHECK();
     }
+    BEM_TRY(A.alloc(&t.fbox, t.nbox));
+    (k_box_floats<<<(t.nbox + 255) / 256, 256, 0, s>>>(t.nbox, t.cx, t.cy, t.cz, t.r, t.fbox), ::bem::count_launch());
     // lists, level by level; level-l lists only read level < l lists
     BEM_TRY(A.alloc(&t.near_ptr, t.nbox + 1));
     BEM_TRY(A.alloc(&t.inter_ptr, t.nbox + 1));
@@ -660,7 +680,7 @@ int build_radii_lists(bem_plan *P, cudaStream_t s) {
     for (int l = 1; l < t.nlev; l++) {
         int off = t.lev_off[l], cnt = t.lev_off[l + 1] - off;
         ListArgs a{t.parent, t.child0, t.nchild, t.cx, t.cy, t.cz, t.r, t.near_ptr, near_idx, P->prm.eta,
-                   P->prm.leaf_descend};
+                   P->prm.leaf_descend, t.fbox};
         // level l-1 pointers must be closed for the walk: ptr[off] = running total
         (k_close_ptr<<<1, 1, 0, s>>>(t.near_ptr, off, nnear), ::bem::count_launch());
         (k_close_ptr<<<1, 1, 0, s>>>(t.inter_ptr, off, ninter), ::bem::count_launch());
