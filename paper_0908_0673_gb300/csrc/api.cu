@@ -136,14 +136,47 @@ static int plan_setup(bem_plan *P, cudaStream_t s) {
     BEM_TRY(build_radii_lists(P, s));
     BEM_TRY(build_near_items(P));
     BEM_TRY(lap(2));
-    BEM_TRY(build_correction(P, s));
-    BEM_TRY(lap(3));
     BEM_TRY(build_m2l_classes(P));
     BEM_TRY(lap(4));
-    BEM_TRY(compute_diagonal(P, s));
-    BEM_TRY(lap(5));
+    // The special-pair correction (stream s) and the diagonal's product (s2)
+    // run side by side: every allocation of both is made before the first
+    // long kernel is enqueued, and the product joins s before the diagonal
+    // adds the correction's row sums.  Stage times of the two are the GPU
+    // spans on their streams (they overlap).
+    cudaStream_t s2 = P->setup_stream[1];
+    cudaEvent_t ev[6] = {};
+    for (auto &e : ev) BEM_CUDA(cudaEventCreate(&e));
+    auto fin = [&](int rc) {
+        for (auto &e : ev) cudaEventDestroy(e);
+        return rc;
+    };
+    BEM_CUDA(cudaEventRecord(ev[0], s));
+    BEM_CUDA(cudaStreamWaitEvent(s2, ev[0], 0));
+    BEM_CUDA(cudaEventRecord(ev[2], s2));
+    int rc = diagonal_prepare(P, s2);
+    if (rc == BEM_OK) rc = build_correction(P, s);
+    if (rc == BEM_OK) BEM_CUDA(cudaEventRecord(ev[1], s));
+    if (rc == BEM_OK) rc = diagonal_product(P, s2);
+    if (rc == BEM_OK) BEM_CUDA(cudaEventRecord(ev[3], s2));
+    if (rc == BEM_OK) BEM_CUDA(cudaStreamWaitEvent(s, ev[3], 0));
+    if (rc == BEM_OK) rc = diagonal_finish(P, s);
+    if (rc == BEM_OK) BEM_CUDA(cudaEventRecord(ev[4], s));
+    if (rc != BEM_OK) {
+        cudaStreamSynchronize(s);
+        cudaStreamSynchronize(s2);
+        return fin(rc);
+    }
+    BEM_CUDA(cudaStreamSynchronize(s));
+    for (void *q : P->deferred) A.release(q);
+    P->deferred.clear();
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    P->setup_ms[3] = ms;
+    cudaEventElapsedTime(&ms, ev[2], ev[4]);
+    P->setup_ms[5] = ms;
+    t0 = std::chrono::steady_clock::now();
     BEM_TRY(lap(6));
-    return BEM_OK;
+    return fin(BEM_OK);
 }
 
 template <class T>
@@ -161,6 +194,8 @@ bem_plan::~bem_plan() {
     if (cycle_graph) cudaGraphExecDestroy(cycle_graph);
     if (hostbuf) cudaFreeHost(hostbuf);
     if (capture_stream) cudaStreamDestroy(capture_stream);
+    for (auto st : setup_stream)
+        if (st) cudaStreamDestroy(st);
 }
 
 using namespace bem;
@@ -232,14 +267,26 @@ int bem_plan_create(bem_mesh *mesh, int green, double k, const bem_fmm_params *p
     P->Q = mesh->n_elems * NQ;
     P->nchi = mesh->n_chi;
     P->npe = mesh->npe;
-    cudaStream_t s = (cudaStream_t)cuda_stream;
-    int rc = plan_setup(P, s);
+    // set-up runs on two streams of its own, after the caller's stream
+    cudaStream_t cs = (cudaStream_t)cuda_stream;
+    for (auto &st : P->setup_stream) BEM_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    cudaStream_t s = P->setup_stream[0];
+    int rc = BEM_OK;
+    {
+        cudaEvent_t e0;
+        BEM_CUDA(cudaEventCreateWithFlags(&e0, cudaEventDisableTiming));
+        cudaError_t e = cudaEventRecord(e0, cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, e0, 0);
+        cudaEventDestroy(e0);
+        if (e != cudaSuccess) rc = cuda_fail(e, "plan set-up stream", __FILE__, __LINE__);
+    }
+    if (rc == BEM_OK) rc = plan_setup(P, s);
     if (rc == BEM_OK) {
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) rc = cuda_fail(e, "plan set-up", __FILE__, __LINE__);
     }
     if (rc != BEM_OK) {
-        cudaStreamSynchronize(s);
+        for (auto st : P->setup_stream) cudaStreamSynchronize(st);
         delete P;
         return rc;
     }

@@ -220,6 +220,9 @@ struct bem_plan {
     // counters
     double setup_ms[BEM_NSETUP] = {};
     int64_t near_pairs = 0;
+    std::vector<void *> deferred;       // set-up temporaries released after the next synchronisation
+    double *diag_ones = nullptr;        // phi = 1 of the diagonal's product (set-up only)
+    cudaStream_t setup_stream[2] = {nullptr, nullptr};
     int2 *near_items[2] = {nullptr, nullptr};   // float32 near-field work items, 64- and 32-target passes
     int near_nitems[2] = {0, 0};
     int last_op = -1;
@@ -266,11 +269,13 @@ template <class R, int C>
 int launch_m2m(bem_plan *P, R *M, cudaStream_t s);
 int field_moments(bem_plan *P, const void *phi, const void *chi, cudaStream_t s);
 int build_near_items(bem_plan *P);
+int diagonal_prepare(bem_plan *P, cudaStream_t s);
+int diagonal_product(bem_plan *P, cudaStream_t s);
+int diagonal_finish(bem_plan *P, cudaStream_t s);
 int enqueue_matvec(bem_plan *P, int op, int green, double k, cudaStream_t s);
 int set_slots(bem_plan *P, const void *x, void *y, cudaStream_t s);
 int enqueue_matvec_raw(bem_plan *P, int op, int green, double k, int with_diag, cudaStream_t s,
                        cudaEvent_t *ev = nullptr);
-int compute_diagonal(bem_plan *P, cudaStream_t s);
 int solve(bem_plan *P, const void *chi, void *phi, int nrhs, const bem_solve_params *sp,
           bem_solve_info *info, cudaStream_t s);
 int64_t mesh_chi_index(const double *nodes, int64_t nn, const int32_t *elems, int64_t ne, int npe,

@@ -972,32 +972,55 @@ int enqueue_matvec_raw(bem_plan *P, int op, int green, double kwave, int with_di
 // in full; this one product therefore runs in float64 at the largest
 // supported order (error ~ eta^-(p+1)), on the same tree and lists, before
 // the buffers are sized for the plan's own order and precision.
-int compute_diagonal(bem_plan *P, cudaStream_t s) {
+// The order, precision and Green's function of the diagonal's product.
+struct DiagSwap {
+    int p, precision, green;
+};
+static DiagSwap diag_fields(const bem_plan *P) {
+    const bool mixed = P->prm.precision == BEM_MIXED;
+    return DiagSwap{mixed ? std::min(PMAX, P->prm.p + 4) : PMAX, mixed ? BEM_MIXED : BEM_F64, BEM_LAPLACE};
+}
+static DiagSwap swap_fields(bem_plan *P, const DiagSwap &d) {
+    const DiagSwap old{P->prm.p, P->prm.precision, P->green};
+    P->prm.p = d.p;
+    P->prm.precision = d.precision;
+    P->green = d.green;
+    return old;
+}
+
+// Three steps, so that the product can run on its own stream beside the
+// correction: prepare (buffers and tables at the diagonal's order; all
+// allocations happen here), product (phi = 1, into ytmp), finish (C += ytmp
+// once the correction's row sums are in C, then the buffers of the plan's own
+// order).  The plan's fields are switched only while each step runs.
+int diagonal_prepare(bem_plan *P, cudaStream_t s) {
+    const DiagSwap keep = swap_fields(P, diag_fields(P));
+    int rc = alloc_fmm(P, s);
+    if (rc == BEM_OK) rc = P->arena.alloc(&P->diag_ones, P->N);
+    swap_fields(P, keep);
+    return rc;
+}
+
+int diagonal_product(bem_plan *P, cudaStream_t s) {
     const int N = (int)P->N;
-    const int p_keep = P->prm.p, prec_keep = P->prm.precision, green_keep = P->green;
-    // the diagonal uses the Laplace kernel whatever the plan's Green's function:
-    // buffers and derivative tables are built for a real Laplace product.  A
-    // float64 plan takes order PMAX in float64; a mixed plan, whose stated
-    // error is larger, takes order p + 4 in float32 (truncation reduced by
-    // about eta^-4 against its own order).
-    const bool mixed = prec_keep == BEM_MIXED;
-    P->prm.p = mixed ? std::min(PMAX, p_keep + 4) : PMAX;
-    P->prm.precision = mixed ? BEM_MIXED : BEM_F64;
-    P->green = BEM_LAPLACE;
-    BEM_TRY(alloc_fmm(P, s));
-    double *ones = nullptr;
-    BEM_TRY(P->arena.alloc(&ones, N));
-    (k_fill<<<(N + 255) / 256, 256, 0, s>>>(N, 1.0, ones), ::bem::count_launch());
-    BEM_TRY(set_slots(P, ones, nullptr, s));
-    BEM_TRY(enqueue_matvec_raw(P, BEM_OP_A, BEM_LAPLACE, 0.0, 0, s, nullptr));
+    const DiagSwap keep = swap_fields(P, diag_fields(P));
+    (k_fill<<<(N + 255) / 256, 256, 0, s>>>(N, 1.0, P->diag_ones), ::bem::count_launch());
+    int rc = set_slots(P, P->diag_ones, nullptr, s);
+    if (rc == BEM_OK) rc = enqueue_matvec_raw(P, BEM_OP_A, BEM_LAPLACE, 0.0, 0, s, nullptr);
+    swap_fields(P, keep);
+    return rc;
+}
+
+int diagonal_finish(bem_plan *P, cudaStream_t s) {
+    const int N = (int)P->N;
     (k_finish_diag<<<(N + 255) / 256, 256, 0, s>>>(N, P->ytmp, P->C), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
     BEM_CUDA(cudaStreamSynchronize(s));
-    P->arena.release(ones);
+    P->arena.release(P->diag_ones);
+    P->diag_ones = nullptr;
+    const DiagSwap keep = swap_fields(P, diag_fields(P));
     free_fmm(P);
-    P->prm.p = p_keep;
-    P->prm.precision = prec_keep;
-    P->green = green_keep;
+    swap_fields(P, keep);
     return alloc_fmm(P, s);
 }
 

@@ -921,6 +921,10 @@ int build_correction(bem_plan *P, cudaStream_t s) {
     double *d0pair, *d0row;
     BEM_TRY(A.alloc(&d0pair, npairs));
     BEM_TRY(A.alloc(&d0row, N));
+    // every allocation comes before the long kernels, so that work other
+    // streams enqueue next can overlap them
+    BEM_TRY(A.alloc(&K.fvalD, K.nnzD * C));
+    BEM_TRY(A.alloc(&K.fvalS, K.nnzS * C));
     (k_rows_ptr<<<(N + 256) / 256, 256, 0, s>>>(N, npe, off, K.ptrD), ::bem::count_launch());
     (k_corr_csr<<<(npairs + 255) / 256, 256, 0, s>>>(npairs, npe, pair_e, t.el_phi, t.el_chi, K.colD, K.colS), ::bem::count_launch());
     {
@@ -947,8 +951,6 @@ int build_correction(bem_plan *P, cudaStream_t s) {
     }
     (k_d0_rowsum<<<(N + 255) / 256, 256, 0, s>>>(N, off, d0pair, d0row), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
-    BEM_TRY(A.alloc(&K.fvalD, K.nnzD * C));
-    BEM_TRY(A.alloc(&K.fvalS, K.nnzS * C));
     int64_t nv = K.nnzD * C;
     (k_to_float<<<(int)((nv + 255) / 256), 256, 0, s>>>(nv, K.valD, K.fvalD), ::bem::count_launch());
     (k_to_float<<<(int)((nv + 255) / 256), 256, 0, s>>>(nv, K.valS, K.fvalS), ::bem::count_launch());
@@ -956,10 +958,10 @@ int build_correction(bem_plan *P, cudaStream_t s) {
     // the diagonal starts as 1 + (correction row sum of D0); the regular part
     // is added by one Laplace double-layer product on phi = 1
     P->C = d0row;
-    BEM_CUDA(cudaStreamSynchronize(s));
-    A.release(cnt); A.release(tot); A.release(pair_node); A.release(d0pair);
-    A.release(ecx); A.release(ecy); A.release(ecz); A.release(eh); A.release(ebnd); A.release(frho); A.release(rho); A.release(off);
-    A.release(pair_e);
+    // the temporaries are released once the stream has finished with them
+    for (void *q : {(void *)cnt, (void *)tot, (void *)pair_node, (void *)d0pair, (void *)ecx, (void *)ecy, (void *)ecz,
+                    (void *)eh, (void *)ebnd, (void *)frho, (void *)rho, (void *)off, (void *)pair_e})
+        P->deferred.push_back(q);
     return BEM_OK;
 }
 
