@@ -222,6 +222,9 @@ struct bem_plan {
     int64_t near_pairs = 0;
     std::vector<void *> deferred;       // set-up temporaries released after the next synchronisation
     double *diag_ones = nullptr;        // phi = 1 of the diagonal's product (set-up only)
+    bool diag_mode = false;             // alloc_fmm for the diagonal's order
+    float *p2m_W = nullptr;             // [Q][np] stored double-layer P2M weights (float32 plans)
+    float *xf = nullptr;                // float32 copy of a product's input (correction product)
     cudaStream_t setup_stream[2] = {nullptr, nullptr};
     int2 *near_items[2] = {nullptr, nullptr};   // float32 near-field work items, 64- and 32-target passes
     int near_nitems[2] = {0, 0};

@@ -81,9 +81,11 @@ __global__ void k_p2q(int Q, int npe, const int *__restrict__ el_idx, const doub
 // ---------------------------------------------------------------------------
 constexpr int P2M_T = 128, P2M_B = 32, P2M_SLOTS = (969 + P2M_T - 1) / P2M_T;
 
-template <class R, int C, bool DL>
+// WEIGHTS: instead of the moments, write each point's row of P2M weights
+// W[o][a] (the value that multiplies f[o] in moment a) for the stored form.
+template <class R, int C, bool DL, bool WEIGHTS = false>
 __global__ void __launch_bounds__(P2M_T) k_p2m(int nleaf, Tabs tb, TreeView tv, QuadView qv, const R *__restrict__ f,
-                                               R *__restrict__ M, const int *__restrict__ skip) {
+                                               R *__restrict__ M, const int *__restrict__ skip, R *__restrict__ W = nullptr) {
     if (skip && *skip) return;
     const int li = blockIdx.x;
     if (li >= nleaf) return;
@@ -132,8 +134,9 @@ __global__ void __launch_bounds__(P2M_T) k_p2m(int nleaf, Tabs tb, TreeView tv, 
         } else if (tid < 3 * P2M_B + P2M_B) {
             int pt = tid - 3 * P2M_B;
             int o = base + pt;
+            if (!WEIGHTS)
 #pragma unroll
-            for (int c = 0; c < C; c++) sf[pt][c] = pt < nb ? f[(size_t)o * C + c] : (R)0;
+                for (int c = 0; c < C; c++) sf[pt][c] = pt < nb ? f[(size_t)o * C + c] : (R)0;
             if (DL) {
                 if constexpr (sizeof(R) == sizeof(double)) {
                     sn[0][pt] = pt < nb ? (R)qv.nx[o] : (R)0;
@@ -162,11 +165,16 @@ __global__ void __launch_bounds__(P2M_T) k_p2m(int nleaf, Tabs tb, TreeView tv, 
                     if (k) val += (R)k * sn[2][pt] * pw[0][pt][m] * pw[1][pt][n] * pw[2][pt][k - 1];
                     val *= hinv;
                 }
+                if (WEIGHTS) {
+                    W[(size_t)(base + pt) * np + tid + s * P2M_T] = val;
+                } else {
 #pragma unroll
-                for (int c = 0; c < C; c++) acc[s][c] += val * sf[pt][c];
+                    for (int c = 0; c < C; c++) acc[s][c] += val * sf[pt][c];
+                }
             }
         }
     }
+    if (WEIGHTS) return;
 #pragma unroll
     for (int s = 0; s < P2M_SLOTS; s++) {
         int a = tid + s * P2M_T;
@@ -174,6 +182,69 @@ __global__ void __launch_bounds__(P2M_T) k_p2m(int nleaf, Tabs tb, TreeView tv, 
 #pragma unroll
             for (int c = 0; c < C; c++) M[((size_t)b * np + a) * C + c] = acc[s][c];
     }
+}
+
+// ---------------------------------------------------------------------------
+// P2M from stored weights (float32 double-layer moments): M[a] = sum over the
+// leaf's points of W[o][a] f[o] with W the values the on-the-fly form builds;
+// each product only streams the weight rows (coalesced across the indices a),
+// two halves of the block taking alternate chunks of points to keep more
+// loads in flight.
+// ---------------------------------------------------------------------------
+constexpr int P2S_T = 2 * P2M_T, P2S_U = 8;           // two halves of P2M_T threads; points per chunk
+
+template <int C>
+__global__ void __launch_bounds__(P2S_T) k_p2m_stored(int nleaf, int np, TreeView tv, const float *__restrict__ W,
+                                                      const float *__restrict__ f, float *__restrict__ M,
+                                                      const int *__restrict__ skip) {
+    if (skip && *skip) return;
+    const int li = blockIdx.x;
+    if (li >= nleaf) return;
+    __shared__ float part[P2M_SLOTS][C][P2M_T];
+    const int b = tv.leaves[li], half = threadIdx.x / P2M_T, tid = threadIdx.x % P2M_T;
+    const int q0 = tv.eb[b] * NQ, q1 = tv.ee[b] * NQ;
+    float acc[P2M_SLOTS][C];
+#pragma unroll
+    for (int s = 0; s < P2M_SLOTS; s++)
+#pragma unroll
+        for (int c = 0; c < C; c++) acc[s][c] = 0.f;
+    // chunks of P2S_U points alternate between the halves; within a half the
+    // points are summed in order, then half 1's sums are added to half 0's
+    for (int o0 = q0 + half * P2S_U; o0 < q1; o0 += 2 * P2S_U) {
+        const int n = min(P2S_U, q1 - o0);
+        float w[P2S_U][P2M_SLOTS], fv[P2S_U][C];
+#pragma unroll
+        for (int u = 0; u < P2S_U; u++) {
+            const bool on = u < n;
+#pragma unroll
+            for (int c = 0; c < C; c++) fv[u][c] = on ? __ldg(f + (size_t)(o0 + u) * C + c) : 0.f;
+#pragma unroll
+            for (int s = 0; s < P2M_SLOTS; s++) {
+                const int a = tid + s * P2M_T;
+                w[u][s] = on && a < np ? __ldg(W + (size_t)(o0 + u) * np + a) : 0.f;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < P2S_U; u++)
+#pragma unroll
+            for (int s = 0; s < P2M_SLOTS; s++)
+#pragma unroll
+                for (int c = 0; c < C; c++) acc[s][c] += w[u][s] * fv[u][c];
+    }
+    if (half == 1)
+#pragma unroll
+        for (int s = 0; s < P2M_SLOTS; s++)
+#pragma unroll
+            for (int c = 0; c < C; c++) part[s][c][tid] = acc[s][c];
+    __syncthreads();
+    if (half == 0)
+#pragma unroll
+        for (int s = 0; s < P2M_SLOTS; s++) {
+            const int a = tid + s * P2M_T;
+            if (a < np)
+#pragma unroll
+                for (int c = 0; c < C; c++) M[((size_t)b * np + a) * C + c] = acc[s][c] + part[s][c][tid];
+        }
 }
 
 // ---------------------------------------------------------------------------
@@ -729,6 +800,56 @@ __global__ void k_combine(int N, const int *__restrict__ ptr, const int *__restr
     }
 }
 
+// float32 correction product (mixed plans): the vector is first copied to
+// float32 (one conversion per entry instead of one per nonzero: float64
+// arithmetic is a small fraction of the float32 rate), each lane sums its
+// nonzeros with compensation, the lanes' sums combine in float64.
+__global__ void k_x_float(int64_t n, const void *const *__restrict__ xslot, float *__restrict__ xf,
+                          const int *__restrict__ skip) {
+    if (skip && *skip) return;
+    const double *x = (const double *)*xslot;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        xf[i] = (float)x[i];
+}
+
+template <int C, bool OPA>
+__global__ void k_combine_f(int N, const int *__restrict__ ptr, const int *__restrict__ col,
+                            const float *__restrict__ val, const float *__restrict__ xf,
+                            const double *__restrict__ Cdiag, const double *__restrict__ ytmp,
+                            const void *const *__restrict__ xslot, void *const *__restrict__ yslot,
+                            const int *__restrict__ skip) {
+    if (skip && *skip) return;
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (w >= N) return;
+    KahanF k[C];
+    for (int q = ptr[w] + lane; q < ptr[w + 1]; q += 32) {
+        const int j = __ldg(col + q);
+        if (C == 1) {
+            k[0].add(__ldg(val + q) * __ldg(xf + j));
+        } else {
+            const float2 v = __ldg(reinterpret_cast<const float2 *>(val) + q);
+            const float2 x = __ldg(reinterpret_cast<const float2 *>(xf) + j);
+            k[0].add(fmaf(v.x, x.x, -v.y * x.y));
+            k[C - 1].add(fmaf(v.x, x.y, v.y * x.x));
+        }
+    }
+    double s[C];
+#pragma unroll
+    for (int c = 0; c < C; c++) {
+        s[c] = (double)k[c].s - (double)k[c].c;
+        for (int off = 16; off; off >>= 1) s[c] += __shfl_xor_sync(0xffffffffu, s[c], off);
+    }
+    if (lane == 0) {
+        const double *x = (const double *)*xslot;
+        double *y = (double *)*yslot;
+#pragma unroll
+        for (int c = 0; c < C; c++) {
+            const double tot = ytmp[(size_t)w * C + c] + s[c];
+            y[(size_t)w * C + c] = OPA ? Cdiag[w] * x[(size_t)w * C + c] - tot : -tot;
+        }
+    }
+}
+
 // C_i = 1 + (regular Laplace double layer of phi = 1) + (correction row sum)
 __global__ void k_finish_diag(int N, const double *__restrict__ ytmp, double *Cdiag) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -851,6 +972,15 @@ int alloc_fmm(bem_plan *P, cudaStream_t s) {
     BEM_TRY(A.alloc(&P->ytmp, (size_t)P->N * C));
     BEM_TRY(A.alloc(&P->xptr, 2));
     BEM_TRY(A.alloc(&P->yptr, 2));
+    if (mx) BEM_TRY(A.alloc(&P->xf, (size_t)std::max(P->N, P->nchi) * C));
+    if (mx && !P->diag_mode) {
+        // stored P2M weights of the double layer (op A, every product of a solve)
+        BEM_TRY(A.alloc(&P->p2m_W, (size_t)P->Q * np));
+        const Tree &t = P->t;
+        (k_p2m<float, 1, true, true><<<t.nleaf, P2M_T, 0, s>>>(t.nleaf, tabs_of(P), view_of(P), quad_of(P), nullptr,
+                                                                nullptr, nullptr, P->p2m_W), ::bem::count_launch());
+        BEM_LAUNCH_CHECK();
+    }
     set_translation_attributes();
     set_near_attributes();
     BEM_TRY(build_translation_tables(P, s));
@@ -873,8 +1003,15 @@ static int run_fmm(bem_plan *P, int op, double kwave, R *f, R *M, R *L, cudaStre
     const int Q = (int)P->Q;
     (k_p2q<R, C><<<(Q + 255) / 256, 256, 0, s>>>(Q, P->npe, el, P->q.w, P->xptr, f, sk), ::bem::count_launch());
     if (ev) BEM_CUDA(cudaEventRecord(ev[1], s));
-    if (op == BEM_OP_A) (k_p2m<R, C, true><<<t.nleaf, P2M_T, 0, s>>>(t.nleaf, tb, tv, qv, f, M, sk), ::bem::count_launch());
-    else (k_p2m<R, C, false><<<t.nleaf, P2M_T, 0, s>>>(t.nleaf, tb, tv, qv, f, M, sk), ::bem::count_launch());
+    if constexpr (sizeof(R) == sizeof(float)) {
+        if (op == BEM_OP_A && P->p2m_W)
+            (k_p2m_stored<C><<<t.nleaf, P2S_T, 0, s>>>(t.nleaf, np, tv, P->p2m_W, f, M, sk), ::bem::count_launch());
+        else if (op == BEM_OP_A) (k_p2m<R, C, true><<<t.nleaf, P2M_T, 0, s>>>(t.nleaf, tb, tv, qv, f, M, sk), ::bem::count_launch());
+        else (k_p2m<R, C, false><<<t.nleaf, P2M_T, 0, s>>>(t.nleaf, tb, tv, qv, f, M, sk), ::bem::count_launch());
+    } else {
+        if (op == BEM_OP_A) (k_p2m<R, C, true><<<t.nleaf, P2M_T, 0, s>>>(t.nleaf, tb, tv, qv, f, M, sk), ::bem::count_launch());
+        else (k_p2m<R, C, false><<<t.nleaf, P2M_T, 0, s>>>(t.nleaf, tb, tv, qv, f, M, sk), ::bem::count_launch());
+    }
     BEM_LAUNCH_CHECK();
     if (ev) BEM_CUDA(cudaEventRecord(ev[2], s));
     BEM_TRY((launch_translations<R, C>(P, M, L, s, ev)));
@@ -958,7 +1095,20 @@ int enqueue_matvec_raw(bem_plan *P, int op, int green, double kwave, int with_di
         if (C == 1) (k_combine<RV, 1, false><<<blocks, 256, 0, s>>>(N, K.ptrS, K.colS, VS, P->C, P->ytmp, P->xptr, P->yptr, P->skip), ::bem::count_launch()); \
         else (k_combine<RV, 2, false><<<blocks, 256, 0, s>>>(N, K.ptrS, K.colS, VS, P->C, P->ytmp, P->xptr, P->yptr, P->skip), ::bem::count_launch());       \
     }
-    if (mx) { BEM_COMBINE(float, K.fvalD, K.fvalS) } else { BEM_COMBINE(double, K.valD, K.valS) }
+    if (mx) {
+        const int64_t nx = (int64_t)(op == BEM_OP_A ? N : P->nchi) * C;
+        (k_x_float<<<(int)std::min<int64_t>((nx + 255) / 256, 4096), 256, 0, s>>>(nx, P->xptr, P->xf, P->skip),
+         ::bem::count_launch());
+        if (op == BEM_OP_A) {
+            if (C == 1) (k_combine_f<1, true><<<blocks, 256, 0, s>>>(N, K.ptrD, K.colD, K.fvalD, P->xf, P->C, P->ytmp, P->xptr, P->yptr, P->skip), ::bem::count_launch());
+            else (k_combine_f<2, true><<<blocks, 256, 0, s>>>(N, K.ptrD, K.colD, K.fvalD, P->xf, P->C, P->ytmp, P->xptr, P->yptr, P->skip), ::bem::count_launch());
+        } else {
+            if (C == 1) (k_combine_f<1, false><<<blocks, 256, 0, s>>>(N, K.ptrS, K.colS, K.fvalS, P->xf, P->C, P->ytmp, P->xptr, P->yptr, P->skip), ::bem::count_launch());
+            else (k_combine_f<2, false><<<blocks, 256, 0, s>>>(N, K.ptrS, K.colS, K.fvalS, P->xf, P->C, P->ytmp, P->xptr, P->yptr, P->skip), ::bem::count_launch());
+        }
+    } else {
+        BEM_COMBINE(double, K.valD, K.valS)
+    }
 #undef BEM_COMBINE
     BEM_LAUNCH_CHECK();
     if (ev) BEM_CUDA(cudaEventRecord(ev[7], s));
@@ -995,7 +1145,9 @@ static DiagSwap swap_fields(bem_plan *P, const DiagSwap &d) {
 // order).  The plan's fields are switched only while each step runs.
 int diagonal_prepare(bem_plan *P, cudaStream_t s) {
     const DiagSwap keep = swap_fields(P, diag_fields(P));
+    P->diag_mode = true;                              // no stored weights at the diagonal's order
     int rc = alloc_fmm(P, s);
+    P->diag_mode = false;
     if (rc == BEM_OK) rc = P->arena.alloc(&P->diag_ones, P->N);
     swap_fields(P, keep);
     return rc;
@@ -1030,8 +1182,10 @@ void free_fmm(bem_plan *P) {
     Arena &A = P->arena;
     for (void *q : {(void *)P->d_m, (void *)P->d_n, (void *)P->d_k, (void *)P->d_idx3, (void *)P->d_fact,
                     (void *)P->d_binom, (void *)P->f, (void *)P->M, (void *)P->L, (void *)P->ff, (void *)P->fM,
-                    (void *)P->fL, (void *)P->ytmp, (void *)P->xptr, (void *)P->yptr})
+                    (void *)P->fL, (void *)P->ytmp, (void *)P->xptr, (void *)P->yptr, (void *)P->p2m_W, (void *)P->xf})
         A.release(q);
+    P->p2m_W = nullptr;
+    P->xf = nullptr;
     P->d_m = P->d_n = P->d_k = P->d_idx3 = nullptr;
     P->d_fact = P->d_binom = nullptr;
     P->f = P->M = P->L = P->ytmp = nullptr;
