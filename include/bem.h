@@ -93,8 +93,12 @@ typedef struct {
 typedef struct {
     int restart;      /* GMRES restart length (30) */
     double tol;       /* stop when ||b - A x|| / ||b|| <= tol */
-    int max_iter;     /* total Arnoldi steps allowed */
+    int max_iter;     /* total Arnoldi steps (GMRES) or iterations (BiCGStab) allowed */
+    int method;       /* BEM_GMRES (default) or BEM_BICGSTAB (bem_solve only) */
 } bem_solve_params;
+
+#define BEM_GMRES 0
+#define BEM_BICGSTAB 1   /* the paper's solver (Section 4): two products per iteration */
 
 typedef struct {
     int iters;            /* Arnoldi steps taken */

@@ -20,6 +20,7 @@ BEM_TRI3, BEM_TRI6 = 1, 2
 BEM_LAPLACE, BEM_HELMHOLTZ = 0, 1
 BEM_F64, BEM_MIXED = 0, 1
 BEM_OP_A, BEM_OP_B = 0, 1
+BEM_GMRES, BEM_BICGSTAB = 0, 1
 
 # every symbol include/bem.h declares
 EXPORTS = [
@@ -46,7 +47,7 @@ class bem_fmm_params(C.Structure):
 
 
 class bem_solve_params(C.Structure):
-    _fields_ = [("restart", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int)]
+    _fields_ = [("restart", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int), ("method", C.c_int)]
 
 
 class bem_solve_info(C.Structure):

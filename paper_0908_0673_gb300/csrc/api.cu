@@ -222,6 +222,7 @@ void bem_solve_params_default(bem_solve_params *p) {
     p->restart = 30;
     p->tol = 1e-10;
     p->max_iter = 1000;
+    p->method = BEM_GMRES;
 }
 
 int bem_ctx_create(int device, bem_ctx **out) {
@@ -317,6 +318,7 @@ int bem_solve(bem_plan *P, const void *chi_dev, void *phi_dev, int nrhs, const b
     bem_solve_params_default(&sp);
     if (params) sp = *params;
     if (!(sp.tol > 0.0) || sp.max_iter < 1) { set_error("bem_solve: tol must be > 0 and max_iter >= 1"); return BEM_EINVAL; }
+    if (sp.method != BEM_GMRES && sp.method != BEM_BICGSTAB) { set_error("bem_solve: unknown method %d", sp.method); return BEM_EINVAL; }
     cudaStream_t s = (cudaStream_t)cuda_stream;
     BEM_CUDA(cudaMemsetAsync(P->skip, 0, sizeof(int), s));
     return solve(P, chi_dev, phi_dev, nrhs, &sp, info, s);

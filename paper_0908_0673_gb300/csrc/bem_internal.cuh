@@ -231,6 +231,8 @@ struct bem_plan {
     int last_op = -1;
     // GMRES workspace
     double *V = nullptr, *H = nullptr, *gs = nullptr, *w = nullptr, *xk = nullptr, *bvec = nullptr;
+    double *bc_vec = nullptr, *bc_sc = nullptr;   // BiCGStab vectors (r, rh, p, v, s, t) and scalars
+    int *bc_st = nullptr;
     double *scal = nullptr;             // device scalars
     double *hostbuf = nullptr;          // pinned read-back of GMRES scalars
     void **gm_slot = nullptr;           // device pointer slots of the current solve: [0] chi, [1] x

@@ -618,8 +618,281 @@ static int gm_run(GmSolver &g, bool blocking) {
     return g.P->green == BEM_HELMHOLTZ ? gm_advance<2>(g, blocking) : gm_advance<1>(g, blocking);
 }
 
+// ---------------------------------------------------------------------------
+// BiCGStab (the paper's solver, Section 4), device resident in float64:
+//   rho = rh^H r, beta = (rho / rho_prev)(alpha / omega), p = r + beta (p - omega v),
+//   v = A p, alpha = rho / (rh^H v), s = r - alpha v, t = A s,
+//   omega = (t^H s) / (t^H t), x += alpha p + omega s, r = s - omega t,
+// with rh the residual at the (re)start.  The iteration stops on the device
+// (the shared skip flag) once ||r|| / ||b|| reaches the tolerance or a
+// denominator vanishes; the host then evaluates the true residual b - A x and
+// restarts from it (rh = r) while it is above the tolerance, with the same
+// stopping rule as GMRES (mixed plans: max(tol, TAU_MIXED), or a restart that
+// fails to halve the true residual).  Steps go out in chunks of four with at
+// most two in flight, each chunk reading back the flag.
+// ---------------------------------------------------------------------------
+struct BcState {
+    // scalars (complex as pairs): [0] rho, [2] rho_prev, [4] alpha, [6] omega,
+    // [8] rh^H v, [10] t^H s, [12] ||t||, [13] ||r||, [14] ||r|| / ||b||
+    double *sc;
+    int *st;                            // [0] steps since the (re)start, [1] breakdown
+    double *r, *rh, *p, *v, *s, *t;
+    const double *bn, *tol;             // ||b|| and the tolerance (GMRES scalars 0 and 3)
+};
+
+static int bc_workspace(bem_plan *P) {
+    const int C = P->green == BEM_HELMHOLTZ ? 2 : 1;
+    if (!P->bc_vec) {
+        BEM_TRY(P->arena.alloc(&P->bc_vec, (size_t)6 * P->N * C));
+        BEM_TRY(P->arena.alloc(&P->bc_sc, 32));
+        BEM_TRY(P->arena.alloc(&P->bc_st, 4));
+    }
+    return BEM_OK;
+}
+
+static BcState bc_state(bem_plan *P, int C) {
+    const size_t ne = (size_t)P->N * C;
+    double *b = P->bc_vec;
+    return BcState{P->bc_sc, P->bc_st, b, b + ne, b + 2 * ne, b + 3 * ne, b + 4 * ne, b + 5 * ne, P->scal, P->scal + 3};
+}
+
+__device__ __forceinline__ void cmul(double ar, double ai, double br, double bi, double &cr, double &ci) {
+    cr = ar * br - ai * bi;
+    ci = ar * bi + ai * br;
+}
+__device__ __forceinline__ void cdiv(double ar, double ai, double br, double bi, double &cr, double &ci) {
+    const double d = br * br + bi * bi;
+    cr = (ar * br + ai * bi) / d;
+    ci = (ai * br - ar * bi) / d;
+}
+
+// at a (re)start: rh = r, p = v = 0, rho_prev = alpha = omega = 1
+template <int C>
+__global__ void k_bc_reset(int ne, BcState B) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < ne) {
+        B.rh[i] = B.r[i];
+        B.p[i] = 0.0;
+        B.v[i] = 0.0;
+    }
+    if (i == 0) {
+        B.sc[2] = 1.0; B.sc[3] = 0.0; B.sc[4] = 1.0; B.sc[5] = 0.0; B.sc[6] = 1.0; B.sc[7] = 0.0;
+        B.st[0] = 0;
+        B.st[1] = 0;
+    }
+}
+
+// p = r + beta (p - omega v)
+template <int C>
+__global__ void k_bc_p(int n, BcState B, const int *__restrict__ skip) {
+    if (*skip) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double q0, q1, br, bi;
+    cdiv(B.sc[0], C == 2 ? B.sc[1] : 0.0, B.sc[2], C == 2 ? B.sc[3] : 0.0, q0, q1);
+    double a0, a1;
+    cdiv(B.sc[4], C == 2 ? B.sc[5] : 0.0, B.sc[6], C == 2 ? B.sc[7] : 0.0, a0, a1);
+    cmul(q0, q1, a0, a1, br, bi);
+    if (C == 1) {
+        B.p[i] = B.r[i] + br * (B.p[i] - B.sc[6] * B.v[i]);
+    } else {
+        double wr, wi;
+        cmul(B.sc[6], B.sc[7], B.v[2 * i], B.v[2 * i + 1], wr, wi);
+        const double dr = B.p[2 * i] - wr, di = B.p[2 * i + 1] - wi;
+        double er, ei;
+        cmul(br, bi, dr, di, er, ei);
+        B.p[2 * i] = B.r[2 * i] + er;
+        B.p[2 * i + 1] = B.r[2 * i + 1] + ei;
+    }
+}
+
+// alpha = rho / (rh^H v), s = r - alpha v; a vanishing denominator stops the run
+template <int C>
+__global__ void k_bc_s(int n, BcState B, int *skip) {
+    if (*skip) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const double sr = B.sc[8], si = C == 2 ? B.sc[9] : 0.0;
+    if (sr == 0.0 && si == 0.0) {
+        if (i == 0) B.st[1] = 1;
+        return;
+    }
+    double ar, ai;
+    cdiv(B.sc[0], C == 2 ? B.sc[1] : 0.0, sr, si, ar, ai);
+    if (i == 0) { B.sc[4] = ar; B.sc[5] = ai; }
+    if (i >= n) return;
+    if (C == 1) {
+        B.s[i] = B.r[i] - ar * B.v[i];
+    } else {
+        double wr, wi;
+        cmul(ar, ai, B.v[2 * i], B.v[2 * i + 1], wr, wi);
+        B.s[2 * i] = B.r[2 * i] - wr;
+        B.s[2 * i + 1] = B.r[2 * i + 1] - wi;
+    }
+}
+
+// omega = (t^H s) / ||t||^2, x += alpha p + omega s, r = s - omega t
+template <int C>
+__global__ void k_bc_xr(int n, BcState B, void *const *xslot, const int *skip) {
+    if (*skip || B.st[1]) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const double tt = B.sc[12] * B.sc[12];
+    double wr = 0.0, wi = 0.0;
+    if (tt > 0.0) {
+        wr = B.sc[10] / tt;
+        wi = C == 2 ? B.sc[11] / tt : 0.0;
+    }
+    if (i == 0) { B.sc[6] = wr; B.sc[7] = wi; }
+    if (i >= n) return;
+    double *x = (double *)*xslot;
+    const double ar = B.sc[4], ai = C == 2 ? B.sc[5] : 0.0;
+    if (C == 1) {
+        x[i] += ar * B.p[i] + wr * B.s[i];
+        B.r[i] = B.s[i] - wr * B.t[i];
+    } else {
+        double pr, pi, qr, qi, tr, ti;
+        cmul(ar, ai, B.p[2 * i], B.p[2 * i + 1], pr, pi);
+        cmul(wr, wi, B.s[2 * i], B.s[2 * i + 1], qr, qi);
+        cmul(wr, wi, B.t[2 * i], B.t[2 * i + 1], tr, ti);
+        x[2 * i] += pr + qr;
+        x[2 * i + 1] += pi + qi;
+        B.r[2 * i] = B.s[2 * i] - tr;
+        B.r[2 * i + 1] = B.s[2 * i + 1] - ti;
+    }
+}
+
+// end of a step: residual estimate, step count, stop flag
+__global__ void k_bc_check(BcState B, int *skip, int max_steps) {
+    if (*skip) return;
+    const double bn = *B.bn;
+    const double est = bn > 0.0 ? B.sc[13] / bn : 0.0;
+    B.sc[14] = est;
+    B.st[0] += 1;
+    B.sc[2] = B.sc[0];
+    B.sc[3] = B.sc[1];
+    const bool wzero = B.sc[6] == 0.0 && B.sc[7] == 0.0;
+    if (B.st[1] || wzero) B.st[1] = 1;
+    if (est <= *B.tol || B.st[1] || B.st[0] >= max_steps) *skip = 1;
+}
+
+template <int C>
+static int bc_k_step(bem_plan *P, const BcState &B, int max_steps, cudaStream_t s) {
+    const int n = (int)P->N, nb = (n + 255) / 256;
+    const size_t ld = (size_t)n * C;
+    double *partial = P->scal + 16;
+    int *skip = P->istate;
+    (k_mdot<C><<<GM_BLK, GM_T, 0, s>>>(n, 1, B.rh, ld, B.r, partial, skip), ::bem::count_launch());
+    (k_mdot_final<C><<<1, 32, 0, s>>>(1, partial, B.sc + 0, 0, skip), ::bem::count_launch());
+    (k_bc_p<C><<<nb, 256, 0, s>>>(n, B, skip), ::bem::count_launch());
+    BEM_TRY(set_slots(P, B.p, B.v, s));
+    BEM_TRY(gm_product(P, BEM_OP_A, s, false));
+    (k_mdot<C><<<GM_BLK, GM_T, 0, s>>>(n, 1, B.rh, ld, B.v, partial, skip), ::bem::count_launch());
+    (k_mdot_final<C><<<1, 32, 0, s>>>(1, partial, B.sc + 8, 0, skip), ::bem::count_launch());
+    (k_bc_s<C><<<nb, 256, 0, s>>>(n, B, skip), ::bem::count_launch());
+    BEM_TRY(set_slots(P, B.s, B.t, s));
+    BEM_TRY(gm_product(P, BEM_OP_A, s, false));
+    (k_mdot<C><<<GM_BLK, GM_T, 0, s>>>(n, 1, B.t, ld, B.s, partial, skip), ::bem::count_launch());
+    (k_mdot_final<C><<<1, 32, 0, s>>>(1, partial, B.sc + 10, 0, skip), ::bem::count_launch());
+    (k_nrm2_partial<C><<<GM_BLK, GM_T, 0, s>>>(n, B.t, partial, skip), ::bem::count_launch());
+    (k_nrm2_final<<<1, 32, 0, s>>>(partial, B.sc + 12, skip), ::bem::count_launch());
+    (k_bc_xr<C><<<nb, 256, 0, s>>>(n, B, (void *const *)P->gm_slot + 1, skip), ::bem::count_launch());
+    (k_nrm2_partial<C><<<GM_BLK, GM_T, 0, s>>>(n, B.r, partial, skip), ::bem::count_launch());
+    (k_nrm2_final<<<1, 32, 0, s>>>(partial, B.sc + 13, skip), ::bem::count_launch());
+    (k_bc_check<<<1, 1, 0, s>>>(B, skip, max_steps), ::bem::count_launch());
+    BEM_LAUNCH_CHECK();
+    return BEM_OK;
+}
+
+template <int C>
+static int bicgstab_one(bem_plan *P, const double *chi, double *x, const bem_solve_params &sp, bem_solve_info *info,
+                        cudaStream_t s) {
+    BEM_TRY(gm_workspace(P, P->gm_restart > 0 ? P->gm_restart : 1));
+    BEM_TRY(bc_workspace(P));
+    const BcState B = bc_state(P, C);
+    const size_t ne = (size_t)P->N * C;
+    const double tol = gm_tol(P, sp.tol);
+    const bool mixed = P->prm.precision == BEM_MIXED;
+    cudaEvent_t ev[2];
+    for (auto &e : ev) BEM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    auto done = [&](int rc) {
+        for (auto &e : ev) cudaEventDestroy(e);
+        return rc;
+    };
+    BEM_CUDA(cudaMemsetAsync(P->istate, 0, sizeof(int) * 3, s));
+    (k_set_ptrs<<<1, 1, 0, s>>>((void **)P->gm_slot, chi, x), ::bem::count_launch());
+    BEM_TRY(gm_k_start<C>(P, tol, s, false));                    // b, ||b||, x = 0
+    BEM_CUDA(cudaMemcpyAsync(B.r, P->bvec, sizeof(double) * ne, cudaMemcpyDeviceToDevice, s));
+    BEM_CUDA(cudaMemcpyAsync(P->hostbuf, P->scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+    BEM_CUDA(cudaStreamSynchronize(s));
+    const double bnorm = P->hostbuf[0];
+    int iters = 0, restarts = 0, status = BEM_ENOCONV;
+    double rel = bnorm > 0.0 ? 1.0 : 0.0, prev = 2.0;
+    if (bnorm == 0.0) status = BEM_OK;
+    while (status != BEM_OK && iters < sp.max_iter) {
+        const int budget = sp.max_iter - iters;
+        BEM_CUDA(cudaMemsetAsync(P->istate, 0, sizeof(int), s));
+        (k_bc_reset<C><<<(int)((ne + 255) / 256), 256, 0, s>>>((int)ne, B), ::bem::count_launch());
+        // chunks of steps, at most two in flight, each reading back the stop flag
+        int sent = 0, nfly = 0, seq = 0;
+        bool stop = false;
+        for (;;) {
+            if (!stop && sent < budget && nfly < 2) {
+                const int j1 = std::min(budget, sent + GM_CHUNK), k = (seq + nfly) & 1;
+                for (int j = sent; j < j1; j++) BEM_TRY(bc_k_step<C>(P, B, budget, s));
+                BEM_CUDA(cudaMemcpyAsync(P->hostbuf + 4 + k, P->istate, sizeof(int), cudaMemcpyDeviceToHost, s));
+                BEM_CUDA(cudaEventRecord(ev[k], s));
+                sent = j1;
+                nfly++;
+                continue;
+            }
+            if (nfly == 0) break;
+            const int k = seq & 1;
+            BEM_CUDA(cudaEventSynchronize(ev[k]));
+            int flag;
+            memcpy(&flag, P->hostbuf + 4 + k, sizeof(int));
+            nfly--;
+            seq++;
+            if (flag) stop = true;
+        }
+        int st[2];
+        BEM_CUDA(cudaMemcpyAsync(st, B.st, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+        // true residual r = b - A x (into V_0), its norm; the next run starts from it
+        BEM_TRY(gm_k_residual<C>(P, s, false));
+        BEM_CUDA(cudaMemcpyAsync(P->hostbuf, P->scal, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+        BEM_CUDA(cudaMemcpyAsync(B.r, P->V, sizeof(double) * ne, cudaMemcpyDeviceToDevice, s));
+        BEM_CUDA(cudaStreamSynchronize(s));
+        iters += st[0];
+        restarts++;
+        rel = P->hostbuf[1] / bnorm;
+        if (rel <= tol || (mixed && restarts > 1 && rel > 0.5 * prev)) {
+            status = BEM_OK;
+            break;
+        }
+        if (st[0] == 0) break;                               // no progress from this residual
+        prev = rel;
+    }
+    if (info) *info = bem_solve_info{iters, restarts, rel, status};
+    return done(status);
+}
+
+static int bicgstab(bem_plan *P, const void *chi, void *phi, int nrhs, const bem_solve_params *sp,
+                    bem_solve_info *info, cudaStream_t s) {
+    const int C = P->green == BEM_HELMHOLTZ ? 2 : 1;
+    const size_t nchi = (size_t)P->nchi * C, ne = (size_t)P->N * C;
+    int worst = BEM_OK;
+    for (int r = 0; r < nrhs; r++) {
+        const double *c = (const double *)chi + r * nchi;
+        double *x = (double *)phi + r * ne;
+        const int rc = C == 2 ? bicgstab_one<2>(P, c, x, *sp, info ? info + r : nullptr, s)
+                              : bicgstab_one<1>(P, c, x, *sp, info ? info + r : nullptr, s);
+        if (rc == BEM_ENOCONV) worst = BEM_ENOCONV;
+        else if (rc != BEM_OK) return rc;
+    }
+    return worst;
+}
+
 int solve(bem_plan *P, const void *chi, void *phi, int nrhs, const bem_solve_params *sp, bem_solve_info *info,
           cudaStream_t s) {
+    if (sp->method == BEM_BICGSTAB) return bicgstab(P, chi, phi, nrhs, sp, info, s);
     const int C = P->green == BEM_HELMHOLTZ ? 2 : 1;
     int worst = BEM_OK;
     const size_t nchi = (size_t)P->nchi * C, ne = (size_t)P->N * C;
@@ -783,6 +1056,7 @@ int bem_batch_submit(bem_batch *b, bem_plan *P, const void *chi_dev, void *phi_d
     bem_solve_params sp;
     bem_solve_params_default(&sp);
     if (params) sp = *params;
+    if (sp.method != BEM_GMRES) { set_error("bem_batch_submit: batched solves use GMRES"); return BEM_EINVAL; }
     int free_slot = -1;
     for (int i = 0; i < b->nslot; i++) {
         if (b->used[i] == 0 && free_slot < 0) free_slot = i;
@@ -907,6 +1181,7 @@ int bem_group_solve(bem_group *G, const void *const *chis, void *const *phis, co
     bem_solve_params_default(&sp);
     if (params) sp = *params;
     if (!(sp.tol > 0.0) || sp.max_iter < 1) { set_error("bem_group_solve: tol must be > 0 and max_iter >= 1"); return BEM_EINVAL; }
+    if (sp.method != BEM_GMRES) { set_error("bem_group_solve: group solves use GMRES"); return BEM_EINVAL; }
     BEM_CUDA(cudaSetDevice(G->device));
     const int n = G->n;
     const void **h_chi = (const void **)G->h_pin;
