@@ -282,6 +282,34 @@ def matvec_rate(bem, torch, mesh, stream, dev, prm, n_phi, flush):
     return rate, stages, setup_stages, st
 
 
+def solver_compare(bem, torch, mesh, stream, dev, prm, chi_d, n_phi, reps=3):
+    """GMRES and BiCGStab on one built plan (solve phase only, same RHS):
+    solves/s, iterations, products per solve, and the distance between the
+    two solutions."""
+    plan = bem.bem_plan_create(mesh, bem.BEM_LAPLACE, 0.0, prm, stream)
+    out, phis = {}, {}
+    for name, method in (("gmres", bem.BEM_GMRES), ("bicgstab", bem.BEM_BICGSTAB)):
+        sp = bem.bem_solve_params_default(restart=30, tol=1e-10, max_iter=600, method=method)
+        phi = torch.empty(n_phi, device=dev, dtype=torch.float64)
+        bem.bem_solve(plan, chi_d, phi, 1, sp, stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            code, info = bem.bem_solve(plan, chi_d, phi, 1, sp, stream)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        it = info[0].iters
+        out[name] = {"solve_ms": ms, "solves_per_s": 1000.0 / ms, "iters": it, "restarts": info[0].restarts,
+                     "products_per_solve": 1 + (it if method == bem.BEM_GMRES else 2 * it) + info[0].restarts,
+                     "rel_residual": info[0].rel_residual}
+        phis[name] = phi
+    out["rel_diff_bicgstab_vs_gmres"] = float(torch.linalg.norm(phis["bicgstab"] - phis["gmres"]) /
+                                              torch.linalg.norm(phis["gmres"]))
+    bem.bem_plan_destroy(plan)
+    return out
+
+
 def serving(args):
     """The same Poisson request stream twice: the mixed form with continuous
     batching, then the plain float64 form one request at a time."""
@@ -578,6 +606,8 @@ def main():
     }
     if other is not None:
         out["f64_form"] = other
+    if rank == 0 and world == 1:
+        out["solvers"] = solver_compare(bem, torch, mesh, stream, dev, prm, chi_d, n_phi)
     if rank == 0 and world == 1 and args.serve_requests > 0:
         out["serving"] = serving(args)
     if rank == 0 and world == 1 and args.group > 0:

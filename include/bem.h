@@ -77,7 +77,16 @@ typedef struct bem_plan bem_plan;
  *   precision    BEM_F64 or BEM_MIXED.
  *   n_duffy      Gauss-Legendre order of the Duffy self-element rule.
  *   tau_near     near-singular threshold: |x_i - X_e(1/3,1/3)| < tau h_e.
- *   max_subdiv   depth limit of the near-singular 4-way subdivision. */
+ *   max_subdiv   depth limit of the near-singular 4-way subdivision.
+ *   p_min        0: every box uses order p.  Otherwise the order depends on
+ *                the level (Section 3.6, end): L_l = min(p, p_min + l_max - l),
+ *                l_max the deepest level, so the smallest boxes use p_min and
+ *                the order grows by one per level towards the root.  Moments
+ *                and locals of a box stop at its level's order; a shift or a
+ *                translation keeps the terms both sides hold (an M2L between
+ *                boxes of orders p_s, p_t keeps |alpha| <= p_s, |beta| <= p_t,
+ *                |alpha| + |beta| <= max(p_s, p_t)).  The tensor-core M2L
+ *                needs a single order; with p_min the SIMT form runs. */
 typedef struct {
     int p;
     int leaf_size;
@@ -88,6 +97,7 @@ typedef struct {
     int n_duffy;
     double tau_near;
     int max_subdiv;
+    int p_min;
 } bem_fmm_params;
 
 typedef struct {

@@ -43,7 +43,7 @@ STAGE_NAMES = ["p2q", "p2m", "m2m", "m2l", "l2l", "near_l2p", "combine"]
 class bem_fmm_params(C.Structure):
     _fields_ = [("p", C.c_int), ("leaf_size", C.c_int), ("eta", C.c_double), ("max_level", C.c_int),
                 ("leaf_descend", C.c_int), ("precision", C.c_int), ("n_duffy", C.c_int),
-                ("tau_near", C.c_double), ("max_subdiv", C.c_int)]
+                ("tau_near", C.c_double), ("max_subdiv", C.c_int), ("p_min", C.c_int)]
 
 
 class bem_solve_params(C.Structure):

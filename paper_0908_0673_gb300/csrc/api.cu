@@ -97,6 +97,7 @@ static int validate_params(const bem_fmm_params &p) {
     if (p.n_duffy < 2 || p.n_duffy > 64) { set_error("n_duffy = %d outside [2, 64]", p.n_duffy); return BEM_EINVAL; }
     if (!(p.tau_near >= 0.0 && p.tau_near <= 16.0)) { set_error("tau_near = %g outside [0, 16]", p.tau_near); return BEM_EINVAL; }
     if (p.max_subdiv < 0 || p.max_subdiv > 10) { set_error("max_subdiv = %d outside [0, 10]", p.max_subdiv); return BEM_EINVAL; }
+    if (p.p_min < 0 || p.p_min > p.p) { set_error("p_min = %d outside [0, p = %d]", p.p_min, p.p); return BEM_EINVAL; }
     return BEM_OK;
 }
 
@@ -215,6 +216,7 @@ void bem_fmm_params_default(bem_fmm_params *p) {
     p->n_duffy = 12;
     p->tau_near = 2.0;
     p->max_subdiv = 6;
+    p->p_min = 0;
 }
 
 void bem_solve_params_default(bem_solve_params *p) {

@@ -204,6 +204,8 @@ struct bem_plan {
     int *sy_sig_u = nullptr;            // [pair] symmetry id (permutation * 8 + sign bits)
     std::vector<int> sy_hcls, sy_hsig, sy_hsrc, sy_hip;   // host: per pair class, symmetry, source; list offsets
     std::vector<int> sy_bt, sy_bb, sy_bu;                 // host: per run, first tile, target and pair (size runs + 1)
+    std::vector<int> sy_hlev, sy_hdl;                     // host: per canonical class, target level (when keyed) and dl
+    int *sy_ord = nullptr;              // [class][2] source and target order
     double *sy_D = nullptr;             // [class][np][C] derivative tables
     float *sy_fD = nullptr;
     unsigned short *sy_fwd = nullptr;   // [48][np] signed index maps (sign in bit 15)
@@ -225,6 +227,9 @@ struct bem_plan {
     bool diag_mode = false;             // alloc_fmm for the diagonal's order
     float *p2m_W = nullptr;             // [Q][np] stored double-layer P2M weights (float32 plans)
     float *xf = nullptr;                // float32 copy of a product's input (correction product)
+    std::vector<int> lev_p;             // expansion order of each tree level
+    int *d_lev_p = nullptr;
+    bool lev_var = false;               // the order varies with the level (p_min > 0 and more than one order)
     cudaStream_t setup_stream[2] = {nullptr, nullptr};
     int2 *near_items[2] = {nullptr, nullptr};   // float32 near-field work items, 64- and 32-target passes
     int near_nitems[2] = {0, 0};

@@ -31,6 +31,7 @@ struct FieldArgs {
     const double *cx, *cy, *cz, *r;
     const int *level, *child0, *nchild, *eb, *ee;
     const int *tm, *tn, *tk, *idx3;
+    const int *lev_p;                   // order of each level (nullptr: p everywhere)
     const double *fact;
     const void *M;                      // float or double moments [nbox][np][C]
     int mfloat;
@@ -276,7 +277,8 @@ __global__ void __launch_bounds__(FW * 32) k_field(int64_t npts, const double *_
             // I_g = (scaled moment) h^|g|
             warp_derivs(a, rr, Gh, up, cur);
             const double h = scalbn(a.side, -a.level[b]);
-            for (int g = lane; g < np; g += 32) {
+            const int pb = a.lev_p ? a.lev_p[a.level[b]] : a.p, npb = (pb + 1) * (pb + 2) * (pb + 3) / 6;
+            for (int g = lane; g < npb; g += 32) {
                 const int m = a.tm[g], n = a.tn[g], k = a.tk[g], dg = m + n + k;
                 const double cf = ((dg & 1) ? -1.0 : 1.0) * pow(h, (double)dg) / (a.fact[m] * a.fact[n] * a.fact[k]);
                 double mr, mi = 0.0;
@@ -335,6 +337,7 @@ static int launch_field(bem_plan *P, int64_t npts, const double *pts, double *u,
     a.cx = t.cx; a.cy = t.cy; a.cz = t.cz; a.r = t.r;
     a.level = t.level; a.child0 = t.child0; a.nchild = t.nchild; a.eb = t.eb; a.ee = t.ee;
     a.tm = P->d_m; a.tn = P->d_n; a.tk = P->d_k; a.idx3 = P->d_idx3;
+    a.lev_p = P->lev_var ? P->d_lev_p : nullptr;
     a.fact = P->d_fact;
     a.mfloat = P->prm.precision == BEM_MIXED;
     a.M = a.mfloat ? (const void *)P->fM : (const void *)P->M;

@@ -32,8 +32,13 @@ __constant__ double c_Lq[2][NQ][6];   // shape values at the 7 rule points (tri3
 struct Tabs {
     const int *m, *n, *k, *idx3;
     const double *binom, *fact;
-    int p, np;
+    int p, np;                          // largest order, and the coefficient count (array stride)
+    const int *lev_p;                   // order of each tree level (nullptr: p everywhere)
 };
+
+// number of multi-indices of degree <= q (the coefficients of order q)
+__host__ __device__ __forceinline__ int np_of(int q) { return (q + 1) * (q + 2) * (q + 3) / 6; }
+__device__ __forceinline__ int order_of(const Tabs &tb, int level) { return tb.lev_p ? tb.lev_p[level] : tb.p; }
 
 struct TreeView {
     const int *level, *ix, *iy, *iz, *parent, *child0, *nchild, *nb, *ne, *eb, *ee, *leaves;
@@ -90,7 +95,8 @@ __global__ void __launch_bounds__(P2M_T) k_p2m(int nleaf, Tabs tb, TreeView tv, 
     const int li = blockIdx.x;
     if (li >= nleaf) return;
     const int b = tv.leaves[li];
-    const int p = tb.p, np = tb.np, tid = threadIdx.x;
+    const int np = tb.np, tid = threadIdx.x;
+    const int p = order_of(tb, tv.level[b]), npl = np_of(p);   // this leaf's order; np is the stride
     __shared__ R pw[3][P2M_B][PMAX + 1];             // [axis][point][power]: lanes with distinct powers hit distinct banks
     __shared__ R sf[P2M_B][C];
     __shared__ R sn[3][P2M_B];
@@ -102,9 +108,9 @@ __global__ void __launch_bounds__(P2M_T) k_p2m(int nleaf, Tabs tb, TreeView tv, 
 #pragma unroll
     for (int s = 0; s < P2M_SLOTS; s++) {
         int a = tid + s * P2M_T;
-        am[s] = a < np ? tb.m[a] : 0;
-        an[s] = a < np ? tb.n[a] : 0;
-        ak[s] = a < np ? tb.k[a] : 0;
+        am[s] = a < npl ? tb.m[a] : 0;
+        an[s] = a < npl ? tb.n[a] : 0;
+        ak[s] = a < npl ? tb.k[a] : 0;
 #pragma unroll
         for (int c = 0; c < C; c++) acc[s][c] = (R)0;
     }
@@ -153,7 +159,7 @@ __global__ void __launch_bounds__(P2M_T) k_p2m(int nleaf, Tabs tb, TreeView tv, 
         for (int pt = 0; pt < nb; pt++) {
 #pragma unroll
             for (int s = 0; s < P2M_SLOTS; s++) {
-                if (tid + s * P2M_T >= np) break;
+                if (tid + s * P2M_T >= npl) break;
                 const int m = am[s], n = an[s], k = ak[s];
                 R val;
                 if (!DL) {
@@ -178,7 +184,7 @@ __global__ void __launch_bounds__(P2M_T) k_p2m(int nleaf, Tabs tb, TreeView tv, 
 #pragma unroll
     for (int s = 0; s < P2M_SLOTS; s++) {
         int a = tid + s * P2M_T;
-        if (a < np)
+        if (a < npl)
 #pragma unroll
             for (int c = 0; c < C; c++) M[((size_t)b * np + a) * C + c] = acc[s][c];
     }
@@ -289,7 +295,7 @@ __global__ void __launch_bounds__(NF_T) k_near(int nleaf, Tabs tb, TreeView tv, 
     if (li >= nleaf) return;
     const int b = tv.leaves[li];
     const int tid = threadIdx.x, tt = tid % NF_TGT, sl = tid / NF_TGT;
-    const int p = tb.p, np = tb.np;
+    const int np = tb.np, p = order_of(tb, tv.level[b]), npl = np_of(p);   // the leaf's order; np the stride
     __shared__ R sx[NF_TILE], sy[NF_TILE], sz[NF_TILE], snx[NF_TILE], sny[NF_TILE], snz[NF_TILE];
     __shared__ R sf[NF_TILE][C];
     __shared__ double red[NF_T][C];
@@ -356,7 +362,7 @@ __global__ void __launch_bounds__(NF_T) k_near(int nleaf, Tabs tb, TreeView tv, 
                 py[e] = py[e - 1] * dy;
                 pz[e] = pz[e - 1] * dz;
             }
-            for (int a = sl; a < np; a += NF_SL) {
+            for (int a = sl; a < npl; a += NF_SL) {
                 const R mono = px[tb.m[a]] * py[tb.n[a]] * pz[tb.k[a]];
 #pragma unroll
                 for (int c = 0; c < C; c++) loc[c] += (double)(mono * L[((size_t)b * np + a) * C + c]);
@@ -533,7 +539,7 @@ __global__ void __launch_bounds__(NF2_T, 4) k_near_f32(int nitem, const int2 *__
     __shared__ float toff[SLOTS][3];                  // target - target leaf centre
     const double cbx = tv.cx[b], cby = tv.cy[b], cbz = tv.cz[b];
     const float kw = (float)kwave;
-    const int p = tb.p, np = tb.np;
+    const int np = tb.np, p = order_of(tb, tv.level[b]), npl = np_of(p);   // the leaf's order; np the stride
     const int t0 = item.y, nt = min(SLOTS, tv.ne[b] - t0);
     const int G = (nt + U - 1) / U, S = NF2_T / G, tg = tid % G, sl = tid / G;
     const bool worker = sl < S;
@@ -735,7 +741,7 @@ __global__ void __launch_bounds__(NF2_T, 4) k_near_f32(int nitem, const int2 *__
         KahanF loc[C];
         if (slot < nt) {
             const float *sp = spow + (size_t)slot * 3 * (PMAX + 1);
-            for (int a = part_id; a < np; a += LP) {
+            for (int a = part_id; a < npl; a += LP) {
                 const float mono = sp[tb.m[a]] * sp[PMAX + 1 + tb.n[a]] * sp[2 * (PMAX + 1) + tb.k[a]];
 #pragma unroll
                 for (int c = 0; c < C; c++) loc[c].add(mono * L[((size_t)b * np + a) * C + c]);
@@ -884,7 +890,8 @@ void MIndex::init(int p_) {
 }
 
 static Tabs tabs_of(const bem_plan *P) {
-    return Tabs{P->d_m, P->d_n, P->d_k, P->d_idx3, P->d_binom, P->d_fact, P->mi.p, P->mi.np};
+    return Tabs{P->d_m, P->d_n, P->d_k, P->d_idx3, P->d_binom, P->d_fact, P->mi.p, P->mi.np,
+                P->lev_var ? P->d_lev_p : nullptr};
 }
 
 static TreeView view_of(const bem_plan *P) {
@@ -940,6 +947,19 @@ int alloc_fmm(bem_plan *P, cudaStream_t s) {
     Arena &A = P->arena;
     MIndex &mi = P->mi;
     mi.init(P->prm.p);
+    // order of each level: L_l = min(p, p_min + l_max - l) (Section 3.6), or p
+    {
+        const int nlev = std::max(1, P->t.nlev), lmax = nlev - 1;
+        P->lev_p.assign(nlev, P->prm.p);
+        P->lev_var = false;
+        if (P->prm.p_min > 0)
+            for (int l = 0; l < nlev; l++) {
+                P->lev_p[l] = std::min(P->prm.p, P->prm.p_min + lmax - l);
+                if (P->lev_p[l] != P->prm.p) P->lev_var = true;
+            }
+        BEM_TRY(A.alloc(&P->d_lev_p, nlev));
+        BEM_CUDA(cudaMemcpy(P->d_lev_p, P->lev_p.data(), sizeof(int) * nlev, cudaMemcpyHostToDevice));
+    }
     const int np = mi.np, nbox = P->t.nbox, C = P->green == BEM_HELMHOLTZ ? 2 : 1;
     BEM_TRY(A.alloc(&P->d_m, np));
     BEM_TRY(A.alloc(&P->d_n, np));
@@ -973,7 +993,7 @@ int alloc_fmm(bem_plan *P, cudaStream_t s) {
     BEM_TRY(A.alloc(&P->xptr, 2));
     BEM_TRY(A.alloc(&P->yptr, 2));
     if (mx) BEM_TRY(A.alloc(&P->xf, (size_t)std::max(P->N, P->nchi) * C));
-    if (mx && !P->diag_mode) {
+    if (mx && !P->diag_mode && !P->lev_var) {
         // stored P2M weights of the double layer (op A, every product of a solve)
         BEM_TRY(A.alloc(&P->p2m_W, (size_t)P->Q * np));
         const Tree &t = P->t;
@@ -1124,17 +1144,19 @@ int enqueue_matvec_raw(bem_plan *P, int op, int green, double kwave, int with_di
 // the buffers are sized for the plan's own order and precision.
 // The order, precision and Green's function of the diagonal's product.
 struct DiagSwap {
-    int p, precision, green;
+    int p, precision, green, p_min;
 };
+// the diagonal's product runs at one order for every level
 static DiagSwap diag_fields(const bem_plan *P) {
     const bool mixed = P->prm.precision == BEM_MIXED;
-    return DiagSwap{mixed ? std::min(PMAX, P->prm.p + 4) : PMAX, mixed ? BEM_MIXED : BEM_F64, BEM_LAPLACE};
+    return DiagSwap{mixed ? std::min(PMAX, P->prm.p + 4) : PMAX, mixed ? BEM_MIXED : BEM_F64, BEM_LAPLACE, 0};
 }
 static DiagSwap swap_fields(bem_plan *P, const DiagSwap &d) {
-    const DiagSwap old{P->prm.p, P->prm.precision, P->green};
+    const DiagSwap old{P->prm.p, P->prm.precision, P->green, P->prm.p_min};
     P->prm.p = d.p;
     P->prm.precision = d.precision;
     P->green = d.green;
+    P->prm.p_min = d.p_min;
     return old;
 }
 
@@ -1182,10 +1204,12 @@ void free_fmm(bem_plan *P) {
     Arena &A = P->arena;
     for (void *q : {(void *)P->d_m, (void *)P->d_n, (void *)P->d_k, (void *)P->d_idx3, (void *)P->d_fact,
                     (void *)P->d_binom, (void *)P->f, (void *)P->M, (void *)P->L, (void *)P->ff, (void *)P->fM,
-                    (void *)P->fL, (void *)P->ytmp, (void *)P->xptr, (void *)P->yptr, (void *)P->p2m_W, (void *)P->xf})
+                    (void *)P->fL, (void *)P->ytmp, (void *)P->xptr, (void *)P->yptr, (void *)P->p2m_W, (void *)P->xf, (void *)P->d_lev_p})
         A.release(q);
     P->p2m_W = nullptr;
     P->xf = nullptr;
+    P->d_lev_p = nullptr;
+    P->lev_var = false;
     P->d_m = P->d_n = P->d_k = P->d_idx3 = nullptr;
     P->d_fact = P->d_binom = nullptr;
     P->f = P->M = P->L = P->ytmp = nullptr;

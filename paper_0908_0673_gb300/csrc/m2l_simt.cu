@@ -41,6 +41,7 @@ struct SyArgs {
     int p, np, ldp, ntile, u0;          // rows of this run's pairs: row u - u0
     const int *tile_cls, *tile_start, *tile_cnt;
     const int *src, *sig, *pair, *dl;
+    const int *ord;                     // [class][2] source and target order
     const unsigned short *fwd;          // [48][np] signed index maps (sign in bit 15)
     const int *mexp;                    // [np] exponents m | n << 8 | k << 16 | degree << 24
     const int *idx3;                    // [(p+1)^3] multi-index -> index
@@ -145,11 +146,14 @@ __global__ void __launch_bounds__(SY_T) k_m2l_sy(const __grid_constant__ SyArgs 
             prev_dl = dl;
         }
         __syncthreads();
-        for (int b0 = 0; b0 < np; b0 += BB) {
+        // orders of the class: moments |a| <= ps, locals |b| <= pt, |a| + |b| <= max(ps, pt)
+        const int ps = a.ord[2 * cls], pt = a.ord[2 * cls + 1], pm = max(ps, pt);
+        const int nps = n_upto(ps), npt = n_upto(pt);
+        for (int b0 = 0; b0 < npt; b0 += BB) {
             // columns needed by the chunk (its first row has the lowest degree)
             // and by this thread's rows; products beyond them are zero
-            const int kext = min(np, n_upto(p - (sExp[b0] >> 24)));
-            const int kthr = b0 + tb * RB < np ? min(np, n_upto(p - (sExp[b0 + tb * RB] >> 24))) : 0;
+            const int kext = min(nps, n_upto(pm - (sExp[b0] >> 24)));
+            const int kthr = b0 + tb * RB < npt ? min(nps, n_upto(pm - (sExp[b0 + tb * RB] >> 24))) : 0;
             R acc[RB][8][C];
 #pragma unroll
             for (int r = 0; r < RB; r++)
@@ -165,9 +169,9 @@ __global__ void __launch_bounds__(SY_T) k_m2l_sy(const __grid_constant__ SyArgs 
                     R v[C];
 #pragma unroll
                     for (int c = 0; c < C; c++) v[c] = (R)0;
-                    if (ai < kext && b < np) {
+                    if (ai < kext && b < npt) {
                         const int ea = sExp[ai], eb = sExp[b];
-                        if ((ea >> 24) + (eb >> 24) <= p) {
+                        if ((ea >> 24) + (eb >> 24) <= pm) {
                             const int m = (ea & 0xff) + (eb & 0xff), n = ((ea >> 8) & 0xff) + ((eb >> 8) & 0xff),
                                       kk = ((ea >> 16) & 0xff) + ((eb >> 16) & 0xff);
                             const int g = sIdx[(m * P1 + n) * P1 + kk];
@@ -231,7 +235,7 @@ __global__ void __launch_bounds__(SY_T) k_m2l_sy(const __grid_constant__ SyArgs 
                 R *row = Lp + ((size_t)(u - a.u0) * a.ldp + b0 + tb * RB) * C;
 #pragma unroll
                 for (int r = 0; r < RB; r++)
-                    if (b0 + tb * RB + r < np)
+                    if (b0 + tb * RB + r < npt)
 #pragma unroll
                         for (int c = 0; c < C; c++) row[r * C + c] = acc[r][q][c];
             }
@@ -244,7 +248,8 @@ __global__ void __launch_bounds__(SY_T) k_m2l_sy(const __grid_constant__ SyArgs 
 constexpr int SG_LIST = 256;
 template <class R, int C>
 __global__ void __launch_bounds__(256) k_m2l_gather_sy(int t0, int nbox, const int *__restrict__ level, double side,
-                                                       const int *__restrict__ inter_ptr, int u0r, int np, int ldp,
+                                                       const int *__restrict__ lev_p, const int *__restrict__ inter_ptr,
+                                                       int u0r, int np, int ldp,
                                                        const int *__restrict__ sig_u, const int *__restrict__ inv,
                                                        const R *__restrict__ Lp, R *__restrict__ L,
                                                        const int *__restrict__ skip) {
@@ -254,7 +259,8 @@ __global__ void __launch_bounds__(256) k_m2l_gather_sy(int t0, int nbox, const i
     if (t >= nbox) return;
     const R sc = (R)(1.0 / scalbn(side, -level[t]));
     const int u0 = inter_ptr[t], u1 = inter_ptr[t + 1];
-    for (int b0 = 0; b0 < np; b0 += blockDim.x) {
+    const int npt = lev_p ? n_upto(lev_p[level[t]]) : np;   // the target's own coefficients
+    for (int b0 = 0; b0 < npt; b0 += blockDim.x) {
         const int b = b0 + threadIdx.x;
         R sum[C];
 #pragma unroll
@@ -264,7 +270,7 @@ __global__ void __launch_bounds__(256) k_m2l_gather_sy(int t0, int nbox, const i
             __syncthreads();
             for (int i = threadIdx.x; i < n; i += blockDim.x) sOff[i] = sig_u[base + i] * np;
             __syncthreads();
-            if (b < np) {
+            if (b < npt) {
                 int i = 0;
                 for (; i + 4 <= n; i += 4) {
                     int f[4];
@@ -291,7 +297,7 @@ __global__ void __launch_bounds__(256) k_m2l_gather_sy(int t0, int nbox, const i
                 }
             }
         }
-        if (b < np)
+        if (b < npt)
 #pragma unroll
             for (int c = 0; c < C; c++) L[((size_t)t * np + b) * C + c] = sum[c] * sc;
     }
@@ -315,6 +321,7 @@ int launch_m2l_sy(bem_plan *P, const R *M, R *L, cudaStream_t s) {
     a.sig = P->sy_sig;
     a.pair = P->sy_pair;
     a.dl = P->sy_dl;
+    a.ord = P->sy_ord;
     a.fwd = P->sy_fwd;
     a.mexp = P->sy_mexp;
     a.idx3 = P->d_idx3;
@@ -336,7 +343,8 @@ int launch_m2l_sy(bem_plan *P, const R *M, R *L, cudaStream_t s) {
         if (nt > 0)
             (k_m2l_sy<R, C><<<std::min(nt, 2 * std::max(1, P->sm_count)), SY_T, sm, s>>>(a), ::bem::count_launch());
         if (ntg > 0)
-            (k_m2l_gather_sy<R, C><<<ntg, 256, 0, s>>>(tg0, t.nbox, t.level, t.side, t.inter_ptr, a.u0, a.np, a.ldp,
+            (k_m2l_gather_sy<R, C><<<ntg, 256, 0, s>>>(tg0, t.nbox, t.level, t.side, P->lev_var ? P->d_lev_p : nullptr,
+                                                       t.inter_ptr, a.u0, a.np, a.ldp,
                                                        P->sy_sig_u, P->sy_inv, (const R *)P->sy_Lp, L, P->skip),
              ::bem::count_launch());
     }

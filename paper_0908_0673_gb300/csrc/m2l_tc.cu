@@ -402,6 +402,7 @@ int build_m2l_sym(bem_plan *P, const std::vector<int> &pair_cls, const std::vect
     std::sort(fidx.begin(), fidx.end(), [&](int x, int y) { return fkey[x] < fkey[y] || (!(fkey[y] < fkey[x]) && x < y); });
     std::vector<int> fcan(nfull), dlc;
     std::vector<double> rho, khc;
+    P->sy_hlev.clear();
     const bool helm = P->green == BEM_HELMHOLTZ;
     int nc = 0;
     for (int i = 0; i < nfull; i++) {
@@ -414,6 +415,7 @@ int build_m2l_sym(bem_plan *P, const std::vector<int> &pair_cls, const std::vect
             rho.push_back(k.v[4] * sc);
             khc.push_back(helm ? P->k * std::ldexp(P->t.side, -(int)k.v[1]) : 0.0);
             dlc.push_back(dl);
+            P->sy_hlev.push_back((int)k.v[1]);
             nc++;
         }
         fcan[fidx[i]] = nc - 1;
@@ -439,6 +441,7 @@ int build_m2l_sym(bem_plan *P, const std::vector<int> &pair_cls, const std::vect
     BEM_TRY(up(&P->sy_rho, rho));
     BEM_TRY(up(&P->sy_kh, khc));
     BEM_TRY(up(&P->sy_dl, dlc));
+    P->sy_hdl = dlc;
     BEM_TRY(up(&P->sy_sig_u, P->sy_hsig));
     return BEM_OK;
 }
@@ -633,7 +636,20 @@ int build_sym_tables(bem_plan *P, cudaStream_t s) {
     int ldp = 0, nkc = 0;
     std::vector<uint4> sched;
     std::vector<int> sptr;
-    const bool tc = C == 1 && mx && ncls > 0 && tc_plan(mi, deg, g, ldp, nkc, sched, sptr);
+    const bool tc = C == 1 && mx && ncls > 0 && !P->lev_var && tc_plan(mi, deg, g, ldp, nkc, sched, sptr);
+    // source and target order of every canonical class (one order unless it varies with the level;
+    // the class key then holds the target level)
+    {
+        std::vector<int> ord(2 * (size_t)std::max(1, ncls), p);
+        if (P->lev_var)
+            for (int c = 0; c < ncls; c++) {
+                const int lt = P->sy_hlev[c], ls = lt - P->sy_hdl[c];
+                auto at = [&](int l) { return l >= 0 && l < (int)P->lev_p.size() ? P->lev_p[l] : p; };
+                ord[2 * c] = at(ls);
+                ord[2 * c + 1] = at(lt);
+            }
+        BEM_TRY(up(&P->sy_ord, ord));
+    }
     if (tc) {
         // class-matrix gather table in shared-memory layout order
         std::vector<int> tidx(g.tsize, -1);
@@ -677,10 +693,11 @@ void free_sym_tables(bem_plan *P) {
     Arena &A = P->arena;
     for (void *q : {(void *)P->sy_tidx, (void *)P->sy_tfac, (void *)P->sy_fwd, (void *)P->sy_inv, (void *)P->sy_D,
                     (void *)P->sy_fD, (void *)P->sy_Lp, (void *)P->sy_sched, (void *)P->sy_sched_ptr,
-                    (void *)P->sy_mexp, (void *)P->sy_invf, (void *)P->sy_tile_cls, (void *)P->sy_tile_start,
+                    (void *)P->sy_mexp, (void *)P->sy_invf, (void *)P->sy_ord, (void *)P->sy_tile_cls, (void *)P->sy_tile_start,
                     (void *)P->sy_tile_cnt, (void *)P->sy_src, (void *)P->sy_sig, (void *)P->sy_pair})
         A.release(q);
     P->sy_tile_cls = P->sy_tile_start = P->sy_tile_cnt = P->sy_src = P->sy_sig = P->sy_pair = nullptr;
+    P->sy_ord = nullptr;
     P->sy_ntile = 0;
     P->sy_tidx = P->sy_inv = P->sy_mexp = nullptr;
     P->sy_fwd = nullptr;

@@ -51,11 +51,16 @@ __device__ __forceinline__ void cmac(R *acc, R cf, const R *v) {
 // ---------------------------------------------------------------------------
 constexpr int MM_T = 512;
 
+// idx3 is laid out for order pt1 - 1 (the plan's largest); the shared copy
+// for order p (<= pt1 - 1) uses stride p + 1
 template <class R>
-__device__ __forceinline__ void shift_tables(int p, const int *__restrict__ idx3, const double *__restrict__ binom,
+__device__ __forceinline__ void shift_tables(int p, int pt1, const int *__restrict__ idx3, const double *__restrict__ binom,
                                              bool m2m, short *sIdx, R *sG) {
     const int P1 = p + 1;
-    for (int i = threadIdx.x; i < P1 * P1 * P1; i += blockDim.x) sIdx[i] = (short)idx3[i];
+    for (int i = threadIdx.x; i < P1 * P1 * P1; i += blockDim.x) {
+        const int m = i / (P1 * P1), n = (i / P1) % P1, k = i % P1;
+        sIdx[i] = (short)idx3[(m * pt1 + n) * pt1 + k];
+    }
     for (int i = threadIdx.x; i < P1 * P1; i += blockDim.x) {
         const int a = i / P1, g = i - a * P1;
         // M2M: binom(a, g) 2^-g (g <= a);  L2L: binom(a + g, a) 4^-g (a + g <= p)
@@ -97,6 +102,7 @@ template <class R, int C>
 __global__ void __launch_bounds__(MM_T) k_m2m_sep(int off, int cnt, const int *__restrict__ child0,
                                                   const int *__restrict__ nchild, const int *__restrict__ ix,
                                                   const int *__restrict__ iy, const int *__restrict__ iz, int p, int np,
+                                                  int nps, int pt1, int npc,
                                                   int grp, const int *__restrict__ tm, const int *__restrict__ tn,
                                                   const int *__restrict__ tk, const int *__restrict__ idx3,
                                                   const double *__restrict__ binom, R *__restrict__ M,
@@ -114,11 +120,15 @@ __global__ void __launch_bounds__(MM_T) k_m2m_sep(int off, int cnt, const int *_
     const int b = off + blockIdx.x, nch = nchild[b];
     if (nch == 0) return;
     const int c0 = child0[b], tid = threadIdx.x;
-    shift_tables<R>(p, idx3, binom, true, sIdx, sG);
+    shift_tables<R>(p, pt1, idx3, binom, true, sIdx, sG);
     for (int g0 = 0; g0 < nch; g0 += grp) {
         const int ng = min(grp, nch - g0);
         __syncthreads();
-        for (int t = tid; t < ng * np * C; t += MM_T) sA[t] = M[(size_t)(c0 + g0) * np * C + t];   // consecutive
+        // children (consecutive boxes, row stride nps) hold npc coefficients; the rest enter as zero
+        for (int t = tid; t < ng * np * C; t += MM_T) {
+            const int j = t / (np * C), r = t - j * np * C, a = r / C;
+            sA[t] = a < npc ? M[((size_t)(c0 + g0 + j) * nps) * C + r] : (R)0;
+        }
         // a child on the low side of an axis has offset -1/4 of the parent edge
         if (tid < ng) {
             const int c = c0 + g0 + tid;
@@ -141,14 +151,15 @@ __global__ void __launch_bounds__(MM_T) k_m2m_sep(int off, int cnt, const int *_
     for (int a = tid; a < np; a += MM_T) {
         const R sc = (R)ldexp(1.0, -(tm[a] + tn[a] + tk[a]));
 #pragma unroll
-        for (int c = 0; c < C; c++) M[((size_t)b * np + a) * C + c] = sS[(size_t)a * C + c] * sc;
+        for (int c = 0; c < C; c++) M[((size_t)b * nps + a) * C + c] = sS[(size_t)a * C + c] * sc;
     }
 }
 
 template <class R, int C>
 __global__ void __launch_bounds__(MM_T) k_l2l_sep(int off, int cnt, const int *__restrict__ parent,
                                                   const int *__restrict__ ix, const int *__restrict__ iy,
-                                                  const int *__restrict__ iz, int p, int np, const int *__restrict__ tm,
+                                                  const int *__restrict__ iz, int p, int np, int nps, int pt1, int npo,
+                                                  const int *__restrict__ tm,
                                                   const int *__restrict__ tn, const int *__restrict__ tk,
                                                   const int *__restrict__ idx3, const double *__restrict__ binom,
                                                   R *__restrict__ L, const int *__restrict__ skip) {
@@ -162,8 +173,8 @@ __global__ void __launch_bounds__(MM_T) k_l2l_sep(int off, int cnt, const int *_
     __shared__ int smask[1];
     if (blockIdx.x >= cnt) return;
     const int b = off + blockIdx.x, pa = parent[b], tid = threadIdx.x;
-    for (int t = tid; t < np * C; t += MM_T) sA[t] = L[(size_t)pa * np * C + t];
-    shift_tables<R>(p, idx3, binom, false, sIdx, sG);
+    for (int t = tid; t < np * C; t += MM_T) sA[t] = L[(size_t)pa * nps * C + t];   // the parent's np coefficients
+    shift_tables<R>(p, pt1, idx3, binom, false, sIdx, sG);
     if (tid == 0) smask[0] = ((ix[b] & 1) ? 0 : 1) | ((iy[b] & 1) ? 0 : 2) | ((iz[b] & 1) ? 0 : 4);
     __syncthreads();
     shift_pass<R, C, false>(2, 1, p, np, tm, tn, tk, sIdx, sG, smask, sA, sB);
@@ -172,10 +183,10 @@ __global__ void __launch_bounds__(MM_T) k_l2l_sep(int off, int cnt, const int *_
     __syncthreads();
     shift_pass<R, C, false>(0, 1, p, np, tm, tn, tk, sIdx, sG, smask, sA, sB);
     __syncthreads();
-    for (int a = tid; a < np; a += MM_T) {
+    for (int a = tid; a < npo; a += MM_T) {         // the child keeps its own order's npo coefficients
         const R sc = (R)ldexp(1.0, -(tm[a] + tn[a] + tk[a]));
 #pragma unroll
-        for (int c = 0; c < C; c++) L[((size_t)b * np + a) * C + c] += sB[(size_t)a * C + c] * sc;
+        for (int c = 0; c < C; c++) L[((size_t)b * nps + a) * C + c] += sB[(size_t)a * C + c] * sc;
     }
 }
 
@@ -292,7 +303,7 @@ int build_m2l_classes(bem_plan *P) {
     std::vector<long long> kvec;        // integer offset vector of every class
     auto new_class = [&](int b, int dl, long long kx, long long ky, long long kz) {
         const int c = (int)dls.size();
-        levs.push_back(helm ? lev[b] : 0);
+        levs.push_back(helm || P->prm.p_min > 0 ? lev[b] : 0);
         dls.push_back(dl);
         kvec.push_back(kx);
         kvec.push_back(ky);
@@ -307,7 +318,9 @@ int build_m2l_classes(bem_plan *P) {
                 return (long long)(2 * it_ + 1) * (1ll << e) - (long long)(2 * is_ + 1) * (1ll << (dl + e));
             };
             const long long kx = K(ix[b], ix[s]), ky = K(iy[b], iy[s]), kz = K(iz[b], iz[s]);
-            const int lv = helm ? lev[b] : 0;
+            // the target level enters the key when the derivatives (Helmholtz: k h_t) or
+            // the orders (level-dependent order) depend on it
+            const int lv = helm || P->prm.p_min > 0 ? lev[b] : 0;
             int c;
             if (std::llabs(kx) <= KMAX && std::llabs(ky) <= KMAX && std::llabs(kz) <= KMAX && dl > -64 && dl < 64) {
                 const unsigned long long key =
@@ -353,20 +366,25 @@ void free_translation_tables(bem_plan *P) { free_sym_tables(P); }
 // host: launchers
 // ---------------------------------------------------------------------------
 // upward pass: moments of every parent from its children, level by level
+static int np_host(int q) { return (q + 1) * (q + 2) * (q + 3) / 6; }
+static int level_order(const bem_plan *P, int l) {
+    return l < (int)P->lev_p.size() ? P->lev_p[l] : P->mi.p;
+}
+
 template <class R, int C>
 int launch_m2m(bem_plan *P, R *M, cudaStream_t s) {
     const Tree &t = P->t;
-    const int np = P->mi.np;
+    const int nps = P->mi.np, pt1 = P->mi.p + 1;
     const int *sk = P->skip;
-    const int P1 = P->mi.p + 1;
-    const size_t tab_sm = sizeof(R) * P1 * P1 + sizeof(short) * P1 * P1 * P1 + 16;
-    int grp = 8;                                 // children shifted together (shared memory permitting)
-    while (grp > 1 && sizeof(R) * (2 * grp + 1) * np * C + tab_sm > 220 * 1024) grp /= 2;
-    const size_t m2m_sm = sizeof(R) * (2 * grp + 1) * np * C + tab_sm;
     for (int l = t.nlev - 2; l >= 0; l--) {
         const int off = t.lev_off[l], cnt = t.lev_off[l + 1] - off;
-        (k_m2m_sep<R, C><<<cnt, MM_T, m2m_sm, s>>>(off, cnt, t.child0, t.nchild, t.ix, t.iy, t.iz, P->mi.p, np, grp,
-                                                   P->d_m, P->d_n, P->d_k, P->d_idx3, P->d_binom, M, sk),
+        const int p = level_order(P, l), np = np_host(p), npc = np_host(level_order(P, l + 1)), P1 = p + 1;
+        const size_t tab_sm = sizeof(R) * P1 * P1 + sizeof(short) * P1 * P1 * P1 + 16;
+        int grp = 8;                             // children shifted together (shared memory permitting)
+        while (grp > 1 && sizeof(R) * (2 * grp + 1) * np * C + tab_sm > 220 * 1024) grp /= 2;
+        const size_t m2m_sm = sizeof(R) * (2 * grp + 1) * np * C + tab_sm;
+        (k_m2m_sep<R, C><<<cnt, MM_T, m2m_sm, s>>>(off, cnt, t.child0, t.nchild, t.ix, t.iy, t.iz, p, np, nps, pt1, npc,
+                                                   grp, P->d_m, P->d_n, P->d_k, P->d_idx3, P->d_binom, M, sk),
          ::bem::count_launch());
     }
     BEM_LAUNCH_CHECK();
@@ -378,8 +396,6 @@ int launch_translations(bem_plan *P, R *M, R *L, cudaStream_t s, cudaEvent_t *ev
     const Tree &t = P->t;
     const int np = P->mi.np;
     const int *sk = P->skip;
-    const int P1 = P->mi.p + 1;
-    const size_t tab_sm = sizeof(R) * P1 * P1 + sizeof(short) * P1 * P1 * P1 + 16;
     BEM_TRY((launch_m2m<R, C>(P, M, s)));
     BEM_LAUNCH_CHECK();
     if (ev) BEM_CUDA(cudaEventRecord(ev[3], s));
@@ -391,10 +407,13 @@ int launch_translations(bem_plan *P, R *M, R *L, cudaStream_t s, cudaEvent_t *ev
     BEM_LAUNCH_CHECK();
     if (ev) BEM_CUDA(cudaEventRecord(ev[4], s));
     for (int l = 1; l < t.nlev; l++) {
+        // the shift runs at the parent's order; the child keeps its own order's terms
         const int off = t.lev_off[l], cnt = t.lev_off[l + 1] - off;
-        (k_l2l_sep<R, C><<<cnt, MM_T, sizeof(R) * 2 * np * C + tab_sm, s>>>(off, cnt, t.parent, t.ix, t.iy, t.iz,
-                                                                       P->mi.p, np, P->d_m, P->d_n, P->d_k, P->d_idx3,
-                                                                       P->d_binom, L, sk),
+        const int p = level_order(P, l - 1), pnp = np_host(p), npo = np_host(level_order(P, l)), P1 = p + 1;
+        const size_t tab_sm = sizeof(R) * P1 * P1 + sizeof(short) * P1 * P1 * P1 + 16;
+        (k_l2l_sep<R, C><<<cnt, MM_T, sizeof(R) * 2 * pnp * C + tab_sm, s>>>(off, cnt, t.parent, t.ix, t.iy, t.iz, p,
+                                                                           pnp, np, P->mi.p + 1, npo, P->d_m, P->d_n,
+                                                                           P->d_k, P->d_idx3, P->d_binom, L, sk),
          ::bem::count_launch());
     }
     BEM_LAUNCH_CHECK();

@@ -30,12 +30,14 @@ def test_library_exports_every_declared_symbol():
 
 def test_params_defaults():
     p = bem.bem_fmm_params_default()
-    assert (p.p, p.leaf_size, p.eta, p.leaf_descend, p.n_duffy, p.tau_near, p.max_subdiv) == (8, 64, 2.0, 1, 12, 2.0, 6)
+    assert (p.p, p.leaf_size, p.eta, p.leaf_descend, p.n_duffy, p.tau_near, p.max_subdiv, p.p_min) == \
+        (8, 64, 2.0, 1, 12, 2.0, 6, 0)
     s = bem.bem_solve_params_default()
     assert (s.restart, s.tol, s.max_iter, s.method) == (30, 1e-10, 1000, bem.BEM_GMRES)
     # the struct the binding declares has the C layout: method is the last field
     import ctypes as C
     assert C.sizeof(bem.bem_solve_params) == 24 and bem.bem_solve_params.method.offset == 20
+    assert C.sizeof(bem.bem_fmm_params) == 48 and bem.bem_fmm_params.p_min.offset == 44
 
 
 @pytest.mark.parametrize("mesh", [lambda: I.cube(5, I.TRI3), lambda: I.cube(4, I.TRI6),
