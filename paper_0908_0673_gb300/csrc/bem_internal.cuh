@@ -38,7 +38,7 @@ extern thread_local long long *tl_capture_count;
 #define BEM_LAUNCH_CHECK() BEM_CUDA(cudaGetLastError())
 
 constexpr int QBITS = 21;   // Morton bits per axis
-constexpr int PMAX = 16;    // largest supported expansion order
+constexpr int PMAX = 20;    // largest supported expansion order
 constexpr int NQ = 7;       // regular quadrature points per element
 
 // ---------------------------------------------------------------------------

@@ -12,6 +12,7 @@
 // per field point; the derivatives of G at the point's offset from a box come
 // from the same recursions as the translation tables, evaluated per box by the
 // warp; everything after the moments is float64.
+#include <algorithm>
 #include <cmath>
 
 #include "bem_internal.cuh"
@@ -254,7 +255,7 @@ __global__ void __launch_bounds__(FW * 32) k_field(int64_t npts, const double *_
     double *up = Gh + 2 * (PMAX + 2), *cur = up + 2 * np;
     __shared__ int stack[FW][FSTACK];
     __shared__ int sp[FW];
-    const int64_t i = (int64_t)blockIdx.x * FW + warp;
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;   // blockDim.x / 32 <= FW points per block
     if (i >= npts) return;                            // warp-uniform
     const double x[3] = {pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]};
     double acc[2] = {0.0, 0.0};
@@ -347,10 +348,13 @@ static int launch_field(bem_plan *P, int64_t npts, const double *pts, double *u,
     a.phi = phi;
     a.chi = chi;
     a.err = P->dev_err;
-    const size_t sm = sizeof(double) * FW * (2 * (PMAX + 2) + 4 * (size_t)a.np);
+    // derivative scratch per warp; fewer warps per block at high orders
+    const size_t per_warp = sizeof(double) * (2 * (PMAX + 2) + 4 * (size_t)a.np);
+    const int fw = (int)std::max<size_t>(1, std::min<size_t>(FW, (size_t)(200 * 1024) / per_warp));
+    const size_t sm = per_warp * fw;
     BEM_CUDA(cudaFuncSetAttribute(k_field<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    const int64_t nblk = (npts + FW - 1) / FW;
-    if (nblk > 0) (k_field<C><<<(unsigned)nblk, FW * 32, sm, s>>>(npts, pts, u, a), ::bem::count_launch());
+    const int64_t nblk = (npts + fw - 1) / fw;
+    if (nblk > 0) (k_field<C><<<(unsigned)nblk, fw * 32, sm, s>>>(npts, pts, u, a), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
     return BEM_OK;
 }

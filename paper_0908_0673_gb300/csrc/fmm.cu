@@ -84,11 +84,14 @@ __global__ void k_p2q(int Q, int npe, const int *__restrict__ el_idx, const doub
 // ---------------------------------------------------------------------------
 // P2M: one block per leaf, threads over multi-indices, sources in batches of 32
 // ---------------------------------------------------------------------------
-constexpr int P2M_T = 128, P2M_B = 32, P2M_SLOTS = (969 + P2M_T - 1) / P2M_T;
+constexpr int P2M_T = 128, P2M_B = 32;
+// index slots per thread (NS >= ceil(n_p / P2M_T)): instantiated for orders
+// up to 11 (3), 16 (8) and 20 (14)
+constexpr int p2m_slots(int np) { return np <= 3 * P2M_T ? 3 : np <= 8 * P2M_T ? 8 : 14; }
 
 // WEIGHTS: instead of the moments, write each point's row of P2M weights
 // W[o][a] (the value that multiplies f[o] in moment a) for the stored form.
-template <class R, int C, bool DL, bool WEIGHTS = false>
+template <class R, int C, bool DL, bool WEIGHTS, int NS>
 __global__ void __launch_bounds__(P2M_T) k_p2m(int nleaf, Tabs tb, TreeView tv, QuadView qv, const R *__restrict__ f,
                                                R *__restrict__ M, const int *__restrict__ skip, R *__restrict__ W = nullptr) {
     if (skip && *skip) return;
@@ -103,10 +106,10 @@ __global__ void __launch_bounds__(P2M_T) k_p2m(int nleaf, Tabs tb, TreeView tv, 
     const double h = scalbn(tv.side, -tv.level[b]);
     const R hinv = (R)(1.0 / h);
     const double c0 = tv.cx[b], c1 = tv.cy[b], c2 = tv.cz[b];
-    int am[P2M_SLOTS], an[P2M_SLOTS], ak[P2M_SLOTS];
-    R acc[P2M_SLOTS][C];
+    int am[NS], an[NS], ak[NS];
+    R acc[NS][C];
 #pragma unroll
-    for (int s = 0; s < P2M_SLOTS; s++) {
+    for (int s = 0; s < NS; s++) {
         int a = tid + s * P2M_T;
         am[s] = a < npl ? tb.m[a] : 0;
         an[s] = a < npl ? tb.n[a] : 0;
@@ -158,7 +161,7 @@ __global__ void __launch_bounds__(P2M_T) k_p2m(int nleaf, Tabs tb, TreeView tv, 
         __syncthreads();
         for (int pt = 0; pt < nb; pt++) {
 #pragma unroll
-            for (int s = 0; s < P2M_SLOTS; s++) {
+            for (int s = 0; s < NS; s++) {
                 if (tid + s * P2M_T >= npl) break;
                 const int m = am[s], n = an[s], k = ak[s];
                 R val;
@@ -182,7 +185,7 @@ __global__ void __launch_bounds__(P2M_T) k_p2m(int nleaf, Tabs tb, TreeView tv, 
     }
     if (WEIGHTS) return;
 #pragma unroll
-    for (int s = 0; s < P2M_SLOTS; s++) {
+    for (int s = 0; s < NS; s++) {
         int a = tid + s * P2M_T;
         if (a < npl)
 #pragma unroll
@@ -199,33 +202,33 @@ __global__ void __launch_bounds__(P2M_T) k_p2m(int nleaf, Tabs tb, TreeView tv, 
 // ---------------------------------------------------------------------------
 constexpr int P2S_T = 2 * P2M_T, P2S_U = 8;           // two halves of P2M_T threads; points per chunk
 
-template <int C>
+template <int C, int NS>
 __global__ void __launch_bounds__(P2S_T) k_p2m_stored(int nleaf, int np, TreeView tv, const float *__restrict__ W,
                                                       const float *__restrict__ f, float *__restrict__ M,
                                                       const int *__restrict__ skip) {
     if (skip && *skip) return;
     const int li = blockIdx.x;
     if (li >= nleaf) return;
-    __shared__ float part[P2M_SLOTS][C][P2M_T];
+    __shared__ float part[NS][C][P2M_T];
     const int b = tv.leaves[li], half = threadIdx.x / P2M_T, tid = threadIdx.x % P2M_T;
     const int q0 = tv.eb[b] * NQ, q1 = tv.ee[b] * NQ;
-    float acc[P2M_SLOTS][C];
+    float acc[NS][C];
 #pragma unroll
-    for (int s = 0; s < P2M_SLOTS; s++)
+    for (int s = 0; s < NS; s++)
 #pragma unroll
         for (int c = 0; c < C; c++) acc[s][c] = 0.f;
     // chunks of P2S_U points alternate between the halves; within a half the
     // points are summed in order, then half 1's sums are added to half 0's
     for (int o0 = q0 + half * P2S_U; o0 < q1; o0 += 2 * P2S_U) {
         const int n = min(P2S_U, q1 - o0);
-        float w[P2S_U][P2M_SLOTS], fv[P2S_U][C];
+        float w[P2S_U][NS], fv[P2S_U][C];
 #pragma unroll
         for (int u = 0; u < P2S_U; u++) {
             const bool on = u < n;
 #pragma unroll
             for (int c = 0; c < C; c++) fv[u][c] = on ? __ldg(f + (size_t)(o0 + u) * C + c) : 0.f;
 #pragma unroll
-            for (int s = 0; s < P2M_SLOTS; s++) {
+            for (int s = 0; s < NS; s++) {
                 const int a = tid + s * P2M_T;
                 w[u][s] = on && a < np ? __ldg(W + (size_t)(o0 + u) * np + a) : 0.f;
             }
@@ -233,24 +236,44 @@ __global__ void __launch_bounds__(P2S_T) k_p2m_stored(int nleaf, int np, TreeVie
 #pragma unroll
         for (int u = 0; u < P2S_U; u++)
 #pragma unroll
-            for (int s = 0; s < P2M_SLOTS; s++)
+            for (int s = 0; s < NS; s++)
 #pragma unroll
                 for (int c = 0; c < C; c++) acc[s][c] += w[u][s] * fv[u][c];
     }
     if (half == 1)
 #pragma unroll
-        for (int s = 0; s < P2M_SLOTS; s++)
+        for (int s = 0; s < NS; s++)
 #pragma unroll
             for (int c = 0; c < C; c++) part[s][c][tid] = acc[s][c];
     __syncthreads();
     if (half == 0)
 #pragma unroll
-        for (int s = 0; s < P2M_SLOTS; s++) {
+        for (int s = 0; s < NS; s++) {
             const int a = tid + s * P2M_T;
             if (a < np)
 #pragma unroll
                 for (int c = 0; c < C; c++) M[((size_t)b * np + a) * C + c] = acc[s][c] + part[s][c][tid];
         }
+}
+
+
+// P2M launches with the slot count of the plan's largest order
+template <class R, int C, bool DL, bool WEIGHTS = false>
+static void launch_p2m(int nleaf, const Tabs &tb, const TreeView &tv, const QuadView &qv, const R *f, R *M,
+                       const int *skip, cudaStream_t s, R *W = nullptr) {
+    const int ns = p2m_slots(tb.np);
+    if (ns == 3) (k_p2m<R, C, DL, WEIGHTS, 3><<<nleaf, P2M_T, 0, s>>>(nleaf, tb, tv, qv, f, M, skip, W), ::bem::count_launch());
+    else if (ns == 8) (k_p2m<R, C, DL, WEIGHTS, 8><<<nleaf, P2M_T, 0, s>>>(nleaf, tb, tv, qv, f, M, skip, W), ::bem::count_launch());
+    else (k_p2m<R, C, DL, WEIGHTS, 14><<<nleaf, P2M_T, 0, s>>>(nleaf, tb, tv, qv, f, M, skip, W), ::bem::count_launch());
+}
+
+template <int C>
+static void launch_p2m_stored(int nleaf, int np, const TreeView &tv, const float *W, const float *f, float *M,
+                              const int *skip, cudaStream_t s) {
+    const int ns = p2m_slots(np);
+    if (ns == 3) (k_p2m_stored<C, 3><<<nleaf, P2S_T, 0, s>>>(nleaf, np, tv, W, f, M, skip), ::bem::count_launch());
+    else if (ns == 8) (k_p2m_stored<C, 8><<<nleaf, P2S_T, 0, s>>>(nleaf, np, tv, W, f, M, skip), ::bem::count_launch());
+    else (k_p2m_stored<C, 14><<<nleaf, P2S_T, 0, s>>>(nleaf, np, tv, W, f, M, skip), ::bem::count_launch());
 }
 
 // ---------------------------------------------------------------------------
@@ -997,8 +1020,8 @@ int alloc_fmm(bem_plan *P, cudaStream_t s) {
         // stored P2M weights of the double layer (op A, every product of a solve)
         BEM_TRY(A.alloc(&P->p2m_W, (size_t)P->Q * np));
         const Tree &t = P->t;
-        (k_p2m<float, 1, true, true><<<t.nleaf, P2M_T, 0, s>>>(t.nleaf, tabs_of(P), view_of(P), quad_of(P), nullptr,
-                                                                nullptr, nullptr, P->p2m_W), ::bem::count_launch());
+        launch_p2m<float, 1, true, true>(t.nleaf, tabs_of(P), view_of(P), quad_of(P), nullptr, nullptr, nullptr, s,
+                                         P->p2m_W);
         BEM_LAUNCH_CHECK();
     }
     set_translation_attributes();
@@ -1025,12 +1048,12 @@ static int run_fmm(bem_plan *P, int op, double kwave, R *f, R *M, R *L, cudaStre
     if (ev) BEM_CUDA(cudaEventRecord(ev[1], s));
     if constexpr (sizeof(R) == sizeof(float)) {
         if (op == BEM_OP_A && P->p2m_W)
-            (k_p2m_stored<C><<<t.nleaf, P2S_T, 0, s>>>(t.nleaf, np, tv, P->p2m_W, f, M, sk), ::bem::count_launch());
-        else if (op == BEM_OP_A) (k_p2m<R, C, true><<<t.nleaf, P2M_T, 0, s>>>(t.nleaf, tb, tv, qv, f, M, sk), ::bem::count_launch());
-        else (k_p2m<R, C, false><<<t.nleaf, P2M_T, 0, s>>>(t.nleaf, tb, tv, qv, f, M, sk), ::bem::count_launch());
+            launch_p2m_stored<C>(t.nleaf, np, tv, P->p2m_W, f, M, sk, s);
+        else if (op == BEM_OP_A) launch_p2m<R, C, true>(t.nleaf, tb, tv, qv, f, M, sk, s);
+        else launch_p2m<R, C, false>(t.nleaf, tb, tv, qv, f, M, sk, s);
     } else {
-        if (op == BEM_OP_A) (k_p2m<R, C, true><<<t.nleaf, P2M_T, 0, s>>>(t.nleaf, tb, tv, qv, f, M, sk), ::bem::count_launch());
-        else (k_p2m<R, C, false><<<t.nleaf, P2M_T, 0, s>>>(t.nleaf, tb, tv, qv, f, M, sk), ::bem::count_launch());
+        if (op == BEM_OP_A) launch_p2m<R, C, true>(t.nleaf, tb, tv, qv, f, M, sk, s);
+        else launch_p2m<R, C, false>(t.nleaf, tb, tv, qv, f, M, sk, s);
     }
     BEM_LAUNCH_CHECK();
     if (ev) BEM_CUDA(cudaEventRecord(ev[2], s));
@@ -1071,10 +1094,10 @@ static int field_moments_t(bem_plan *P, const void *phi, const void *chi, R *f, 
     const int *sk = P->skip;
     BEM_TRY(set_slots(P, phi, nullptr, s));
     (k_p2q<R, C><<<(Q + 255) / 256, 256, 0, s>>>(Q, P->npe, t.el_phi, P->q.w, P->xptr, f, sk), ::bem::count_launch());
-    (k_p2m<R, C, true><<<t.nleaf, P2M_T, 0, s>>>(t.nleaf, tb, tv, qv, f, M, sk), ::bem::count_launch());
+    launch_p2m<R, C, true>(t.nleaf, tb, tv, qv, f, M, sk, s);
     BEM_TRY(set_slots(P, chi, nullptr, s));
     (k_p2q<R, C><<<(Q + 255) / 256, 256, 0, s>>>(Q, P->npe, t.el_chi, P->q.w, P->xptr, f, sk), ::bem::count_launch());
-    (k_p2m<R, C, false><<<t.nleaf, P2M_T, 0, s>>>(t.nleaf, tb, tv, qv, f, Bm, sk), ::bem::count_launch());
+    launch_p2m<R, C, false>(t.nleaf, tb, tv, qv, f, Bm, sk, s);
     const size_t n = (size_t)t.nbox * P->mi.np * C;
     (k_sub_moments<R><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, M, Bm), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
@@ -1146,10 +1169,13 @@ int enqueue_matvec_raw(bem_plan *P, int op, int green, double kwave, int with_di
 struct DiagSwap {
     int p, precision, green, p_min;
 };
-// the diagonal's product runs at one order for every level
+// the diagonal's product runs at one order for every level, at most DIAG_P
+// (float64: DIAG_P; mixed: p + 4): its truncation error is then below the
+// float64 diagonal's stated 5e-8
+constexpr int DIAG_P = 16;
 static DiagSwap diag_fields(const bem_plan *P) {
     const bool mixed = P->prm.precision == BEM_MIXED;
-    return DiagSwap{mixed ? std::min(PMAX, P->prm.p + 4) : PMAX, mixed ? BEM_MIXED : BEM_F64, BEM_LAPLACE, 0};
+    return DiagSwap{mixed ? std::min(DIAG_P, P->prm.p + 4) : DIAG_P, mixed ? BEM_MIXED : BEM_F64, BEM_LAPLACE, 0};
 }
 static DiagSwap swap_fields(bem_plan *P, const DiagSwap &d) {
     const DiagSwap old{P->prm.p, P->prm.precision, P->green, P->prm.p_min};

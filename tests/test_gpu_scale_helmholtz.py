@@ -58,3 +58,31 @@ def test_sphere_plane_wave_at_scale(oracle_lib, sphere6, ka, p):
     mie = oracle_lib.mie_rigid_sphere_scattered(ka, m.nodes[:, 2])
     assert rel_l2(out[bem.BEM_F64][1], mie) <= MIE_TOL
     assert rel_l2(out[bem.BEM_MIXED][1], out[bem.BEM_F64][1]) <= MX_VS_F64_TOL
+
+
+def test_sphere_plane_wave_ka16(oracle_lib):
+    """ka = 16 on the level-5 icosphere (20,480 six-node triangles, 40,962
+    nodes, 13 nodes per wavelength), mixed form.  The coarse interaction
+    levels hold boxes several wavelengths across; the Cartesian expansions
+    there need a wider separation (eta = 3) at order 16 (at eta = 2 even order
+    20 leaves 6.5e-4).  Product against the oracle's matrix-free rows, solution
+    against the Mie series."""
+    ka = 16.0
+    m = I.icosphere(5, I.TRI6)
+    P = Plan(m, bem.BEM_HELMHOLTZ, ka, p=16, leaf_size=64, eta=3.0, precision=bem.BEM_MIXED)
+    try:
+        rows = np.sort(np.random.default_rng(16).choice(P.n_phi, 32, replace=False))
+        x = I.random_vector(P.n_phi, 1, complex_=True)
+        y = P.matvec(bem.BEM_OP_A, x)
+        ref = oracle_lib.apply_rows(m.nodes, m.elems, P.chi_idx, oracle_lib.OP_A, x, rows, oracle_lib.HELMHOLTZ, ka)
+        err = rel_l2(y[rows], ref)
+        chi = oracle_lib.chi_from_elem(P.chi_idx, P.n_chi, I.plane_wave_rigid(m, ka))
+        phi, code, info = P.solve(chi, tol=1e-10, max_iter=1500)
+        mie = oracle_lib.mie_rigid_sphere_scattered(ka, m.nodes[:, 2])
+        emie = rel_l2(phi, mie)
+        print(f"ka=16: product {err:.2e}, iters {info.iters}, Mie {emie:.2e}")
+        assert code == bem.BEM_OK and bem.bem_plan_device_status(P.plan) == 0
+        assert err <= 2e-5
+        assert emie <= 3e-4
+    finally:
+        P.close()
