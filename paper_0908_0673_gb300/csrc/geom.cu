@@ -644,7 +644,7 @@ __device__ void refine_serial(const double *X, const double xi[3], const R *d, c
 }
 
 template <class R, bool HELM, int NPE>
-__global__ void __launch_bounds__(32 * SP_WARPS, 4) k_special_pair(CorrArgs a, int npairs, const int *__restrict__ pair_node,
+__global__ void __launch_bounds__(32 * SP_WARPS, 3) k_special_pair(CorrArgs a, int npairs, const int *__restrict__ pair_node,
                                                                 const int *__restrict__ pair_e, double *valD,
                                                                 double *valS, double *d0pair) {
     constexpr int C = HELM ? 2 : 1;
@@ -663,15 +663,35 @@ __global__ void __launch_bounds__(32 * SP_WARPS, 4) k_special_pair(CorrArgs a, i
     const float *df = sdf[warp];
     const R kk = (R)a.k;
     const float tau2 = (float)(a.tau * a.tau);
-    for (int pr = blockIdx.x * SP_WARPS + warp; pr < npairs; pr += gridDim.x * SP_WARPS) {
-        const int node = pair_node[pr], e = pair_e[pr];
-        const double xi[3] = {a.nodes[3 * (size_t)node], a.nodes[3 * (size_t)node + 1], a.nodes[3 * (size_t)node + 2]};
+    // the next pair's indices and coordinates are loaded while the current
+    // one is integrated (a two-stage pipeline over the grid-stride loop)
+    const int stride = gridDim.x * SP_WARPS;
+    int pr = blockIdx.x * SP_WARPS + warp;
+    int node_n = 0, e_n = 0, vid_n = -1;
+    double xin[3] = {0.0, 0.0, 0.0}, xv_n = 0.0;
+    auto fetch_head = [&](int q) {
+        if (q < npairs) { node_n = pair_node[q]; e_n = pair_e[q]; }
+    };
+    auto fetch_tail = [&](int q) {
+        if (q < npairs) {
+            xin[0] = a.nodes[3 * (size_t)node_n];
+            xin[1] = a.nodes[3 * (size_t)node_n + 1];
+            xin[2] = a.nodes[3 * (size_t)node_n + 2];
+            vid_n = lane < 3 * NPE ? a.el_phi[(size_t)e_n * NPE + lane / 3] : -1;
+            xv_n = vid_n >= 0 ? a.nodes[3 * (size_t)vid_n + lane % 3] : 0.0;
+        }
+    };
+    fetch_head(pr);
+    fetch_tail(pr);
+    for (; pr < npairs; pr += stride) {
+        const int node = node_n;
+        const double xi[3] = {xin[0], xin[1], xin[2]};
+        const int vid = vid_n;
+        const double xv = xv_n;
+        fetch_head(pr + stride);
         __syncwarp();                                   // the previous pair's reads of the tables are done
-        int vid = -1;
         if (lane < 3 * NPE) {
             const int c = lane % 3;
-            vid = a.el_phi[(size_t)e * NPE + lane / 3];
-            const double xv = a.nodes[3 * (size_t)vid + c];
             sX[warp][lane] = xv;
             sd[warp][lane] = (R)(xv - xi[c]);
             sdf[warp][lane] = (float)(xv - xi[c]);
@@ -811,6 +831,7 @@ __global__ void __launch_bounds__(32 * SP_WARPS, 4) k_special_pair(CorrArgs a, i
                 if (head + lane < tail) eval_st<R, HELM, NPE>(d, kk, rs[k], rt[k], rw[k], v);
             }
         }
+        fetch_tail(pr + stride);
         // transposing butterfly: after the step of width k a lane keeps the
         // half of its values selected by bit k of its index, so value l of
         // the pair ends on lane l (with 16 values, a plain step across the
