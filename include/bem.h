@@ -343,8 +343,11 @@ int bem_plan_stage_times(bem_plan *plan, int op, const void *x_dev, void *y_dev,
 #define BEM_NSETUP 7   /* mesh upload, octree, geometry + radii + lists, special-pair correction,
                           offset classes, diagonal + translation tables, stats */
 
-/* Wall-clock milliseconds of every set-up stage of the plan (host array of
- * BEM_NSETUP), measured with the stream synchronised at each stage boundary. */
+/* Milliseconds of every set-up stage of the plan (host array of BEM_NSETUP).
+ * Upload, octree, geometry and stats are wall clock with the stream
+ * synchronised at each boundary.  The correction and the diagonal are GPU
+ * spans on two streams that overlap; the offset classes are host time spent
+ * while the correction runs. */
 int bem_plan_setup_times(const bem_plan *plan, double *ms);
 
 /* Kernel launches issued by this library in this process so far (a graph

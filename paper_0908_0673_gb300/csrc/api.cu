@@ -137,13 +137,12 @@ static int plan_setup(bem_plan *P, cudaStream_t s) {
     BEM_TRY(build_radii_lists(P, s));
     BEM_TRY(build_near_items(P));
     BEM_TRY(lap(2));
-    BEM_TRY(build_m2l_classes(P));
-    BEM_TRY(lap(4));
-    // The special-pair correction (stream s) and the diagonal's product (s2)
-    // run side by side: every allocation of both is made before the first
-    // long kernel is enqueued, and the product joins s before the diagonal
-    // adds the correction's row sums.  Stage times of the two are the GPU
-    // spans on their streams (they overlap).
+    // The special-pair correction (stream s) is enqueued first; the host then
+    // builds the M2L offset classes while it runs, and the diagonal's product
+    // (s2) runs beside it.  The product joins s before the diagonal adds the
+    // correction's row sums.  Stage times of the correction and the diagonal
+    // are the GPU spans on their streams (they overlap); the class stage is
+    // host time.
     cudaStream_t s2 = P->setup_stream[1];
     cudaEvent_t ev[6] = {};
     for (auto &e : ev) BEM_CUDA(cudaEventCreate(&e));
@@ -153,10 +152,17 @@ static int plan_setup(bem_plan *P, cudaStream_t s) {
     };
     BEM_CUDA(cudaEventRecord(ev[0], s));
     BEM_CUDA(cudaStreamWaitEvent(s2, ev[0], 0));
-    BEM_CUDA(cudaEventRecord(ev[2], s2));
-    int rc = diagonal_prepare(P, s2);
-    if (rc == BEM_OK) rc = build_correction(P, s);
+    int rc = build_correction(P, s);
     if (rc == BEM_OK) BEM_CUDA(cudaEventRecord(ev[1], s));
+    if (rc != BEM_OK) {
+        cudaStreamSynchronize(s);
+        return fin(rc);
+    }
+    t0 = std::chrono::steady_clock::now();
+    rc = build_m2l_classes(P);
+    P->setup_ms[4] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (rc == BEM_OK) BEM_CUDA(cudaEventRecord(ev[2], s2));
+    if (rc == BEM_OK) rc = diagonal_prepare(P, s2);
     if (rc == BEM_OK) rc = diagonal_product(P, s2);
     if (rc == BEM_OK) BEM_CUDA(cudaEventRecord(ev[3], s2));
     if (rc == BEM_OK) BEM_CUDA(cudaStreamWaitEvent(s, ev[3], 0));
