@@ -138,11 +138,12 @@ static int plan_setup(bem_plan *P, cudaStream_t s) {
     BEM_TRY(build_near_items(P));
     BEM_TRY(lap(2));
     // The special-pair correction (stream s) is enqueued first; the host then
-    // builds the M2L offset classes while it runs, and the diagonal's product
-    // (s2) runs beside it.  The product joins s before the diagonal adds the
-    // correction's row sums.  Stage times of the correction and the diagonal
-    // are the GPU spans on their streams (they overlap); the class stage is
-    // host time.
+    // builds the M2L offset classes while it runs, enqueues the diagonal's
+    // tables and product at the diagonal's order (s2), and builds the plan's
+    // own order (alloc_fmm, its kernels on s) while both run.  The product
+    // joins s before the diagonal adds the correction's row sums.  Stage times
+    // of the correction and the diagonal are the GPU spans on their streams
+    // (they overlap); the class stage is host time.
     cudaStream_t s2 = P->setup_stream[1];
     cudaEvent_t ev[6] = {};
     for (auto &e : ev) BEM_CUDA(cudaEventCreate(&e));
@@ -165,6 +166,7 @@ static int plan_setup(bem_plan *P, cudaStream_t s) {
     if (rc == BEM_OK) rc = diagonal_prepare(P, s2);
     if (rc == BEM_OK) rc = diagonal_product(P, s2);
     if (rc == BEM_OK) BEM_CUDA(cudaEventRecord(ev[3], s2));
+    if (rc == BEM_OK) rc = alloc_fmm(P, s);
     if (rc == BEM_OK) BEM_CUDA(cudaStreamWaitEvent(s, ev[3], 0));
     if (rc == BEM_OK) rc = diagonal_finish(P, s);
     if (rc == BEM_OK) BEM_CUDA(cudaEventRecord(ev[4], s));

@@ -158,22 +158,15 @@ struct bem_mesh {
     ~bem_mesh();
 };
 
-struct bem_plan {
-    bem_mesh *mesh = nullptr;
-    int device = 0, sm_count = 0;
-    int green = BEM_LAPLACE;
-    double k = 0.0;
-    bem_fmm_params prm{};
-    int64_t N = 0, E = 0, Q = 0, nchi = 0;
-    int npe = 0;
-    bem::Arena arena;
+namespace bem {
+// What alloc_fmm builds for one expansion order and free_fmm releases: index
+// tables, product buffers and the order-dependent M2L tables.  The plan holds
+// one (its own order); during set-up the diagonal's product runs from a
+// second one at the diagonal's order (bem_plan::diag_state), so that the
+// plan's own can be built while that product runs.  std::swap of the base
+// moves a whole state in or out.
+struct FmmState {
     bem::MIndex mi;
-    bem::Tree t;
-    bem::Quad q;
-    bem::Correction corr;
-    // device copies of mesh data (original order)
-    double *nodes = nullptr;            // [N][3]
-    int *elems = nullptr, *chi = nullptr;
     // multi-index tables on the device
     int *d_m = nullptr, *d_n = nullptr, *d_k = nullptr, *d_idx3 = nullptr;
     double *d_binom = nullptr;          // [(PMAX+1)^2]
@@ -182,29 +175,17 @@ struct bem_plan {
     double *f = nullptr;                // quadrature strengths [Q] (x2 for complex)
     double *M = nullptr, *L = nullptr;  // [nbox][np] scaled moments / locals (x2 complex)
     double *ytmp = nullptr;             // [N] far + near regular sums (x2 complex)
-    double *C = nullptr;                // diagonal [N]
     float *fM = nullptr, *fL = nullptr, *ff = nullptr;   // mixed-precision copies
     const void **xptr = nullptr;        // device slot: input vector of the next matvec
     void **yptr = nullptr;              // device slot: output vector
-    int *skip = nullptr;                // device flag: kernels return at once when set
-    // graphs
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
-    long long graph_kernels[2] = {0, 0};
-    cudaStream_t capture_stream = nullptr;
-    // M2L on canonical offset classes (m2l_tc.cu: tensor-core form and tables;
-    // m2l_simt.cu: SIMT form)
-    int sy_ncls = 0, sy_ntile = 0, sy_ldp = 0, sy_nkc = 0;
+    // M2L on canonical offset classes: the order-dependent part (m2l_tc.cu,
+    // m2l_simt.cu); the classes themselves belong to the plan
+    int sy_ntile = 0, sy_ldp = 0, sy_nkc = 0;
     int sy_ready = 0;                   // order-dependent tables built for the current order
     int sy_tc = 0;                      // the tensor-core form runs (mixed-precision Laplace)
-    double *sy_rho = nullptr;           // [class][3] canonical offsets / h_t
-    double *sy_kh = nullptr;            // [class] k h_t (Helmholtz)
-    int *sy_dl = nullptr;               // [class] level difference
     int *sy_tile_cls = nullptr, *sy_tile_start = nullptr, *sy_tile_cnt = nullptr;
     int *sy_src = nullptr, *sy_sig = nullptr, *sy_pair = nullptr;   // pairs in class order
-    int *sy_sig_u = nullptr;            // [pair] symmetry id (permutation * 8 + sign bits)
-    std::vector<int> sy_hcls, sy_hsig, sy_hsrc, sy_hip;   // host: per pair class, symmetry, source; list offsets
     std::vector<int> sy_bt, sy_bb, sy_bu;                 // host: per run, first tile, target and pair (size runs + 1)
-    std::vector<int> sy_hlev, sy_hdl;                     // host: per canonical class, target level (when keyed) and dl
     int *sy_ord = nullptr;              // [class][2] source and target order
     double *sy_D = nullptr;             // [class][np][C] derivative tables
     float *sy_fD = nullptr;
@@ -218,18 +199,52 @@ struct bem_plan {
     uint4 *sy_sched = nullptr;          // MMA schedule of a tile
     int *sy_sched_ptr = nullptr, sy_nsched = 0;
     bem::TcGroups sy_g;
+    float *p2m_W = nullptr;             // [Q][np] stored double-layer P2M weights (float32 plans)
+    float *xf = nullptr;                // float32 copy of a product's input (correction product)
+    std::vector<int> lev_p;             // expansion order of each tree level
+    int *d_lev_p = nullptr;
+    bool lev_var = false;               // the order varies with the level (p_min > 0 and more than one order)
+};
+}  // namespace bem
+
+struct bem_plan : bem::FmmState {
+    bem_mesh *mesh = nullptr;
+    int device = 0, sm_count = 0;
+    int green = BEM_LAPLACE;
+    double k = 0.0;
+    bem_fmm_params prm{};
+    int64_t N = 0, E = 0, Q = 0, nchi = 0;
+    int npe = 0;
+    bem::Arena arena;
+    bem::Tree t;
+    bem::Quad q;
+    bem::Correction corr;
+    // device copies of mesh data (original order)
+    double *nodes = nullptr;            // [N][3]
+    int *elems = nullptr, *chi = nullptr;
+    double *C = nullptr;                // diagonal [N]
+    int *skip = nullptr;                // device flag: kernels return at once when set
+    // graphs
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    long long graph_kernels[2] = {0, 0};
+    cudaStream_t capture_stream = nullptr;
+    // M2L on canonical offset classes (m2l_tc.cu: tensor-core form and tables;
+    // m2l_simt.cu: SIMT form)
+    int sy_ncls = 0;
+    double *sy_rho = nullptr;           // [class][3] canonical offsets / h_t
+    double *sy_kh = nullptr;            // [class] k h_t (Helmholtz)
+    int *sy_dl = nullptr;               // [class] level difference
+    int *sy_sig_u = nullptr;            // [pair] symmetry id (permutation * 8 + sign bits)
+    std::vector<int> sy_hcls, sy_hsig, sy_hsrc, sy_hip;   // host: per pair class, symmetry, source; list offsets
+    std::vector<int> sy_hlev, sy_hdl;                     // host: per canonical class, target level (when keyed) and dl
     int *dev_err = nullptr;             // device word: set when a kernel's bounded wait gave up
     // counters
     double setup_ms[BEM_NSETUP] = {};
     int64_t near_pairs = 0;
     std::vector<void *> deferred;       // set-up temporaries released after the next synchronisation
     double *diag_ones = nullptr;        // phi = 1 of the diagonal's product (set-up only)
+    bem::FmmState diag_state;           // the diagonal's order while its product runs (set-up only)
     bool diag_mode = false;             // alloc_fmm for the diagonal's order
-    float *p2m_W = nullptr;             // [Q][np] stored double-layer P2M weights (float32 plans)
-    float *xf = nullptr;                // float32 copy of a product's input (correction product)
-    std::vector<int> lev_p;             // expansion order of each tree level
-    int *d_lev_p = nullptr;
-    bool lev_var = false;               // the order varies with the level (p_min > 0 and more than one order)
     cudaStream_t setup_stream[2] = {nullptr, nullptr};
     int2 *near_items[2] = {nullptr, nullptr};   // float32 near-field work items, 64- and 32-target passes
     int near_nitems[2] = {0, 0};

@@ -1187,16 +1187,21 @@ static DiagSwap swap_fields(bem_plan *P, const DiagSwap &d) {
 }
 
 // Three steps, so that the product can run on its own stream beside the
-// correction: prepare (buffers and tables at the diagonal's order; all
-// allocations happen here), product (phi = 1, into ytmp), finish (C += ytmp
-// once the correction's row sums are in C, then the buffers of the plan's own
-// order).  The plan's fields are switched only while each step runs.
+// correction: prepare (buffers and tables at the diagonal's order, built into
+// the plan and then moved to diag_state; all allocations happen here),
+// product (phi = 1, into the diagonal's ytmp), finish (C += that ytmp once the
+// correction's row sums are in C, then the diagonal's buffers are released).
+// The plan's own order is built between product and finish, while the product
+// runs.  The plan's fields are switched only while each step runs.
+static void swap_state(bem_plan *P) { std::swap(static_cast<FmmState &>(*P), P->diag_state); }
+
 int diagonal_prepare(bem_plan *P, cudaStream_t s) {
     const DiagSwap keep = swap_fields(P, diag_fields(P));
     P->diag_mode = true;                              // no stored weights at the diagonal's order
     int rc = alloc_fmm(P, s);
     P->diag_mode = false;
     if (rc == BEM_OK) rc = P->arena.alloc(&P->diag_ones, P->N);
+    swap_state(P);                                    // the plan's own state is empty until alloc_fmm
     swap_fields(P, keep);
     return rc;
 }
@@ -1204,24 +1209,26 @@ int diagonal_prepare(bem_plan *P, cudaStream_t s) {
 int diagonal_product(bem_plan *P, cudaStream_t s) {
     const int N = (int)P->N;
     const DiagSwap keep = swap_fields(P, diag_fields(P));
+    swap_state(P);
     (k_fill<<<(N + 255) / 256, 256, 0, s>>>(N, 1.0, P->diag_ones), ::bem::count_launch());
     int rc = set_slots(P, P->diag_ones, nullptr, s);
     if (rc == BEM_OK) rc = enqueue_matvec_raw(P, BEM_OP_A, BEM_LAPLACE, 0.0, 0, s, nullptr);
+    swap_state(P);
     swap_fields(P, keep);
     return rc;
 }
 
 int diagonal_finish(bem_plan *P, cudaStream_t s) {
     const int N = (int)P->N;
-    (k_finish_diag<<<(N + 255) / 256, 256, 0, s>>>(N, P->ytmp, P->C), ::bem::count_launch());
+    (k_finish_diag<<<(N + 255) / 256, 256, 0, s>>>(N, P->diag_state.ytmp, P->C), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
     BEM_CUDA(cudaStreamSynchronize(s));
     P->arena.release(P->diag_ones);
     P->diag_ones = nullptr;
-    const DiagSwap keep = swap_fields(P, diag_fields(P));
+    swap_state(P);
     free_fmm(P);
-    swap_fields(P, keep);
-    return alloc_fmm(P, s);
+    swap_state(P);
+    return BEM_OK;
 }
 
 // releases what alloc_fmm allocated

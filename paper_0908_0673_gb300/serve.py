@@ -91,19 +91,21 @@ class EngineError(RuntimeError):
 # (p = 10, leaf sizes 32-128, eta = 2, Duffy order 12, tau = 2) and a GMRES(30)
 # basis, by (Green's function, precision).  The correction matrix dominates
 # (a few hundred entries per row for each of D and S); then the translation
-# tables, the diagonal's higher-order temporaries and the Krylov basis.  The
-# values bound the measured peaks (9-28 kB per node on spheres, ellipsoids and
-# graded cubes of 1k-18k quadratic elements) with a margin; the GPU tests
-# check the bound.  The fixed part holds the M2L row buffer, which is capped
-# at 128 MiB whatever the mesh (its rows are computed and gathered in runs of
-# targets), and 64 MiB of small tables.
+# tables, the diagonal's higher-order buffers (held while the plan's own order
+# is built beside them: both sets of buffers, the stored P2M weights included,
+# exist at the set-up peak) and the Krylov basis.  The values bound the
+# measured peaks (9-28 kB per node on spheres, ellipsoids and graded cubes of
+# 1k-18k quadratic elements, before the two orders overlapped) with a margin;
+# the GPU tests check the bound.  The fixed part holds the M2L row buffers of
+# the two orders, each capped at 128 MiB whatever the mesh (rows are computed
+# and gathered in runs of targets), and 64 MiB of small tables.
 _BYTES_PER_NODE = {
-    (bem.BEM_LAPLACE, bem.BEM_F64): 28_000,
-    (bem.BEM_LAPLACE, bem.BEM_MIXED): 28_000,
-    (bem.BEM_HELMHOLTZ, bem.BEM_F64): 36_000,
-    (bem.BEM_HELMHOLTZ, bem.BEM_MIXED): 36_000,
+    (bem.BEM_LAPLACE, bem.BEM_F64): 36_000,
+    (bem.BEM_LAPLACE, bem.BEM_MIXED): 36_000,
+    (bem.BEM_HELMHOLTZ, bem.BEM_F64): 44_000,
+    (bem.BEM_HELMHOLTZ, bem.BEM_MIXED): 44_000,
 }
-_BYTES_FIXED = (64 + 128) << 20
+_BYTES_FIXED = (64 + 2 * 128) << 20
 
 
 def estimate_peak_footprint(n_nodes: int, green: int, precision: int) -> int:
