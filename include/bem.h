@@ -302,7 +302,11 @@ int bem_plan_export_correction(const bem_plan *plan, int64_t *counts, int64_t *r
 
 /* Multipole moments and local expansions left by the last bem_matvec, per
  * box (level-by-level numbering) and multi-index, unscaled, float64 (complex
- * pairs for Helmholtz); mnk: host int32 [n_p][3] multi-indices.  Blocks. */
+ * pairs for Helmholtz); mnk: host int32 [n_p][3] multi-indices.  Blocks.
+ * The product forms moments only at levels at or below the coarsest level
+ * holding an interaction-list source, and locals only at or below the
+ * coarsest level holding an interaction-list target (coarser ones never
+ * reach the result); the values exported for coarser boxes are unspecified. */
 int bem_plan_export_expansions(const bem_plan *plan, int32_t *mnk, double *moments, double *locals);
 
 /* Diagonal C_i = 1 + sum_j D0_ij (Eq. 2-3) as computed at set-up: host [n_phi]. */

@@ -231,6 +231,9 @@ struct bem_plan : bem::FmmState {
     // M2L on canonical offset classes (m2l_tc.cu: tensor-core form and tables;
     // m2l_simt.cu: SIMT form)
     int sy_ncls = 0;
+    // coarsest tree level holding an M2L source (whose moments are used) and an
+    // M2L target (whose locals can be nonzero); nlev when there is none
+    int m2l_src_lmin = 0, m2l_tgt_lmin = 0;
     double *sy_rho = nullptr;           // [class][3] canonical offsets / h_t
     double *sy_kh = nullptr;            // [class] k h_t (Helmholtz)
     int *sy_dl = nullptr;               // [class] level difference
@@ -291,7 +294,7 @@ int launch_m2l_derivs(bem_plan *P, int ncls, const double *rho, const double *kh
 template <class R, int C>
 int launch_translations(bem_plan *P, R *M, R *L, cudaStream_t s, cudaEvent_t *ev);
 template <class R, int C>
-int launch_m2m(bem_plan *P, R *M, cudaStream_t s);
+int launch_m2m(bem_plan *P, R *M, cudaStream_t s, int lmin = 0);
 int field_moments(bem_plan *P, const void *phi, const void *chi, cudaStream_t s);
 int build_near_items(bem_plan *P);
 int diagonal_prepare(bem_plan *P, cudaStream_t s);

@@ -450,6 +450,7 @@ static double gm_tol(const bem_plan *P, double tol) {
     return P->prm.precision == BEM_MIXED ? std::max(tol, TAU_MIXED) : tol;
 }
 
+
 // host decision after a true residual: returns true when the solve has ended
 static bool gm_after_residual(GmSolver &g, double bnorm, double beta) {
     g.restarts++;
@@ -498,7 +499,7 @@ static int gm_enqueue_start(GmSolver &g) {
     return BEM_OK;
 }
 
-constexpr int GM_CHUNK = 4;         // Arnoldi steps per chunk
+constexpr int GM_CHUNK = 2;         // Arnoldi steps per chunk (two chunks in flight)
 
 template <int C>
 static int gm_enqueue_cycle(GmSolver &g) {
@@ -628,8 +629,8 @@ static int gm_run(GmSolver &g, bool blocking) {
 // denominator vanishes; the host then evaluates the true residual b - A x and
 // restarts from it (rh = r) while it is above the tolerance, with the same
 // stopping rule as GMRES (mixed plans: max(tol, TAU_MIXED), or a restart that
-// fails to halve the true residual).  Steps go out in chunks of four with at
-// most two in flight, each chunk reading back the flag.
+// fails to halve the true residual).  Steps go out in chunks of GM_CHUNK with
+// at most two in flight, each chunk reading back the flag.
 // ---------------------------------------------------------------------------
 struct BcState {
     // scalars (complex as pairs): [0] rho, [2] rho_prev, [4] alpha, [6] omega,

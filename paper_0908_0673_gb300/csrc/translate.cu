@@ -342,6 +342,10 @@ int build_m2l_classes(bem_plan *P) {
             }
             pair_cls[u] = c;
         }
+    P->m2l_src_lmin = P->m2l_tgt_lmin = t.nlev;
+    for (int b = 0; b < t.nbox; b++)
+        if (ip[b + 1] > ip[b]) P->m2l_tgt_lmin = std::min(P->m2l_tgt_lmin, lev[b]);
+    for (int64_t u = 0; u < t.n_inter; u++) P->m2l_src_lmin = std::min(P->m2l_src_lmin, lev[ii[u]]);
     return build_m2l_sym(P, pair_cls, kvec, dls, levs, ii, ip);
 }
 
@@ -365,18 +369,19 @@ void free_translation_tables(bem_plan *P) { free_sym_tables(P); }
 // ---------------------------------------------------------------------------
 // host: launchers
 // ---------------------------------------------------------------------------
-// upward pass: moments of every parent from its children, level by level
 static int np_host(int q) { return (q + 1) * (q + 2) * (q + 3) / 6; }
 static int level_order(const bem_plan *P, int l) {
     return l < (int)P->lev_p.size() ? P->lev_p[l] : P->mi.p;
 }
 
+// upward pass: moments of every parent from its children, level by level,
+// up to level lmin (coarser moments are not formed)
 template <class R, int C>
-int launch_m2m(bem_plan *P, R *M, cudaStream_t s) {
+int launch_m2m(bem_plan *P, R *M, cudaStream_t s, int lmin) {
     const Tree &t = P->t;
     const int nps = P->mi.np, pt1 = P->mi.p + 1;
     const int *sk = P->skip;
-    for (int l = t.nlev - 2; l >= 0; l--) {
+    for (int l = t.nlev - 2; l >= std::max(0, lmin); l--) {
         const int off = t.lev_off[l], cnt = t.lev_off[l + 1] - off;
         const int p = level_order(P, l), np = np_host(p), npc = np_host(level_order(P, l + 1)), P1 = p + 1;
         const size_t tab_sm = sizeof(R) * P1 * P1 + sizeof(short) * P1 * P1 * P1 + 16;
@@ -396,7 +401,11 @@ int launch_translations(bem_plan *P, R *M, R *L, cudaStream_t s, cudaEvent_t *ev
     const Tree &t = P->t;
     const int np = P->mi.np;
     const int *sk = P->skip;
-    BEM_TRY((launch_m2m<R, C>(P, M, s)));
+    // M2L reads moments at levels >= m2l_src_lmin only, and every local
+    // coarser than m2l_tgt_lmin is zero (the gathers write each box's local),
+    // so the upward pass stops at the first and the downward one starts below
+    // the second
+    BEM_TRY((launch_m2m<R, C>(P, M, s, P->m2l_src_lmin)));
     BEM_LAUNCH_CHECK();
     if (ev) BEM_CUDA(cudaEventRecord(ev[3], s));
     if (std::is_same<R, float>::value && C == 1 && P->sy_tc) {
@@ -406,7 +415,7 @@ int launch_translations(bem_plan *P, R *M, R *L, cudaStream_t s, cudaEvent_t *ev
     }
     BEM_LAUNCH_CHECK();
     if (ev) BEM_CUDA(cudaEventRecord(ev[4], s));
-    for (int l = 1; l < t.nlev; l++) {
+    for (int l = std::max(1, P->m2l_tgt_lmin + 1); l < t.nlev; l++) {
         // the shift runs at the parent's order; the child keeps its own order's terms
         const int off = t.lev_off[l], cnt = t.lev_off[l + 1] - off;
         const int p = level_order(P, l - 1), pnp = np_host(p), npo = np_host(level_order(P, l)), P1 = p + 1;
@@ -437,10 +446,10 @@ void set_translation_attributes() {
     set_sy_attributes();
 }
 
-template int launch_m2m<double, 1>(bem_plan *, double *, cudaStream_t);
-template int launch_m2m<double, 2>(bem_plan *, double *, cudaStream_t);
-template int launch_m2m<float, 1>(bem_plan *, float *, cudaStream_t);
-template int launch_m2m<float, 2>(bem_plan *, float *, cudaStream_t);
+template int launch_m2m<double, 1>(bem_plan *, double *, cudaStream_t, int);
+template int launch_m2m<double, 2>(bem_plan *, double *, cudaStream_t, int);
+template int launch_m2m<float, 1>(bem_plan *, float *, cudaStream_t, int);
+template int launch_m2m<float, 2>(bem_plan *, float *, cudaStream_t, int);
 template int launch_translations<double, 1>(bem_plan *, double *, double *, cudaStream_t, cudaEvent_t *);
 template int launch_translations<double, 2>(bem_plan *, double *, double *, cudaStream_t, cudaEvent_t *);
 template int launch_translations<float, 1>(bem_plan *, float *, float *, cudaStream_t, cudaEvent_t *);
