@@ -278,9 +278,16 @@ int bem_plan_create(bem_mesh *mesh, int green, double k, const bem_fmm_params *p
     P->Q = mesh->n_elems * NQ;
     P->nchi = mesh->n_chi;
     P->npe = mesh->npe;
-    // set-up runs on two streams of its own, after the caller's stream
+    // set-up runs on two streams of its own, after the caller's stream; the
+    // second (the diagonal's product) has the higher priority, so its blocks
+    // are scheduled first as the correction's quadrature blocks retire
     cudaStream_t cs = (cudaStream_t)cuda_stream;
-    for (auto &st : P->setup_stream) BEM_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    {
+        int least = 0, greatest = 0;
+        BEM_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        BEM_CUDA(cudaStreamCreateWithPriority(&P->setup_stream[0], cudaStreamNonBlocking, least));
+        BEM_CUDA(cudaStreamCreateWithPriority(&P->setup_stream[1], cudaStreamNonBlocking, greatest));
+    }
     cudaStream_t s = P->setup_stream[0];
     int rc = BEM_OK;
     {

@@ -391,6 +391,7 @@ __global__ void __launch_bounds__(32 * SS_WARPS) k_special_write(CorrArgs a, con
 // fixed order, so the stored values are the same on every run.
 // ---------------------------------------------------------------------------
 constexpr int SP_WARPS = 4;        // warps per block
+constexpr int SP_PAIRS_PER_WARP = 16;   // pairs per warp (grid-stride), launch granularity
 constexpr int SP_QCAP = 64;        // pieces per level buffer and warp (float32; half for float64)
 constexpr int SP_RING = 256;       // pending points per warp: a power of two >= 31 + 7 * 32
 constexpr float SP_UNIT = 1024.f;  // piece corners are multiples of 2^-10 (max_subdiv <= 10)
@@ -951,14 +952,12 @@ int build_correction(bem_plan *P, cudaStream_t s) {
     {
         const bool mx = P->prm.precision == BEM_MIXED, helm = P->green == BEM_HELMHOLTZ;
         // a grid-stride loop over pairs: as many blocks as fit on the device at once
-        auto grid_of = [&](const void *fn) {
-            int per_sm = 0;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * SP_WARPS, 0) != cudaSuccess || per_sm < 1)
-                per_sm = 1;
-            const long long want = ((long long)npairs + SP_WARPS - 1) / SP_WARPS;
-            return (int)std::max(1LL, std::min(want, (long long)per_sm * std::max(1, P->sm_count)));
-        };
-#define BEM_SW(R, H, NP) (k_special_pair<R, H, NP><<<grid_of((const void *)k_special_pair<R, H, NP>), 32 * SP_WARPS, 0, s>>>(a, npairs, pair_node, pair_e, K.valD, K.valS, d0pair), ::bem::count_launch())
+        // not a persistent grid: about SP_PAIRS_PER_WARP pairs per warp, so that
+        // blocks retire throughout and the diagonal's product (a stream of
+        // higher priority) gets SMs while the quadrature is still running
+        const int grid = (int)std::max<int64_t>(1, ((int64_t)npairs + SP_WARPS * SP_PAIRS_PER_WARP - 1) /
+                                                       (SP_WARPS * SP_PAIRS_PER_WARP));
+#define BEM_SW(R, H, NP) (k_special_pair<R, H, NP><<<grid, 32 * SP_WARPS, 0, s>>>(a, npairs, pair_node, pair_e, K.valD, K.valS, d0pair), ::bem::count_launch())
         if (npairs > 0) {
             if (npe == 3) {
                 if (mx) { if (helm) BEM_SW(float, true, 3); else BEM_SW(float, false, 3); }
