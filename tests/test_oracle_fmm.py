@@ -9,6 +9,8 @@
   list, and every interaction pair is well separated (Eq. 13);
 * the four-step matrix multiplication converges to the dense operator as the
   order p and the separation factor eta grow;
+* locals coarser than the coarsest interaction-list target are exactly zero
+  (what lets the product skip the coarse levels of both passes);
 * the oracle's GMRES agrees with the LU solve.
 """
 import numpy as np
@@ -127,3 +129,37 @@ def test_gmres_matches_lu(oracle_lib):
     x, it, rel = O.gmres(lambda v: A @ v, b, restart=30, tol=1e-10)
     assert rel <= 1e-10
     assert np.linalg.norm(x - x_lu) / np.linalg.norm(x_lu) < 1e-8
+
+
+@pytest.mark.parametrize("mesh,B,eta", [
+    (lambda: I.icosphere(3), 16, 2.0),
+    (lambda: I.cube(6, I.TRI6), 24, 2.0),
+    (lambda: I.geodesic(8, I.TRI6, axes=(0.6, 1.0, 1.7)), 32, 2.0),
+    (lambda: I.icosphere(3), 16, 1.0),
+])
+def test_coarse_expansions_never_reach_the_product(oracle_lib, mesh, B, eta):
+    """Section 3.6 as the product uses it: moments are read only by the
+    interaction lists, and a box's local is its parent's shifted local plus
+    its own list terms, so every local coarser than the coarsest box with a
+    nonempty interaction list is exactly zero, and the product can stop the
+    upward pass at the coarsest source level and start the downward pass
+    below the coarsest target level.  At eta = 2 neither level 0 nor level 1
+    interacts on these meshes."""
+    O = oracle_lib
+    m = mesh()
+    ci, nchi = O.chi_index(m.nodes, m.elems)
+    T = O.Tree(m.nodes, m.elems, B=B, eta=eta)
+    ip, lev = T.inter_ptr, T.level
+    assert len(T.inter_idx) > 0
+    src_lmin = int(lev[T.inter_idx].min())
+    tgt_lmin = int(lev[np.flatnonzero(ip[1:] > ip[:-1])].min())
+    if eta >= 2.0:
+        assert src_lmin >= 2 and tgt_lmin >= 2
+    corr = dict(row=np.zeros(0, np.int64), col_phi=np.zeros(0, np.int32), col_chi=np.zeros(0, np.int32),
+                D=np.zeros(0, complex), S=np.zeros(0, complex))
+    x = I.random_vector(m.n_nodes, 12)
+    _, mom, loc = O.fmm_apply(T, ci, O.OP_A, x, np.zeros(m.n_nodes), corr, 6, want_expansions=True)
+    coarse = lev < tgt_lmin
+    assert np.all(np.asarray(loc)[coarse] == 0)
+    assert np.any(np.asarray(loc)[~coarse] != 0)
+    assert np.any(np.asarray(mom)[lev < src_lmin] != 0) or src_lmin == 0   # formed by the oracle, unused
