@@ -330,14 +330,6 @@ __global__ void k_box_elems(int nbox, int E, const unsigned long long *__restric
     ee[b] = ull_lower_bound(ekeys, E, (unsigned long long)ne[b]);
 }
 
-__global__ void k_list_leaves(int nbox, const int *__restrict__ nchild, int *leaves, int *count) {
-    int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nbox) return;
-    if (nchild[b] == 0) {
-        // leaves are written in box order by a second pass below
-    }
-}
-
 template <class T>
 static int grow(Arena &A, T **p, size_t &cap, size_t need, size_t used, cudaStream_t s) {
     if (need <= cap) return BEM_OK;
