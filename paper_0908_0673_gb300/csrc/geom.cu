@@ -951,10 +951,10 @@ int build_correction(bem_plan *P, cudaStream_t s) {
     (k_corr_csr<<<(npairs + 255) / 256, 256, 0, s>>>(npairs, npe, pair_e, t.el_phi, t.el_chi, K.colD, K.colS), ::bem::count_launch());
     {
         const bool mx = P->prm.precision == BEM_MIXED, helm = P->green == BEM_HELMHOLTZ;
-        // a grid-stride loop over pairs: as many blocks as fit on the device at once
-        // not a persistent grid: about SP_PAIRS_PER_WARP pairs per warp, so that
-        // blocks retire throughout and the diagonal's product (a stream of
-        // higher priority) gets SMs while the quadrature is still running
+        // a grid-stride loop over pairs, but not a persistent grid: about
+        // SP_PAIRS_PER_WARP pairs per warp, so that blocks retire throughout and
+        // the diagonal's product (a stream of higher priority) gets SMs while
+        // the quadrature is still running
         const int grid = (int)std::max<int64_t>(1, ((int64_t)npairs + SP_WARPS * SP_PAIRS_PER_WARP - 1) /
                                                        (SP_WARPS * SP_PAIRS_PER_WARP));
 #define BEM_SW(R, H, NP) (k_special_pair<R, H, NP><<<grid, 32 * SP_WARPS, 0, s>>>(a, npairs, pair_node, pair_e, K.valD, K.valS, d0pair), ::bem::count_launch())
