@@ -159,46 +159,104 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(m, chi_idx, n_phi, iters, budget_s=15.0):
-    """The oracle's matrix-free rows of A on a bounded sample of this
-    workload, extrapolated to solves/s ((iters + 1) full products per solve)."""
-    import oracle as O
-    O.build()
-    rng = np.random.default_rng(0)
+def _omp_threads(n):
+    """Sets the OpenMP thread count of the oracle's runtime (libgomp is shared
+    by the process, so this reaches the oracle's parallel loops)."""
+    import ctypes
+    try:
+        ctypes.CDLL("libgomp.so.1").omp_set_num_threads(int(n))
+        return True
+    except OSError:
+        return False
+
+
+def _oracle_rows(O, m, chi_idx, n_phi, budget_s, seed=0):
+    """Rows of the oracle's matrix-free A product on a row sample sized to
+    about budget_s seconds: (rows timed, seconds)."""
+    rng = np.random.default_rng(seed)
     x = rng.standard_normal(n_phi)
     t0 = time.perf_counter()
-    rows = rng.choice(n_phi, 16, replace=False)
+    rows = rng.choice(n_phi, min(n_phi, 16), replace=False)
     O.apply_rows(m.nodes, m.elems, chi_idx, O.OP_A, x, rows)
     dt = time.perf_counter() - t0
     nrows = int(max(16, min(n_phi, 16 * budget_s / max(dt, 1e-3))))
     rows = rng.choice(n_phi, nrows, replace=False)
     t0 = time.perf_counter()
     O.apply_rows(m.nodes, m.elems, chi_idx, O.OP_A, x, rows)
-    dt = time.perf_counter() - t0
+    return nrows, time.perf_counter() - t0
+
+
+def oracle_small_problem(O):
+    """The paper's first test at full size (level-3 icosphere, 1280 flat
+    triangles, 642 nodes, point source inside): the oracle's dense assembly,
+    its LU solve and its restarted GMRES(30) solve (tol 1e-10) with the
+    direct matrix-free product, on all host cores."""
+    from paper_0908_0673_gb300 import inputs as I
+    m = I.icosphere(3, I.TRI3)
+    ci, n_chi = O.chi_index(m.nodes, m.elems)
+    _, chi_e = I.point_source(m, (0.1, 0.2, -0.15))
+    chi = O.chi_from_elem(ci, n_chi, chi_e)
+    t0 = time.perf_counter()
+    A, B, _ = O.operators(m.nodes, m.elems, ci, n_chi)
+    t_asm = time.perf_counter() - t0
+    b = (B @ chi).real
+    t0 = time.perf_counter()
+    phi_lu = O.solve_dense(A.real, b)
+    t_lu = time.perf_counter() - t0
+    # GMRES with the oracle's direct product (the right-hand side from it too)
+    t0 = time.perf_counter()
+    rhs = O.apply_rows(m.nodes, m.elems, ci, O.OP_B, chi)
+    phi_g, it, rel = O.gmres(lambda v: O.apply_rows(m.nodes, m.elems, ci, O.OP_A, v), rhs, restart=30, tol=1e-10)
+    t_gm = time.perf_counter() - t0
+    return {"workload": "icosphere3-tri3-laplace (1280 elements, 642 nodes)",
+            "dense_assembly_s": t_asm, "lu_solve_s": t_lu, "gmres_solve_s": t_gm, "gmres_iters": int(it),
+            "gmres_rel_residual": rel,
+            "gmres_vs_lu_rel_diff": float(np.linalg.norm(phi_g - phi_lu) / np.linalg.norm(phi_lu))}
+
+
+def cpu_baseline(m, chi_idx, n_phi, iters, budget_s=15.0, extra_legs=True):
+    """The oracle's matrix-free rows of A on a bounded sample of this
+    workload, extrapolated to solves/s ((iters + 1) full products per solve:
+    one for the right-hand side, one per Arnoldi step).  extra_legs adds the
+    same rate on one thread and the oracle's dense assembly, LU and GMRES
+    times on the paper's level-3 sphere."""
+    import oracle as O
+    O.build()
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    nrows, dt = _oracle_rows(O, m, chi_idx, n_phi, budget_s)
     rows_per_s = nrows / dt
     matvecs_per_s = rows_per_s / n_phi
     solves_per_s = matvecs_per_s / (iters + 1)
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": solves_per_s, "unit": "solves/s", "cores": cores, "kind": "oracle",
-            "sample": f"{nrows} of {n_phi} rows of one operator product ({dt:.1f} s), "
-                      f"extrapolated to (1 + {iters}) products per solve",
-            "matvecs_per_s": matvecs_per_s}
+    out = {"value": solves_per_s, "unit": "solves/s", "cores": cores, "kind": "oracle",
+           "sample": f"{nrows} of {n_phi} rows of one operator product ({dt:.1f} s), "
+                     f"extrapolated to (1 + {iters}) products per solve ({iters} = Arnoldi steps of the "
+                     f"float64 GMRES(30) solve of this workload to 1e-10 on the GPU)",
+           "matvecs_per_s": matvecs_per_s}
+    if extra_legs:
+        if _omp_threads(1):
+            n1, d1 = _oracle_rows(O, m, chi_idx, n_phi, budget_s / 4, seed=1)
+            _omp_threads(cores)
+            out["one_thread"] = {"matvecs_per_s": n1 / d1 / n_phi,
+                                 "solves_per_s": n1 / d1 / n_phi / (iters + 1),
+                                 "sample": f"{n1} rows ({d1:.1f} s), 1 thread",
+                                 "parallel_speedup": rows_per_s / (n1 / d1)}
+        out["small_problem"] = oracle_small_problem(O)
+    return out
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    from paper_0908_0673_gb300 import bem
+    import oracle as O
+    O.build()
     m, _, _ = workload(args.n)
-    h = bem.bem_mesh_create(None, m.nodes, m.elems, bem.BEM_TRI6)
-    n_phi, n_chi = bem.bem_mesh_sizes(h)
-    chi_idx = bem.bem_mesh_chi_index(h, m.n_elems, 6)
-    bem.bem_mesh_destroy(h)
+    chi_idx, n_chi = O.chi_index(m.nodes, m.elems)
+    n_phi = int(m.n_nodes)
     vals = []
     per = max(3.0, 60.0 / max(1, args.steps + args.warmup))
     for i in range(args.warmup + args.steps):
-        cb = cpu_baseline(m, chi_idx, n_phi, GMRES_ITERS_CUBE45, budget_s=per)
+        cb = cpu_baseline(m, chi_idx, n_phi, GMRES_ITERS_CUBE45, budget_s=per, extra_legs=False)
         if i >= args.warmup:
             vals.append(cb)
     v = statistics.median([c["value"] for c in vals])
@@ -616,7 +674,7 @@ def main():
     if rank == 0 and world == 1 and args.group > 0:
         out["grouped"] = grouped(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(m, chi_idx, n_phi, statistics.median(iters) if iters else 60)
+        out["cpu_baseline"] = cpu_baseline(m, chi_idx, n_phi, GMRES_ITERS_CUBE45)
     if rank == 0:
         print(json.dumps(out))
     bem.bem_mesh_destroy(mesh)

@@ -200,7 +200,8 @@ int bem_matvec(bem_plan *plan, int op, const void *x_dev, void *y_dev, void *cud
  * up the array's address, so make it before any stream capture.  BEM_EINVAL
  * (with the sizes in the message) if the plan needs more scratch than the
  * array holds.  All calls share the array: calls that overlap on the GPU race;
- * order them on one stream. */
+ * order them on one stream.  The result equals bem_matvec's bit for bit, and
+ * the caller's current device is the same after the call as before. */
 int bem_matvec_noalloc(bem_plan *plan, int op, const void *x_dev, void *y_dev, void *cuda_stream);
 
 /* Solves A phi = B chi for nrhs right-hand sides: b = B chi by one
@@ -211,10 +212,29 @@ int bem_matvec_noalloc(bem_plan *plan, int op, const void *x_dev, void *y_dev, v
  * stopped at max_iter; its best iterate is written.  Synchronises the stream
  * once per restart cycle.  A BEM_MIXED plan aims at max(tol, 5e-8), just
  * above the float32 operator's residual floor, and also stops when a whole
- * restart cycle fails to halve the true residual; info reports the residual
- * reached. */
+ * restart cycle fails to halve the true residual: that stop is BEM_OK when the
+ * residual reached is at most max(tol, 1e-6) and BEM_ENOCONV above it
+ * (bem_solve_stop_rule); info reports the residual reached. */
 int bem_solve(bem_plan *plan, const void *chi_dev, void *phi_dev, int nrhs,
               const bem_solve_params *params, bem_solve_info *info, void *cuda_stream);
+
+/* The decision bem_solve (GMRES and BiCGStab), bem_batch and bem_group take
+ * after every true residual, as a host function without device work, so that
+ * a caller or a test can check it.  precision: the plan's (BEM_F64 or
+ * BEM_MIXED); tol, max_iter: the solve parameters; restarts: true residuals
+ * evaluated so far, this one included; rel: this true relative residual
+ * ||b - A x|| / ||b||; prev_rel: the previous one (any value above 2 rel on
+ * the first); iters: Arnoldi steps (or iterations) taken.  Returns 1 when the
+ * solve ends here and writes *status:
+ *   rel <= tol (mixed: max(tol, 5e-8))                    -> BEM_OK;
+ *   mixed, restarts > 1 and rel > prev_rel / 2 (a stall)  -> BEM_OK if
+ *       rel <= max(tol, 1e-6), else BEM_ENOCONV;
+ *   iters >= max_iter                                     -> BEM_ENOCONV.
+ * Returns 0 (status untouched) when the solve goes on.  The paper's solver
+ * (Section 4) stops on its tolerance alone; the stall rule is this library's
+ * for float32 operators, whose rounding sets a residual floor. */
+int bem_solve_stop_rule(int precision, double tol, int restarts, double rel, double prev_rel, int iters,
+                        int max_iter, int *status);
 
 /* Field of the surface data at points off the surface (Section 2.2,
  * accelerated field evaluation): u(x) = integral over S of
@@ -326,12 +346,15 @@ int bem_plan_device_status(const bem_plan *plan, int *status);
  * solve adds the Krylov basis, so this is what admission control must reserve. */
 int bem_plan_peak_footprint(const bem_plan *plan, size_t *hbm_bytes);
 
-/* Integer counters of the plan (host array of 12): [0] n_boxes, [1] n_leaves,
- * [2] n_levels, [3] near-list entries, [4] interaction-list entries,
- * [5] near-field source-target pairs per matrix multiplication, [6] correction
- * nnz (D), [7] correction nnz (S), [8] quadrature points, [9] n_p,
- * [10] / [11] kernels in the captured op A / op B product graph (0 until the
- * first product). */
+/* Integer counters of the plan (host array of BEM_NSTATS): [0] n_boxes,
+ * [1] n_leaves, [2] n_levels, [3] near-list entries, [4] interaction-list
+ * entries, [5] near-field source-target pairs per matrix multiplication,
+ * [6] correction nnz (D), [7] correction nnz (S), [8] quadrature points,
+ * [9] n_p, [10] / [11] kernels in the captured op A / op B product graph (0
+ * until the first product), [12] 1 when the M2L runs on the tensor cores
+ * (tcgen05), 0 for the SIMT form, [13] canonical offset classes of the
+ * interaction pairs. */
+#define BEM_NSTATS 14
 int bem_plan_stats(const bem_plan *plan, int64_t *stats);
 
 /* Stages of one product, in launch order, for bem_plan_stage_times. */

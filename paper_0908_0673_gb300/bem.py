@@ -33,6 +33,7 @@ EXPORTS = [
     "bem_batch_create", "bem_batch_destroy", "bem_batch_submit", "bem_batch_progress", "bem_batch_poll",
     "bem_batch_wait", "bem_batch_release", "bem_batch_stream", "bem_plan_peak_footprint",
     "bem_plan_device_status", "bem_field", "bem_group_create", "bem_group_destroy", "bem_group_solve",
+    "bem_solve_stop_rule",
 ]
 BEM_NSETUP = 7
 SETUP_NAMES = ["upload", "tree", "geometry_radii_lists", "correction", "m2l_classes", "diagonal_tables", "stats"]
@@ -124,6 +125,7 @@ def load(build_if_missing: bool = True):
     L.bem_batch_release.argtypes = [P, i32]
     L.bem_batch_stream.argtypes = [P, i32]
     L.bem_batch_stream.restype = P
+    L.bem_solve_stop_rule.argtypes = [i32, dbl, i32, dbl, dbl, i32, i32, P]
     for name in EXPORTS:
         if name not in ("bem_fmm_params_default", "bem_solve_params_default", "bem_ctx_destroy",
                         "bem_last_error", "bem_mesh_destroy", "bem_plan_destroy", "bem_batch_destroy",
@@ -239,6 +241,15 @@ def bem_matvec_noalloc(plan, op, x, y, stream=None):
     """bem_matvec without any allocation (scratch in the library's fixed
     device array); see include/bem.h."""
     _check(load().bem_matvec_noalloc(plan, int(op), _ptr(x), _ptr(y), _stream(stream)))
+
+
+def bem_solve_stop_rule(precision, tol, restarts, rel, prev_rel, iters, max_iter):
+    """The solvers' decision after a true residual (host only): returns
+    (ended, status); status is None while the solve goes on."""
+    st = C.c_int(1)
+    end = load().bem_solve_stop_rule(int(precision), float(tol), int(restarts), float(rel), float(prev_rel),
+                                     int(iters), int(max_iter), C.byref(st))
+    return bool(end), (st.value if end else None)
 
 
 def bem_solve(plan, chi, phi, nrhs=1, params=None, stream=None):
@@ -394,7 +405,8 @@ def bem_plan_peak_footprint(plan) -> int:
 
 
 STAT_NAMES = ["n_boxes", "n_leaves", "n_levels", "n_near", "n_inter", "near_pairs", "corr_nnz_D",
-              "corr_nnz_S", "n_quad", "n_p", "graph_kernels_A", "graph_kernels_B"]
+              "corr_nnz_S", "n_quad", "n_p", "graph_kernels_A", "graph_kernels_B", "m2l_tensor_cores",
+              "m2l_classes"]
 
 
 def bem_plan_stage_times(plan, op, x, y, reps=5, stream=None) -> dict:
@@ -422,6 +434,6 @@ def bem_measure_peak(kind, stream=None) -> float:
 
 
 def bem_plan_stats(plan) -> dict:
-    st = np.zeros(12, np.int64)
+    st = np.zeros(len(STAT_NAMES), np.int64)
     _check(load().bem_plan_stats(plan, _ptr(st)))
     return dict(zip(STAT_NAMES, (int(v) for v in st)))

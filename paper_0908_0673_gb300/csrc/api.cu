@@ -530,6 +530,8 @@ int bem_plan_stats(const bem_plan *P, int64_t *st) {
     st[9] = P->mi.np;
     st[10] = P->graph_kernels[0];
     st[11] = P->graph_kernels[1];
+    st[12] = P->sy_tc;
+    st[13] = P->sy_ncls;
     return BEM_OK;
 }
 

@@ -302,8 +302,15 @@ int diagonal_product(bem_plan *P, cudaStream_t s);
 int diagonal_finish(bem_plan *P, cudaStream_t s);
 int enqueue_matvec(bem_plan *P, int op, int green, double k, cudaStream_t s);
 int set_slots(bem_plan *P, const void *x, void *y, cudaStream_t s);
+// Work buffers of one product: quadrature strengths, moments, locals (float32
+// or float64 with the plan's precision, complex pairs for Helmholtz) and the
+// float64 regular far + near sums.
+struct WorkBufs {
+    void *f, *M, *L;
+    double *ytmp;
+};
 int enqueue_matvec_raw(bem_plan *P, int op, int green, double k, int with_diag, cudaStream_t s,
-                       cudaEvent_t *ev = nullptr);
+                       cudaEvent_t *ev = nullptr, const WorkBufs *wb = nullptr);
 int solve(bem_plan *P, const void *chi, void *phi, int nrhs, const bem_solve_params *sp,
           bem_solve_info *info, cudaStream_t s);
 int64_t mesh_chi_index(const double *nodes, int64_t nn, const int32_t *elems, int64_t ne, int npe,

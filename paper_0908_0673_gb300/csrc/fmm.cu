@@ -1034,7 +1034,8 @@ int alloc_fmm(bem_plan *P, cudaStream_t s) {
 // ev (optional, BEM_NSTAGES + 1 events): recorded before the first stage and
 // after every stage, for per-stage timing outside graphs.
 template <class R, int C>
-static int run_fmm(bem_plan *P, int op, double kwave, R *f, R *M, R *L, cudaStream_t s, cudaEvent_t *ev) {
+static int run_fmm(bem_plan *P, int op, double kwave, R *f, R *M, R *L, double *ytmp, cudaStream_t s,
+                   cudaEvent_t *ev) {
     if (ev) BEM_CUDA(cudaEventRecord(ev[0], s));
     const Tabs tb = tabs_of(P);
     const TreeView tv = view_of(P);
@@ -1063,12 +1064,12 @@ static int run_fmm(bem_plan *P, int op, double kwave, R *f, R *M, R *L, cudaStre
         const int ni = P->near_nitems[C - 1];
         const int2 *it = P->near_items[C - 1];
         if (ni > 0) {
-            if (op == BEM_OP_A) (k_near_f32<C, true><<<ni, NF2_T, tile_sm, s>>>(ni, it, tb, tv, qv, kwave, f, L, P->ytmp, sk), ::bem::count_launch());
-            else (k_near_f32<C, false><<<ni, NF2_T, tile_sm, s>>>(ni, it, tb, tv, qv, kwave, f, L, P->ytmp, sk), ::bem::count_launch());
+            if (op == BEM_OP_A) (k_near_f32<C, true><<<ni, NF2_T, tile_sm, s>>>(ni, it, tb, tv, qv, kwave, f, L, ytmp, sk), ::bem::count_launch());
+            else (k_near_f32<C, false><<<ni, NF2_T, tile_sm, s>>>(ni, it, tb, tv, qv, kwave, f, L, ytmp, sk), ::bem::count_launch());
         }
     } else {
-        if (op == BEM_OP_A) (k_near<R, C, true><<<t.nleaf, NF_T, 0, s>>>(t.nleaf, tb, tv, qv, kwave, f, L, P->ytmp, sk), ::bem::count_launch());
-        else (k_near<R, C, false><<<t.nleaf, NF_T, 0, s>>>(t.nleaf, tb, tv, qv, kwave, f, L, P->ytmp, sk), ::bem::count_launch());
+        if (op == BEM_OP_A) (k_near<R, C, true><<<t.nleaf, NF_T, 0, s>>>(t.nleaf, tb, tv, qv, kwave, f, L, ytmp, sk), ::bem::count_launch());
+        else (k_near<R, C, false><<<t.nleaf, NF_T, 0, s>>>(t.nleaf, tb, tv, qv, kwave, f, L, ytmp, sk), ::bem::count_launch());
     }
     BEM_LAUNCH_CHECK();
     if (ev) BEM_CUDA(cudaEventRecord(ev[6], s));
@@ -1114,40 +1115,48 @@ int field_moments(bem_plan *P, const void *phi, const void *chi, cudaStream_t s)
 
 // Enqueues one product on stream s.  The input and output vectors are read
 // from the device slots P->xptr[0] / P->yptr[0].  with_diag = 0 leaves the
-// regular far + near sums in P->ytmp (used for the diagonal).
+// regular far + near sums in the regular-sum buffer (used for the diagonal).
+// wb (optional) names the work buffers of this product; NULL = the plan's.
 int enqueue_matvec_raw(bem_plan *P, int op, int green, double kwave, int with_diag, cudaStream_t s,
-                       cudaEvent_t *ev) {
+                       cudaEvent_t *ev, const WorkBufs *wb) {
     const int C = green == BEM_HELMHOLTZ ? 2 : 1;
     const bool mx = P->prm.precision == BEM_MIXED;
+    WorkBufs w;
+    if (wb) w = *wb;
+    else if (mx) w = WorkBufs{P->ff, P->fM, P->fL, P->ytmp};
+    else w = WorkBufs{P->f, P->M, P->L, P->ytmp};
     if (!mx) {
-        if (C == 1) BEM_TRY((run_fmm<double, 1>(P, op, kwave, P->f, P->M, P->L, s, ev)));
-        else BEM_TRY((run_fmm<double, 2>(P, op, kwave, P->f, P->M, P->L, s, ev)));
+        double *f = (double *)w.f, *M = (double *)w.M, *L = (double *)w.L;
+        if (C == 1) BEM_TRY((run_fmm<double, 1>(P, op, kwave, f, M, L, w.ytmp, s, ev)));
+        else BEM_TRY((run_fmm<double, 2>(P, op, kwave, f, M, L, w.ytmp, s, ev)));
     } else {
-        if (C == 1) BEM_TRY((run_fmm<float, 1>(P, op, kwave, P->ff, P->fM, P->fL, s, ev)));
-        else BEM_TRY((run_fmm<float, 2>(P, op, kwave, P->ff, P->fM, P->fL, s, ev)));
+        float *f = (float *)w.f, *M = (float *)w.M, *L = (float *)w.L;
+        if (C == 1) BEM_TRY((run_fmm<float, 1>(P, op, kwave, f, M, L, w.ytmp, s, ev)));
+        else BEM_TRY((run_fmm<float, 2>(P, op, kwave, f, M, L, w.ytmp, s, ev)));
     }
     if (!with_diag) return BEM_OK;
+    double *const ytmp = w.ytmp;
     const int N = (int)P->N;
     const Correction &K = P->corr;
     const int blocks = (N * 32 + 255) / 256;
 #define BEM_COMBINE(RV, VD, VS)                                                                                 \
     if (op == BEM_OP_A) {                                                                                       \
-        if (C == 1) (k_combine<RV, 1, true><<<blocks, 256, 0, s>>>(N, K.ptrD, K.colD, VD, P->C, P->ytmp, P->xptr, P->yptr, P->skip), ::bem::count_launch()); \
-        else (k_combine<RV, 2, true><<<blocks, 256, 0, s>>>(N, K.ptrD, K.colD, VD, P->C, P->ytmp, P->xptr, P->yptr, P->skip), ::bem::count_launch());       \
+        if (C == 1) (k_combine<RV, 1, true><<<blocks, 256, 0, s>>>(N, K.ptrD, K.colD, VD, P->C, ytmp, P->xptr, P->yptr, P->skip), ::bem::count_launch()); \
+        else (k_combine<RV, 2, true><<<blocks, 256, 0, s>>>(N, K.ptrD, K.colD, VD, P->C, ytmp, P->xptr, P->yptr, P->skip), ::bem::count_launch());       \
     } else {                                                                                                    \
-        if (C == 1) (k_combine<RV, 1, false><<<blocks, 256, 0, s>>>(N, K.ptrS, K.colS, VS, P->C, P->ytmp, P->xptr, P->yptr, P->skip), ::bem::count_launch()); \
-        else (k_combine<RV, 2, false><<<blocks, 256, 0, s>>>(N, K.ptrS, K.colS, VS, P->C, P->ytmp, P->xptr, P->yptr, P->skip), ::bem::count_launch());       \
+        if (C == 1) (k_combine<RV, 1, false><<<blocks, 256, 0, s>>>(N, K.ptrS, K.colS, VS, P->C, ytmp, P->xptr, P->yptr, P->skip), ::bem::count_launch()); \
+        else (k_combine<RV, 2, false><<<blocks, 256, 0, s>>>(N, K.ptrS, K.colS, VS, P->C, ytmp, P->xptr, P->yptr, P->skip), ::bem::count_launch());       \
     }
     if (mx) {
         const int64_t nx = (int64_t)(op == BEM_OP_A ? N : P->nchi) * C;
         (k_x_float<<<(int)std::min<int64_t>((nx + 255) / 256, 4096), 256, 0, s>>>(nx, P->xptr, P->xf, P->skip),
          ::bem::count_launch());
         if (op == BEM_OP_A) {
-            if (C == 1) (k_combine_f<1, true><<<blocks, 256, 0, s>>>(N, K.ptrD, K.colD, K.fvalD, P->xf, P->C, P->ytmp, P->xptr, P->yptr, P->skip), ::bem::count_launch());
-            else (k_combine_f<2, true><<<blocks, 256, 0, s>>>(N, K.ptrD, K.colD, K.fvalD, P->xf, P->C, P->ytmp, P->xptr, P->yptr, P->skip), ::bem::count_launch());
+            if (C == 1) (k_combine_f<1, true><<<blocks, 256, 0, s>>>(N, K.ptrD, K.colD, K.fvalD, P->xf, P->C, ytmp, P->xptr, P->yptr, P->skip), ::bem::count_launch());
+            else (k_combine_f<2, true><<<blocks, 256, 0, s>>>(N, K.ptrD, K.colD, K.fvalD, P->xf, P->C, ytmp, P->xptr, P->yptr, P->skip), ::bem::count_launch());
         } else {
-            if (C == 1) (k_combine_f<1, false><<<blocks, 256, 0, s>>>(N, K.ptrS, K.colS, K.fvalS, P->xf, P->C, P->ytmp, P->xptr, P->yptr, P->skip), ::bem::count_launch());
-            else (k_combine_f<2, false><<<blocks, 256, 0, s>>>(N, K.ptrS, K.colS, K.fvalS, P->xf, P->C, P->ytmp, P->xptr, P->yptr, P->skip), ::bem::count_launch());
+            if (C == 1) (k_combine_f<1, false><<<blocks, 256, 0, s>>>(N, K.ptrS, K.colS, K.fvalS, P->xf, P->C, ytmp, P->xptr, P->yptr, P->skip), ::bem::count_launch());
+            else (k_combine_f<2, false><<<blocks, 256, 0, s>>>(N, K.ptrS, K.colS, K.fvalS, P->xf, P->C, ytmp, P->xptr, P->yptr, P->skip), ::bem::count_launch());
         }
     } else {
         BEM_COMBINE(double, K.valD, K.valS)
@@ -1262,7 +1271,9 @@ void free_fmm(bem_plan *P) {
 // bem_matvec_noalloc.  It launches the same kernels as bem_matvec, directly
 // (no graph is instantiated), and keeps the per-product scratch (quadrature
 // strengths, moments, local expansions, regular sums) in the file-scope array
-// below instead of the plan's own buffers.  The array is NOALLOC_BYTES long
+// below instead of the plan's own buffers: the array's pieces go to the
+// launches as arguments (WorkBufs), and no field of the plan is changed, so
+// other host threads see the plan as it was.  The array is NOALLOC_BYTES long
 // and every GPU that loads this library holds it until the process exits.
 // Its device address is looked up once per device, on the first call made
 // on that device (so that first call should come before any stream capture).
@@ -1296,39 +1307,31 @@ extern "C" int bem_matvec_noalloc(bem_plan *P, int op, const void *x_dev, void *
                   need, NOALLOC_BYTES);
         return BEM_EINVAL;
     }
+    int prev_dev = -1;
+    BEM_CUDA(cudaGetDevice(&prev_dev));
     BEM_CUDA(cudaSetDevice(P->device));
+    int rc = BEM_OK;
     if (!g_noalloc_addr[P->device]) {
         void *ptr = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)", __FILE__, __LINE__);
-        g_noalloc_addr[P->device] = ptr;
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)", __FILE__, __LINE__);
+        else g_noalloc_addr[P->device] = ptr;
     }
-    unsigned char *base = (unsigned char *)g_noalloc_addr[P->device];
-    cudaStream_t s = (cudaStream_t)cuda_stream;
-    // point the plan's work buffers at the scratch for this one enqueue; the
-    // kernels take the pointers by value, so the plan's own are restored at once
-    double *keep_f = P->f, *keep_M = P->M, *keep_L = P->L, *keep_y = P->ytmp;
-    float *keep_ff = P->ff, *keep_fM = P->fM, *keep_fL = P->fL;
-    if (mx) {
-        P->ff = (float *)base;
-        P->fM = (float *)(base + bf);
-        P->fL = (float *)(base + bf + bm);
-    } else {
-        P->f = (double *)base;
-        P->M = (double *)(base + bf);
-        P->L = (double *)(base + bf + bm);
-    }
-    P->ytmp = (double *)(base + bf + 2 * bm);
-    int rc = set_slots(P, x_dev, y_dev, s);
     if (rc == BEM_OK) {
-        cudaError_t e = cudaMemsetAsync(P->skip, 0, sizeof(int), s);
-        rc = e == cudaSuccess ? BEM_OK : cuda_fail(e, "cudaMemsetAsync", __FILE__, __LINE__);
+        // this product's work buffers are carved from the scratch and passed to
+        // the launches as arguments; the plan's own fields are not touched
+        unsigned char *base = (unsigned char *)g_noalloc_addr[P->device];
+        const WorkBufs w{base, base + bf, base + bf + bm, (double *)(base + bf + 2 * bm)};
+        cudaStream_t s = (cudaStream_t)cuda_stream;
+        rc = set_slots(P, x_dev, y_dev, s);
+        if (rc == BEM_OK) {
+            cudaError_t e = cudaMemsetAsync(P->skip, 0, sizeof(int), s);
+            rc = e == cudaSuccess ? BEM_OK : cuda_fail(e, "cudaMemsetAsync", __FILE__, __LINE__);
+        }
+        if (rc == BEM_OK) rc = enqueue_matvec_raw(P, op, P->green, P->k, 1, s, nullptr, &w);
     }
-    if (rc == BEM_OK) rc = enqueue_matvec_raw(P, op, P->green, P->k, 1, s, nullptr);
-    P->f = keep_f; P->M = keep_M; P->L = keep_L; P->ytmp = keep_y;
-    P->ff = keep_ff; P->fM = keep_fM; P->fL = keep_fL;
+    cudaSetDevice(prev_dev);
     return rc;
 }
 
-namespace bem {
-}  // namespace bem
+

@@ -68,3 +68,31 @@ def test_mesh_create_rejects_bad_input():
     deg[0, 2] = deg[0, 1]
     with pytest.raises(bem.BemError):
         bem.bem_mesh_create(None, m.nodes, deg, bem.BEM_TRI3)
+
+
+def test_solve_stop_rule():
+    """The host decision after a true residual, without a GPU: a mixed solve
+    whose restart cycle fails to halve the residual stops, as converged only
+    within the stall floor 1e-6 (the second-kind equation's condition number of
+    order 10 keeps the solution within the 1e-5 bar there); above it the status
+    is BEM_ENOCONV.  float64 solves never take the stall exit."""
+    rule = bem.bem_solve_stop_rule
+    F, M = bem.BEM_F64, bem.BEM_MIXED
+    ok, enc = bem.BEM_OK, bem.BEM_ENOCONV
+    # tolerance reached
+    assert rule(F, 1e-10, 1, 5e-11, 2.0, 3, 100) == (True, ok)
+    assert rule(M, 1e-10, 1, 4e-8, 2.0, 3, 100) == (True, ok)       # mixed target max(tol, 5e-8)
+    assert rule(F, 1e-10, 1, 4e-8, 2.0, 3, 100) == (False, None)
+    # stall of a mixed solve: converged near the float32 floor, not above 1e-6
+    assert rule(M, 1e-10, 2, 8e-8, 1e-7, 40, 100) == (True, ok)
+    assert rule(M, 1e-10, 2, 9e-7, 1.0e-6, 40, 100) == (True, ok)
+    assert rule(M, 1e-10, 2, 1e-3, 1.5e-3, 40, 100) == (True, enc)
+    assert rule(M, 1e-10, 3, 2e-6, 3e-6, 40, 100) == (True, enc)
+    assert rule(M, 1e-4, 2, 5e-5, 6e-5, 40, 100) == (True, ok)      # a loose tol raises the floor
+    # halving, or the first residual, is no stall
+    assert rule(M, 1e-10, 2, 1e-3, 2.1e-3, 40, 100) == (False, None)
+    assert rule(M, 1e-10, 1, 1e-3, 2.0, 0, 100) == (False, None)
+    # float64: no stall exit, only the step budget
+    assert rule(F, 1e-10, 2, 1e-3, 1.5e-3, 40, 100) == (False, None)
+    assert rule(F, 1e-10, 2, 1e-3, 1.5e-3, 100, 100) == (True, enc)
+    assert rule(M, 1e-10, 2, 1e-3, 3e-3, 100, 100) == (True, enc)
