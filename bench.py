@@ -56,15 +56,14 @@ NCU_TRAFFIC = {
 
 def tc_issued_macs(p):
     """MACs the tensor-core M2L issues per interaction pair and split term:
-    rows in 16-row bands, each band's K extent the columns its lowest-degree
-    row needs (the kernel's tiling of the |a| + |b| <= p triangle)."""
+    one MMA per K-step of 8 columns a, over the rows b that step reaches (the
+    first cum(p - min|a| + 1) rows in degree order, rounded up to 16)."""
     deg = [d for d in range(p + 1) for _ in range((d + 1) * (d + 2) // 2)]
     cum = lambda d: d * (d + 1) * (d + 2) // 6 if d > 0 else 0
-    ncols = (len(deg) + 15) // 16 * 16
     total = 0
-    for b0 in range(0, ncols, 16):
-        K = max([8] + [cum(p - deg[b] + 1) for b in range(b0, min(b0 + 16, len(deg)))])
-        total += 16 * ((K + 7) // 8 * 8)
+    for j in range((len(deg) + 7) // 8):
+        dmin = min(deg[8 * j:8 * j + 8])
+        total += 8 * ((cum(p - dmin + 1) + 15) // 16 * 16)
     return total
 
 
@@ -613,7 +612,7 @@ def main():
         t = stages["m2l"] * 1e-3
         alg = st["n_inter"] * 2.0 * math.comb(10 + 6, 6) / t / 1e12
         issued = st["n_inter"] * 3 * 2.0 * tc_issued_macs(10) / t / 1e12
-        m2l_tensor = {"kernel": "k_m2l_tc + k_m2l_gather_sym (tcgen05 kind::tf32, hi/lo split, 3 products)",
+        m2l_tensor = {"kernel": "k_m2l_permute + k_m2l_tc + k_m2l_gather_sym (tcgen05 kind::tf32, hi/lo split, 3 products)",
                       "bound": "tensor", "unit": "TFLOP/s", "peak": tf32,
                       "peak_source": "TF32 = 0.5 x measured BF16 (MEASURED_PEAKS.json, nominal ratio)",
                       "achieved_algorithmic": alg, "frac_algorithmic": alg / tf32,

@@ -84,13 +84,14 @@ struct MIndex {
     void init(int p_);
 };
 
-// Degree bands of the tensor-core M2L class matrix (m2l_tc.cu): band q holds
-// rows b0[q] .. b0[q] + n[q] - 1 (n a multiple of 16) with K extent k[q] (a
-// multiple of 8), stored from float offset off[q] of the matrix in shared memory.
-constexpr int TC_MAXG = 16;
-struct TcGroups {
-    int ng = 0, tsize = 0, ncols = 0;
-    int b0[TC_MAXG], n[TC_MAXG], k[TC_MAXG], off[TC_MAXG];
+// Class-matrix image of the tensor-core M2L (m2l_tc.cu): one block per K-step
+// of 8 columns alpha, holding the rows beta that K-step reaches (a prefix of
+// the degree-ordered rows, a multiple of 16): block j starts at float ks_off[j]
+// of an image plane and has ks_n[j] rows.
+constexpr int TC_MAXKS = 64;
+struct TcPlan {
+    int nks = 0, img_floats = 0;        // K-steps; floats of one image plane (tf32 hi or lo)
+    int ks_off[TC_MAXKS], ks_n[TC_MAXKS];
 };
 
 // Tree and plan state (everything device-resident unless named h_*).
@@ -190,15 +191,15 @@ struct FmmState {
     double *sy_D = nullptr;             // [class][np][C] derivative tables
     float *sy_fD = nullptr;
     unsigned short *sy_fwd = nullptr;   // [48][np] signed index maps (sign in bit 15)
+    unsigned short *sy_fwdq = nullptr;  // [6][np] index maps of the axis permutations (tensor-core form)
+    unsigned *sy_sgn = nullptr;         // [48][ldp / 32] sign bits of the canonical-frame moments (tensor-core form)
+    float *sy_Mq = nullptr;             // [box][6][ldp] moments under each axis permutation, per product (tensor-core form)
     int *sy_inv = nullptr;              // [48][np] signed index maps (sign in bit 31)
     int *sy_mexp = nullptr;             // [np] exponents m | n << 8 | k << 16 | degree << 24
     double *sy_invf = nullptr;          // [np] 1 / a!
-    int *sy_tidx = nullptr;             // class-matrix gather table (shared-memory layout)
-    float *sy_tfac = nullptr;
+    float *sy_img = nullptr;            // [class][hi, lo][image floats] class-matrix images (tensor-core form)
     void *sy_Lp = nullptr;              // [pair][sy_ldp][C] canonical-frame local contributions
-    uint4 *sy_sched = nullptr;          // MMA schedule of a tile
-    int *sy_sched_ptr = nullptr, sy_nsched = 0;
-    bem::TcGroups sy_g;
+    bem::TcPlan sy_g;
     float *p2m_W = nullptr;             // [Q][np] stored double-layer P2M weights (float32 plans)
     float *xf = nullptr;                // float32 copy of a product's input (correction product)
     std::vector<int> lev_p;             // expansion order of each tree level

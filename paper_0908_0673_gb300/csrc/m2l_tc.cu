@@ -14,16 +14,20 @@
 // Contraction.  For a tile of up to 128 pairs of one canonical class the
 // product is a dense GEMM  D[pair][b] = sum_a Mom[pair][a] T[b][a]  with
 // T[b][a] = Dhat[a + b] / b! (zero where |a| + |b| > p), issued as tcgen05
-// kind::tf32 MMAs: M = 128 pairs (TMEM lanes), N = rows b in degree bands
-// whose K extent (the largest number of columns a any row of the band needs)
-// shrinks with the degree, so most of the zero triangle is skipped.  Each
-// float32 operand is split into tf32 hi + lo and the product accumulated as
-// hi*hi + hi*lo + lo*hi in float32 (about 2^-21 relative per product).  The
-// moments are gathered, sign-permuted and scaled into shared memory in K
-// chunks of 32 (double-buffered against the MMAs); the class matrix is built
-// in shared memory once per run of tiles of one class.  Each pair's row of
-// Lhat is written out; a gather kernel sums every target's rows in list
-// order, undoing the permutation: deterministic, no atomics.
+// kind::tf32 MMAs: M = 128 pairs (TMEM lanes), K = 8 columns a per MMA, and N
+// = the rows b that K-step reaches (|b| <= p - min |a| of the step: a prefix of
+// the degree-ordered rows), so the zero triangle is mostly skipped with one
+// MMA per K-step (two when N exceeds 256).  Each float32 operand is split into
+// tf32 hi + lo and the product accumulated as hi*hi + hi*lo + lo*hi in float32
+// (about 2^-21 relative per product).  The class matrices are built once per
+// plan as shared-memory images (one block per K-step) and brought in by one
+// bulk copy when the class changes.  The moments are gathered, permuted and
+// sign-flipped by 11 producer warps through 4-byte cp.async copies into a
+// three-stage ring of 32-column K chunks, converted to hi/lo in place by the
+// thread that copied them; one thread of a fifth warp issues the MMAs, four
+// warps read the accumulator back.  Each pair's row of Lhat is written out; a
+// gather kernel sums every target's rows in list order, undoing the
+// permutation: deterministic, no atomics.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -37,35 +41,31 @@ namespace {
 
 constexpr int TC_T = 512;           // threads per block (16 warps)
 constexpr int TC_M = 128;           // pairs per tile (MMA M, TMEM lanes)
-constexpr int TC_KC = 32;           // K chunk of the moment operand
-constexpr int TC_MOM_BYTES = TC_M * TC_KC * 4;   // one tf32 plane of a chunk
-constexpr int TC_PAD = 1024;        // slack after the last operand
-constexpr int TC_MAXE = 192;        // MMA schedule entries
+constexpr int TC_KC = 32;           // K chunk of the moment operand (4 K-steps of 8)
+constexpr int TC_NS = 3;            // moment chunks in flight
+constexpr int TC_PLANE = TC_M * TC_KC * 4;       // one tf32 plane of a chunk
+constexpr int TC_EPI = 4;           // epilogue warps 0-3 (TMEM lane quadrants)
+constexpr int TC_MMA_WARP = 4;      // one thread of warp 4 issues the MMAs
+constexpr int TC_PROD0 = 5;         // producer warps 5-15
+constexpr int TC_NPROD = TC_T / 32 - TC_PROD0;
 constexpr long long TC_WAIT = 4000000000ll;      // clock cycles before a wait gives up
-constexpr int TC_SMEM_MAX = 220 * 1024;
+constexpr int TC_SMEM_MAX = 227 * 1024;
 
 // the six axis permutations; PERMS[q][i] = canonical position of axis i
 constexpr int PERMS[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
 
 struct TcArgs {
-    TcGroups g;
-    int np, ntile, nkc, nsched;
+    TcPlan g;
+    int np, ldp, ntile, nkc;
     const int *tile_cls, *tile_start, *tile_cnt;
     const int *src, *sig, *pair;
-    const int *dl, *tidx;
-    const unsigned short *fwd;
-    const float *tfac, *fD, *M;
-    const uint4 *sched;                 // MMA schedule: {T offset, sbo, idesc, dcol | ks << 16 | acc << 31}
-    const int *sched_ptr;               // [nkc + 1] schedule entries of each chunk
+    const float *img;                   // [class][hi, lo][g.img_floats]
+    const unsigned *sgn;                // [48][ldp / 32] sign bit of every canonical-frame moment
+    const float *Mq;                    // [box][6][ldp] moments permuted by each axis permutation
     float *Lp;                          // rows of this run's pairs, row u - u0
-    int ldp, u0;
+    int u0;
     int *err;
     const int *skip;
-};
-
-struct SchedEntry {                     // one tf32 MMA triple, descriptors resolved in shared memory
-    uint64_t bh, bl;
-    uint32_t idesc, meta;
 };
 
 __device__ __forceinline__ uint32_t mom_off(int r, int k) {   // byte offset in a chunk plane
@@ -73,17 +73,19 @@ __device__ __forceinline__ uint32_t mom_off(int r, int k) {   // byte offset in 
 }
 
 // shared-memory layout of the tensor-core M2L block
+constexpr int TC_XLD = 36;              // row stride (floats) of the epilogue's transpose buffer
+constexpr int TC_XPOSE = 32 * TC_XLD;   // floats of one epilogue warp's transpose buffer
 struct TcLayout {
-    size_t mom, fwd, d, sched, bars, total;
+    size_t img, stage, sgn, xpose, bars, total;
 };
-__host__ __device__ inline TcLayout tc_layout(const TcGroups &g, int ldp) {
+__host__ __device__ inline TcLayout tc_layout(const TcPlan &g, int ldp) {
     TcLayout L;
-    L.mom = ((2 * (size_t)g.tsize * 4 + 1023) / 1024) * 1024;
-    L.fwd = L.mom + 4 * (size_t)TC_MOM_BYTES;
-    L.d = L.fwd + ((48 * (size_t)ldp * 2 + 15) / 16) * 16;
-    L.sched = L.d + (size_t)ldp * 4;
-    L.bars = L.sched + (size_t)TC_MAXE * sizeof(SchedEntry);
-    L.total = L.bars + 8 * 8 + 16 + TC_PAD;
+    L.img = 0;
+    L.stage = ((2 * (size_t)g.img_floats * 4 + 1023) / 1024) * 1024;
+    L.sgn = L.stage + (size_t)TC_NS * 2 * TC_PLANE;
+    L.xpose = L.sgn + ((48 * (size_t)(ldp / 32) * 4 + 15) / 16) * 16;
+    L.bars = L.xpose + (size_t)TC_EPI * TC_XPOSE * 4;
+    L.total = L.bars + 16 * 8 + 16 + 1024;
     return L;
 }
 
@@ -103,111 +105,93 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
 }
 
-// Roles: warp 0 lane 0 issues the MMAs; warps 0-3 read the accumulator back
-// (warp w owns TMEM lanes 32 w .. 32 w + 31, i.e. pairs); warps 4-15 gather
-// the moments into the two chunk buffers and rebuild the class matrix when
-// the class changes.  Handshakes: full[b] (12 producer warps) -> MMA;
-// empty[b] (MMA commit) -> producers; tfull (commit after a tile's last
-// chunk) -> epilogue and producers; tempty (4 epilogue warps) -> MMA.
+// Roles: warps 0-3 read the accumulator back (warp w owns TMEM lanes
+// 32 w .. 32 w + 31, i.e. pairs); warp 4 lane 0 loads the class image and
+// issues the MMAs; warps 5-15 gather the moments into the chunk ring.
+// Handshakes: full[s] (11 producer warps) -> MMA; empty[s] (MMA commit) ->
+// producers; tfull (commit after a tile's last chunk) -> epilogue; tempty
+// (4 epilogue warps) -> MMA; bfull (bulk copy of a class image) -> MMA.
 __global__ void __launch_bounds__(TC_T, 1) k_m2l_tc(const __grid_constant__ TcArgs a) {
     if (a.skip && *a.skip) return;
     extern __shared__ __align__(1024) unsigned char smem[];
-    const TcGroups &G = a.g;
+    const TcPlan &G = a.g;
     const TcLayout LY = tc_layout(G, a.ldp);
-    const int np = a.np, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    float *sTh = (float *)smem, *sTl = sTh + G.tsize;                 // class matrix, tf32 hi / lo
-    unsigned char *sMom = smem + LY.mom;                                // [2 buffers][hi, lo] chunk planes
-    unsigned short *sFwd = (unsigned short *)(smem + LY.fwd);          // [48][ldp] signed index maps
-    SchedEntry *sSched = (SchedEntry *)(smem + LY.sched);
-    uint64_t *full = (uint64_t *)(smem + LY.bars), *empty = full + 2, *tfull = full + 4, *tempty = full + 5,
-             *fin = full + 6;
-    uint32_t *sTmem = (uint32_t *)(full + 8);
+    const int ldp = a.ldp, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    float *sImg = (float *)(smem + LY.img);                             // class image: hi plane, lo plane
+    unsigned char *sStage = smem + LY.stage;                            // [TC_NS][hi, lo] chunk planes
+    unsigned *sSgn = (unsigned *)(smem + LY.sgn);                       // [48][ldp / 32]
+    float *sX = (float *)(smem + LY.xpose);                             // [TC_EPI][32][33]
+    uint64_t *full = (uint64_t *)(smem + LY.bars), *empty = full + TC_NS, *tfull = full + 2 * TC_NS,
+             *tempty = tfull + 1, *bfull = tfull + 2, *fin = tfull + 3;
+    uint32_t *sTmem = (uint32_t *)(fin + 1);
     volatile int *sAbort = (volatile int *)(sTmem + 1);
+    const int nw = ldp / 32;
 
     if (tid == 0) {
-        tc::mbar_init(&full[0], 12);
-        tc::mbar_init(&full[1], 12);
-        tc::mbar_init(&empty[0], 1);
-        tc::mbar_init(&empty[1], 1);
+        for (int s = 0; s < TC_NS; s++) {
+            tc::mbar_init(&full[s], TC_NPROD);
+            tc::mbar_init(&empty[s], 1);
+        }
         tc::mbar_init(tfull, 1);
-        tc::mbar_init(tempty, 4);
+        tc::mbar_init(tempty, TC_EPI);
+        tc::mbar_init(bfull, 1);
         tc::mbar_init(fin, 1);
         *sAbort = 0;
         tc::mbar_fence_init();
     }
-    for (int i = tid; i < 48 * a.ldp; i += TC_T) {
-        const int sg = i / a.ldp, h = i - sg * a.ldp;
-        sFwd[i] = h < np ? a.fwd[(size_t)sg * np + h] : 0;
-    }
+    for (int i = tid; i < 48 * nw; i += TC_T) sSgn[i] = a.sgn[i];
     if (warp == 0) tc::tmem_alloc(sTmem, 512);
     tc::tc_fence_before_sync();
     __syncthreads();
     tc::tc_fence_after_sync();
     const uint32_t tmem = *sTmem;
-    {   // schedule with resolved descriptors (class matrix addresses are fixed)
-        const uint32_t th = tc::smem_u32(sTh), tl = tc::smem_u32(sTl);
-        for (int i = tid; i < a.nsched; i += TC_T) {
-            const uint4 e = a.sched[i];
-            sSched[i].bh = tc::smem_desc(th + e.x, 128, e.y);
-            sSched[i].bl = tc::smem_desc(tl + e.x, 128, e.y);
-            sSched[i].idesc = e.z;
-            sSched[i].meta = e.w;
-        }
-    }
-    __syncthreads();
 
     const int t_begin = (int)((long long)a.ntile * blockIdx.x / gridDim.x);
     const int t_end = (int)((long long)a.ntile * (blockIdx.x + 1) / gridDim.x);
+    bool bulk_pending = false;                        // MMA thread: a class image copy not yet observed complete
+    uint32_t nbulk = 0;
 
-    if (warp < 4) {
-        // ---- MMA issue (warp 0 lane 0) and accumulator read-back (warps 0-3) ----
-        int it = 0;                                       // running chunk counter
+    if (warp < TC_EPI) {
+        // ---- accumulator read-back: TMEM lane 32 w + lane = pair row ----
+        const uint64_t pol = tc::policy_evict_last();    // the gather reads these rows next
+        const int r = 32 * warp + lane;
         for (int tile = t_begin; tile < t_end; tile++) {
             const int k = tile - t_begin;
-            if (warp == 0) {
-                bool ok = true;
-                if (lane == 0) {
-                    if (k > 0) ok = wait_or_abort(tempty, (uint32_t)((k - 1) & 1), sAbort);
-                    tc::tc_fence_after_sync();
-                    const uint32_t mb = tc::smem_u32(sMom);
-                    for (int kc = 0; kc < a.nkc && ok; kc++, it++) {
-                        const int b = it & 1;
-                        ok = wait_or_abort(&full[b], (uint32_t)((it >> 1) & 1), sAbort);
-                        if (!ok) break;
-                        tc::tc_fence_after_sync();
-                        const uint64_t ah0 = tc::smem_desc(mb + (uint32_t)b * 2 * TC_MOM_BYTES, 128, 1024);
-                        const uint64_t al0 = tc::smem_desc(mb + (uint32_t)b * 2 * TC_MOM_BYTES + TC_MOM_BYTES, 128, 1024);
-                        for (int e = a.sched_ptr[kc]; e < a.sched_ptr[kc + 1]; e++) {
-                            const SchedEntry &S = sSched[e];
-                            const uint32_t d = tmem + (S.meta & 0xffffu);
-                            const uint64_t ks16 = (uint64_t)((S.meta >> 16) & 3u) * 16u;   // 256 B steps
-                            const bool acc = (S.meta >> 31) != 0;
-                            tc::mma_tf32(d, ah0 + ks16, S.bh, S.idesc, acc);
-                            tc::mma_tf32(d, ah0 + ks16, S.bl, S.idesc, true);
-                            tc::mma_tf32(d, al0 + ks16, S.bh, S.idesc, true);
-                        }
-                        tc::mma_commit(&empty[b]);
-                    }
-                    if (ok) tc::mma_commit(tfull);
-                }
-                __syncwarp();
-            }
-            // read-back of this tile's accumulator
+            const int cnt = a.tile_cnt[tile];
+            const int u = r < cnt ? a.pair[a.tile_start[tile] + r] : -1;
             bool ok = wait_or_abort(tfull, (uint32_t)(k & 1), sAbort);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) break;
             tc::tc_fence_after_sync();
-            const int r = 32 * warp + lane;
-            const int cnt = a.tile_cnt[tile];
-            const int u = r < cnt ? a.pair[a.tile_start[tile] + r] : -1;
-            const int nch = G.ncols / 32;
-            for (int c = 0; c < nch; c++) {
-                float v[32];
-                tc::tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * c), v);
-                if (u >= 0) {
-                    float4 *dst = (float4 *)(a.Lp + (size_t)(u - a.u0) * a.ldp + 32 * c);
+            // 32 x 32 blocks through shared memory: lane l holds row l after
+            // the TMEM load; after the transpose a store of 32 lanes writes 16
+            // bytes each, 128 contiguous bytes of four rows
+            float *xb = sX + warp * TC_XPOSE;
+            const int ur = u >= 0 ? u - a.u0 : -1;
+            const int rq = lane >> 3, cg = lane & 7;
+            const uint32_t base = tmem + ((uint32_t)(32 * warp) << 16);
+            for (int c = 0; c < ldp; c += 64) {
+                uint32_t v0[32], v1[32];
+                tc::tmem_ld32_nowait(base + (uint32_t)c, v0);
+                if (c + 32 < ldp) tc::tmem_ld32_nowait(base + (uint32_t)(c + 32), v1);
+                tc::tmem_wait_ld2(v0, v1);
+                for (int h = 0; h < 2 && c + 32 * h < ldp; h++) {
+                    __syncwarp();
 #pragma unroll
-                    for (int i = 0; i < 8; i++) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                    for (int k = 0; k < 8; k++) {
+                        const uint32_t *v = h ? v1 : v0;
+                        *(float4 *)(xb + lane * TC_XLD + 4 * k) = make_float4(
+                            __uint_as_float(v[4 * k]), __uint_as_float(v[4 * k + 1]), __uint_as_float(v[4 * k + 2]),
+                            __uint_as_float(v[4 * k + 3]));
+                    }
+                    __syncwarp();
+#pragma unroll
+                    for (int i = 0; i < 8; i++) {
+                        const int row = 4 * i + rq;
+                        const int uq = __shfl_sync(0xffffffffu, ur, row);
+                        const float4 x = *(const float4 *)(xb + row * TC_XLD + 4 * cg);
+                        if (uq >= 0) tc::st_v4_hint(a.Lp + (size_t)uq * ldp + c + 32 * h + 4 * cg, x.x, x.y, x.z, x.w, pol);
+                    }
                 }
             }
             tc::tc_fence_before_sync();
@@ -215,96 +199,153 @@ __global__ void __launch_bounds__(TC_T, 1) k_m2l_tc(const __grid_constant__ TcAr
             if (lane == 0) mbar_arrive(tempty);
             if (__any_sync(0xffffffffu, *sAbort != 0)) break;
         }
-    } else {
-        // ---- producers: warps 4-15 ----
-        const int pt = tid - 128;                         // 0 .. 383
-        constexpr int NE = (TC_M * TC_KC + 383) / 384;    // elements per thread per chunk (11)
-        int it = 0, prev_cls = -1;
-        for (int tile = t_begin; tile < t_end; tile++) {
-            const int k = tile - t_begin;
-            const int cls = a.tile_cls[tile], st = a.tile_start[tile], cnt = a.tile_cnt[tile];
-            // this thread's elements: e = pt + 384 i -> row r = 8 rg + lane / 4, column 4 kq + lane % 4
-            int srow[NE], sgo[NE], col[NE];
-#pragma unroll
-            for (int i = 0; i < NE; i++) {
-                const int e = pt + 384 * i, gi = e >> 5;
-                const int r = (gi >> 3) * 8 + (lane >> 2);
-                col[i] = (gi & 7) * 4 + (lane & 3);
-                const bool v = e < TC_M * TC_KC && r < cnt;
-                srow[i] = v ? a.src[st + r] : -1;
-                sgo[i] = v ? a.sig[st + r] * a.ldp : 0;
-            }
-            if (cls != prev_cls) {
-                // the class matrix may only change once the previous tile's MMAs
-                // are done: T[b][a] = Dhat[a+b] (-1)^|a| 2^(dl |a|) / (a! b!)
-                if (k > 0 && !__all_sync(0xffffffffu, wait_or_abort(tfull, (uint32_t)((k - 1) & 1), sAbort))) break;
-                const int dl = a.dl[cls];
-                const float *Dc = a.fD + (size_t)cls * np;
-                for (int e0 = pt; e0 < G.tsize; e0 += 4 * 384) {
-                    int gi[4];
-                    float fc[4], dv[4];
-#pragma unroll
-                    for (int q = 0; q < 4; q++) {
-                        const int e = e0 + q * 384;
-                        gi[q] = e < G.tsize ? __ldg(a.tidx + e) : -1;
-                        fc[q] = e < G.tsize ? __ldg(a.tfac + e) : 0.f;
-                    }
-#pragma unroll
-                    for (int q = 0; q < 4; q++) dv[q] = gi[q] >= 0 ? __ldg(Dc + (gi[q] & 0xffff)) : 0.f;
-#pragma unroll
-                    for (int q = 0; q < 4; q++) {
-                        const int e = e0 + q * 384;
-                        if (e < G.tsize) {
-                            const float v = gi[q] >= 0 ? ldexpf(dv[q] * fc[q], dl * (gi[q] >> 16)) : 0.f;
-                            const float hi = tc::to_tf32(v);
-                            sTh[e] = hi;
-                            sTl[e] = tc::to_tf32(v - hi);
+    } else if (warp == TC_MMA_WARP) {
+        // ---- class images and MMA issue (one thread) ----
+        if (lane == 0) {
+            const uint32_t img_bytes = (uint32_t)G.img_floats * 4u;
+            const uint32_t ih = tc::smem_u32(sImg), il = ih + img_bytes, st0 = tc::smem_u32(sStage);
+            int it = 0, cur_cls = -1;
+            bool ok = true;
+            for (int tile = t_begin; tile < t_end && ok; tile++) {
+                const int k = tile - t_begin, cls = a.tile_cls[tile];
+                // the accumulator and the image are free once the epilogue has
+                // read the previous tile (all of its MMAs have completed)
+                if (k > 0) ok = wait_or_abort(tempty, (uint32_t)((k - 1) & 1), sAbort);
+                if (!ok) break;
+                if (cls != cur_cls) {
+                    tc::mbar_arrive_expect_tx(bfull, 2u * img_bytes);
+                    tc::bulk_g2s(sImg, a.img + (size_t)cls * 2 * G.img_floats, 2u * img_bytes, bfull);
+                    bulk_pending = true;
+                    ok = wait_or_abort(bfull, nbulk & 1u, sAbort);
+                    if (!ok) break;
+                    bulk_pending = false;
+                    nbulk++;
+                    cur_cls = cls;
+                }
+                tc::tc_fence_after_sync();
+                for (int kc = 0; kc < a.nkc; kc++, it++) {
+                    const int s = it % TC_NS;
+                    ok = wait_or_abort(&full[s], (uint32_t)((it / TC_NS) & 1), sAbort);
+                    if (!ok) break;
+                    tc::tc_fence_after_sync();
+                    const uint32_t ab = st0 + (uint32_t)s * 2u * TC_PLANE;
+                    const uint64_t ah0 = tc::smem_desc(ab, 128, 1024), al0 = tc::smem_desc(ab + TC_PLANE, 128, 1024);
+                    for (int ks = 0; ks < 4; ks++) {
+                        const int j = kc * 4 + ks;
+                        if (j >= G.nks) break;
+                        const uint32_t boff = (uint32_t)G.ks_off[j] * 4u;
+                        const int n = G.ks_n[j];
+                        for (int part = 0; part < n; part += 256) {
+                            const int nn = min(256, n - part);
+                            const uint32_t po = boff + (uint32_t)(part / 8) * 256u;
+                            const uint64_t bh = tc::smem_desc(ih + po, 128, 256), bl = tc::smem_desc(il + po, 128, 256);
+                            const uint32_t id = tc::idesc_tf32(TC_M, nn), d = tmem + (uint32_t)part;
+                            const uint64_t ao = (uint64_t)ks * 16u;   // 256 B per K-step
+                            tc::mma_tf32(d, ah0 + ao, bh, id, j > 0);
+                            tc::mma_tf32(d, ah0 + ao, bl, id, true);
+                            tc::mma_tf32(d, al0 + ao, bh, id, true);
                         }
                     }
+                    tc::mma_commit(&empty[s]);
                 }
-                prev_cls = cls;
+                if (ok) tc::mma_commit(tfull);
             }
-            float raw[NE];
-            auto fetch = [&](int kc) {
+            if (bulk_pending) {
+                // a copy in flight when a wait gave up: let it land before exit
+                if (!tc::mbar_wait_bounded(bfull, nbulk & 1u, TC_WAIT)) *sAbort = 1;
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---- producers: warps 5-15, 16-byte asynchronous copies ----
+        // A chunk is 128 rows x 8 groups of 4 columns, in 32 slots of 32 lanes:
+        // slot sl holds rows 8 (sl / 2) + lane % 8 and groups 4 (sl % 2) +
+        // lane / 8 (64 contiguous bytes per row in global memory, 4 shared-
+        // memory wavefronts per slot).  This thread's slots: pw + 11 i.
+        constexpr int NI = (32 + TC_NPROD - 1) / TC_NPROD;       // 3
+        const int pw = warp - TC_PROD0;
+        size_t srow[NI];                              // Mq row of the pair (box, permutation), or ~0 if none
+        unsigned pvm = 0u;                            // items of the pending chunk that were copied
+        int it = 0;
+        bool ok = true, pend = false;
+        auto item = [&](int i, int &r, int &g) {
+            const int sl = pw + TC_NPROD * i;
+            r = (sl >> 1) * 8 + (lane & 7);
+            g = (sl & 1) * 4 + (lane >> 3);
+            return sl < 32;
+        };
+        int psig[NI];                                 // symmetry of each item of the pending chunk
+        // sign flips and hi/lo split of chunk `c` in place, zeros where nothing was copied
+        auto convert = [&](int c, unsigned vm) {
+            unsigned char *hi = sStage + (size_t)(c % TC_NS) * 2 * TC_PLANE, *lo = hi + TC_PLANE;
+            const int kc = c % a.nkc;
 #pragma unroll
-                for (int i = 0; i < NE; i++) {
-                    const int al = kc * TC_KC + col[i];
-                    float x = 0.f;
-                    if (srow[i] >= 0 && al < np) {
-                        const unsigned f = sFwd[sgo[i] + al];
-                        x = __int_as_float(__float_as_int(__ldg(a.M + (size_t)srow[i] * np + (f & 0x7fffu))) ^
-                                           (int)((f & 0x8000u) << 16));
-                    }
-                    raw[i] = x;
+            for (int i = 0; i < NI; i++) {
+                int r, g;
+                if (!item(i, r, g)) continue;
+                const uint32_t o = mom_off(r, 4 * g);
+                float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+                if ((vm >> i) & 1u) {
+                    x = *(const float4 *)(hi + o);
+                    const unsigned sb = (sSgn[psig[i] * nw + kc] >> (4 * g)) & 15u;
+                    x.x = (sb & 1u) ? -x.x : x.x;
+                    x.y = (sb & 2u) ? -x.y : x.y;
+                    x.z = (sb & 4u) ? -x.z : x.z;
+                    x.w = (sb & 8u) ? -x.w : x.w;
                 }
-            };
-            fetch(0);
-            bool ok = true;
+                float4 h, l;
+                h.x = tc::to_tf32(x.x); l.x = tc::to_tf32(x.x - h.x);
+                h.y = tc::to_tf32(x.y); l.y = tc::to_tf32(x.y - h.y);
+                h.z = tc::to_tf32(x.z); l.z = tc::to_tf32(x.z - h.z);
+                h.w = tc::to_tf32(x.w); l.w = tc::to_tf32(x.w - h.w);
+                *(float4 *)(hi + o) = h;
+                *(float4 *)(lo + o) = l;
+            }
+            tc::fence_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&full[c % TC_NS]);
+        };
+        int csig[NI];
+        for (int tile = t_begin; tile < t_end && ok; tile++) {
+            const int st = a.tile_start[tile], cnt = a.tile_cnt[tile];
+#pragma unroll
+            for (int i = 0; i < NI; i++) {
+                int r, g;
+                const bool v = item(i, r, g) && r < cnt;
+                const int sg = v ? a.sig[st + r] : 0;
+                srow[i] = v ? ((size_t)a.src[st + r] * 6 + (size_t)(sg >> 3)) * ldp : ~(size_t)0;
+                csig[i] = sg;
+            }
             for (int kc = 0; kc < a.nkc; kc++, it++) {
-                const int b = it & 1, n = it >> 1;
+                const int s = it % TC_NS, n = it / TC_NS;
                 if (n > 0) {
-                    ok = __all_sync(0xffffffffu, wait_or_abort(&empty[b], (uint32_t)((n - 1) & 1), sAbort));
+                    ok = __all_sync(0xffffffffu, wait_or_abort(&empty[s], (uint32_t)((n - 1) & 1), sAbort));
                     if (!ok) break;
                 }
-                unsigned char *hi = sMom + (size_t)b * 2 * TC_MOM_BYTES, *lo = hi + TC_MOM_BYTES;
+                unsigned char *hi = sStage + (size_t)s * 2 * TC_PLANE;
+                unsigned vm = 0u;
 #pragma unroll
-                for (int i = 0; i < NE; i++) {
-                    const int e = pt + 384 * i;
-                    if (e < TC_M * TC_KC) {
-                        const int gi = e >> 5, r = (gi >> 3) * 8 + (lane >> 2);
-                        const uint32_t o = mom_off(r, col[i]);
-                        const float h = tc::to_tf32(raw[i]);
-                        *(float *)(hi + o) = h;
-                        *(float *)(lo + o) = tc::to_tf32(raw[i] - h);
+                for (int i = 0; i < NI; i++) {
+                    int r, g;
+                    item(i, r, g);
+                    if (srow[i] != ~(size_t)0) {
+                        tc::cp_async16(hi + mom_off(r, 4 * g), a.Mq + srow[i] + kc * TC_KC + 4 * g);
+                        vm |= 1u << i;
                     }
                 }
-                if (kc + 1 < a.nkc) fetch(kc + 1);       // in flight while the chunk is consumed
-                tc::fence_async_smem();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&full[b]);
+                tc::cp_async_commit();
+                if (pend) {                               // the previous chunk has landed: convert it
+                    tc::cp_async_wait<1>();
+                    convert(it - 1, pvm);
+                }
+#pragma unroll
+                for (int i = 0; i < NI; i++) psig[i] = csig[i];
+                pvm = vm;
+                pend = true;
             }
-            if (!ok) break;
         }
+        tc::cp_async_wait<0>();
+        if (pend && ok) convert(it - 1, pvm);
     }
     // every MMA issued has completed before the accumulator is released
     __syncthreads();
@@ -317,6 +358,41 @@ __global__ void __launch_bounds__(TC_T, 1) k_m2l_tc(const __grid_constant__ TcAr
     __syncthreads();
     tc::tc_fence_after_sync();
     if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+// Class-matrix images of every canonical class: element e of a plane (in the
+// K-step block layout) is T[b][a] = Dhat[a+b] (-1)^|a| 2^(dl |a|) / (a! b!),
+// tidx[e] = index of a + b | |a| << 16 (-1 outside the triangle), tfac[e] the
+// factorial and sign factor; split into tf32 hi and lo planes.
+__global__ void k_tc_images(int img_floats, int np, const int *__restrict__ tidx, const float *__restrict__ tfac,
+                            const float *__restrict__ fD, const int *__restrict__ dl, float *__restrict__ img) {
+    const int cls = blockIdx.y;
+    float *hi = img + (size_t)cls * 2 * img_floats, *lo = hi + img_floats;
+    const float *Dc = fD + (size_t)cls * np;
+    const int d = dl[cls];
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < img_floats; e += gridDim.x * blockDim.x) {
+        const int gi = tidx[e];
+        const float v = gi >= 0 ? ldexpf(Dc[gi & 0xffff] * tfac[e], d * (gi >> 16)) : 0.f;
+        const float h = tc::to_tf32(v);
+        hi[e] = h;
+        lo[e] = tc::to_tf32(v - h);
+    }
+}
+
+// Moments of every box under each of the six axis permutations, rows of ldp
+// floats (zero beyond np): Mq[box][q][h] = M[box][a], a = h o pi_q, so that a
+// tile's producers copy contiguous row segments.
+__global__ void k_m2l_permute(int nbox, int np, int ldp, const unsigned short *__restrict__ fwdq,
+                              const float *__restrict__ M, float *__restrict__ Mq, const int *__restrict__ skip) {
+    if (skip && *skip) return;
+    const int64_t n = (int64_t)nbox * 6 * ldp;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int h = (int)(i % ldp);
+        const int64_t rq = i / ldp;
+        const int q = (int)(rq % 6);
+        const int64_t box = rq / 6;
+        Mq[i] = h < np ? M[box * np + fwdq[q * np + h]] : 0.f;
+    }
 }
 
 // L_t[b] = (1 / h_t) sum over t's interaction list, in list order, of
@@ -514,65 +590,31 @@ static int build_sym_tiles(bem_plan *P, size_t row_bytes, int64_t &max_rows) {
 // host: order-dependent tables (symmetry maps, class-matrix layout, derivative
 // tables of the canonical classes); decides whether the tensor-core form runs
 // ---------------------------------------------------------------------------
-size_t tc_smem_bytes(const TcGroups &g, int ldp) { return tc_layout(g, ldp).total; }
+size_t tc_smem_bytes(const TcPlan &g, int ldp) { return tc_layout(g, ldp).total; }
 
-// The TC tables of the current order, when the tensor-core form applies:
-// degree bands of the class matrix, its gather table in shared-memory layout
-// order, the MMA schedule.  Returns false (nothing allocated) when the order
-// does not fit the fixed band table, the schedule or shared memory.
-static bool tc_plan(const MIndex &mi, const std::vector<int> &deg, TcGroups &g, int &ldp, int &nkc,
-                    std::vector<uint4> &sched, std::vector<int> &sptr) {
+// The class-matrix image layout of the current order, when the tensor-core
+// form applies: K-step j (columns a in [8j, 8j + 8)) reaches the rows b with
+// |b| <= p - min |a| of the step, the first cum(p - min|a| + 1) rows in degree
+// order, rounded up to 16 (MMA N).  Returns false when the order does not fit
+// the K-step table, TMEM or shared memory.
+static bool tc_plan(const MIndex &mi, const std::vector<int> &deg, TcPlan &g, int &ldp, int &nkc) {
     const int p = mi.p, np = mi.np;
-    // degree bands of rows b: K extent = columns a with |a| <= p - |b|, i.e.
-    // the count of multi-indices of degree <= p - |b|
     auto cum = [](int d) { return d <= 0 ? 0 : d * (d + 1) * (d + 2) / 6; };
-    g = TcGroups{};
-    const int ncols = (np + 15) / 16 * 16;
-    std::vector<int> bk;
-    for (int b0 = 0; b0 < ncols; b0 += 16) {
-        int K = 8;
-        for (int b = b0; b < b0 + 16 && b < np; b++) K = std::max(K, cum(p - deg[b] + 1));
-        bk.push_back((K + 7) / 8 * 8);
+    g = TcPlan{};
+    g.nks = (np + 7) / 8;
+    if (g.nks > TC_MAXKS) return false;
+    int off = 0;
+    for (int j = 0; j < g.nks; j++) {
+        int dmin = p;
+        for (int al = 8 * j; al < std::min(np, 8 * j + 8); al++) dmin = std::min(dmin, deg[al]);
+        g.ks_off[j] = off;
+        g.ks_n[j] = (cum(p - dmin + 1) + 15) / 16 * 16;
+        off += g.ks_n[j] * 8;
     }
-    g.ng = 0;
-    for (size_t i = 0; i < bk.size();) {
-        size_t j = i;
-        while (j < bk.size() && bk[j] == bk[i] && (int)(j - i + 1) * 16 <= 256) j++;
-        if (g.ng >= TC_MAXG) return false;        // does not fit the fixed group table
-        g.b0[g.ng] = (int)i * 16;
-        g.n[g.ng] = (int)(j - i) * 16;
-        g.k[g.ng] = bk[i];
-        g.ng++;
-        i = j;
-    }
-    g.tsize = 0;
-    for (int q = 0; q < g.ng; q++) {
-        g.off[q] = g.tsize;
-        g.tsize += g.n[q] * g.k[q];
-    }
-    ldp = (ncols + 31) / 32 * 32;                 // TMEM columns read back, 32 at a time
-    g.ncols = ldp;
-    const int kmax = (g.k[0] + TC_KC - 1) / TC_KC * TC_KC;
-    nkc = kmax / TC_KC;
-    // MMA schedule: per chunk, every band whose K extent reaches into it,
-    // 8 columns (one tf32 MMA) at a time
-    sched.clear();
-    sptr.assign(nkc + 1, 0);
-    for (int kc = 0; kc < nkc; kc++) {
-        sptr[kc] = (int)sched.size();
-        for (int q = 0; q < g.ng; q++) {
-            const int kext = g.k[q] - kc * TC_KC;
-            for (int ks = 0; ks < std::min(4, kext / 8); ks++) {
-                const int j = kc * 4 + ks;
-                sched.push_back(make_uint4((unsigned)(g.off[q] * 4 + j * 256), (unsigned)(g.k[q] / 4 * 128),
-                                           tc::idesc_tf32(TC_M, g.n[q]),
-                                           (unsigned)g.b0[q] | ((unsigned)ks << 16) | (j > 0 ? 0x80000000u : 0u)));
-            }
-        }
-    }
-    sptr[nkc] = (int)sched.size();
-    if ((int)sched.size() > TC_MAXE) return false;
-    return tc_smem_bytes(g, ldp) <= (size_t)TC_SMEM_MAX && ldp <= 512;
+    g.img_floats = off;
+    ldp = (g.ks_n[0] + 31) / 32 * 32;             // TMEM columns read back, 32 at a time
+    nkc = (g.nks + 3) / 4;
+    return ldp <= 512 && tc_smem_bytes(g, ldp) <= (size_t)TC_SMEM_MAX;
 }
 
 // Order-dependent tables of the M2L on canonical classes: symmetry maps,
@@ -632,11 +674,9 @@ int build_sym_tables(bem_plan *P, cudaStream_t s) {
     BEM_TRY(A.alloc(&P->sy_D, std::max<size_t>(1, (size_t)ncls * np * C)));
     if (mx) BEM_TRY(A.alloc(&P->sy_fD, std::max<size_t>(1, (size_t)ncls * np * C)));
     BEM_TRY(launch_m2l_derivs(P, ncls, P->sy_rho, C == 2 ? P->sy_kh : nullptr, P->sy_D, mx ? P->sy_fD : nullptr, s));
-    TcGroups g{};
+    TcPlan g{};
     int ldp = 0, nkc = 0;
-    std::vector<uint4> sched;
-    std::vector<int> sptr;
-    const bool tc = C == 1 && mx && ncls > 0 && !P->lev_var && tc_plan(mi, deg, g, ldp, nkc, sched, sptr);
+    const bool tc = C == 1 && mx && ncls > 0 && !P->lev_var && tc_plan(mi, deg, g, ldp, nkc);
     // source and target order of every canonical class (one order unless it varies with the level;
     // the class key then holds the target level)
     {
@@ -651,26 +691,45 @@ int build_sym_tables(bem_plan *P, cudaStream_t s) {
         BEM_TRY(up(&P->sy_ord, ord));
     }
     if (tc) {
-        // class-matrix gather table in shared-memory layout order
-        std::vector<int> tidx(g.tsize, -1);
-        std::vector<float> tfac(g.tsize, 0.f);
-        for (int q = 0; q < g.ng; q++)
-            for (int bl = 0; bl < g.n[q]; bl++)
-                for (int al = 0; al < g.k[q]; al++) {
-                    const int b = g.b0[q] + bl, e = g.off[q] + (bl >> 3) * (g.k[q] / 4) * 32 + (al >> 2) * 32 +
-                                                    (bl & 7) * 4 + (al & 3);
+        // class-matrix images of every canonical class, built once: gather
+        // table (index of a + b and |a|) and factors in image layout order
+        std::vector<int> tidx(g.img_floats, -1);
+        std::vector<float> tfac(g.img_floats, 0.f);
+        for (int j = 0; j < g.nks; j++)
+            for (int b = 0; b < g.ks_n[j]; b++)
+                for (int kk = 0; kk < 8; kk++) {
+                    const int al = 8 * j + kk, e = g.ks_off[j] + (b >> 3) * 64 + (kk >> 2) * 32 + (b & 7) * 4 + (kk & 3);
                     if (b < np && al < np && deg[b] + deg[al] <= p) {
                         tidx[e] = idx(mi.m[al] + mi.m[b], mi.n[al] + mi.n[b], mi.k[al] + mi.k[b]) | (deg[al] << 16);
                         tfac[e] = (float)(((deg[al] & 1) ? -1.0 : 1.0) * invf[al] * invf[b]);
                     }
                 }
-        BEM_TRY(up(&P->sy_tidx, tidx));
-        BEM_TRY(up(&P->sy_tfac, tfac));
-        BEM_TRY(up(&P->sy_sched, sched));
-        BEM_TRY(up(&P->sy_sched_ptr, sptr));
+        int *d_tidx = nullptr;
+        float *d_tfac = nullptr;
+        BEM_TRY(up(&d_tidx, tidx));
+        BEM_TRY(up(&d_tfac, tfac));
+        BEM_TRY(A.alloc(&P->sy_img, (size_t)ncls * 2 * g.img_floats));
+        (k_tc_images<<<dim3((g.img_floats + 255) / 256, ncls), 256, 0, s>>>(g.img_floats, np, d_tidx, d_tfac, P->sy_fD,
+                                                                            P->sy_dl, P->sy_img),
+         ::bem::count_launch());
+        BEM_LAUNCH_CHECK();
+        P->deferred.push_back(d_tidx);
+        P->deferred.push_back(d_tfac);
+        // permutation maps without the sign, and the sign bits per symmetry
+        // in words of 32 canonical-frame columns (one word per K chunk)
+        std::vector<unsigned short> fq(6 * (size_t)np);
+        for (int q = 0; q < 6; q++)
+            for (int h = 0; h < np; h++) fq[(size_t)q * np + h] = fwd[(size_t)(q * 8) * np + h] & 0x7fff;
+        BEM_TRY(up(&P->sy_fwdq, fq));
+        const int nw = ldp / 32;
+        std::vector<unsigned> sg(48 * (size_t)nw, 0u);
+        for (int sig = 0; sig < 48; sig++)
+            for (int h = 0; h < np; h++)
+                if (fwd[(size_t)sig * np + h] & 0x8000) sg[(size_t)sig * nw + h / 32] |= 1u << (h % 32);
+        BEM_TRY(up(&P->sy_sgn, sg));
+        BEM_TRY(A.alloc(&P->sy_Mq, (size_t)P->t.nbox * 6 * ldp));
         P->sy_g = g;
         P->sy_nkc = nkc;
-        P->sy_nsched = (int)sched.size();
     } else {
         ldp = (np + 3) / 4 * 4;
         if (sy_simt_smem_bytes(mx, C, np, p) > (size_t)200 * 1024) {
@@ -691,19 +750,19 @@ int build_sym_tables(bem_plan *P, cudaStream_t s) {
 
 void free_sym_tables(bem_plan *P) {
     Arena &A = P->arena;
-    for (void *q : {(void *)P->sy_tidx, (void *)P->sy_tfac, (void *)P->sy_fwd, (void *)P->sy_inv, (void *)P->sy_D,
-                    (void *)P->sy_fD, (void *)P->sy_Lp, (void *)P->sy_sched, (void *)P->sy_sched_ptr,
-                    (void *)P->sy_mexp, (void *)P->sy_invf, (void *)P->sy_ord, (void *)P->sy_tile_cls, (void *)P->sy_tile_start,
-                    (void *)P->sy_tile_cnt, (void *)P->sy_src, (void *)P->sy_sig, (void *)P->sy_pair})
+    for (void *q : {(void *)P->sy_img, (void *)P->sy_fwdq, (void *)P->sy_sgn, (void *)P->sy_Mq, (void *)P->sy_fwd, (void *)P->sy_inv, (void *)P->sy_D,
+                    (void *)P->sy_fD, (void *)P->sy_Lp, (void *)P->sy_mexp, (void *)P->sy_invf, (void *)P->sy_ord,
+                    (void *)P->sy_tile_cls, (void *)P->sy_tile_start, (void *)P->sy_tile_cnt, (void *)P->sy_src,
+                    (void *)P->sy_sig, (void *)P->sy_pair})
         A.release(q);
     P->sy_tile_cls = P->sy_tile_start = P->sy_tile_cnt = P->sy_src = P->sy_sig = P->sy_pair = nullptr;
     P->sy_ord = nullptr;
     P->sy_ntile = 0;
-    P->sy_tidx = P->sy_inv = P->sy_mexp = nullptr;
-    P->sy_fwd = nullptr;
-    P->sy_sched = nullptr;
-    P->sy_sched_ptr = nullptr;
-    P->sy_tfac = P->sy_fD = nullptr;
+    P->sy_inv = P->sy_mexp = nullptr;
+    P->sy_fwd = P->sy_fwdq = nullptr;
+    P->sy_sgn = nullptr;
+    P->sy_Mq = nullptr;
+    P->sy_img = P->sy_fD = nullptr;
     P->sy_Lp = nullptr;
     P->sy_D = P->sy_invf = nullptr;
     P->sy_tc = 0;
@@ -715,24 +774,24 @@ int launch_m2l_tc(bem_plan *P, const float *M, float *L, cudaStream_t s) {
     TcArgs a{};
     a.g = P->sy_g;
     a.np = P->mi.np;
+    a.ldp = P->sy_ldp;
     a.nkc = P->sy_nkc;
-    a.nsched = P->sy_nsched;
-    a.sched = P->sy_sched;
-    a.sched_ptr = P->sy_sched_ptr;
     a.src = P->sy_src;
     a.sig = P->sy_sig;
     a.pair = P->sy_pair;
-    a.dl = P->sy_dl;
-    a.fwd = P->sy_fwd;
-    a.tidx = P->sy_tidx;
-    a.tfac = P->sy_tfac;
-    a.fD = P->sy_fD;
-    a.M = M;
+    a.img = P->sy_img;
+    a.sgn = P->sy_sgn;
+    a.Mq = P->sy_Mq;
     a.Lp = (float *)P->sy_Lp;
-    a.ldp = P->sy_ldp;
     a.err = P->dev_err;
     a.skip = P->skip;
     const size_t sm = tc_smem_bytes(a.g, a.ldp);
+    {
+        const int64_t n = (int64_t)t.nbox * 6 * a.ldp;
+        const int grid = (int)std::min<int64_t>((n + 255) / 256, 8 * std::max(1, P->sm_count));
+        (k_m2l_permute<<<grid, 256, 0, s>>>(t.nbox, a.np, a.ldp, P->sy_fwdq, M, P->sy_Mq, P->skip),
+         ::bem::count_launch());
+    }
     // one run of targets at a time: its tiles, then the gather of its targets
     for (size_t r = 0; r + 1 < P->sy_bt.size(); r++) {
         const int bt0 = P->sy_bt[r], nt = P->sy_bt[r + 1] - bt0, tg0 = P->sy_bb[r], ntg = P->sy_bb[r + 1] - tg0;
