@@ -319,7 +319,9 @@ int64_t mesh_chi_index(const double *nodes, int64_t nn, const int32_t *elems, in
 // radix sort of (key, value) pairs, stable, ascending in the low `bits` bits of key
 int radix_sort_pairs(unsigned long long *keys, int *vals, unsigned long long *tmpk, int *tmpv,
                      int n, int bits, unsigned int *hist, int nblk_cap, cudaStream_t s);
-int scan_exclusive(const int *in, int *out, int n, int *total_dev, cudaStream_t s);
+// exclusive scan of n ints, total to *total_dev; blk: device scratch of scan_scratch(n) ints
+int scan_exclusive(const int *in, int *out, int n, int *total_dev, int *blk, cudaStream_t s);
+size_t scan_scratch(int n);
 }  // namespace bem
 
 #ifdef __CUDACC__

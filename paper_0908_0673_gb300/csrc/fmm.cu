@@ -1178,13 +1178,15 @@ int enqueue_matvec_raw(bem_plan *P, int op, int green, double kwave, int with_di
 struct DiagSwap {
     int p, precision, green, p_min;
 };
-// the diagonal's product runs at one order for every level, at most DIAG_P
-// (float64: DIAG_P; mixed: p + 4): its truncation error is then below the
-// float64 diagonal's stated 5e-8
+// the diagonal's product runs at one order for every level: float64 plans at
+// DIAG_P, where its truncation error is below the float64 diagonal's stated
+// 5e-8; mixed plans at p + 2, at most DIAG_P: there float32 rounding, not the
+// truncation, sets the diagonal's error (its difference from the float64
+// plan's diagonal is the same at p + 2, p + 3 and p + 4)
 constexpr int DIAG_P = 16;
 static DiagSwap diag_fields(const bem_plan *P) {
     const bool mixed = P->prm.precision == BEM_MIXED;
-    return DiagSwap{mixed ? std::min(DIAG_P, P->prm.p + 4) : DIAG_P, mixed ? BEM_MIXED : BEM_F64, BEM_LAPLACE, 0};
+    return DiagSwap{mixed ? std::min(DIAG_P, P->prm.p + 2) : DIAG_P, mixed ? BEM_MIXED : BEM_F64, BEM_LAPLACE, 0};
 }
 static DiagSwap swap_fields(bem_plan *P, const DiagSwap &d) {
     const DiagSwap old{P->prm.p, P->prm.precision, P->green, P->prm.p_min};

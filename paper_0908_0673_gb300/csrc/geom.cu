@@ -757,10 +757,14 @@ __global__ void __launch_bounds__(32 * SP_WARPS, 3) k_special_pair(CorrArgs a, i
                     } else {
                         m01 = map_f<NPE>(df, 0.5f, 0.f); m12 = map_f<NPE>(df, 0.5f, 0.5f); m20 = map_f<NPE>(df, 0.f, 0.5f);
                     }
-                    PieceF ch[4];
-                    split4(PieceF{0.f, 0.f, 1.f, 0.f, 0.f, 1.f, 0}, ch);
+                    // the children of split4 on the reference triangle, by lane
+                    // (selected, not indexed, so that nothing goes to local memory)
+                    const PieceF ch = lane == 0   ? PieceF{0.f, 0.f, 0.5f, 0.f, 0.f, 0.5f, 1}
+                                      : lane == 1 ? PieceF{0.5f, 0.f, 1.f, 0.f, 0.5f, 0.5f, 1}
+                                      : lane == 2 ? PieceF{0.f, 0.5f, 0.5f, 0.5f, 0.f, 1.f, 1}
+                                                  : PieceF{0.5f, 0.f, 0.5f, 0.5f, 0.f, 0.5f, 1};
                     QPiece Q;
-                    Q.piece = pack_piece(ch[lane]);
+                    Q.piece = pack_piece(ch);
                     Q.A = lane == 0 ? v0 : lane == 2 ? m20 : m01;
                     Q.B = lane == 0 ? m01 : lane == 1 ? v1 : m12;
                     Q.Cc = lane == 0 ? m20 : lane == 1 ? m12 : lane == 2 ? v2 : m20;
@@ -918,10 +922,12 @@ int build_correction(bem_plan *P, cudaStream_t s) {
     BEM_TRY(A.alloc(&cnt, N + 1));
     BEM_TRY(A.alloc(&off, N + 1));
     BEM_TRY(A.alloc(&tot, 1));
+    int *sblk = nullptr;
+    BEM_TRY(A.alloc(&sblk, scan_scratch(N + 1)));
     BEM_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (N + 1), s));
     (k_special_count<<<(N + SS_WARPS - 1) / SS_WARPS, 32 * SS_WARPS, 0, s>>>(a, cnt), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
-    BEM_TRY(scan_exclusive(cnt, off, N + 1, tot, s));
+    BEM_TRY(scan_exclusive(cnt, off, N + 1, tot, sblk, s));
     int npairs = 0;
     BEM_CUDA(cudaMemcpyAsync(&npairs, tot, sizeof(int), cudaMemcpyDeviceToHost, s));
     BEM_CUDA(cudaStreamSynchronize(s));
@@ -979,7 +985,7 @@ int build_correction(bem_plan *P, cudaStream_t s) {
     // is added by one Laplace double-layer product on phi = 1
     P->C = d0row;
     // the temporaries are released once the stream has finished with them
-    for (void *q : {(void *)cnt, (void *)tot, (void *)pair_node, (void *)d0pair, (void *)ecx, (void *)ecy, (void *)ecz,
+    for (void *q : {(void *)cnt, (void *)tot, (void *)sblk, (void *)pair_node, (void *)d0pair, (void *)ecx, (void *)ecy, (void *)ecz,
                     (void *)eh, (void *)ebnd, (void *)frho, (void *)rho, (void *)off, (void *)pair_e})
         P->deferred.push_back(q);
     return BEM_OK;

@@ -1,7 +1,7 @@
 // M2L (Eq. 7) on the canonical offset classes, SIMT form: every product the
 // tensor-core form does not take (float32 Helmholtz, float64 of either
 // Green's function, and orders beyond the tensor-core tables, such as the
-// order p + 4 of the mixed plan's diagonal product).
+// order p + 2 of the mixed plan's diagonal product).
 //
 // The pairs, tiles, symmetry maps and canonical derivative tables are those
 // of the tensor-core form (m2l_tc.cu): a tile holds up to 128 pairs of one
@@ -161,6 +161,28 @@ __global__ void __launch_bounds__(SY_T) k_m2l_sy(const __grid_constant__ SyArgs 
                 for (int q = 0; q < 8; q++)
 #pragma unroll
                     for (int c = 0; c < C; c++) acc[r][q][c] = (R)0;
+            // moment chunks are gathered one chunk ahead into registers, so
+            // their loads are in flight while the previous chunk is multiplied:
+            // element i of this thread is pair j = tid / SY_KA + 16 i, column
+            // k = tid % SY_KA of the chunk; Mhat[k][j] = sign * M[src_j][a o pi_j]
+            constexpr int NG = SY_KA * SY_M / SY_T;   // 8
+            R pre[NG][C];
+            auto gather = [&](int k0g) {
+                const int k = tid % SY_KA, ai = k0g + k;
+#pragma unroll
+                for (int i = 0; i < NG; i++) {
+                    const int j = tid / SY_KA + (SY_T / SY_KA) * i, s = sSrc[j];
+#pragma unroll
+                    for (int c = 0; c < C; c++) pre[i][c] = (R)0;
+                    if (s >= 0 && ai < kext) {
+                        const unsigned f = __ldg(a.fwd + sSig[j] + ai);
+                        const R *src = Mg + ((size_t)s * np + (f & 0x7fffu)) * C;
+#pragma unroll
+                        for (int c = 0; c < C; c++) pre[i][c] = (f & 0x8000u) ? -__ldg(src + c) : __ldg(src + c);
+                    }
+                }
+            };
+            gather(0);
             for (int k0 = 0; k0 < kext; k0 += SY_KA) {
                 __syncthreads();                          // the previous chunk is consumed
                 // class matrix chunk: T[k][bl] = Dhat[a + b] fa fb
@@ -183,21 +205,16 @@ __global__ void __launch_bounds__(SY_T) k_m2l_sy(const __grid_constant__ SyArgs 
 #pragma unroll
                     for (int c = 0; c < C; c++) sT[(c * SY_KA + k) * BB + bl] = v[c];
                 }
-                // moment chunk: Mhat[k][j] = sign * M[src_j][a o pi_j]
-                for (int e = tid; e < SY_KA * SY_M; e += SY_T) {
-                    const int j = e / SY_KA, k = e - j * SY_KA, ai = k0 + k, s = sSrc[j];
-                    R v[C];
+                {
+                    const int k = tid % SY_KA;
 #pragma unroll
-                    for (int c = 0; c < C; c++) v[c] = (R)0;
-                    if (s >= 0 && ai < kext) {
-                        const unsigned f = __ldg(a.fwd + sSig[j] + ai);
-                        const R *src = Mg + ((size_t)s * np + (f & 0x7fffu)) * C;
+                    for (int i = 0; i < NG; i++) {
+                        const int j = tid / SY_KA + (SY_T / SY_KA) * i;
 #pragma unroll
-                        for (int c = 0; c < C; c++) v[c] = (f & 0x8000u) ? -__ldg(src + c) : __ldg(src + c);
+                        for (int c = 0; c < C; c++) sMo[(c * SY_KA + k) * SY_MS + j] = pre[i][c];
                     }
-#pragma unroll
-                    for (int c = 0; c < C; c++) sMo[(c * SY_KA + k) * SY_MS + j] = v[c];
                 }
+                if (k0 + SY_KA < kext) gather(k0 + SY_KA);
                 __syncthreads();
                 const int kn = min(SY_KA, kthr - k0);
                 for (int k = 0; k < kn; k++) {
@@ -302,6 +319,7 @@ __global__ void __launch_bounds__(256) k_m2l_gather_sy(int t0, int nbox, const i
             for (int c = 0; c < C; c++) L[((size_t)t * np + b) * C + c] = sum[c] * sc;
     }
 }
+
 
 }  // namespace
 

@@ -15,36 +15,106 @@
 namespace bem {
 
 // ---------------------------------------------------------------------------
-// single-block exclusive scan (set-up sizes: up to a few million entries)
+// exclusive scan: blocks of SCAN_BLK elements are scanned in shared memory;
+// with more than one block, the block totals are scanned by one block and
+// added in a third pass.  Integer sums, so the result is exact.
 // ---------------------------------------------------------------------------
-__global__ void k_scan_single(const int *__restrict__ in, int *__restrict__ out, int n, int *total) {
-    __shared__ int part[1024];
-    const int T = blockDim.x, tid = threadIdx.x;
-    const int per = (n + T - 1) / T;
-    const int b = tid * per, e = min(n, b + per);
-    int s = 0;
-    for (int i = b; i < e; i++) s += in[i];
-    part[tid] = s;
+constexpr int SCAN_T = 512, SCAN_PER = 8, SCAN_BLK = SCAN_T * SCAN_PER;
+
+// exclusive scan of the block's SCAN_BLK elements of sh[] in place; returns the block total
+template <class T>
+__device__ T block_scan(T *sh, T *warp_tot) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    T v[SCAN_PER], s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_PER; i++) {
+        v[i] = sh[tid * SCAN_PER + i];
+        s += v[i];
+    }
+    T x = s;                                   // inclusive scan of the thread sums
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const T y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[warp] = x;
     __syncthreads();
-    for (int off = 1; off < T; off <<= 1) {
-        int v = tid >= off ? part[tid - off] : 0;
-        __syncthreads();
-        part[tid] += v;
-        __syncthreads();
+    if (warp == 0) {
+        T w = lane < SCAN_T / 32 ? warp_tot[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const T y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < SCAN_T / 32) warp_tot[lane] = w;   // inclusive warp offsets
     }
-    int run = part[tid] - s;
-    for (int i = b; i < e; i++) {
-        int v = in[i];
-        out[i] = run;
-        run += v;
+    __syncthreads();
+    T run = x - s + (warp > 0 ? warp_tot[warp - 1] : 0);
+    const T total = warp_tot[SCAN_T / 32 - 1];
+#pragma unroll
+    for (int i = 0; i < SCAN_PER; i++) {
+        sh[tid * SCAN_PER + i] = run;
+        run += v[i];
     }
-    if (tid == T - 1 && total) *total = part[T - 1];
+    __syncthreads();
+    return total;
 }
 
-int scan_exclusive(const int *in, int *out, int n, int *total_dev, cudaStream_t s) {
-    (k_scan_single<<<1, 1024, 0, s>>>(in, out, n, total_dev), ::bem::count_launch());
+// mode 0: block totals only (blk[b]); mode 1: out = scan + blk[b] (blk scanned);
+// mode 2: one block scans in[] of n <= SCAN_BLK elements, total to *total
+template <class T>
+__global__ void __launch_bounds__(SCAN_T) k_scan(const T *__restrict__ in, T *__restrict__ out, int n, T *blk,
+                                               T *total, int mode) {
+    __shared__ T sh[SCAN_BLK];
+    __shared__ T wt[SCAN_T / 32];
+    const int b0 = blockIdx.x * SCAN_BLK;
+    for (int i = threadIdx.x; i < SCAN_BLK; i += SCAN_T) sh[i] = b0 + i < n ? in[b0 + i] : (T)0;
+    __syncthreads();
+    if (mode == 0) {
+        T s = 0;
+#pragma unroll
+        for (int i = 0; i < SCAN_PER; i++) s += sh[threadIdx.x * SCAN_PER + i];
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) wt[warp] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            T t = 0;
+            for (int w = 0; w < SCAN_T / 32; w++) t += wt[w];
+            blk[blockIdx.x] = t;
+        }
+        return;
+    }
+    const T tot = block_scan<T>(sh, wt);
+    const T add = mode == 1 ? blk[blockIdx.x] : (T)0;
+    for (int i = threadIdx.x; i < SCAN_BLK; i += SCAN_T)
+        if (b0 + i < n) out[b0 + i] = sh[i] + add;
+    if (mode == 2 && threadIdx.x == 0 && total) *total = tot;
+}
+
+// exclusive scan of n values (in and out may alias); *total_dev = sum;
+// blk: device scratch of at least scan_scratch(n) values
+size_t scan_scratch(int n) { return (size_t)(n + SCAN_BLK - 1) / SCAN_BLK + 1; }
+
+template <class T>
+static int scan_t(const T *in, T *out, int n, T *total_dev, T *blk, cudaStream_t s) {
+    if (n <= 0) return BEM_OK;
+    const int nb = (n + SCAN_BLK - 1) / SCAN_BLK;
+    if (nb == 1) {
+        (k_scan<T><<<1, SCAN_T, 0, s>>>(in, out, n, nullptr, total_dev, 2), ::bem::count_launch());
+    } else {
+        if (nb > SCAN_BLK) { set_error("scan: %d elements exceed the two-level scan", n); return BEM_EINVAL; }
+        (k_scan<T><<<nb, SCAN_T, 0, s>>>(in, out, n, blk, nullptr, 0), ::bem::count_launch());
+        (k_scan<T><<<1, SCAN_T, 0, s>>>(blk, blk, nb, nullptr, total_dev, 2), ::bem::count_launch());
+        (k_scan<T><<<nb, SCAN_T, 0, s>>>(in, out, n, blk, nullptr, 1), ::bem::count_launch());
+    }
     BEM_LAUNCH_CHECK();
     return BEM_OK;
+}
+
+int scan_exclusive(const int *in, int *out, int n, int *total_dev, int *blk, cudaStream_t s) {
+    return scan_t<int>(in, out, n, total_dev, blk, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -92,31 +162,8 @@ __global__ void k_rs_scatter(const unsigned long long *__restrict__ keys, const 
     }
 }
 
-__global__ void k_scan_u32_single(unsigned int *__restrict__ a, int n) {
-    __shared__ unsigned int part[1024];
-    const int T = blockDim.x, tid = threadIdx.x;
-    const int per = (n + T - 1) / T;
-    const int b = tid * per, e = min(n, b + per);
-    unsigned int s = 0;
-    for (int i = b; i < e; i++) s += a[i];
-    part[tid] = s;
-    __syncthreads();
-    for (int off = 1; off < T; off <<= 1) {
-        unsigned int v = tid >= off ? part[tid - off] : 0;
-        __syncthreads();
-        part[tid] += v;
-        __syncthreads();
-    }
-    unsigned int run = part[tid] - s;
-    for (int i = b; i < e; i++) {
-        unsigned int v = a[i];
-        a[i] = run;
-        run += v;
-    }
-}
-
 // keys/vals are sorted in place (ping-pong through tmp); hist needs
-// 256 * ceil(n/256) entries.
+// 256 * ceil(n/256) entries followed by scan_scratch(256 * ceil(n/256)).
 int radix_sort_pairs(unsigned long long *keys, int *vals, unsigned long long *tmpk, int *tmpv, int n, int bits,
                      unsigned int *hist, int nblk_cap, cudaStream_t s) {
     if (n <= 1) return BEM_OK;
@@ -128,7 +175,7 @@ int radix_sort_pairs(unsigned long long *keys, int *vals, unsigned long long *tm
     for (int p = 0; p < passes; p++) {
         int shift = 8 * p;
         (k_rs_hist<<<nblk, RS_THREADS, 0, s>>>(ka, n, shift, hist, nblk), ::bem::count_launch());
-        (k_scan_u32_single<<<1, 1024, 0, s>>>(hist, 256 * nblk), ::bem::count_launch());
+        BEM_TRY(scan_t<unsigned int>(hist, hist, 256 * nblk, nullptr, hist + (size_t)256 * nblk_cap, s));
         (k_rs_scatter<<<nblk, RS_THREADS, 0, s>>>(ka, va, n, shift, hist, nblk, kb, vb), ::bem::count_launch());
         BEM_LAUNCH_CHECK();
         std::swap(ka, kb);
@@ -144,35 +191,58 @@ int radix_sort_pairs(unsigned long long *keys, int *vals, unsigned long long *tm
 // ---------------------------------------------------------------------------
 // root cube and Morton codes
 // ---------------------------------------------------------------------------
-// root[0..2] lower corner, root[3] side, root[4] 2^21 / side.
-__global__ void k_root(const double *__restrict__ nodes, int n, double *root) {
-    __shared__ double mn[3][1024], mx[3][1024];
+// Bounding box of the vertices: each block reduces a strided share to
+// part[block][6] (min x, y, z, max x, y, z; min and max are exact, so the order
+// does not matter), then one block combines them and writes root[0..2] lower
+// corner, root[3] side, root[4] 2^21 / side.
+constexpr int ROOT_T = 256, ROOT_BLOCKS = 304;
+__global__ void __launch_bounds__(ROOT_T) k_root_part(const double *__restrict__ nodes, int n, double *part) {
+    __shared__ double sh[6][ROOT_T];
     const int tid = threadIdx.x;
     double lo[3] = {nodes[0], nodes[1], nodes[2]}, hi[3] = {nodes[0], nodes[1], nodes[2]};
-    for (int i = tid; i < n; i += blockDim.x)
+    for (int i = blockIdx.x * ROOT_T + tid; i < n; i += gridDim.x * ROOT_T)
         for (int c = 0; c < 3; c++) {
-            double v = nodes[3 * i + c];
+            const double v = nodes[3 * (size_t)i + c];
             lo[c] = fmin(lo[c], v);
             hi[c] = fmax(hi[c], v);
         }
-    for (int c = 0; c < 3; c++) { mn[c][tid] = lo[c]; mx[c][tid] = hi[c]; }
+    for (int c = 0; c < 3; c++) { sh[c][tid] = lo[c]; sh[3 + c][tid] = hi[c]; }
     __syncthreads();
-    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    for (int off = ROOT_T / 2; off > 0; off >>= 1) {
         if (tid < off)
             for (int c = 0; c < 3; c++) {
-                mn[c][tid] = fmin(mn[c][tid], mn[c][tid + off]);
-                mx[c][tid] = fmax(mx[c][tid], mx[c][tid + off]);
+                sh[c][tid] = fmin(sh[c][tid], sh[c][tid + off]);
+                sh[3 + c][tid] = fmax(sh[3 + c][tid], sh[3 + c][tid + off]);
             }
         __syncthreads();
     }
+    if (tid < 6) part[(size_t)blockIdx.x * 6 + tid] = sh[tid][0];
+}
+
+__global__ void __launch_bounds__(ROOT_T) k_root(const double *__restrict__ part, int nparts, double *root) {
+    __shared__ double sh[6][ROOT_T];
+    const int tid = threadIdx.x;
+    double v[6];
+    for (int c = 0; c < 6; c++) v[c] = part[c];
+    for (int b = tid; b < nparts; b += ROOT_T)
+        for (int c = 0; c < 6; c++) v[c] = c < 3 ? fmin(v[c], part[6 * b + c]) : fmax(v[c], part[6 * b + c]);
+    for (int c = 0; c < 6; c++) sh[c][tid] = v[c];
+    __syncthreads();
+    for (int off = ROOT_T / 2; off > 0; off >>= 1) {
+        if (tid < off)
+            for (int c = 0; c < 6; c++)
+                sh[c][tid] = c < 3 ? fmin(sh[c][tid], sh[c][tid + off]) : fmax(sh[c][tid], sh[c][tid + off]);
+        __syncthreads();
+    }
     if (tid == 0) {
-        double ext = __dsub_rn(mx[0][0], mn[0][0]);
-        double ey = __dsub_rn(mx[1][0], mn[1][0]), ez = __dsub_rn(mx[2][0], mn[2][0]);
+        const double mn[3] = {sh[0][0], sh[1][0], sh[2][0]}, mx[3] = {sh[3][0], sh[4][0], sh[5][0]};
+        double ext = __dsub_rn(mx[0], mn[0]);
+        double ey = __dsub_rn(mx[1], mn[1]), ez = __dsub_rn(mx[2], mn[2]);
         if (ey > ext) ext = ey;
         if (ez > ext) ext = ez;
         double side = __dmul_rn(ext, 1.0 + 0x1p-20);
         for (int c = 0; c < 3; c++)
-            root[c] = __dsub_rn(__dmul_rn(__dadd_rn(mn[c][0], mx[c][0]), 0.5), __dmul_rn(side, 0.5));
+            root[c] = __dsub_rn(__dmul_rn(__dadd_rn(mn[c], mx[c]), 0.5), __dmul_rn(side, 0.5));
         root[3] = side;
         root[4] = __ddiv_rn(0x1p21, side);
     }
@@ -353,8 +423,12 @@ int build_tree(bem_plan *P, cudaStream_t s) {
     const int nblk = (std::max(N, E) + RS_THREADS - 1) / RS_THREADS;
     // root cube
     double *root = nullptr;
-    BEM_TRY(A.alloc(&root, 8));
-    (k_root<<<1, 1024, 0, s>>>(P->nodes, N, root), ::bem::count_launch());
+    BEM_TRY(A.alloc(&root, 8 + 6 * ROOT_BLOCKS));
+    {
+        const int nparts = std::max(1, std::min(ROOT_BLOCKS, (N + ROOT_T - 1) / ROOT_T));
+        (k_root_part<<<nparts, ROOT_T, 0, s>>>(P->nodes, N, root + 8), ::bem::count_launch());
+        (k_root<<<1, ROOT_T, 0, s>>>(root + 8, nparts, root), ::bem::count_launch());
+    }
     BEM_LAUNCH_CHECK();
     // Morton codes, sorted
     unsigned long long *tmpk = nullptr;
@@ -364,7 +438,9 @@ int build_tree(bem_plan *P, cudaStream_t s) {
     BEM_TRY(A.alloc(&t.node_perm, N));
     BEM_TRY(A.alloc(&tmpk, std::max(N, E)));
     BEM_TRY(A.alloc(&tmpv, std::max(N, E)));
-    BEM_TRY(A.alloc(&hist, (size_t)256 * nblk));
+    BEM_TRY(A.alloc(&hist, (size_t)256 * nblk + scan_scratch(256 * nblk)));
+    int *sblk = nullptr;
+    BEM_TRY(A.alloc(&sblk, scan_scratch(2 * N + 2)));
     (k_morton<<<(N + 255) / 256, 256, 0, s>>>(P->nodes, N, root, t.codes, t.node_perm), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
     BEM_TRY(radix_sort_pairs(t.codes, t.node_perm, tmpk, tmpv, N, 3 * QBITS, hist, nblk, s));
@@ -420,7 +496,7 @@ int build_tree(bem_plan *P, cudaStream_t s) {
         (k_count_children<<<(cnt + 255) / 256, 256, 0, s>>>(t.codes, nb, ne, off, cnt, level, P->prm.leaf_size,
                                                            P->prm.max_level, nch), ::bem::count_launch());
         BEM_LAUNCH_CHECK();
-        BEM_TRY(scan_exclusive(nch, choff, cnt, total, s));
+        BEM_TRY(scan_exclusive(nch, choff, cnt, total, sblk, s));
         int htot = 0;
         BEM_CUDA(cudaMemcpyAsync(&htot, total, sizeof(int), cudaMemcpyDeviceToHost, s));
         BEM_CUDA(cudaStreamSynchronize(s));
@@ -491,6 +567,7 @@ int build_tree(bem_plan *P, cudaStream_t s) {
     A.release(tmpk);
     A.release(tmpv);
     A.release(hist);
+    A.release(sblk);
     A.release(ekeys);
     A.release(nch);
     A.release(choff);
@@ -669,6 +746,8 @@ int build_radii_lists(bem_plan *P, cudaStream_t s) {
     BEM_TRY(A.alloc(&on, maxcnt));
     BEM_TRY(A.alloc(&oi, maxcnt));
     BEM_TRY(A.alloc(&tot, 2));
+    int *sblk = nullptr;
+    BEM_TRY(A.alloc(&sblk, scan_scratch(maxcnt)));
     for (int l = 1; l < t.nlev; l++) {
         int off = t.lev_off[l], cnt = t.lev_off[l + 1] - off;
         ListArgs a{t.parent, t.child0, t.nchild, t.cx, t.cy, t.cz, t.r, t.near_ptr, near_idx, P->prm.eta,
@@ -678,8 +757,8 @@ int build_radii_lists(bem_plan *P, cudaStream_t s) {
         (k_close_ptr<<<1, 1, 0, s>>>(t.inter_ptr, off, ninter), ::bem::count_launch());
         (k_lists_count<<<(cnt + 127) / 128, 128, 0, s>>>(a, off, cnt, cn, ci), ::bem::count_launch());
         BEM_LAUNCH_CHECK();
-        BEM_TRY(scan_exclusive(cn, on, cnt, tot, s));
-        BEM_TRY(scan_exclusive(ci, oi, cnt, tot + 1, s));
+        BEM_TRY(scan_exclusive(cn, on, cnt, tot, sblk, s));
+        BEM_TRY(scan_exclusive(ci, oi, cnt, tot + 1, sblk, s));
         int h[2];
         BEM_CUDA(cudaMemcpyAsync(h, tot, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
         BEM_CUDA(cudaStreamSynchronize(s));
@@ -704,6 +783,7 @@ int build_radii_lists(bem_plan *P, cudaStream_t s) {
     A.release(ci);
     A.release(on);
     A.release(oi);
+    A.release(sblk);
     return BEM_OK;
 }
 
