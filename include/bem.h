@@ -210,8 +210,8 @@ int bem_matvec_noalloc(bem_plan *plan, int op, const void *x_dev, void *y_dev, v
  * [nrhs][n_chi]; phi_dev: device [nrhs][n_phi] (written).  info: host array
  * of nrhs entries (may be NULL).  Returns BEM_ENOCONV if any right-hand side
  * stopped at max_iter; its best iterate is written.  Synchronises the stream
- * once per restart cycle.  A BEM_MIXED plan aims at max(tol, 5e-8), just
- * above the float32 operator's residual floor, and also stops when a whole
+ * once per restart cycle.  A BEM_MIXED plan aims at max(tol, 1e-7), a little
+ * above the float32 operator's residual floor (2-5e-8), and also stops when a whole
  * restart cycle fails to halve the true residual: that stop is BEM_OK when the
  * residual reached is at most max(tol, 1e-6) and BEM_ENOCONV above it
  * (bem_solve_stop_rule); info reports the residual reached. */
@@ -226,7 +226,7 @@ int bem_solve(bem_plan *plan, const void *chi_dev, void *phi_dev, int nrhs,
  * ||b - A x|| / ||b||; prev_rel: the previous one (any value above 2 rel on
  * the first); iters: Arnoldi steps (or iterations) taken.  Returns 1 when the
  * solve ends here and writes *status:
- *   rel <= tol (mixed: max(tol, 5e-8))                    -> BEM_OK;
+ *   rel <= tol (mixed: max(tol, 1e-7))                    -> BEM_OK;
  *   mixed, restarts > 1 and rel > prev_rel / 2 (a stall)  -> BEM_OK if
  *       rel <= max(tol, 1e-6), else BEM_ENOCONV;
  *   iters >= max_iter                                     -> BEM_ENOCONV.

@@ -147,7 +147,14 @@ __global__ void k_resid(int n, const double *__restrict__ b, double *r, const in
 // cycle, [2] halt (the solve has ended: every kernel of the solve returns)
 __global__ void k_arm(int *st) { st[0] = st[2]; }
 
-constexpr double TAU_MIXED = 5e-8;
+// Targets of a mixed-precision solve.  The float32 operator's rounding leaves
+// a true (float64) residual floor of 2-5e-8.  Arnoldi steps go on until the
+// estimated residual reaches TAU_MIXED_CYCLE, just above that floor, and a
+// true residual up to TAU_MIXED is accepted: the cycle that reaches the
+// estimate ends the solve, instead of a second, one-step cycle taken to push
+// the true residual from just above the floor to just below it.
+constexpr double TAU_MIXED = 1e-7;
+constexpr double TAU_MIXED_CYCLE = 5e-8;
 // A mixed solve that stops because a restart cycle failed to halve the true
 // residual has converged only if that residual is at most max(tol, TAU_STALL).
 // The second-kind collocation equation is well conditioned (condition numbers
@@ -474,10 +481,8 @@ static int gm_k_cycle(bem_plan *P, int steps, cudaStream_t s, bool raw) {
 }
 
 static double gm_tol(const bem_plan *P, double tol) {
-    // With a float32 operator the true (float64) residual levels off near
-    // 2e-8; a mixed-precision solve therefore aims at max(tol, TAU_MIXED) and
-    // also stops once a whole restart cycle fails to halve the true residual.
-    return P->prm.precision == BEM_MIXED ? std::max(tol, TAU_MIXED) : tol;
+    // the Arnoldi estimate's target; the true residual's is bem_solve_stop_rule's
+    return P->prm.precision == BEM_MIXED ? std::max(tol, TAU_MIXED_CYCLE) : tol;
 }
 
 

@@ -81,10 +81,12 @@ def test_solve_stop_rule():
     ok, enc = bem.BEM_OK, bem.BEM_ENOCONV
     # tolerance reached
     assert rule(F, 1e-10, 1, 5e-11, 2.0, 3, 100) == (True, ok)
-    assert rule(M, 1e-10, 1, 4e-8, 2.0, 3, 100) == (True, ok)       # mixed target max(tol, 5e-8)
+    assert rule(M, 1e-10, 1, 4e-8, 2.0, 3, 100) == (True, ok)       # mixed target max(tol, 1e-7)
+    assert rule(M, 1e-10, 1, 9e-8, 2.0, 3, 100) == (True, ok)
+    assert rule(M, 1e-10, 1, 1.2e-7, 2.0, 3, 100) == (False, None)
     assert rule(F, 1e-10, 1, 4e-8, 2.0, 3, 100) == (False, None)
     # stall of a mixed solve: converged near the float32 floor, not above 1e-6
-    assert rule(M, 1e-10, 2, 8e-8, 1e-7, 40, 100) == (True, ok)
+    assert rule(M, 1e-10, 2, 1.5e-7, 2e-7, 40, 100) == (True, ok)
     assert rule(M, 1e-10, 2, 9e-7, 1.0e-6, 40, 100) == (True, ok)
     assert rule(M, 1e-10, 2, 1e-3, 1.5e-3, 40, 100) == (True, enc)
     assert rule(M, 1e-10, 3, 2e-6, 3e-6, 40, 100) == (True, enc)
