@@ -392,8 +392,6 @@ __global__ void __launch_bounds__(32 * SS_WARPS) k_special_write(CorrArgs a, con
 // ---------------------------------------------------------------------------
 constexpr int SP_WARPS = 4;        // warps per block
 constexpr int SP_PAIRS_PER_WARP = 16;   // pairs per warp (grid-stride), launch granularity
-constexpr int SP_QCAP = 64;        // pieces per level buffer and warp (float32; half for float64)
-constexpr int SP_RING = 256;       // pending points per warp: a power of two >= 31 + 7 * 32
 constexpr float SP_UNIT = 1024.f;  // piece corners are multiples of 2^-10 (max_subdiv <= 10)
 
 struct PieceF {
@@ -467,9 +465,17 @@ __device__ __forceinline__ void point_acc(const R *d, R kk, const R (&N)[NPE], c
         vx += Nt[a] * dx; vy += Nt[a] * dy; vz += Nt[a] * dz;
     }
     const R nx = uy * vz - uz * vy, ny = uz * vx - ux * vz, nz = ux * vy - uy * vx;   // |n| = J
-    const R J = sqrt(nx * nx + ny * ny + nz * nz);
-    const R r2 = rx * rx + ry * ry + rz * rz;
-    const R inv = (R)1 / sqrt(r2);
+    const R n2 = nx * nx + ny * ny + nz * nz, r2 = rx * rx + ry * ry + rz * rz;
+    R J, inv;
+    if constexpr (sizeof(R) == sizeof(float)) {
+        // float32 sums: the hardware reciprocal square root (2 ulp) in place of
+        // the correctly rounded square root and division
+        J = n2 * rsqrtf(n2);
+        inv = rsqrtf(r2);
+    } else {
+        J = sqrt(n2);
+        inv = (R)1 / sqrt(r2);
+    }
     const R c4 = (R)(0.25 / M_PI) * wref;
     const R wS = c4 * J * inv;                                           // w J G0
     const R wD = c4 * (rx * nx + ry * ny + rz * nz) * inv * inv * inv;   // w J dG0/dn1
@@ -644,220 +650,279 @@ __device__ void refine_serial(const double *X, const double xi[3], const R *d, c
     }
 }
 
+// Loads the element of a pair into the group's tables: node coordinates
+// (float64) and their offsets from the collocation point (working precision
+// and float32).  W lanes of the group share the 3 NPE values.
+template <class R, int NPE, int W>
+__device__ __forceinline__ void load_pair(const CorrArgs &a, int node, int e, int sl, double xi[3], double *X, R *d,
+                                          float *df) {
+    xi[0] = a.nodes[3 * (size_t)node];
+    xi[1] = a.nodes[3 * (size_t)node + 1];
+    xi[2] = a.nodes[3 * (size_t)node + 2];
+    for (int i = sl; i < 3 * NPE; i += W) {
+        const int c = i % 3, vid = a.el_phi[(size_t)e * NPE + i / 3];
+        const double xv = a.nodes[3 * (size_t)vid + c];
+        X[i] = xv;
+        d[i] = (R)(xv - xi[c]);
+        df[i] = (float)(xv - xi[c]);
+    }
+}
+
+// Sums the lanes' partial values of a pair over the W lanes of its group by a
+// transposing butterfly, in blocks of W values: after the steps of widths
+// W/2 .. 1 (a lane keeps the half of a block selected by bit k of its lane
+// index), lane l holds value l of every block.  Value l + W b goes to S at
+// l + W b < NPE C, to D below 2 NPE C, to the D0 row sum at 2 NPE C.
+template <class R, bool HELM, int NPE, int W>
+__device__ __forceinline__ void reduce_store(R (&v)[sp_nvp(HELM, NPE)], unsigned wmask, int sl, int pr, double *valD,
+                                             double *valS, double *d0pair) {
+    constexpr int C = HELM ? 2 : 1, NVP = sp_nvp(HELM, NPE);
+    if constexpr (W > NVP) {
+        // fewer values than lanes: plain sums across the lanes beyond NVP first
+#pragma unroll
+        for (int k = W / 2; k >= NVP; k >>= 1)
+#pragma unroll
+            for (int i = 0; i < NVP; i++) v[i] += __shfl_xor_sync(wmask, v[i], k);
+    }
+    constexpr int BW = W < NVP ? W : NVP;          // block width
+#pragma unroll
+    for (int b0 = 0; b0 < NVP; b0 += BW) {
+#pragma unroll
+        for (int k = BW / 2; k >= 1; k >>= 1) {
+            const bool up = (sl & k) != 0;
+#pragma unroll
+            for (int i = 0; i < k; i++) {
+                const R lo = v[b0 + i], hi = v[b0 + i + k];
+                v[b0 + i] = (up ? hi : lo) + __shfl_xor_sync(wmask, up ? lo : hi, k);
+            }
+        }
+        const int vi = b0 + (sl % BW);
+        if (sl < BW) {
+            if (vi < NPE * C) valS[(size_t)pr * NPE * C + vi] = (double)v[b0];
+            else if (vi < 2 * NPE * C) valD[(size_t)pr * NPE * C + vi - NPE * C] = (double)v[b0];
+            else if (vi == 2 * NPE * C) d0pair[pr] = (double)v[b0];
+        }
+    }
+}
+
+// Self pairs (the collocation node is a node of the element), one warp per
+// pair: the Duffy rule collapsed at the node (split at a mid-side node), then
+// the regular rule subtracted, all by point index, one point per lane.
 template <class R, bool HELM, int NPE>
-__global__ void __launch_bounds__(32 * SP_WARPS, 3) k_special_pair(CorrArgs a, int npairs, const int *__restrict__ pair_node,
-                                                                const int *__restrict__ pair_e, double *valD,
-                                                                double *valS, double *d0pair) {
-    constexpr int C = HELM ? 2 : 1;
+__global__ void __launch_bounds__(32 * SP_WARPS) k_special_self(CorrArgs a, int nlist, const int *__restrict__ list,
+                                                               const int *__restrict__ pair_node,
+                                                               const int *__restrict__ pair_e, double *valD,
+                                                               double *valS, double *d0pair) {
+    constexpr int NVP = sp_nvp(HELM, NPE);
     constexpr unsigned FULL = 0xffffffffu;
-    constexpr int QCAP = sizeof(R) == 4 ? SP_QCAP : SP_QCAP / 2;   // static shared memory stays under 48 KB
-    __shared__ QPiece qbuf[SP_WARPS][2][QCAP];
-    __shared__ R ring[SP_WARPS][3][SP_RING];
     __shared__ double sX[SP_WARPS][18];
     __shared__ R sd[SP_WARPS][18];
     __shared__ float sdf[SP_WARPS][18];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
-    R *rs = ring[warp][0], *rt = ring[warp][1], *rw = ring[warp][2];
-    const double *X = sX[warp];
-    const R *d = sd[warp];
-    const float *df = sdf[warp];
     const R kk = (R)a.k;
-    const float tau2 = (float)(a.tau * a.tau);
-    // the next pair's indices and coordinates are loaded while the current
-    // one is integrated (a two-stage pipeline over the grid-stride loop)
-    const int stride = gridDim.x * SP_WARPS;
-    int pr = blockIdx.x * SP_WARPS + warp;
-    int node_n = 0, e_n = 0, vid_n = -1;
-    double xin[3] = {0.0, 0.0, 0.0}, xv_n = 0.0;
-    auto fetch_head = [&](int q) {
-        if (q < npairs) { node_n = pair_node[q]; e_n = pair_e[q]; }
-    };
-    auto fetch_tail = [&](int q) {
-        if (q < npairs) {
-            xin[0] = a.nodes[3 * (size_t)node_n];
-            xin[1] = a.nodes[3 * (size_t)node_n + 1];
-            xin[2] = a.nodes[3 * (size_t)node_n + 2];
-            vid_n = lane < 3 * NPE ? a.el_phi[(size_t)e_n * NPE + lane / 3] : -1;
-            xv_n = vid_n >= 0 ? a.nodes[3 * (size_t)vid_n + lane % 3] : 0.0;
-        }
-    };
-    fetch_head(pr);
-    fetch_tail(pr);
-    for (; pr < npairs; pr += stride) {
-        const int node = node_n;
-        const double xi[3] = {xin[0], xin[1], xin[2]};
-        const int vid = vid_n;
-        const double xv = xv_n;
-        fetch_head(pr + stride);
+    for (int li = blockIdx.x * SP_WARPS + warp; li < nlist; li += gridDim.x * SP_WARPS) {
+        const int pr = list[li], node = pair_node[pr], e = pair_e[pr];
+        double xi[3];
         __syncwarp();                                   // the previous pair's reads of the tables are done
-        if (lane < 3 * NPE) {
-            const int c = lane % 3;
-            sX[warp][lane] = xv;
-            sd[warp][lane] = (R)(xv - xi[c]);
-            sdf[warp][lane] = (float)(xv - xi[c]);
-        }
-        const unsigned sing = __ballot_sync(FULL, vid == node && lane % 3 == 0);
-        const int as = sing ? (__ffs(sing) - 1) / 3 : -1;
+        load_pair<R, NPE, 32>(a, node, e, lane, xi, sX[warp], sd[warp], sdf[warp]);
+        int as = 0;
+        for (int v = 0; v < NPE; v++)
+            if (a.el_phi[(size_t)e * NPE + v] == node) as = v;
         __syncwarp();
-        constexpr int NVP = sp_nvp(HELM, NPE);
+        const R *d = sd[warp];
         R v[NVP];
 #pragma unroll
         for (int i = 0; i < NVP; i++) v[i] = 0;
-        if (as >= 0) {
-            // self element: Duffy rule collapsed at the node (split at a mid-side
-            // node), then the regular rule subtracted, all by point index
-            const R p0 = as == 1 || as == 3 || as == 4 ? (R)(as == 1 ? 1 : 0.5) : (R)0;
-            const R p1 = as == 2 || as == 4 || as == 5 ? (R)(as == 2 ? 1 : 0.5) : (R)0;
-            R NP[NPE], NsP[NPE], NtP[NPE];
-            shape_all<R, NPE>(p0, p1, NP, NsP, NtP);
-            const int nsub = as < 3 ? 1 : 2, nd = a.nd, per = nd * nd, go = nd * (nd - 1) / 2;
-            const int nduffy = nsub * per;
-            for (int j = lane; j < nduffy + NQ; j += 32) {
-                if (j >= nduffy) {
-                    const int q = j - nduffy;
-                    eval_st<R, HELM, NPE>(d, kk, rule_s<R>(q), rule_t<R>(q), -rule_w<R>(q), v);
-                    continue;
-                }
-                const int sub = j / per, rem = j - sub * per, iu = rem / nd, iv = rem - iu * nd;
-                // the sub-triangle (P, Q1, Q2): Q1, Q2 the corners (r+1) mod 3 and
-                // (r+2) mod 3 of the reference triangle, corners 0 (0,0), 1 (1,0), 2 (0,1)
-                const int r = as < 3 ? as : (as - 3 + sub) % 3, k1 = (r + 1) % 3, k2 = (r + 2) % 3;
-                const R q10 = (R)(k1 == 1), q11 = (R)(k1 == 2), q20 = (R)(k2 == 1), q21 = (R)(k2 == 2);
-                const R det = fabs((q10 - p0) * (q21 - p1) - (q11 - p1) * (q20 - p0));
-                R u, wu, w2, wv;
-                gl01<R>(go + iu, u, wu);
-                gl01<R>(go + iv, w2, wv);
-                const R uv = u * w2;
-                const R ds = u * (q10 - p0) + uv * (q20 - q10);
-                const R dt = u * (q11 - p1) + uv * (q21 - q11);
-                R N[NPE], Ns[NPE], Nt[NPE];
-                shape_all<R, NPE>(p0 + ds, p1 + dt, N, Ns, Nt);
+        const R p0 = as == 1 || as == 3 || as == 4 ? (R)(as == 1 ? 1 : 0.5) : (R)0;
+        const R p1 = as == 2 || as == 4 || as == 5 ? (R)(as == 2 ? 1 : 0.5) : (R)0;
+        R NP[NPE], NsP[NPE], NtP[NPE];
+        shape_all<R, NPE>(p0, p1, NP, NsP, NtP);
+        const int nsub = as < 3 ? 1 : 2, nd = a.nd, per = nd * nd, go = nd * (nd - 1) / 2;
+        const int nduffy = nsub * per;
+        for (int j = lane; j < nduffy + NQ; j += 32) {
+            if (j >= nduffy) {
+                const int q = j - nduffy;
+                eval_st<R, HELM, NPE>(d, kk, rule_s<R>(q), rule_t<R>(q), -rule_w<R>(q), v);
+                continue;
+            }
+            const int sub = j / per, rem = j - sub * per, iu = rem / nd, iv = rem - iu * nd;
+            // the sub-triangle (P, Q1, Q2): Q1, Q2 the corners (r+1) mod 3 and
+            // (r+2) mod 3 of the reference triangle, corners 0 (0,0), 1 (1,0), 2 (0,1)
+            const int r = as < 3 ? as : (as - 3 + sub) % 3, k1 = (r + 1) % 3, k2 = (r + 2) % 3;
+            const R q10 = (R)(k1 == 1), q11 = (R)(k1 == 2), q20 = (R)(k2 == 1), q21 = (R)(k2 == 2);
+            const R det = fabs((q10 - p0) * (q21 - p1) - (q11 - p1) * (q20 - p0));
+            R u, wu, w2, wv;
+            gl01<R>(go + iu, u, wu);
+            gl01<R>(go + iv, w2, wv);
+            const R uv = u * w2;
+            const R ds = u * (q10 - p0) + uv * (q20 - q10);
+            const R dt = u * (q11 - p1) + uv * (q21 - q11);
+            R N[NPE], Ns[NPE], Nt[NPE];
+            shape_all<R, NPE>(p0 + ds, p1 + dt, N, Ns, Nt);
 #pragma unroll
-                for (int b = 0; b < NPE; b++)
-                    N[b] = (b == as ? (R)1 : (R)0) + (R)0.5 * ((NsP[b] + Ns[b]) * ds + (NtP[b] + Nt[b]) * dt);
-                point_acc<R, HELM, NPE>(d, kk, N, Ns, Nt, wu * wv * u * det, v);
-            }
-        } else {
-            // near-singular element: the regular rule with negative weights,
-            // then the leaf pieces of a level-synchronous 4-way refinement
-            if (lane < NQ) { rs[lane] = rule_s<R>(lane); rt[lane] = rule_t<R>(lane); rw[lane] = -rule_w<R>(lane); }
-            int head = 0, tail = NQ;
-            QPiece *cur = qbuf[warp][0], *nxt = qbuf[warp][1];
-            int ncur = 0;
-            auto img = [&](int v) { return make_float4(df[3 * v], df[3 * v + 1], df[3 * v + 2], 0.f); };
-            if (a.maxdepth > 0) {
-                // the pair was selected by the root's own test, so the root
-                // splits: its four children, corner images from the nodes
-                if (lane < 4) {
-                    const float4 v0 = img(0), v1 = img(1), v2 = img(2);
-                    float4 m01, m12, m20;
-                    if (NPE == 6) {
-                        m01 = img(3 % NPE); m12 = img(4 % NPE); m20 = img(5 % NPE);
-                    } else {
-                        m01 = map_f<NPE>(df, 0.5f, 0.f); m12 = map_f<NPE>(df, 0.5f, 0.5f); m20 = map_f<NPE>(df, 0.f, 0.5f);
-                    }
-                    // the children of split4 on the reference triangle, by lane
-                    // (selected, not indexed, so that nothing goes to local memory)
-                    const PieceF ch = lane == 0   ? PieceF{0.f, 0.f, 0.5f, 0.f, 0.f, 0.5f, 1}
-                                      : lane == 1 ? PieceF{0.5f, 0.f, 1.f, 0.f, 0.5f, 0.5f, 1}
-                                      : lane == 2 ? PieceF{0.f, 0.5f, 0.5f, 0.5f, 0.f, 1.f, 1}
-                                                  : PieceF{0.5f, 0.f, 0.5f, 0.5f, 0.f, 0.5f, 1};
-                    QPiece Q;
-                    Q.piece = pack_piece(ch);
-                    Q.A = lane == 0 ? v0 : lane == 2 ? m20 : m01;
-                    Q.B = lane == 0 ? m01 : lane == 1 ? v1 : m12;
-                    Q.Cc = lane == 0 ? m20 : lane == 1 ? m12 : lane == 2 ? v2 : m20;
-                    cur[lane] = Q;
-                }
-                ncur = 4;
-            } else if (lane < NQ) {
-                // no subdivision: the special rule is the regular rule
-                rs[NQ + lane] = rule_s<R>(lane); rt[NQ + lane] = rule_t<R>(lane); rw[NQ + lane] = rule_w<R>(lane);
-            }
-            if (a.maxdepth <= 0) tail = 2 * NQ;
-            __syncwarp();
-            while (ncur > 0) {
-                int nnext = 0;
-                for (int base = 0; base < ncur; base += 32) {
-                    const int i = base + lane;
-                    PieceF P = {};
-                    QPiece Q;
-                    bool split = false, leaf = false;
-                    if (i < ncur) {
-                        Q = cur[i];
-                        P = unpack_piece(Q.piece);
-                        split = split_test<NPE>(df, Q, P, X, xi, tau2, a.tau, a.maxdepth);
-                        leaf = !split;
-                    }
-                    const unsigned ms = __ballot_sync(FULL, split), ml = __ballot_sync(FULL, leaf);
-                    if (split) {
-                        const int pos = nnext + 4 * __popc(ms & lt);
-                        if (pos + 4 <= QCAP) {
-                            PieceF ch[4];
-                            split4(P, ch);
-                            const float4 mab = map_f<NPE>(df, ch[0].b0, ch[0].b1);   // (a + b) / 2
-                            const float4 mca = map_f<NPE>(df, ch[0].c0, ch[0].c1);   // (c + a) / 2
-                            const float4 mbc = map_f<NPE>(df, ch[1].c0, ch[1].c1);   // (b + c) / 2
-                            QPiece *o = nxt + pos;
-                            o[0].piece = pack_piece(ch[0]); o[0].A = Q.A; o[0].B = mab; o[0].Cc = mca;
-                            o[1].piece = pack_piece(ch[1]); o[1].A = mab; o[1].B = Q.B; o[1].Cc = mbc;
-                            o[2].piece = pack_piece(ch[2]); o[2].A = mca; o[2].B = mbc; o[2].Cc = Q.Cc;
-                            o[3].piece = pack_piece(ch[3]); o[3].A = mab; o[3].B = mbc; o[3].Cc = mca;
-                        } else {
-                            refine_serial<R, HELM, NPE>(X, xi, d, df, kk, a.tau, a.maxdepth, P, v);
-                        }
-                    }
-                    if (leaf) {
-                        const int p0 = tail + NQ * __popc(ml & lt);
-#pragma unroll
-                        for (int q = 0; q < NQ; q++) {
-                            R s, t, w;
-                            leaf_point<R>(P, q, s, t, w);
-                            const int k = (p0 + q) & (SP_RING - 1);
-                            rs[k] = s; rt[k] = t; rw[k] = w;
-                        }
-                    }
-                    tail += NQ * __popc(ml);
-                    nnext = min(QCAP, nnext + 4 * __popc(ms));
-                    nnext -= nnext % 4;
-                    __syncwarp();
-                    for (; tail - head >= 32; head += 32) {
-                        const int k = (head + lane) & (SP_RING - 1);
-                        eval_st<R, HELM, NPE>(d, kk, rs[k], rt[k], rw[k], v);
-                    }
-                    __syncwarp();                       // ring reads done before the next writes
-                }
-                QPiece *sw = cur; cur = nxt; nxt = sw;
-                ncur = nnext;
-            }
-            for (; tail - head > 0; head += 32) {
-                const int k = (head + lane) & (SP_RING - 1);
-                if (head + lane < tail) eval_st<R, HELM, NPE>(d, kk, rs[k], rt[k], rw[k], v);
-            }
+            for (int b = 0; b < NPE; b++)
+                N[b] = (b == as ? (R)1 : (R)0) + (R)0.5 * ((NsP[b] + Ns[b]) * ds + (NtP[b] + Nt[b]) * dt);
+            point_acc<R, HELM, NPE>(d, kk, N, Ns, Nt, wu * wv * u * det, v);
         }
-        fetch_tail(pr + stride);
-        // transposing butterfly: after the step of width k a lane keeps the
-        // half of its values selected by bit k of its index, so value l of
-        // the pair ends on lane l (with 16 values, a plain step across the
-        // half-warps comes first and lanes l and l + 16 both hold value l)
-        if (NVP == 16) {
-#pragma unroll
-            for (int i = 0; i < NVP; i++) v[i] += __shfl_xor_sync(FULL, v[i], 16);
-        }
-#pragma unroll
-        for (int k = NVP / 2; k >= 1; k >>= 1) {
-            const bool up = (lane & k) != 0;
-#pragma unroll
-            for (int i = 0; i < k; i++) {
-                const R lo = v[i], hi = v[i + k];
-                v[i] = (up ? hi : lo) + __shfl_xor_sync(FULL, up ? lo : hi, k);
-            }
-        }
-        if (lane < NPE * C) valS[(size_t)pr * NPE * C + lane] = (double)v[0];
-        else if (lane < 2 * NPE * C) valD[(size_t)pr * NPE * C + lane - NPE * C] = (double)v[0];
-        else if (lane == 2 * NPE * C) d0pair[pr] = (double)v[0];
+        reduce_store<R, HELM, NPE, 32>(v, FULL, lane, pr, valD, valS, d0pair);
     }
+}
+
+// Near-singular pairs, one group of SPN_W lanes per pair (four pairs per
+// warp, so that the refinement's few pieces per level keep more lanes busy):
+// the regular rule with negative weights, then the leaf pieces of a
+// level-synchronous 4-way refinement.  Quadrature points go to the group's
+// ring and are evaluated SPN_W at a time, one per lane, in a fixed order.
+constexpr int SPN_W = 8;            // lanes per pair
+constexpr int SPN_WARPS = 2;        // warps per block
+constexpr int SPN_G = SPN_WARPS * 32 / SPN_W;   // groups per block
+constexpr int SPN_QCAP = 32;        // pieces per level buffer and group
+constexpr int SPN_RING = 64;        // pending points per group: a power of two >= SPN_W - 1 + 7 SPN_W
+
+template <class R, bool HELM, int NPE>
+__global__ void __launch_bounds__(32 * SPN_WARPS) k_special_near(CorrArgs a, int nlist, const int *__restrict__ list,
+                                                                const int *__restrict__ pair_node,
+                                                                const int *__restrict__ pair_e, double *valD,
+                                                                double *valS, double *d0pair) {
+    constexpr int NVP = sp_nvp(HELM, NPE), W = SPN_W, QCAP = SPN_QCAP, RING = SPN_RING;
+    __shared__ QPiece qbuf[SPN_G][2][QCAP];
+    __shared__ R ring[SPN_G][3][RING];
+    __shared__ double sX[SPN_G][18];
+    __shared__ R sd[SPN_G][18];
+    __shared__ float sdf[SPN_G][18];
+    const int lane = threadIdx.x & 31, g = threadIdx.x / W, sl = threadIdx.x % W;
+    const unsigned wmask = ((1u << W) - 1u) << (lane - sl);
+    const unsigned lt = (1u << sl) - 1u;
+    auto ballot = [&](bool p) { return (__ballot_sync(wmask, p) >> (lane - sl)) & ((1u << W) - 1u); };
+    R *rs = ring[g][0], *rt = ring[g][1], *rw = ring[g][2];
+    const double *X = sX[g];
+    const R *d = sd[g];
+    const float *df = sdf[g];
+    const R kk = (R)a.k;
+    const float tau2 = (float)(a.tau * a.tau);
+    for (int li = blockIdx.x * SPN_G + g; li < nlist; li += gridDim.x * SPN_G) {
+        const int pr = list[li], node = pair_node[pr], e = pair_e[pr];
+        double xi[3];
+        __syncwarp(wmask);                              // the previous pair's reads of the tables are done
+        load_pair<R, NPE, W>(a, node, e, sl, xi, sX[g], sd[g], sdf[g]);
+        __syncwarp(wmask);
+        R v[NVP];
+#pragma unroll
+        for (int i = 0; i < NVP; i++) v[i] = 0;
+        for (int q = sl; q < NQ; q += W) { rs[q] = rule_s<R>(q); rt[q] = rule_t<R>(q); rw[q] = -rule_w<R>(q); }
+        int head = 0, tail = NQ;
+        QPiece *cur = qbuf[g][0], *nxt = qbuf[g][1];
+        int ncur = 0;
+        auto img = [&](int vtx) { return make_float4(df[3 * vtx], df[3 * vtx + 1], df[3 * vtx + 2], 0.f); };
+        if (a.maxdepth > 0) {
+            // the pair was selected by the root's own test, so the root
+            // splits: its four children, corner images from the nodes
+            if (sl < 4) {
+                const float4 v0 = img(0), v1 = img(1), v2 = img(2);
+                float4 m01, m12, m20;
+                if (NPE == 6) {
+                    m01 = img(3 % NPE); m12 = img(4 % NPE); m20 = img(5 % NPE);
+                } else {
+                    m01 = map_f<NPE>(df, 0.5f, 0.f); m12 = map_f<NPE>(df, 0.5f, 0.5f); m20 = map_f<NPE>(df, 0.f, 0.5f);
+                }
+                // the children of split4 on the reference triangle, by lane
+                const PieceF ch = sl == 0   ? PieceF{0.f, 0.f, 0.5f, 0.f, 0.f, 0.5f, 1}
+                                  : sl == 1 ? PieceF{0.5f, 0.f, 1.f, 0.f, 0.5f, 0.5f, 1}
+                                  : sl == 2 ? PieceF{0.f, 0.5f, 0.5f, 0.5f, 0.f, 1.f, 1}
+                                            : PieceF{0.5f, 0.f, 0.5f, 0.5f, 0.f, 0.5f, 1};
+                QPiece Q;
+                Q.piece = pack_piece(ch);
+                Q.A = sl == 0 ? v0 : sl == 2 ? m20 : m01;
+                Q.B = sl == 0 ? m01 : sl == 1 ? v1 : m12;
+                Q.Cc = sl == 0 ? m20 : sl == 1 ? m12 : sl == 2 ? v2 : m20;
+                cur[sl] = Q;
+            }
+            ncur = 4;
+        } else {
+            // no subdivision: the special rule is the regular rule
+            for (int q = sl; q < NQ; q += W) { rs[NQ + q] = rule_s<R>(q); rt[NQ + q] = rule_t<R>(q); rw[NQ + q] = rule_w<R>(q); }
+            tail = 2 * NQ;
+        }
+        __syncwarp(wmask);
+        while (ncur > 0) {
+            int nnext = 0;
+            for (int base = 0; base < ncur; base += W) {
+                const int i = base + sl;
+                PieceF P = {};
+                QPiece Q;
+                bool split = false, leaf = false;
+                if (i < ncur) {
+                    Q = cur[i];
+                    P = unpack_piece(Q.piece);
+                    split = split_test<NPE>(df, Q, P, X, xi, tau2, a.tau, a.maxdepth);
+                    leaf = !split;
+                }
+                const unsigned ms = ballot(split), ml = ballot(leaf);
+                if (split) {
+                    const int pos = nnext + 4 * __popc(ms & lt);
+                    if (pos + 4 <= QCAP) {
+                        PieceF ch[4];
+                        split4(P, ch);
+                        const float4 mab = map_f<NPE>(df, ch[0].b0, ch[0].b1);   // (a + b) / 2
+                        const float4 mca = map_f<NPE>(df, ch[0].c0, ch[0].c1);   // (c + a) / 2
+                        const float4 mbc = map_f<NPE>(df, ch[1].c0, ch[1].c1);   // (b + c) / 2
+                        QPiece *o = nxt + pos;
+                        o[0].piece = pack_piece(ch[0]); o[0].A = Q.A; o[0].B = mab; o[0].Cc = mca;
+                        o[1].piece = pack_piece(ch[1]); o[1].A = mab; o[1].B = Q.B; o[1].Cc = mbc;
+                        o[2].piece = pack_piece(ch[2]); o[2].A = mca; o[2].B = mbc; o[2].Cc = Q.Cc;
+                        o[3].piece = pack_piece(ch[3]); o[3].A = mab; o[3].B = mbc; o[3].Cc = mca;
+                    } else {
+                        refine_serial<R, HELM, NPE>(X, xi, d, df, kk, a.tau, a.maxdepth, P, v);
+                    }
+                }
+                if (leaf) {
+                    const int p0 = tail + NQ * __popc(ml & lt);
+#pragma unroll
+                    for (int q = 0; q < NQ; q++) {
+                        R s, t, w;
+                        leaf_point<R>(P, q, s, t, w);
+                        const int k = (p0 + q) & (RING - 1);
+                        rs[k] = s; rt[k] = t; rw[k] = w;
+                    }
+                }
+                tail += NQ * __popc(ml);
+                nnext = min(QCAP, nnext + 4 * __popc(ms));
+                nnext -= nnext % 4;
+                __syncwarp(wmask);
+                for (; tail - head >= W; head += W) {
+                    const int k = (head + sl) & (RING - 1);
+                    eval_st<R, HELM, NPE>(d, kk, rs[k], rt[k], rw[k], v);
+                }
+                __syncwarp(wmask);                      // ring reads done before the next writes
+            }
+            QPiece *sw = cur; cur = nxt; nxt = sw;
+            ncur = nnext;
+        }
+        for (; tail - head > 0; head += W) {
+            const int k = (head + sl) & (RING - 1);
+            if (head + sl < tail) eval_st<R, HELM, NPE>(d, kk, rs[k], rt[k], rw[k], v);
+        }
+        reduce_store<R, HELM, NPE, W>(v, wmask, sl, pr, valD, valS, d0pair);
+    }
+}
+
+// kind of every special pair: 1 if the collocation node is a node of the element
+__global__ void k_pair_kind(int npairs, int npe, const int *__restrict__ pair_node, const int *__restrict__ pair_e,
+                            const int *__restrict__ el_phi, int *self) {
+    const int pr = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pr >= npairs) return;
+    const int node = pair_node[pr], e = pair_e[pr];
+    int f = 0;
+    for (int v = 0; v < npe; v++) f |= el_phi[(size_t)e * npe + v] == node;
+    self[pr] = f;
+}
+
+// stable partition of the pairs: self pairs to list[0 .. nself), the others after
+__global__ void k_pair_split(int npairs, const int *__restrict__ self, const int *__restrict__ off, int nself,
+                             int *list) {
+    const int pr = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pr >= npairs) return;
+    list[self[pr] ? off[pr] : nself + pr - off[pr]] = pr;
 }
 
 __global__ void k_pair_nodes(int N, const int *__restrict__ off, int *pair_node) {
@@ -955,15 +1020,45 @@ int build_correction(bem_plan *P, cudaStream_t s) {
     BEM_TRY(A.alloc(&K.fvalS, K.nnzS * C));
     (k_rows_ptr<<<(N + 256) / 256, 256, 0, s>>>(N, npe, off, K.ptrD), ::bem::count_launch());
     (k_corr_csr<<<(npairs + 255) / 256, 256, 0, s>>>(npairs, npe, pair_e, t.el_phi, t.el_chi, K.colD, K.colS), ::bem::count_launch());
+    // self pairs first, then the near-singular ones (stable), so that each kernel
+    // takes one kind
+    int *kind = nullptr, *koff = nullptr, *klist = nullptr, *ktot = nullptr, *kblk = nullptr;
+    BEM_TRY(A.alloc(&kind, std::max(1, npairs)));
+    BEM_TRY(A.alloc(&koff, std::max(1, npairs)));
+    BEM_TRY(A.alloc(&klist, std::max(1, npairs)));
+    BEM_TRY(A.alloc(&ktot, 1));
+    BEM_TRY(A.alloc(&kblk, scan_scratch(npairs)));
+    int nself = 0;
+    if (npairs > 0) {
+        (k_pair_kind<<<(npairs + 255) / 256, 256, 0, s>>>(npairs, npe, pair_node, pair_e, t.el_phi, kind),
+         ::bem::count_launch());
+        BEM_TRY(scan_exclusive(kind, koff, npairs, ktot, kblk, s));
+        BEM_CUDA(cudaMemcpyAsync(&nself, ktot, sizeof(int), cudaMemcpyDeviceToHost, s));
+        BEM_CUDA(cudaStreamSynchronize(s));
+        (k_pair_split<<<(npairs + 255) / 256, 256, 0, s>>>(npairs, kind, koff, nself, klist), ::bem::count_launch());
+    }
+    const int nnear = npairs - nself;
     {
         const bool mx = P->prm.precision == BEM_MIXED, helm = P->green == BEM_HELMHOLTZ;
-        // a grid-stride loop over pairs, but not a persistent grid: about
-        // SP_PAIRS_PER_WARP pairs per warp, so that blocks retire throughout and
-        // the diagonal's product (a stream of higher priority) gets SMs while
-        // the quadrature is still running
-        const int grid = (int)std::max<int64_t>(1, ((int64_t)npairs + SP_WARPS * SP_PAIRS_PER_WARP - 1) /
-                                                       (SP_WARPS * SP_PAIRS_PER_WARP));
-#define BEM_SW(R, H, NP) (k_special_pair<R, H, NP><<<grid, 32 * SP_WARPS, 0, s>>>(a, npairs, pair_node, pair_e, K.valD, K.valS, d0pair), ::bem::count_launch())
+        // grid-stride loops over the pair lists, but not persistent grids:
+        // about SP_PAIRS_PER_WARP pairs per warp or group, so that blocks retire
+        // throughout and the diagonal's product (a stream of higher priority)
+        // gets SMs while the quadrature is still running
+        const int gs = (int)std::max<int64_t>(1, ((int64_t)nself + SP_WARPS * SP_PAIRS_PER_WARP - 1) /
+                                                     (SP_WARPS * SP_PAIRS_PER_WARP));
+        const int gn = (int)std::max<int64_t>(1, ((int64_t)nnear + SPN_G * SP_PAIRS_PER_WARP - 1) /
+                                                     (SPN_G * SP_PAIRS_PER_WARP));
+#define BEM_SW(R, H, NP)                                                                                          \
+    do {                                                                                                          \
+        if (nnear > 0)                                                                                            \
+            (k_special_near<R, H, NP><<<gn, 32 * SPN_WARPS, 0, s>>>(a, nnear, klist + nself, pair_node, pair_e,    \
+                                                                    K.valD, K.valS, d0pair),                      \
+             ::bem::count_launch());                                                                              \
+        if (nself > 0)                                                                                            \
+            (k_special_self<R, H, NP><<<gs, 32 * SP_WARPS, 0, s>>>(a, nself, klist, pair_node, pair_e, K.valD,    \
+                                                                   K.valS, d0pair),                               \
+             ::bem::count_launch());                                                                              \
+    } while (0)
         if (npairs > 0) {
             if (npe == 3) {
                 if (mx) { if (helm) BEM_SW(float, true, 3); else BEM_SW(float, false, 3); }
@@ -985,7 +1080,7 @@ int build_correction(bem_plan *P, cudaStream_t s) {
     // is added by one Laplace double-layer product on phi = 1
     P->C = d0row;
     // the temporaries are released once the stream has finished with them
-    for (void *q : {(void *)cnt, (void *)tot, (void *)sblk, (void *)pair_node, (void *)d0pair, (void *)ecx, (void *)ecy, (void *)ecz,
+    for (void *q : {(void *)kind, (void *)koff, (void *)klist, (void *)ktot, (void *)kblk, (void *)cnt, (void *)tot, (void *)sblk, (void *)pair_node, (void *)d0pair, (void *)ecx, (void *)ecy, (void *)ecz,
                     (void *)eh, (void *)ebnd, (void *)frho, (void *)rho, (void *)off, (void *)pair_e})
         P->deferred.push_back(q);
     return BEM_OK;
