@@ -135,10 +135,9 @@ static int plan_setup(bem_plan *P, cudaStream_t s) {
     BEM_TRY(lap(1));
     BEM_TRY(build_geometry(P, s));
     BEM_TRY(build_radii_lists(P, s));
-    BEM_TRY(build_near_items(P));
     BEM_TRY(lap(2));
     // The special-pair correction (stream s) is enqueued first; the host then
-    // builds the M2L offset classes while it runs, enqueues the diagonal's
+    // builds the near-field work items and the M2L offset classes while it runs, enqueues the diagonal's
     // tables and product at the diagonal's order (s2), and builds the plan's
     // own order (alloc_fmm, its kernels on s) while both run.  The product
     // joins s before the diagonal adds the correction's row sums.  Stage times
@@ -159,8 +158,11 @@ static int plan_setup(bem_plan *P, cudaStream_t s) {
         cudaStreamSynchronize(s);
         return fin(rc);
     }
+    // host work in the shadow of the correction's kernels: the near-field work
+    // items, then the M2L offset classes (the lists were synchronised above)
     t0 = std::chrono::steady_clock::now();
-    rc = build_m2l_classes(P);
+    rc = build_near_items(P);
+    if (rc == BEM_OK) rc = build_m2l_classes(P);
     P->setup_ms[4] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (rc == BEM_OK) BEM_CUDA(cudaEventRecord(ev[2], s2));
     if (rc == BEM_OK) rc = diagonal_prepare(P, s2);

@@ -298,6 +298,7 @@ __device__ __forceinline__ int classify_pair(const CorrArgs &a, int node, const 
 // only adds candidates); elements pass a float32 rejection and then the
 // exact float64 classification.
 constexpr int SS_WARPS = 4, SS_STACK = 8 * 24;
+constexpr int SS_CAP = 192;         // special elements per node kept by the counting search
 
 __device__ __forceinline__ bool box_may_hold(const CorrArgs &a, int b, const float xf[3], float ax) {
     const float4 c = a.fbox[b];
@@ -306,7 +307,7 @@ __device__ __forceinline__ bool box_may_hold(const CorrArgs &a, int b, const flo
     return dx * dx + dy * dy + dz * dz <= lim * lim;
 }
 
-__device__ int find_special_warp(const CorrArgs &a, int node, int *out_e, int *stack) {
+__device__ int find_special_warp(const CorrArgs &a, int node, int *out_e, int *stack, int cap = 1 << 30) {
     const int lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu, lt = (1u << lane) - 1u;
     const double xi[3] = {a.nodes[3 * (size_t)node], a.nodes[3 * (size_t)node + 1], a.nodes[3 * (size_t)node + 2]};
@@ -343,19 +344,31 @@ __device__ int find_special_warp(const CorrArgs &a, int node, int *out_e, int *s
                 }
             }
             const unsigned m = __ballot_sync(FULL, hit);
-            if (out_e && hit) out_e[cnt + __popc(m & lt)] = e;
+            if (out_e && hit && cnt + __popc(m & lt) < cap) out_e[cnt + __popc(m & lt)] = e;
             cnt += __popc(m);
         }
     }
     return cnt;
 }
 
-__global__ void __launch_bounds__(32 * SS_WARPS) k_special_count(CorrArgs a, int *cnt) {
+// Counts every node's special pairs and keeps the first `cap` of their
+// elements in tmp[node * cap ...]; *overflow is set when a node has more.
+__global__ void __launch_bounds__(32 * SS_WARPS) k_special_count(CorrArgs a, int *cnt, int *tmp, int cap,
+                                                                int *overflow) {
     __shared__ int stack[SS_WARPS][SS_STACK];
     const int w = threadIdx.x >> 5, i = blockIdx.x * SS_WARPS + w;
     if (i >= a.N) return;                              // uniform within the warp
-    const int c = find_special_warp(a, i, nullptr, stack[w]);
-    if ((threadIdx.x & 31) == 0) cnt[i] = c;
+    const int c = find_special_warp(a, i, tmp + (size_t)i * cap, stack[w], cap);
+    if ((threadIdx.x & 31) == 0) {
+        cnt[i] = c;
+        if (c > cap) atomicOr(overflow, 1);
+    }
+}
+
+// the kept elements of every node into the pair list at the node's offset
+__global__ void k_special_copy(int N, const int *__restrict__ off, const int *__restrict__ tmp, int cap, int *pair_e) {
+    const int i = blockIdx.x, n = off[i + 1] - off[i];
+    for (int j = threadIdx.x; j < n; j += blockDim.x) pair_e[off[i] + j] = tmp[(size_t)i * cap + j];
 }
 
 __global__ void __launch_bounds__(32 * SS_WARPS) k_special_write(CorrArgs a, const int *__restrict__ off, int *pair_e) {
@@ -986,20 +999,28 @@ int build_correction(bem_plan *P, cudaStream_t s) {
     int *cnt, *off, *tot;
     BEM_TRY(A.alloc(&cnt, N + 1));
     BEM_TRY(A.alloc(&off, N + 1));
-    BEM_TRY(A.alloc(&tot, 1));
+    BEM_TRY(A.alloc(&tot, 2));
     int *sblk = nullptr;
     BEM_TRY(A.alloc(&sblk, scan_scratch(N + 1)));
+    // one search: the count pass keeps up to SS_CAP elements per node, which
+    // are copied into place; a node with more makes the search run again
+    int *ptmp = nullptr;
+    BEM_TRY(A.alloc(&ptmp, (size_t)N * SS_CAP));
     BEM_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (N + 1), s));
-    (k_special_count<<<(N + SS_WARPS - 1) / SS_WARPS, 32 * SS_WARPS, 0, s>>>(a, cnt), ::bem::count_launch());
+    BEM_CUDA(cudaMemsetAsync(tot + 1, 0, sizeof(int), s));
+    (k_special_count<<<(N + SS_WARPS - 1) / SS_WARPS, 32 * SS_WARPS, 0, s>>>(a, cnt, ptmp, SS_CAP, tot + 1),
+     ::bem::count_launch());
     BEM_LAUNCH_CHECK();
     BEM_TRY(scan_exclusive(cnt, off, N + 1, tot, sblk, s));
-    int npairs = 0;
-    BEM_CUDA(cudaMemcpyAsync(&npairs, tot, sizeof(int), cudaMemcpyDeviceToHost, s));
+    int hcnt[2] = {0, 0};
+    BEM_CUDA(cudaMemcpyAsync(hcnt, tot, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
     BEM_CUDA(cudaStreamSynchronize(s));
+    const int npairs = hcnt[0];
     int *pair_e, *pair_node;
     BEM_TRY(A.alloc(&pair_e, npairs));
     BEM_TRY(A.alloc(&pair_node, npairs));
-    (k_special_write<<<(N + SS_WARPS - 1) / SS_WARPS, 32 * SS_WARPS, 0, s>>>(a, off, pair_e), ::bem::count_launch());
+    if (hcnt[1]) (k_special_write<<<(N + SS_WARPS - 1) / SS_WARPS, 32 * SS_WARPS, 0, s>>>(a, off, pair_e), ::bem::count_launch());
+    else (k_special_copy<<<N, 64, 0, s>>>(N, off, ptmp, SS_CAP, pair_e), ::bem::count_launch());
     (k_pair_nodes<<<(N + 255) / 256, 256, 0, s>>>(N, off, pair_node), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
     const int C = P->green == BEM_HELMHOLTZ ? 2 : 1;
@@ -1080,7 +1101,7 @@ int build_correction(bem_plan *P, cudaStream_t s) {
     // is added by one Laplace double-layer product on phi = 1
     P->C = d0row;
     // the temporaries are released once the stream has finished with them
-    for (void *q : {(void *)kind, (void *)koff, (void *)klist, (void *)ktot, (void *)kblk, (void *)cnt, (void *)tot, (void *)sblk, (void *)pair_node, (void *)d0pair, (void *)ecx, (void *)ecy, (void *)ecz,
+    for (void *q : {(void *)ptmp, (void *)kind, (void *)koff, (void *)klist, (void *)ktot, (void *)kblk, (void *)cnt, (void *)tot, (void *)sblk, (void *)pair_node, (void *)d0pair, (void *)ecx, (void *)ecy, (void *)ecz,
                     (void *)eh, (void *)ebnd, (void *)frho, (void *)rho, (void *)off, (void *)pair_e})
         P->deferred.push_back(q);
     return BEM_OK;

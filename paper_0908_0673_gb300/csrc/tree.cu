@@ -656,7 +656,7 @@ __global__ void k_box_floats(int nbox, const double *__restrict__ cx, const doub
 // Walks the parent's near list for box b; when `write`, stores the entries.
 // Returns the (near, interaction) counts.  A small explicit stack opens
 // non-leaf entries for a leaf b when leaf_descend is on.
-__device__ int2 walk_lists(const ListArgs &a, int b, bool write, int *near_out, int *inter_out) {
+__device__ int2 walk_lists(const ListArgs &a, int b, bool write, int *near_out, int *inter_out, int cap = 1 << 30) {
     int nn = 0, ni = 0;
     int p = a.parent[b];
     bool bleaf = a.nchild[b] == 0;
@@ -672,12 +672,12 @@ __device__ int2 walk_lists(const ListArgs &a, int b, bool write, int *near_out, 
         while (sp > 0) {
             int C = stack[--sp];
             if (separated(a, b, C)) {
-                if (write) inter_out[ni] = C;
+                if (write && ni < cap) inter_out[ni] = C;
                 ni++;
             } else if (bleaf && a.leaf_descend && a.nchild[C] != 0) {
                 for (int c = a.child0[C] + a.nchild[C] - 1; c >= a.child0[C]; c--) stack[sp++] = c;
             } else {
-                if (write) near_out[nn] = C;
+                if (write && nn < cap) near_out[nn] = C;
                 nn++;
             }
         }
@@ -685,12 +685,32 @@ __device__ int2 walk_lists(const ListArgs &a, int b, bool write, int *near_out, 
     return make_int2(nn, ni);
 }
 
-__global__ void k_lists_count(ListArgs a, int off, int cnt, int *cnear, int *cinter) {
+// Counts every box's entries and keeps the first `cap` of each list in
+// tnear / tinter[j * cap ...]; *overflow is set when a list is longer.
+__global__ void k_lists_count(ListArgs a, int off, int cnt, int *cnear, int *cinter, int *tnear, int *tinter, int cap,
+                              int *overflow) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= cnt) return;
-    int2 c = walk_lists(a, off + j, false, nullptr, nullptr);
+    int2 c = walk_lists(a, off + j, true, tnear + (size_t)j * cap, tinter + (size_t)j * cap, cap);
     cnear[j] = c.x;
     cinter[j] = c.y;
+    if (c.x > cap || c.y > cap) atomicOr(overflow, 1);
+}
+
+// the kept lists into place, with their pointers
+__global__ void k_lists_copy(int off, int cnt, const int *__restrict__ onear, const int *__restrict__ ointer,
+                             const int *__restrict__ cnear, const int *__restrict__ cinter, const int *__restrict__ tnear,
+                             const int *__restrict__ tinter, int cap, int near_base, int inter_base, int *near_ptr,
+                             int *near_idx, int *inter_ptr, int *inter_idx) {
+    const int j = blockIdx.x;
+    if (threadIdx.x == 0) {
+        near_ptr[off + j] = near_base + onear[j];
+        inter_ptr[off + j] = inter_base + ointer[j];
+    }
+    for (int i = threadIdx.x; i < cnear[j]; i += blockDim.x)
+        near_idx[near_base + onear[j] + i] = tnear[(size_t)j * cap + i];
+    for (int i = threadIdx.x; i < cinter[j]; i += blockDim.x)
+        inter_idx[inter_base + ointer[j] + i] = tinter[(size_t)j * cap + i];
 }
 
 __global__ void k_lists_write(ListArgs a, int off, int cnt, const int *__restrict__ onear, const int *__restrict__ ointer,
@@ -745,9 +765,15 @@ int build_radii_lists(bem_plan *P, cudaStream_t s) {
     BEM_TRY(A.alloc(&ci, maxcnt));
     BEM_TRY(A.alloc(&on, maxcnt));
     BEM_TRY(A.alloc(&oi, maxcnt));
-    BEM_TRY(A.alloc(&tot, 2));
+    BEM_TRY(A.alloc(&tot, 3));
     int *sblk = nullptr;
     BEM_TRY(A.alloc(&sblk, scan_scratch(maxcnt)));
+    // one walk per level: up to LIST_CAP entries of each list are kept by the
+    // counting walk and copied into place; a longer list makes the level walk again
+    constexpr int LIST_CAP = 256;
+    int *tn = nullptr, *ti = nullptr;
+    BEM_TRY(A.alloc(&tn, (size_t)maxcnt * LIST_CAP));
+    BEM_TRY(A.alloc(&ti, (size_t)maxcnt * LIST_CAP));
     for (int l = 1; l < t.nlev; l++) {
         int off = t.lev_off[l], cnt = t.lev_off[l + 1] - off;
         ListArgs a{t.parent, t.child0, t.nchild, t.cx, t.cy, t.cz, t.r, t.near_ptr, near_idx, P->prm.eta,
@@ -755,18 +781,24 @@ int build_radii_lists(bem_plan *P, cudaStream_t s) {
         // level l-1 pointers must be closed for the walk: ptr[off] = running total
         (k_close_ptr<<<1, 1, 0, s>>>(t.near_ptr, off, nnear), ::bem::count_launch());
         (k_close_ptr<<<1, 1, 0, s>>>(t.inter_ptr, off, ninter), ::bem::count_launch());
-        (k_lists_count<<<(cnt + 127) / 128, 128, 0, s>>>(a, off, cnt, cn, ci), ::bem::count_launch());
+        BEM_CUDA(cudaMemsetAsync(tot + 2, 0, sizeof(int), s));
+        (k_lists_count<<<(cnt + 127) / 128, 128, 0, s>>>(a, off, cnt, cn, ci, tn, ti, LIST_CAP, tot + 2),
+         ::bem::count_launch());
         BEM_LAUNCH_CHECK();
         BEM_TRY(scan_exclusive(cn, on, cnt, tot, sblk, s));
         BEM_TRY(scan_exclusive(ci, oi, cnt, tot + 1, sblk, s));
-        int h[2];
-        BEM_CUDA(cudaMemcpyAsync(h, tot, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+        int h[3];
+        BEM_CUDA(cudaMemcpyAsync(h, tot, sizeof(int) * 3, cudaMemcpyDeviceToHost, s));
         BEM_CUDA(cudaStreamSynchronize(s));
         BEM_TRY(grow(A, &near_idx, capn, (size_t)nnear + h[0], (size_t)nnear, s));
         BEM_TRY(grow(A, &inter_idx, capi, (size_t)ninter + h[1], (size_t)ninter, s));
         a.pnear_idx = near_idx;
-        (k_lists_write<<<(cnt + 127) / 128, 128, 0, s>>>(a, off, cnt, on, oi, nnear, ninter, t.near_ptr, near_idx,
-                                                        t.inter_ptr, inter_idx), ::bem::count_launch());
+        if (h[2])
+            (k_lists_write<<<(cnt + 127) / 128, 128, 0, s>>>(a, off, cnt, on, oi, nnear, ninter, t.near_ptr, near_idx,
+                                                            t.inter_ptr, inter_idx), ::bem::count_launch());
+        else
+            (k_lists_copy<<<cnt, 64, 0, s>>>(off, cnt, on, oi, cn, ci, tn, ti, LIST_CAP, nnear, ninter, t.near_ptr,
+                                             near_idx, t.inter_ptr, inter_idx), ::bem::count_launch());
         BEM_LAUNCH_CHECK();
         nnear += h[0];
         ninter += h[1];
@@ -784,6 +816,8 @@ int build_radii_lists(bem_plan *P, cudaStream_t s) {
     A.release(on);
     A.release(oi);
     A.release(sblk);
+    A.release(tn);
+    A.release(ti);
     return BEM_OK;
 }
 
