@@ -49,8 +49,11 @@ FLOPS_PER_PAIR = {"A": 20.0, "B": 11.0}   # near-field kernel, Laplace double / 
 # capture of this workload (the command is in profiles/); reported while the
 # kernel's source file is unchanged, null otherwise.
 NCU_TRAFFIC = {
-    "near_l2p": {"bytes": 7452416, "source": "paper_0908_0673_gb300/csrc/fmm.cu", "sha256": "173cd193ac20e8439aaf4fd9ac54a1a9ae5f0f2e9e1a84e674e87b3dda544e91"},
-    "m2l": {"bytes": 3144192 + 63385088, "source": "paper_0908_0673_gb300/csrc/m2l_tc.cu", "sha256": "e4c4bb902cb967f898ab6712d1658221a2ed512f15070c907ca4575ba8546233"},
+    "near_l2p": {"bytes": 7522432, "source": "paper_0908_0673_gb300/csrc/fmm.cu",
+                 "sha256": "61ffd3ebdc7ecca8f1e00da4cd3385a1d6d6c14540f48640289d1a999b7e8bd2"},
+    # the M2L stage: k_m2l_permute + k_m2l_tc + k_m2l_gather_sym
+    "m2l": {"bytes": 1216588 + 80498176 + 123093964, "source": "paper_0908_0673_gb300/csrc/m2l_tc.cu",
+            "sha256": "4fb25e7900c934069f0c3806f4e026e920f1de9e46584fd02dd58c4e9da3f3df"},
 }
 
 
@@ -617,7 +620,8 @@ def main():
                       "peak_source": "TF32 = 0.5 x measured BF16 (MEASURED_PEAKS.json, nominal ratio)",
                       "achieved_algorithmic": alg, "frac_algorithmic": alg / tf32,
                       "achieved_issued": issued, "frac_issued": issued / tf32,
-                      "stage_ms": stages["m2l"], "traffic": ncu_traffic("m2l"), "traffic_unit": "bytes per launch",
+                      "stage_ms": stages["m2l"], "traffic": ncu_traffic("m2l"),
+                      "traffic_unit": "DRAM bytes per M2L stage (permute + tcgen05 + gather launches)",
                       "work": f"{st['n_inter']} pairs x 2 x C(16,6) algorithmic; x 3 x {tc_issued_macs(10)} MACs issued"}
 
     # end to end through the public API from pinned host buffers
