@@ -104,6 +104,10 @@ def parse():
     ap.add_argument("--group-max-rhs", type=int, default=3)
     ap.add_argument("--serve-requests", type=int, default=8, help="requests in the serving stream (0: skip)")
     ap.add_argument("--serve-max-elems", type=int, default=20000, help="largest mesh of the serving stream")
+    ap.add_argument("--serve-kmax", type=float, default=4.0, help="largest Helmholtz wavenumber of the serving stream")
+    ap.add_argument("--group-kmax", type=float, default=4.0, help="largest Helmholtz wavenumber of the grouped instances")
+    ap.add_argument("--only", default="", choices=["", "grouped", "serving"],
+                    help="run one section alone and print its JSON (not the benchmark line)")
     return ap.parse_args()
 
 
@@ -379,11 +383,11 @@ def serving(args):
     from paper_0908_0673_gb300 import bem
     from paper_0908_0673_gb300.serve import CudaEngine, Server, summarize, synthetic_stream
     reqs = synthetic_stream(args.serve_requests, rate_per_s=200.0, elems=(1000, args.serve_max_elems),
-                            k_range=(1.0, 4.0), rhs=(1, 8), seed=0)
+                            k_range=(1.0, args.serve_kmax), rhs=(1, 8), seed=0)
     out = {"stream": {"requests": len(reqs), "arrivals": "Poisson, 200 /s, seed 0",
                       "elements": f"log-uniform 1000-{args.serve_max_elems}, 6-node triangles",
                       "geometry": "geodesic sphere | ellipsoid (axes U[0.5,2]) | graded cube",
-                      "green": "50% Laplace, 50% Helmholtz k U[1,4]", "rhs": "1-8 interior point sources",
+                      "green": f"50% Laplace, 50% Helmholtz k U[1,{args.serve_kmax:g}]", "rhs": "1-8 interior point sources",
                       "total_solves": sum(len(r.rhs) for r in reqs)}}
     phis = {}
     for name, prec, slots, threads in (("mixed_continuous", bem.BEM_MIXED, 8, 2),
@@ -432,7 +436,7 @@ def grouped(args):
             m = I.geodesic(max(2, int(round(math.sqrt(E / 20.0)))), I.TRI6, axes=axes)
             rmax = 0.3 * min(axes)
         helm = rng.uniform() < 0.5
-        k = float(rng.uniform(1.0, 4.0)) if helm else 0.0
+        k = float(rng.uniform(1.0, args.group_kmax)) if helm else 0.0
         nr = int(rng.integers(1, args.group_max_rhs + 1))
         srcs = []
         for _ in range(nr):
@@ -478,13 +482,14 @@ def grouped(args):
     torch.cuda.synchronize()
     t_first = time.perf_counter() - t0
     t0 = time.perf_counter()
-    iters, launches = [], 0
+    iters, launches, nconv = [], 0, 0
     for r in range(nrhs_max):
         chis = [ch[r] if r < len(ch) else None for *_, ch in mx]
         outs = [p[r] if r < len(p) else None for p in phis_g]
         code, infos, nl = bem.bem_group_solve(group, chis, outs, sp)
         launches += nl
         iters += [inf.iters for inf, c in zip(infos, chis) if c is not None]
+        nconv += sum(1 for inf, c in zip(infos, chis) if c is not None and inf.status != bem.BEM_OK)
     torch.cuda.synchronize()
     t_group = time.perf_counter() - t0
     # the same solves one at a time
@@ -516,13 +521,15 @@ def grouped(args):
             bem.bem_mesh_destroy(mh)
     bem.bem_ctx_destroy(ctx)
     return {"instances": n_inst, "elements": f"uniform {args.group_min_elems}-{args.group_max_elems}, 6-node triangles",
-            "geometry": "geodesic sphere | ellipsoid (axes U[0.5,2]) | graded cube", "green": "50% Laplace, 50% Helmholtz k U[1,4]",
+            "geometry": "geodesic sphere | ellipsoid (axes U[0.5,2]) | graded cube",
+            "green": f"50% Laplace, 50% Helmholtz k U[1,{args.group_kmax:g}]",
             "rhs": f"1-{args.group_max_rhs} interior point sources", "total_solves": total,
             "total_elements": int(sum(s[0].n_elems for s in insts)),
             "build_s": t_build, "first_call_with_capture_s": t_first,
             "group": {"solves_per_s": total / t_group, "seconds": t_group, "graph_kernels": int(launches)},
             "one_at_a_time": {"solves_per_s": total / t_single, "seconds": t_single},
             "speedup": t_single / t_group, "gmres_iters_mean": float(np.mean(iters)),
+            "gmres_iters_max": int(max(iters)), "not_converged": int(nconv),
             "rel_err_vs_own_f64": {"max": max(errs), "within_1e-5": int(sum(e <= 1e-5 for e in errs)), "solves": len(errs),
                                    "worst": worst}}
 
@@ -531,6 +538,11 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps(grouped(args) if args.only == "grouped" else serving(args)))
+        return
     import torch
     import torch.distributed as dist
     from paper_0908_0673_gb300 import bem
