@@ -1,0 +1,63 @@
+"""The high-wavenumber limit of the Cartesian Taylor expansions (Section 3.3),
+settled by the oracle: tests/golden/highk_sweep.json holds the error of the
+oracle's four-step fast product (op A, Helmholtz double layer) against its
+direct product on the level-4 geodesic sphere of 6-node triangles, leaf size
+128, over ka, the separation factor eta and the order p (written by
+oracle/highk_sweep.py, which calls only the oracle).
+
+Conclusions pinned here (they fix the readings the GPU tests and the streams
+use): the error falls with p and with eta at fixed ka and grows with ka; the
+configs' 1e-6 product bar is met at ka = 2 from p = 10 (eta = 2), is not met at
+ka = 8 by any p <= 16, eta <= 3 on boxes this large (the level-6 sphere's boxes,
+four times smaller across, meet it at p = 16), and at ka = 16 the expansions
+do not converge at all on these boxes (errors of order one); the oracle still
+reproduces a stored entry."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+TABLE = os.path.join(ROOT, "tests", "golden", "highk_sweep.json")
+
+
+def _table():
+    with open(TABLE) as f:
+        d = json.load(f)
+    return d, {(r["ka"], r["eta"], r["p"]): r["rel_err"] for r in d["runs"]}
+
+
+def test_sweep_conclusions():
+    d, e = _table()
+    assert d["elements"] == 5120 and d["leaf_size"] == 128
+    for ka in (2.0, 8.0):
+        for eta in (2.0, 3.0):
+            errs = [e[(ka, eta, p)] for p in (8, 10, 12, 16)]
+            assert all(a > b for a, b in zip(errs, errs[1:])), (ka, eta, errs)       # falls with p
+        for p in (8, 10, 12, 16):
+            assert e[(ka, 3.0, p)] < e[(ka, 2.0, p)]                                # falls with eta
+    for eta in (2.0, 3.0):
+        for p in (8, 10, 12, 16):
+            assert e[(2.0, eta, p)] < e[(8.0, eta, p)] < e[(16.0, eta, p)]         # grows with ka
+    assert e[(2.0, 2.0, 10)] <= 1e-6 and e[(2.0, 2.0, 8)] > 1e-7
+    assert min(e[(8.0, eta, p)] for eta in (2.0, 3.0) for p in (8, 10, 12, 16)) > 1e-6
+    assert min(e[(16.0, eta, p)] for eta in (2.0, 3.0) for p in (8, 10, 12, 16)) > 0.1
+
+
+def test_oracle_reproduces_a_stored_entry(oracle_lib):
+    """ka = 2, eta = 2, p = 8 recomputed (about 20 s on 8 cores)."""
+    from paper_0908_0673_gb300 import inputs as I
+    O = oracle_lib
+    _, e = _table()
+    m = I.icosphere(4, I.TRI6)
+    ci, n_chi = O.chi_index(m.nodes, m.elems)
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(m.n_nodes) + 1j * rng.standard_normal(m.n_nodes)
+    _, _, d0 = O.assemble(m.nodes, m.elems, ci, n_chi, rows=np.arange(m.n_nodes))
+    ref = O.apply_rows(m.nodes, m.elems, ci, O.OP_A, x, None, green=O.HELMHOLTZ, k=2.0)
+    corr = O.correction(m.nodes, m.elems, ci, green=O.HELMHOLTZ, k=2.0)
+    T = O.Tree(m.nodes, m.elems, B=128, eta=2.0)
+    y = O.fmm_apply(T, ci, O.OP_A, x, d0, corr, 8, green=O.HELMHOLTZ, k=2.0)
+    err = float(np.linalg.norm(y - ref) / np.linalg.norm(ref))
+    assert err == pytest.approx(e[(2.0, 2.0, 8)], rel=1e-6)
