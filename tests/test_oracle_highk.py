@@ -8,8 +8,8 @@ oracle/highk_sweep.py, which calls only the oracle).
 Conclusions pinned here (they fix the readings the GPU tests and the streams
 use): the error falls with p and with eta at fixed ka and grows with ka; the
 configs' 1e-6 product bar is met at ka = 2 from p = 10 (eta = 2), is not met at
-ka = 8 by any p <= 16, eta <= 3 on boxes this large (the level-6 sphere's boxes,
-four times smaller across, meet it at p = 16), and at ka = 16 the expansions
+ka = 8 by any p <= 16, eta <= 3 on boxes this large (the level-6 sphere's
+smaller leaf boxes meet it at p = 16), and at ka = 16 the expansions
 do not converge at all on these boxes (errors of order one); the oracle still
 reproduces a stored entry."""
 import json
