@@ -41,6 +41,28 @@ constexpr int QBITS = 21;   // Morton bits per axis
 constexpr int PMAX = 20;    // largest supported expansion order
 constexpr int NQ = 7;       // regular quadrature points per element
 
+// Radon's 7-point degree-5 rule on the reference triangle (Stroud T2:5-1),
+// point q in owner order: the centroid with weight 9/80, then two orbits,
+// a = (6 - sqrt15)/21, b = (9 + 2 sqrt15)/21 with weight (155 - sqrt15)/2400
+// and c = (6 + sqrt15)/21, d = (9 - 2 sqrt15)/21 with weight (155 + sqrt15)/2400
+// (weights sum to 1/2).  The one definition both the geometry tables and the
+// field evaluator use.
+__host__ __device__ inline void radon7(int q, double &s, double &t, double &w) {
+    const double r15 = 3.872983346207417;   // sqrt(15), correctly rounded
+    const double a = (6.0 - r15) / 21.0, b = (9.0 + 2.0 * r15) / 21.0;
+    const double c = (6.0 + r15) / 21.0, d = (9.0 - 2.0 * r15) / 21.0;
+    const double wa = (155.0 - r15) / 2400.0, wc = (155.0 + r15) / 2400.0;
+    switch (q) {
+    case 0: s = 1.0 / 3.0; t = 1.0 / 3.0; w = 9.0 / 80.0; break;
+    case 1: s = a; t = a; w = wa; break;
+    case 2: s = b; t = a; w = wa; break;
+    case 3: s = a; t = b; w = wa; break;
+    case 4: s = c; t = c; w = wc; break;
+    case 5: s = d; t = c; w = wc; break;
+    default: s = c; t = d; w = wc; break;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // device buffers owned by a plan
 // ---------------------------------------------------------------------------

@@ -97,23 +97,6 @@ __device__ __forceinline__ void field_point(const FieldArgs &a, const double *x,
     }
 }
 
-// Radon's degree-5 rule on the reference triangle (weights sum to 1/2)
-__device__ __forceinline__ void rule7(int q, double &s, double &t, double &w) {
-    const double r15 = 3.872983346207417;
-    const double A = (6.0 - r15) / 21.0, B = (9.0 + 2.0 * r15) / 21.0, Cc = (6.0 + r15) / 21.0,
-                 D = (9.0 - 2.0 * r15) / 21.0;
-    const double wa = (155.0 - r15) / 2400.0, wc = (155.0 + r15) / 2400.0;
-    switch (q) {
-    case 0: s = 1.0 / 3.0; t = 1.0 / 3.0; w = 9.0 / 80.0; break;
-    case 1: s = A; t = A; w = wa; break;
-    case 2: s = B; t = A; w = wa; break;
-    case 3: s = A; t = B; w = wa; break;
-    case 4: s = Cc; t = Cc; w = wc; break;
-    case 5: s = D; t = Cc; w = wc; break;
-    default: s = Cc; t = D; w = wc; break;
-    }
-}
-
 __device__ __forceinline__ void map_param(const FieldArgs &a, const double *X, double s, double t, double *y) {
     double N[6], Ns[6], Nt[6];
     shape6(a.npe, s, t, N, Ns, Nt);
@@ -162,7 +145,7 @@ __device__ void field_element(const FieldArgs &a, const double *x, int e, double
             const double det = fabs((pb[0] - pa[0]) * (pc[1] - pa[1]) - (pb[1] - pa[1]) * (pc[0] - pa[0]));
             for (int q = 0; q < 7; q++) {
                 double s, t, w;
-                rule7(q, s, t, w);
+                radon7(q, s, t, w);
                 field_point<C>(a, x, X, ph, ch, pa[0] + s * (pb[0] - pa[0]) + t * (pc[0] - pa[0]),
                                pa[1] + s * (pb[1] - pa[1]) + t * (pc[1] - pa[1]), w * det, acc);
             }

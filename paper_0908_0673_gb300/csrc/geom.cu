@@ -28,19 +28,9 @@ struct Rule7 {
     double s[7], t[7], w[7];
 };
 
-// Radon's rule (Stroud T2:5-1): centroid weight 9/80, two orbits with
-// a = (6 - sqrt15)/21, b = (9 + 2 sqrt15)/21, weight (155 - sqrt15)/2400 and
-// c = (6 + sqrt15)/21, d = (9 - 2 sqrt15)/21, weight (155 + sqrt15)/2400.
 static Rule7 make_rule7() {
     Rule7 r;
-    const double q = std::sqrt(15.0);
-    const double a = (6.0 - q) / 21.0, b = (9.0 + 2.0 * q) / 21.0;
-    const double c = (6.0 + q) / 21.0, d = (9.0 - 2.0 * q) / 21.0;
-    const double wa = (155.0 - q) / 2400.0, wc = (155.0 + q) / 2400.0;
-    const double S[7] = {1.0 / 3.0, a, b, a, c, d, c};
-    const double T[7] = {1.0 / 3.0, a, a, b, c, c, d};
-    const double W[7] = {9.0 / 80.0, wa, wa, wa, wc, wc, wc};
-    for (int i = 0; i < 7; i++) { r.s[i] = S[i]; r.t[i] = T[i]; r.w[i] = W[i]; }
+    for (int q = 0; q < NQ; q++) radon7(q, r.s[q], r.t[q], r.w[q]);
     return r;
 }
 
