@@ -106,6 +106,10 @@ def parse():
     ap.add_argument("--serve-max-elems", type=int, default=20000, help="largest mesh of the serving stream")
     ap.add_argument("--serve-kmax", type=float, default=4.0, help="largest Helmholtz wavenumber of the serving stream")
     ap.add_argument("--group-kmax", type=float, default=4.0, help="largest Helmholtz wavenumber of the grouped instances")
+    ap.add_argument("--group-f64-rhs", type=int, default=1,
+                    help="right-hand sides per grouped instance checked against its float64 solution")
+    ap.add_argument("--serve-f64-max-elems", type=int, default=30000,
+                    help="largest request of the float64 comparison stream (the subset served by both forms)")
     ap.add_argument("--only", default="", choices=["", "grouped", "serving"],
                     help="run one section alone and print its JSON (not the benchmark line)")
     return ap.parse_args()
@@ -389,27 +393,38 @@ def serving(args):
                       "geometry": "geodesic sphere | ellipsoid (axes U[0.5,2]) | graded cube",
                       "green": f"50% Laplace, 50% Helmholtz k U[1,{args.serve_kmax:g}]", "rhs": "1-8 interior point sources",
                       "total_solves": sum(len(r.rhs) for r in reqs)}}
+    # the whole stream in the mixed form; then the requests up to
+    # serve_f64_max_elems elements (same arrival times) in both forms, for the
+    # float64 comparison and the speedup on a common set
+    sub = [r for r in reqs if r.mesh.n_elems <= args.serve_f64_max_elems]
+    out["comparison_subset"] = {"requests": len(sub), "max_elems": args.serve_f64_max_elems,
+                                "solves": sum(len(r.rhs) for r in sub)}
     phis = {}
-    for name, prec, slots, threads in (("mixed_continuous", bem.BEM_MIXED, 8, 2),
-                                       ("f64_one_at_a_time", bem.BEM_F64, 1, 1)):
+    for name, prec, slots, threads, stream in (("mixed_continuous", bem.BEM_MIXED, 8, 2, reqs),
+                                               ("mixed_subset", bem.BEM_MIXED, 8, 2, sub),
+                                               ("f64_one_at_a_time", bem.BEM_F64, 1, 1, sub)):
+        if not stream or (name == "mixed_subset" and len(sub) == len(reqs)):
+            continue
         eng = CudaEngine(precision=prec, max_slots=slots)
         try:
-            res = Server(eng, max_inflight=slots, setup_threads=threads, keep_phi=True).run(reqs)
+            res = Server(eng, max_inflight=slots, setup_threads=threads, keep_phi=True).run(stream)
         finally:
             eng.close()
         out[name] = summarize(res)
+        out[name]["largest_served_elems"] = max((r.n_elems for r in res if r.status in ("ok", "noconv")), default=0)
         phis[name] = {r.rid: r.phi for r in res if r.phi is not None}
     errs = []
-    for rid, ph in phis["mixed_continuous"].items():
-        ref = phis["f64_one_at_a_time"].get(rid)
+    for rid, ph in phis.get("mixed_continuous", {}).items():
+        ref = phis.get("f64_one_at_a_time", {}).get(rid)
         if ref is None:
             continue
         for a, b in zip(ph, ref):
             errs.append(float(np.linalg.norm(a - b) / np.linalg.norm(b)))
     out["rel_err_vs_f64"] = {"max": max(errs) if errs else None,
                              "within_1e-5": int(sum(e <= 1e-5 for e in errs)), "solves": len(errs)}
-    mx, f64 = out["mixed_continuous"], out["f64_one_at_a_time"]
-    out["speedup_solves_per_s"] = mx["solves_per_s"] / f64["solves_per_s"]
+    mx_sub = out.get("mixed_subset", out["mixed_continuous"] if len(sub) == len(reqs) else None)
+    if mx_sub is not None and "f64_one_at_a_time" in out:
+        out["speedup_solves_per_s"] = mx_sub["solves_per_s"] / out["f64_one_at_a_time"]["solves_per_s"]
     return out
 
 
@@ -501,24 +516,28 @@ def grouped(args):
     torch.cuda.synchronize()
     t_single = time.perf_counter() - t0
     bem.bem_group_destroy(group)
-    # float64 references, one at a time (not timed)
+    # float64 references (not timed): the first group_f64_rhs right-hand sides
+    # of every instance, each instance's float64 plan built and released in turn
+    for mh, pl, _, _ in mx:
+        bem.bem_plan_destroy(pl)
     errs, worst = [], []
-    f64, _ = build(bem.BEM_F64)
-    for i, ((mh, pl, npp, ch), g) in enumerate(zip(f64, phis_g)):
-        for c, pg in zip(ch, g):
+    for i, (mh, _, npp, ch) in enumerate(mx):
+        m, green, k, _s = insts[i]
+        prm = tune.choose(m.n_elems, green, bem.BEM_MIXED)
+        prm["precision"] = bem.BEM_F64
+        pl = bem.bem_plan_create(mh, green, k, bem.bem_fmm_params_default(**prm))
+        for c, pg in list(zip(ch, phis_g[i]))[:max(0, args.group_f64_rhs)]:
             out = torch.empty(npp, device="cuda", dtype=c.dtype)
             bem.bem_solve(pl, c, out, 1, sp)
             a, b = pg.cpu().numpy(), out.cpu().numpy()
             errs.append(float(np.linalg.norm(a - b) / np.linalg.norm(b)))
-            m, green, k, _s = insts[i]
             worst.append((errs[-1], {"instance": i, "mesh": m.name, "elements": int(m.n_elems),
                                      "green": "helmholtz" if green == bem.BEM_HELMHOLTZ else "laplace", "k": k,
                                      "rel_err": errs[-1]}))
+        bem.bem_plan_destroy(pl)
     worst = [w for _, w in sorted(worst, key=lambda t: -t[0])[:4]]
-    for lst in (mx, f64):
-        for mh, pl, _, _ in lst:
-            bem.bem_plan_destroy(pl)
-            bem.bem_mesh_destroy(mh)
+    for mh, _, _, _ in mx:
+        bem.bem_mesh_destroy(mh)
     bem.bem_ctx_destroy(ctx)
     return {"instances": n_inst, "elements": f"uniform {args.group_min_elems}-{args.group_max_elems}, 6-node triangles",
             "geometry": "geodesic sphere | ellipsoid (axes U[0.5,2]) | graded cube",
@@ -531,6 +550,7 @@ def grouped(args):
             "speedup": t_single / t_group, "gmres_iters_mean": float(np.mean(iters)),
             "gmres_iters_max": int(max(iters)), "not_converged": int(nconv),
             "rel_err_vs_own_f64": {"max": max(errs), "within_1e-5": int(sum(e <= 1e-5 for e in errs)), "solves": len(errs),
+                                   "checked": f"first {args.group_f64_rhs} right-hand side(s) of every instance",
                                    "worst": worst}}
 
 

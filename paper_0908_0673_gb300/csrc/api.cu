@@ -4,8 +4,11 @@
 #include <atomic>
 #include <chrono>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstring>
 #include <new>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "bem_internal.cuh"
@@ -104,6 +107,7 @@ static int validate_params(const bem_fmm_params &p) {
 static int plan_setup(bem_plan *P, cudaStream_t s) {
     bem_mesh *m = P->mesh;
     Arena &A = P->arena;
+    A.deferring = true;                                // released blocks stay reserved until the end
     BEM_TRY(A.alloc(&P->nodes, 3 * P->N));
     BEM_TRY(A.alloc(&P->elems, P->E * P->npe));
     BEM_TRY(A.alloc(&P->chi, P->E * P->npe));
@@ -136,10 +140,11 @@ static int plan_setup(bem_plan *P, cudaStream_t s) {
     BEM_TRY(build_geometry(P, s));
     BEM_TRY(build_radii_lists(P, s));
     BEM_TRY(lap(2));
-    // The special-pair correction (stream s) is enqueued first; the host then
-    // builds the near-field work items and the M2L offset classes while it runs, enqueues the diagonal's
-    // tables and product at the diagonal's order (s2), and builds the plan's
-    // own order (alloc_fmm, its kernels on s) while both run.  The product
+    // The special-pair correction (stream s) is enqueued while a second host
+    // thread builds the near-field work items and the M2L offset classes; then
+    // the diagonal's tables and product at the diagonal's order (s2) are
+    // enqueued, and the plan's own order (alloc_fmm, its kernels on s) is
+    // built while both run.  The product
     // joins s before the diagonal adds the correction's row sums.  Stage times
     // of the correction and the diagonal are the GPU spans on their streams
     // (they overlap); the class stage is host time.
@@ -152,18 +157,34 @@ static int plan_setup(bem_plan *P, cudaStream_t s) {
     };
     BEM_CUDA(cudaEventRecord(ev[0], s));
     BEM_CUDA(cudaStreamWaitEvent(s2, ev[0], 0));
+    // host work beside the correction's enqueue (which waits once for the pair
+    // count): the near-field work items, then the M2L offset classes (the
+    // lists were synchronised above); device copies on the null stream, which
+    // the plan's non-blocking streams do not wait for
+    int host_rc = BEM_OK;
+    std::string host_err;
+    std::thread worker([&] {
+        const auto h0 = std::chrono::steady_clock::now();
+        cudaError_t e = cudaSetDevice(P->device);
+        host_rc = e == cudaSuccess ? build_near_items(P) : cuda_fail(e, "cudaSetDevice", __FILE__, __LINE__);
+        if (host_rc == BEM_OK) host_rc = build_m2l_classes(P);
+        if (host_rc != BEM_OK) host_err = bem_last_error();
+        P->setup_ms[4] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - h0).count();
+    });
     int rc = build_correction(P, s);
-    if (rc == BEM_OK) BEM_CUDA(cudaEventRecord(ev[1], s));
+    if (rc == BEM_OK) {
+        cudaError_t e = cudaEventRecord(ev[1], s);
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaEventRecord", __FILE__, __LINE__);
+    }
+    worker.join();
+    if (rc == BEM_OK && host_rc != BEM_OK) {
+        set_error("%s", host_err.c_str());
+        rc = host_rc;
+    }
     if (rc != BEM_OK) {
         cudaStreamSynchronize(s);
         return fin(rc);
     }
-    // host work in the shadow of the correction's kernels: the near-field work
-    // items, then the M2L offset classes (the lists were synchronised above)
-    t0 = std::chrono::steady_clock::now();
-    rc = build_near_items(P);
-    if (rc == BEM_OK) rc = build_m2l_classes(P);
-    P->setup_ms[4] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (rc == BEM_OK) BEM_CUDA(cudaEventRecord(ev[2], s2));
     if (rc == BEM_OK) rc = diagonal_prepare(P, s2);
     if (rc == BEM_OK) rc = diagonal_product(P, s2);
@@ -180,6 +201,7 @@ static int plan_setup(bem_plan *P, cudaStream_t s) {
     BEM_CUDA(cudaStreamSynchronize(s));
     for (void *q : P->deferred) A.release(q);
     P->deferred.clear();
+    A.end_defer();                                     // both build streams are done
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ev[0], ev[1]);
     P->setup_ms[3] = ms;
@@ -248,6 +270,8 @@ int bem_ctx_create(int device, bem_ctx **out) {
     if (!c) { set_error("bem_ctx_create: out of host memory"); return BEM_ENOMEM; }
     c->device = device;
     BEM_CUDA(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device));
+    c->cache = std::make_shared<DevCache>();
+    if (const char *ev = std::getenv("BEM_CACHE_BYTES")) c->cache->limit = (size_t)std::strtoull(ev, nullptr, 10);
     *out = c;
     return BEM_OK;
 }
@@ -272,6 +296,7 @@ int bem_plan_create(bem_mesh *mesh, int green, double k, const bem_fmm_params *p
     P->mesh = mesh;
     P->device = mesh->ctx->device;
     P->sm_count = mesh->ctx->sm_count;
+    P->arena.cache = mesh->ctx->cache;
     P->green = green;
     P->k = green == BEM_HELMHOLTZ ? k : 0.0;
     P->prm = prm;

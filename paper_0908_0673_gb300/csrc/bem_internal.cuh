@@ -6,6 +6,9 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <map>
+#include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -64,36 +67,130 @@ __host__ __device__ inline void radon7(int q, double &s, double &t, double &w) {
 }
 
 // ---------------------------------------------------------------------------
+// device memory of a context, kept for reuse
+// ---------------------------------------------------------------------------
+// Blocks that the context's plans give back wait here for the next
+// allocation of the context (plans are built and destroyed per request in a
+// serving loop; cudaMalloc and cudaFree cost tens of microseconds each and
+// cudaFree synchronises the device).  A request takes the smallest cached
+// block of at least its size and at most twice it.  At most `limit` bytes
+// are kept (environment BEM_CACHE_BYTES, default 4 GiB); what would exceed
+// it is freed.  A block is given back only when no work can still use it.
+struct DevCache {
+    std::mutex mu;
+    std::multimap<size_t, void *> blocks;   // size -> block
+    size_t cached = 0, limit = (size_t)4 << 30;
+    void *take(size_t n, size_t *got) {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = blocks.lower_bound(n);
+        if (it == blocks.end() || it->first > 2 * n) return nullptr;
+        void *p = it->second;
+        *got = it->first;
+        cached -= it->first;
+        blocks.erase(it);
+        return p;
+    }
+    void give(void *p, size_t n) {
+        std::lock_guard<std::mutex> lock(mu);
+        if (cached + n > limit) {
+            cudaFree(p);
+            return;
+        }
+        blocks.emplace(n, p);
+        cached += n;
+    }
+    void flush() {
+        std::lock_guard<std::mutex> lock(mu);
+        for (auto &b : blocks) cudaFree(b.second);
+        blocks.clear();
+        cached = 0;
+    }
+    ~DevCache() { flush(); }
+};
+
+// ---------------------------------------------------------------------------
 // device buffers owned by a plan
 // ---------------------------------------------------------------------------
+// Sizes are rounded up to 256 bytes.  Allocations may come from two host
+// threads of one plan build (the lock keeps the lists consistent).  While a
+// build defers, released blocks stay reserved until the build has
+// synchronised its streams (end_defer); otherwise a release waits for the
+// device, as cudaFree would, before the block goes back to the cache.
 struct Arena {
+    std::mutex mu;
+    std::shared_ptr<DevCache> cache;    // the context's, or none
     std::vector<void *> ptrs;
     std::vector<size_t> sizes;
+    std::vector<std::pair<void *, size_t>> pending;
+    bool deferring = false;
     size_t bytes = 0;                   // bytes currently held
     size_t peak = 0;                    // most bytes held at any time
     template <class T>
     int alloc(T **p, size_t n) {
         *p = nullptr;
         if (n == 0) n = 1;
-        cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc", __FILE__, __LINE__);
-        ptrs.push_back(*p);
-        sizes.push_back(n * sizeof(T));
-        bytes += n * sizeof(T);
+        const size_t want = (n * sizeof(T) + 255) & ~(size_t)255;
+        std::lock_guard<std::mutex> lock(mu);
+        size_t got = want;                // a cached block may be up to twice the request
+        void *q = cache ? cache->take(want, &got) : nullptr;
+        if (!q) {
+            got = want;
+            cudaError_t e = cudaMalloc(&q, want);
+            if (e != cudaSuccess && cache) {
+                cudaGetLastError();
+                cudaDeviceSynchronize();
+                cache->flush();
+                e = cudaMalloc(&q, want);
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc", __FILE__, __LINE__);
+        }
+        *p = (T *)q;
+        ptrs.push_back(q);
+        sizes.push_back(got);
+        bytes += got;
         if (bytes > peak) peak = bytes;
         return BEM_OK;
     }
     void release(void *p) {
+        std::lock_guard<std::mutex> lock(mu);
         for (size_t i = 0; i < ptrs.size(); i++)
             if (ptrs[i] == p && p) {
-                cudaFree(p);
+                if (deferring) {
+                    pending.emplace_back(p, sizes[i]);
+                } else if (cache) {
+                    cudaDeviceSynchronize();
+                    cache->give(p, sizes[i]);
+                } else {
+                    cudaFree(p);
+                }
                 ptrs[i] = nullptr;
                 bytes -= sizes[i];
             }
     }
+    // the build's streams are synchronised: its released blocks are free
+    void end_defer() {
+        std::lock_guard<std::mutex> lock(mu);
+        deferring = false;
+        for (auto &b : pending) {
+            if (cache) cache->give(b.first, b.second);
+            else cudaFree(b.first);
+        }
+        pending.clear();
+    }
     ~Arena() {
-        for (void *p : ptrs)
-            if (p) cudaFree(p);
+        bool any = !pending.empty();
+        for (void *p : ptrs) any = any || p;
+        if (!any) return;
+        if (cache) cudaDeviceSynchronize();
+        for (size_t i = 0; i < ptrs.size(); i++)
+            if (ptrs[i]) {
+                if (cache) cache->give(ptrs[i], sizes[i]);
+                else cudaFree(ptrs[i]);
+            }
+        for (auto &b : pending) {
+            if (cache) cache->give(b.first, b.second);
+            else cudaFree(b.first);
+        }
     }
 };
 
@@ -164,6 +261,7 @@ struct Correction {                     // CSR by node (row), special - regular
 struct bem_ctx {
     int device = 0;
     int sm_count = 0;
+    std::shared_ptr<bem::DevCache> cache;   // device memory given back by the context's plans
 };
 
 struct bem_mesh {

@@ -287,16 +287,35 @@ int build_m2l_classes(bem_plan *P) {
     // Class key: (dl, level for Helmholtz, K).  Offsets of interacting boxes
     // are small integers, so the key packs into 64 bits (17 bits per K
     // component, biased) and goes into a flat open-addressing table; a key
-    // that does not fit the packing uses an ordered map.
+    // that does not fit the packing uses an ordered map.  The table starts
+    // small and doubles at half load: the pairs are many, their classes few
+    // (a few hundred per level), and a table that stays in cache keeps the
+    // per-pair lookups cheap.
     const int KB = 17;
     const long long KMAX = (1ll << (KB - 1)) - 1;
-    std::vector<unsigned long long> tkey;
-    std::vector<int> tval;
-    size_t tmask = 1;
-    while (tmask < 2 * (size_t)t.n_inter + 1024) tmask <<= 1;     // more slots than keys: probing ends
-    tkey.assign(tmask, 0ull);
-    tval.assign(tmask, -1);
-    tmask -= 1;
+    std::vector<unsigned long long> tkey(4096, 0ull);
+    std::vector<int> tval(4096, -1);
+    size_t tmask = 4095, tused = 0;
+    auto slot_of = [&](unsigned long long key) {
+        size_t h = (size_t)((key * 0x9E3779B97F4A7C15ull) >> 20) & tmask;
+        while (tkey[h] != 0ull && tkey[h] != key) h = (h + 1) & tmask;
+        return h;
+    };
+    auto grow = [&]() {
+        std::vector<unsigned long long> ok;
+        std::vector<int> ov;
+        ok.swap(tkey);
+        ov.swap(tval);
+        tmask = 2 * (tmask + 1) - 1;
+        tkey.assign(tmask + 1, 0ull);
+        tval.assign(tmask + 1, -1);
+        for (size_t i = 0; i < ok.size(); i++)
+            if (ok[i]) {
+                const size_t h = slot_of(ok[i]);
+                tkey[h] = ok[i];
+                tval[h] = ov[i];
+            }
+    };
     std::map<std::tuple<int, int, long long, long long, long long>, int> wide;
     std::vector<int> pair_cls(std::max<int64_t>(1, t.n_inter));
     std::vector<int> dls, levs;
@@ -327,11 +346,15 @@ int build_m2l_classes(bem_plan *P) {
                     1ull + (((unsigned long long)(kx + KMAX)) | ((unsigned long long)(ky + KMAX) << KB) |
                             ((unsigned long long)(kz + KMAX) << (2 * KB)) |
                             ((unsigned long long)(dl + 64) << (3 * KB)) | ((unsigned long long)lv << (3 * KB + 7)));
-                size_t h = (size_t)((key * 0x9E3779B97F4A7C15ull) >> 20) & tmask;
-                while (tkey[h] != 0ull && tkey[h] != key) h = (h + 1) & tmask;
+                size_t h = slot_of(key);
                 if (tkey[h] == 0ull) {
+                    if (2 * (tused + 1) > tmask + 1) {
+                        grow();
+                        h = slot_of(key);
+                    }
                     tkey[h] = key;
                     tval[h] = new_class(b, dl, kx, ky, kz);
+                    tused++;
                 }
                 c = tval[h];
             } else {
