@@ -412,6 +412,10 @@ def serving(args):
             eng.close()
         out[name] = summarize(res)
         out[name]["largest_served_elems"] = max((r.n_elems for r in res if r.status in ("ok", "noconv")), default=0)
+        bad = [r for r in res if r.status in ("error", "refused")]
+        if bad:
+            out[name]["failed"] = [{"request": r.rid, "elements": r.n_elems, "k": r.k, "status": r.status,
+                                    "why": r.error[:200]} for r in bad[:6]]
         phis[name] = {r.rid: r.phi for r in res if r.phi is not None}
     errs = []
     for rid, ph in phis.get("mixed_continuous", {}).items():

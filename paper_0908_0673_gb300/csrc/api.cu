@@ -148,7 +148,7 @@ static int plan_setup(bem_plan *P, cudaStream_t s) {
     // joins s before the diagonal adds the correction's row sums.  Stage times
     // of the correction and the diagonal are the GPU spans on their streams
     // (they overlap); the class stage is host time.
-    cudaStream_t s2 = P->setup_stream[1];
+    cudaStream_t s2 = P->setup_stream[1], s3 = P->setup_stream[2];
     cudaEvent_t ev[6] = {};
     for (auto &e : ev) BEM_CUDA(cudaEventCreate(&e));
     auto fin = [&](int rc) {
@@ -157,6 +157,7 @@ static int plan_setup(bem_plan *P, cudaStream_t s) {
     };
     BEM_CUDA(cudaEventRecord(ev[0], s));
     BEM_CUDA(cudaStreamWaitEvent(s2, ev[0], 0));
+    BEM_CUDA(cudaStreamWaitEvent(s3, ev[0], 0));
     // host work beside the correction's enqueue (which waits once for the pair
     // count): the near-field work items, then the M2L offset classes (the
     // lists were synchronised above); device copies on the null stream, which
@@ -189,13 +190,16 @@ static int plan_setup(bem_plan *P, cudaStream_t s) {
     if (rc == BEM_OK) rc = diagonal_prepare(P, s2);
     if (rc == BEM_OK) rc = diagonal_product(P, s2);
     if (rc == BEM_OK) BEM_CUDA(cudaEventRecord(ev[3], s2));
-    if (rc == BEM_OK) rc = alloc_fmm(P, s);
+    if (rc == BEM_OK) rc = alloc_fmm(P, s3);
+    if (rc == BEM_OK) BEM_CUDA(cudaEventRecord(ev[5], s3));
+    if (rc == BEM_OK) BEM_CUDA(cudaStreamWaitEvent(s, ev[5], 0));
     if (rc == BEM_OK) BEM_CUDA(cudaStreamWaitEvent(s, ev[3], 0));
     if (rc == BEM_OK) rc = diagonal_finish(P, s);
     if (rc == BEM_OK) BEM_CUDA(cudaEventRecord(ev[4], s));
     if (rc != BEM_OK) {
         cudaStreamSynchronize(s);
         cudaStreamSynchronize(s2);
+        cudaStreamSynchronize(s3);
         return fin(rc);
     }
     BEM_CUDA(cudaStreamSynchronize(s));
@@ -305,15 +309,17 @@ int bem_plan_create(bem_mesh *mesh, int green, double k, const bem_fmm_params *p
     P->Q = mesh->n_elems * NQ;
     P->nchi = mesh->n_chi;
     P->npe = mesh->npe;
-    // set-up runs on two streams of its own, after the caller's stream; the
+    // set-up runs on three streams of its own, after the caller's stream; the
     // second (the diagonal's product) has the higher priority, so its blocks
-    // are scheduled first as the correction's quadrature blocks retire
+    // are scheduled first as the correction's quadrature blocks retire; the
+    // third builds the plan's own order meanwhile
     cudaStream_t cs = (cudaStream_t)cuda_stream;
     {
         int least = 0, greatest = 0;
         BEM_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
         BEM_CUDA(cudaStreamCreateWithPriority(&P->setup_stream[0], cudaStreamNonBlocking, least));
         BEM_CUDA(cudaStreamCreateWithPriority(&P->setup_stream[1], cudaStreamNonBlocking, greatest));
+        BEM_CUDA(cudaStreamCreateWithPriority(&P->setup_stream[2], cudaStreamNonBlocking, least));
     }
     cudaStream_t s = P->setup_stream[0];
     int rc = BEM_OK;

@@ -369,7 +369,7 @@ struct bem_plan : bem::FmmState {
     double *diag_ones = nullptr;        // phi = 1 of the diagonal's product (set-up only)
     bem::FmmState diag_state;           // the diagonal's order while its product runs (set-up only)
     bool diag_mode = false;             // alloc_fmm for the diagonal's order
-    cudaStream_t setup_stream[2] = {nullptr, nullptr};
+    cudaStream_t setup_stream[3] = {nullptr, nullptr, nullptr};
     int2 *near_items[2] = {nullptr, nullptr};   // float32 near-field work items, 64- and 32-target passes
     int near_nitems[2] = {0, 0};
     int last_op = -1;

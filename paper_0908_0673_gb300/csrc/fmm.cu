@@ -452,7 +452,9 @@ int build_near_items(bem_plan *P) {
         pairs += n * (ne[b] - nb[b]);
     }
     P->near_pairs = pairs;
-    for (int v = 0; v < 2; v++) {
+    // real items for every plan (the diagonal's product is Laplace), complex
+    // ones for Helmholtz plans only
+    for (int v = 0; v < (P->green == BEM_HELMHOLTZ ? 2 : 1); v++) {
         const int slots = 8 * nf2_u(v + 1);
         std::vector<int2> items;
         std::vector<int64_t> cost;

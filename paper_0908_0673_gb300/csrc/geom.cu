@@ -783,7 +783,8 @@ constexpr int SPN_QCAP = 32;        // pieces per level buffer and group
 constexpr int SPN_RING = 64;        // pending points per group: a power of two >= SPN_W - 1 + 7 SPN_W
 
 template <class R, bool HELM, int NPE>
-__global__ void __launch_bounds__(32 * SPN_WARPS) k_special_near(CorrArgs a, int nlist, const int *__restrict__ list,
+__global__ void __launch_bounds__(32 * SPN_WARPS) k_special_near(CorrArgs a, const int *__restrict__ nlist_dev,
+                                                                const int *__restrict__ list,
                                                                 const int *__restrict__ pair_node,
                                                                 const int *__restrict__ pair_e, double *valD,
                                                                 double *valS, double *d0pair) {
@@ -803,6 +804,7 @@ __global__ void __launch_bounds__(32 * SPN_WARPS) k_special_near(CorrArgs a, int
     const float *df = sdf[g];
     const R kk = (R)a.k;
     const float tau2 = (float)(a.tau * a.tau);
+    const int nlist = *nlist_dev;
     for (int li = blockIdx.x * SPN_G + g; li < nlist; li += gridDim.x * SPN_G) {
         const int pr = list[li], node = pair_node[pr], e = pair_e[pr];
         double xi[3];
@@ -906,6 +908,222 @@ __global__ void __launch_bounds__(32 * SPN_WARPS) k_special_near(CorrArgs a, int
             if (head + sl < tail) eval_st<R, HELM, NPE>(d, kk, rs[k], rt[k], rw[k], v);
         }
         reduce_store<R, HELM, NPE, W>(v, wmask, sl, pr, valD, valS, d0pair);
+    }
+}
+
+// A piece of the 4-way subdivision as a 32-bit code: its first corner a in
+// units of 2^-10 (bits 0-10 and 11-21), its depth (bits 22-25) and which of
+// the six edge frames (e, f) = (b - a, c - a) / 2^-depth it has (bits 26-28).
+// split4 keeps the frame in children 0-2 and turns (e, f) into (f, f - e) in
+// child 3, so six frames are all there are.
+// The frames' components (e0 e1 f0 f1, each -1, 0 or 1) packed two bits each
+// (value + 1), one byte per frame, so that a lane reads its frame from a
+// register constant whatever frame the other lanes have.
+constexpr int FRAMES[6][4] = {{1, 0, 0, 1}, {0, 1, -1, 1}, {-1, 1, -1, 0},
+                              {-1, 0, 0, -1}, {0, -1, 1, -1}, {1, -1, 1, 0}};
+constexpr unsigned long long frame_bits() {
+    unsigned long long t = 0;
+    for (int f = 0; f < 6; f++)
+        for (int i = 0; i < 4; i++) t |= (unsigned long long)(FRAMES[f][i] + 1) << (8 * f + 2 * i);
+    return t;
+}
+constexpr unsigned long long FRAME_BITS = frame_bits();
+__device__ __forceinline__ int frame_comp(int fr, int i) { return (int)((FRAME_BITS >> (8 * fr + 2 * i)) & 3ull) - 1; }
+
+__device__ __forceinline__ unsigned piece_code(int a0, int a1, int depth, int frame) {
+    return (unsigned)a0 | ((unsigned)a1 << 11) | ((unsigned)depth << 22) | ((unsigned)frame << 26);
+}
+
+__device__ __forceinline__ PieceF code_piece(unsigned code) {
+    const int a0 = code & 2047, a1 = (code >> 11) & 2047, depth = (code >> 22) & 15, fr = code >> 26;
+    const int h = 1024 >> depth;
+    const float k = 1.f / SP_UNIT;
+    return {a0 * k, a1 * k, (a0 + frame_comp(fr, 0) * h) * k, (a1 + frame_comp(fr, 1) * h) * k,
+            (a0 + frame_comp(fr, 2) * h) * k, (a1 + frame_comp(fr, 3) * h) * k, depth};
+}
+
+// child c of a coded piece (split4's numbering)
+__device__ __forceinline__ unsigned child_of(unsigned code, int c) {
+    const int a0 = code & 2047, a1 = (code >> 11) & 2047, depth = (code >> 22) & 15, fr = code >> 26;
+    const int h = 512 >> depth;                           // half an edge
+    const int b0 = a0 + (c == 1 || c == 3 ? frame_comp(fr, 0) * h : c == 2 ? frame_comp(fr, 2) * h : 0);
+    const int b1 = a1 + (c == 1 || c == 3 ? frame_comp(fr, 1) * h : c == 2 ? frame_comp(fr, 3) * h : 0);
+    return piece_code(b0, b1, depth + 1, c == 3 ? (fr + 1) % 6 : fr);
+}
+
+struct PieceImg {
+    float4 A, B, Cc;            // corner images (node offsets from the collocation point)
+};
+
+// children's corner images from the parent's and the three edge midpoints
+__device__ __forceinline__ PieceImg child_img(const PieceImg &P, float4 mab, float4 mbc, float4 mca, int c) {
+    if (c == 0) return {P.A, mab, mca};
+    if (c == 1) return {mab, P.B, mbc};
+    if (c == 2) return {mca, mbc, P.Cc};
+    return {mab, mbc, mca};
+}
+
+template <int NPE>
+__device__ __forceinline__ void mid_imgs(const float *df, const PieceF &P, float4 &mab, float4 &mbc, float4 &mca) {
+    mab = map_f<NPE>(df, 0.5f * (P.a0 + P.b0), 0.5f * (P.a1 + P.b1));
+    mbc = map_f<NPE>(df, 0.5f * (P.b0 + P.c0), 0.5f * (P.b1 + P.c1));
+    mca = map_f<NPE>(df, 0.5f * (P.c0 + P.a0), 0.5f * (P.c1 + P.a1));
+}
+
+template <int NPE>
+__device__ __forceinline__ bool split_coded(const float *df, unsigned code, const PieceImg &I, const double *X,
+                                            const double xi[3], float tau2, double tau, int maxdepth) {
+    QPiece Q;
+    Q.A = I.A; Q.B = I.B; Q.Cc = I.Cc;
+    return split_test<NPE>(df, Q, code_piece(code), X, xi, tau2, tau, maxdepth);
+}
+
+// Near-singular pairs, the light ones in two steps.  Most pairs refine at
+// most twice (the root, which always splits, and some of its children): one
+// thread per pair walks those two levels unrolled in registers and writes
+// the pair's leaf pieces (at most 16) as 32-bit codes into the pair's slots;
+// a pair with a piece of level 2 that splits as well goes to a list of deep
+// pairs for k_special_near, whose 8 lanes per pair refine it level by level.
+// The light pairs' points are then evaluated by k_near_eval without the
+// refinement's control flow.  Both paths decide every piece by split_test
+// (the float32 estimate from the corner images, else the float64 test), so
+// the pieces are the same as the oracle's.
+constexpr int NW_T = 128;           // threads per block of the walk
+constexpr int NW_SLOTS = 16;        // leaf slots per light pair: 4 children x 4 grandchildren
+constexpr int NE_W = 8;             // lanes per pair in the evaluation
+constexpr int NE_WARPS = 4;         // warps per block of the evaluation
+
+template <int NPE>
+__global__ void __launch_bounds__(NW_T) k_near_walk(CorrArgs a, int nlist, const int *__restrict__ list,
+                                                    const int *__restrict__ pair_node, const int *__restrict__ pair_e,
+                                                    int *cnt, unsigned *leaves, int *deep_list, int *ndeep) {
+    const int li = blockIdx.x * NW_T + threadIdx.x;
+    if (li >= nlist) return;
+    const int pr = list[li], node = pair_node[pr], e = pair_e[pr];
+    double xi[3], X[3 * NPE];
+    float df[3 * NPE];
+    xi[0] = a.nodes[3 * (size_t)node];
+    xi[1] = a.nodes[3 * (size_t)node + 1];
+    xi[2] = a.nodes[3 * (size_t)node + 2];
+#pragma unroll
+    for (int i = 0; i < 3 * NPE; i++) {
+        const int c = i % 3, vid = a.el_phi[(size_t)e * NPE + i / 3];
+        X[i] = a.nodes[3 * (size_t)vid + c];
+        df[i] = (float)(X[i] - xi[c]);
+    }
+    const float tau2 = (float)(a.tau * a.tau);
+    const int maxdepth = a.maxdepth;
+    unsigned *out = leaves + (size_t)li * NW_SLOTS;
+    int n = 0;
+    const unsigned root = piece_code(0, 0, 0, 0);
+    bool deep = false;
+    if (maxdepth <= 0) {
+        out[n++] = root;                                 // no subdivision: the special rule is the regular rule
+    } else {
+        const float4 v0 = make_float4(df[0], df[1], df[2], 0.f), v1 = make_float4(df[3], df[4], df[5], 0.f),
+                     v2 = make_float4(df[6], df[7], df[8], 0.f);
+        float4 m01, m12, m20;
+        if (NPE == 6) {
+            m01 = make_float4(df[9 % (3 * NPE)], df[10 % (3 * NPE)], df[11 % (3 * NPE)], 0.f);
+            m12 = make_float4(df[12 % (3 * NPE)], df[13 % (3 * NPE)], df[14 % (3 * NPE)], 0.f);
+            m20 = make_float4(df[15 % (3 * NPE)], df[16 % (3 * NPE)], df[17 % (3 * NPE)], 0.f);
+        } else {
+            m01 = map_f<NPE>(df, 0.5f, 0.f); m12 = map_f<NPE>(df, 0.5f, 0.5f); m20 = map_f<NPE>(df, 0.f, 0.5f);
+        }
+        const PieceImg rimg{v0, v1, v2};
+#pragma unroll
+        for (int c1 = 0; c1 < 4; c1++) {
+            const unsigned k1 = child_of(root, c1);
+            const PieceImg i1 = child_img(rimg, m01, m12, m20, c1);
+            if (deep) break;
+            if (!split_coded<NPE>(df, k1, i1, X, xi, tau2, a.tau, maxdepth)) {
+                out[n++] = k1;
+                continue;
+            }
+            float4 mab, mbc, mca;
+            mid_imgs<NPE>(df, code_piece(k1), mab, mbc, mca);
+            for (int c2 = 0; c2 < 4 && !deep; c2++) {
+                const unsigned k2 = child_of(k1, c2);
+                const PieceImg i2 = child_img(i1, mab, mbc, mca, c2);
+                if (split_coded<NPE>(df, k2, i2, X, xi, tau2, a.tau, maxdepth)) deep = true;
+                else out[n++] = k2;
+            }
+        }
+    }
+    if (deep) {
+        cnt[li] = -1;
+        deep_list[atomicAdd(ndeep, 1)] = pr;             // list order does not matter: pairs are independent
+    } else {
+        cnt[li] = n;
+    }
+}
+
+// Evaluation of the light pairs.  A block takes chunks of NE_CHUNK
+// consecutive pairs of the list, ranks them by point count (descending; ties
+// in list order; deep pairs last, skipped) and gives the pairs of
+// neighbouring ranks to the groups of one warp, so that the four groups of a
+// warp run about the same number of rounds.
+constexpr int NE_CHUNK = 64;
+
+template <class R, bool HELM, int NPE, int W>
+__global__ void __launch_bounds__(32 * NE_WARPS) k_near_eval(CorrArgs a, int nlist, const int *__restrict__ list,
+                                                             const int *__restrict__ pair_node,
+                                                             const int *__restrict__ pair_e, const int *__restrict__ cnt,
+                                                             const unsigned *__restrict__ leaves, double *valD,
+                                                             double *valS, double *d0pair) {
+    constexpr int NVP = sp_nvp(HELM, NPE), G = NE_WARPS * 32 / W;
+    static_assert(NE_CHUNK % G == 0 && NE_CHUNK <= 32 * NE_WARPS, "chunk");
+    __shared__ R sd[G][3 * NPE];
+    __shared__ int skey[NE_CHUNK], sorder[NE_CHUNK];
+    const int tid = threadIdx.x, lane = tid & 31, g = tid / W, sl = tid % W;
+    const unsigned wmask = (W == 32 ? 0xffffffffu : ((1u << W) - 1u)) << (lane - sl);
+    const R kk = (R)a.k;
+    for (int c0 = blockIdx.x * NE_CHUNK; c0 < nlist; c0 += gridDim.x * NE_CHUNK) {
+        __syncthreads();                                 // the previous chunk's order and keys have been read
+        if (tid < NE_CHUNK) skey[tid] = c0 + tid < nlist ? cnt[c0 + tid] : -1;
+        __syncthreads();
+        if (tid < NE_CHUNK) {
+            const int k = skey[tid];
+            int r = 0;
+            for (int j = 0; j < NE_CHUNK; j++) {
+                const int kj = skey[j];
+                r += kj > k || (kj == k && j < tid);
+            }
+            sorder[r] = tid;
+        }
+        __syncthreads();
+        for (int r0 = 0; r0 < NE_CHUNK; r0 += G) {
+            const int o = sorder[r0 + g], li = c0 + o;
+            if (skey[o] < 0) continue;                   // empty slots and deep pairs rank last
+            const int pr = list[li], node = pair_node[pr], e = pair_e[pr];
+            __syncwarp(wmask);                           // the previous pair's reads of the table are done
+            for (int i = sl; i < 3 * NPE; i += W) {
+                const int c = i % 3, vid = a.el_phi[(size_t)e * NPE + i / 3];
+                sd[g][i] = (R)(a.nodes[3 * (size_t)vid + c] - a.nodes[3 * (size_t)node + c]);
+            }
+            __syncwarp(wmask);
+            R v[NVP];
+#pragma unroll
+            for (int i = 0; i < NVP; i++) v[i] = 0;
+            const int npt = NQ * (1 + skey[o]);
+            const unsigned *lv = leaves + (size_t)li * NW_SLOTS;
+            // point j = NQ pc + q: pc = 0 the regular rule (negative weights),
+            // pc >= 1 leaf pc - 1; lane sl takes j = sl, sl + W, ...
+            int pc = sl / NQ, q = sl % NQ;
+            for (int j = sl; j < npt; j += W) {
+                R s, t, w;
+                if (pc == 0) {
+                    s = rule_s<R>(q); t = rule_t<R>(q); w = -rule_w<R>(q);
+                } else {
+                    leaf_point<R>(code_piece(lv[pc - 1]), q, s, t, w);
+                }
+                eval_st<R, HELM, NPE>(sd[g], kk, s, t, w, v);
+                pc += W / NQ;
+                q += W % NQ;
+                if (q >= NQ) { q -= NQ; pc++; }
+            }
+            reduce_store<R, HELM, NPE, W>(v, wmask, sl, pr, valD, valS, d0pair);
+        }
     }
 }
 
@@ -1049,6 +1267,23 @@ int build_correction(bem_plan *P, cudaStream_t s) {
         (k_pair_split<<<(npairs + 255) / 256, 256, 0, s>>>(npairs, kind, koff, nself, klist), ::bem::count_launch());
     }
     const int nnear = npairs - nself;
+    // light near-singular pairs: leaf codes and their counts; deep pairs: a list
+    int *lcnt = nullptr, *deep_list = nullptr, *ndeep = nullptr;
+    unsigned *leaves = nullptr;
+    BEM_TRY(A.alloc(&lcnt, std::max(1, nnear)));
+    BEM_TRY(A.alloc(&deep_list, std::max(1, nnear)));
+    BEM_TRY(A.alloc(&ndeep, 1));
+    BEM_TRY(A.alloc(&leaves, (size_t)std::max(1, nnear) * NW_SLOTS));
+    BEM_CUDA(cudaMemsetAsync(ndeep, 0, sizeof(int), s));
+    if (nnear > 0) {
+        if (npe == 3)
+            (k_near_walk<3><<<(nnear + NW_T - 1) / NW_T, NW_T, 0, s>>>(a, nnear, klist + nself, pair_node, pair_e, lcnt,
+                                                                      leaves, deep_list, ndeep), ::bem::count_launch());
+        else
+            (k_near_walk<6><<<(nnear + NW_T - 1) / NW_T, NW_T, 0, s>>>(a, nnear, klist + nself, pair_node, pair_e, lcnt,
+                                                                      leaves, deep_list, ndeep), ::bem::count_launch());
+        BEM_LAUNCH_CHECK();
+    }
     {
         const bool mx = P->prm.precision == BEM_MIXED, helm = P->green == BEM_HELMHOLTZ;
         // grid-stride loops over the pair lists, but not persistent grids:
@@ -1057,14 +1292,18 @@ int build_correction(bem_plan *P, cudaStream_t s) {
         // gets SMs while the quadrature is still running
         const int gs = (int)std::max<int64_t>(1, ((int64_t)nself + SP_WARPS * SP_PAIRS_PER_WARP - 1) /
                                                      (SP_WARPS * SP_PAIRS_PER_WARP));
-        const int gn = (int)std::max<int64_t>(1, ((int64_t)nnear + SPN_G * SP_PAIRS_PER_WARP - 1) /
-                                                     (SPN_G * SP_PAIRS_PER_WARP));
+        const int ge = (int)std::max<int64_t>(1, ((int64_t)nnear + 4 * NE_CHUNK - 1) / (4 * NE_CHUNK));
+        const int gn = 5 * std::max(1, P->sm_count);       // deep pairs: a few per cent, count on the device
 #define BEM_SW(R, H, NP)                                                                                          \
     do {                                                                                                          \
-        if (nnear > 0)                                                                                            \
-            (k_special_near<R, H, NP><<<gn, 32 * SPN_WARPS, 0, s>>>(a, nnear, klist + nself, pair_node, pair_e,    \
+        if (nnear > 0) {                                                                                          \
+            (k_near_eval<R, H, NP, NE_W><<<ge, 32 * NE_WARPS, 0, s>>>(a, nnear, klist + nself, pair_node, pair_e,  \
+                                                                       lcnt, leaves, K.valD, K.valS, d0pair),     \
+             ::bem::count_launch());                                                                              \
+            (k_special_near<R, H, NP><<<gn, 32 * SPN_WARPS, 0, s>>>(a, ndeep, deep_list, pair_node, pair_e,        \
                                                                     K.valD, K.valS, d0pair),                      \
              ::bem::count_launch());                                                                              \
+        }                                                                                                         \
         if (nself > 0)                                                                                            \
             (k_special_self<R, H, NP><<<gs, 32 * SP_WARPS, 0, s>>>(a, nself, klist, pair_node, pair_e, K.valD,    \
                                                                    K.valS, d0pair),                               \
@@ -1091,7 +1330,7 @@ int build_correction(bem_plan *P, cudaStream_t s) {
     // is added by one Laplace double-layer product on phi = 1
     P->C = d0row;
     // the temporaries are released once the stream has finished with them
-    for (void *q : {(void *)ptmp, (void *)kind, (void *)koff, (void *)klist, (void *)ktot, (void *)kblk, (void *)cnt, (void *)tot, (void *)sblk, (void *)pair_node, (void *)d0pair, (void *)ecx, (void *)ecy, (void *)ecz,
+    for (void *q : {(void *)ptmp, (void *)lcnt, (void *)deep_list, (void *)ndeep, (void *)leaves, (void *)kind, (void *)koff, (void *)klist, (void *)ktot, (void *)kblk, (void *)cnt, (void *)tot, (void *)sblk, (void *)pair_node, (void *)d0pair, (void *)ecx, (void *)ecy, (void *)ecz,
                     (void *)eh, (void *)ebnd, (void *)frho, (void *)rho, (void *)off, (void *)pair_e})
         P->deferred.push_back(q);
     return BEM_OK;

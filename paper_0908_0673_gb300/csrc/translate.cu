@@ -296,8 +296,10 @@ int build_m2l_classes(bem_plan *P) {
     std::vector<unsigned long long> tkey(4096, 0ull);
     std::vector<int> tval(4096, -1);
     size_t tmask = 4095, tused = 0;
+    int tbits = 12;
+    // Fibonacci hashing: the product's top bits depend on every bit of the key
     auto slot_of = [&](unsigned long long key) {
-        size_t h = (size_t)((key * 0x9E3779B97F4A7C15ull) >> 20) & tmask;
+        size_t h = (size_t)((key * 0x9E3779B97F4A7C15ull) >> (64 - tbits));
         while (tkey[h] != 0ull && tkey[h] != key) h = (h + 1) & tmask;
         return h;
     };
@@ -307,6 +309,7 @@ int build_m2l_classes(bem_plan *P) {
         ok.swap(tkey);
         ov.swap(tval);
         tmask = 2 * (tmask + 1) - 1;
+        tbits++;
         tkey.assign(tmask + 1, 0ull);
         tval.assign(tmask + 1, -1);
         for (size_t i = 0; i < ok.size(); i++)

@@ -94,8 +94,16 @@ __global__ void __launch_bounds__(SCAN_T) k_scan(const T *__restrict__ in, T *__
 }
 
 // exclusive scan of n values (in and out may alias); *total_dev = sum;
-// blk: device scratch of at least scan_scratch(n) values
-size_t scan_scratch(int n) { return (size_t)(n + SCAN_BLK - 1) / SCAN_BLK + 1; }
+// blk: device scratch of at least scan_scratch(n) values (the block totals
+// of every level: more than SCAN_BLK blocks are scanned the same way)
+size_t scan_scratch(int n) {
+    size_t t = 1;
+    for (int64_t m = n; m > SCAN_BLK;) {
+        m = (m + SCAN_BLK - 1) / SCAN_BLK;
+        t += (size_t)m;
+    }
+    return t + 1;
+}
 
 template <class T>
 static int scan_t(const T *in, T *out, int n, T *total_dev, T *blk, cudaStream_t s) {
@@ -104,9 +112,8 @@ static int scan_t(const T *in, T *out, int n, T *total_dev, T *blk, cudaStream_t
     if (nb == 1) {
         (k_scan<T><<<1, SCAN_T, 0, s>>>(in, out, n, nullptr, total_dev, 2), ::bem::count_launch());
     } else {
-        if (nb > SCAN_BLK) { set_error("scan: %d elements exceed the two-level scan", n); return BEM_EINVAL; }
         (k_scan<T><<<nb, SCAN_T, 0, s>>>(in, out, n, blk, nullptr, 0), ::bem::count_launch());
-        (k_scan<T><<<1, SCAN_T, 0, s>>>(blk, blk, nb, nullptr, total_dev, 2), ::bem::count_launch());
+        BEM_TRY(scan_t<T>(blk, blk, nb, total_dev, blk + nb, s));   // the block totals, in place
         (k_scan<T><<<nb, SCAN_T, 0, s>>>(in, out, n, blk, nullptr, 1), ::bem::count_launch());
     }
     BEM_LAUNCH_CHECK();
@@ -770,7 +777,7 @@ int build_radii_lists(bem_plan *P, cudaStream_t s) {
     BEM_TRY(A.alloc(&sblk, scan_scratch(maxcnt)));
     // one walk per level: up to LIST_CAP entries of each list are kept by the
     // counting walk and copied into place; a longer list makes the level walk again
-    constexpr int LIST_CAP = 256;
+    constexpr int LIST_CAP = 1024;
     int *tn = nullptr, *ti = nullptr;
     BEM_TRY(A.alloc(&tn, (size_t)maxcnt * LIST_CAP));
     BEM_TRY(A.alloc(&ti, (size_t)maxcnt * LIST_CAP));
