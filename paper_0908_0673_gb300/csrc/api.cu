@@ -159,25 +159,26 @@ static int plan_setup(bem_plan *P, cudaStream_t s) {
     BEM_CUDA(cudaStreamWaitEvent(s2, ev[0], 0));
     BEM_CUDA(cudaStreamWaitEvent(s3, ev[0], 0));
     // host work beside the correction's enqueue (which waits once for the pair
-    // count): the near-field work items, then the M2L offset classes (the
-    // lists were synchronised above); device copies on the null stream, which
-    // the plan's non-blocking streams do not wait for
+    // count): the M2L offset classes on a second thread, the near-field work
+    // items on this one once the correction is enqueued (the lists were
+    // synchronised above); device copies on the null stream, which the plan's
+    // non-blocking streams do not wait for
     int host_rc = BEM_OK;
     std::string host_err;
+    const auto h0 = std::chrono::steady_clock::now();
     std::thread worker([&] {
-        const auto h0 = std::chrono::steady_clock::now();
         cudaError_t e = cudaSetDevice(P->device);
-        host_rc = e == cudaSuccess ? build_near_items(P) : cuda_fail(e, "cudaSetDevice", __FILE__, __LINE__);
-        if (host_rc == BEM_OK) host_rc = build_m2l_classes(P);
+        host_rc = e == cudaSuccess ? build_m2l_classes(P) : cuda_fail(e, "cudaSetDevice", __FILE__, __LINE__);
         if (host_rc != BEM_OK) host_err = bem_last_error();
-        P->setup_ms[4] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - h0).count();
     });
     int rc = build_correction(P, s);
     if (rc == BEM_OK) {
         cudaError_t e = cudaEventRecord(ev[1], s);
         if (e != cudaSuccess) rc = cuda_fail(e, "cudaEventRecord", __FILE__, __LINE__);
     }
+    if (rc == BEM_OK) rc = build_near_items(P);
     worker.join();
+    P->setup_ms[4] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - h0).count();
     if (rc == BEM_OK && host_rc != BEM_OK) {
         set_error("%s", host_err.c_str());
         rc = host_rc;

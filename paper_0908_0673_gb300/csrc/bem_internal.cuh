@@ -211,6 +211,10 @@ constexpr int TC_MAXKS = 64;
 struct TcPlan {
     int nks = 0, img_floats = 0;        // K-steps; floats of one image plane (tf32 hi or lo)
     int ks_off[TC_MAXKS], ks_n[TC_MAXKS];
+    // an image too large for shared memory is held in two parts, K-steps
+    // [0, ks_split) and [ks_split, nks), loaded one after the other per tile
+    int ks_split = 0;                   // nks when the image is held whole
+    int part_floats[2] = {0, 0};        // floats of each part's plane
 };
 
 // Tree and plan state (everything device-resident unless named h_*).

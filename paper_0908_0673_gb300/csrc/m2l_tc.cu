@@ -59,7 +59,7 @@ struct TcArgs {
     int np, ldp, ntile, nkc;
     const int *tile_cls, *tile_start, *tile_cnt;
     const int *src, *sig, *pair;
-    const float *img;                   // [class][hi, lo][g.img_floats]
+    const float *img;                   // [class][part][hi, lo][g.part_floats[part]]
     const unsigned *sgn;                // [48][ldp / 32] sign bit of every canonical-frame moment
     const float *Mq;                    // [box][6][ldp] moments permuted by each axis permutation
     float *Lp;                          // rows of this run's pairs, row u - u0
@@ -81,7 +81,8 @@ struct TcLayout {
 __host__ __device__ inline TcLayout tc_layout(const TcPlan &g, int ldp) {
     TcLayout L;
     L.img = 0;
-    L.stage = ((2 * (size_t)g.img_floats * 4 + 1023) / 1024) * 1024;
+    const int pf = g.part_floats[0] > g.part_floats[1] ? g.part_floats[0] : g.part_floats[1];
+    L.stage = ((2 * (size_t)pf * 4 + 1023) / 1024) * 1024;
     L.sgn = L.stage + (size_t)TC_NS * 2 * TC_PLANE;
     L.xpose = L.sgn + ((48 * (size_t)(ldp / 32) * 4 + 15) / 16) * 16;
     L.bars = L.xpose + (size_t)TC_EPI * TC_XPOSE * 4;
@@ -122,8 +123,8 @@ __global__ void __launch_bounds__(TC_T, 1) k_m2l_tc(const __grid_constant__ TcAr
     unsigned *sSgn = (unsigned *)(smem + LY.sgn);                       // [48][ldp / 32]
     float *sX = (float *)(smem + LY.xpose);                             // [TC_EPI][32][33]
     uint64_t *full = (uint64_t *)(smem + LY.bars), *empty = full + TC_NS, *tfull = full + 2 * TC_NS,
-             *tempty = tfull + 1, *bfull = tfull + 2, *fin = tfull + 3;
-    uint32_t *sTmem = (uint32_t *)(fin + 1);
+             *tempty = tfull + 1, *bfull = tfull + 2, *fin = tfull + 3, *imgfree = tfull + 4;
+    uint32_t *sTmem = (uint32_t *)(imgfree + 1);
     volatile int *sAbort = (volatile int *)(sTmem + 1);
     const int nw = ldp / 32;
 
@@ -136,6 +137,7 @@ __global__ void __launch_bounds__(TC_T, 1) k_m2l_tc(const __grid_constant__ TcAr
         tc::mbar_init(tempty, TC_EPI);
         tc::mbar_init(bfull, 1);
         tc::mbar_init(fin, 1);
+        tc::mbar_init(imgfree, 1);
         *sAbort = 0;
         tc::mbar_fence_init();
     }
@@ -202,28 +204,38 @@ __global__ void __launch_bounds__(TC_T, 1) k_m2l_tc(const __grid_constant__ TcAr
     } else if (warp == TC_MMA_WARP) {
         // ---- class images and MMA issue (one thread) ----
         if (lane == 0) {
-            const uint32_t img_bytes = (uint32_t)G.img_floats * 4u;
-            const uint32_t ih = tc::smem_u32(sImg), il = ih + img_bytes, st0 = tc::smem_u32(sStage);
-            int it = 0, cur_cls = -1;
+            const bool split = G.ks_split < G.nks;
+            const uint32_t pb0 = (uint32_t)G.part_floats[0] * 4u, pb1 = (uint32_t)G.part_floats[1] * 4u;
+            const uint32_t ih = tc::smem_u32(sImg), st0 = tc::smem_u32(sStage);
+            int it = 0, cur_cls = -1, cur_part = -1;
+            uint32_t nfree = 0;
             bool ok = true;
+            // one part of a class image into shared memory (hi plane, then lo)
+            auto load_part = [&](int cls, int part) {
+                const float *src = a.img + (size_t)cls * 2 * G.img_floats + (part ? 2 * (size_t)G.part_floats[0] : 0);
+                const uint32_t bytes = 2u * (part ? pb1 : pb0);
+                tc::mbar_arrive_expect_tx(bfull, bytes);
+                tc::bulk_g2s(sImg, src, bytes, bfull);
+                bulk_pending = true;
+                if (!wait_or_abort(bfull, nbulk & 1u, sAbort)) return false;
+                bulk_pending = false;
+                nbulk++;
+                cur_cls = cls;
+                cur_part = part;
+                return true;
+            };
             for (int tile = t_begin; tile < t_end && ok; tile++) {
                 const int k = tile - t_begin, cls = a.tile_cls[tile];
                 // the accumulator and the image are free once the epilogue has
                 // read the previous tile (all of its MMAs have completed)
                 if (k > 0) ok = wait_or_abort(tempty, (uint32_t)((k - 1) & 1), sAbort);
                 if (!ok) break;
-                if (cls != cur_cls) {
-                    tc::mbar_arrive_expect_tx(bfull, 2u * img_bytes);
-                    tc::bulk_g2s(sImg, a.img + (size_t)cls * 2 * G.img_floats, 2u * img_bytes, bfull);
-                    bulk_pending = true;
-                    ok = wait_or_abort(bfull, nbulk & 1u, sAbort);
+                if (cls != cur_cls || cur_part != 0) {
+                    ok = load_part(cls, 0);
                     if (!ok) break;
-                    bulk_pending = false;
-                    nbulk++;
-                    cur_cls = cls;
                 }
                 tc::tc_fence_after_sync();
-                for (int kc = 0; kc < a.nkc; kc++, it++) {
+                for (int kc = 0; kc < a.nkc && ok; kc++, it++) {
                     const int s = it % TC_NS;
                     ok = wait_or_abort(&full[s], (uint32_t)((it / TC_NS) & 1), sAbort);
                     if (!ok) break;
@@ -233,7 +245,20 @@ __global__ void __launch_bounds__(TC_T, 1) k_m2l_tc(const __grid_constant__ TcAr
                     for (int ks = 0; ks < 4; ks++) {
                         const int j = kc * 4 + ks;
                         if (j >= G.nks) break;
-                        const uint32_t boff = (uint32_t)G.ks_off[j] * 4u;
+                        if (split && j == G.ks_split) {
+                            // every MMA so far reads the first part: once they have
+                            // completed, the second part replaces it
+                            tc::mma_commit(imgfree);
+                            ok = wait_or_abort(imgfree, nfree & 1u, sAbort);
+                            nfree++;
+                            if (!ok) break;
+                            ok = load_part(cls, 1);
+                            if (!ok) break;
+                            tc::tc_fence_after_sync();
+                        }
+                        const int pbase = cur_part ? G.part_floats[0] : 0;   // == ks_off[ks_split]
+                        const uint32_t il = ih + (cur_part ? pb1 : pb0);
+                        const uint32_t boff = (uint32_t)(G.ks_off[j] - pbase) * 4u;
                         const int n = G.ks_n[j];
                         for (int part = 0; part < n; part += 256) {
                             const int nn = min(256, n - part);
@@ -246,6 +271,7 @@ __global__ void __launch_bounds__(TC_T, 1) k_m2l_tc(const __grid_constant__ TcAr
                             tc::mma_tf32(d, al0 + ao, bh, id, true);
                         }
                     }
+                    if (!ok) break;
                     tc::mma_commit(&empty[s]);
                 }
                 if (ok) tc::mma_commit(tfull);
@@ -364,18 +390,22 @@ __global__ void __launch_bounds__(TC_T, 1) k_m2l_tc(const __grid_constant__ TcAr
 // K-step block layout) is T[b][a] = Dhat[a+b] (-1)^|a| 2^(dl |a|) / (a! b!),
 // tidx[e] = index of a + b | |a| << 16 (-1 outside the triangle), tfac[e] the
 // factorial and sign factor; split into tf32 hi and lo planes.
-__global__ void k_tc_images(int img_floats, int np, const int *__restrict__ tidx, const float *__restrict__ tfac,
-                            const float *__restrict__ fD, const int *__restrict__ dl, float *__restrict__ img) {
+__global__ void k_tc_images(int img_floats, int part0, int np, const int *__restrict__ tidx,
+                            const float *__restrict__ tfac, const float *__restrict__ fD, const int *__restrict__ dl,
+                            float *__restrict__ img) {
     const int cls = blockIdx.y;
-    float *hi = img + (size_t)cls * 2 * img_floats, *lo = hi + img_floats;
+    float *ci = img + (size_t)cls * 2 * img_floats;   // part 0: hi, lo; part 1: hi, lo
     const float *Dc = fD + (size_t)cls * np;
     const int d = dl[cls];
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < img_floats; e += gridDim.x * blockDim.x) {
         const int gi = tidx[e];
         const float v = gi >= 0 ? ldexpf(Dc[gi & 0xffff] * tfac[e], d * (gi >> 16)) : 0.f;
         const float h = tc::to_tf32(v);
-        hi[e] = h;
-        lo[e] = tc::to_tf32(v - h);
+        const bool second = e >= part0;
+        const int pn = second ? img_floats - part0 : part0, eo = second ? e - part0 : e;
+        float *hi = ci + (second ? 2 * (size_t)part0 : 0);
+        hi[eo] = h;
+        hi[pn + eo] = tc::to_tf32(v - h);
     }
 }
 
@@ -475,7 +505,27 @@ int build_m2l_sym(bem_plan *P, const std::vector<int> &pair_cls, const std::vect
     }
     std::vector<int> fidx(nfull);
     for (int c = 0; c < nfull; c++) fidx[c] = c;
-    std::sort(fidx.begin(), fidx.end(), [&](int x, int y) { return fkey[x] < fkey[y] || (!(fkey[y] < fkey[x]) && x < y); });
+    // the keys as one 64-bit word when every field fits (level difference
+    // + 64 in 7 bits, level in 6, the sorted offset magnitudes in 17 each):
+    // the same order, one integer compare
+    bool packs = true;
+    for (int c = 0; c < nfull && packs; c++) {
+        const long long *v = fkey[c].v;
+        packs = v[0] > -64 && v[0] < 64 && v[1] >= 0 && v[1] < 64 && v[2] < (1 << 17) && v[3] < (1 << 17) && v[4] < (1 << 17);
+    }
+    if (packs) {
+        std::vector<std::pair<unsigned long long, int>> kp(nfull);
+        for (int c = 0; c < nfull; c++) {
+            const long long *v = fkey[c].v;
+            kp[c] = {((unsigned long long)(v[0] + 64) << 57) | ((unsigned long long)v[1] << 51) |
+                         ((unsigned long long)v[2] << 34) | ((unsigned long long)v[3] << 17) | (unsigned long long)v[4],
+                     c};
+        }
+        std::sort(kp.begin(), kp.end());
+        for (int c = 0; c < nfull; c++) fidx[c] = kp[c].second;
+    } else {
+        std::sort(fidx.begin(), fidx.end(), [&](int x, int y) { return fkey[x] < fkey[y] || (!(fkey[y] < fkey[x]) && x < y); });
+    }
     std::vector<int> fcan(nfull), dlc;
     std::vector<double> rho, khc;
     P->sy_hlev.clear();
@@ -614,7 +664,19 @@ static bool tc_plan(const MIndex &mi, const std::vector<int> &deg, TcPlan &g, in
     g.img_floats = off;
     ldp = (g.ks_n[0] + 31) / 32 * 32;             // TMEM columns read back, 32 at a time
     nkc = (g.nks + 3) / 4;
-    return ldp <= 512 && tc_smem_bytes(g, ldp) <= (size_t)TC_SMEM_MAX;
+    if (ldp > 512) return false;
+    g.ks_split = g.nks;
+    g.part_floats[0] = off;
+    g.part_floats[1] = 0;
+    if (tc_smem_bytes(g, ldp) <= (size_t)TC_SMEM_MAX) return true;
+    // two parts of about equal size
+    int best = 1;
+    for (int j = 1; j < g.nks; j++)
+        if (std::max(g.ks_off[j], off - g.ks_off[j]) < std::max(g.ks_off[best], off - g.ks_off[best])) best = j;
+    g.ks_split = best;
+    g.part_floats[0] = g.ks_off[best];
+    g.part_floats[1] = off - g.ks_off[best];
+    return tc_smem_bytes(g, ldp) <= (size_t)TC_SMEM_MAX;
 }
 
 // Order-dependent tables of the M2L on canonical classes: symmetry maps,
@@ -709,7 +771,7 @@ int build_sym_tables(bem_plan *P, cudaStream_t s) {
         BEM_TRY(up(&d_tidx, tidx));
         BEM_TRY(up(&d_tfac, tfac));
         BEM_TRY(A.alloc(&P->sy_img, (size_t)ncls * 2 * g.img_floats));
-        (k_tc_images<<<dim3((g.img_floats + 255) / 256, ncls), 256, 0, s>>>(g.img_floats, np, d_tidx, d_tfac, P->sy_fD,
+        (k_tc_images<<<dim3((g.img_floats + 255) / 256, ncls), 256, 0, s>>>(g.img_floats, g.part_floats[0], np, d_tidx, d_tfac, P->sy_fD,
                                                                             P->sy_dl, P->sy_img),
          ::bem::count_launch());
         BEM_LAUNCH_CHECK();

@@ -22,7 +22,31 @@ CASES = {
     "cube8_tri6": (lambda: I.cube(8, I.TRI6), dict(p=10, leaf_size=32, eta=2.0), (0.2, -0.1, 0.3)),
     "sphere_tri6_l2": (lambda: I.icosphere(2, I.TRI6), dict(p=8, leaf_size=16, eta=2.0), (0.1, 0.2, -0.15)),
     "cube6_p9": (lambda: I.cube(6, I.TRI6), dict(p=9, leaf_size=24, eta=2.0), (0.2, -0.1, 0.3)),
+    "cube8_p12": (lambda: I.cube(8, I.TRI6), dict(p=12, leaf_size=32, eta=2.0), (0.2, -0.1, 0.3)),
 }
+
+
+@pytest.mark.parametrize("p", [11, 12])
+def test_two_part_class_images(p):
+    """Orders 11 and 12: the class-matrix image no longer fits shared memory
+    whole, so the tcgen05 M2L brings it in two parts per tile.  The product
+    must still run on the tensor cores and match the float64 plan's product
+    at the same order within the mixed form's 2e-6."""
+    m = I.icosphere(3, I.TRI6)
+    prm = dict(p=p, leaf_size=32, eta=2.0)
+    Pm = Plan(m, precision=bem.BEM_MIXED, **prm)
+    Pd = Plan(m, **prm)
+    try:
+        assert Pm.stats()["m2l_tensor_cores"] == 1
+        for op, n, seed in ((bem.BEM_OP_A, Pm.n_phi, 3), (bem.BEM_OP_B, Pm.n_chi, 4)):
+            x = I.random_vector(n, seed)
+            e = rel_l2(Pm.matvec(op, x), Pd.matvec(op, x))
+            print(f"p = {p}, op {op}: mixed vs float64 {e:.3e}")
+            assert e <= MX_MATVEC_TOL, e
+        assert bem.bem_plan_device_status(Pm.plan) == 0
+    finally:
+        Pm.close()
+        Pd.close()
 
 
 @pytest.mark.parametrize("name", list(CASES))
