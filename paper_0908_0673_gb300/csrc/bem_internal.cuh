@@ -379,6 +379,8 @@ struct bem_plan : bem::FmmState {
     int last_op = -1;
     // GMRES workspace
     double *V = nullptr, *H = nullptr, *gs = nullptr, *w = nullptr, *xk = nullptr, *bvec = nullptr;
+    double *zbuf = nullptr;             // the preconditioned Arnoldi vector M^-1 V_j (the product's input)
+    double *dinv = nullptr;             // 1 / C_i: GMRES's right preconditioner M = diag(C) [N]
     double *bc_vec = nullptr, *bc_sc = nullptr;   // BiCGStab vectors (r, rh, p, v, s, t) and scalars
     int *bc_st = nullptr;
     double *scal = nullptr;             // device scalars

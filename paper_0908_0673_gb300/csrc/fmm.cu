@@ -881,10 +881,15 @@ __global__ void k_combine_f(int N, const int *__restrict__ ptr, const int *__res
     }
 }
 
-// C_i = 1 + (regular Laplace double layer of phi = 1) + (correction row sum)
-__global__ void k_finish_diag(int N, const double *__restrict__ ytmp, double *Cdiag) {
+// C_i = 1 + (regular Laplace double layer of phi = 1) + (correction row sum),
+// and 1 / C_i for the solver's diagonal preconditioner
+__global__ void k_finish_diag(int N, const double *__restrict__ ytmp, double *Cdiag, double *dinv) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < N) Cdiag[i] = 1.0 + ytmp[i] + Cdiag[i];
+    if (i < N) {
+        const double c = 1.0 + ytmp[i] + Cdiag[i];
+        Cdiag[i] = c;
+        dinv[i] = 1.0 / c;
+    }
 }
 
 __global__ void k_fill(int64_t n, double v, double *a) {
@@ -1233,7 +1238,8 @@ int diagonal_product(bem_plan *P, cudaStream_t s) {
 
 int diagonal_finish(bem_plan *P, cudaStream_t s) {
     const int N = (int)P->N;
-    (k_finish_diag<<<(N + 255) / 256, 256, 0, s>>>(N, P->diag_state.ytmp, P->C), ::bem::count_launch());
+    BEM_TRY(P->arena.alloc(&P->dinv, P->N));
+    (k_finish_diag<<<(N + 255) / 256, 256, 0, s>>>(N, P->diag_state.ytmp, P->C, P->dinv), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
     BEM_CUDA(cudaStreamSynchronize(s));
     P->arena.release(P->diag_ones);

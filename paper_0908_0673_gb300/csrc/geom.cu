@@ -979,25 +979,36 @@ __device__ __forceinline__ bool split_coded(const float *df, unsigned code, cons
 }
 
 // Near-singular pairs, the light ones in two steps.  Most pairs refine at
-// most twice (the root, which always splits, and some of its children): one
-// thread per pair walks those two levels unrolled in registers and writes
-// the pair's leaf pieces (at most 16) as 32-bit codes into the pair's slots;
-// a pair with a piece of level 2 that splits as well goes to a list of deep
-// pairs for k_special_near, whose 8 lanes per pair refine it level by level.
-// The light pairs' points are then evaluated by k_near_eval without the
-// refinement's control flow.  Both paths decide every piece by split_test
-// (the float32 estimate from the corner images, else the float64 test), so
-// the pieces are the same as the oracle's.
+// most twice or three times (the root always splits): one thread per pair
+// walks the first levels unrolled in registers and writes the pair's leaf
+// pieces as 32-bit codes into slots of its own, and k_near_eval then
+// evaluates their points without the refinement's control flow.  The first
+// walk covers two levels (16 slots per pair); the pairs with a level-2 piece
+// that splits (about a tenth) are listed in pair order and walked again over
+// three levels (64 slots, for up to NW_DEEP_SHARE of the pairs); the pairs
+// that refine further, or beyond that share, go to k_special_near, whose 8
+// lanes per pair refine level by level.  Every path decides each piece by
+// split_test (the float32 estimate from the corner images, else the float64
+// test), so the pieces are the same as the oracle's, and which path a pair
+// takes depends on its geometry only.
 constexpr int NW_T = 128;           // threads per block of the walk
-constexpr int NW_SLOTS = 16;        // leaf slots per light pair: 4 children x 4 grandchildren
+constexpr int NW_DEEP_SHARE = 8;    // the second walk takes up to 1 / 8 of the pairs
 constexpr int NE_W = 8;             // lanes per pair in the evaluation
 constexpr int NE_WARPS = 4;         // warps per block of the evaluation
 
-template <int NPE>
-__global__ void __launch_bounds__(NW_T) k_near_walk(CorrArgs a, int nlist, const int *__restrict__ list,
-                                                    const int *__restrict__ pair_node, const int *__restrict__ pair_e,
-                                                    int *cnt, unsigned *leaves, int *deep_list, int *ndeep) {
+__host__ __device__ constexpr int nw_slots(int levels) { return levels == 2 ? 16 : 64; }
+
+// LEVELS = 2: cnt[li] = leaves, or -1 and flag[li] = 1 for a deeper pair;
+// LEVELS = 3: the list is the deeper pairs' (length min(nlist, *nlist_dev)),
+// cnt[li] = leaves, or -1 with the pair appended to deeper[] for the refinement
+template <int NPE, int LEVELS>
+__global__ void __launch_bounds__(NW_T) k_near_walk(CorrArgs a, int nlist, const int *__restrict__ nlist_dev,
+                                                    const int *__restrict__ list, const int *__restrict__ pair_node,
+                                                    const int *__restrict__ pair_e, int *cnt, unsigned *leaves,
+                                                    int *flag, int *deeper, int *ndeeper) {
+    constexpr int SLOTS = nw_slots(LEVELS);
     const int li = blockIdx.x * NW_T + threadIdx.x;
+    if (nlist_dev) nlist = min(nlist, *nlist_dev);
     if (li >= nlist) return;
     const int pr = list[li], node = pair_node[pr], e = pair_e[pr];
     double xi[3], X[3 * NPE];
@@ -1013,7 +1024,7 @@ __global__ void __launch_bounds__(NW_T) k_near_walk(CorrArgs a, int nlist, const
     }
     const float tau2 = (float)(a.tau * a.tau);
     const int maxdepth = a.maxdepth;
-    unsigned *out = leaves + (size_t)li * NW_SLOTS;
+    unsigned *out = leaves + (size_t)li * SLOTS;
     int n = 0;
     const unsigned root = piece_code(0, 0, 0, 0);
     bool deep = false;
@@ -1033,9 +1044,9 @@ __global__ void __launch_bounds__(NW_T) k_near_walk(CorrArgs a, int nlist, const
         const PieceImg rimg{v0, v1, v2};
 #pragma unroll
         for (int c1 = 0; c1 < 4; c1++) {
+            if (deep) break;
             const unsigned k1 = child_of(root, c1);
             const PieceImg i1 = child_img(rimg, m01, m12, m20, c1);
-            if (deep) break;
             if (!split_coded<NPE>(df, k1, i1, X, xi, tau2, a.tau, maxdepth)) {
                 out[n++] = k1;
                 continue;
@@ -1045,17 +1056,43 @@ __global__ void __launch_bounds__(NW_T) k_near_walk(CorrArgs a, int nlist, const
             for (int c2 = 0; c2 < 4 && !deep; c2++) {
                 const unsigned k2 = child_of(k1, c2);
                 const PieceImg i2 = child_img(i1, mab, mbc, mca, c2);
-                if (split_coded<NPE>(df, k2, i2, X, xi, tau2, a.tau, maxdepth)) deep = true;
-                else out[n++] = k2;
+                if (!split_coded<NPE>(df, k2, i2, X, xi, tau2, a.tau, maxdepth)) {
+                    out[n++] = k2;
+                    continue;
+                }
+                if (LEVELS == 2) {
+                    deep = true;
+                    break;
+                }
+                float4 nab, nbc, nca;
+                mid_imgs<NPE>(df, code_piece(k2), nab, nbc, nca);
+                for (int c3 = 0; c3 < 4 && !deep; c3++) {
+                    const unsigned k3 = child_of(k2, c3);
+                    const PieceImg i3 = child_img(i2, nab, nbc, nca, c3);
+                    if (split_coded<NPE>(df, k3, i3, X, xi, tau2, a.tau, maxdepth)) deep = true;
+                    else out[n++] = k3;
+                }
             }
         }
     }
-    if (deep) {
-        cnt[li] = -1;
-        deep_list[atomicAdd(ndeep, 1)] = pr;             // list order does not matter: pairs are independent
-    } else {
-        cnt[li] = n;
-    }
+    cnt[li] = deep ? -1 : n;
+    if (LEVELS == 2) flag[li] = deep ? 1 : 0;
+    else if (deep) deeper[atomicAdd(ndeeper, 1)] = pr;   // their order does not matter: pairs are independent
+}
+
+// the flagged pairs of a list, in list order
+__global__ void k_compact_flagged(int n, const int *__restrict__ flag, const int *__restrict__ pos,
+                                  const int *__restrict__ list, int *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && flag[i]) out[pos[i]] = list[i];
+}
+
+// the deeper pairs beyond the second walk's share go straight to the refinement
+__global__ void k_deep_overflow(int cap, const int *__restrict__ ndeep, const int *__restrict__ deep_list, int *deeper,
+                                int *ndeeper) {
+    const int n = *ndeep;
+    for (int i = cap + blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        deeper[atomicAdd(ndeeper, 1)] = deep_list[i];
 }
 
 // Evaluation of the light pairs.  A block takes chunks of NE_CHUNK
@@ -1066,7 +1103,8 @@ __global__ void __launch_bounds__(NW_T) k_near_walk(CorrArgs a, int nlist, const
 constexpr int NE_CHUNK = 64;
 
 template <class R, bool HELM, int NPE, int W>
-__global__ void __launch_bounds__(32 * NE_WARPS) k_near_eval(CorrArgs a, int nlist, const int *__restrict__ list,
+__global__ void __launch_bounds__(32 * NE_WARPS) k_near_eval(CorrArgs a, int nlist, const int *__restrict__ nlist_dev,
+                                                             int slots, const int *__restrict__ list,
                                                              const int *__restrict__ pair_node,
                                                              const int *__restrict__ pair_e, const int *__restrict__ cnt,
                                                              const unsigned *__restrict__ leaves, double *valD,
@@ -1075,9 +1113,16 @@ __global__ void __launch_bounds__(32 * NE_WARPS) k_near_eval(CorrArgs a, int nli
     static_assert(NE_CHUNK % G == 0 && NE_CHUNK <= 32 * NE_WARPS, "chunk");
     __shared__ R sd[G][3 * NPE];
     __shared__ int skey[NE_CHUNK], sorder[NE_CHUNK];
+    __shared__ R srule[3][NQ];                           // the rule in shared memory: lanes read different points
+    if (threadIdx.x < NQ) {
+        srule[0][threadIdx.x] = rule_s<R>(threadIdx.x);
+        srule[1][threadIdx.x] = rule_t<R>(threadIdx.x);
+        srule[2][threadIdx.x] = rule_w<R>(threadIdx.x);
+    }
     const int tid = threadIdx.x, lane = tid & 31, g = tid / W, sl = tid % W;
     const unsigned wmask = (W == 32 ? 0xffffffffu : ((1u << W) - 1u)) << (lane - sl);
     const R kk = (R)a.k;
+    if (nlist_dev) nlist = min(nlist, *nlist_dev);
     for (int c0 = blockIdx.x * NE_CHUNK; c0 < nlist; c0 += gridDim.x * NE_CHUNK) {
         __syncthreads();                                 // the previous chunk's order and keys have been read
         if (tid < NE_CHUNK) skey[tid] = c0 + tid < nlist ? cnt[c0 + tid] : -1;
@@ -1106,16 +1151,22 @@ __global__ void __launch_bounds__(32 * NE_WARPS) k_near_eval(CorrArgs a, int nli
 #pragma unroll
             for (int i = 0; i < NVP; i++) v[i] = 0;
             const int npt = NQ * (1 + skey[o]);
-            const unsigned *lv = leaves + (size_t)li * NW_SLOTS;
+            const unsigned *lv = leaves + (size_t)li * slots;
             // point j = NQ pc + q: pc = 0 the regular rule (negative weights),
             // pc >= 1 leaf pc - 1; lane sl takes j = sl, sl + W, ...
             int pc = sl / NQ, q = sl % NQ;
             for (int j = sl; j < npt; j += W) {
                 R s, t, w;
+                const R rs = srule[0][q], rt = srule[1][q], rw = srule[2][q];
                 if (pc == 0) {
-                    s = rule_s<R>(q); t = rule_t<R>(q); w = -rule_w<R>(q);
+                    s = rs; t = rt; w = -rw;
                 } else {
-                    leaf_point<R>(code_piece(lv[pc - 1]), q, s, t, w);
+                    // the q-th point of the rule on the piece, as leaf_point
+                    const PieceF P = code_piece(lv[pc - 1]);
+                    const R e0 = (R)P.b0 - (R)P.a0, e1 = (R)P.b1 - (R)P.a1, f0 = (R)P.c0 - (R)P.a0, f1 = (R)P.c1 - (R)P.a1;
+                    s = (R)P.a0 + rs * e0 + rt * f0;
+                    t = (R)P.a1 + rs * e1 + rt * f1;
+                    w = rw * fabs(e0 * f1 - e1 * f0);
                 }
                 eval_st<R, HELM, NPE>(sd[g], kk, s, t, w, v);
                 pc += W / NQ;
@@ -1267,21 +1318,44 @@ int build_correction(bem_plan *P, cudaStream_t s) {
         (k_pair_split<<<(npairs + 255) / 256, 256, 0, s>>>(npairs, kind, koff, nself, klist), ::bem::count_launch());
     }
     const int nnear = npairs - nself;
-    // light near-singular pairs: leaf codes and their counts; deep pairs: a list
-    int *lcnt = nullptr, *deep_list = nullptr, *ndeep = nullptr;
-    unsigned *leaves = nullptr;
+    // near-singular pairs: the two-level walk over all of them, the
+    // three-level walk over those it leaves (in pair order, up to a share),
+    // the refinement over the rest
+    const int dcap = std::max(1024, nnear / NW_DEEP_SHARE);
+    int *lcnt = nullptr, *dflag = nullptr, *dpos = nullptr, *dblk = nullptr, *deep_list = nullptr, *ndeep = nullptr;
+    int *cnt2 = nullptr, *deeper = nullptr, *ndeeper = nullptr;
+    unsigned *leaves = nullptr, *leaves2 = nullptr;
     BEM_TRY(A.alloc(&lcnt, std::max(1, nnear)));
+    BEM_TRY(A.alloc(&dflag, std::max(1, nnear)));
+    BEM_TRY(A.alloc(&dpos, std::max(1, nnear)));
+    BEM_TRY(A.alloc(&dblk, scan_scratch(std::max(1, nnear))));
     BEM_TRY(A.alloc(&deep_list, std::max(1, nnear)));
     BEM_TRY(A.alloc(&ndeep, 1));
-    BEM_TRY(A.alloc(&leaves, (size_t)std::max(1, nnear) * NW_SLOTS));
+    BEM_TRY(A.alloc(&cnt2, dcap));
+    BEM_TRY(A.alloc(&deeper, std::max(1, nnear)));
+    BEM_TRY(A.alloc(&ndeeper, 1));
+    BEM_TRY(A.alloc(&leaves, (size_t)std::max(1, nnear) * nw_slots(2)));
+    BEM_TRY(A.alloc(&leaves2, (size_t)dcap * nw_slots(3)));
     BEM_CUDA(cudaMemsetAsync(ndeep, 0, sizeof(int), s));
+    BEM_CUDA(cudaMemsetAsync(ndeeper, 0, sizeof(int), s));
     if (nnear > 0) {
+        const int *nl = klist + nself;
+        const int gw = (nnear + NW_T - 1) / NW_T, gw2 = (dcap + NW_T - 1) / NW_T;
         if (npe == 3)
-            (k_near_walk<3><<<(nnear + NW_T - 1) / NW_T, NW_T, 0, s>>>(a, nnear, klist + nself, pair_node, pair_e, lcnt,
-                                                                      leaves, deep_list, ndeep), ::bem::count_launch());
+            (k_near_walk<3, 2><<<gw, NW_T, 0, s>>>(a, nnear, nullptr, nl, pair_node, pair_e, lcnt, leaves, dflag,
+                                                  nullptr, nullptr), ::bem::count_launch());
         else
-            (k_near_walk<6><<<(nnear + NW_T - 1) / NW_T, NW_T, 0, s>>>(a, nnear, klist + nself, pair_node, pair_e, lcnt,
-                                                                      leaves, deep_list, ndeep), ::bem::count_launch());
+            (k_near_walk<6, 2><<<gw, NW_T, 0, s>>>(a, nnear, nullptr, nl, pair_node, pair_e, lcnt, leaves, dflag,
+                                                  nullptr, nullptr), ::bem::count_launch());
+        BEM_TRY(scan_exclusive(dflag, dpos, nnear, ndeep, dblk, s));
+        (k_compact_flagged<<<(nnear + 255) / 256, 256, 0, s>>>(nnear, dflag, dpos, nl, deep_list), ::bem::count_launch());
+        if (npe == 3)
+            (k_near_walk<3, 3><<<gw2, NW_T, 0, s>>>(a, dcap, ndeep, deep_list, pair_node, pair_e, cnt2, leaves2,
+                                                   nullptr, deeper, ndeeper), ::bem::count_launch());
+        else
+            (k_near_walk<6, 3><<<gw2, NW_T, 0, s>>>(a, dcap, ndeep, deep_list, pair_node, pair_e, cnt2, leaves2,
+                                                   nullptr, deeper, ndeeper), ::bem::count_launch());
+        (k_deep_overflow<<<64, 256, 0, s>>>(dcap, ndeep, deep_list, deeper, ndeeper), ::bem::count_launch());
         BEM_LAUNCH_CHECK();
     }
     {
@@ -1293,14 +1367,20 @@ int build_correction(bem_plan *P, cudaStream_t s) {
         const int gs = (int)std::max<int64_t>(1, ((int64_t)nself + SP_WARPS * SP_PAIRS_PER_WARP - 1) /
                                                      (SP_WARPS * SP_PAIRS_PER_WARP));
         const int ge = (int)std::max<int64_t>(1, ((int64_t)nnear + 4 * NE_CHUNK - 1) / (4 * NE_CHUNK));
+        const int ge2 = (int)std::max<int64_t>(1, ((int64_t)dcap + 4 * NE_CHUNK - 1) / (4 * NE_CHUNK));
         const int gn = 5 * std::max(1, P->sm_count);       // deep pairs: a few per cent, count on the device
 #define BEM_SW(R, H, NP)                                                                                          \
     do {                                                                                                          \
         if (nnear > 0) {                                                                                          \
-            (k_near_eval<R, H, NP, NE_W><<<ge, 32 * NE_WARPS, 0, s>>>(a, nnear, klist + nself, pair_node, pair_e,  \
-                                                                       lcnt, leaves, K.valD, K.valS, d0pair),     \
+            (k_near_eval<R, H, NP, NE_W><<<ge, 32 * NE_WARPS, 0, s>>>(a, nnear, nullptr, nw_slots(2), klist + nself,\
+                                                                       pair_node, pair_e, lcnt, leaves, K.valD,   \
+                                                                       K.valS, d0pair),                           \
              ::bem::count_launch());                                                                              \
-            (k_special_near<R, H, NP><<<gn, 32 * SPN_WARPS, 0, s>>>(a, ndeep, deep_list, pair_node, pair_e,        \
+            (k_near_eval<R, H, NP, NE_W><<<ge2, 32 * NE_WARPS, 0, s>>>(a, dcap, ndeep, nw_slots(3), deep_list,     \
+                                                                        pair_node, pair_e, cnt2, leaves2, K.valD, \
+                                                                        K.valS, d0pair),                          \
+             ::bem::count_launch());                                                                              \
+            (k_special_near<R, H, NP><<<gn, 32 * SPN_WARPS, 0, s>>>(a, ndeeper, deeper, pair_node, pair_e,         \
                                                                     K.valD, K.valS, d0pair),                      \
              ::bem::count_launch());                                                                              \
         }                                                                                                         \
@@ -1330,7 +1410,7 @@ int build_correction(bem_plan *P, cudaStream_t s) {
     // is added by one Laplace double-layer product on phi = 1
     P->C = d0row;
     // the temporaries are released once the stream has finished with them
-    for (void *q : {(void *)ptmp, (void *)lcnt, (void *)deep_list, (void *)ndeep, (void *)leaves, (void *)kind, (void *)koff, (void *)klist, (void *)ktot, (void *)kblk, (void *)cnt, (void *)tot, (void *)sblk, (void *)pair_node, (void *)d0pair, (void *)ecx, (void *)ecy, (void *)ecz,
+    for (void *q : {(void *)ptmp, (void *)lcnt, (void *)dflag, (void *)dpos, (void *)dblk, (void *)deep_list, (void *)ndeep, (void *)cnt2, (void *)deeper, (void *)ndeeper, (void *)leaves, (void *)leaves2, (void *)kind, (void *)koff, (void *)klist, (void *)ktot, (void *)kblk, (void *)cnt, (void *)tot, (void *)sblk, (void *)pair_node, (void *)d0pair, (void *)ecx, (void *)ecy, (void *)ecz,
                     (void *)eh, (void *)ebnd, (void *)frho, (void *)rho, (void *)off, (void *)pair_e})
         P->deferred.push_back(q);
     return BEM_OK;

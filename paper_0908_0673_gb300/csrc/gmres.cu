@@ -271,9 +271,10 @@ __global__ void k_backsolve(GmState S, int m) {
     }
 }
 
-// x += sum_{i<k} y_i V_i
+// x += M^-1 sum_{i<k} y_i V_i  (right preconditioner M = diag(C): dinv = 1 / C)
 template <int C>
-__global__ void k_xupdate(int n, const double *__restrict__ V, size_t ld, GmState S, double *const *xslot) {
+__global__ void k_xupdate(int n, const double *__restrict__ V, size_t ld, GmState S, double *const *xslot,
+                          const double *__restrict__ dinv) {
     if (S.st[2]) return;
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
@@ -281,7 +282,7 @@ __global__ void k_xupdate(int n, const double *__restrict__ V, size_t ld, GmStat
     const int k = S.st[1];
     double a[C];
 #pragma unroll
-    for (int c = 0; c < C; c++) a[c] = x[(size_t)r * C + c];
+    for (int c = 0; c < C; c++) a[c] = 0.0;
     for (int i = 0; i < k; i++) {
         const double *v = V + (size_t)i * ld;
         if (C == 1) {
@@ -293,7 +294,18 @@ __global__ void k_xupdate(int n, const double *__restrict__ V, size_t ld, GmStat
         }
     }
 #pragma unroll
-    for (int c = 0; c < C; c++) x[(size_t)r * C + c] = a[c];
+    for (int c = 0; c < C; c++) x[(size_t)r * C + c] += dinv[r] * a[c];
+}
+
+// z = M^-1 v (the Arnoldi vector into the preconditioned product's input)
+template <int C>
+__global__ void k_precond(int n, const double *__restrict__ v, const double *__restrict__ dinv, double *z,
+                          const int *__restrict__ skip) {
+    if (skip && *skip) return;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+#pragma unroll
+    for (int c = 0; c < C; c++) z[(size_t)r * C + c] = dinv[r] * v[(size_t)r * C + c];
 }
 
 __global__ void k_cycle_init(GmState S, int m) {
@@ -367,6 +379,7 @@ static int gm_workspace(bem_plan *P, int m) {
     }
     if (!P->w) {
         BEM_TRY(P->arena.alloc(&P->w, ne));
+        BEM_TRY(P->arena.alloc(&P->zbuf, ne));
         BEM_TRY(P->arena.alloc(&P->bvec, ne));
         BEM_TRY(P->arena.alloc(&P->scal, 16 + (size_t)GM_BLK * 2 * (200 + 2)));
         BEM_TRY(P->arena.alloc(&P->gm_slot, 2));
@@ -445,7 +458,8 @@ static int gm_k_step(bem_plan *P, int j, cudaStream_t s, bool raw) {
     GmState S = gm_state<C>(P);
     const int eb = (ne + 255) / 256, nb = (n + 255) / 256;
     int *skip = P->istate;
-    BEM_TRY(set_slots(P, V + (size_t)j * ld, w, s));
+    (k_precond<C><<<nb, 256, 0, s>>>(n, V + (size_t)j * ld, P->dinv, P->zbuf, skip), ::bem::count_launch());
+    BEM_TRY(set_slots(P, P->zbuf, w, s));
     BEM_TRY(gm_product(P, BEM_OP_A, s, raw));
     // CGS2: two classical Gram-Schmidt passes against V_0..V_j
     (k_mdot<C><<<GM_BLK, GM_T, 0, s>>>(n, j + 1, V, ld, w, partial, skip), ::bem::count_launch());
@@ -467,7 +481,7 @@ static int gm_k_cycle_end(bem_plan *P, cudaStream_t s) {
     const int n = (int)P->N;
     GmState S = gm_state<C>(P);
     (k_backsolve<C><<<1, 1, 0, s>>>(S, P->gm_restart), ::bem::count_launch());
-    (k_xupdate<C><<<(n + 255) / 256, 256, 0, s>>>(n, P->V, (size_t)n * C, S, (double *const *)P->gm_slot + 1),
+    (k_xupdate<C><<<(n + 255) / 256, 256, 0, s>>>(n, P->V, (size_t)n * C, S, (double *const *)P->gm_slot + 1, P->dinv),
      ::bem::count_launch());
     BEM_LAUNCH_CHECK();
     return BEM_OK;
