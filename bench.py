@@ -84,7 +84,7 @@ def ncu_traffic(stage):
 # used only to extrapolate the CPU oracle's rate to solves (the oracle's
 # product is float64 too).  One RHS product plus these steps; the final
 # true-residual product is left out, in the oracle's favour.
-GMRES_ITERS_CUBE45 = 15
+GMRES_ITERS_CUBE45 = 14
 
 
 def parse():

@@ -8,44 +8,43 @@
 
 namespace bem {
 
-// Outward element normal at local node a of a 3- or 6-node triangle:
-// t1 x t2 / |t1 x t2| with t1 = dx/ds, t2 = dx/dt of the isoparametric map.
+// Outward element normal at local node a of a 3- or 6-node triangle, not
+// normalised: t1 x t2 with t1 = dx/ds, t2 = dx/dt of the isoparametric map
+// (the shape-function derivatives at the node are fixed numbers, tabulated).
 static void node_normal(const double *X, int npe, int a, double n[3]) {
-    static const double S[6] = {0.0, 1.0, 0.0, 0.5, 0.5, 0.0};
-    static const double T[6] = {0.0, 0.0, 1.0, 0.0, 0.5, 0.5};
-    double s = S[a], t = T[a];
-    double ds[6], dt[6];
-    if (npe == 3) {
-        ds[0] = -1; ds[1] = 1; ds[2] = 0;
-        dt[0] = -1; dt[1] = 0; dt[2] = 1;
-    } else {
-        double l0 = 1.0 - s - t;
-        ds[0] = 1.0 - 4.0 * l0; ds[1] = 4.0 * s - 1.0; ds[2] = 0.0;
-        ds[3] = 4.0 * (l0 - s); ds[4] = 4.0 * t; ds[5] = -4.0 * t;
-        dt[0] = 1.0 - 4.0 * l0; dt[1] = 0.0; dt[2] = 4.0 * t - 1.0;
-        dt[3] = -4.0 * s; dt[4] = 4.0 * s; dt[5] = 4.0 * (l0 - t);
-    }
+    // d N_b / ds and d N_b / dt at node a: 6-node rows at (s, t) of node a
+    static const double DS6[6][6] = {{-3, -1, 0, 4, 0, 0},  {1, 3, 0, -4, 0, 0},  {1, -1, 0, 0, 4, -4},
+                                     {-1, 1, 0, 0, 0, 0},   {1, 1, 0, -2, 2, -2}, {-1, -1, 0, 2, 2, -2}};
+    static const double DT6[6][6] = {{-3, 0, -1, 0, 0, 4},  {1, 0, -1, -4, 4, 0}, {1, 0, 3, 0, 0, -4},
+                                     {-1, 0, -1, -2, 2, 2}, {1, 0, 1, -2, 2, -2}, {-1, 0, 1, 0, 0, 0}};
     double u[3] = {0, 0, 0}, v[3] = {0, 0, 0};
-    for (int b = 0; b < npe; b++)
+    if (npe == 3) {
         for (int c = 0; c < 3; c++) {
-            u[c] += ds[b] * X[3 * b + c];
-            v[c] += dt[b] * X[3 * b + c];
+            u[c] = X[3 + c] - X[c];
+            v[c] = X[6 + c] - X[c];
         }
+    } else {
+        for (int b = 0; b < 6; b++)
+            for (int c = 0; c < 3; c++) {
+                u[c] += DS6[a][b] * X[3 * b + c];
+                v[c] += DT6[a][b] * X[3 * b + c];
+            }
+    }
     n[0] = u[1] * v[2] - u[2] * v[1];
     n[1] = u[2] * v[0] - u[0] * v[2];
     n[2] = u[0] * v[1] - u[1] * v[0];
-    double len = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
-    n[0] /= len; n[1] /= len; n[2] /= len;
 }
 
 // Elements are visited in order; at each of their nodes the element normal
 // either joins the first existing cluster of that node whose opening normal is
-// within the angle tolerance, or opens a new cluster (a new chi index).
+// within the angle tolerance, or opens a new cluster (a new chi index).  The
+// clusters live in one flat array: a node's first cluster at its own index,
+// further ones (edges and corners) appended and chained in creation order.
 int64_t mesh_chi_index(const double *nodes, int64_t nn, const int32_t *elems, int64_t ne, int npe,
                        double angle_deg, int32_t *chi) {
     const double cos_tol = std::cos(angle_deg * M_PI / 180.0);
-    struct Cluster { double n[3]; int32_t id; };
-    std::vector<std::vector<Cluster>> per_node(nn);
+    struct Cluster { double n[3]; int32_t id, next; };
+    std::vector<Cluster> cl((size_t)nn, Cluster{{0.0, 0.0, 0.0}, -1, -1});
     int64_t count = 0;
     double X[18];
     for (int64_t e = 0; e < ne; e++) {
@@ -54,13 +53,23 @@ int64_t mesh_chi_index(const double *nodes, int64_t nn, const int32_t *elems, in
         for (int a = 0; a < npe; a++) {
             double n[3];
             node_normal(X, npe, a, n);
-            auto &list = per_node[elems[e * npe + a]];
+            const double len = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+            // clusters keep unit normals: cos(angle) >= cos_tol  <=>  n . m >= cos_tol |n|
+            const double thr = cos_tol * len;
+            int64_t k = elems[e * npe + a], last = -1;
             int32_t id = -1;
-            for (const Cluster &cl : list)
-                if (n[0] * cl.n[0] + n[1] * cl.n[1] + n[2] * cl.n[2] >= cos_tol) { id = cl.id; break; }
+            if (cl[k].id >= 0)
+                for (; k >= 0; last = k, k = cl[k].next)
+                    if (n[0] * cl[k].n[0] + n[1] * cl[k].n[1] + n[2] * cl[k].n[2] >= thr) { id = cl[k].id; break; }
             if (id < 0) {
                 id = (int32_t)count++;
-                list.push_back({{n[0], n[1], n[2]}, id});
+                const Cluster c{{n[0] / len, n[1] / len, n[2] / len}, id, -1};
+                if (last < 0) {
+                    cl[elems[e * npe + a]] = c;                 // the node's first cluster
+                } else {
+                    cl[last].next = (int32_t)cl.size();
+                    cl.push_back(c);
+                }
             }
             chi[e * npe + a] = id;
         }
