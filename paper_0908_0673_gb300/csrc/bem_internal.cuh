@@ -380,6 +380,7 @@ struct bem_plan : bem::FmmState {
     // GMRES workspace
     double *V = nullptr, *H = nullptr, *gs = nullptr, *w = nullptr, *xk = nullptr, *bvec = nullptr;
     double *zbuf = nullptr;             // the preconditioned Arnoldi vector M^-1 V_j (the product's input)
+    double *npart = nullptr;            // per-block partial sums of |w|^2 [ceil(N / 256)]
     double *dinv = nullptr;             // 1 / C_i: GMRES's right preconditioner M = diag(C) [N]
     double *bc_vec = nullptr, *bc_sc = nullptr;   // BiCGStab vectors (r, rh, p, v, s, t) and scalars
     int *bc_st = nullptr;

@@ -78,28 +78,86 @@ __global__ void k_mdot_final(int nv, const double *__restrict__ partial, double 
         for (int c = 0; c < C; c++) out[(size_t)i * C + c] = (accumulate ? out[(size_t)i * C + c] : 0.0) + s[c];
 }
 
-// w -= sum_{i<nv} h_i V_i   (h from the latest Gram-Schmidt pass)
+// One Gram-Schmidt update with its reduction: h_i = sum_blk partial[i][blk]
+// (every block sums the partials itself, in k_mdot_final's order; block 0
+// stores h), then w -= sum_i h_i V_i on this block's rows.  NORM: the block
+// also leaves the sum of |w|^2 over its rows in npart[block].
+constexpr int GM_MAXV = 201;    // Krylov vectors of a cycle at most (restart <= 200)
+template <int C, bool NORM>
+__global__ void __launch_bounds__(GM_T) k_orth_fused(int n, int nv, const double *__restrict__ V, size_t ld,
+                                                     const double *__restrict__ partial, double *hout, double *w,
+                                                     double *npart, const int *__restrict__ skip) {
+    if (skip && *skip) return;
+    __shared__ double hs[GM_MAXV * C];
+    __shared__ double red[GM_T / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = warp; i < nv; i += GM_T / 32) {
+        double t[C];
+#pragma unroll
+        for (int c = 0; c < C; c++) t[c] = 0.0;
+        for (int b = lane; b < GM_BLK; b += 32)
+#pragma unroll
+            for (int c = 0; c < C; c++) t[c] += partial[((size_t)i * GM_BLK + b) * C + c];
+#pragma unroll
+        for (int c = 0; c < C; c++)
+            for (int off = 16; off; off >>= 1) t[c] += __shfl_xor_sync(0xffffffffu, t[c], off);
+        if (lane == 0)
+#pragma unroll
+            for (int c = 0; c < C; c++) {
+                hs[i * C + c] = t[c];
+                if (blockIdx.x == 0) hout[(size_t)i * C + c] = t[c];
+            }
+    }
+    __syncthreads();
+    const int r = blockIdx.x * GM_T + tid;
+    double sq = 0.0;
+    if (r < n) {
+        double a[C];
+#pragma unroll
+        for (int c = 0; c < C; c++) a[c] = w[(size_t)r * C + c];
+        for (int i = 0; i < nv; i++) {
+            const double *v = V + (size_t)i * ld;
+            if (C == 1) {
+                a[0] -= hs[i] * v[r];
+            } else {
+                double hr = hs[2 * i], hi = hs[2 * i + 1], vr = v[2 * (size_t)r], vi = v[2 * (size_t)r + 1];
+                a[0] -= hr * vr - hi * vi;
+                a[C - 1] -= hr * vi + hi * vr;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < C; c++) {
+            w[(size_t)r * C + c] = a[c];
+            sq += a[c] * a[c];
+        }
+    }
+    if (NORM) {
+        for (int off = 16; off; off >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, off);
+        if (lane == 0) red[warp] = sq;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int k = 0; k < GM_T / 32; k++) t += red[k];
+            npart[blockIdx.x] = t;
+        }
+    }
+}
+
+// V_out = x / *den (0 if *den is 0) and z = M^-1 V_out: the next Arnoldi
+// vector and the preconditioned product's input
 template <int C>
-__global__ void k_orth_update(int n, int nv, const double *__restrict__ V, size_t ld, const double *__restrict__ h,
-                              double *w, const int *__restrict__ skip) {
+__global__ void k_scale_precond(int n, const double *__restrict__ x, const double *__restrict__ den, double *vout,
+                                const double *__restrict__ dinv, double *z, const int *__restrict__ skip) {
     if (skip && *skip) return;
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
-    double a[C];
+    const double d = *den, di = dinv[r];
 #pragma unroll
-    for (int c = 0; c < C; c++) a[c] = w[(size_t)r * C + c];
-    for (int i = 0; i < nv; i++) {
-        const double *v = V + (size_t)i * ld;
-        if (C == 1) {
-            a[0] -= h[i] * v[r];
-        } else {
-            double hr = h[2 * i], hi = h[2 * i + 1], vr = v[2 * (size_t)r], vi = v[2 * (size_t)r + 1];
-            a[0] -= hr * vr - hi * vi;
-            a[C - 1] -= hr * vi + hi * vr;
-        }
+    for (int c = 0; c < C; c++) {
+        const double v = d > 0.0 ? x[(size_t)r * C + c] / d : 0.0;
+        vout[(size_t)r * C + c] = v;
+        z[(size_t)r * C + c] = di * v;
     }
-#pragma unroll
-    for (int c = 0; c < C; c++) w[(size_t)r * C + c] = a[c];
 }
 
 // out = sum of |v|^2 partials
@@ -124,16 +182,6 @@ __global__ void k_nrm2_final(const double *__restrict__ partial, double *out, co
     for (int b = threadIdx.x; b < GM_BLK; b += 32) s += partial[b];
     for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
     if (threadIdx.x == 0) *out = sqrt(s);
-}
-
-// y = a * x  (a = 1 / *den), used for V_{j+1} = w / ||w|| and V_0 = r / beta
-__global__ void k_scale(int n, const double *__restrict__ x, const double *__restrict__ den, double *y,
-                        const int *__restrict__ skip) {
-    if (skip && *skip) return;
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    const double d = *den;
-    y[r] = d > 0.0 ? x[r] / d : 0.0;
 }
 
 // r = b - r  (r holds A x on entry)
@@ -206,9 +254,17 @@ struct GmState {
 
 // Hessenberg column j: fold in h (from CGS2) and ||w||, apply previous
 // rotations, compute the new one, update g and the residual estimate.
+// (launched with one warp: the norm ||w|| from nblk block partials first)
 template <int C>
-__global__ void k_givens(GmState S, int m, int j) {
+__global__ void k_givens(GmState S, int m, int j, const double *__restrict__ npart, int nblk) {
     if (S.st[0]) return;
+    {
+        double t = 0.0;
+        for (int b = threadIdx.x; b < nblk; b += 32) t += npart[b];
+        for (int off = 16; off; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+        if (threadIdx.x != 0) return;
+        S.sc[4] = sqrt(t);
+    }
     double *Hc = S.H + (size_t)j * (m + 1) * 2;       // column j, rows 0..j+1, complex pairs
     for (int i = 0; i <= j; i++) {
         Hc[2 * i] = S.hcol[i * C] + S.hcol2[i * C];
@@ -297,17 +353,6 @@ __global__ void k_xupdate(int n, const double *__restrict__ V, size_t ld, GmStat
     for (int c = 0; c < C; c++) x[(size_t)r * C + c] += dinv[r] * a[c];
 }
 
-// z = M^-1 v (the Arnoldi vector into the preconditioned product's input)
-template <int C>
-__global__ void k_precond(int n, const double *__restrict__ v, const double *__restrict__ dinv, double *z,
-                          const int *__restrict__ skip) {
-    if (skip && *skip) return;
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
-#pragma unroll
-    for (int c = 0; c < C; c++) z[(size_t)r * C + c] = dinv[r] * v[(size_t)r * C + c];
-}
-
 __global__ void k_cycle_init(GmState S, int m) {
     S.st[0] = S.st[2];
     S.st[1] = 0;
@@ -380,6 +425,7 @@ static int gm_workspace(bem_plan *P, int m) {
     if (!P->w) {
         BEM_TRY(P->arena.alloc(&P->w, ne));
         BEM_TRY(P->arena.alloc(&P->zbuf, ne));
+        BEM_TRY(P->arena.alloc(&P->npart, ((size_t)P->N + 255) / 256));
         BEM_TRY(P->arena.alloc(&P->bvec, ne));
         BEM_TRY(P->arena.alloc(&P->scal, 16 + (size_t)GM_BLK * 2 * (200 + 2)));
         BEM_TRY(P->arena.alloc(&P->gm_slot, 2));
@@ -442,10 +488,12 @@ static int gm_k_residual(bem_plan *P, cudaStream_t s, bool raw) {
 // captured group graphs the whole cycle.
 template <int C>
 static int gm_k_cycle_begin(bem_plan *P, cudaStream_t s) {
-    const int ne = (int)P->N * C, eb = (ne + 255) / 256;
+    const int n = (int)P->N, nb = (n + 255) / 256;
     GmState S = gm_state<C>(P);
-    (k_scale<<<eb, 256, 0, s>>>(ne, P->V, S.sc + 1, P->V, P->istate), ::bem::count_launch());
+    (k_scale_precond<C><<<nb, 256, 0, s>>>(n, P->V, S.sc + 1, P->V, P->dinv, P->zbuf, P->istate), ::bem::count_launch());
     (k_cycle_init<<<1, 1, 0, s>>>(S, P->gm_restart), ::bem::count_launch());
+    // every product of the cycle reads M^-1 V_j from zbuf and writes w
+    BEM_TRY(set_slots(P, P->zbuf, P->w, s));
     BEM_LAUNCH_CHECK();
     return BEM_OK;
 }
@@ -456,22 +504,20 @@ static int gm_k_step(bem_plan *P, int j, cudaStream_t s, bool raw) {
     const size_t ld = (size_t)ne;
     double *V = P->V, *w = P->w, *partial = P->scal + 16;
     GmState S = gm_state<C>(P);
-    const int eb = (ne + 255) / 256, nb = (n + 255) / 256;
+    const int nb = (n + 255) / 256;
     int *skip = P->istate;
-    (k_precond<C><<<nb, 256, 0, s>>>(n, V + (size_t)j * ld, P->dinv, P->zbuf, skip), ::bem::count_launch());
-    BEM_TRY(set_slots(P, P->zbuf, w, s));
+    // the product of M^-1 V_j (zbuf, written with V_j) into w
     BEM_TRY(gm_product(P, BEM_OP_A, s, raw));
-    // CGS2: two classical Gram-Schmidt passes against V_0..V_j
+    // CGS2: two classical Gram-Schmidt passes against V_0..V_j, each a
+    // partial-sum pass and an update that reduces the partials itself; the
+    // second also sums |w|^2 per block for the norm in the rotation step
     (k_mdot<C><<<GM_BLK, GM_T, 0, s>>>(n, j + 1, V, ld, w, partial, skip), ::bem::count_launch());
-    (k_mdot_final<C><<<(j + 1 + 7) / 8, 256, 0, s>>>(j + 1, partial, S.hcol, 0, skip), ::bem::count_launch());
-    (k_orth_update<C><<<nb, 256, 0, s>>>(n, j + 1, V, ld, S.hcol, w, skip), ::bem::count_launch());
+    (k_orth_fused<C, false><<<nb, GM_T, 0, s>>>(n, j + 1, V, ld, partial, S.hcol, w, nullptr, skip), ::bem::count_launch());
     (k_mdot<C><<<GM_BLK, GM_T, 0, s>>>(n, j + 1, V, ld, w, partial, skip), ::bem::count_launch());
-    (k_mdot_final<C><<<(j + 1 + 7) / 8, 256, 0, s>>>(j + 1, partial, S.hcol2, 0, skip), ::bem::count_launch());
-    (k_orth_update<C><<<nb, 256, 0, s>>>(n, j + 1, V, ld, S.hcol2, w, skip), ::bem::count_launch());
-    (k_nrm2_partial<C><<<GM_BLK, GM_T, 0, s>>>(n, w, partial, skip), ::bem::count_launch());
-    (k_nrm2_final<<<1, 32, 0, s>>>(partial, S.sc + 4, skip), ::bem::count_launch());
-    (k_givens<C><<<1, 1, 0, s>>>(S, m, j), ::bem::count_launch());
-    (k_scale<<<eb, 256, 0, s>>>(ne, w, S.sc + 4, V + (size_t)(j + 1) * ld, skip), ::bem::count_launch());
+    (k_orth_fused<C, true><<<nb, GM_T, 0, s>>>(n, j + 1, V, ld, partial, S.hcol2, w, P->npart, skip), ::bem::count_launch());
+    (k_givens<C><<<1, 32, 0, s>>>(S, m, j, P->npart, nb), ::bem::count_launch());
+    (k_scale_precond<C><<<nb, 256, 0, s>>>(n, w, S.sc + 4, V + (size_t)(j + 1) * ld, P->dinv, P->zbuf, skip),
+     ::bem::count_launch());
     BEM_LAUNCH_CHECK();
     return BEM_OK;
 }
