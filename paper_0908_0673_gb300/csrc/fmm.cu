@@ -425,7 +425,12 @@ __global__ void __launch_bounds__(NF_T) k_near(int nleaf, Tabs tb, TreeView tv, 
 constexpr int NF2_T = 256, NF2_TILE = 1024, NF2_ENT = 256;
 __host__ __device__ constexpr int nf2_u(int C) { return C == 1 ? 8 : 4; }
 // sources per staged round: 3 float4 each in the packed real form, 2 complex
-__host__ __device__ constexpr int nf2_tile(int C) { return C == 1 ? 640 : NF2_TILE; }
+// (1024 real sources per round, three blocks per SM: 0.437 ms against 0.456 for
+// 640 at four blocks on the cube workload, the rounds' barriers and staging
+// halved)
+__host__ __device__ constexpr int nf2_tile(int C) { return C == 1 ? 1024 : NF2_TILE; }
+// float4 slots of the staged-source region
+__host__ __device__ constexpr int nf2_stage(int C) { return C == 1 ? 3 * nf2_tile(1) : 2 * NF2_TILE; }
 
 // Work items of the float32 near field: one per (leaf, pass of up to 8 U
 // targets), ordered by decreasing pair count (targets x near sources, ties in
@@ -530,7 +535,7 @@ struct KahanF {
 // shared memory of the float32 near field beyond its static part: the staged
 // sources (sa, sb) and the per-thread compensated sums
 __host__ __device__ constexpr size_t nf2_dyn_bytes(int C) {
-    return 2 * NF2_TILE * sizeof(float4) + 2 * (size_t)nf2_u(C) * C * NF2_T * sizeof(float);
+    return (size_t)nf2_stage(C) * sizeof(float4) + 2 * (size_t)nf2_u(C) * C * NF2_T * sizeof(float);
 }
 
 template <int C, bool DL>
@@ -553,7 +558,7 @@ __global__ void __launch_bounds__(NF2_T, 4) k_near_f32(int nitem, const int2 *__
     extern __shared__ float4 near_tile[];
     float4 *sa = near_tile, *sb = near_tile + NF2_TILE;                 // C = 2: position | Re f, normal | Im f
     float4 *s0 = near_tile, *s1 = s0 + TILE, *s2 = s1 + TILE;           // C = 1: packed (see the staging)
-    float *ks = (float *)(near_tile + 2 * NF2_TILE);  // [UC][NF2_T] compensated sums
+    float *ks = (float *)(near_tile + nf2_stage(C));  // [UC][NF2_T] compensated sums
     float *kc = ks + UC * NF2_T;                      // [UC][NF2_T] their carries
     float *red = (float *)near_tile;                  // [slice][slot][C]
     float *lred = red + NF2_T * UC;                   // [part][slot][C]

@@ -297,46 +297,48 @@ __device__ int digit_lower_bound(const unsigned long long *codes, int b, int e, 
     return b;
 }
 
+// Splitting a level: eight lanes per box, lane d finding the code range of
+// child octant d by two binary searches; a ballot over the group gives the
+// number of non-empty octants and each one's place among them.
 __global__ void k_count_children(const unsigned long long *__restrict__ codes, const int *__restrict__ nb,
                                  const int *__restrict__ ne, int off, int cnt, int level, int B, int max_level,
                                  int *__restrict__ nch) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= cnt) return;
-    int b = off + j, s = nb[b], e = ne[b], c = 0;
-    if (e - s >= B && level < max_level) {
-        for (int d = 0; d < 8; d++) {
-            int lo = digit_lower_bound(codes, s, e, level, d);
-            int hi = digit_lower_bound(codes, s, e, level, d + 1);
-            c += hi > lo;
-        }
-    }
-    nch[j] = c;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, j = tid >> 3, d = tid & 7, lane = threadIdx.x & 31;
+    const unsigned gmask = 0xffu << (lane & ~7);
+    if (j >= cnt) return;                              // whole groups leave together (cnt * 8 threads)
+    const int b = off + j, s = nb[b], e = ne[b];
+    bool has = false;
+    if (e - s >= B && level < max_level)
+        has = digit_lower_bound(codes, s, e, level, d + 1) > digit_lower_bound(codes, s, e, level, d);
+    const unsigned m = __ballot_sync(gmask, has) & gmask;
+    if (d == 0) nch[j] = __popc(m);
 }
 
 __global__ void k_write_children(const unsigned long long *__restrict__ codes, int off, int cnt, int level,
                                  const int *__restrict__ nch, const int *__restrict__ choff, int child_base,
                                  int *nb, int *ne, int *ix, int *iy, int *iz, int *lev, int *parent,
                                  int *child0, int *nchild) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, j = tid >> 3, d = tid & 7, lane = threadIdx.x & 31;
+    const unsigned gmask = 0xffu << (lane & ~7);
     if (j >= cnt) return;
-    int b = off + j;
-    nchild[b] = nch[j];
-    child0[b] = nch[j] ? child_base + choff[j] : -1;
-    if (!nch[j]) return;
-    int s = nb[b], e = ne[b], w = child_base + choff[j];
-    for (int d = 0; d < 8; d++) {
-        int lo = digit_lower_bound(codes, s, e, level, d);
-        int hi = digit_lower_bound(codes, s, e, level, d + 1);
-        if (hi <= lo) continue;
-        nb[w] = lo;
-        ne[w] = hi;
-        ix[w] = 2 * ix[b] + (d & 1);
-        iy[w] = 2 * iy[b] + ((d >> 1) & 1);
-        iz[w] = 2 * iz[b] + ((d >> 2) & 1);
-        lev[w] = level + 1;
-        parent[w] = b;
-        w++;
+    const int b = off + j, n = nch[j];
+    if (d == 0) {
+        nchild[b] = n;
+        child0[b] = n ? child_base + choff[j] : -1;
     }
+    if (!n) return;                                    // the whole group
+    const int s = nb[b], e = ne[b];
+    const int lo = digit_lower_bound(codes, s, e, level, d), hi = digit_lower_bound(codes, s, e, level, d + 1);
+    const unsigned m = __ballot_sync(gmask, hi > lo) & gmask;
+    if (hi <= lo) return;
+    const int w = child_base + choff[j] + __popc(m & ((1u << lane) - 1u) & gmask);
+    nb[w] = lo;
+    ne[w] = hi;
+    ix[w] = 2 * ix[b] + (d & 1);
+    iy[w] = 2 * iy[b] + ((d >> 1) & 1);
+    iz[w] = 2 * iz[b] + ((d >> 2) & 1);
+    lev[w] = level + 1;
+    parent[w] = b;
 }
 
 __global__ void k_box_geometry(int nbox, const int *__restrict__ lev, const int *__restrict__ ix,
@@ -500,7 +502,7 @@ int build_tree(bem_plan *P, cudaStream_t s) {
         BEM_TRY(grow(A, &nch, c1, (size_t)cnt, 0, s));
         BEM_TRY(grow(A, &choff, c2, (size_t)cnt, 0, s));
         cap_tmp = std::min(c1, c2);
-        (k_count_children<<<(cnt + 255) / 256, 256, 0, s>>>(t.codes, nb, ne, off, cnt, level, P->prm.leaf_size,
+        (k_count_children<<<(8 * cnt + 255) / 256, 256, 0, s>>>(t.codes, nb, ne, off, cnt, level, P->prm.leaf_size,
                                                            P->prm.max_level, nch), ::bem::count_launch());
         BEM_LAUNCH_CHECK();
         BEM_TRY(scan_exclusive(nch, choff, cnt, total, sblk, s));
@@ -509,7 +511,7 @@ int build_tree(bem_plan *P, cudaStream_t s) {
         BEM_CUDA(cudaStreamSynchronize(s));
         int base = t.lev_off[level + 1];
         BEM_TRY(grow_all((size_t)base + htot, (size_t)base));
-        (k_write_children<<<(cnt + 255) / 256, 256, 0, s>>>(t.codes, off, cnt, level, nch, choff, base, nb, ne, ix,
+        (k_write_children<<<(8 * cnt + 255) / 256, 256, 0, s>>>(t.codes, off, cnt, level, nch, choff, base, nb, ne, ix,
                                                            iy, iz, lev, par, c0, nc), ::bem::count_launch());
         BEM_LAUNCH_CHECK();
         t.lev_off.push_back(base + htot);
@@ -692,16 +694,69 @@ __device__ int2 walk_lists(const ListArgs &a, int b, bool write, int *near_out, 
     return make_int2(nn, ni);
 }
 
+// One entry N of the parent's near list, walked as walk_lists does (its
+// children, or N itself when a leaf; non-leaf boxes opened for a leaf b when
+// leaf_descend is on); entries go to near_out / inter_out from positions
+// nbase / ibase on, below cap.  Returns the counts.
+__device__ int2 walk_entry(const ListArgs &a, int b, bool bleaf, int N, bool write, int *near_out, int *inter_out,
+                           int nbase, int ibase, int cap) {
+    int nn = 0, ni = 0;
+    int stack[8 * 24];
+    int sp = 0;
+    if (a.nchild[N] == 0) {
+        stack[sp++] = N;
+    } else {
+        for (int c = a.child0[N] + a.nchild[N] - 1; c >= a.child0[N]; c--) stack[sp++] = c;
+    }
+    while (sp > 0) {
+        int C = stack[--sp];
+        if (separated(a, b, C)) {
+            if (write && ibase + ni < cap) inter_out[ibase + ni] = C;
+            ni++;
+        } else if (bleaf && a.leaf_descend && a.nchild[C] != 0) {
+            for (int c = a.child0[C] + a.nchild[C] - 1; c >= a.child0[C]; c--) stack[sp++] = c;
+        } else {
+            if (write && nbase + nn < cap) near_out[nbase + nn] = C;
+            nn++;
+        }
+    }
+    return make_int2(nn, ni);
+}
+
 // Counts every box's entries and keeps the first `cap` of each list in
-// tnear / tinter[j * cap ...]; *overflow is set when a list is longer.
-__global__ void k_lists_count(ListArgs a, int off, int cnt, int *cnear, int *cinter, int *tnear, int *tinter, int cap,
-                              int *overflow) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
+// tnear / tinter[j * cap ...]; *overflow is set when a list is longer.  One
+// warp per box: lane l walks the parent's near-list entries l, l + 32, ...,
+// counting first; a warp prefix sum of the counts places each lane's entries
+// where the serial walk would put them, and a second walk writes them.
+constexpr int LW_WARPS = 4;
+__global__ void __launch_bounds__(32 * LW_WARPS) k_lists_count_w(ListArgs a, int off, int cnt, int *cnear,
+                                                                 int *cinter, int *tnear, int *tinter, int cap,
+                                                                 int *overflow) {
+    const int lane = threadIdx.x & 31, j = blockIdx.x * LW_WARPS + (threadIdx.x >> 5);
     if (j >= cnt) return;
-    int2 c = walk_lists(a, off + j, true, tnear + (size_t)j * cap, tinter + (size_t)j * cap, cap);
-    cnear[j] = c.x;
-    cinter[j] = c.y;
-    if (c.x > cap || c.y > cap) atomicOr(overflow, 1);
+    const int b = off + j, p = a.parent[b];
+    const bool bleaf = a.nchild[b] == 0;
+    int *no = tnear + (size_t)j * cap, *io = tinter + (size_t)j * cap;
+    int nn = 0, ni = 0;
+    const int t1 = a.pnear_ptr[p + 1];
+    for (int t0 = a.pnear_ptr[p]; t0 < t1; t0 += 32) {
+        const int t = t0 + lane;
+        const int N = t < t1 ? a.pnear_idx[t] : -1;
+        int2 c = N >= 0 ? walk_entry(a, b, bleaf, N, false, nullptr, nullptr, 0, 0, cap) : make_int2(0, 0);
+        int pn = c.x, pi = c.y;                          // inclusive prefix sums over the lanes
+        for (int o = 1; o < 32; o <<= 1) {
+            const int yn = __shfl_up_sync(0xffffffffu, pn, o), yi = __shfl_up_sync(0xffffffffu, pi, o);
+            if (lane >= o) { pn += yn; pi += yi; }
+        }
+        if (N >= 0) walk_entry(a, b, bleaf, N, true, no, io, nn + pn - c.x, ni + pi - c.y, cap);
+        nn += __shfl_sync(0xffffffffu, pn, 31);
+        ni += __shfl_sync(0xffffffffu, pi, 31);
+    }
+    if (lane == 0) {
+        cnear[j] = nn;
+        cinter[j] = ni;
+        if (nn > cap || ni > cap) atomicOr(overflow, 1);
+    }
 }
 
 // the kept lists into place, with their pointers
@@ -789,7 +844,8 @@ int build_radii_lists(bem_plan *P, cudaStream_t s) {
         (k_close_ptr<<<1, 1, 0, s>>>(t.near_ptr, off, nnear), ::bem::count_launch());
         (k_close_ptr<<<1, 1, 0, s>>>(t.inter_ptr, off, ninter), ::bem::count_launch());
         BEM_CUDA(cudaMemsetAsync(tot + 2, 0, sizeof(int), s));
-        (k_lists_count<<<(cnt + 127) / 128, 128, 0, s>>>(a, off, cnt, cn, ci, tn, ti, LIST_CAP, tot + 2),
+        (k_lists_count_w<<<(cnt + LW_WARPS - 1) / LW_WARPS, 32 * LW_WARPS, 0, s>>>(a, off, cnt, cn, ci, tn, ti,
+                                                                                 LIST_CAP, tot + 2),
          ::bem::count_launch());
         BEM_LAUNCH_CHECK();
         BEM_TRY(scan_exclusive(cn, on, cnt, tot, sblk, s));
