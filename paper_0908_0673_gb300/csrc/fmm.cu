@@ -993,17 +993,17 @@ int alloc_fmm(bem_plan *P, cudaStream_t s) {
                 if (P->lev_p[l] != P->prm.p) P->lev_var = true;
             }
         BEM_TRY(A.alloc(&P->d_lev_p, nlev));
-        BEM_CUDA(cudaMemcpy(P->d_lev_p, P->lev_p.data(), sizeof(int) * nlev, cudaMemcpyHostToDevice));
+        BEM_CUDA(cudaMemcpyAsync(P->d_lev_p, P->lev_p.data(), sizeof(int) * nlev, cudaMemcpyHostToDevice, s));
     }
     const int np = mi.np, nbox = P->t.nbox, C = P->green == BEM_HELMHOLTZ ? 2 : 1;
     BEM_TRY(A.alloc(&P->d_m, np));
     BEM_TRY(A.alloc(&P->d_n, np));
     BEM_TRY(A.alloc(&P->d_k, np));
     BEM_TRY(A.alloc(&P->d_idx3, mi.idx3.size()));
-    BEM_CUDA(cudaMemcpy(P->d_m, mi.m.data(), sizeof(int) * np, cudaMemcpyHostToDevice));
-    BEM_CUDA(cudaMemcpy(P->d_n, mi.n.data(), sizeof(int) * np, cudaMemcpyHostToDevice));
-    BEM_CUDA(cudaMemcpy(P->d_k, mi.k.data(), sizeof(int) * np, cudaMemcpyHostToDevice));
-    BEM_CUDA(cudaMemcpy(P->d_idx3, mi.idx3.data(), sizeof(int) * mi.idx3.size(), cudaMemcpyHostToDevice));
+    BEM_CUDA(cudaMemcpyAsync(P->d_m, mi.m.data(), sizeof(int) * np, cudaMemcpyHostToDevice, s));
+    BEM_CUDA(cudaMemcpyAsync(P->d_n, mi.n.data(), sizeof(int) * np, cudaMemcpyHostToDevice, s));
+    BEM_CUDA(cudaMemcpyAsync(P->d_k, mi.k.data(), sizeof(int) * np, cudaMemcpyHostToDevice, s));
+    BEM_CUDA(cudaMemcpyAsync(P->d_idx3, mi.idx3.data(), sizeof(int) * mi.idx3.size(), cudaMemcpyHostToDevice, s));
     std::vector<double> fact(2 * PMAX + 2), binom((PMAX + 1) * (PMAX + 1), 0.0);
     fact[0] = 1.0;
     for (int i = 1; i < (int)fact.size(); i++) fact[i] = fact[i - 1] * i;
@@ -1011,8 +1011,8 @@ int alloc_fmm(bem_plan *P, cudaStream_t s) {
         for (int b = 0; b <= a; b++) binom[a * (PMAX + 1) + b] = std::round(fact[a] / (fact[b] * fact[a - b]));
     BEM_TRY(A.alloc(&P->d_fact, fact.size()));
     BEM_TRY(A.alloc(&P->d_binom, binom.size()));
-    BEM_CUDA(cudaMemcpy(P->d_fact, fact.data(), sizeof(double) * fact.size(), cudaMemcpyHostToDevice));
-    BEM_CUDA(cudaMemcpy(P->d_binom, binom.data(), sizeof(double) * binom.size(), cudaMemcpyHostToDevice));
+    BEM_CUDA(cudaMemcpyAsync(P->d_fact, fact.data(), sizeof(double) * fact.size(), cudaMemcpyHostToDevice, s));
+    BEM_CUDA(cudaMemcpyAsync(P->d_binom, binom.data(), sizeof(double) * binom.size(), cudaMemcpyHostToDevice, s));
     BEM_TRY(init_shape_table(P->device));
     const bool mx = P->prm.precision == BEM_MIXED;
     if (mx) {

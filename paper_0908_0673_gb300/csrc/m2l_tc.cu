@@ -493,8 +493,12 @@ int build_m2l_sym(bem_plan *P, const std::vector<int> &pair_cls, const std::vect
     std::vector<int> fsig(nfull);
     for (int c = 0; c < nfull; c++) {
         const long long *K = &kvec[3 * (size_t)c];
+        // axes by decreasing |K|, ties in axis order (a stable insertion sort of
+        // three: std::stable_sort would take a heap buffer per class)
         int order[3] = {0, 1, 2};
-        std::stable_sort(order, order + 3, [&](int x, int y) { return std::llabs(K[x]) > std::llabs(K[y]); });
+        for (int x = 1; x < 3; x++)
+            for (int y = x; y > 0 && std::llabs(K[order[y]]) > std::llabs(K[order[y - 1]]); y--)
+                std::swap(order[y], order[y - 1]);
         int pi[3];
         for (int j = 0; j < 3; j++) pi[order[j]] = j;
         int q = 0;
@@ -581,7 +585,7 @@ int build_m2l_sym(bem_plan *P, const std::vector<int> &pair_cls, const std::vect
 // large the mesh, and every target's sum keeps its list order.
 constexpr size_t SY_LP_BYTES = (size_t)128 << 20;
 
-static int build_sym_tiles(bem_plan *P, size_t row_bytes, int64_t &max_rows) {
+static int build_sym_tiles(bem_plan *P, size_t row_bytes, int64_t &max_rows, cudaStream_t s) {
     const int nbox = P->t.nbox, nc = P->sy_ncls;
     const std::vector<int> &ip = P->sy_hip;
     const int64_t npair = P->t.n_inter;
@@ -624,7 +628,8 @@ static int build_sym_tiles(bem_plan *P, size_t row_bytes, int64_t &max_rows) {
     auto up = [&](auto **d, const auto &h) -> int {
         using T = std::decay_t<decltype(h[0])>;
         BEM_TRY(A.alloc((T **)d, std::max<size_t>(1, h.size())));
-        if (!h.empty()) BEM_CUDA(cudaMemcpy(*d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice));
+        // (pageable source: staged before the call returns, so h may go)
+        if (!h.empty()) BEM_CUDA(cudaMemcpyAsync(*d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, s));
         return BEM_OK;
     };
     BEM_TRY(up(&P->sy_tile_cls, tcls));
@@ -725,7 +730,8 @@ int build_sym_tables(bem_plan *P, cudaStream_t s) {
     auto up = [&](auto **d, const auto &h) -> int {
         using T = std::decay_t<decltype(h[0])>;
         BEM_TRY(A.alloc((T **)d, std::max<size_t>(1, h.size())));
-        if (!h.empty()) BEM_CUDA(cudaMemcpy(*d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice));
+        // (pageable source: staged before the call returns, so h may go)
+        if (!h.empty()) BEM_CUDA(cudaMemcpyAsync(*d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, s));
         return BEM_OK;
     };
     BEM_TRY(up(&P->sy_fwd, fwd));
@@ -800,7 +806,7 @@ int build_sym_tables(bem_plan *P, cudaStream_t s) {
         }
     }
     int64_t max_rows = 0;
-    BEM_TRY(build_sym_tiles(P, (size_t)ldp * C * (mx ? sizeof(float) : sizeof(double)), max_rows));
+    BEM_TRY(build_sym_tiles(P, (size_t)ldp * C * (mx ? sizeof(float) : sizeof(double)), max_rows, s));
     const size_t nLp = std::max<size_t>(1, (size_t)max_rows * ldp * C);
     if (mx) BEM_TRY(A.alloc((float **)&P->sy_Lp, nLp));
     else BEM_TRY(A.alloc((double **)&P->sy_Lp, nLp));

@@ -21,6 +21,7 @@
 #include <cmath>
 #include <type_traits>
 #include <map>
+#include <thread>
 #include <tuple>
 #include <unordered_map>
 #include <vector>
@@ -273,6 +274,90 @@ __global__ void __launch_bounds__(TT) k_m2l_tables(int ncls, int p, int np, int 
 // host: tables
 // ---------------------------------------------------------------------------
 
+// Offset classes: key (dl, level for Helmholtz, K).  Offsets of interacting
+// boxes are small integers, so the key packs into 64 bits (17 bits per K
+// component, biased) and goes into a flat open-addressing table (Fibonacci
+// hashing: the product's top bits depend on every bit of the key; the table
+// starts small and doubles at half load, so it stays in cache); a key that
+// does not pack goes to an ordered map.  Per class its offset vector, level
+// difference and key level, in order of first appearance.
+struct ClassSet {
+    std::vector<unsigned long long> tkey = std::vector<unsigned long long>(4096, 0ull);
+    std::vector<int> tval = std::vector<int>(4096, -1);
+    size_t tmask = 4095, tused = 0;
+    int tbits = 12;
+    std::map<std::tuple<int, int, long long, long long, long long>, int> wide;
+    std::vector<int> dls, levs;
+    std::vector<long long> kvec;
+    int find_or_add(long long kx, long long ky, long long kz, int dl, int lv) {
+        constexpr int KB = 17;
+        constexpr long long KMAX = (1ll << (KB - 1)) - 1;
+        if (std::llabs(kx) <= KMAX && std::llabs(ky) <= KMAX && std::llabs(kz) <= KMAX && dl > -64 && dl < 64) {
+            const unsigned long long key =
+                1ull + (((unsigned long long)(kx + KMAX)) | ((unsigned long long)(ky + KMAX) << KB) |
+                        ((unsigned long long)(kz + KMAX) << (2 * KB)) | ((unsigned long long)(dl + 64) << (3 * KB)) |
+                        ((unsigned long long)lv << (3 * KB + 7)));
+            unsigned long long *tk = tkey.data();
+            size_t h = (size_t)((key * 0x9E3779B97F4A7C15ull) >> (64 - tbits));
+            while (tk[h] != 0ull && tk[h] != key) h = (h + 1) & tmask;
+            if (tk[h] == key) return tval[h];
+            if (2 * (tused + 1) > tmask + 1) {
+                grow();
+                tk = tkey.data();
+                h = (size_t)((key * 0x9E3779B97F4A7C15ull) >> (64 - tbits));
+                while (tk[h] != 0ull) h = (h + 1) & tmask;
+            }
+            tk[h] = key;
+            tused++;
+            return tval[h] = add(kx, ky, kz, dl, lv);
+        }
+        auto wk = std::make_tuple(dl, lv, kx, ky, kz);
+        auto it = wide.find(wk);
+        if (it == wide.end()) it = wide.emplace(wk, add(kx, ky, kz, dl, lv)).first;
+        return it->second;
+    }
+    int add(long long kx, long long ky, long long kz, int dl, int lv) {
+        dls.push_back(dl);
+        levs.push_back(lv);
+        kvec.push_back(kx);
+        kvec.push_back(ky);
+        kvec.push_back(kz);
+        return (int)dls.size() - 1;
+    }
+    void grow() {
+        std::vector<unsigned long long> ok;
+        std::vector<int> ov;
+        ok.swap(tkey);
+        ov.swap(tval);
+        tmask = 2 * (tmask + 1) - 1;
+        tbits++;
+        tkey.assign(tmask + 1, 0ull);
+        tval.assign(tmask + 1, -1);
+        for (size_t i = 0; i < ok.size(); i++)
+            if (ok[i]) {
+                size_t h = (size_t)((ok[i] * 0x9E3779B97F4A7C15ull) >> (64 - tbits));
+                while (tkey[h] != 0ull) h = (h + 1) & tmask;
+                tkey[h] = ok[i];
+                tval[h] = ov[i];
+            }
+    }
+};
+
+// the classes of the pairs of boxes [b0, b1), in a set of their own
+static void number_classes(int b0, int b1, bool by_level, const int *lev, const int *ix, const int *iy, const int *iz,
+                           const int *ip, const int *ii, int *pair_cls, ClassSet &S) {
+    for (int b = b0; b < b1; b++) {
+        const int lb = lev[b], xb = ix[b], yb = iy[b], zb = iz[b], lv = by_level ? lb : 0;
+        for (int u = ip[b]; u < ip[b + 1]; u++) {
+            const int s = ii[u], dl = lb - lev[s], e = std::max(0, -dl);
+            // 2 rho 2^e = (2 i_t + 1) 2^e - (2 i_s + 1) 2^(dl + e), an integer vector
+            const long long ft = 1ll << e, fs = 1ll << (dl + e);
+            pair_cls[u] = S.find_or_add((2ll * xb + 1) * ft - (2ll * ix[s] + 1) * fs, (2ll * yb + 1) * ft - (2ll * iy[s] + 1) * fs,
+                                        (2ll * zb + 1) * ft - (2ll * iz[s] + 1) * fs, dl, lv);
+        }
+    }
+}
+
 // Offset classes of the interaction pairs (independent of the order p).
 int build_m2l_classes(bem_plan *P) {
     const Tree &t = P->t;
@@ -284,90 +369,42 @@ int build_m2l_classes(bem_plan *P) {
     BEM_CUDA(cudaMemcpy(ip.data(), t.inter_ptr, sizeof(int) * (t.nbox + 1), cudaMemcpyDeviceToHost));
     if (t.n_inter) BEM_CUDA(cudaMemcpy(ii.data(), t.inter_idx, sizeof(int) * t.n_inter, cudaMemcpyDeviceToHost));
     const bool helm = P->green == BEM_HELMHOLTZ;
-    // Class key: (dl, level for Helmholtz, K).  Offsets of interacting boxes
-    // are small integers, so the key packs into 64 bits (17 bits per K
-    // component, biased) and goes into a flat open-addressing table; a key
-    // that does not fit the packing uses an ordered map.  The table starts
-    // small and doubles at half load: the pairs are many, their classes few
-    // (a few hundred per level), and a table that stays in cache keeps the
-    // per-pair lookups cheap.
-    const int KB = 17;
-    const long long KMAX = (1ll << (KB - 1)) - 1;
-    std::vector<unsigned long long> tkey(4096, 0ull);
-    std::vector<int> tval(4096, -1);
-    size_t tmask = 4095, tused = 0;
-    int tbits = 12;
-    // Fibonacci hashing: the product's top bits depend on every bit of the key
-    auto slot_of = [&](unsigned long long key) {
-        size_t h = (size_t)((key * 0x9E3779B97F4A7C15ull) >> (64 - tbits));
-        while (tkey[h] != 0ull && tkey[h] != key) h = (h + 1) & tmask;
-        return h;
-    };
-    auto grow = [&]() {
-        std::vector<unsigned long long> ok;
-        std::vector<int> ov;
-        ok.swap(tkey);
-        ov.swap(tval);
-        tmask = 2 * (tmask + 1) - 1;
-        tbits++;
-        tkey.assign(tmask + 1, 0ull);
-        tval.assign(tmask + 1, -1);
-        for (size_t i = 0; i < ok.size(); i++)
-            if (ok[i]) {
-                const size_t h = slot_of(ok[i]);
-                tkey[h] = ok[i];
-                tval[h] = ov[i];
-            }
-    };
-    std::map<std::tuple<int, int, long long, long long, long long>, int> wide;
-    std::vector<int> pair_cls(std::max<int64_t>(1, t.n_inter));
-    std::vector<int> dls, levs;
-    std::vector<long long> kvec;        // integer offset vector of every class
-    auto new_class = [&](int b, int dl, long long kx, long long ky, long long kz) {
-        const int c = (int)dls.size();
-        levs.push_back(helm || P->prm.p_min > 0 ? lev[b] : 0);
-        dls.push_back(dl);
-        kvec.push_back(kx);
-        kvec.push_back(ky);
-        kvec.push_back(kz);
-        return c;
-    };
-    for (int b = 0; b < t.nbox; b++)
-        for (int u = ip[b]; u < ip[b + 1]; u++) {
-            const int s = ii[u], dl = lev[b] - lev[s], e = std::max(0, -dl);
-            // 2 rho 2^e = (2 i_t + 1) 2^e - (2 i_s + 1) 2^(dl + e), an integer vector
-            auto K = [&](int it_, int is_) {
-                return (long long)(2 * it_ + 1) * (1ll << e) - (long long)(2 * is_ + 1) * (1ll << (dl + e));
-            };
-            const long long kx = K(ix[b], ix[s]), ky = K(iy[b], iy[s]), kz = K(iz[b], iz[s]);
-            // the target level enters the key when the derivatives (Helmholtz: k h_t) or
-            // the orders (level-dependent order) depend on it
-            const int lv = helm || P->prm.p_min > 0 ? lev[b] : 0;
-            int c;
-            if (std::llabs(kx) <= KMAX && std::llabs(ky) <= KMAX && std::llabs(kz) <= KMAX && dl > -64 && dl < 64) {
-                const unsigned long long key =
-                    1ull + (((unsigned long long)(kx + KMAX)) | ((unsigned long long)(ky + KMAX) << KB) |
-                            ((unsigned long long)(kz + KMAX) << (2 * KB)) |
-                            ((unsigned long long)(dl + 64) << (3 * KB)) | ((unsigned long long)lv << (3 * KB + 7)));
-                size_t h = slot_of(key);
-                if (tkey[h] == 0ull) {
-                    if (2 * (tused + 1) > tmask + 1) {
-                        grow();
-                        h = slot_of(key);
-                    }
-                    tkey[h] = key;
-                    tval[h] = new_class(b, dl, kx, ky, kz);
-                    tused++;
-                }
-                c = tval[h];
-            } else {
-                auto wk = std::make_tuple(dl, lv, kx, ky, kz);
-                auto it = wide.find(wk);
-                if (it == wide.end()) it = wide.emplace(wk, new_class(b, dl, kx, ky, kz)).first;
-                c = it->second;
-            }
-            pair_cls[u] = c;
-        }
+    const bool by_level = helm || P->prm.p_min > 0;   // the target level enters the key
+    // Classes are numbered in order of first appearance over the pairs in list
+    // order.  The boxes are cut into up to three ranges of about equal pair
+    // counts, numbered on threads of their own (number_classes); the ranges'
+    // classes are then numbered together in range order, which is the
+    // numbering of one pass over all pairs.
+    const int64_t npair = t.n_inter;
+    const int nth = (int)std::max<int64_t>(1, std::min<int64_t>(3, npair / 32768));
+    std::vector<int> bcut(nth + 1, t.nbox);
+    bcut[0] = 0;
+    for (int k = 1, b = 0; k < nth; k++) {
+        while (b < t.nbox && (int64_t)ip[b] * nth < npair * k) b++;
+        bcut[k] = b;
+    }
+    std::vector<int> pair_cls(std::max<int64_t>(1, npair));
+    std::vector<ClassSet> sets(nth);
+    {
+        std::vector<std::thread> th;
+        for (int k = 1; k < nth; k++)
+            th.emplace_back(number_classes, bcut[k], bcut[k + 1], by_level, lev.data(), ix.data(), iy.data(),
+                            iz.data(), ip.data(), ii.data(), pair_cls.data(), std::ref(sets[k]));
+        number_classes(bcut[0], bcut[1], by_level, lev.data(), ix.data(), iy.data(), iz.data(), ip.data(), ii.data(),
+                       pair_cls.data(), sets[0]);
+        for (auto &x : th) x.join();
+    }
+    // the first range's numbers are already global; later ranges' are mapped
+    ClassSet &all = sets[0];
+    for (int k = 1; k < nth; k++) {
+        const ClassSet &R = sets[k];
+        std::vector<int> to(R.dls.size());
+        for (size_t c = 0; c < R.dls.size(); c++)
+            to[c] = all.find_or_add(R.kvec[3 * c], R.kvec[3 * c + 1], R.kvec[3 * c + 2], R.dls[c], R.levs[c]);
+        for (int u = ip[bcut[k]]; u < ip[bcut[k + 1]]; u++) pair_cls[u] = to[pair_cls[u]];
+    }
+    const std::vector<int> &dls = all.dls, &levs = all.levs;
+    const std::vector<long long> &kvec = all.kvec;
     P->m2l_src_lmin = P->m2l_tgt_lmin = t.nlev;
     for (int b = 0; b < t.nbox; b++)
         if (ip[b + 1] > ip[b]) P->m2l_tgt_lmin = std::min(P->m2l_tgt_lmin, lev[b]);
