@@ -316,7 +316,8 @@ int bem_plan_export_tree(const bem_plan *plan, bem_tree_view *view);
  * singular and near-singular pairs) as host COO triplets.  counts[0] = nnz of
  * the double-layer part (columns: node index), counts[1] = nnz of the
  * single-layer part (columns: chi index).  Call with NULL arrays to get the
- * counts.  Values are float64 (complex pairs for Helmholtz). */
+ * counts.  Values are returned as float64 (complex pairs for Helmholtz); a
+ * mixed-precision plan holds and returns them rounded to float32. */
 int bem_plan_export_correction(const bem_plan *plan, int64_t *counts, int64_t *rowD, int64_t *colD,
                                double *valD, int64_t *rowS, int64_t *colS, double *valS);
 

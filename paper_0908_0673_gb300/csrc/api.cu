@@ -439,7 +439,14 @@ int bem_plan_export_correction(const bem_plan *P, int64_t *counts, int64_t *rowD
     std::vector<double> vD, vS;
     BEM_TRY(fetch(ptr, K.ptrD, P->N + 1));
     BEM_TRY(fetch(cD, K.colD, K.nnzD)); BEM_TRY(fetch(cS, K.colS, K.nnzS));
-    BEM_TRY(fetch(vD, K.valD, K.nnzD * C)); BEM_TRY(fetch(vS, K.valS, K.nnzS * C));
+    if (K.valD) {
+        BEM_TRY(fetch(vD, K.valD, K.nnzD * C)); BEM_TRY(fetch(vS, K.valS, K.nnzS * C));
+    } else {                                           // mixed plans hold float32 values
+        std::vector<float> fD, fS;
+        BEM_TRY(fetch(fD, K.fvalD, K.nnzD * C)); BEM_TRY(fetch(fS, K.fvalS, K.nnzS * C));
+        vD.assign(fD.begin(), fD.end());
+        vS.assign(fS.begin(), fS.end());
+    }
     for (int64_t i = 0; i < P->N; i++)
         for (int q = ptr[i]; q < ptr[i + 1]; q++) {
             if (rowD) { rowD[q] = i; colD[q] = cD[q]; for (int c = 0; c < C; c++) valD[q * C + c] = vD[q * C + c]; }

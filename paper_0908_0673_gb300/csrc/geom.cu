@@ -241,7 +241,23 @@ struct CorrArgs {
     const float *frho;                    // per box float32 search radius, rounded up
     const double *bcx, *bcy, *bcz, *brho; // per box centre and search radius
     const int *child0, *nchild, *eb, *ee;
+    const float *nh, *nl;                 // node coordinates as float32 pairs: x = nh + nl
 };
+
+// float32 offset X_v - x_n of two nodes from their float pairs: the high
+// parts' difference (exact for nearby coordinates) plus the low parts'
+__device__ __forceinline__ float node_diff(const CorrArgs &a, int v, int n, int c) {
+    return (a.nh[3 * (size_t)v + c] - a.nh[3 * (size_t)n + c]) + (a.nl[3 * (size_t)v + c] - a.nl[3 * (size_t)n + c]);
+}
+
+__global__ void k_nodes_split(int64_t n3, const double *__restrict__ x, float *hi, float *lo) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n3) {
+        const float h = (float)x[i];
+        hi[i] = h;
+        lo[i] = (float)(x[i] - (double)h);
+    }
+}
 
 // Per box: radius of a ball around the centre that holds every point a
 // special pair can involve: max over the subtree's elements of
@@ -677,8 +693,8 @@ __device__ __forceinline__ void load_pair(const CorrArgs &a, int node, int e, in
 // index), lane l holds value l of every block.  Value l + W b goes to S at
 // l + W b < NPE C, to D below 2 NPE C, to the D0 row sum at 2 NPE C.
 template <class R, bool HELM, int NPE, int W>
-__device__ __forceinline__ void reduce_store(R (&v)[sp_nvp(HELM, NPE)], unsigned wmask, int sl, int pr, double *valD,
-                                             double *valS, double *d0pair) {
+__device__ __forceinline__ void reduce_store(R (&v)[sp_nvp(HELM, NPE)], unsigned wmask, int sl, int pr, R *valD,
+                                             R *valS, double *d0pair) {
     constexpr int C = HELM ? 2 : 1, NVP = sp_nvp(HELM, NPE);
     if constexpr (W > NVP) {
         // fewer values than lanes: plain sums across the lanes beyond NVP first
@@ -701,8 +717,8 @@ __device__ __forceinline__ void reduce_store(R (&v)[sp_nvp(HELM, NPE)], unsigned
         }
         const int vi = b0 + (sl % BW);
         if (sl < BW) {
-            if (vi < NPE * C) valS[(size_t)pr * NPE * C + vi] = (double)v[b0];
-            else if (vi < 2 * NPE * C) valD[(size_t)pr * NPE * C + vi - NPE * C] = (double)v[b0];
+            if (vi < NPE * C) valS[(size_t)pr * NPE * C + vi] = (R)v[b0];
+            else if (vi < 2 * NPE * C) valD[(size_t)pr * NPE * C + vi - NPE * C] = (R)v[b0];
             else if (vi == 2 * NPE * C) d0pair[pr] = (double)v[b0];
         }
     }
@@ -714,8 +730,8 @@ __device__ __forceinline__ void reduce_store(R (&v)[sp_nvp(HELM, NPE)], unsigned
 template <class R, bool HELM, int NPE>
 __global__ void __launch_bounds__(32 * SP_WARPS) k_special_self(CorrArgs a, int nlist, const int *__restrict__ list,
                                                                const int *__restrict__ pair_node,
-                                                               const int *__restrict__ pair_e, double *valD,
-                                                               double *valS, double *d0pair) {
+                                                               const int *__restrict__ pair_e, R *valD,
+                                                               R *valS, double *d0pair) {
     constexpr int NVP = sp_nvp(HELM, NPE);
     constexpr unsigned FULL = 0xffffffffu;
     __shared__ double sX[SP_WARPS][18];
@@ -786,8 +802,8 @@ template <class R, bool HELM, int NPE>
 __global__ void __launch_bounds__(32 * SPN_WARPS) k_special_near(CorrArgs a, const int *__restrict__ nlist_dev,
                                                                 const int *__restrict__ list,
                                                                 const int *__restrict__ pair_node,
-                                                                const int *__restrict__ pair_e, double *valD,
-                                                                double *valS, double *d0pair) {
+                                                                const int *__restrict__ pair_e, R *valD,
+                                                                R *valS, double *d0pair) {
     constexpr int NVP = sp_nvp(HELM, NPE), W = SPN_W, QCAP = SPN_QCAP, RING = SPN_RING;
     __shared__ QPiece qbuf[SPN_G][2][QCAP];
     __shared__ R ring[SPN_G][3][RING];
@@ -970,12 +986,28 @@ __device__ __forceinline__ void mid_imgs(const float *df, const PieceF &P, float
     mca = map_f<NPE>(df, 0.5f * (P.c0 + P.a0), 0.5f * (P.c1 + P.a1));
 }
 
+// the float64 test for a piece the float32 estimate leaves open, with the
+// element's nodes loaded for it
 template <int NPE>
-__device__ __forceinline__ bool split_coded(const float *df, unsigned code, const PieceImg &I, const double *X,
-                                            const double xi[3], float tau2, double tau, int maxdepth) {
-    QPiece Q;
-    Q.A = I.A; Q.B = I.B; Q.Cc = I.Cc;
-    return split_test<NPE>(df, Q, code_piece(code), X, xi, tau2, tau, maxdepth);
+__device__ __noinline__ bool split_exact(const CorrArgs &a, int e, int node, const PieceF &P) {
+    double xi[3], X[3 * NPE];
+    for (int c = 0; c < 3; c++) xi[c] = a.nodes[3 * (size_t)node + c];
+    for (int i = 0; i < 3 * NPE; i++) X[i] = a.nodes[3 * (size_t)a.el_phi[(size_t)e * NPE + i / 3] + i % 3];
+    return must_split<NPE>(X, xi, a.tau, a.maxdepth, P);
+}
+
+// split_test on a coded piece, the element's float64 nodes read only when
+// the estimate is too close to call
+template <int NPE>
+__device__ __forceinline__ bool split_coded(const float *df, unsigned code, const PieceImg &I, const CorrArgs &a, int e,
+                                            int node, float tau2, int maxdepth) {
+    const PieceF P = code_piece(code);
+    if (P.depth >= maxdepth) return false;
+    const float4 m = map_f<NPE>(df, (P.a0 + P.b0 + P.c0) * (1.f / 3.f), (P.a1 + P.b1 + P.c1) * (1.f / 3.f));
+    const float h2 = fmaxf(dist2f(I.A, I.B), fmaxf(dist2f(I.B, I.Cc), dist2f(I.Cc, I.A)));
+    const float th = tau2 * h2, q = m.x * m.x + m.y * m.y + m.z * m.z - th;
+    if (fabsf(q) > 2e-4f * th) return q < 0.f;
+    return split_exact<NPE>(a, e, node, P);
 }
 
 // Near-singular pairs, the light ones in two steps.  Most pairs refine at
@@ -1011,17 +1043,9 @@ __global__ void __launch_bounds__(NW_T) k_near_walk(CorrArgs a, int nlist, const
     if (nlist_dev) nlist = min(nlist, *nlist_dev);
     if (li >= nlist) return;
     const int pr = list[li], node = pair_node[pr], e = pair_e[pr];
-    double xi[3], X[3 * NPE];
     float df[3 * NPE];
-    xi[0] = a.nodes[3 * (size_t)node];
-    xi[1] = a.nodes[3 * (size_t)node + 1];
-    xi[2] = a.nodes[3 * (size_t)node + 2];
 #pragma unroll
-    for (int i = 0; i < 3 * NPE; i++) {
-        const int c = i % 3, vid = a.el_phi[(size_t)e * NPE + i / 3];
-        X[i] = a.nodes[3 * (size_t)vid + c];
-        df[i] = (float)(X[i] - xi[c]);
-    }
+    for (int i = 0; i < 3 * NPE; i++) df[i] = node_diff(a, a.el_phi[(size_t)e * NPE + i / 3], node, i % 3);
     const float tau2 = (float)(a.tau * a.tau);
     const int maxdepth = a.maxdepth;
     unsigned *out = leaves + (size_t)li * SLOTS;
@@ -1047,7 +1071,7 @@ __global__ void __launch_bounds__(NW_T) k_near_walk(CorrArgs a, int nlist, const
             if (deep) break;
             const unsigned k1 = child_of(root, c1);
             const PieceImg i1 = child_img(rimg, m01, m12, m20, c1);
-            if (!split_coded<NPE>(df, k1, i1, X, xi, tau2, a.tau, maxdepth)) {
+            if (!split_coded<NPE>(df, k1, i1, a, e, node, tau2, maxdepth)) {
                 out[n++] = k1;
                 continue;
             }
@@ -1056,7 +1080,7 @@ __global__ void __launch_bounds__(NW_T) k_near_walk(CorrArgs a, int nlist, const
             for (int c2 = 0; c2 < 4 && !deep; c2++) {
                 const unsigned k2 = child_of(k1, c2);
                 const PieceImg i2 = child_img(i1, mab, mbc, mca, c2);
-                if (!split_coded<NPE>(df, k2, i2, X, xi, tau2, a.tau, maxdepth)) {
+                if (!split_coded<NPE>(df, k2, i2, a, e, node, tau2, maxdepth)) {
                     out[n++] = k2;
                     continue;
                 }
@@ -1069,7 +1093,7 @@ __global__ void __launch_bounds__(NW_T) k_near_walk(CorrArgs a, int nlist, const
                 for (int c3 = 0; c3 < 4 && !deep; c3++) {
                     const unsigned k3 = child_of(k2, c3);
                     const PieceImg i3 = child_img(i2, nab, nbc, nca, c3);
-                    if (split_coded<NPE>(df, k3, i3, X, xi, tau2, a.tau, maxdepth)) deep = true;
+                    if (split_coded<NPE>(df, k3, i3, a, e, node, tau2, maxdepth)) deep = true;
                     else out[n++] = k3;
                 }
             }
@@ -1107,8 +1131,8 @@ __global__ void __launch_bounds__(32 * NE_WARPS) k_near_eval(CorrArgs a, int nli
                                                              int slots, const int *__restrict__ list,
                                                              const int *__restrict__ pair_node,
                                                              const int *__restrict__ pair_e, const int *__restrict__ cnt,
-                                                             const unsigned *__restrict__ leaves, double *valD,
-                                                             double *valS, double *d0pair) {
+                                                             const unsigned *__restrict__ leaves, R *valD,
+                                                             R *valS, double *d0pair) {
     constexpr int NVP = sp_nvp(HELM, NPE), G = NE_WARPS * 32 / W;
     static_assert(NE_CHUNK % G == 0 && NE_CHUNK <= 32 * NE_WARPS, "chunk");
     __shared__ R sd[G][3 * NPE];
@@ -1144,7 +1168,8 @@ __global__ void __launch_bounds__(32 * NE_WARPS) k_near_eval(CorrArgs a, int nli
             __syncwarp(wmask);                           // the previous pair's reads of the table are done
             for (int i = sl; i < 3 * NPE; i += W) {
                 const int c = i % 3, vid = a.el_phi[(size_t)e * NPE + i / 3];
-                sd[g][i] = (R)(a.nodes[3 * (size_t)vid + c] - a.nodes[3 * (size_t)node + c]);
+                if (sizeof(R) == sizeof(float)) sd[g][i] = (R)node_diff(a, vid, node, c);
+                else sd[g][i] = (R)(a.nodes[3 * (size_t)vid + c] - a.nodes[3 * (size_t)node + c]);
             }
             __syncwarp(wmask);
             R v[NVP];
@@ -1229,10 +1254,10 @@ __global__ void k_d0_rowsum(int N, const int *__restrict__ off, const double *__
     d0row[i] = s;
 }
 
-__global__ void k_to_float(int64_t n, const double *__restrict__ a, float *b) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) b[i] = (float)a[i];
-}
+// the correction's value array in the quadrature's working precision
+template <class R> static R *corr_out(float *f, double *d);
+template <> float *corr_out<float>(float *f, double *) { return f; }
+template <> double *corr_out<double>(float *, double *d) { return d; }
 
 int build_correction(bem_plan *P, cudaStream_t s) {
     Tree &t = P->t;
@@ -1247,9 +1272,13 @@ int build_correction(bem_plan *P, cudaStream_t s) {
     BEM_TRY(A.alloc(&rho, t.nbox));
     (k_elem_centroid<<<(E + 255) / 256, 256, 0, s>>>(E, npe, P->prm.tau_near, t.el_phi, P->nodes, ecx, ecy, ecz, eh, ebnd),
      ::bem::count_launch());
+    float *nh, *nl;
+    BEM_TRY(A.alloc(&nh, 3 * (size_t)N));
+    BEM_TRY(A.alloc(&nl, 3 * (size_t)N));
+    (k_nodes_split<<<(3 * N + 255) / 256, 256, 0, s>>>(3 * (int64_t)N, P->nodes, nh, nl), ::bem::count_launch());
     CorrArgs a{N, E, npe, P->green, P->prm.n_duffy, P->prm.max_subdiv, P->k, P->prm.tau_near, P->nodes,
                t.el_phi, t.el_chi, ecx, ecy, ecz, eh, ebnd, t.fbox, frho, t.cx, t.cy, t.cz, rho, t.child0, t.nchild,
-               t.eb, t.ee};
+               t.eb, t.ee, nh, nl};
     BEM_CUDA(cudaMemsetAsync(rho, 0, sizeof(double) * t.nbox, s));
     (k_elem_search_radius<<<(E + 255) / 256, 256, 0, s>>>(a, t.leaf_of_node, t.parent, (unsigned long long *)rho),
      ::bem::count_launch());
@@ -1288,16 +1317,23 @@ int build_correction(bem_plan *P, cudaStream_t s) {
     BEM_TRY(A.alloc(&K.ptrD, N + 1));
     BEM_TRY(A.alloc(&K.colD, K.nnzD));
     BEM_TRY(A.alloc(&K.colS, K.nnzS));
-    BEM_TRY(A.alloc(&K.valD, K.nnzD * C));
-    BEM_TRY(A.alloc(&K.valS, K.nnzS * C));
+    // the values in the plan's working precision: float32 for mixed plans
+    // (what their products read), float64 otherwise
+    const bool fcorr = P->prm.precision == BEM_MIXED;
+    if (!fcorr) {
+        BEM_TRY(A.alloc(&K.valD, K.nnzD * C));
+        BEM_TRY(A.alloc(&K.valS, K.nnzS * C));
+    }
     K.ptrS = K.ptrD;
     double *d0pair, *d0row;
     BEM_TRY(A.alloc(&d0pair, npairs));
     BEM_TRY(A.alloc(&d0row, N));
     // every allocation comes before the long kernels, so that work other
     // streams enqueue next can overlap them
-    BEM_TRY(A.alloc(&K.fvalD, K.nnzD * C));
-    BEM_TRY(A.alloc(&K.fvalS, K.nnzS * C));
+    if (fcorr) {
+        BEM_TRY(A.alloc(&K.fvalD, K.nnzD * C));
+        BEM_TRY(A.alloc(&K.fvalS, K.nnzS * C));
+    }
     (k_rows_ptr<<<(N + 256) / 256, 256, 0, s>>>(N, npe, off, K.ptrD), ::bem::count_launch());
     (k_corr_csr<<<(npairs + 255) / 256, 256, 0, s>>>(npairs, npe, pair_e, t.el_phi, t.el_chi, K.colD, K.colS), ::bem::count_launch());
     // self pairs first, then the near-singular ones (stable), so that each kernel
@@ -1373,20 +1409,20 @@ int build_correction(bem_plan *P, cudaStream_t s) {
     do {                                                                                                          \
         if (nnear > 0) {                                                                                          \
             (k_near_eval<R, H, NP, NE_W><<<ge, 32 * NE_WARPS, 0, s>>>(a, nnear, nullptr, nw_slots(2), klist + nself,\
-                                                                       pair_node, pair_e, lcnt, leaves, K.valD,   \
-                                                                       K.valS, d0pair),                           \
+                                                                       pair_node, pair_e, lcnt, leaves, corr_out<R>(K.fvalD, K.valD),\
+                                                                       corr_out<R>(K.fvalS, K.valS), d0pair),                           \
              ::bem::count_launch());                                                                              \
             (k_near_eval<R, H, NP, NE_W><<<ge2, 32 * NE_WARPS, 0, s>>>(a, dcap, ndeep, nw_slots(3), deep_list,     \
-                                                                        pair_node, pair_e, cnt2, leaves2, K.valD, \
-                                                                        K.valS, d0pair),                          \
+                                                                        pair_node, pair_e, cnt2, leaves2, corr_out<R>(K.fvalD, K.valD),\
+                                                                        corr_out<R>(K.fvalS, K.valS), d0pair),                          \
              ::bem::count_launch());                                                                              \
             (k_special_near<R, H, NP><<<gn, 32 * SPN_WARPS, 0, s>>>(a, ndeeper, deeper, pair_node, pair_e,         \
-                                                                    K.valD, K.valS, d0pair),                      \
+                                                                    corr_out<R>(K.fvalD, K.valD), corr_out<R>(K.fvalS, K.valS), d0pair), \
              ::bem::count_launch());                                                                              \
         }                                                                                                         \
         if (nself > 0)                                                                                            \
-            (k_special_self<R, H, NP><<<gs, 32 * SP_WARPS, 0, s>>>(a, nself, klist, pair_node, pair_e, K.valD,    \
-                                                                   K.valS, d0pair),                               \
+            (k_special_self<R, H, NP><<<gs, 32 * SP_WARPS, 0, s>>>(a, nself, klist, pair_node, pair_e,           \
+                                                                   corr_out<R>(K.fvalD, K.valD), corr_out<R>(K.fvalS, K.valS), d0pair),                               \
              ::bem::count_launch());                                                                              \
     } while (0)
         if (npairs > 0) {
@@ -1402,15 +1438,12 @@ int build_correction(bem_plan *P, cudaStream_t s) {
     }
     (k_d0_rowsum<<<(N + 255) / 256, 256, 0, s>>>(N, off, d0pair, d0row), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
-    int64_t nv = K.nnzD * C;
-    (k_to_float<<<(int)((nv + 255) / 256), 256, 0, s>>>(nv, K.valD, K.fvalD), ::bem::count_launch());
-    (k_to_float<<<(int)((nv + 255) / 256), 256, 0, s>>>(nv, K.valS, K.fvalS), ::bem::count_launch());
     BEM_LAUNCH_CHECK();
     // the diagonal starts as 1 + (correction row sum of D0); the regular part
     // is added by one Laplace double-layer product on phi = 1
     P->C = d0row;
     // the temporaries are released once the stream has finished with them
-    for (void *q : {(void *)ptmp, (void *)lcnt, (void *)dflag, (void *)dpos, (void *)dblk, (void *)deep_list, (void *)ndeep, (void *)cnt2, (void *)deeper, (void *)ndeeper, (void *)leaves, (void *)leaves2, (void *)kind, (void *)koff, (void *)klist, (void *)ktot, (void *)kblk, (void *)cnt, (void *)tot, (void *)sblk, (void *)pair_node, (void *)d0pair, (void *)ecx, (void *)ecy, (void *)ecz,
+    for (void *q : {(void *)ptmp, (void *)nh, (void *)nl, (void *)lcnt, (void *)dflag, (void *)dpos, (void *)dblk, (void *)deep_list, (void *)ndeep, (void *)cnt2, (void *)deeper, (void *)ndeeper, (void *)leaves, (void *)leaves2, (void *)kind, (void *)koff, (void *)klist, (void *)ktot, (void *)kblk, (void *)cnt, (void *)tot, (void *)sblk, (void *)pair_node, (void *)d0pair, (void *)ecx, (void *)ecy, (void *)ecz,
                     (void *)eh, (void *)ebnd, (void *)frho, (void *)rho, (void *)off, (void *)pair_e})
         P->deferred.push_back(q);
     return BEM_OK;
