@@ -91,18 +91,24 @@ constexpr int p2m_slots(int np) { return np <= 3 * P2M_T ? 3 : np <= 8 * P2M_T ?
 
 // WEIGHTS: instead of the moments, write each point's row of P2M weights
 // W[o][a] (the value that multiplies f[o] in moment a) for the stored form.
+//
+// Per batch of points, shared memory holds for every point and axis the pairs
+// (d^e, e n d^(e-1) / h) (d = offset / h, n the normal's component), so a
+// monopole coefficient is Px Py Pz and a double-layer one, the normal
+// derivative of the monomial, (Qx Py + Px Qy) Pz + Px Py Qz: three paired
+// loads and no branches per (point, coefficient).
 template <class R, int C, bool DL, bool WEIGHTS, int NS>
 __global__ void __launch_bounds__(P2M_T) k_p2m(int nleaf, Tabs tb, TreeView tv, QuadView qv, const R *__restrict__ f,
                                                R *__restrict__ M, const int *__restrict__ skip, R *__restrict__ W = nullptr) {
+    using R2 = typename std::conditional<sizeof(R) == sizeof(float), float2, double2>::type;
     if (skip && *skip) return;
     const int li = blockIdx.x;
     if (li >= nleaf) return;
     const int b = tv.leaves[li];
     const int np = tb.np, tid = threadIdx.x;
     const int p = order_of(tb, tv.level[b]), npl = np_of(p);   // this leaf's order; np is the stride
-    __shared__ R pw[3][P2M_B][PMAX + 1];             // [axis][point][power]: lanes with distinct powers hit distinct banks
+    __shared__ R2 pq[3][P2M_B][PMAX + 1];            // [axis][point][power]: (d^e, e n d^(e-1) / h)
     __shared__ R sf[P2M_B][C];
-    __shared__ R sn[3][P2M_B];
     const double h = scalbn(tv.side, -tv.level[b]);
     const R hinv = (R)(1.0 / h);
     const double c0 = tv.cx[b], c1 = tv.cy[b], c2 = tv.cz[b];
@@ -123,57 +129,46 @@ __global__ void __launch_bounds__(P2M_T) k_p2m(int nleaf, Tabs tb, TreeView tv, 
         __syncthreads();
         if (tid < 3 * P2M_B) {
             int pt = tid % P2M_B, ax = tid / P2M_B;
-            R d = (R)0;
+            R d = (R)0, nd = (R)0;
             if (pt < nb) {
                 int o = base + pt;
                 if constexpr (sizeof(R) == sizeof(double)) {
                     double xx = ax == 0 ? qv.x[o] - c0 : (ax == 1 ? qv.y[o] - c1 : qv.z[o] - c2);
                     d = (R)(xx / h);
+                    if (DL) nd = (R)(ax == 0 ? qv.nx[o] : (ax == 1 ? qv.ny[o] : qv.nz[o]));
                 } else {
                     // float path: offsets from the owning leaf (this box) centre
                     R xx = ax == 0 ? (R)qv.fx[o] : (ax == 1 ? (R)qv.fy[o] : (R)qv.fz[o]);
                     d = xx * hinv;
+                    if (DL) nd = (R)(ax == 0 ? qv.fnx[o] : (ax == 1 ? qv.fny[o] : qv.fnz[o]));
                 }
             }
-            R v = (R)1;
+            nd *= hinv;
+            R v = (R)1, vm = (R)0;                    // d^e, d^(e-1)
             for (int e = 0; e <= p; e++) {
-                pw[ax][pt][e] = v;
+                R2 t;
+                t.x = v;
+                t.y = DL ? (R)e * nd * vm : (R)0;
+                pq[ax][pt][e] = t;
+                vm = v;
                 v *= d;
             }
-        } else if (tid < 3 * P2M_B + P2M_B) {
+        } else if (!WEIGHTS && tid < 3 * P2M_B + P2M_B) {
             int pt = tid - 3 * P2M_B;
             int o = base + pt;
-            if (!WEIGHTS)
 #pragma unroll
-                for (int c = 0; c < C; c++) sf[pt][c] = pt < nb ? f[(size_t)o * C + c] : (R)0;
-            if (DL) {
-                if constexpr (sizeof(R) == sizeof(double)) {
-                    sn[0][pt] = pt < nb ? (R)qv.nx[o] : (R)0;
-                    sn[1][pt] = pt < nb ? (R)qv.ny[o] : (R)0;
-                    sn[2][pt] = pt < nb ? (R)qv.nz[o] : (R)0;
-                } else {
-                    sn[0][pt] = pt < nb ? (R)qv.fnx[o] : (R)0;
-                    sn[1][pt] = pt < nb ? (R)qv.fny[o] : (R)0;
-                    sn[2][pt] = pt < nb ? (R)qv.fnz[o] : (R)0;
-                }
-            }
+            for (int c = 0; c < C; c++) sf[pt][c] = pt < nb ? f[(size_t)o * C + c] : (R)0;
         }
         __syncthreads();
         for (int pt = 0; pt < nb; pt++) {
 #pragma unroll
             for (int s = 0; s < NS; s++) {
                 if (tid + s * P2M_T >= npl) break;
-                const int m = am[s], n = an[s], k = ak[s];
+                const R2 X = pq[0][pt][am[s]], Y = pq[1][pt][an[s]], Z = pq[2][pt][ak[s]];
+                const R xy = X.x * Y.x;
                 R val;
-                if (!DL) {
-                    val = pw[0][pt][m] * pw[1][pt][n] * pw[2][pt][k];
-                } else {
-                    val = (R)0;
-                    if (m) val += (R)m * sn[0][pt] * pw[0][pt][m - 1] * pw[1][pt][n] * pw[2][pt][k];
-                    if (n) val += (R)n * sn[1][pt] * pw[0][pt][m] * pw[1][pt][n - 1] * pw[2][pt][k];
-                    if (k) val += (R)k * sn[2][pt] * pw[0][pt][m] * pw[1][pt][n] * pw[2][pt][k - 1];
-                    val *= hinv;
-                }
+                if (!DL) val = xy * Z.x;
+                else val = xy * Z.y + (X.y * Y.x + X.x * Y.y) * Z.x;
                 if (WEIGHTS) {
                     W[(size_t)(base + pt) * np + tid + s * P2M_T] = val;
                 } else {

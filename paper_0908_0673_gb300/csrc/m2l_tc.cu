@@ -110,8 +110,12 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 // 32 w .. 32 w + 31, i.e. pairs); warp 4 lane 0 loads the class image and
 // issues the MMAs; warps 5-15 gather the moments into the chunk ring.
 // Handshakes: full[s] (11 producer warps) -> MMA; empty[s] (MMA commit) ->
-// producers; tfull (commit after a tile's last chunk) -> epilogue; tempty
+// producers; tfull (commit after a tile's last chunk) -> epilogue; tovl
 // (4 epilogue warps) -> MMA; bfull (bulk copy of a class image) -> MMA.
+// Two accumulators: even tiles use TMEM columns [0, ldp), odd tiles
+// [512 - ldp, 512).  Where the two share columns (ldp > 256), the epilogue
+// reads the shared ones first and then arrives on tovl, so the MMAs of the
+// next tile run while it reads the rest of the previous one.
 __global__ void __launch_bounds__(TC_T, 1) k_m2l_tc(const __grid_constant__ TcArgs a) {
     if (a.skip && *a.skip) return;
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -123,10 +127,13 @@ __global__ void __launch_bounds__(TC_T, 1) k_m2l_tc(const __grid_constant__ TcAr
     unsigned *sSgn = (unsigned *)(smem + LY.sgn);                       // [48][ldp / 32]
     float *sX = (float *)(smem + LY.xpose);                             // [TC_EPI][32][33]
     uint64_t *full = (uint64_t *)(smem + LY.bars), *empty = full + TC_NS, *tfull = full + 2 * TC_NS,
-             *tempty = tfull + 1, *bfull = tfull + 2, *fin = tfull + 3, *imgfree = tfull + 4;
+             *tovl = tfull + 1, *bfull = tfull + 2, *fin = tfull + 3, *imgfree = tfull + 4;
     uint32_t *sTmem = (uint32_t *)(imgfree + 1);
     volatile int *sAbort = (volatile int *)(sTmem + 1);
     const int nw = ldp / 32;
+    const int colB = 512 - ldp;                         // first column of the second accumulator
+    const int gs = colB < ldp ? colB / 32 : 0;          // first group of the first one that the second shares
+    const int novl = colB < ldp ? nw - gs : 0;          // groups the two accumulators share
 
     if (tid == 0) {
         for (int s = 0; s < TC_NS; s++) {
@@ -134,7 +141,7 @@ __global__ void __launch_bounds__(TC_T, 1) k_m2l_tc(const __grid_constant__ TcAr
             tc::mbar_init(&empty[s], 1);
         }
         tc::mbar_init(tfull, 1);
-        tc::mbar_init(tempty, TC_EPI);
+        tc::mbar_init(tovl, TC_EPI);
         tc::mbar_init(bfull, 1);
         tc::mbar_init(fin, 1);
         tc::mbar_init(imgfree, 1);
@@ -171,20 +178,36 @@ __global__ void __launch_bounds__(TC_T, 1) k_m2l_tc(const __grid_constant__ TcAr
             float *xb = sX + warp * TC_XPOSE;
             const int ur = u >= 0 ? u - a.u0 : -1;
             const int rq = lane >> 3, cg = lane & 7;
-            const uint32_t base = tmem + ((uint32_t)(32 * warp) << 16);
-            for (int c = 0; c < ldp; c += 64) {
+            // odd tiles use the second accumulator; the first accumulator's
+            // shared groups go first, so that the next tile can start
+            const bool second = (k & 1) != 0;
+            const int start = second ? 0 : gs;
+            const uint32_t base = tmem + ((uint32_t)(32 * warp) << 16) + (second ? (uint32_t)colB : 0u);
+            bool sig = false;
+            auto release = [&]() {
+                tc::tc_fence_before_sync();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(tovl);
+                sig = true;
+            };
+            if (novl == 0) release();
+            for (int q = 0; q < nw; q += 2) {
+                const int g0 = (start + q) % nw, g1 = (start + q + 1) % nw;
+                const bool two = q + 1 < nw;
                 uint32_t v0[32], v1[32];
-                tc::tmem_ld32_nowait(base + (uint32_t)c, v0);
-                if (c + 32 < ldp) tc::tmem_ld32_nowait(base + (uint32_t)(c + 32), v1);
+                tc::tmem_ld32_nowait(base + (uint32_t)(32 * g0), v0);
+                if (two) tc::tmem_ld32_nowait(base + (uint32_t)(32 * g1), v1);
                 tc::tmem_wait_ld2(v0, v1);
-                for (int h = 0; h < 2 && c + 32 * h < ldp; h++) {
+                if (!sig && q + 2 >= novl) release();
+                for (int h = 0; h < 2 && (h == 0 || two); h++) {
+                    const int col = 32 * (h ? g1 : g0);
                     __syncwarp();
 #pragma unroll
-                    for (int k = 0; k < 8; k++) {
+                    for (int k4 = 0; k4 < 8; k4++) {
                         const uint32_t *v = h ? v1 : v0;
-                        *(float4 *)(xb + lane * TC_XLD + 4 * k) = make_float4(
-                            __uint_as_float(v[4 * k]), __uint_as_float(v[4 * k + 1]), __uint_as_float(v[4 * k + 2]),
-                            __uint_as_float(v[4 * k + 3]));
+                        *(float4 *)(xb + lane * TC_XLD + 4 * k4) = make_float4(
+                            __uint_as_float(v[4 * k4]), __uint_as_float(v[4 * k4 + 1]),
+                            __uint_as_float(v[4 * k4 + 2]), __uint_as_float(v[4 * k4 + 3]));
                     }
                     __syncwarp();
 #pragma unroll
@@ -192,13 +215,11 @@ __global__ void __launch_bounds__(TC_T, 1) k_m2l_tc(const __grid_constant__ TcAr
                         const int row = 4 * i + rq;
                         const int uq = __shfl_sync(0xffffffffu, ur, row);
                         const float4 x = *(const float4 *)(xb + row * TC_XLD + 4 * cg);
-                        if (uq >= 0) tc::st_v4_hint(a.Lp + (size_t)uq * ldp + c + 32 * h + 4 * cg, x.x, x.y, x.z, x.w, pol);
+                        if (uq >= 0) tc::st_v4_hint(a.Lp + (size_t)uq * ldp + col + 4 * cg, x.x, x.y, x.z, x.w, pol);
                     }
                 }
             }
-            tc::tc_fence_before_sync();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(tempty);
+            if (!sig) release();
             if (__any_sync(0xffffffffu, *sAbort != 0)) break;
         }
     } else if (warp == TC_MMA_WARP) {
@@ -226,15 +247,17 @@ __global__ void __launch_bounds__(TC_T, 1) k_m2l_tc(const __grid_constant__ TcAr
             };
             for (int tile = t_begin; tile < t_end && ok; tile++) {
                 const int k = tile - t_begin, cls = a.tile_cls[tile];
-                // the accumulator and the image are free once the epilogue has
-                // read the previous tile (all of its MMAs have completed)
-                if (k > 0) ok = wait_or_abort(tempty, (uint32_t)((k - 1) & 1), sAbort);
+                // this tile's accumulator is free once the epilogue has read the
+                // columns it shares with the previous tile's (which it does after
+                // every MMA of that tile has completed, so the image is free too)
+                if (k > 0) ok = wait_or_abort(tovl, (uint32_t)((k - 1) & 1), sAbort);
                 if (!ok) break;
                 if (cls != cur_cls || cur_part != 0) {
                     ok = load_part(cls, 0);
                     if (!ok) break;
                 }
                 tc::tc_fence_after_sync();
+                const uint32_t dacc = tmem + ((k & 1) ? (uint32_t)colB : 0u);
                 for (int kc = 0; kc < a.nkc && ok; kc++, it++) {
                     const int s = it % TC_NS;
                     ok = wait_or_abort(&full[s], (uint32_t)((it / TC_NS) & 1), sAbort);
@@ -264,7 +287,7 @@ __global__ void __launch_bounds__(TC_T, 1) k_m2l_tc(const __grid_constant__ TcAr
                             const int nn = min(256, n - part);
                             const uint32_t po = boff + (uint32_t)(part / 8) * 256u;
                             const uint64_t bh = tc::smem_desc(ih + po, 128, 256), bl = tc::smem_desc(il + po, 128, 256);
-                            const uint32_t id = tc::idesc_tf32(TC_M, nn), d = tmem + (uint32_t)part;
+                            const uint32_t id = tc::idesc_tf32(TC_M, nn), d = dacc + (uint32_t)part;
                             const uint64_t ao = (uint64_t)ks * 16u;   // 256 B per K-step
                             tc::mma_tf32(d, ah0 + ao, bh, id, j > 0);
                             tc::mma_tf32(d, ah0 + ao, bl, id, true);
@@ -790,6 +813,9 @@ int build_sym_tables(bem_plan *P, cudaStream_t s) {
             for (int h = 0; h < np; h++) fq[(size_t)q * np + h] = fwd[(size_t)(q * 8) * np + h] & 0x7fff;
         BEM_TRY(up(&P->sy_fwdq, fq));
         const int nw = ldp / 32;
+    const int colB = 512 - ldp;                         // first column of the second accumulator
+    const int gs = colB < ldp ? colB / 32 : 0;          // first group of the first one that the second shares
+    const int novl = colB < ldp ? nw - gs : 0;          // groups the two accumulators share
         std::vector<unsigned> sg(48 * (size_t)nw, 0u);
         for (int sig = 0; sig < 48; sig++)
             for (int h = 0; h < np; h++)

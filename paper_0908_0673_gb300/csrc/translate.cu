@@ -52,35 +52,52 @@ __device__ __forceinline__ void cmac(R *acc, R cf, const R *v) {
 // ---------------------------------------------------------------------------
 constexpr int MM_T = 512;
 
-// idx3 is laid out for order pt1 - 1 (the plan's largest); the shared copy
-// for order p (<= pt1 - 1) uses stride p + 1
+// Shift tables in shared memory, built from the multi-indices alone: the np
+// coefficients' (m, n, k) packed as m | n << 8 | k << 16, the index of every
+// multi-index of degree <= p (the only ones a pass looks up) at
+// (m (p + 1) + n) (p + 1) + k, and the per-axis factors from exact integer
+// binomials.  One round of global loads (tm, tn, tk) per block.
+__device__ __forceinline__ int binom_int(int n, int k) {
+    int b = 1;                                  // C(n - k + i, i) after step i: exact
+    for (int i = 1; i <= k; i++) b = b * (n - k + i) / i;
+    return b;
+}
 template <class R>
-__device__ __forceinline__ void shift_tables(int p, int pt1, const int *__restrict__ idx3, const double *__restrict__ binom,
-                                             bool m2m, short *sIdx, R *sG) {
+__device__ __forceinline__ void shift_tables(int p, int np, const int *__restrict__ tm, const int *__restrict__ tn,
+                                             const int *__restrict__ tk, bool m2m, short *sIdx, R *sG, int *sMNK) {
     const int P1 = p + 1;
-    for (int i = threadIdx.x; i < P1 * P1 * P1; i += blockDim.x) {
-        const int m = i / (P1 * P1), n = (i / P1) % P1, k = i % P1;
-        sIdx[i] = (short)idx3[(m * pt1 + n) * pt1 + k];
+    for (int a = threadIdx.x; a < np; a += blockDim.x) {
+        const int m = tm[a], n = tn[a], k = tk[a];
+        sMNK[a] = m | n << 8 | k << 16;
+        sIdx[(m * P1 + n) * P1 + k] = (short)a;
     }
     for (int i = threadIdx.x; i < P1 * P1; i += blockDim.x) {
         const int a = i / P1, g = i - a * P1;
         // M2M: binom(a, g) 2^-g (g <= a);  L2L: binom(a + g, a) 4^-g (a + g <= p)
-        double v = 0.0;
-        if (m2m && g <= a) v = ldexp(binom[a * (PMAX + 1) + g], -g);
-        if (!m2m && a + g <= p) v = ldexp(binom[(a + g) * (PMAX + 1) + a], -2 * g);
-        sG[i] = (R)v;
+        R v = (R)0, sc = (R)1;
+        for (int j = 0; j < g; j++) sc *= m2m ? (R)0.5 : (R)0.25;
+        if (m2m && g <= a) v = (R)binom_int(a, g) * sc;
+        if (!m2m && a + g <= p) v = (R)binom_int(a + g, a) * sc;
+        sG[i] = v;
     }
+}
+
+// shared-memory bytes of the shift tables at order p (sG, sIdx, sMNK)
+template <class R>
+__host__ __device__ inline size_t shift_tab_bytes(int p, int np) {
+    const int P1 = p + 1;
+    return (((size_t)sizeof(R) * P1 * P1 + sizeof(short) * P1 * P1 * P1 + 15) / 16) * 16 + 4 * (size_t)np + 16;
 }
 
 // one axis pass over nv vectors: out[v][a] = sum_g G[a_ax][g] s_v^g in[v][a -/+ g e_ax]
 template <class R, int C, bool DOWN>
-__device__ __forceinline__ void shift_pass(int ax, int nv, int p, int np, const int *__restrict__ tm,
-                                           const int *__restrict__ tn, const int *__restrict__ tk, const short *sIdx,
+__device__ __forceinline__ void shift_pass(int ax, int nv, int p, int np, const int *sMNK, const short *sIdx,
                                            const R *sG, const int *smask, const R *in, R *out) {
     const int P1 = p + 1;
     for (int t = threadIdx.x; t < nv * np; t += blockDim.x) {
         const int v = t / np, a = t - v * np;
-        int c3[3] = {tm[a], tn[a], tk[a]};
+        const int mnk = sMNK[a];
+        int c3[3] = {mnk & 255, (mnk >> 8) & 255, mnk >> 16};
         const int e = c3[ax], rest = p - (c3[0] + c3[1] + c3[2]);
         const R sg = (smask[v] >> ax) & 1 ? (R)-1 : (R)1;
         const R *iv = in + (size_t)v * np * C;
@@ -99,15 +116,21 @@ __device__ __forceinline__ void shift_pass(int ax, int nv, int p, int np, const 
     }
 }
 
+// 2^-|a| of the coefficient with packed multi-index mnk
+template <class R>
+__device__ __forceinline__ R deg_scale(int mnk) {
+    const int d = (mnk & 255) + ((mnk >> 8) & 255) + (mnk >> 16);
+    if constexpr (sizeof(R) == sizeof(float)) return ldexpf(1.f, -d);
+    else return ldexp(1.0, -d);
+}
+
 template <class R, int C>
 __global__ void __launch_bounds__(MM_T) k_m2m_sep(int off, int cnt, const int *__restrict__ child0,
                                                   const int *__restrict__ nchild, const int *__restrict__ ix,
                                                   const int *__restrict__ iy, const int *__restrict__ iz, int p, int np,
-                                                  int nps, int pt1, int npc,
-                                                  int grp, const int *__restrict__ tm, const int *__restrict__ tn,
-                                                  const int *__restrict__ tk, const int *__restrict__ idx3,
-                                                  const double *__restrict__ binom, R *__restrict__ M,
-                                                  const int *__restrict__ skip) {
+                                                  int nps, int npc, int grp, const int *__restrict__ tm,
+                                                  const int *__restrict__ tn, const int *__restrict__ tk,
+                                                  R *__restrict__ M, const int *__restrict__ skip) {
     if (skip && *skip) return;
     extern __shared__ unsigned char smem_raw[];
     const int P1 = p + 1;
@@ -116,19 +139,39 @@ __global__ void __launch_bounds__(MM_T) k_m2m_sep(int off, int cnt, const int *_
     R *sS = sB + (size_t)grp * np * C;                       // [np][C] sum over children
     R *sG = sS + (size_t)np * C;                             // [P1][P1]
     short *sIdx = (short *)(sG + P1 * P1);                   // [P1^3]
+    int *sMNK = (int *)((unsigned char *)sG + (shift_tab_bytes<R>(p, np) - 4 * (size_t)np - 16));   // [np]
     __shared__ int smask[8];
     if (blockIdx.x >= cnt) return;
-    const int b = off + blockIdx.x, nch = nchild[b];
+    const int b = off + blockIdx.x, nch = nchild[b], c0 = child0[b], tid = threadIdx.x;
     if (nch == 0) return;
-    const int c0 = child0[b], tid = threadIdx.x;
-    shift_tables<R>(p, pt1, idx3, binom, true, sIdx, sG);
-    for (int g0 = 0; g0 < nch; g0 += grp) {
-        const int ng = min(grp, nch - g0);
-        __syncthreads();
-        // children (consecutive boxes, row stride nps) hold npc coefficients; the rest enter as zero
-        for (int t = tid; t < ng * np * C; t += MM_T) {
+    // children (consecutive boxes, row stride nps) hold npc coefficients; the
+    // rest enter as zero.  U values per thread are loaded before any is
+    // stored, so their latencies overlap (and the first ones the tables')
+    constexpr int U = 6 * C;
+    R v[U];
+    auto load = [&](int g0, int nt, int t0) {
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int t = t0 + u * MM_T;
             const int j = t / (np * C), r = t - j * np * C, a = r / C;
-            sA[t] = a < npc ? M[((size_t)(c0 + g0 + j) * nps) * C + r] : (R)0;
+            v[u] = t < nt && a < npc ? M[((size_t)(c0 + g0 + j) * nps) * C + r] : (R)0;
+        }
+    };
+    auto store = [&](int nt, int t0) {
+#pragma unroll
+        for (int u = 0; u < U; u++)
+            if (t0 + u * MM_T < nt) sA[t0 + u * MM_T] = v[u];
+    };
+    load(0, min(grp, nch) * np * C, tid);
+    shift_tables<R>(p, np, tm, tn, tk, true, sIdx, sG, sMNK);
+    for (int g0 = 0; g0 < nch; g0 += grp) {
+        const int ng = min(grp, nch - g0), nt = ng * np * C;
+        __syncthreads();
+        if (g0 > 0) load(g0, nt, tid);
+        store(nt, tid);
+        for (int t0 = tid + U * MM_T; t0 < nt; t0 += U * MM_T) {
+            load(g0, nt, t0);
+            store(nt, t0);
         }
         // a child on the low side of an axis has offset -1/4 of the parent edge
         if (tid < ng) {
@@ -136,11 +179,11 @@ __global__ void __launch_bounds__(MM_T) k_m2m_sep(int off, int cnt, const int *_
             smask[tid] = ((ix[c] & 1) ? 0 : 1) | ((iy[c] & 1) ? 0 : 2) | ((iz[c] & 1) ? 0 : 4);
         }
         __syncthreads();
-        shift_pass<R, C, true>(0, ng, p, np, tm, tn, tk, sIdx, sG, smask, sA, sB);
+        shift_pass<R, C, true>(0, ng, p, np, sMNK, sIdx, sG, smask, sA, sB);
         __syncthreads();
-        shift_pass<R, C, true>(1, ng, p, np, tm, tn, tk, sIdx, sG, smask, sB, sA);
+        shift_pass<R, C, true>(1, ng, p, np, sMNK, sIdx, sG, smask, sB, sA);
         __syncthreads();
-        shift_pass<R, C, true>(2, ng, p, np, tm, tn, tk, sIdx, sG, smask, sA, sB);
+        shift_pass<R, C, true>(2, ng, p, np, sMNK, sIdx, sG, smask, sA, sB);
         __syncthreads();
         for (int t = tid; t < np * C; t += MM_T) {
             R sum = g0 == 0 ? (R)0 : sS[t];
@@ -150,7 +193,7 @@ __global__ void __launch_bounds__(MM_T) k_m2m_sep(int off, int cnt, const int *_
     }
     __syncthreads();
     for (int a = tid; a < np; a += MM_T) {
-        const R sc = (R)ldexp(1.0, -(tm[a] + tn[a] + tk[a]));
+        const R sc = deg_scale<R>(sMNK[a]);
 #pragma unroll
         for (int c = 0; c < C; c++) M[((size_t)b * nps + a) * C + c] = sS[(size_t)a * C + c] * sc;
     }
@@ -159,11 +202,10 @@ __global__ void __launch_bounds__(MM_T) k_m2m_sep(int off, int cnt, const int *_
 template <class R, int C>
 __global__ void __launch_bounds__(MM_T) k_l2l_sep(int off, int cnt, const int *__restrict__ parent,
                                                   const int *__restrict__ ix, const int *__restrict__ iy,
-                                                  const int *__restrict__ iz, int p, int np, int nps, int pt1, int npo,
-                                                  const int *__restrict__ tm,
-                                                  const int *__restrict__ tn, const int *__restrict__ tk,
-                                                  const int *__restrict__ idx3, const double *__restrict__ binom,
-                                                  R *__restrict__ L, const int *__restrict__ skip) {
+                                                  const int *__restrict__ iz, int p, int np, int nps, int npo,
+                                                  const int *__restrict__ tm, const int *__restrict__ tn,
+                                                  const int *__restrict__ tk, R *__restrict__ L,
+                                                  const int *__restrict__ skip) {
     if (skip && *skip) return;
     extern __shared__ unsigned char smem_raw[];
     const int P1 = p + 1;
@@ -171,21 +213,34 @@ __global__ void __launch_bounds__(MM_T) k_l2l_sep(int off, int cnt, const int *_
     R *sB = sA + (size_t)np * C;                             // [np][C]
     R *sG = sB + (size_t)np * C;                             // [P1][P1]
     short *sIdx = (short *)(sG + P1 * P1);                   // [P1^3]
+    int *sMNK = (int *)((unsigned char *)sG + (shift_tab_bytes<R>(p, np) - 4 * (size_t)np - 16));   // [np]
     __shared__ int smask[1];
     if (blockIdx.x >= cnt) return;
     const int b = off + blockIdx.x, pa = parent[b], tid = threadIdx.x;
-    for (int t = tid; t < np * C; t += MM_T) sA[t] = L[(size_t)pa * nps * C + t];   // the parent's np coefficients
-    shift_tables<R>(p, pt1, idx3, binom, false, sIdx, sG);
+    // the parent's np coefficients, all of a thread's in flight before the tables
+    constexpr int U = 2 * C;
+    const int nt = np * C;
+    R v[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        const int t = tid + u * MM_T;
+        v[u] = t < nt ? L[(size_t)pa * nps * C + t] : (R)0;
+    }
     if (tid == 0) smask[0] = ((ix[b] & 1) ? 0 : 1) | ((iy[b] & 1) ? 0 : 2) | ((iz[b] & 1) ? 0 : 4);
+    shift_tables<R>(p, np, tm, tn, tk, false, sIdx, sG, sMNK);
+#pragma unroll
+    for (int u = 0; u < U; u++)
+        if (tid + u * MM_T < nt) sA[tid + u * MM_T] = v[u];
+    for (int t = tid + U * MM_T; t < nt; t += MM_T) sA[t] = L[(size_t)pa * nps * C + t];
     __syncthreads();
-    shift_pass<R, C, false>(2, 1, p, np, tm, tn, tk, sIdx, sG, smask, sA, sB);
+    shift_pass<R, C, false>(2, 1, p, np, sMNK, sIdx, sG, smask, sA, sB);
     __syncthreads();
-    shift_pass<R, C, false>(1, 1, p, np, tm, tn, tk, sIdx, sG, smask, sB, sA);
+    shift_pass<R, C, false>(1, 1, p, np, sMNK, sIdx, sG, smask, sB, sA);
     __syncthreads();
-    shift_pass<R, C, false>(0, 1, p, np, tm, tn, tk, sIdx, sG, smask, sA, sB);
+    shift_pass<R, C, false>(0, 1, p, np, sMNK, sIdx, sG, smask, sA, sB);
     __syncthreads();
-    for (int a = tid; a < npo; a += MM_T) {         // the child keeps its own order's npo coefficients
-        const R sc = (R)ldexp(1.0, -(tm[a] + tn[a] + tk[a]));
+    for (int a = tid; a < npo; a += MM_T) {         // the child keeps its own order's npo coefficients (npo <= np)
+        const R sc = deg_scale<R>(sMNK[a]);
 #pragma unroll
         for (int c = 0; c < C; c++) L[((size_t)b * nps + a) * C + c] += sB[(size_t)a * C + c] * sc;
     }
@@ -442,17 +497,17 @@ static int level_order(const bem_plan *P, int l) {
 template <class R, int C>
 int launch_m2m(bem_plan *P, R *M, cudaStream_t s, int lmin) {
     const Tree &t = P->t;
-    const int nps = P->mi.np, pt1 = P->mi.p + 1;
+    const int nps = P->mi.np;
     const int *sk = P->skip;
     for (int l = t.nlev - 2; l >= std::max(0, lmin); l--) {
         const int off = t.lev_off[l], cnt = t.lev_off[l + 1] - off;
-        const int p = level_order(P, l), np = np_host(p), npc = np_host(level_order(P, l + 1)), P1 = p + 1;
-        const size_t tab_sm = sizeof(R) * P1 * P1 + sizeof(short) * P1 * P1 * P1 + 16;
+        const int p = level_order(P, l), np = np_host(p), npc = np_host(level_order(P, l + 1));
+        const size_t tab_sm = shift_tab_bytes<R>(p, np);
         int grp = 8;                             // children shifted together (shared memory permitting)
         while (grp > 1 && sizeof(R) * (2 * grp + 1) * np * C + tab_sm > 220 * 1024) grp /= 2;
         const size_t m2m_sm = sizeof(R) * (2 * grp + 1) * np * C + tab_sm;
-        (k_m2m_sep<R, C><<<cnt, MM_T, m2m_sm, s>>>(off, cnt, t.child0, t.nchild, t.ix, t.iy, t.iz, p, np, nps, pt1, npc,
-                                                   grp, P->d_m, P->d_n, P->d_k, P->d_idx3, P->d_binom, M, sk),
+        (k_m2m_sep<R, C><<<cnt, MM_T, m2m_sm, s>>>(off, cnt, t.child0, t.nchild, t.ix, t.iy, t.iz, p, np, nps, npc, grp,
+                                                   P->d_m, P->d_n, P->d_k, M, sk),
          ::bem::count_launch());
     }
     BEM_LAUNCH_CHECK();
@@ -481,11 +536,11 @@ int launch_translations(bem_plan *P, R *M, R *L, cudaStream_t s, cudaEvent_t *ev
     for (int l = std::max(1, P->m2l_tgt_lmin + 1); l < t.nlev; l++) {
         // the shift runs at the parent's order; the child keeps its own order's terms
         const int off = t.lev_off[l], cnt = t.lev_off[l + 1] - off;
-        const int p = level_order(P, l - 1), pnp = np_host(p), npo = np_host(level_order(P, l)), P1 = p + 1;
-        const size_t tab_sm = sizeof(R) * P1 * P1 + sizeof(short) * P1 * P1 * P1 + 16;
+        const int p = level_order(P, l - 1), pnp = np_host(p), npo = np_host(level_order(P, l));
+        const size_t tab_sm = shift_tab_bytes<R>(p, pnp);
         (k_l2l_sep<R, C><<<cnt, MM_T, sizeof(R) * 2 * pnp * C + tab_sm, s>>>(off, cnt, t.parent, t.ix, t.iy, t.iz, p,
-                                                                           pnp, np, P->mi.p + 1, npo, P->d_m, P->d_n,
-                                                                           P->d_k, P->d_idx3, P->d_binom, L, sk),
+                                                                           pnp, np, npo, P->d_m, P->d_n, P->d_k, L,
+                                                                           sk),
          ::bem::count_launch());
     }
     BEM_LAUNCH_CHECK();
