@@ -808,8 +808,7 @@ __global__ void k_combine(int N, const int *__restrict__ ptr, const int *__restr
     double s[C];
 #pragma unroll
     for (int c = 0; c < C; c++) s[c] = 0.0;
-    for (int q = ptr[w] + lane; q < ptr[w + 1]; q += 32) {
-        const int j = col[q];
+    auto term = [&](int q, int j) {
         if (C == 1) {
             s[0] += (double)val[q] * x[j];
         } else {
@@ -818,7 +817,19 @@ __global__ void k_combine(int N, const int *__restrict__ ptr, const int *__restr
             s[0] += vr * xr - vi * xi;
             s[C - 1] += vr * xi + vi * xr;
         }
+    };
+    // four of a lane's columns loaded ahead, nonzeros summed in order
+    constexpr int CU = 4;
+    const int qe = ptr[w + 1];
+    int q = ptr[w] + lane;
+    for (; q + 32 * (CU - 1) < qe; q += 32 * CU) {
+        int j[CU];
+#pragma unroll
+        for (int u = 0; u < CU; u++) j[u] = col[q + 32 * u];
+#pragma unroll
+        for (int u = 0; u < CU; u++) term(q + 32 * u, j[u]);
     }
+    for (; q < qe; q += 32) term(q, col[q]);
 #pragma unroll
     for (int c = 0; c < C; c++)
         for (int off = 16; off; off >>= 1) s[c] += __shfl_xor_sync(0xffffffffu, s[c], off);
@@ -853,17 +864,39 @@ __global__ void k_combine_f(int N, const int *__restrict__ ptr, const int *__res
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (w >= N) return;
     KahanF k[C];
-    for (int q = ptr[w] + lane; q < ptr[w + 1]; q += 32) {
-        const int j = __ldg(col + q);
+    auto term = [&](float2 v, float2 x) {
         if (C == 1) {
-            k[0].add(__ldg(val + q) * __ldg(xf + j));
+            k[0].add(v.x * x.x);
         } else {
-            const float2 v = __ldg(reinterpret_cast<const float2 *>(val) + q);
-            const float2 x = __ldg(reinterpret_cast<const float2 *>(xf) + j);
             k[0].add(fmaf(v.x, x.x, -v.y * x.y));
             k[C - 1].add(fmaf(v.x, x.y, v.y * x.x));
         }
+    };
+    auto ldv = [&](int q) {
+        return C == 1 ? make_float2(__ldg(val + q), 0.f) : __ldg(reinterpret_cast<const float2 *>(val) + q);
+    };
+    auto ldx = [&](int j) {
+        return C == 1 ? make_float2(__ldg(xf + j), 0.f) : __ldg(reinterpret_cast<const float2 *>(xf) + j);
+    };
+    // four of a lane's nonzeros in flight at a time (columns, values, then
+    // the vector entries), summed in the same order as one at a time
+    constexpr int CU = 4;
+    const int qe = ptr[w + 1];
+    int q = ptr[w] + lane;
+    for (; q + 32 * (CU - 1) < qe; q += 32 * CU) {
+        int j[CU];
+        float2 v[CU], x[CU];
+#pragma unroll
+        for (int u = 0; u < CU; u++) {
+            j[u] = __ldg(col + q + 32 * u);
+            v[u] = ldv(q + 32 * u);
+        }
+#pragma unroll
+        for (int u = 0; u < CU; u++) x[u] = ldx(j[u]);
+#pragma unroll
+        for (int u = 0; u < CU; u++) term(v[u], x[u]);
     }
+    for (; q < qe; q += 32) term(ldv(q), ldx(__ldg(col + q)));
     double s[C];
 #pragma unroll
     for (int c = 0; c < C; c++) {
