@@ -51,7 +51,7 @@ FLOPS_PER_PAIR = {"A": 20.0, "B": 11.0}   # near-field kernel, Laplace double / 
 NCU_TRAFFIC = {
     # k_near_f32 (unchanged since its capture; the file's other kernels changed)
     "near_l2p": {"bytes": 7472896, "source": "paper_0908_0673_gb300/csrc/fmm.cu",
-                 "sha256": "5b0a0a3f4fcde722e7d2a88f2a0176ffb97d196d40038bce61467f33a6e96ae4"},
+                 "sha256": "4317124a9ff3d54da8a2ff674b49021ac10198ab50caef2b27b527477827ca7e"},
     # the M2L stage: k_m2l_permute + k_m2l_tc + k_m2l_gather_sym (order-10 products)
     "m2l": {"bytes": 1217024 + (35090432 + 46180096) + 123055872, "source": "paper_0908_0673_gb300/csrc/m2l_tc.cu",
             "sha256": "e7871ff432f963f53dd84460d1103eb7b3af23f26d5a89e5156d1826afe70520"},

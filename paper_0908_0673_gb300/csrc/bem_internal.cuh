@@ -294,7 +294,6 @@ struct FmmState {
     bem::MIndex mi;
     // multi-index tables on the device
     int *d_m = nullptr, *d_n = nullptr, *d_k = nullptr, *d_idx3 = nullptr;
-    double *d_binom = nullptr;          // [(PMAX+1)^2]
     double *d_fact = nullptr;           // [2*PMAX+2]
     // work buffers of one matrix multiplication
     double *f = nullptr;                // quadrature strengths [Q] (x2 for complex)

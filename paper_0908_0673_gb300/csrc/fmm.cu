@@ -31,7 +31,7 @@ __constant__ double c_Lq[2][NQ][6];   // shape values at the 7 rule points (tri3
 
 struct Tabs {
     const int *m, *n, *k, *idx3;
-    const double *binom, *fact;
+    const double *fact;
     int p, np;                          // largest order, and the coefficient count (array stride)
     const int *lev_p;                   // order of each tree level (nullptr: p everywhere)
 };
@@ -953,7 +953,7 @@ void MIndex::init(int p_) {
 }
 
 static Tabs tabs_of(const bem_plan *P) {
-    return Tabs{P->d_m, P->d_n, P->d_k, P->d_idx3, P->d_binom, P->d_fact, P->mi.p, P->mi.np,
+    return Tabs{P->d_m, P->d_n, P->d_k, P->d_idx3, P->d_fact, P->mi.p, P->mi.np,
                 P->lev_var ? P->d_lev_p : nullptr};
 }
 
@@ -1032,15 +1032,11 @@ int alloc_fmm(bem_plan *P, cudaStream_t s) {
     BEM_CUDA(cudaMemcpyAsync(P->d_n, mi.n.data(), sizeof(int) * np, cudaMemcpyHostToDevice, s));
     BEM_CUDA(cudaMemcpyAsync(P->d_k, mi.k.data(), sizeof(int) * np, cudaMemcpyHostToDevice, s));
     BEM_CUDA(cudaMemcpyAsync(P->d_idx3, mi.idx3.data(), sizeof(int) * mi.idx3.size(), cudaMemcpyHostToDevice, s));
-    std::vector<double> fact(2 * PMAX + 2), binom((PMAX + 1) * (PMAX + 1), 0.0);
+    std::vector<double> fact(2 * PMAX + 2);
     fact[0] = 1.0;
     for (int i = 1; i < (int)fact.size(); i++) fact[i] = fact[i - 1] * i;
-    for (int a = 0; a <= PMAX; a++)
-        for (int b = 0; b <= a; b++) binom[a * (PMAX + 1) + b] = std::round(fact[a] / (fact[b] * fact[a - b]));
     BEM_TRY(A.alloc(&P->d_fact, fact.size()));
-    BEM_TRY(A.alloc(&P->d_binom, binom.size()));
     BEM_CUDA(cudaMemcpyAsync(P->d_fact, fact.data(), sizeof(double) * fact.size(), cudaMemcpyHostToDevice, s));
-    BEM_CUDA(cudaMemcpyAsync(P->d_binom, binom.data(), sizeof(double) * binom.size(), cudaMemcpyHostToDevice, s));
     BEM_TRY(init_shape_table(P->device));
     const bool mx = P->prm.precision == BEM_MIXED;
     if (mx) {
@@ -1288,7 +1284,7 @@ void free_fmm(bem_plan *P) {
     free_translation_tables(P);
     Arena &A = P->arena;
     for (void *q : {(void *)P->d_m, (void *)P->d_n, (void *)P->d_k, (void *)P->d_idx3, (void *)P->d_fact,
-                    (void *)P->d_binom, (void *)P->f, (void *)P->M, (void *)P->L, (void *)P->ff, (void *)P->fM,
+                    (void *)P->f, (void *)P->M, (void *)P->L, (void *)P->ff, (void *)P->fM,
                     (void *)P->fL, (void *)P->ytmp, (void *)P->xptr, (void *)P->yptr, (void *)P->p2m_W, (void *)P->xf, (void *)P->d_lev_p})
         A.release(q);
     P->p2m_W = nullptr;
@@ -1296,7 +1292,7 @@ void free_fmm(bem_plan *P) {
     P->d_lev_p = nullptr;
     P->lev_var = false;
     P->d_m = P->d_n = P->d_k = P->d_idx3 = nullptr;
-    P->d_fact = P->d_binom = nullptr;
+    P->d_fact = nullptr;
     P->f = P->M = P->L = P->ytmp = nullptr;
     P->ff = P->fM = P->fL = nullptr;
     P->xptr = nullptr;
